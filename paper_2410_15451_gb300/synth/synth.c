@@ -1,0 +1,278 @@
+/*
+ * Seeded synthetic inputs for dynamic Leiden: graphs and batch updates.
+ *
+ * This module holds no part of the community-detection arithmetic.  It only
+ * draws graphs and edge batches whose shapes follow the paper's workloads
+ * (random batch updates with an 80:20 insertion:deletion mix, unit weights,
+ * undirected, no new vertices -- Section 4.1.3 "Batch generation"), and it is
+ * the one piece of code shared by the CUDA path's tests and the CPU oracle's.
+ *
+ * Every random number is a pure function of (seed, stream, counter): the
+ * SplitMix64 output function (Steele, Lea and Flood, "Fast splittable
+ * pseudorandom number generators", OOPSLA 2014) applied to
+ * seed + (counter + 1) * 0x9E3779B97F4A7C15, with the stream folded into the
+ * seed.  The result does not depend on thread count or call order.
+ *
+ * All graphs are returned as symmetric CSR (int64 offsets, int32 columns and
+ * int32 weights), rows sorted by column, without self-loops or duplicates.
+ * Buffers are malloc'd here and released with synth_free().
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+
+#define GOLDEN 0x9E3779B97F4A7C15ULL
+
+static inline uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+static inline uint64_t rng_u64(uint64_t seed, uint64_t stream, uint64_t ctr) {
+  uint64_t s = mix64(seed ^ (stream * 0xD1B54A32D192ED03ULL + 0x8CB92BA72F3D8DD7ULL));
+  return mix64(s + (ctr + 1) * GOLDEN);
+}
+
+/* Uniform integer in [0, n): Lemire's multiply-shift on the top 32 bits is
+ * not enough for n > 2^32, so use the 128-bit product of a 64-bit draw. */
+static inline uint64_t rng_below(uint64_t seed, uint64_t stream, uint64_t ctr, uint64_t n) {
+  unsigned __int128 p = (unsigned __int128)rng_u64(seed, stream, ctr) * n;
+  return (uint64_t)(p >> 64);
+}
+
+/* ---------------------------------------------------------------- sorting */
+
+/* LSD radix sort of 64-bit keys on their low `bits` bits (8-bit digits). */
+static void radix_sort_u64(uint64_t *a, int64_t n, int bits) {
+  if (n <= 1) return;
+  uint64_t *tmp = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+  uint64_t *src = a, *dst = tmp;
+  for (int shift = 0; shift < bits; shift += 8) {
+    int64_t count[257];
+    memset(count, 0, sizeof(count));
+    for (int64_t i = 0; i < n; i++) count[((src[i] >> shift) & 255) + 1]++;
+    for (int d = 0; d < 256; d++) count[d + 1] += count[d];
+    for (int64_t i = 0; i < n; i++) dst[count[(src[i] >> shift) & 255]++] = src[i];
+    uint64_t *t = src; src = dst; dst = t;
+  }
+  if (src != a) memcpy(a, src, (size_t)n * sizeof(uint64_t));
+  free(tmp);
+}
+
+static int bits_for(int64_t n) {
+  int b = 1;
+  while (((int64_t)1 << b) < n) b++;
+  return b;
+}
+
+/* Turn a list of undirected pairs (u, v), u != v, into a symmetric CSR with
+ * unit weights.  Keys are (src << 32 | dst); duplicates collapse. */
+static int build_csr_from_pairs(int64_t n, const int64_t *u, const int64_t *v, int64_t m,
+                                int64_t **off_out, int32_t **col_out, int32_t **w_out,
+                                int64_t *arcs_out) {
+  uint64_t *keys = (uint64_t *)malloc((size_t)(2 * m + 1) * sizeof(uint64_t));
+  if (!keys) return -1;
+  int64_t k = 0;
+  for (int64_t e = 0; e < m; e++) {
+    if (u[e] == v[e]) continue;
+    keys[k++] = ((uint64_t)u[e] << 32) | (uint64_t)v[e];
+    keys[k++] = ((uint64_t)v[e] << 32) | (uint64_t)u[e];
+  }
+  int vb = bits_for(n);
+  radix_sort_u64(keys, k, 32 + vb);
+  int64_t uniq = 0;
+  for (int64_t i = 0; i < k; i++)
+    if (i == 0 || keys[i] != keys[i - 1]) keys[uniq++] = keys[i];
+  int64_t *off = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+  int32_t *col = (int32_t *)malloc((size_t)(uniq + 1) * sizeof(int32_t));
+  int32_t *w = (int32_t *)malloc((size_t)(uniq + 1) * sizeof(int32_t));
+  if (!off || !col || !w) { free(keys); free(off); free(col); free(w); return -1; }
+  for (int64_t i = 0; i < uniq; i++) {
+    off[(keys[i] >> 32) + 1]++;
+    col[i] = (int32_t)(keys[i] & 0xffffffffULL);
+    w[i] = 1;
+  }
+  for (int64_t i = 0; i < n; i++) off[i + 1] += off[i];
+  free(keys);
+  *off_out = off; *col_out = col; *w_out = w; *arcs_out = uniq;
+  return 0;
+}
+
+void synth_free(void *p) { free(p); }
+
+/* ------------------------------------------------------ planted partition */
+
+typedef struct { uint64_t *k; int64_t cap; } keyset; /* open addressing, 0 = empty */
+
+static int keyset_insert(keyset *s, uint64_t key) { /* key must be != 0; returns 1 if new */
+  uint64_t h = mix64(key) & (uint64_t)(s->cap - 1);
+  while (s->k[h]) {
+    if (s->k[h] == key) return 0;
+    h = (h + 1) & (uint64_t)(s->cap - 1);
+  }
+  s->k[h] = key;
+  return 1;
+}
+
+static uint64_t pair_key(int64_t a, int64_t b) {
+  int64_t x = a < b ? a : b, y = a < b ? b : a;
+  return (((uint64_t)x << 32) | (uint64_t)y) + 1;
+}
+
+/* n vertices in `blocks` equal consecutive blocks; exactly round(n*k_in/2)
+ * distinct edges drawn uniformly inside blocks and round(n*k_out/2) distinct
+ * edges drawn uniformly across blocks, where k_in = (1-mu)*avg_deg and
+ * k_out = mu*avg_deg (repeated pairs and self-pairs are redrawn). */
+int synth_planted_partition(int64_t n, int64_t blocks, double avg_deg, double mu, uint64_t seed,
+                            int64_t **off, int32_t **col, int32_t **w, int64_t *arcs) {
+  if (n < 2 || blocks < 1 || blocks > n) return -1;
+  int64_t bs = n / blocks;
+  int64_t m_in = (int64_t)llround((double)n * (1.0 - mu) * avg_deg / 2.0);
+  int64_t m_out = (int64_t)llround((double)n * mu * avg_deg / 2.0);
+  if (blocks == 1) { m_in += m_out; m_out = 0; }
+  /* cap the request at the number of available pairs */
+  double in_pairs = (double)blocks * (double)bs * (double)(bs - 1) / 2.0;
+  if ((double)m_in > 0.9 * in_pairs) m_in = (int64_t)(0.9 * in_pairs);
+  int64_t m = m_in + m_out;
+  int64_t *u = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+  int64_t *v = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+  int64_t cap = 16;
+  while (cap < 2 * m + 16) cap <<= 1;
+  keyset s = {(uint64_t *)calloc((size_t)cap, sizeof(uint64_t)), cap};
+  if (!u || !v || !s.k) { free(u); free(v); free(s.k); return -1; }
+  int64_t got = 0;
+  for (uint64_t t = 0; got < m_in; t++) {
+    int64_t b = (int64_t)rng_below(seed, 1, 3 * t, (uint64_t)blocks);
+    int64_t lo = b * bs, sz = (b == blocks - 1) ? n - lo : bs;
+    int64_t x = lo + (int64_t)rng_below(seed, 1, 3 * t + 1, (uint64_t)sz);
+    int64_t y = lo + (int64_t)rng_below(seed, 1, 3 * t + 2, (uint64_t)sz);
+    if (x == y || !keyset_insert(&s, pair_key(x, y))) continue;
+    u[got] = x; v[got] = y; got++;
+  }
+  for (uint64_t t = 0; got < m; t++) {
+    /* one endpoint uniform over all vertices, the other uniform inside a
+     * uniformly chosen different block */
+    int64_t x = (int64_t)rng_below(seed, 2, 3 * t, (uint64_t)n);
+    int64_t bx = x / bs < blocks ? x / bs : blocks - 1;
+    int64_t by = (bx + 1 + (int64_t)rng_below(seed, 2, 3 * t + 1, (uint64_t)(blocks - 1))) % blocks;
+    int64_t lo = by * bs, sz = (by == blocks - 1) ? n - lo : bs;
+    int64_t y = lo + (int64_t)rng_below(seed, 2, 3 * t + 2, (uint64_t)sz);
+    if (!keyset_insert(&s, pair_key(x, y))) continue;
+    u[got] = x; v[got] = y; got++;
+  }
+  free(s.k);
+  int rc = build_csr_from_pairs(n, u, v, m, off, col, w, arcs);
+  free(u); free(v);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ R-MAT */
+
+/* R-MAT (Chakrabarti, Zhan, Faloutsos 2004): 2^scale vertices and
+ * edge_factor * 2^scale sampled edges; each edge descends `scale` levels of
+ * the adjacency quadrants with probabilities (a, b, c, 1-a-b-c).  Vertex IDs
+ * are then relabelled by a seeded random permutation, as the Graph500
+ * generator does, so that degree is not correlated with ID.  The result is
+ * symmetrised and deduplicated, and self-loops are dropped. */
+int synth_rmat(int scale, int64_t edge_factor, double a, double b, double c, uint64_t seed,
+               int64_t **off, int32_t **col, int32_t **w, int64_t *arcs) {
+  if (scale < 1 || scale > 30) return -1;
+  int64_t n = (int64_t)1 << scale;
+  int64_t m = edge_factor * n;
+  uint32_t ta = (uint32_t)llround(a * 65536.0);
+  uint32_t tb = (uint32_t)llround((a + b) * 65536.0);
+  uint32_t tc = (uint32_t)llround((a + b + c) * 65536.0);
+  int64_t *perm = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  int64_t *u = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+  int64_t *v = (int64_t *)malloc((size_t)m * sizeof(int64_t));
+  if (!perm || !u || !v) { free(perm); free(u); free(v); return -1; }
+  for (int64_t i = 0; i < n; i++) perm[i] = i;
+  for (int64_t i = n - 1; i > 0; i--) { /* Fisher-Yates */
+    int64_t j = (int64_t)rng_below(seed, 7, (uint64_t)i, (uint64_t)(i + 1));
+    int64_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+  }
+  for (int64_t e = 0; e < m; e++) {
+    int64_t x = 0, y = 0;
+    uint64_t r = 0;
+    for (int l = 0; l < scale; l++) {
+      if ((l & 3) == 0) r = rng_u64(seed, 8, (uint64_t)e * 8 + (uint64_t)(l >> 2));
+      uint32_t q = (uint32_t)(r & 0xffff);
+      r >>= 16;
+      int bx = 0, by = 0;
+      if (q < ta) { } else if (q < tb) { by = 1; } else if (q < tc) { bx = 1; } else { bx = 1; by = 1; }
+      x = (x << 1) | bx;
+      y = (y << 1) | by;
+    }
+    u[e] = perm[x];
+    v[e] = perm[y];
+  }
+  free(perm);
+  int rc = build_csr_from_pairs(n, u, v, m, off, col, w, arcs);
+  free(u); free(v);
+  return rc;
+}
+
+/* ---------------------------------------------------------- batch updates */
+
+static int has_edge(const int64_t *off, const int32_t *col, int64_t u, int64_t v) {
+  int64_t lo = off[u], hi = off[u + 1];
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (col[mid] < v) lo = mid + 1; else hi = mid;
+  }
+  return lo < off[u + 1] && col[lo] == v;
+}
+
+/* A random batch on the CSR graph (off, col) of n vertices: n_del distinct
+ * existing undirected edges chosen uniformly (by drawing a uniform arc and
+ * keeping its undirected edge once), and n_ins distinct vertex pairs u != v
+ * chosen uniformly among pairs that are not edges of the graph, each with
+ * weight drawn uniformly from [w_lo, w_hi].  Edges are written as (u, v, w)
+ * triples, one per undirected edge, into del3 (w = stored weight) and ins3. */
+int synth_batch(int64_t n, const int64_t *off, const int32_t *col, const int32_t *wt,
+                int64_t n_del, int64_t n_ins, int32_t w_lo, int32_t w_hi, uint64_t seed,
+                int32_t *del3, int32_t *ins3) {
+  int64_t arcs = off[n];
+  if (n < 2) return -1;
+  if (n_del > arcs / 2) return -2;
+  int64_t cap = 16;
+  while (cap < 2 * (n_del + n_ins) + 16) cap <<= 1;
+  keyset s = {(uint64_t *)calloc((size_t)cap, sizeof(uint64_t)), cap};
+  if (!s.k) return -1;
+  int64_t got = 0;
+  for (uint64_t t = 0; got < n_del; t++) {
+    if (t > (uint64_t)(64 * (n_del + 16))) { free(s.k); return -3; }
+    int64_t a = (int64_t)rng_below(seed, 11, t, (uint64_t)arcs);
+    int64_t lo = 0, hi = n; /* row of arc a */
+    while (hi - lo > 1) {
+      int64_t mid = (lo + hi) >> 1;
+      if (off[mid] <= a) lo = mid; else hi = mid;
+    }
+    int64_t u = lo, v = col[a];
+    if (!keyset_insert(&s, pair_key(u, v))) continue;
+    del3[3 * got] = (int32_t)u; del3[3 * got + 1] = (int32_t)v; del3[3 * got + 2] = wt ? wt[a] : 1;
+    got++;
+  }
+  got = 0;
+  for (uint64_t t = 0; got < n_ins; t++) {
+    if (t > (uint64_t)(64 * (n_ins + 16))) { free(s.k); return -3; }
+    int64_t u = (int64_t)rng_below(seed, 12, 2 * t, (uint64_t)n);
+    int64_t v = (int64_t)rng_below(seed, 12, 2 * t + 1, (uint64_t)n);
+    if (u == v || has_edge(off, col, u, v)) continue;
+    if (!keyset_insert(&s, pair_key(u, v))) continue;
+    int32_t wv = w_lo;
+    if (w_hi > w_lo) wv = w_lo + (int32_t)rng_below(seed, 13, t, (uint64_t)(w_hi - w_lo + 1));
+    ins3[3 * got] = (int32_t)u; ins3[3 * got + 1] = (int32_t)v; ins3[3 * got + 2] = wv;
+    got++;
+  }
+  free(s.k);
+  return 0;
+}
+
+/* Uniform integers in [0, n) for (seed, stream): used by callers that need
+ * seeded choices (e.g. which configuration sample to time). */
+void synth_uniform(uint64_t seed, uint64_t stream, int64_t count, uint64_t n, int64_t *out) {
+  for (int64_t i = 0; i < count; i++) out[i] = (int64_t)rng_below(seed, stream, (uint64_t)i, n);
+}

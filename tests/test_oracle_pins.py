@@ -1,0 +1,424 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics
+(no GPU).  Each test names what it pins; none re-types the oracle's own code.
+"""
+from __future__ import annotations
+
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_15451_gb300 import synth
+from tests.helpers import (components, csr_from_edges, disconnected_communities, newman_numerator,
+                           set_partitions)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SCHEDULES = [oracle.SEQ, oracle.SYNC]
+
+
+def clique_edges(base, k):
+    return [(base + a, base + b) for a in range(k) for b in range(a + 1, k)]
+
+
+def random_graph(n, p, seed, wmax=1, loops=False):
+    rng = np.random.default_rng(seed)
+    edges, ws = [], []
+    for u in range(n):
+        for v in range(u + (0 if loops else 1), n):
+            if rng.random() < p:
+                edges.append((u, v))
+                ws.append(int(rng.integers(1, wmax + 1)))
+    return csr_from_edges(n, edges, ws)
+
+
+# ---------------------------------------------------------------- Eq. 1
+
+def _closed_form_cases():
+    with open(os.path.join(GOLDEN, "modularity_closed_forms.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            fam, n, k, num, den = line.split()
+            yield fam, int(n), int(k), Fraction(int(num), int(den))
+
+
+@pytest.mark.parametrize("case", list(_closed_form_cases()), ids=lambda c: f"{c[0]}-{c[1]}x{c[2]}")
+def test_modularity_closed_forms(case):
+    """Eq. 1 on disjoint cliques (1 - 1/n) and rings of cliques (L/(L+1) - 1/n)."""
+    fam, n, k, expect = case
+    edges = []
+    for c in range(n):
+        edges += clique_edges(c * k, k)
+    if fam == "ring":
+        for c in range(n):
+            edges.append((c * k, ((c + 1) % n) * k + 1))
+    off, col, w = csr_from_edges(n * k, edges)
+    C = np.repeat(np.arange(n), k).astype(np.int32) * k  # community id = first vertex
+    q, num = oracle.modularity(off, col, w, C)
+    m2 = int(w.sum())
+    assert Fraction(num, m2 * m2) == expect
+    assert q == pytest.approx(float(expect), abs=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_modularity_matches_newman_pairwise_form(seed):
+    """Eq. 1 equals Newman's pairwise form, exactly, with weights and self-loops."""
+    n = 12
+    off, col, w = random_graph(n, 0.35, seed, wmax=5, loops=True)
+    rng = np.random.default_rng(100 + seed)
+    C = rng.integers(0, 4, n).astype(np.int32)
+    q, num = oracle.modularity(off, col, w, C)
+    assert num == newman_numerator(off, col, w, C)
+    assert -0.5 <= q <= 1.0  # range stated in Section 3.2
+
+
+# ---------------------------------------------------------------- Eq. 2
+
+@pytest.mark.parametrize("seed", range(5))
+def test_delta_modularity_is_exact_change_of_q(seed):
+    """dQ of Eq. 2 (times 2m^2) equals Q(after) - Q(before) for every single
+    move, in exact integers: 2 g = numerator(after) - numerator(before).
+    Uses self-loops so that K_{i->c} must exclude i itself."""
+    n = 10
+    off, col, w = random_graph(n, 0.4, seed, wmax=4, loops=True)
+    rng = np.random.default_rng(200 + seed)
+    C = rng.integers(0, 4, n).astype(np.int32)
+    before = newman_numerator(off, col, w, C)
+    for i in range(n):
+        for c in range(4):
+            g = oracle.move_gain(off, col, w, C, i, c)
+            C2 = C.copy()
+            C2[i] = c
+            assert 2 * g == newman_numerator(off, col, w, C2) - before
+
+
+# ------------------------------------------------- optimum on tiny graphs
+
+TINY = {
+    "two_triangles_bridge": (6, [(0, 1), (0, 2), (1, 2), (3, 4), (3, 5), (4, 5), (2, 3)]),
+    "two_k4_bridge": (8, clique_edges(0, 4) + clique_edges(4, 4) + [(3, 4)]),
+    "three_k3_ring": (9, clique_edges(0, 3) + clique_edges(3, 3) + clique_edges(6, 3) + [(0, 3), (3, 6), (6, 0)]),
+}
+
+
+def brute_force_best(off, col, w):
+    n = len(off) - 1
+    m2 = int(w.sum())
+    best = None
+    for part in set_partitions(n):
+        num = newman_numerator(off, col, w, part)
+        if best is None or num > best:
+            best = num
+    return Fraction(best, m2 * m2)
+
+
+@pytest.mark.parametrize("name", sorted(TINY))
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_static_reaches_brute_force_optimum_on_easy_graphs(name, schedule):
+    """Leiden's result never beats the optimum and reaches it on these graphs."""
+    n, edges = TINY[name]
+    off, col, w = csr_from_edges(n, edges)
+    opt = brute_force_best(off, col, w)
+    o = oracle.Oracle(n, off, col, w.astype(np.int32), schedule=schedule)
+    C = o.static()
+    _, num = oracle.modularity(off, col, w, C)
+    m2 = int(w.sum())
+    assert Fraction(num, m2 * m2) == opt
+
+
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_static_never_exceeds_optimum(seed, schedule):
+    n = 8
+    off, col, w = random_graph(n, 0.45, seed, wmax=3)
+    if w.sum() == 0:
+        pytest.skip("empty graph")
+    opt = brute_force_best(off, col, w)
+    o = oracle.Oracle(n, off, col, w.astype(np.int32), schedule=schedule)
+    C = o.static()
+    _, num = oracle.modularity(off, col, w, C)
+    m2 = int(w.sum())
+    got = Fraction(num, m2 * m2)
+    assert got <= opt
+    assert got >= opt - Fraction(1, 5)  # heuristic, but not far off on 8 vertices
+
+
+# ----------------------------------------------- aggregation (Alg. leidenag)
+
+@pytest.mark.parametrize("seed", range(4))
+def test_aggregation_preserves_modularity(seed):
+    """Q(G', singletons) == Q(G, C) exactly, and total weight is preserved."""
+    g = synth.planted_partition(300, 6, 10, 0.3, seed + 7)
+    rng = np.random.default_rng(seed)
+    C = rng.integers(0, 25, g.n).astype(np.int32)
+    uniq, C = np.unique(C, return_inverse=True)
+    C = C.astype(np.int32)
+    w = g.w.astype(np.int64)
+    _, num = oracle.modularity(g.off, g.col, w, C)
+    yo, yc, yw = oracle.aggregate(g.off, g.col, w, C, len(uniq))
+    _, num2 = oracle.modularity(yo, yc, yw, np.arange(len(uniq), dtype=np.int32))
+    assert num == num2
+    assert yw.sum() == w.sum()
+    # rows sorted, no duplicate neighbours
+    for c in range(len(uniq)):
+        r = yc[yo[c]:yo[c + 1]]
+        assert np.all(np.diff(r) > 0)
+
+
+# --------------------------------------------------- splitting (Alg. leidensp)
+
+def test_split_caption_example():
+    """The split example of the figure on disconnected communities (golden)."""
+    spec = {}
+    with open(os.path.join(GOLDEN, "split_caption_example.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *vals = line.split()
+            spec[key] = vals
+    n = int(spec["n"][0])
+    edges = [tuple(int(x) for x in e.split("-")) for e in spec["edges"]]
+    off, col, _ = csr_from_edges(n, edges)
+    C = np.array([int(x) for x in spec["membership"]], np.int32)
+    flags = np.zeros(n, np.uint8)
+    flags[int(spec["split_flag_community"][0])] = 1
+    got = oracle.split(off, col, C, flags)
+    assert got.tolist() == [int(x) for x in spec["expected"]]
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_split_equals_bfs_components(seed):
+    """Split labels equal the connected components (min vertex id) found by
+    an independent BFS over each flagged community."""
+    n = 60
+    off, col, _ = random_graph(n, 0.05, seed)
+    rng = np.random.default_rng(seed)
+    C = rng.integers(0, 5, n).astype(np.int32)
+    flags = np.zeros(n, np.uint8)
+    flags[[0, 2, 3]] = 1
+    got = oracle.split(off, col, C, flags)
+    expect = C.copy()
+    for c in (0, 2, 3):
+        members = set(np.flatnonzero(C == c).tolist())
+        for comp in components(off, col, members):
+            expect[comp] = min(comp)
+    assert got.tolist() == expect.tolist()
+
+
+# -------------------------------------------------- static Leiden end to end
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_planted_partition_recovered(schedule):
+    """10k-vertex planted partition, 100 blocks, mixing 0.2: the planted
+    partition has Q = (1 - mu) - 1/100 = 0.79 in expectation; Leiden finds
+    100 communities, all connected, at that Q."""
+    g = synth.workload_small()
+    o = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=schedule)
+    C = o.static()
+    q = o.modularity()
+    assert abs(q - 0.79) < 0.01
+    assert len(np.unique(C)) == 100
+    assert disconnected_communities(g.off, g.col, C) == 0
+    blocks = np.arange(g.n) // 100
+    # every found community is one planted block
+    for c in np.unique(C):
+        assert len(np.unique(blocks[C == c])) == 1
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_static_ids_follow_tracking_rule(schedule):
+    """Static Leiden tracks against singletons (Alg. leiden calls leidenTrack),
+    so each community's id is its member of largest degree (ties: lowest)."""
+    g = synth.rmat(10, seed=11)
+    o = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=schedule)
+    C = o.static()
+    K = np.diff(g.off)  # unit weights
+    for c in np.unique(C):
+        mem = np.flatnonzero(C == c)
+        best = mem[np.argmax(K[mem])]  # argmax returns the first (lowest id) on ties
+        assert c == best
+
+
+# ---------------------------------------------------- dynamic: ND / DS / DF
+
+def _dyn_setup(seed=3, n_edges=60, schedule=oracle.SYNC):
+    g = synth.planted_partition(2000, 20, 12, 0.3, 900 + seed)
+    o = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=schedule)
+    o.static()
+    dels, ins = synth.random_batch(g, n_edges, seed=1000 + seed)
+    return g, o, dels, ins
+
+
+@pytest.mark.parametrize("mode", [oracle.ND, oracle.DS, oracle.DF])
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_update_keeps_auxiliary_state_exact(mode, schedule):
+    """After an update: G^t equals an independent edge-set update, K^t equals
+    the row sums of G^t, Sigma^t the member sums, sum Sigma = 2m (Alg. update)."""
+    g, o, dels, ins = _dyn_setup(schedule=schedule)
+    o.update(dels, ins, mode)
+    off, col, w = o.graph()
+    g2 = synth.apply_batch_numpy(g, dels, ins)
+    assert np.array_equal(off, g2.off)
+    assert np.array_equal(col, g2.col)
+    assert np.array_equal(w, g2.w.astype(np.int64))
+    st = o.state()
+    rows = np.add.reduceat(w, off[:-1]) if len(w) else np.zeros(g.n)
+    rows[np.diff(off) == 0] = 0
+    assert np.array_equal(st["K"], rows)
+    S = np.zeros(g.n, np.int64)
+    np.add.at(S, st["C"], st["K"])
+    assert np.array_equal(st["Sigma"], S)
+    assert st["m2"] == int(w.sum()) == int(S.sum())
+    assert disconnected_communities(off, col, st["C"]) == 0
+
+
+def _df_reference_marks(g_prev_C, dels, ins, n):
+    """Alg. frontier's marking loops written out: endpoints of same-community
+    deletions and of cross-community insertions."""
+    dV = np.zeros(n, np.uint8)
+    for u, v, _ in dels:
+        if g_prev_C[u] == g_prev_C[v]:
+            dV[u] = dV[v] = 1
+    for u, v, _ in ins:
+        if g_prev_C[u] != g_prev_C[v]:
+            dV[u] = dV[v] = 1
+    return dV
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_marking_set_algebra(schedule):
+    """ND marks all; DF marks exactly the endpoint rule; DF is a subset of DS;
+    DS contains the members of communities hit by same-community deletions."""
+    res = {}
+    for mode in (oracle.ND, oracle.DS, oracle.DF):
+        g, o, dels, ins = _dyn_setup(schedule=schedule)
+        Cprev = o.state()["C"]
+        o.update(dels, ins, mode)
+        res[mode] = o.affected().astype(bool)
+    assert res[oracle.ND].all()
+    assert np.array_equal(res[oracle.DF], _df_reference_marks(Cprev, dels, ins, g.n).astype(bool))
+    assert np.all(res[oracle.DS] | ~res[oracle.DF])
+    for u, v, _ in dels:
+        if Cprev[u] == Cprev[v]:
+            assert res[oracle.DS][Cprev == Cprev[u]].all()
+    assert res[oracle.DF].sum() < res[oracle.DS].sum() <= g.n
+
+
+@pytest.mark.parametrize("mode", [oracle.ND, oracle.DS, oracle.DF])
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_empty_batch_changes_nothing(mode, schedule):
+    """DS and DF mark nothing on an empty batch and return C^{t-1} unchanged;
+    ND re-processes every vertex (Section 2.4.1), so it may still improve Q."""
+    g, o, _, _ = _dyn_setup(schedule=schedule)
+    before = o.state()
+    q0 = o.modularity()
+    C = o.update(np.zeros((0, 3), np.int32), np.zeros((0, 3), np.int32), mode)
+    after = o.state()
+    assert np.array_equal(before["K"], after["K"])
+    if mode == oracle.ND:
+        assert o.affected().all()
+        assert o.modularity() > q0 - 1e-3
+        return
+    assert o.affected().sum() == 0
+    assert np.array_equal(C, before["C"])
+    for k in ("Sigma", "dSigma"):
+        assert np.array_equal(before[k], after[k])
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_delete_then_reinsert_tracks_ids(schedule):
+    """The stability protocol of Section 3.1: delete a batch, reinsert it; with
+    tracking, most vertices keep the community id they had before."""
+    g = synth.planted_partition(3000, 30, 14, 0.2, 77)
+    o = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=schedule)
+    C0 = o.static()
+    dels, _ = synth.random_batch(g, 150, seed=78, frac_ins=0.0)
+    o.update(dels, np.zeros((0, 3), np.int32), oracle.DF)
+    C2 = o.update(np.zeros((0, 3), np.int32), dels, oracle.DF)
+    assert (C2 == C0).mean() > 0.95
+    off, col, _ = o.graph()
+    assert np.array_equal(off, g.off) and np.array_equal(col, g.col)
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_refinement_threshold_rule(schedule):
+    """Alg. leidenmk with tau_re = 0.6 (Section 3.3): deletions inside a
+    community add to its cumulative change dSigma (both directions count);
+    the community is marked for refinement in the batch where
+    dSigma/Sigma first exceeds 0.6, and its dSigma then resets to 0."""
+    # two 6-cliques joined by the edge 5-6: community A = {0..5} has
+    # Sigma = 6*5 + 1 = 31.  Deleting k edges inside A gives dSigma = 2k,
+    # Sigma = 31 - 2k, and 2k/(31-2k) > 0.6 first holds at k = 6.
+    edges = clique_edges(0, 6) + clique_edges(6, 6) + [(5, 6)]
+    off, col, w = csr_from_edges(12, edges)
+    o = oracle.Oracle(12, off, col, w.astype(np.int32), schedule=schedule)
+    C = o.static()
+    assert len(np.unique(C)) == 2
+    cA = C[0]
+    assert o.state()["Sigma"][cA] == 31
+    inner = [(0, 1), (2, 3), (0, 4), (1, 2), (3, 4), (0, 2)]
+    for k, (u, v) in enumerate(inner, start=1):
+        o.update(np.array([[u, v, 1]], np.int32), np.zeros((0, 3), np.int32), oracle.DF)
+        st = o.state()
+        assert st["C"][0] == cA
+        refined = o.trace()["passes"][0]["refined_any"]
+        assert st["Sigma"][cA] == 31 - 2 * k
+        if k < 6:
+            assert refined == 0 and st["dSigma"][cA] == 2 * k
+        else:
+            assert refined == 1 and st["dSigma"][cA] == 0
+
+
+def test_invalid_batches_rejected_without_change():
+    g, o, dels, ins = _dyn_setup()
+    before = o.state()
+    bad = [
+        (np.array([[0, 0, 1]], np.int32), np.zeros((0, 3), np.int32)),       # self-loop deletion
+        (np.zeros((0, 3), np.int32), np.array([[5, 5, 1]], np.int32)),       # self-loop insertion
+        (np.zeros((0, 3), np.int32), np.array([[1, 2, 0]], np.int32)),       # zero weight
+        (np.zeros((0, 3), np.int32), np.array([[1, g.n, 1]], np.int32)),     # out of range
+    ]
+    # a deletion of an absent edge
+    for v in range(1, g.n):
+        if v not in g.col[g.off[0]:g.off[1]]:
+            bad.append((np.array([[0, v, 1]], np.int32), np.zeros((0, 3), np.int32)))
+            break
+    for d, i in bad:
+        with pytest.raises(oracle.OracleError) as e:
+            o.update(d, i, oracle.DF)
+        assert e.value.rc == oracle.ERR_BATCH
+    after = o.state()
+    for k in ("C", "K", "Sigma", "dSigma"):
+        assert np.array_equal(before[k], after[k])
+
+
+@pytest.mark.parametrize("schedule", SCHEDULES)
+def test_dynamic_quality_close_to_static(schedule):
+    """Section 4.2: the dynamic result stays close to static Leiden's Q."""
+    g = synth.planted_partition(4000, 40, 14, 0.3, 55)
+    dels, ins = synth.random_batch(g, 400, seed=56)
+    g2 = synth.apply_batch_numpy(g, dels, ins)
+    qs = {}
+    for mode in (oracle.ND, oracle.DS, oracle.DF):
+        o = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=schedule)
+        o.static()
+        o.update(dels, ins, mode)
+        qs[mode] = o.modularity()
+    s = oracle.Oracle(g2.n, g2.off, g2.col, g2.w, schedule=schedule)
+    s.static()
+    qstat = s.modularity()
+    for mode, q in qs.items():
+        assert q > qstat - 0.005, (mode, q, qstat)
+
+
+def test_sync_and_seq_agree_in_quality():
+    g = synth.rmat(13, seed=21)
+    q = {}
+    for sch in SCHEDULES:
+        o = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=sch)
+        C = o.static()
+        q[sch] = o.modularity()
+        assert disconnected_communities(g.off, g.col, C) == 0
+    assert abs(q[oracle.SEQ] - q[oracle.SYNC]) < 0.01
