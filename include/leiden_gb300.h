@@ -1,0 +1,175 @@
+/*
+ * leiden_gb300.h -- C ABI of the GB300 (sm_103a) dynamic Leiden library.
+ *
+ * The library tracks the communities of one evolving undirected graph on one
+ * GPU, following "Heuristic-based Dynamic Leiden Algorithm for Efficient
+ * Tracking of Communities on Evolving Graphs" (Sahu, arXiv 2410.15451).  The
+ * functions mirror the paper's statement of the problem: Alg. "naive",
+ * "delta" and "frontier" (Appendix A.1-A.3) take the updated graph G^t, the
+ * batch (deletions Delta^{t-}, insertions Delta^{t+}) and the auxiliary
+ * state {C^{t-1}, K^{t-1}, Sigma^{t-1}, Delta Sigma^{t-1}}, and return
+ * {C^t, K^t, Sigma^t, Delta Sigma^t}.  Here the handle owns G and that
+ * state on the device, so a call passes only the batch.
+ *
+ * Conventions for every function:
+ *  - Host pointers unless the name ends in _device; the library copies host
+ *    inputs before returning and never keeps a caller pointer.
+ *  - Vertex ids are int32 in [0, n); n is fixed for the life of a handle
+ *    (the paper adds or removes no vertices, Section 4.1.3).  Edge weights
+ *    are positive int32; degrees and community totals are exact int64.
+ *  - Errors are reported by status code only; no exception or abort crosses
+ *    the ABI.  leiden_last_error() gives a message for the last failure.
+ *  - One handle is used by one host thread at a time; all its GPU work runs
+ *    on the stream given at creation.  Different handles are independent.
+ */
+#ifndef LEIDEN_GB300_H
+#define LEIDEN_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LEIDEN_OK = 0,
+  LEIDEN_ERR_ARG = 1,      /* bad argument (null pointer, size, mode)           */
+  LEIDEN_ERR_BATCH = 2,    /* invalid batch; the handle is left unchanged        */
+  LEIDEN_ERR_OOM = 3,      /* device memory exhausted                            */
+  LEIDEN_ERR_CUDA = 4,     /* a CUDA call failed (the message names it)          */
+  LEIDEN_ERR_TIMEOUT = 5,  /* a bounded device wait gave up                      */
+  LEIDEN_ERR_STATE = 6     /* call order violated (update before static)         */
+} leiden_status;
+
+/* Affected-vertex marking of the batch (Appendix A.1, A.2, A.3). */
+typedef enum { LEIDEN_ND = 0, LEIDEN_DS = 1, LEIDEN_DF = 2 } leiden_mode;
+
+/* One undirected edge; the library adds the reverse direction itself. */
+typedef struct {
+  int32_t u, v, w;
+} leiden_edge;
+
+typedef struct {
+  double tau;             /* iteration tolerance of local moving, 1e-2 (Section 4.1.2)   */
+  double tau_drop;        /* TOLERANCE_DECLINE_FACTOR, 10                                 */
+  double tau_refine;      /* refinement tolerance tau_re, 0.6 (Section 3.3)               */
+  int32_t max_iterations; /* MAX_ITERATIONS per pass, 20                                  */
+  int32_t max_passes;     /* MAX_PASSES, 10                                               */
+  int32_t deterministic;  /* 1: snapshot schedule, bit-identical run to run (default);    */
+                          /* 0: moves applied in place as vertices decide (the paper's    */
+                          /*    asynchronous style; results may vary between runs)        */
+  int32_t classes;        /* sub-sweeps per local-moving iteration, power of two, 4       */
+  double slack;           /* spare CSR capacity per row as a fraction of its degree, 0.25 */
+  int32_t min_slack;      /* minimum spare arcs per row, 4                                */
+  int32_t collect_stats;  /* 1: time each phase with CUDA events (adds syncs)             */
+} leiden_params;
+
+/* Counters and phase times of the last static/update call. */
+typedef struct {
+  int64_t passes;              /* Leiden passes run                                     */
+  int64_t lm_iterations;       /* local-moving iterations, all passes                   */
+  int64_t lm_vertices;         /* vertex visits in local moving                          */
+  int64_t lm_arcs;             /* arcs scanned in local moving                           */
+  int64_t lm_moves;            /* community changes in local moving                      */
+  int64_t refine_vertices;     /* vertex visits in refinement                            */
+  int64_t refine_arcs;         /* arcs scanned in refinement                             */
+  int64_t aggregate_arcs;      /* arcs read by aggregation                               */
+  int64_t affected;            /* |dV| after marking (pass 1 affected set)               */
+  int64_t communities;         /* communities in C^t                                     */
+  int64_t batch_arcs;          /* arcs applied (both directions, after deduplication)    */
+  double ms_total;             /* wall time of the call on the stream                    */
+  double ms_batch;             /* batch canonicalisation, apply, marking (collect_stats) */
+  double ms_move;              /* local moving (collect_stats)                           */
+  double ms_refine;            /* renumber + split + refinement (collect_stats)          */
+  double ms_aggregate;         /* dense renumber + aggregation (collect_stats)           */
+  double ms_track;             /* lookup + tracking (collect_stats)                      */
+} leiden_stats;
+
+typedef struct leiden_handle leiden_handle;
+
+/* Fill *p with the defaults listed above. */
+void leiden_default_params(leiden_params *p);
+
+/* Create a handle for the graph G^0 given as symmetric CSR on the host:
+ * offsets[n+1] (int64, offsets[0] = 0), cols[offsets[n]] (int32, in [0, n)),
+ * weights[offsets[n]] (int32 > 0, NULL = unit).  Rows need not be sorted;
+ * self-loops and repeated arcs are rejected (LEIDEN_ERR_ARG).  The graph is
+ * copied to a device CSR with per-row slack.  cuda_stream is a cudaStream_t
+ * (NULL = the legacy default stream).  On success *out owns all device state;
+ * release it with leiden_destroy(). */
+leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_t *offsets,
+                            const int32_t *cols, const int32_t *weights, void *cuda_stream,
+                            leiden_handle **out);
+
+/* Static Leiden (Section 4.1.4 baseline, Alg. "leiden" with C^{t-1} = singletons,
+ * every vertex affected, every community refined) on the current graph.
+ * Resets the auxiliary state: C^t = result, K^t = weighted degrees,
+ * Sigma^t = community totals, Delta Sigma^t = 0.  membership_out: host
+ * int32[n] or NULL. */
+leiden_status leiden_static(leiden_handle *h, int32_t *membership_out);
+
+/* Apply one batch update and update the communities (Alg. "naive" / "delta" /
+ * "frontier" with Alg. "leiden" and "leidenTrack").  del/ins are host arrays
+ * of undirected edges.  Batch rules: ids in [0, n), u != v, insertion
+ * weights > 0; a deletion must name an existing edge (its w is ignored and
+ * the stored weight is removed); repeated deletions collapse, repeated
+ * insertions add up; inserting an existing edge adds to its weight;
+ * deletions apply before insertions.  Any violation returns
+ * LEIDEN_ERR_BATCH with the handle unchanged.  Requires a prior
+ * leiden_static (else LEIDEN_ERR_STATE).  membership_out: host int32[n] or
+ * NULL (C^t stays on the device). */
+leiden_status leiden_update(leiden_handle *h, const leiden_edge *del, int64_t n_del,
+                            const leiden_edge *ins, int64_t n_ins, leiden_mode mode,
+                            int32_t *membership_out);
+
+/* As leiden_update, but del, ins and membership_out are device pointers on
+ * the handle's device (membership_out may be NULL).  The call returns when
+ * the result is complete on the device. */
+leiden_status leiden_update_device(leiden_handle *h, const leiden_edge *del, int64_t n_del,
+                                   const leiden_edge *ins, int64_t n_ins, leiden_mode mode,
+                                   int32_t *membership_out);
+
+/* Modularity Q of Eq. 1 on the current graph for `membership` (host
+ * int32[n] with ids in [0, n); NULL = the handle's C^t).  Computed exactly in
+ * integers (2m * sum sigma_c - sum Sigma_c^2) and divided once by (2m)^2. */
+leiden_status leiden_modularity(leiden_handle *h, const int32_t *membership, double *q_out);
+
+/* Device pointer to the handle's current membership C^t (int32[n]); valid
+ * until the next call on the handle. */
+leiden_status leiden_membership_device(leiden_handle *h, const int32_t **d_membership);
+
+/* Host copies of the auxiliary state {C^t, K^t, Sigma^t, Delta Sigma^t} and
+ * 2m.  Any output pointer may be NULL. */
+leiden_status leiden_get_state(leiden_handle *h, int32_t *C, int64_t *K, int64_t *Sigma,
+                               int64_t *dSigma, int64_t *m2);
+
+/* Number of arcs of G^t (twice the number of edges). */
+int64_t leiden_graph_arcs(leiden_handle *h);
+
+/* Host copy of G^t as compact CSR with rows sorted by neighbour:
+ * off[n+1], col[arcs], w[arcs] (arcs from leiden_graph_arcs). */
+leiden_status leiden_get_graph(leiden_handle *h, int64_t *off, int32_t *col, int64_t *w);
+
+/* Affected flags dV (uint8[n]) of the last call (all ones for static/ND). */
+leiden_status leiden_get_affected(leiden_handle *h, uint8_t *dV);
+
+/* Per-pass trace of the last call, int64[2 + 10*25]: [0] passes, [1] |dV|,
+ * then per pass: level vertex count, local-moving iterations, communities
+ * after refinement, any community refined, refinement rounds, moves in
+ * local-moving iterations 0..19. */
+leiden_status leiden_get_trace(leiden_handle *h, int64_t *trace);
+
+/* Counters and phase times of the last call. */
+leiden_status leiden_get_stats(leiden_handle *h, leiden_stats *stats);
+
+/* Message for the last failed call on h (or for the last failed
+ * leiden_create when h is NULL).  Never NULL. */
+const char *leiden_last_error(leiden_handle *h);
+
+/* Free all device and host memory of the handle (NULL is a no-op). */
+void leiden_destroy(leiden_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEIDEN_GB300_H */

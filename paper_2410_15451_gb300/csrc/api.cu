@@ -1,0 +1,614 @@
+// C ABI of the GB300 dynamic Leiden library and the pass loop of Alg.
+// "leiden" (Appendix A.4) that drives the kernels.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// int128 -> double in a fixed order (|x| = hi*2^64 + lo, then the sign).
+double i128_to_double(i128 x) {
+  bool neg = x < 0;
+  u128 u = neg ? (u128)(-(x + 1)) + 1 : (u128)x;
+  double hi = (double)(uint64_t)(u >> 64);
+  double lo = (double)(uint64_t)u;
+  double r = hi * 18446744073709551616.0 + lo;
+  return neg ? -r : r;
+}
+
+i128 read_i128(const unsigned long long *p) { return (i128)(((u128)p[1] << 64) | (u128)p[0]); }
+
+// dQ of a sum of gains g (Eq. 2 times 2m^2): 2g / (2m)^2.
+double gains_to_dq(i128 g, int64_t m2) {
+  if (g == 0 || m2 == 0) return 0.0;
+  return i128_to_double(2 * g) / ((double)m2 * (double)m2);
+}
+
+#define CK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                    \
+      return e_ == cudaErrorMemoryAllocation ? LEIDEN_ERR_OOM : LEIDEN_ERR_CUDA;      \
+    }                                                                                 \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(leiden_handle *h, T **p, int64_t count) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (size_t)std::max<int64_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  h->owned.push_back(q);
+  *p = (T *)q;
+  return cudaSuccess;
+}
+
+void sync_counters(leiden_handle *h) {
+  cudaMemcpyAsync(h->hcnt, h->dcnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+}
+
+#define CKF()                             \
+  do {                                    \
+    if (h->fatal != LEIDEN_OK) {          \
+      leiden_status f_ = h->fatal;        \
+      h->fatal = LEIDEN_OK;               \
+      return f_;                          \
+    }                                     \
+  } while (0)
+
+LevelGraph level0(leiden_handle *h) {
+  LevelGraph g;
+  g.n = h->n;
+  g.off = h->g_off;
+  g.deg = h->g_deg;
+  g.col = h->g_col;
+  g.w = h->g_w;
+  g.w64 = false;
+  g.maxdeg = h->g_maxdeg;
+  return g;
+}
+
+float ev_ms(leiden_handle *h, int a, int b) {
+  float ms = 0;
+  cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]);
+  return ms;
+}
+
+void mark(leiden_handle *h, int k) {
+  if (h->p.collect_stats) cudaEventRecord(h->ev[k], h->stream);
+}
+
+// Alg. leiden: passes of local moving, subset renumbering, splitting,
+// refinement, then renumbering, lookup and aggregation; finally lookup and
+// tracking.  Expects: Cp = C^{t-1} copy source in h->C, Kp/Sp from h->K,
+// h->Sig, dS/dR marked, dV = affected.
+leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range) {
+  cudaStream_t s = h->stream;
+  const leiden_params &p = h->p;
+  int64_t N = h->n;
+  memset(h->trace, 0, sizeof(h->trace));
+  // initialisation
+  mark_unprocessed_from_flags(h, h->dV, N);
+  launch_iota_i32(h->Ctop, N, s);
+  CK(cudaMemcpyAsync(h->Cp, h->C, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->Kp, h->K, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->Sp, h->Sig, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(&h->dcnt->processed, 0, 5 * sizeof(int64_t), s));
+  int64_t m2 = h->m2;
+  LevelGraph g = level0(h);
+  double tau = p.tau;
+  int slot = 0;
+  int passes = 0;
+  leiden_stats &st = h->stats;
+  float t_move = 0, t_ref = 0, t_agg = 0;
+  int64_t moves_total = 0;
+  for (int lp = 0; lp < p.max_passes; lp++) {
+    int64_t n = g.n;
+    int64_t *tr = &h->trace[2 + lp * 25];
+    passes++;
+    tr[0] = n;
+    mark(h, 2);
+    lm_prepare(h, g);
+    int li = p.max_iterations;
+    for (int it = 0; it < p.max_iterations; it++) {
+      CK(cudaMemsetAsync(&h->dcnt->dq[0], 0, 2 * sizeof(unsigned long long), s));
+      CK(cudaMemsetAsync(&h->dcnt->moves, 0, sizeof(int64_t), s));
+      for (int cls = 0; cls < p.classes; cls++) lm_subsweep(h, g, cls, lp == 0 ? in_range : nullptr, dynamic);
+      sync_counters(h);
+      CK(cudaGetLastError());
+      CKF();
+      i128 dq = read_i128(h->hcnt->dq);
+      int64_t mv = h->hcnt->moves;
+      if (it < 20) tr[5 + it] = mv;
+      moves_total += mv;
+      st.lm_iterations++;
+      if (gains_to_dq(dq, m2) <= tau) { li = it + 1; break; }
+    }
+    tr[1] = li;
+    mark(h, 3);
+    subset_renumber(h, n);
+    split_communities(h, g);
+    CK(cudaMemcpyAsync(h->CB, h->Cp, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    refine_reset(h, g);
+    int rounds = 0;
+    int refined_any = 0;
+    int max_rounds = p.deterministic ? p.max_iterations : 1;
+    for (int r = 0; r < max_rounds; r++) {
+      refine_round(h, g, r & 1);
+      rounds++;
+      sync_counters(h);
+      CK(cudaGetLastError());
+      CKF();
+      if (r == 0) refined_any = h->hcnt->cand_count[0] > 0;
+      if (h->hcnt->accepted == 0) break;
+    }
+    if (max_rounds == 0) { sync_counters(h); refined_any = h->hcnt->cand_count[0] > 0; }
+    tr[3] = refined_any;
+    tr[4] = rounds;
+    count_communities(h, n);
+    sync_counters(h);
+    tr[2] = h->hcnt->list_count;
+    mark(h, 4);
+    if (h->p.collect_stats) {
+      cudaEventSynchronize(h->ev[4]);
+      t_move += ev_ms(h, 2, 3);
+      t_ref += ev_ms(h, 3, 4);
+    }
+    if (li <= 1 && !refined_any) break;
+    if (li <= 1 && lp > 0) break;
+    if (lp == p.max_passes - 1) {
+      // the pass limit is reached: lookup with C' below, as when breaking
+      break;
+    }
+    renumber_dense(h, n);
+    sync_counters(h);
+    int64_t ncomm = 0;
+    {
+      int64_t tot = 0;
+      CK(cudaMemcpyAsync(&tot, h->lbuf0 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      ncomm = tot;
+    }
+    lookup_dendrogram(h);
+    aggregate(h, g, ncomm, slot);
+    reset_next_pass(h, ncomm, slot);
+    level_maxdeg(h, h->y_deg[slot], ncomm);
+    sync_counters(h);
+    CK(cudaGetLastError());
+    CKF();
+    LevelGraph y;
+    y.n = ncomm;
+    y.off = h->y_off[slot];
+    y.deg = h->y_deg[slot];
+    y.col = h->y_col[slot];
+    y.w = h->y_w[slot];
+    y.w64 = true;
+    y.maxdeg = h->hcnt->max_count;
+    g = y;
+    slot ^= 1;
+    tau /= p.tau_drop;
+    mark(h, 5);
+    if (h->p.collect_stats) {
+      cudaEventSynchronize(h->ev[5]);
+      t_agg += ev_ms(h, 4, 5);
+    }
+  }
+  mark(h, 6);
+  lookup_dendrogram(h);
+  track_communities(h);
+  mark(h, 7);
+  sync_counters(h);
+  CK(cudaGetLastError());
+  h->trace[0] = passes;
+  st.passes = passes;
+  st.lm_vertices = h->hcnt->processed;
+  st.lm_arcs = h->hcnt->arcs;
+  st.lm_moves = moves_total;
+  st.refine_vertices = h->hcnt->ref_processed;
+  st.refine_arcs = h->hcnt->ref_arcs;
+  if (h->p.collect_stats) {
+    st.ms_move = t_move;
+    st.ms_refine = t_ref;
+    st.ms_aggregate = t_agg;
+    st.ms_track = ev_ms(h, 6, 7);
+  }
+  return LEIDEN_OK;
+}
+
+leiden_status finish_call(leiden_handle *h, int32_t *out, bool device_out) {
+  cudaStream_t s = h->stream;
+  if (out) {
+    CK(cudaMemcpyAsync(out, h->C, (size_t)h->n * sizeof(int32_t),
+                       device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaStreamSynchronize(s));
+  return LEIDEN_OK;
+}
+
+leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_del, const leiden_edge *d_ins,
+                        int64_t n_ins, leiden_mode mode) {
+  h->stats = leiden_stats{};
+  if (h->p.collect_stats) cudaEventRecord(h->ev[0], h->stream);
+  leiden_status st = batch_apply_and_mark(h, d_del, n_del, d_ins, n_ins, (int)mode);
+  if (st != LEIDEN_OK) return st;
+  mark(h, 1);
+  sync_counters(h);
+  CK(cudaGetLastError());
+  h->m2 = h->hcnt->m2;
+  level_maxdeg(h, h->g_deg, h->n);
+  sync_counters(h);
+  h->g_maxdeg = h->hcnt->max_count;
+  st = run_leiden(h, 1, mode == LEIDEN_DS ? h->dV : nullptr);
+  if (st != LEIDEN_OK) return st;
+  if (h->p.collect_stats) {
+    cudaEventSynchronize(h->ev[7]);
+    h->stats.ms_batch = ev_ms(h, 0, 1);
+    h->stats.ms_total = ev_ms(h, 0, 7);
+  }
+  return LEIDEN_OK;
+}
+
+leiden_status check_handle(leiden_handle *h) {
+  if (!h) return LEIDEN_ERR_ARG;
+  cudaError_t e = cudaSetDevice(h->device);
+  if (e != cudaSuccess) {
+    h->err = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
+    return LEIDEN_ERR_CUDA;
+  }
+  return LEIDEN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void leiden_default_params(leiden_params *p) {
+  if (!p) return;
+  p->tau = 1e-2;
+  p->tau_drop = 10.0;
+  p->tau_refine = 0.6;
+  p->max_iterations = 20;
+  p->max_passes = 10;
+  p->deterministic = 1;
+  p->classes = 4;
+  p->slack = 0.25;
+  p->min_slack = 4;
+  p->collect_stats = 0;
+}
+
+leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_t *offsets, const int32_t *cols,
+                            const int32_t *weights, void *cuda_stream, leiden_handle **out) {
+  g_create_error.clear();
+  if (!out) { g_create_error = "out is NULL"; return LEIDEN_ERR_ARG; }
+  *out = nullptr;
+  if (n < 1 || n > 0x7ffffffe || !offsets || (offsets[n] > 0 && !cols)) {
+    g_create_error = "invalid n, offsets or cols";
+    return LEIDEN_ERR_ARG;
+  }
+  leiden_params p;
+  leiden_default_params(&p);
+  if (params) p = *params;
+  if (p.classes < 1 || (p.classes & (p.classes - 1)) || p.max_iterations < 1 || p.max_passes < 1 || p.slack < 0 ||
+      p.min_slack < 0 || p.tau_drop <= 0) {
+    g_create_error = "invalid parameters (classes must be a power of two)";
+    return LEIDEN_ERR_ARG;
+  }
+  // host validation and canonical rows
+  int64_t arcs = offsets[n];
+  if (offsets[0] != 0 || arcs < 0) { g_create_error = "offsets[0] must be 0"; return LEIDEN_ERR_ARG; }
+  std::vector<int64_t> cap_off(n + 1, 0);
+  std::vector<int32_t> deg(n);
+  for (int64_t i = 0; i < n; i++) {
+    int64_t d = offsets[i + 1] - offsets[i];
+    if (d < 0 || d > 0x7fffffff) { g_create_error = "offsets not monotone"; return LEIDEN_ERR_ARG; }
+    deg[i] = (int32_t)d;
+    int64_t extra = std::max<int64_t>((int64_t)((double)d * p.slack), p.min_slack);
+    cap_off[i + 1] = cap_off[i] + d + extra;
+  }
+  int64_t cap = cap_off[n];
+  std::vector<int32_t> hcol((size_t)std::max<int64_t>(cap, 1), 0), hw((size_t)std::max<int64_t>(cap, 1), 0);
+  std::vector<std::pair<int32_t, int32_t>> row;
+  int32_t maxdeg = 0;
+  for (int64_t i = 0; i < n; i++) {
+    row.clear();
+    for (int64_t a = offsets[i]; a < offsets[i + 1]; a++) {
+      int32_t j = cols[a];
+      int32_t w = weights ? weights[a] : 1;
+      if (j < 0 || j >= n || j == i || w <= 0) {
+        g_create_error = "column out of range, self-loop or weight <= 0";
+        return LEIDEN_ERR_ARG;
+      }
+      row.emplace_back(j, w);
+    }
+    std::sort(row.begin(), row.end());
+    for (size_t k = 1; k < row.size(); k++)
+      if (row[k].first == row[k - 1].first) { g_create_error = "repeated arc"; return LEIDEN_ERR_ARG; }
+    for (size_t k = 0; k < row.size(); k++) {
+      hcol[cap_off[i] + k] = row[k].first;
+      hw[cap_off[i] + k] = row[k].second;
+    }
+    maxdeg = std::max<int32_t>(maxdeg, deg[i]);
+  }
+  // symmetry: every arc (i, j, w) must have (j, i, w)
+  for (int64_t i = 0; i < n; i++) {
+    for (int64_t k = 0; k < deg[i]; k++) {
+      int32_t j = hcol[cap_off[i] + k];
+      const int32_t *rb = hcol.data() + cap_off[j];
+      const int32_t *re = rb + deg[j];
+      const int32_t *it = std::lower_bound(rb, re, (int32_t)i);
+      if (it == re || *it != i || hw[cap_off[j] + (it - rb)] != hw[cap_off[i] + k]) {
+        g_create_error = "graph is not symmetric";
+        return LEIDEN_ERR_ARG;
+      }
+    }
+  }
+  leiden_handle *h = new leiden_handle();
+  h->p = p;
+  h->n = n;
+  h->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&h->device);
+  cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  auto bail = [&](leiden_status st, const std::string &m) {
+    g_create_error = m.empty() ? h->err : m;
+    leiden_destroy(h);
+    return st;
+  };
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
+  A(dalloc(h, &h->g_off, n + 1));
+  A(dalloc(h, &h->g_deg, n));
+  A(dalloc(h, &h->g_col, cap));
+  A(dalloc(h, &h->g_w, cap));
+  A(dalloc(h, &h->C, n));
+  A(dalloc(h, &h->K, n));
+  A(dalloc(h, &h->Sig, n));
+  A(dalloc(h, &h->dSig, n));
+  A(dalloc(h, &h->dV, n));
+  int32_t **i32s[] = {&h->Cp, &h->CB, &h->Ctop, &h->csize, &h->rep, &h->prop, &h->parent,
+                      &h->ibuf0, &h->ibuf1, &h->ibuf2, &h->movers, &h->mtarget, &h->cverts};
+  for (auto pp : i32s) A(dalloc(h, pp, n + 1));
+  int64_t **i64s[] = {&h->Kp, &h->Sp, &h->S2, &h->lbuf0, &h->lbuf1, &h->lbuf2, &h->lbuf3, &h->coff, &h->cflat};
+  for (auto pp : i64s) A(dalloc(h, pp, n + 2));
+  uint8_t **u8s[] = {&h->dS, &h->dR, &h->dS2, &h->dR2, &h->dE, &h->dCf};
+  for (auto pp : u8s) A(dalloc(h, pp, n + 1));
+  A(dalloc(h, &h->unproc, n / 32 + 2));
+  A(dalloc(h, &h->bins, (int64_t)NBINS * n));
+  A(dalloc(h, &h->cand, 2 * n));
+  for (int k = 0; k < 2; k++) {
+    A(dalloc(h, &h->y_off[k], n + 2));
+    A(dalloc(h, &h->y_deg[k], n + 1));
+    A(dalloc(h, &h->y_col[k], cap));
+    A(dalloc(h, &h->y_w[k], cap));
+  }
+  h->y_cap = cap;
+  int64_t tc = 1;
+  while (tc < 2 * n) tc <<= 1;
+  A(dalloc(h, &h->tr_keys, tc));
+  A(dalloc(h, &h->tr_vals, tc));
+  h->tr_cap = tc;
+  A(dalloc(h, &h->dcnt, 1));
+  size_t stb = scan_tmp_bytes(2 * n + 2);
+  void *stp = nullptr;
+  A(cudaMalloc(&stp, stb));
+  if (stp) { h->owned.push_back(stp); h->scan_tmp = stp; h->scan_tmp_bytes = stb; }
+  A(cudaMallocHost((void **)&h->hcnt, sizeof(DevCounters)));
+  for (auto &ev : h->ev) A(cudaEventCreate(&ev));
+  if (e != cudaSuccess)
+    return bail(e == cudaErrorMemoryAllocation ? LEIDEN_ERR_OOM : LEIDEN_ERR_CUDA,
+                std::string("device allocation: ") + cudaGetErrorString(e));
+  cudaStream_t s = h->stream;
+  A(cudaMemcpyAsync(h->g_off, cap_off.data(), (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  A(cudaMemcpyAsync(h->g_deg, deg.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  A(cudaMemcpyAsync(h->g_col, hcol.data(), (size_t)cap * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  A(cudaMemcpyAsync(h->g_w, hw.data(), (size_t)cap * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  A(cudaMemsetAsync(h->dcnt, 0, sizeof(DevCounters), s));
+  A(cudaStreamSynchronize(s));
+  if (e != cudaSuccess) return bail(LEIDEN_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
+  h->g_cap = cap;
+  h->g_arcs = arcs;
+  h->g_maxdeg = maxdeg;
+  ensure_hscratch(h, std::max<int64_t>(maxdeg, BIN_BLOCK_MAX + 1));
+  *out = h;
+  return LEIDEN_OK;
+}
+
+leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
+  leiden_status st = check_handle(h);
+  if (st != LEIDEN_OK) return st;
+  cudaStream_t s = h->stream;
+  h->stats = leiden_stats{};
+  if (h->p.collect_stats) cudaEventRecord(h->ev[0], s);
+  int64_t N = h->n;
+  recompute_weights(h);
+  launch_iota_i32(h->C, N, s);
+  CK(cudaMemcpyAsync(h->Sig, h->K, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemsetAsync(h->dSig, 0, (size_t)N * sizeof(int64_t), s));
+  CK(cudaMemsetAsync(h->dV, 1, (size_t)N, s));
+  CK(cudaMemsetAsync(h->dS, 0, (size_t)N, s));
+  CK(cudaMemsetAsync(h->dR, 1, (size_t)N, s));
+  sync_counters(h);
+  CK(cudaGetLastError());
+  h->m2 = h->hcnt->m2;
+  mark(h, 1);
+  st = run_leiden(h, 0, nullptr);
+  if (st != LEIDEN_OK) return st;
+  h->has_static = true;
+  if (h->p.collect_stats) {
+    cudaEventSynchronize(h->ev[7]);
+    h->stats.ms_total = ev_ms(h, 0, 7);
+  }
+  return finish_call(h, membership_out, false);
+}
+
+leiden_status leiden_update(leiden_handle *h, const leiden_edge *del, int64_t n_del, const leiden_edge *ins,
+                            int64_t n_ins, leiden_mode mode, int32_t *membership_out) {
+  leiden_status st = check_handle(h);
+  if (st != LEIDEN_OK) return st;
+  if (!h->has_static) { h->err = "leiden_update before leiden_static"; return LEIDEN_ERR_STATE; }
+  if (n_del < 0 || n_ins < 0 || (n_del && !del) || (n_ins && !ins) || mode < LEIDEN_ND || mode > LEIDEN_DF) {
+    h->err = "invalid batch arguments";
+    return LEIDEN_ERR_ARG;
+  }
+  // stage the host batch in device memory (upload buffers grow on demand)
+  int64_t need = std::max<int64_t>(std::max(n_del, n_ins), 1);
+  if (need > h->up_cap) {
+    for (auto &q : h->owned)
+      if (q && (q == h->up_del || q == h->up_ins)) { cudaFree(q); q = nullptr; }
+    h->up_del = h->up_ins = nullptr;
+    h->up_cap = 0;
+    CK(dalloc(h, &h->up_del, need));
+    CK(dalloc(h, &h->up_ins, need));
+    h->up_cap = need;
+  }
+  leiden_edge *dd = h->up_del, *di = h->up_ins;
+  if (n_del) CK(cudaMemcpyAsync(dd, del, (size_t)n_del * sizeof(leiden_edge), cudaMemcpyHostToDevice, h->stream));
+  if (n_ins) CK(cudaMemcpyAsync(di, ins, (size_t)n_ins * sizeof(leiden_edge), cudaMemcpyHostToDevice, h->stream));
+  st = do_update(h, dd, n_del, di, n_ins, mode);
+  if (st != LEIDEN_OK) return st;
+  return finish_call(h, membership_out, false);
+}
+
+leiden_status leiden_update_device(leiden_handle *h, const leiden_edge *del, int64_t n_del, const leiden_edge *ins,
+                                   int64_t n_ins, leiden_mode mode, int32_t *membership_out) {
+  leiden_status st = check_handle(h);
+  if (st != LEIDEN_OK) return st;
+  if (!h->has_static) { h->err = "leiden_update_device before leiden_static"; return LEIDEN_ERR_STATE; }
+  if (n_del < 0 || n_ins < 0 || (n_del && !del) || (n_ins && !ins) || mode < LEIDEN_ND || mode > LEIDEN_DF) {
+    h->err = "invalid batch arguments";
+    return LEIDEN_ERR_ARG;
+  }
+  st = do_update(h, del, n_del, ins, n_ins, mode);
+  if (st != LEIDEN_OK) return st;
+  return finish_call(h, membership_out, true);
+}
+
+leiden_status leiden_modularity(leiden_handle *h, const int32_t *membership, double *q_out) {
+  leiden_status st = check_handle(h);
+  if (st != LEIDEN_OK) return st;
+  if (!q_out) { h->err = "q_out is NULL"; return LEIDEN_ERR_ARG; }
+  cudaStream_t s = h->stream;
+  const int32_t *C = h->C;
+  if (membership) {
+    for (int64_t i = 0; i < h->n; i++)
+      if (membership[i] < 0 || membership[i] >= h->n) { h->err = "membership id out of range"; return LEIDEN_ERR_ARG; }
+    CK(cudaMemcpyAsync(h->ibuf2, membership, (size_t)h->n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    C = h->ibuf2;
+  }
+  // K must be the row sums of G^t (it is, after static/update); before the
+  // first static call compute them.
+  if (!h->has_static) {
+    recompute_weights(h);
+    sync_counters(h);
+    h->m2 = h->hcnt->m2;
+  }
+  modularity_terms(h, C);
+  sync_counters(h);
+  CK(cudaGetLastError());
+  int64_t m2 = h->m2;
+  if (m2 == 0) { *q_out = 0.0; return LEIDEN_OK; }
+  i128 num = (i128)m2 * h->hcnt->sigma_intra - read_i128(h->hcnt->sq);
+  *q_out = i128_to_double(num) / ((double)m2 * (double)m2);
+  return LEIDEN_OK;
+}
+
+leiden_status leiden_membership_device(leiden_handle *h, const int32_t **d_membership) {
+  if (!h || !d_membership) return LEIDEN_ERR_ARG;
+  *d_membership = h->C;
+  return LEIDEN_OK;
+}
+
+leiden_status leiden_get_state(leiden_handle *h, int32_t *C, int64_t *K, int64_t *Sigma, int64_t *dSigma,
+                               int64_t *m2) {
+  leiden_status st = check_handle(h);
+  if (st != LEIDEN_OK) return st;
+  cudaStream_t s = h->stream;
+  size_t n = (size_t)h->n;
+  if (C) CK(cudaMemcpyAsync(C, h->C, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  if (K) CK(cudaMemcpyAsync(K, h->K, n * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  if (Sigma) CK(cudaMemcpyAsync(Sigma, h->Sig, n * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  if (dSigma) CK(cudaMemcpyAsync(dSigma, h->dSig, n * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (m2) *m2 = h->m2;
+  return LEIDEN_OK;
+}
+
+int64_t leiden_graph_arcs(leiden_handle *h) { return h ? h->g_arcs : -1; }
+
+leiden_status leiden_get_graph(leiden_handle *h, int64_t *off, int32_t *col, int64_t *w) {
+  leiden_status st = check_handle(h);
+  if (st != LEIDEN_OK) return st;
+  if (!off || (h->g_arcs && (!col || !w))) { h->err = "null output"; return LEIDEN_ERR_ARG; }
+  cudaStream_t s = h->stream;
+  int64_t n = h->n;
+  std::vector<int64_t> goff(n + 1);
+  std::vector<int32_t> gdeg(n), gcol((size_t)h->g_cap), gw((size_t)h->g_cap);
+  CK(cudaMemcpyAsync(goff.data(), h->g_off, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(gdeg.data(), h->g_deg, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(gcol.data(), h->g_col, (size_t)h->g_cap * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(gw.data(), h->g_w, (size_t)h->g_cap * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  off[0] = 0;
+  for (int64_t i = 0; i < n; i++) {
+    off[i + 1] = off[i] + gdeg[i];
+    for (int64_t k = 0; k < gdeg[i]; k++) {
+      col[off[i] + k] = gcol[goff[i] + k];
+      w[off[i] + k] = gw[goff[i] + k];
+    }
+  }
+  if (off[n] != h->g_arcs) { h->err = "arc count mismatch"; return LEIDEN_ERR_STATE; }
+  return LEIDEN_OK;
+}
+
+leiden_status leiden_get_affected(leiden_handle *h, uint8_t *dV) {
+  leiden_status st = check_handle(h);
+  if (st != LEIDEN_OK) return st;
+  if (!dV) return LEIDEN_ERR_ARG;
+  CK(cudaMemcpyAsync(dV, h->dV, (size_t)h->n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return LEIDEN_OK;
+}
+
+leiden_status leiden_get_trace(leiden_handle *h, int64_t *trace) {
+  if (!h || !trace) return LEIDEN_ERR_ARG;
+  memcpy(trace, h->trace, sizeof(h->trace));
+  // |dV| (computed on demand)
+  std::vector<uint8_t> dV((size_t)h->n);
+  if (leiden_get_affected(h, dV.data()) == LEIDEN_OK) {
+    int64_t k = 0;
+    for (uint8_t x : dV) k += x;
+    trace[1] = k;
+  }
+  return LEIDEN_OK;
+}
+
+leiden_status leiden_get_stats(leiden_handle *h, leiden_stats *stats) {
+  if (!h || !stats) return LEIDEN_ERR_ARG;
+  *stats = h->stats;
+  return LEIDEN_OK;
+}
+
+const char *leiden_last_error(leiden_handle *h) {
+  if (!h) return g_create_error.c_str();
+  return h->err.c_str();
+}
+
+void leiden_destroy(leiden_handle *h) {
+  if (!h) return;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void *q : h->owned)
+    if (q) cudaFree(q);
+  if (h->hcnt) cudaFreeHost(h->hcnt);
+  for (auto &ev : h->ev)
+    if (ev) cudaEventDestroy(ev);
+  delete h;
+}
+
+}  // extern "C"

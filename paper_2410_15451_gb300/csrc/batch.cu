@@ -1,0 +1,630 @@
+// Batch update: canonicalise the batch, apply it to the slack CSR by sorted
+// merge, mark affected vertices (ND / DS / DF, Appendix A.1-A.3), update
+// K, Sigma and Delta Sigma (Alg. "update"), and mark communities to split /
+// refine (Alg. "leidenmk").
+#include <algorithm>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int TB = 256;
+
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, int32_t x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+__device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *a, int64_t n, uint64_t x) {
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Mirror each undirected edge into two arcs keyed (src << vb) | dst and
+// validate it.  error := 1 on any violation.
+__global__ void k_expand(const leiden_edge *del, int64_t n_del, const leiden_edge *ins, int64_t n_ins,
+                         int64_t n, int vb, uint64_t *dkey, uint64_t *ikey, int64_t *iw, DevCounters *cnt) {
+  for (int64_t e = ld_gtid(); e < n_del + n_ins; e += ld_gstride()) {
+    bool is_del = e < n_del;
+    leiden_edge x = is_del ? del[e] : ins[e - n_del];
+    bool bad = x.u < 0 || x.u >= n || x.v < 0 || x.v >= n || x.u == x.v || (!is_del && x.w <= 0);
+    if (bad) {
+      atomicExch(&cnt->error, 1);
+      x.u = 0; x.v = 1 % (int32_t)(n > 1 ? n : 1); x.w = 1;
+    }
+    uint64_t k1 = ((uint64_t)x.u << vb) | (uint64_t)x.v;
+    uint64_t k2 = ((uint64_t)x.v << vb) | (uint64_t)x.u;
+    if (is_del) {
+      dkey[2 * e] = k1; dkey[2 * e + 1] = k2;
+    } else {
+      int64_t f = e - n_del;
+      ikey[2 * f] = k1; ikey[2 * f + 1] = k2;
+      iw[2 * f] = x.w; iw[2 * f + 1] = x.w;
+    }
+  }
+}
+
+__global__ void k_head_flags(const uint64_t *key, int64_t n, int32_t *flag) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+}
+
+// Unique keys (and summed payload) into out_key/out_w at the scanned positions.
+__global__ void k_unique(const uint64_t *key, const int64_t *w, int64_t n, const int32_t *flag, const int64_t *pos,
+                         uint64_t *out_key, int64_t *out_w) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) {
+    int64_t p = pos[i] + flag[i] - 1;
+    if (flag[i]) out_key[p] = key[i];
+    if (out_w) atomicAdd((unsigned long long *)&out_w[p], (unsigned long long)w[i]);
+  }
+}
+
+// Deletions must name existing arcs; record the stored weight.
+__global__ void k_check_deletions(const uint64_t *dkey, int64_t nd, int vb, const int64_t *off, const int32_t *deg,
+                                  const int32_t *col, const int32_t *w, int64_t *dw, DevCounters *cnt) {
+  uint64_t mask = (1ull << vb) - 1;
+  for (int64_t i = ld_gtid(); i < nd; i += ld_gstride()) {
+    int32_t u = (int32_t)(dkey[i] >> vb), v = (int32_t)(dkey[i] & mask);
+    const int32_t *row = col + off[u];
+    int64_t p = lower_bound_i32(row, deg[u], v);
+    if (p < deg[u] && row[p] == v) dw[i] = w[off[u] + p];
+    else { dw[i] = 0; atomicExch(&cnt->error, 2); }
+  }
+}
+
+// Insertions: existing arc (not deleted in this batch) -> state 1, position;
+// otherwise state 0 (a new arc).
+__global__ void k_classify_insertions(const uint64_t *ikey, int64_t ni, const uint64_t *dkey, int64_t nd, int vb,
+                                      const int64_t *off, const int32_t *deg, const int32_t *col, int32_t *state,
+                                      int64_t *ipos) {
+  uint64_t mask = (1ull << vb) - 1;
+  for (int64_t i = ld_gtid(); i < ni; i += ld_gstride()) {
+    int32_t u = (int32_t)(ikey[i] >> vb), v = (int32_t)(ikey[i] & mask);
+    const int32_t *row = col + off[u];
+    int64_t p = lower_bound_i32(row, deg[u], v);
+    bool found = p < deg[u] && row[p] == v;
+    if (found) {
+      int64_t q = lower_bound_u64(dkey, nd, ikey[i]);
+      if (q < nd && dkey[q] == ikey[i]) found = false;  // deleted, then inserted again
+    }
+    state[i] = found ? 1 : 0;
+    ipos[i] = found ? off[u] + p : -1;
+  }
+}
+
+__global__ void k_new_flags(const int32_t *state, int64_t ni, int32_t *flag) {
+  for (int64_t i = ld_gtid(); i < ni; i += ld_gstride()) flag[i] = state[i] == 0 ? 1 : 0;
+}
+
+__global__ void k_compact_new(const uint64_t *ikey, const int64_t *iw, int64_t ni, const int32_t *flag,
+                              const int64_t *pos, uint64_t *okey, int64_t *ow) {
+  for (int64_t i = ld_gtid(); i < ni; i += ld_gstride())
+    if (flag[i]) { okey[pos[i]] = ikey[i]; ow[pos[i]] = iw[i]; }
+}
+
+__global__ void k_mark_touched(const uint64_t *key, int64_t nk, int vb, int32_t *touched) {
+  for (int64_t i = ld_gtid(); i < nk; i += ld_gstride()) touched[key[i] >> vb] = 1;
+}
+
+__global__ void k_compact_flags(const int32_t *flag, const int64_t *pos, int64_t n, int32_t *out) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride())
+    if (flag[i]) out[pos[i]] = (int32_t)i;
+}
+
+// New length of each touched row and its segments in the two arc lists.
+__global__ void k_row_plan(const int32_t *rows, const int64_t *nrows_p, int vb, const uint64_t *dkey, int64_t nd,
+                           const uint64_t *nkey, const int64_t *nn_p, const int64_t *off, const int32_t *deg,
+                           int32_t *dlo, int32_t *dhi, int32_t *ilo, int32_t *ihi, int64_t *len, DevCounters *cnt) {
+  int64_t nrows = *nrows_p, nn = *nn_p;
+  for (int64_t r = ld_gtid(); r < nrows; r += ld_gstride()) {
+    uint64_t u = (uint64_t)rows[r];
+    int64_t a = lower_bound_u64(dkey, nd, u << vb), b = lower_bound_u64(dkey, nd, (u + 1) << vb);
+    int64_t c = lower_bound_u64(nkey, nn, u << vb), d = lower_bound_u64(nkey, nn, (u + 1) << vb);
+    dlo[r] = (int32_t)a; dhi[r] = (int32_t)b; ilo[r] = (int32_t)c; ihi[r] = (int32_t)d;
+    int64_t L = (int64_t)deg[u] - (b - a) + (d - c);
+    len[r] = L;
+    if (L > off[u + 1] - off[u]) atomicExch(&cnt->overflow, 1);
+  }
+}
+
+__global__ void k_add_existing(const int64_t *ipos, const int32_t *state, const int64_t *iw, int64_t ni, int32_t *w) {
+  for (int64_t i = ld_gtid(); i < ni; i += ld_gstride())
+    if (state[i]) w[ipos[i]] += (int32_t)iw[i];
+}
+
+// Warp per touched row: old row minus deletions plus new arcs, by ranks.
+__global__ void k_merge_rows(const int32_t *rows, const int64_t *nrows_p, int vb, const uint64_t *dkey,
+                             const uint64_t *nkey, const int64_t *nw, const int32_t *dlo, const int32_t *dhi,
+                             const int32_t *ilo, const int32_t *ihi, const int64_t *tmp_off, const int64_t *off,
+                             const int32_t *deg, const int32_t *col, const int32_t *w, int32_t *tcol, int32_t *tw) {
+  int64_t nrows = *nrows_p;
+  int lane = threadIdx.x & 31;
+  int64_t warp = ld_gtid() >> 5, nwarps = ld_gstride() >> 5;
+  uint64_t mask = (1ull << vb) - 1;
+  for (int64_t r = warp; r < nrows; r += nwarps) {
+    int32_t u = rows[r];
+    const int32_t *row = col + off[u];
+    const int32_t *roww = w + off[u];
+    int64_t dg = deg[u];
+    const uint64_t *D = dkey + dlo[r];
+    int64_t nD = dhi[r] - dlo[r];
+    const uint64_t *I = nkey + ilo[r];
+    const int64_t *IW = nw + ilo[r];
+    int64_t nI = ihi[r] - ilo[r];
+    int64_t base = tmp_off[r];
+    uint64_t ubase = (uint64_t)u << vb;
+    for (int64_t p = lane; p < dg; p += 32) {
+      int32_t x = row[p];
+      int64_t dless = lower_bound_u64(D, nD, ubase | (uint64_t)x);
+      if (dless < nD && (D[dless] & mask) == (uint64_t)x) continue;  // deleted
+      int64_t iless = lower_bound_u64(I, nI, ubase | (uint64_t)x);
+      int64_t o = base + (p - dless) + iless;
+      tcol[o] = x;
+      tw[o] = roww[p];
+    }
+    for (int64_t k = lane; k < nI; k += 32) {
+      int32_t y = (int32_t)(I[k] & mask);
+      int64_t rless = lower_bound_i32(row, dg, y);
+      int64_t dless = lower_bound_u64(D, nD, ubase | (uint64_t)y);
+      int64_t o = base + k + (rless - dless);
+      tcol[o] = y;
+      tw[o] = (int32_t)IW[k];
+    }
+  }
+}
+
+__global__ void k_copy_back(const int32_t *rows, const int64_t *nrows_p, const int64_t *tmp_off, const int64_t *len,
+                            const int64_t *off, int32_t *deg, int32_t *col, int32_t *w, const int32_t *tcol,
+                            const int32_t *tw) {
+  int64_t nrows = *nrows_p;
+  int lane = threadIdx.x & 31;
+  int64_t warp = ld_gtid() >> 5, nwarps = ld_gstride() >> 5;
+  for (int64_t r = warp; r < nrows; r += nwarps) {
+    int32_t u = rows[r];
+    int64_t L = len[r], b = tmp_off[r], o = off[u];
+    for (int64_t x = lane; x < L; x += 32) { col[o + x] = tcol[b + x]; w[o + x] = tw[b + x]; }
+    if (lane == 0) deg[u] = (int32_t)L;
+  }
+}
+
+// ----- rebuild with fresh slack (when a row outgrows its capacity)
+__global__ void k_row_lengths(const int32_t *deg, int64_t n, int64_t *len) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) len[i] = deg[i];
+}
+__global__ void k_touched_lengths(const int32_t *rows, const int64_t *nrows_p, const int64_t *rlen, int64_t *len) {
+  for (int64_t r = ld_gtid(); r < *nrows_p; r += ld_gstride()) len[rows[r]] = rlen[r];
+}
+__global__ void k_capacity(const int64_t *len, int64_t n, double slack, int min_slack, int64_t *cap) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) {
+    int64_t L = len[i];
+    int64_t extra = (int64_t)((double)L * slack);
+    if (extra < min_slack) extra = min_slack;
+    cap[i] = L + extra;
+  }
+}
+// rowsrc[i] = index into the touched-row list, or -1
+__global__ void k_copy_rows_rebuild(int64_t n, const int64_t *old_off, const int32_t *old_deg, const int32_t *old_col,
+                                    const int32_t *old_w, const int32_t *rowsrc, const int64_t *tmp_off,
+                                    const int64_t *rlen, const int32_t *tcol, const int32_t *tw,
+                                    const int64_t *new_off, int32_t *new_deg, int32_t *new_col, int32_t *new_w) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ld_gtid() >> 5, nwarps = ld_gstride() >> 5;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    int32_t r = rowsrc ? rowsrc[u] : -1;
+    const int32_t *sc, *sw;
+    int64_t L;
+    if (r >= 0) { sc = tcol + tmp_off[r]; sw = tw + tmp_off[r]; L = rlen[r]; }
+    else { sc = old_col + old_off[u]; sw = old_w + old_off[u]; L = old_deg[u]; }
+    int64_t o = new_off[u];
+    for (int64_t x = lane; x < L; x += 32) { new_col[o + x] = sc[x]; new_w[o + x] = sw[x]; }
+    if (lane == 0) new_deg[u] = (int32_t)L;
+  }
+}
+__global__ void k_rowsrc(const int32_t *rows, const int64_t *nrows_p, int32_t *rowsrc) {
+  for (int64_t r = ld_gtid(); r < *nrows_p; r += ld_gstride()) rowsrc[rows[r]] = (int32_t)r;
+}
+
+// ----- marking (uses C^{t-1}, and K^{t-1}, Sigma^{t-1}, 2m^{t-1} for DS)
+__global__ void k_mark_df(const uint64_t *dkey, int64_t nd, const uint64_t *ikey, int64_t ni, int vb,
+                          const int32_t *C, uint8_t *dV) {
+  uint64_t mask = (1ull << vb) - 1;
+  for (int64_t i = ld_gtid(); i < nd + ni; i += ld_gstride()) {
+    bool del = i < nd;
+    uint64_t k = del ? dkey[i] : ikey[i - nd];
+    int32_t u = (int32_t)(k >> vb), v = (int32_t)(k & mask);
+    bool same = C[u] == C[v];
+    if (del ? same : !same) dV[u] = 1;
+  }
+}
+
+__global__ void k_mark_ds_del(const uint64_t *dkey, int64_t nd, int vb, const int32_t *C, uint8_t *dV, uint8_t *dE,
+                              uint8_t *dCf) {
+  uint64_t mask = (1ull << vb) - 1;
+  for (int64_t i = ld_gtid(); i < nd; i += ld_gstride()) {
+    int32_t u = (int32_t)(dkey[i] >> vb), v = (int32_t)(dkey[i] & mask);
+    if (C[u] == C[v]) { dV[u] = 1; dE[u] = 1; dCf[C[v]] = 1; }
+  }
+}
+
+// (src, C[dst]) keys of the cross-community insertions; same-community
+// arcs get the key ~0 and sort last.
+__global__ void k_ds_keys(const uint64_t *ikey, const int64_t *iw, int64_t ni, int vb, const int32_t *C,
+                          uint64_t *okey, int64_t *ow) {
+  uint64_t mask = (1ull << vb) - 1;
+  for (int64_t i = ld_gtid(); i < ni; i += ld_gstride()) {
+    int32_t u = (int32_t)(ikey[i] >> vb), v = (int32_t)(ikey[i] & mask);
+    if (C[u] != C[v]) { okey[i] = ((uint64_t)u << vb) | (uint64_t)C[v]; ow[i] = iw[i]; }
+    else { okey[i] = ~0ull; ow[i] = 0; }
+  }
+}
+
+// Sorted unique (src, c) pairs with summed weights H; warp per source run:
+// c* = argmax 2m*H[c] - K_src*Sigma_c, ties to the lowest c.
+__global__ void k_ds_best(const uint64_t *pkey, const int64_t *pw, const int64_t *np_p, int vb, const int64_t *K,
+                          const int64_t *Sig, const DevCounters *cnt, uint8_t *dV, uint8_t *dE, uint8_t *dCf) {
+  int64_t np = *np_p;
+  uint64_t mask = (1ull << vb) - 1;
+  int64_t m2 = cnt->m2;
+  for (int64_t i = ld_gtid(); i < np; i += ld_gstride()) {
+    if (pkey[i] == ~0ull) continue;
+    uint64_t src = pkey[i] >> vb;
+    if (i > 0 && (pkey[i - 1] >> vb) == src) continue;  // only the run head works
+    int32_t best = -1;
+    i128 bv = 0;
+    for (int64_t j = i; j < np && pkey[j] != ~0ull && (pkey[j] >> vb) == src; j++) {
+      int32_t c = (int32_t)(pkey[j] & mask);
+      i128 v = (i128)m2 * pw[j] - (i128)K[src] * Sig[c];
+      if (ld_better(v, c, bv, best)) { bv = v; best = c; }
+    }
+    dV[src] = 1; dE[src] = 1; dCf[best] = 1;
+  }
+}
+
+// Warp per vertex with dE: neighbours of G^t become affected.
+__global__ void k_ds_expand_neighbours(const uint8_t *dE, int64_t n, const int64_t *off, const int32_t *deg,
+                                       const int32_t *col, uint8_t *dV) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ld_gtid() >> 5, nwarps = ld_gstride() >> 5;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    if (!dE[i]) continue;
+    for (int64_t a = lane; a < deg[i]; a += 32) dV[col[off[i] + a]] = 1;
+  }
+}
+__global__ void k_ds_expand_communities(const uint8_t *dCf, const int32_t *C, int64_t n, uint8_t *dV) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride())
+    if (dCf[C[i]]) dV[i] = 1;
+}
+
+// Alg. update (updateWeights, updateChanges) on both arc lists.
+__global__ void k_update_weights(const uint64_t *dkey, const int64_t *dw, int64_t nd, const uint64_t *ikey,
+                                 const int64_t *iw, int64_t ni, int vb, const int32_t *C, int64_t *K, int64_t *Sig,
+                                 int64_t *dSig, DevCounters *cnt) {
+  int64_t acc = 0;
+  for (int64_t i = ld_gtid(); i < nd + ni; i += ld_gstride()) {
+    bool del = i < nd;
+    uint64_t k = del ? dkey[i] : ikey[i - nd];
+    int64_t w = del ? dw[i] : iw[i - nd];
+    int32_t u = (int32_t)(k >> vb);
+    int32_t c = C[u];
+    int64_t s = del ? -w : w;
+    atomicAdd((unsigned long long *)&K[u], (unsigned long long)s);
+    atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)s);
+    atomicAdd((unsigned long long *)&dSig[c], (unsigned long long)w);
+    acc += s;
+  }
+  acc = ld_warp_sum_i64(acc);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd((unsigned long long *)&cnt->m2, (unsigned long long)acc);
+}
+
+// Alg. leidenmk: dS for same-community deletions; dR for same-community
+// arcs of either list with dSigma/Sigma > tau_re.
+__global__ void k_mark_communities(const uint64_t *dkey, int64_t nd, const uint64_t *ikey, int64_t ni, int vb,
+                                   const int32_t *C, const int64_t *Sig, const int64_t *dSig, double tau_re,
+                                   uint8_t *dS, uint8_t *dR) {
+  uint64_t mask = (1ull << vb) - 1;
+  for (int64_t i = ld_gtid(); i < nd + ni; i += ld_gstride()) {
+    bool del = i < nd;
+    uint64_t k = del ? dkey[i] : ikey[i - nd];
+    int32_t u = (int32_t)(k >> vb), v = (int32_t)(k & mask);
+    int32_t c = C[u];
+    if (c != C[v]) continue;
+    if (del) dS[c] = 1;
+    if ((double)dSig[c] / (double)Sig[c] > tau_re) dR[c] = 1;
+  }
+}
+__global__ void k_reset_changes(const uint64_t *dkey, int64_t nd, const uint64_t *ikey, int64_t ni, int vb,
+                                const int32_t *C, const uint8_t *dR, int64_t *dSig) {
+  for (int64_t i = ld_gtid(); i < nd + ni; i += ld_gstride()) {
+    uint64_t k = i < nd ? dkey[i] : ikey[i - nd];
+    int32_t c = C[(int32_t)(k >> vb)];
+    if (dR[c]) dSig[c] = 0;
+  }
+}
+
+int bits_for(int64_t n) {
+  int b = 1;
+  while (((int64_t)1 << b) < n) b++;
+  return b;
+}
+
+template <typename T>
+cudaError_t grow(leiden_handle *h, T **p, int64_t count) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, (size_t)std::max<int64_t>(count, 1) * sizeof(T));
+  if (e != cudaSuccess) return e;
+  h->owned.push_back(q);
+  *p = (T *)q;
+  return cudaSuccess;
+}
+
+void release(leiden_handle *h, void *p) {
+  if (!p) return;
+  for (auto &q : h->owned)
+    if (q == p) { cudaFree(q); q = nullptr; }
+}
+
+cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
+  BatchBuffers &b = h->b;
+  if (edges <= b.cap_edges) return cudaSuccess;
+  int64_t cap = std::max<int64_t>(edges, 1024);
+  void *old[] = {b.dkey, b.dkey_alt, b.ikey, b.ikey_alt, b.iw, b.iw_alt, b.dw, b.flag,
+                 b.pos, b.ins_state, b.ins_pos, b.row_dlo, b.row_dhi, b.row_ilo, b.row_ihi, b.row_len,
+                 b.row_tmp_off, b.rows, b.ds_key, b.ds_key_alt, b.ds_w, b.ds_w_alt, b.ds_ukey, b.ds_uw};
+  for (void *p : old) release(h, p);
+  int64_t arcs = 2 * cap;
+  cudaError_t e = cudaSuccess;
+  auto chk = [&](cudaError_t x) { if (x != cudaSuccess) e = x; };
+  chk(grow(h, &b.dkey, arcs));
+  chk(grow(h, &b.dkey_alt, arcs));
+  chk(grow(h, &b.ikey, arcs));
+  chk(grow(h, &b.ikey_alt, arcs));
+  chk(grow(h, &b.iw, arcs));
+  chk(grow(h, &b.iw_alt, arcs));
+  chk(grow(h, &b.dw, arcs));
+  chk(grow(h, &b.flag, arcs + 1));
+  chk(grow(h, &b.pos, arcs + 1));
+  chk(grow(h, &b.ins_state, arcs));
+  chk(grow(h, &b.ins_pos, arcs));
+  int64_t rows = std::min<int64_t>(2 * arcs, h->n) + 1;
+  chk(grow(h, &b.rows, rows));
+  chk(grow(h, &b.row_dlo, rows));
+  chk(grow(h, &b.row_dhi, rows));
+  chk(grow(h, &b.row_ilo, rows));
+  chk(grow(h, &b.row_ihi, rows));
+  chk(grow(h, &b.row_len, rows + 1));
+  chk(grow(h, &b.row_tmp_off, rows + 1));
+  chk(grow(h, &b.ds_key, arcs));
+  chk(grow(h, &b.ds_key_alt, arcs));
+  chk(grow(h, &b.ds_w, arcs));
+  chk(grow(h, &b.ds_w_alt, arcs));
+  chk(grow(h, &b.ds_ukey, arcs));
+  chk(grow(h, &b.ds_uw, arcs));
+  if (!b.counts) chk(grow(h, &b.counts, 8));
+  if (e == cudaSuccess) b.cap_edges = cap;
+  return e;
+}
+
+cudaError_t ensure_scan_tmp(leiden_handle *h, size_t bytes) {
+  if (bytes <= h->scan_tmp_bytes) return cudaSuccess;
+  release(h, h->scan_tmp);
+  void *p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) return e;
+  h->owned.push_back(p);
+  h->scan_tmp = p;
+  h->scan_tmp_bytes = bytes;
+  return cudaSuccess;
+}
+
+cudaError_t ensure_tmp_rows(leiden_handle *h, int64_t arcs) {
+  BatchBuffers &b = h->b;
+  if (arcs <= b.tmp_cap) return cudaSuccess;
+  release(h, b.tmp_col);
+  release(h, b.tmp_w);
+  int64_t cap = std::max<int64_t>(arcs, 4096);
+  cudaError_t e = grow(h, &b.tmp_col, cap);
+  if (e == cudaSuccess) e = grow(h, &b.tmp_w, cap);
+  if (e == cudaSuccess) b.tmp_cap = cap;
+  return e;
+}
+
+leiden_status fail(leiden_handle *h, leiden_status st, const std::string &msg) {
+  h->err = msg;
+  return st;
+}
+
+}  // namespace
+
+// Rebuild G^t with new capacities: rows keep their content (touched rows
+// come from the merge buffer).  Reallocates the aggregation buffers when the
+// arc capacity grows.
+static leiden_status rebuild_graph(leiden_handle *h, int64_t nrows_host, const int64_t *nrows_dev) {
+  cudaStream_t s = h->stream;
+  int64_t n = h->n;
+  BatchBuffers &b = h->b;
+  int64_t *len = h->lbuf0, *cap = h->lbuf1;
+  k_row_lengths<<<grid_for(n, TB), TB, 0, s>>>(h->g_deg, n, len);
+  k_touched_lengths<<<grid_for(nrows_host, TB), TB, 0, s>>>(b.rows, nrows_dev, b.row_len, len);
+  k_capacity<<<grid_for(n, TB), TB, 0, s>>>(len, n, h->p.slack, h->p.min_slack, cap);
+  int64_t *new_off = nullptr;
+  if (grow(h, &new_off, n + 1) != cudaSuccess) return fail(h, LEIDEN_ERR_OOM, "rebuild: offsets");
+  if (ensure_scan_tmp(h, scan_tmp_bytes(n + 1)) != cudaSuccess) return fail(h, LEIDEN_ERR_OOM, "scan tmp");
+  exclusive_scan_i64(cap, new_off, n, h->scan_tmp, s);
+  int64_t total = 0;
+  cudaMemcpyAsync(&total, new_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  int32_t *new_col = nullptr, *new_w = nullptr, *new_deg = nullptr;
+  if (grow(h, &new_col, total) != cudaSuccess || grow(h, &new_w, total) != cudaSuccess ||
+      grow(h, &new_deg, n) != cudaSuccess)
+    return fail(h, LEIDEN_ERR_OOM, "rebuild: arcs");
+  int32_t *rowsrc = h->ibuf2;
+  launch_fill_i32(rowsrc, -1, n, s);
+  k_rowsrc<<<grid_for(nrows_host, TB), TB, 0, s>>>(b.rows, nrows_dev, rowsrc);
+  k_copy_rows_rebuild<<<grid_for(n * 32, TB), TB, 0, s>>>(n, h->g_off, h->g_deg, h->g_col, h->g_w, rowsrc,
+                                                          b.row_tmp_off, b.row_len, b.tmp_col, b.tmp_w, new_off,
+                                                          new_deg, new_col, new_w);
+  cudaStreamSynchronize(s);
+  release(h, h->g_off);
+  release(h, h->g_col);
+  release(h, h->g_w);
+  release(h, h->g_deg);
+  h->g_off = new_off;
+  h->g_col = new_col;
+  h->g_w = new_w;
+  h->g_deg = new_deg;
+  h->g_cap = total;
+  if (total > h->y_cap) {
+    for (int k = 0; k < 2; k++) {
+      release(h, h->y_col[k]);
+      release(h, h->y_w[k]);
+      if (grow(h, &h->y_col[k], total) != cudaSuccess || grow(h, &h->y_w[k], total) != cudaSuccess)
+        return fail(h, LEIDEN_ERR_OOM, "rebuild: aggregation buffers");
+    }
+    h->y_cap = total;
+  }
+  return LEIDEN_OK;
+}
+
+leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, int64_t n_del,
+                                   const leiden_edge *d_ins, int64_t n_ins, int mode) {
+  cudaStream_t s = h->stream;
+  int64_t n = h->n;
+  BatchBuffers &b = h->b;
+  int vb = bits_for(n);
+  DevCounters *cnt = h->dcnt;
+  if (ensure_batch(h, std::max(n_del, n_ins)) != cudaSuccess) return fail(h, LEIDEN_ERR_OOM, "batch buffers");
+  int64_t nda = 2 * n_del, nia = 2 * n_ins;
+  if (ensure_scan_tmp(h, std::max(sort_tmp_bytes(std::max(nda, nia)), scan_tmp_bytes(n + 1))) != cudaSuccess)
+    return fail(h, LEIDEN_ERR_OOM, "scan tmp");
+  cudaMemsetAsync(&cnt->error, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(&cnt->overflow, 0, sizeof(int32_t), s);
+  if (n_del + n_ins > 0)
+    k_expand<<<grid_for(n_del + n_ins, TB), TB, 0, s>>>(d_del, n_del, d_ins, n_ins, n, vb, b.dkey, b.ikey, b.iw, cnt);
+  radix_sort_u64(b.dkey, b.dkey_alt, nullptr, nullptr, nda, 2 * vb, h->scan_tmp, s);
+  radix_sort_u64(b.ikey, b.ikey_alt, b.iw, b.iw_alt, nia, 2 * vb, h->scan_tmp, s);
+  // deduplicate: deletions collapse (-> DK), insertions add up (-> IK, IW)
+  int64_t *counts = b.counts;  // [0] nd, [1] ni, [2] new insertions
+  cudaMemsetAsync(counts, 0, 4 * sizeof(int64_t), s);
+  uint64_t *DK = b.dkey_alt, *IK = b.ikey_alt;
+  int64_t *IW = b.iw_alt, *DW = b.dw;
+  if (nda > 0) {
+    k_head_flags<<<grid_for(nda, TB), TB, 0, s>>>(b.dkey, nda, b.flag);
+    exclusive_scan_i32_to_i64(b.flag, b.pos, nda, h->scan_tmp, s);
+    k_unique<<<grid_for(nda, TB), TB, 0, s>>>(b.dkey, nullptr, nda, b.flag, b.pos, DK, nullptr);
+    cudaMemcpyAsync(counts + 0, b.pos + nda, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  }
+  if (nia > 0) {
+    k_head_flags<<<grid_for(nia, TB), TB, 0, s>>>(b.ikey, nia, b.flag);
+    exclusive_scan_i32_to_i64(b.flag, b.pos, nia, h->scan_tmp, s);
+    cudaMemsetAsync(IW, 0, (size_t)nia * sizeof(int64_t), s);
+    k_unique<<<grid_for(nia, TB), TB, 0, s>>>(b.ikey, b.iw, nia, b.flag, b.pos, IK, IW);
+    cudaMemcpyAsync(counts + 1, b.pos + nia, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  }
+  cudaMemcpyAsync(b.hcounts, counts, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  int64_t nd = b.hcounts[0], ni = b.hcounts[1];
+  // deletions must exist (stored weight -> DW); insertions: existing or new
+  if (nd > 0)
+    k_check_deletions<<<grid_for(nd, TB), TB, 0, s>>>(DK, nd, vb, h->g_off, h->g_deg, h->g_col, h->g_w, DW, cnt);
+  uint64_t *NK = b.ikey;  // new insertions, compacted in sorted order
+  int64_t *NW = b.iw;
+  if (ni > 0) {
+    k_classify_insertions<<<grid_for(ni, TB), TB, 0, s>>>(IK, ni, DK, nd, vb, h->g_off, h->g_deg, h->g_col,
+                                                          b.ins_state, b.ins_pos);
+    k_new_flags<<<grid_for(ni, TB), TB, 0, s>>>(b.ins_state, ni, b.flag);
+    exclusive_scan_i32_to_i64(b.flag, b.pos, ni, h->scan_tmp, s);
+    k_compact_new<<<grid_for(ni, TB), TB, 0, s>>>(IK, IW, ni, b.flag, b.pos, NK, NW);
+    cudaMemcpyAsync(counts + 2, b.pos + ni, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  }
+  cudaMemcpyAsync(b.hcounts + 2, counts + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&h->hcnt->error, &cnt->error, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  if (h->hcnt->error)
+    return fail(h, LEIDEN_ERR_BATCH, h->hcnt->error == 2 ? "batch deletes an edge that does not exist"
+                                                         : "batch edge out of range, self-loop or weight <= 0");
+  int64_t nn = b.hcounts[2];
+  // rows whose structure changes: sources of deletions and of new arcs
+  int32_t *touched = h->ibuf0;
+  int64_t nrows = 0, tmp_total = 0;
+  if (nd + nn > 0) {
+    cudaMemsetAsync(touched, 0, (size_t)n * sizeof(int32_t), s);
+    if (nd > 0) k_mark_touched<<<grid_for(nd, TB), TB, 0, s>>>(DK, nd, vb, touched);
+    if (nn > 0) k_mark_touched<<<grid_for(nn, TB), TB, 0, s>>>(NK, nn, vb, touched);
+    exclusive_scan_i32_to_i64(touched, h->lbuf0, n, h->scan_tmp, s);
+    k_compact_flags<<<grid_for(n, TB), TB, 0, s>>>(touched, h->lbuf0, n, b.rows);
+    cudaMemcpyAsync(counts + 3, h->lbuf0 + n, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+    k_row_plan<<<grid_for(std::min<int64_t>(n, nd + nn), TB), TB, 0, s>>>(
+        b.rows, counts + 3, vb, DK, nd, NK, counts + 2, h->g_off, h->g_deg, b.row_dlo, b.row_dhi, b.row_ilo,
+        b.row_ihi, b.row_len, cnt);
+    cudaMemcpyAsync(b.hcounts + 3, counts + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    nrows = b.hcounts[3];
+    exclusive_scan_i64(b.row_len, b.row_tmp_off, nrows, h->scan_tmp, s);
+    cudaMemcpyAsync(&b.hcounts[4], b.row_tmp_off + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(&h->hcnt->overflow, &cnt->overflow, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    tmp_total = b.hcounts[4];
+  }
+  bool overflow = nrows > 0 && h->hcnt->overflow != 0;
+  if (ensure_tmp_rows(h, tmp_total) != cudaSuccess) return fail(h, LEIDEN_ERR_OOM, "merge buffer");
+  // ---- apply: from here on the handle changes
+  if (ni > 0) k_add_existing<<<grid_for(ni, TB), TB, 0, s>>>(b.ins_pos, b.ins_state, IW, ni, h->g_w);
+  if (nrows > 0) {
+    k_merge_rows<<<grid_for(nrows * 32, TB), TB, 0, s>>>(b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo, b.row_dhi,
+                                                         b.row_ilo, b.row_ihi, b.row_tmp_off, h->g_off, h->g_deg,
+                                                         h->g_col, h->g_w, b.tmp_col, b.tmp_w);
+    if (!overflow) {
+      k_copy_back<<<grid_for(nrows * 32, TB), TB, 0, s>>>(b.rows, counts + 3, b.row_tmp_off, b.row_len, h->g_off,
+                                                          h->g_deg, h->g_col, h->g_w, b.tmp_col, b.tmp_w);
+    } else {
+      leiden_status st = rebuild_graph(h, nrows, counts + 3);
+      if (st != LEIDEN_OK) return st;
+    }
+  }
+  h->g_arcs = h->g_arcs - nd + nn;
+  h->stats.batch_arcs = nd + ni;
+  // ---- affected vertices (C^{t-1}; DS also K^{t-1}, Sigma^{t-1}, 2m^{t-1})
+  uint8_t *dV = h->dV;
+  if (mode == LEIDEN_ND) {
+    cudaMemsetAsync(dV, 1, (size_t)n, s);
+  } else {
+    cudaMemsetAsync(dV, 0, (size_t)n, s);
+    if (mode == LEIDEN_DF) {
+      if (nd + ni > 0) k_mark_df<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, dV);
+    } else {
+      cudaMemsetAsync(h->dE, 0, (size_t)n, s);
+      cudaMemsetAsync(h->dCf, 0, (size_t)n, s);
+      if (nd > 0) k_mark_ds_del<<<grid_for(nd, TB), TB, 0, s>>>(DK, nd, vb, h->C, dV, h->dE, h->dCf);
+      if (ni > 0) {
+        // H of each insertion source: (src, C[dst]) pairs, sorted, runs summed
+        k_ds_keys<<<grid_for(ni, TB), TB, 0, s>>>(IK, IW, ni, vb, h->C, b.ds_key, b.ds_w);
+        radix_sort_u64(b.ds_key, b.ds_key_alt, b.ds_w, b.ds_w_alt, ni, 64, h->scan_tmp, s);
+        k_head_flags<<<grid_for(ni, TB), TB, 0, s>>>(b.ds_key, ni, b.flag);
+        exclusive_scan_i32_to_i64(b.flag, b.pos, ni, h->scan_tmp, s);
+        cudaMemsetAsync(b.ds_uw, 0, (size_t)ni * sizeof(int64_t), s);
+        k_unique<<<grid_for(ni, TB), TB, 0, s>>>(b.ds_key, b.ds_w, ni, b.flag, b.pos, b.ds_ukey, b.ds_uw);
+        k_ds_best<<<grid_for(ni, TB), TB, 0, s>>>(b.ds_ukey, b.ds_uw, b.pos + ni, vb, h->K, h->Sig, cnt, dV, h->dE,
+                                                  h->dCf);
+      }
+      k_ds_expand_neighbours<<<grid_for(n * 32, TB), TB, 0, s>>>(h->dE, n, h->g_off, h->g_deg, h->g_col, dV);
+      k_ds_expand_communities<<<grid_for(n, TB), TB, 0, s>>>(h->dCf, h->C, n, dV);
+    }
+  }
+  // ---- Alg. update, then Alg. leidenmk (dS, dR; reset dSigma of refined)
+  cudaMemsetAsync(h->dS, 0, (size_t)n, s);
+  cudaMemsetAsync(h->dR, 0, (size_t)n, s);
+  if (nd + ni > 0) {
+    k_update_weights<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, DW, nd, IK, IW, ni, vb, h->C, h->K, h->Sig, h->dSig,
+                                                           cnt);
+    k_mark_communities<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, h->Sig, h->dSig,
+                                                             h->p.tau_refine, h->dS, h->dR);
+    k_reset_changes<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, h->dR, h->dSig);
+  }
+  return LEIDEN_OK;
+}

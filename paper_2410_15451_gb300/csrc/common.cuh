@@ -1,0 +1,131 @@
+// Device-side helpers shared by the kernels of the GB300 dynamic Leiden
+// library.  Internal header: not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+typedef __int128 i128;
+typedef unsigned __int128 u128;
+
+#define LD_WARP 32
+#define LD_FULL 0xffffffffu
+#define LD_EMPTY_KEY (-1)
+
+// ---------------------------------------------------------------- counters
+// One block of device counters per handle, mirrored to pinned host memory at
+// the few host synchronisation points of a call.
+struct DevCounters {
+  unsigned long long dq[2];       // sum of accepted gains g (int128, two's complement)
+  int32_t bin_count[4];           // vertices in each degree bin of the current sub-sweep
+  int32_t movers;                 // deferred moves of the current sub-sweep (SYNC)
+  int32_t accepted;               // refinement moves applied in this round
+  int32_t cand_count[2];          // refinement candidate lists (ping-pong)
+  int32_t refined_any;            // a vertex lies in a refined bound
+  int32_t error;                  // batch validation error (first offending arc + 1)
+  int32_t overflow;               // a touched CSR row outgrew its capacity
+  int32_t list_count;             // generic list length
+  int32_t ncomm;                  // communities after dense renumbering
+  int32_t split_count;            // vertices in communities to split
+  int32_t max_count;              // max degree (level), max community degree
+  int64_t processed;              // local-moving vertex visits
+  int64_t arcs;                   // local-moving arcs scanned
+  int64_t moves;                  // local-moving moves
+  int64_t ref_processed;          // refinement vertex visits
+  int64_t ref_arcs;               // refinement arcs scanned
+  int64_t m2;                     // 2m (sum of arc weights), device copy
+  int64_t sigma_intra;            // modularity: intra-community arc weight
+  unsigned long long sq[2];       // modularity: sum of Sigma_c^2 (int128)
+  int64_t batch_dw;               // batch: change of 2m
+  int64_t pad[3];
+};
+
+// ---------------------------------------------------------------- hashing
+// SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).
+__host__ __device__ __forceinline__ uint64_t ld_splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Sub-sweep class of a vertex in the snapshot schedule.
+__device__ __forceinline__ int ld_class_of(int64_t v, int classes_mask) {
+  return (int)(ld_splitmix64((uint64_t)v) & (uint64_t)classes_mask);
+}
+
+// Multiplicative hash of a community id into a power-of-two table.
+__device__ __forceinline__ uint32_t ld_hash32(uint32_t k) {
+  k *= 0x9E3779B1u;
+  return k ^ (k >> 15);
+}
+
+// ---------------------------------------------------------------- int128
+__device__ __forceinline__ void ld_atomic_add_i128(unsigned long long *p, i128 v) {
+  unsigned long long lo = (unsigned long long)(u128)v;
+  unsigned long long hi = (unsigned long long)((u128)v >> 64);
+  if (lo == 0 && hi == 0) return;
+  unsigned long long old = atomicAdd(&p[0], lo);
+  unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+  if (hi + carry) atomicAdd(&p[1], hi + carry);
+}
+
+__device__ __forceinline__ i128 ld_shfl_xor_i128(i128 v, int mask) {
+  long long lo = (long long)(unsigned long long)(u128)v;
+  long long hi = (long long)((u128)v >> 64);
+  lo = __shfl_xor_sync(LD_FULL, lo, mask);
+  hi = __shfl_xor_sync(LD_FULL, hi, mask);
+  return (i128)(((u128)(unsigned long long)hi << 64) | (u128)(unsigned long long)lo);
+}
+
+__device__ __forceinline__ i128 ld_shfl_i128(i128 v, int src) {
+  long long lo = (long long)(unsigned long long)(u128)v;
+  long long hi = (long long)((u128)v >> 64);
+  lo = __shfl_sync(LD_FULL, lo, src);
+  hi = __shfl_sync(LD_FULL, hi, src);
+  return (i128)(((u128)(unsigned long long)hi << 64) | (u128)(unsigned long long)lo);
+}
+
+// Candidate (value, community) ordered by larger value, then smaller id.
+// c < 0 means "no candidate".
+__device__ __forceinline__ bool ld_better(i128 v1, int32_t c1, i128 v2, int32_t c2) {
+  if (c1 < 0) return false;
+  if (c2 < 0) return true;
+  return v1 > v2 || (v1 == v2 && c1 < c2);
+}
+
+// Warp-wide argmax of (v, c); every lane receives the winner.
+__device__ __forceinline__ void ld_warp_argmax(i128 &v, int32_t &c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    i128 v2 = ld_shfl_xor_i128(v, o);
+    int32_t c2 = __shfl_xor_sync(LD_FULL, c, o);
+    if (ld_better(v2, c2, v, c)) { v = v2; c = c2; }
+  }
+}
+
+__device__ __forceinline__ int64_t ld_warp_sum_i64(int64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(LD_FULL, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- bitmaps
+__device__ __forceinline__ bool ld_bit_test(const uint32_t *bm, int64_t i) {
+  return (bm[i >> 5] >> (i & 31)) & 1u;
+}
+// Sets bit i; returns true if it was clear.
+__device__ __forceinline__ bool ld_bit_set(uint32_t *bm, int64_t i) {
+  uint32_t m = 1u << (i & 31);
+  return (atomicOr(&bm[i >> 5], m) & m) == 0;
+}
+
+// Weight load for level 0 (int32) and aggregated levels (int64).
+template <typename W>
+__device__ __forceinline__ int64_t ld_w(const W *w, int64_t a) {
+  return (int64_t)w[a];
+}
+
+// Grid-stride helpers.
+__device__ __forceinline__ int64_t ld_gtid() { return (int64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ int64_t ld_gstride() { return (int64_t)gridDim.x * blockDim.x; }

@@ -1,0 +1,172 @@
+// Internal host-side declarations of the GB300 dynamic Leiden library: the
+// handle, its device buffers, and the launchers each .cu file provides.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/leiden_gb300.h"
+#include "common.cuh"
+
+// A level of the dendrogram as the kernels see it: rows off[i] .. off[i] + deg[i].
+struct LevelGraph {
+  int64_t n = 0;
+  const int64_t *off = nullptr;
+  const int32_t *deg = nullptr;
+  const int32_t *col = nullptr;
+  const void *w = nullptr;  // int32 at level 0, int64 above
+  bool w64 = false;
+  int32_t maxdeg = 0;
+};
+
+// Degree bins of the vertex-centric kernels (local moving, refinement).
+enum { BIN_WARP = 0, BIN_BLOCK = 1, BIN_HUGE = 2, NBINS = 3 };
+constexpr int BIN_WARP_MAX = 128;    // one warp, shared table of <= 256 slots
+constexpr int BIN_BLOCK_MAX = 1024;  // one block, shared table of 2048 slots
+
+struct BatchBuffers {
+  int64_t cap_edges = 0;  // capacity in undirected edges, per side
+  uint64_t *dkey = nullptr, *dkey_alt = nullptr;         // deletion arcs (src<<32|dst)
+  uint64_t *ikey = nullptr, *ikey_alt = nullptr;         // insertion arcs
+  int64_t *iw = nullptr, *iw_alt = nullptr;              // insertion weights
+  int64_t *dw = nullptr;                                 // stored weights of deleted arcs
+  int32_t *flag = nullptr;                               // scan flags
+  int64_t *pos = nullptr;                                // scan output
+  int32_t *ins_state = nullptr;                          // 1 = existing arc, 0 = new arc
+  int64_t *ins_pos = nullptr;                            // arc index of existing insertions
+  int32_t *rows = nullptr;                               // touched rows
+  int32_t *row_dlo = nullptr, *row_dhi = nullptr;        // deletion arc range of a row
+  int32_t *row_ilo = nullptr, *row_ihi = nullptr;        // insertion arc range of a row
+  int64_t *row_len = nullptr;                            // new row length
+  int64_t *row_tmp_off = nullptr;                        // offset into the merge buffer
+  uint64_t *ds_key = nullptr, *ds_key_alt = nullptr, *ds_ukey = nullptr;  // DS (src, C[dst]) pairs
+  int64_t *ds_w = nullptr, *ds_w_alt = nullptr, *ds_uw = nullptr;
+  int64_t *counts = nullptr;                             // device counts of the batch pipeline
+  int64_t hcounts[8] = {};                               // host copies
+  int32_t *tmp_col = nullptr;                            // merged rows
+  int32_t *tmp_w = nullptr;
+  int64_t tmp_cap = 0;
+};
+
+struct leiden_handle {
+  leiden_params p{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sm_count = 152;
+  int64_t n = 0;
+
+  // G^t: device CSR with slack
+  int64_t *g_off = nullptr;  // [n+1] row starts (capacity based)
+  int32_t *g_deg = nullptr;  // [n]
+  int32_t *g_col = nullptr;  // [g_cap]
+  int32_t *g_w = nullptr;    // [g_cap]
+  int64_t g_cap = 0;
+  int64_t g_arcs = 0;
+  int32_t g_maxdeg = 0;
+  int64_t m2 = 0;            // 2m = sum of arc weights
+
+  // auxiliary state {C, K, Sigma, Delta Sigma}
+  int32_t *C = nullptr;
+  int64_t *K = nullptr, *Sig = nullptr, *dSig = nullptr;
+  uint8_t *dV = nullptr;
+  bool has_static = false;
+
+  // per-vertex work arrays (length n or n+1)
+  int32_t *Cp = nullptr, *CB = nullptr, *Ctop = nullptr, *csize = nullptr, *rep = nullptr;
+  int32_t *prop = nullptr, *parent = nullptr, *ibuf0 = nullptr, *ibuf1 = nullptr, *ibuf2 = nullptr;
+  int64_t *Kp = nullptr, *Sp = nullptr, *S2 = nullptr, *lbuf0 = nullptr, *lbuf1 = nullptr;
+  int64_t *lbuf2 = nullptr, *lbuf3 = nullptr;
+  uint8_t *dS = nullptr, *dR = nullptr, *dS2 = nullptr, *dR2 = nullptr, *dE = nullptr, *dCf = nullptr;
+  uint32_t *unproc = nullptr;  // bitmap, words = n/32 + 2
+  int32_t *bins = nullptr;     // NBINS * n
+  int32_t *movers = nullptr;   // [n]
+  int32_t *mtarget = nullptr;  // [n]
+  int32_t *cand = nullptr;     // 2 * n
+
+  // aggregation (ping-pong super-vertex graphs)
+  int64_t *coff = nullptr;   // [n+1] community vertex offsets
+  int32_t *cverts = nullptr; // [n]
+  int64_t *cflat = nullptr;  // [n+1] flat arc offsets in cverts order
+  int64_t *y_off[2] = {nullptr, nullptr};
+  int32_t *y_deg[2] = {nullptr, nullptr};
+  int32_t *y_col[2] = {nullptr, nullptr};
+  int64_t *y_w[2] = {nullptr, nullptr};
+  int64_t y_cap = 0;
+
+  // global hash scratch for the largest vertices / communities
+  void *hscratch = nullptr;
+  size_t hscratch_bytes = 0;
+
+  // tracking hash table of (old, new) pairs
+  uint64_t *tr_keys = nullptr;
+  int64_t *tr_vals = nullptr;
+  int64_t tr_cap = 0;
+
+  // scan scratch
+  void *scan_tmp = nullptr;
+  size_t scan_tmp_bytes = 0;
+
+  DevCounters *dcnt = nullptr;  // device
+  DevCounters *hcnt = nullptr;  // pinned host mirror
+
+  BatchBuffers b;
+  leiden_edge *up_del = nullptr, *up_ins = nullptr;  // staging of host batches
+  int64_t up_cap = 0;
+
+  cudaEvent_t ev[8] = {};
+  leiden_stats stats{};
+  int64_t trace[2 + 10 * 25] = {};
+  std::string err;
+  leiden_status fatal = LEIDEN_OK;  // set by a launcher that could not run
+  std::vector<void *> owned;  // every cudaMalloc of the handle
+};
+
+// ------------------------------------------------------------ prims.cu
+// Exclusive scan of n values; out[n] receives the total.  `tmp` must hold
+// scan_tmp_bytes(n) bytes.  in == out is allowed.
+size_t scan_tmp_bytes(int64_t n);
+cudaError_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s);
+cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s);
+// Stable LSD radix sort of 64-bit keys on their low `bits` bits, with an
+// optional int64 payload.  Buffers are ping-ponged; the result is written
+// back to keys/vals.  `tmp` must hold sort_tmp_bytes(n) bytes.
+size_t sort_tmp_bytes(int64_t n);
+cudaError_t radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, int64_t *vals, int64_t *vals_alt, int64_t n,
+                           int bits, void *tmp, cudaStream_t s);
+void launch_fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s);
+void launch_fill_i64(int64_t *p, int64_t v, int64_t n, cudaStream_t s);
+void launch_iota_i32(int32_t *p, int64_t n, cudaStream_t s);
+int grid_for(int64_t n, int block, int max_blocks = 152 * 16);
+
+// ------------------------------------------------------------ batch.cu
+leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, int64_t n_del,
+                                   const leiden_edge *d_ins, int64_t n_ins, int mode);
+
+// ------------------------------------------------------------ move.cu
+// One local-moving sub-sweep of class `cls` (0 .. classes-1).
+void lm_subsweep(leiden_handle *h, const LevelGraph &g, int cls, const uint8_t *in_range, int dynamic);
+// Refinement: reset, then one round (SYNC) or one sweep (async) of moves.
+void refine_reset(leiden_handle *h, const LevelGraph &g);
+void refine_round(leiden_handle *h, const LevelGraph &g, int slot);
+void lm_prepare(leiden_handle *h, const LevelGraph &g);  // community sizes
+bool ensure_hscratch(leiden_handle *h, int64_t maxdeg);  // false: allocation failed
+
+// ------------------------------------------------------------ phases.cu
+void subset_renumber(leiden_handle *h, int64_t n);
+void split_communities(leiden_handle *h, const LevelGraph &g);
+void renumber_dense(leiden_handle *h, int64_t n);  // ranks in lbuf0, count in lbuf0[n]
+void count_communities(leiden_handle *h, int64_t n);  // distinct ids of Cp -> dcnt->list_count
+void lookup_dendrogram(leiden_handle *h);
+void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out_slot);
+void reset_next_pass(leiden_handle *h, int64_t ncomm, int out_slot);
+void mark_all_unprocessed(leiden_handle *h, int64_t n);
+void mark_unprocessed_from_flags(leiden_handle *h, const uint8_t *flags, int64_t n);
+void level_maxdeg(leiden_handle *h, const int32_t *deg, int64_t n);  // into dcnt->max_count
+
+// ------------------------------------------------------------ track.cu
+void track_communities(leiden_handle *h);  // Ctop vs C -> C, Sig, dSig
+void modularity_terms(leiden_handle *h, const int32_t *C);  // into dcnt->sigma_intra / sq
+void recompute_weights(leiden_handle *h);  // K = row sums, m2 (device)

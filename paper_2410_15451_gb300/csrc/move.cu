@@ -1,0 +1,559 @@
+// Local-moving phase (Alg. "leidenlm") and refinement phase (Alg.
+// "leidenre") of Leiden on one level of the dendrogram.
+//
+// Each vertex scans its neighbours' communities into an open-addressing
+// table (K_{i->c}), takes the community with the largest delta-modularity
+// (Eq. 2 times 2m^2, exact in int128; ties to the lowest community id) and
+// moves when the gain is positive.  Vertices are binned by degree: a warp
+// with a shared-memory table (<= 128 arcs), a block with a shared table
+// (<= 1024 arcs), a block with a table in global scratch (larger).
+//
+// Deterministic mode (snapshot schedule): moves found in a sub-sweep are
+// applied by a separate kernel after all decisions, so every decision reads
+// the state at the start of the sub-sweep.  Asynchronous mode applies each
+// move as soon as it is found.
+#include <algorithm>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int WARP_TABLE = 256;   // slots per warp (bin 0)
+constexpr int WARPS_PER_BLOCK = 8;
+constexpr int BLOCK_TABLE = 2048;  // slots per block (bin 1)
+constexpr int BLOCK_THREADS = 256;
+constexpr int HUGE_THREADS = 1024;
+
+enum Kind { KIND_MOVE = 0, KIND_REFINE = 1 };
+
+struct Args {
+  // level graph
+  int64_t n;
+  const int64_t *off;
+  const int32_t *deg;
+  const int32_t *col;
+  const void *w;
+  // state
+  int32_t *C;
+  int64_t *S;
+  const int64_t *K;
+  int32_t *size;
+  const int32_t *CB;     // refinement bounds
+  int32_t *prop;         // refinement proposals / async states
+  uint8_t *dS;           // split flags (local moving, dynamic)
+  uint32_t *unproc;      // bitmap
+  const uint8_t *in_range;
+  int32_t *movers, *mtarget;
+  const int32_t *list;   // bin list
+  const int32_t *count;  // bin count (device)
+  DevCounters *cnt;
+  int dynamic;
+  int async_mode;
+  int classes_mask;
+  // global scratch for the huge bin
+  int32_t *gkeys;
+  int64_t *gvals;
+  int64_t gslice;
+};
+
+__device__ __forceinline__ int next_pow2(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+__device__ __forceinline__ void table_insert(int32_t *keys, int64_t *vals, int tmask, int32_t c, int64_t w) {
+  uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)tmask;
+  while (true) {
+    int32_t k = atomicCAS(&keys[s], LD_EMPTY_KEY, c);
+    if (k == LD_EMPTY_KEY || k == c) {
+      atomicAdd((unsigned long long *)&vals[s], (unsigned long long)w);
+      return;
+    }
+    s = (s + 1) & (uint32_t)tmask;
+  }
+}
+
+// Decision of one vertex once its table is complete: the best community c*
+// (other than the current d), K_{i->c*}, K_{i->d}.
+struct Best {
+  i128 v;
+  int32_t c;
+  int64_t kc;
+  int64_t kd;
+};
+
+__device__ __forceinline__ void best_merge(Best &a, const Best &b) {
+  if (ld_better(b.v, b.c, a.v, a.c)) { a.v = b.v; a.c = b.c; a.kc = b.kc; }
+  a.kd += b.kd;
+}
+
+__device__ __forceinline__ Best warp_best(Best b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Best t;
+    t.v = ld_shfl_xor_i128(b.v, o);
+    t.c = __shfl_xor_sync(LD_FULL, b.c, o);
+    t.kc = __shfl_xor_sync(LD_FULL, b.kc, o);
+    t.kd = __shfl_xor_sync(LD_FULL, b.kd, o);
+    best_merge(b, t);
+  }
+  return b;
+}
+
+__device__ __forceinline__ Best slot_best(const int32_t *keys, const int64_t *vals, int T, int start, int stride,
+                                          int32_t d, int64_t m2, int64_t Ki, const int64_t *S) {
+  Best b{0, -1, 0, 0};
+  for (int s = start; s < T; s += stride) {
+    int32_t c = keys[s];
+    if (c == LD_EMPTY_KEY) continue;
+    int64_t kv = vals[s];
+    if (c == d) { b.kd += kv; continue; }
+    i128 v = (i128)m2 * kv - (i128)Ki * S[c];
+    if (ld_better(v, c, b.v, b.c)) { b.v = v; b.c = c; b.kc = kv; }
+  }
+  return b;
+}
+
+// Scan arcs [lo, hi) of vertex i with `stride` threads starting at `t0`.
+template <typename W, int KIND>
+__device__ __forceinline__ void scan_arcs(const Args &A, int64_t i, int64_t base, int64_t dg, int t0, int stride,
+                                          int32_t *keys, int64_t *vals, int tmask) {
+  const W *w = (const W *)A.w;
+  int32_t bi = KIND == KIND_REFINE ? A.CB[i] : 0;
+  for (int64_t a = t0; a < dg; a += stride) {
+    int32_t j = A.col[base + a];
+    if (j == i) continue;
+    if (KIND == KIND_REFINE && A.CB[j] != bi) continue;
+    table_insert(keys, vals, tmask, A.C[j], (int64_t)w[base + a]);
+  }
+}
+
+// The decision and its effects, run by one thread (the group leader).
+// Returns the gain counted into dQ (0 if no move).
+template <int KIND>
+__device__ __forceinline__ i128 decide_leader(const Args &A, int64_t i, const Best &b) {
+  int32_t d = A.C[i];
+  int64_t Ki = A.K[i];
+  int64_t m2 = A.cnt->m2;
+  if (b.c < 0) return 0;
+  i128 g = (i128)m2 * (b.kc - b.kd) - (i128)Ki * ((i128)Ki + A.S[b.c] - A.S[d]);
+  if (g <= 0) return 0;
+  if (KIND == KIND_MOVE) {
+    if (A.size[d] == 1 && A.size[b.c] == 1 && b.c > d) return 0;
+    if (A.async_mode) {
+      A.C[i] = b.c;
+      atomicAdd((unsigned long long *)&A.S[d], (unsigned long long)(-Ki));
+      atomicAdd((unsigned long long *)&A.S[b.c], (unsigned long long)Ki);
+      atomicSub(&A.size[d], 1);
+      atomicAdd(&A.size[b.c], 1);
+    } else {
+      int32_t slot = atomicAdd(&A.cnt->movers, 1);
+      A.movers[slot] = (int32_t)i;
+      A.mtarget[slot] = b.c;
+    }
+    if (A.dynamic) A.dS[d] = 1;
+    return g;
+  } else {
+    if (A.C[b.c] != b.c) return 0;  // the representative of c* left it
+    if (!A.async_mode) {
+      A.prop[i] = b.c;
+      return g;
+    }
+    // in place: pin the target (0 -> 1, or already 1), then leave (0 -> 2)
+    int32_t t = atomicCAS(&A.prop[b.c], 0, 1);
+    if (t == 2) return 0;
+    if (atomicCAS(&A.prop[i], 0, 2) != 0) return 0;
+    A.C[i] = b.c;
+    atomicAdd((unsigned long long *)&A.S[d], (unsigned long long)(-Ki));
+    atomicAdd((unsigned long long *)&A.S[b.c], (unsigned long long)Ki);
+    atomicAdd(&A.cnt->accepted, 1);
+    return g;
+  }
+}
+
+__device__ __forceinline__ void mark_neighbours(const Args &A, int64_t i, int64_t base, int64_t dg, int t0,
+                                                int stride) {
+  for (int64_t a = t0; a < dg; a += stride) {
+    int32_t j = A.col[base + a];
+    if (j == i) continue;
+    if (A.in_range && !A.in_range[j]) continue;
+    ld_bit_set(A.unproc, j);
+  }
+}
+
+__device__ __forceinline__ void add_counters(DevCounters *cnt, int kind, int64_t visits, int64_t arcs, int64_t moves,
+                                             i128 dq) {
+  if (kind == KIND_MOVE) {
+    if (visits) atomicAdd((unsigned long long *)&cnt->processed, (unsigned long long)visits);
+    if (arcs) atomicAdd((unsigned long long *)&cnt->arcs, (unsigned long long)arcs);
+    if (moves) atomicAdd((unsigned long long *)&cnt->moves, (unsigned long long)moves);
+    if (dq != 0) ld_atomic_add_i128(cnt->dq, dq);
+  } else {
+    if (visits) atomicAdd((unsigned long long *)&cnt->ref_processed, (unsigned long long)visits);
+    if (arcs) atomicAdd((unsigned long long *)&cnt->ref_arcs, (unsigned long long)arcs);
+  }
+}
+
+// ---------------------------------------------------------------- bin 0: warp per vertex
+template <typename W, int KIND>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) k_decide_warp(Args A) {
+  __shared__ int32_t skeys[WARPS_PER_BLOCK][WARP_TABLE];
+  __shared__ int64_t svals[WARPS_PER_BLOCK][WARP_TABLE];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t *keys = skeys[wid];
+  int64_t *vals = svals[wid];
+  int64_t count = *A.count;
+  int64_t gw = (int64_t)blockIdx.x * WARPS_PER_BLOCK + wid, nw = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+  int64_t visits = 0, arcs = 0, moves = 0;
+  i128 dq = 0;
+  for (int64_t t = gw; t < count; t += nw) {
+    int64_t i = A.list[t];
+    int64_t base = A.off[i], dg = A.deg[i];
+    int T = max(32, next_pow2(2 * (int)dg));
+    for (int s = lane; s < T; s += 32) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
+    __syncwarp();
+    scan_arcs<W, KIND>(A, i, base, dg, lane, 32, keys, vals, T - 1);
+    __syncwarp();
+    Best b = slot_best(keys, vals, T, lane, 32, A.C[i], A.cnt->m2, A.K[i], A.S);
+    b = warp_best(b);
+    __syncwarp();
+    i128 g = 0;
+    if (lane == 0) g = decide_leader<KIND>(A, i, b);
+    int moved = __shfl_sync(LD_FULL, g > 0 ? 1 : 0, 0);
+    if (KIND == KIND_MOVE && moved) mark_neighbours(A, i, base, dg, lane, 32);
+    if (lane == 0) { visits++; arcs += dg; moves += moved; dq += g; }
+  }
+  if (lane == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
+}
+
+// Block-wide merge of per-thread Best values (result valid in thread 0).
+__device__ __forceinline__ Best block_best(Best b) {
+  __shared__ Best sb[32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  b = warp_best(b);
+  if (lane == 0) sb[wid] = b;
+  __syncthreads();
+  if (wid == 0) {
+    Best x = lane < nw ? sb[lane] : Best{0, -1, 0, 0};
+    x = warp_best(x);
+    if (lane == 0) sb[0] = x;
+  }
+  __syncthreads();
+  Best r = sb[0];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------- bin 1: block, shared table
+template <typename W, int KIND>
+__global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Args A) {
+  __shared__ int32_t keys[BLOCK_TABLE];
+  __shared__ int64_t vals[BLOCK_TABLE];
+  __shared__ int moved_s;
+  int64_t count = *A.count;
+  int64_t visits = 0, arcs = 0, moves = 0;
+  i128 dq = 0;
+  for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
+    int64_t i = A.list[t];
+    int64_t base = A.off[i], dg = A.deg[i];
+    int T = next_pow2(2 * (int)dg);
+    if (T > BLOCK_TABLE) T = BLOCK_TABLE;
+    for (int s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
+    __syncthreads();
+    scan_arcs<W, KIND>(A, i, base, dg, threadIdx.x, blockDim.x, keys, vals, T - 1);
+    __syncthreads();
+    Best b = slot_best(keys, vals, T, threadIdx.x, blockDim.x, A.C[i], A.cnt->m2, A.K[i], A.S);
+    b = block_best(b);
+    if (threadIdx.x == 0) {
+      i128 g = decide_leader<KIND>(A, i, b);
+      moved_s = g > 0;
+      visits++; arcs += dg; moves += g > 0; dq += g;
+    }
+    __syncthreads();
+    if (KIND == KIND_MOVE && moved_s) mark_neighbours(A, i, base, dg, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
+}
+
+// ---------------------------------------------------------------- bin 2: block, global table
+template <typename W, int KIND>
+__global__ void __launch_bounds__(HUGE_THREADS) k_decide_huge(Args A) {
+  __shared__ int moved_s;
+  int32_t *keys = A.gkeys + (int64_t)blockIdx.x * A.gslice;
+  int64_t *vals = A.gvals + (int64_t)blockIdx.x * A.gslice;
+  int64_t count = *A.count;
+  int64_t visits = 0, arcs = 0, moves = 0;
+  i128 dq = 0;
+  for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
+    int64_t i = A.list[t];
+    int64_t base = A.off[i], dg = A.deg[i];
+    int64_t T = 1;
+    while (T < 2 * dg) T <<= 1;
+    for (int64_t s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
+    __syncthreads();
+    scan_arcs<W, KIND>(A, i, base, dg, threadIdx.x, blockDim.x, keys, vals, (int)(T - 1));
+    __syncthreads();
+    Best b = slot_best(keys, vals, (int)T, threadIdx.x, blockDim.x, A.C[i], A.cnt->m2, A.K[i], A.S);
+    b = block_best(b);
+    if (threadIdx.x == 0) {
+      i128 g = decide_leader<KIND>(A, i, b);
+      moved_s = g > 0;
+      visits++; arcs += dg; moves += g > 0; dq += g;
+    }
+    __syncthreads();
+    if (KIND == KIND_MOVE && moved_s) mark_neighbours(A, i, base, dg, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
+}
+
+// ---------------------------------------------------------------- collection
+// Take the unprocessed vertices of class `cls` (clearing their bits) and
+// append the in-range ones to the degree bins.
+__global__ void k_collect(int64_t n, uint32_t *unproc, int cls, int classes_mask, const uint8_t *in_range,
+                          const int32_t *deg, int32_t *bins, DevCounters *cnt) {
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
+    int64_t v = base + lane;
+    uint32_t word = unproc[base >> 5];
+    bool take = v < n && ((word >> lane) & 1u) && ld_class_of(v, classes_mask) == cls;
+    uint32_t taken = __ballot_sync(LD_FULL, take);
+    if (lane == 0 && taken) atomicAnd(&unproc[base >> 5], ~taken);
+    bool work = take && (!in_range || in_range[v]);
+    int bin = -1;
+    if (work) {
+      int dg = deg[v];
+      bin = dg <= BIN_WARP_MAX ? BIN_WARP : (dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE);
+    }
+#pragma unroll
+    for (int b = 0; b < NBINS; b++) {
+      uint32_t m = __ballot_sync(LD_FULL, bin == b);
+      if (!m) continue;
+      int32_t pos0 = 0;
+      if (lane == __ffs(m) - 1) pos0 = atomicAdd(&cnt->bin_count[b], __popc(m));
+      pos0 = __shfl_sync(LD_FULL, pos0, __ffs(m) - 1);
+      if (bin == b) bins[(int64_t)b * n + pos0 + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
+    }
+  }
+}
+
+// Deferred moves of a sub-sweep (deterministic mode).
+__global__ void k_apply_moves(const int32_t *movers, const int32_t *target, const DevCounters *cnt_c, int32_t *C,
+                              int64_t *S, const int64_t *K, int32_t *size) {
+  int64_t m = cnt_c->movers;
+  for (int64_t t = ld_gtid(); t < m; t += ld_gstride()) {
+    int32_t i = movers[t], c = target[t];
+    int32_t d = C[i];
+    C[i] = c;
+    atomicAdd((unsigned long long *)&S[d], (unsigned long long)(-K[i]));
+    atomicAdd((unsigned long long *)&S[c], (unsigned long long)K[i]);
+    atomicSub(&size[d], 1);
+    atomicAdd(&size[c], 1);
+  }
+}
+
+__global__ void k_sizes(const int32_t *C, int64_t n, int32_t *size) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) atomicAdd(&size[C[i]], 1);
+}
+
+// ---- refinement
+// Reset the vertices of refined bounds to singletons and list them.
+__global__ void k_refine_reset(int64_t n, const int32_t *CB, const uint8_t *dR, int32_t *C, int64_t *S,
+                               const int64_t *K, int32_t *prop, int32_t *cand, DevCounters *cnt) {
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
+    int64_t i = base + lane;
+    bool r = i < n && dR[CB[i]];
+    if (i < n) prop[i] = r ? 0 : -1;
+    if (r) { C[i] = (int32_t)i; S[i] = K[i]; }
+    uint32_t m = __ballot_sync(LD_FULL, r);
+    if (!m) continue;
+    int32_t p0 = 0;
+    if (lane == 0) p0 = atomicAdd(&cnt->cand_count[0], __popc(m));
+    p0 = __shfl_sync(LD_FULL, p0, 0);
+    if (r) cand[p0 + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
+  }
+}
+
+// Keep the candidates that are still alone in their community and bin them
+// by degree; reset their proposals.
+__global__ void k_refine_collect(const int32_t *cand_in, const int32_t *count_in, int32_t *cand_out,
+                                 int32_t *count_out, int64_t n, const int32_t *C, const int64_t *S, const int64_t *K,
+                                 const int32_t *deg, int32_t *prop, int32_t *bins, DevCounters *cnt, int async_mode) {
+  int lane = threadIdx.x & 31;
+  int64_t m = *count_in;
+  for (int64_t base = (ld_gtid() & ~31ll); base < m; base += ld_gstride()) {
+    int64_t t = base + lane;
+    int32_t i = t < m ? cand_in[t] : -1;
+    bool keep = false;
+    if (i >= 0) {
+      if (!async_mode) prop[i] = -1;
+      keep = S[C[i]] == K[i];
+    }
+    int bin = -1;
+    if (keep) {
+      int dg = deg[i];
+      bin = dg <= BIN_WARP_MAX ? BIN_WARP : (dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE);
+    }
+    uint32_t km = __ballot_sync(LD_FULL, keep);
+    if (km) {
+      int32_t p0 = 0;
+      if (lane == __ffs(km) - 1) p0 = atomicAdd(count_out, __popc(km));
+      p0 = __shfl_sync(LD_FULL, p0, __ffs(km) - 1);
+      if (keep) cand_out[p0 + __popc(km & ((1u << lane) - 1u))] = i;
+    }
+#pragma unroll
+    for (int b = 0; b < NBINS; b++) {
+      uint32_t mm = __ballot_sync(LD_FULL, bin == b);
+      if (!mm) continue;
+      int32_t q0 = 0;
+      if (lane == __ffs(mm) - 1) q0 = atomicAdd(&cnt->bin_count[b], __popc(mm));
+      q0 = __shfl_sync(LD_FULL, q0, __ffs(mm) - 1);
+      if (bin == b) bins[(int64_t)b * n + q0 + __popc(mm & ((1u << lane) - 1u))] = i;
+    }
+  }
+}
+
+// Snapshot rounds: i -> c* applies iff i does not hold and c* holds, where
+// v holds when it proposed nothing, or when v and prop[v] chose each other
+// and v has the smaller id.
+__device__ __forceinline__ bool holds(const int32_t *prop, int32_t v) {
+  int32_t t = prop[v];
+  return t < 0 || (prop[t] == v && v < t);
+}
+__global__ void k_refine_accept(const int32_t *cand, const int32_t *count, const int32_t *prop, int32_t *C, int64_t *S,
+                                const int64_t *K, DevCounters *cnt) {
+  int64_t m = *count;
+  int32_t acc = 0;
+  for (int64_t t = ld_gtid(); t < m; t += ld_gstride()) {
+    int32_t i = cand[t];
+    int32_t c = prop[i];
+    if (c < 0 || holds(prop, i) || !holds(prop, c)) continue;
+    int32_t d = C[i];
+    C[i] = c;
+    atomicAdd((unsigned long long *)&S[d], (unsigned long long)(-K[i]));
+    atomicAdd((unsigned long long *)&S[c], (unsigned long long)K[i]);
+    acc++;
+  }
+  if (acc) atomicAdd(&cnt->accepted, acc);
+}
+
+Args make_args(leiden_handle *h, const LevelGraph &g) {
+  Args A{};
+  A.n = g.n;
+  A.off = g.off;
+  A.deg = g.deg;
+  A.col = g.col;
+  A.w = g.w;
+  A.C = h->Cp;
+  A.S = h->Sp;
+  A.K = h->Kp;
+  A.size = h->csize;
+  A.CB = h->CB;
+  A.prop = h->prop;
+  A.dS = h->dS;
+  A.unproc = h->unproc;
+  A.movers = h->movers;
+  A.mtarget = h->mtarget;
+  A.cnt = h->dcnt;
+  A.async_mode = h->p.deterministic ? 0 : 1;
+  A.classes_mask = h->p.classes - 1;
+  return A;
+}
+
+template <int KIND>
+void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
+  cudaStream_t s = h->stream;
+  int sms = h->sm_count;
+  for (int b = 0; b < NBINS; b++) {
+    A.list = h->bins + (int64_t)b * g.n;
+    A.count = &h->dcnt->bin_count[b];
+    if (b == BIN_HUGE && g.maxdeg <= BIN_BLOCK_MAX) continue;
+    if (b == BIN_BLOCK && g.maxdeg <= BIN_WARP_MAX) continue;
+    if (b == BIN_WARP) {
+      int grid = sms * 8;
+      if (g.w64) k_decide_warp<int64_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
+      else k_decide_warp<int32_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
+    } else if (b == BIN_BLOCK) {
+      int grid = sms * 4;
+      if (g.w64) k_decide_block<int64_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
+      else k_decide_block<int32_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
+    } else {
+      if (!ensure_hscratch(h, g.maxdeg)) { h->fatal = LEIDEN_ERR_OOM; h->err = "global table scratch"; return; }
+      A.gslice = (int64_t)(h->hscratch_bytes / 12 / sms);
+      A.gkeys = (int32_t *)h->hscratch;
+      A.gvals = (int64_t *)((char *)h->hscratch + (size_t)A.gslice * sms * sizeof(int32_t));
+      if (g.w64) k_decide_huge<int64_t, KIND><<<sms, HUGE_THREADS, 0, s>>>(A);
+      else k_decide_huge<int32_t, KIND><<<sms, HUGE_THREADS, 0, s>>>(A);
+    }
+  }
+}
+
+}  // namespace
+
+bool ensure_hscratch(leiden_handle *h, int64_t maxdeg) {
+  int64_t T = 1;
+  while (T < 2 * maxdeg) T <<= 1;
+  // slice = T slots, one per resident block; vals (8 B) after keys (4 B)
+  size_t need = (size_t)T * h->sm_count * 12;
+  if (need <= h->hscratch_bytes) return true;
+  if (h->hscratch) {
+    for (auto &q : h->owned)
+      if (q == h->hscratch) { cudaFree(q); q = nullptr; }
+  }
+  void *p = nullptr;
+  if (cudaMalloc(&p, need) != cudaSuccess) {
+    cudaGetLastError();
+    h->hscratch = nullptr;
+    h->hscratch_bytes = 0;
+    return false;
+  }
+  h->owned.push_back(p);
+  h->hscratch = p;
+  h->hscratch_bytes = need;
+  return true;
+}
+
+void lm_prepare(leiden_handle *h, const LevelGraph &g) {
+  cudaMemsetAsync(h->csize, 0, (size_t)g.n * sizeof(int32_t), h->stream);
+  k_sizes<<<grid_for(g.n, 256), 256, 0, h->stream>>>(h->Cp, g.n, h->csize);
+}
+
+void lm_subsweep(leiden_handle *h, const LevelGraph &g, int cls, const uint8_t *in_range, int dynamic) {
+  cudaStream_t s = h->stream;
+  cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4 + sizeof(int32_t), s);  // bins + movers
+  k_collect<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, h->unproc, cls, h->p.classes - 1, in_range, g.deg, h->bins,
+                                               h->dcnt);
+  Args A = make_args(h, g);
+  A.in_range = in_range;
+  A.dynamic = dynamic;
+  launch_bins<KIND_MOVE>(h, g, A);
+  if (h->p.deterministic)
+    k_apply_moves<<<h->sm_count * 4, 256, 0, s>>>(h->movers, h->mtarget, h->dcnt, h->Cp, h->Sp, h->Kp, h->csize);
+}
+
+void refine_reset(leiden_handle *h, const LevelGraph &g) {
+  cudaStream_t s = h->stream;
+  cudaMemsetAsync(&h->dcnt->cand_count[0], 0, sizeof(int32_t), s);
+  k_refine_reset<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, h->CB, h->dR, h->Cp, h->Sp, h->Kp, h->prop, h->cand,
+                                                    h->dcnt);
+}
+
+// One round on the candidates of list `slot` (cand + slot*n, count
+// cand_count[slot]); the ones still alone go to the other list.
+void refine_round(leiden_handle *h, const LevelGraph &g, int slot) {
+  cudaStream_t s = h->stream;
+  int32_t *in = h->cand + (int64_t)slot * g.n, *out = h->cand + (int64_t)(1 - slot) * g.n;
+  int32_t *cin = &h->dcnt->cand_count[slot], *cout = &h->dcnt->cand_count[1 - slot];
+  cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4, s);
+  cudaMemsetAsync(cout, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(&h->dcnt->accepted, 0, sizeof(int32_t), s);
+  k_refine_collect<<<grid_for(g.n, 256), 256, 0, s>>>(in, cin, out, cout, g.n, h->Cp, h->Sp, h->Kp, g.deg, h->prop,
+                                                      h->bins, h->dcnt, h->p.deterministic ? 0 : 1);
+  Args A = make_args(h, g);
+  launch_bins<KIND_REFINE>(h, g, A);
+  if (h->p.deterministic)
+    k_refine_accept<<<h->sm_count * 4, 256, 0, s>>>(out, cout, h->prop, h->Cp, h->Sp, h->Kp, h->dcnt);
+}

@@ -1,0 +1,459 @@
+// Per-pass phases between local moving and the next pass: subset
+// renumbering (Alg. "leidensr"), splitting (Alg. "leidensp"), dense
+// renumbering with dendrogram lookup (Alg. "leiden"), aggregation (Alg.
+// "leidenag").
+#include <algorithm>
+#include <climits>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int TB = 256;
+
+// ---------------------------------------------------------------- Alg. leidensr
+__global__ void k_sr_init(int64_t n, int32_t *rep, int64_t *S2, uint8_t *dS2, uint8_t *dR2) {
+  for (int64_t c = ld_gtid(); c < n; c += ld_gstride()) { rep[c] = INT_MAX; S2[c] = 0; dS2[c] = 0; dR2[c] = 0; }
+}
+__global__ void k_sr_min(int64_t n, const int32_t *C, int32_t *rep) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) atomicMin(&rep[C[i]], (int32_t)i);
+}
+__global__ void k_sr_rekey(int64_t n, const int32_t *rep, const int64_t *S, const uint8_t *dS, const uint8_t *dR,
+                           int64_t *S2, uint8_t *dS2, uint8_t *dR2) {
+  for (int64_t c = ld_gtid(); c < n; c += ld_gstride()) {
+    int32_t r = rep[c];
+    if (r == INT_MAX) continue;
+    S2[r] = S[c]; dS2[r] = dS[c]; dR2[r] = dR[c];
+  }
+}
+__global__ void k_sr_remap(int64_t n, const int32_t *rep, int32_t *C) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) C[i] = rep[C[i]];
+}
+
+// ---------------------------------------------------------------- Alg. leidensp
+// Components of the flagged communities by lock-free union-find: a root is
+// only ever hooked under a smaller root, so every component ends with its
+// smallest vertex as root -- the label a BFS from the lowest vertex gives.
+__global__ void k_split_init(int64_t n, const int32_t *C, const uint8_t *dS, const uint8_t *dR, int32_t *parent,
+                             int32_t *list, DevCounters *cnt) {
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
+    int64_t i = base + lane;
+    bool f = false;
+    if (i < n) {
+      int32_t c = C[i];
+      f = dS[c] && !dR[c];
+      if (f) parent[i] = (int32_t)i;
+    }
+    uint32_t m = __ballot_sync(LD_FULL, f);
+    if (!m) continue;
+    int32_t p0 = 0;
+    if (lane == 0) p0 = atomicAdd(&cnt->split_count, __popc(m));
+    p0 = __shfl_sync(LD_FULL, p0, 0);
+    if (f) list[p0 + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
+  }
+}
+
+__device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
+  while (true) {
+    int32_t p = parent[x];
+    if (p == x) return x;
+    int32_t gp = parent[p];
+    if (gp != p) parent[x] = gp;  // path halving (parents only decrease)
+    x = p;
+  }
+}
+
+__device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b) {
+  while (true) {
+    a = uf_find(parent, a);
+    b = uf_find(parent, b);
+    if (a == b) return;
+    if (a < b) { int32_t t = a; a = b; b = t; }
+    if (atomicCAS(&parent[a], a, b) == a) return;
+  }
+}
+
+__global__ void k_split_hook(const int32_t *list, const DevCounters *cnt, const int64_t *off, const int32_t *deg,
+                             const int32_t *col, const int32_t *C, int32_t *parent) {
+  int lane = threadIdx.x & 31;
+  int64_t m = cnt->split_count;
+  int64_t warp = ld_gtid() >> 5, nw = ld_gstride() >> 5;
+  for (int64_t t = warp; t < m; t += nw) {
+    int32_t i = list[t];
+    int32_t c = C[i];
+    int64_t b = off[i], d = deg[i];
+    for (int64_t a = lane; a < d; a += 32) {
+      int32_t j = col[b + a];
+      if (j != i && C[j] == c && j < i) uf_unite(parent, i, j);
+    }
+  }
+}
+
+__global__ void k_split_compress(const int32_t *list, const DevCounters *cnt, int32_t *parent, int32_t *C) {
+  int64_t m = cnt->split_count;
+  for (int64_t t = ld_gtid(); t < m; t += ld_gstride()) {
+    int32_t i = list[t];
+    C[i] = uf_find(parent, i);
+  }
+}
+
+// ---------------------------------------------------------------- renumber / lookup
+__global__ void k_used(int64_t n, const int32_t *C, int32_t *used) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) used[C[i]] = 1;
+}
+__global__ void k_rank(int64_t n, const int64_t *rank, int32_t *C) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) C[i] = (int32_t)rank[C[i]];
+}
+__global__ void k_lookup(int64_t N, const int32_t *Cp, int32_t *Ctop) {
+  for (int64_t v = ld_gtid(); v < N; v += ld_gstride()) Ctop[v] = Cp[Ctop[v]];
+}
+__global__ void k_count_distinct(int64_t n, const int32_t *C, int32_t *seen, DevCounters *cnt) {
+  int32_t local = 0;
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride())
+    if (atomicExch(&seen[C[i]], 1) == 0) local++;
+  if (local) atomicAdd(&cnt->list_count, local);
+}
+
+// ---------------------------------------------------------------- Alg. leidenag
+__global__ void k_member_count(int64_t n, const int32_t *C, int32_t *cnt_c) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) atomicAdd(&cnt_c[C[i]], 1);
+}
+__global__ void k_member_fill(int64_t n, const int32_t *C, const int64_t *coff, unsigned long long *cursor,
+                              int32_t *cverts) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) {
+    int32_t c = C[i];
+    unsigned long long p = atomicAdd(&cursor[c], 1ull);
+    cverts[coff[c] + (int64_t)p] = (int32_t)i;
+  }
+}
+__global__ void k_member_deg(int64_t n, const int32_t *cverts, const int32_t *deg, int32_t *mdeg) {
+  for (int64_t t = ld_gtid(); t < n; t += ld_gstride()) mdeg[t] = deg[cverts[t]];
+}
+// super-row offsets: yoff[c] = flat offset of the community's first member
+__global__ void k_yoff(int64_t ncomm, const int64_t *coff, const int64_t *cflat, int64_t *yoff, DevCounters *cnt) {
+  for (int64_t c = ld_gtid(); c <= ncomm; c += ld_gstride()) {
+    yoff[c] = cflat[coff[c]];
+    if (c < ncomm) {
+      int64_t d = cflat[coff[c + 1]] - cflat[coff[c]];
+      atomicMax(&cnt->max_count, (int32_t)(d < INT_MAX ? d : INT_MAX));
+    }
+  }
+}
+
+__device__ __forceinline__ void agg_insert(int32_t *keys, int64_t *vals, int tmask, int32_t c, int64_t w) {
+  uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)tmask;
+  while (true) {
+    int32_t k = atomicCAS(&keys[s], LD_EMPTY_KEY, c);
+    if (k == LD_EMPTY_KEY || k == c) {
+      atomicAdd((unsigned long long *)&vals[s], (unsigned long long)w);
+      return;
+    }
+    s = (s + 1) & (uint32_t)tmask;
+  }
+}
+
+struct AggArgs {
+  int64_t ncomm;
+  const int64_t *off;
+  const int32_t *deg;
+  const int32_t *col;
+  const void *w;
+  const int32_t *C;
+  const int64_t *coff;
+  const int32_t *cverts;
+  const int64_t *cflat;
+  const int64_t *yoff;
+  int32_t *ydeg;
+  int32_t *ycol;
+  int64_t *yw;
+  int64_t *Kout;
+  const int32_t *list;
+  const int32_t *count;
+  int32_t *gkeys;
+  int64_t *gvals;
+  int64_t gslice;
+};
+
+// Flat arcs [f0, f1) of community c, processed by `stride` threads.
+template <typename W>
+__device__ __forceinline__ void agg_scan(const AggArgs &A, int64_t c, int t0, int stride, int32_t *keys,
+                                         int64_t *vals, int tmask) {
+  const W *w = (const W *)A.w;
+  int64_t m0 = A.coff[c], m1 = A.coff[c + 1];
+  int64_t f0 = A.cflat[m0], f1 = A.cflat[m1];
+  for (int64_t f = f0 + t0; f < f1; f += stride) {
+    // member t with cflat[t] <= f < cflat[t+1]
+    int64_t lo = m0, hi = m1 - 1;
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) >> 1;
+      if (A.cflat[mid] <= f) lo = mid; else hi = mid - 1;
+    }
+    int32_t v = A.cverts[lo];
+    int64_t a = A.off[v] + (f - A.cflat[lo]);
+    agg_insert(keys, vals, tmask, A.C[A.col[a]], (int64_t)w[a]);
+  }
+}
+
+template <int GROUP>
+__device__ __forceinline__ void agg_emit(const AggArgs &A, int64_t c, int t0, int stride, const int32_t *keys,
+                                         const int64_t *vals, int T, int32_t *rowcount, int64_t *rowsum) {
+  int64_t base = A.yoff[c];
+  for (int s = t0; s < T; s += stride) {
+    int32_t k = keys[s];
+    if (k == LD_EMPTY_KEY) continue;
+    int32_t p = atomicAdd(rowcount, 1);
+    A.ycol[base + p] = k;
+    A.yw[base + p] = vals[s];
+    atomicAdd((unsigned long long *)rowsum, (unsigned long long)vals[s]);
+  }
+}
+
+constexpr int AGG_WARPS = 8;
+constexpr int AGG_WARP_TABLE = 256;
+constexpr int AGG_BLOCK_TABLE = 2048;
+
+template <typename W>
+__global__ void __launch_bounds__(AGG_WARPS * 32) k_agg_warp(AggArgs A) {
+  __shared__ int32_t skeys[AGG_WARPS][AGG_WARP_TABLE];
+  __shared__ int64_t svals[AGG_WARPS][AGG_WARP_TABLE];
+  __shared__ int32_t scount[AGG_WARPS];
+  __shared__ int64_t ssum[AGG_WARPS];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t count = *A.count;
+  for (int64_t t = (int64_t)blockIdx.x * AGG_WARPS + wid; t < count; t += (int64_t)gridDim.x * AGG_WARPS) {
+    int64_t c = A.list[t];
+    int64_t dg = A.yoff[c + 1] - A.yoff[c];
+    int T = 32;
+    while (T < 2 * dg) T <<= 1;
+    for (int s = lane; s < T; s += 32) { skeys[wid][s] = LD_EMPTY_KEY; svals[wid][s] = 0; }
+    if (lane == 0) { scount[wid] = 0; ssum[wid] = 0; }
+    __syncwarp();
+    agg_scan<W>(A, c, lane, 32, skeys[wid], svals[wid], T - 1);
+    __syncwarp();
+    agg_emit<32>(A, c, lane, 32, skeys[wid], svals[wid], T, &scount[wid], &ssum[wid]);
+    __syncwarp();
+    if (lane == 0) { A.ydeg[c] = scount[wid]; A.Kout[c] = ssum[wid]; }
+    __syncwarp();
+  }
+}
+
+template <typename W>
+__global__ void __launch_bounds__(256) k_agg_block(AggArgs A) {
+  __shared__ int32_t keys[AGG_BLOCK_TABLE];
+  __shared__ int64_t vals[AGG_BLOCK_TABLE];
+  __shared__ int32_t rc;
+  __shared__ int64_t rs;
+  int64_t count = *A.count;
+  for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
+    int64_t c = A.list[t];
+    int64_t dg = A.yoff[c + 1] - A.yoff[c];
+    int T = 32;
+    while (T < 2 * dg) T <<= 1;
+    for (int s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
+    if (threadIdx.x == 0) { rc = 0; rs = 0; }
+    __syncthreads();
+    agg_scan<W>(A, c, threadIdx.x, blockDim.x, keys, vals, T - 1);
+    __syncthreads();
+    agg_emit<256>(A, c, threadIdx.x, blockDim.x, keys, vals, T, &rc, &rs);
+    __syncthreads();
+    if (threadIdx.x == 0) { A.ydeg[c] = rc; A.Kout[c] = rs; }
+    __syncthreads();
+  }
+}
+
+template <typename W>
+__global__ void __launch_bounds__(1024) k_agg_huge(AggArgs A) {
+  __shared__ int32_t rc;
+  __shared__ int64_t rs;
+  int32_t *keys = A.gkeys + (int64_t)blockIdx.x * A.gslice;
+  int64_t *vals = A.gvals + (int64_t)blockIdx.x * A.gslice;
+  int64_t count = *A.count;
+  for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
+    int64_t c = A.list[t];
+    int64_t dg = A.yoff[c + 1] - A.yoff[c];
+    int64_t T = 32;
+    while (T < 2 * dg) T <<= 1;
+    for (int64_t s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
+    if (threadIdx.x == 0) { rc = 0; rs = 0; }
+    __syncthreads();
+    agg_scan<W>(A, c, threadIdx.x, blockDim.x, keys, vals, (int)(T - 1));
+    __syncthreads();
+    agg_emit<1024>(A, c, threadIdx.x, blockDim.x, keys, vals, (int)T, &rc, &rs);
+    __syncthreads();
+    if (threadIdx.x == 0) { A.ydeg[c] = rc; A.Kout[c] = rs; }
+    __syncthreads();
+  }
+}
+
+__global__ void k_agg_bin(int64_t ncomm, const int64_t *yoff, int32_t *bins, DevCounters *cnt) {
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < ncomm; base += ld_gstride()) {
+    int64_t c = base + lane;
+    int bin = -1;
+    if (c < ncomm) {
+      int64_t d = yoff[c + 1] - yoff[c];
+      bin = d <= BIN_WARP_MAX ? BIN_WARP : (d <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE);
+    }
+#pragma unroll
+    for (int b = 0; b < NBINS; b++) {
+      uint32_t m = __ballot_sync(LD_FULL, bin == b);
+      if (!m) continue;
+      int32_t p0 = 0;
+      if (lane == __ffs(m) - 1) p0 = atomicAdd(&cnt->bin_count[b], __popc(m));
+      p0 = __shfl_sync(LD_FULL, p0, __ffs(m) - 1);
+      if (bin == b) bins[(int64_t)b * ncomm + p0 + __popc(m & ((1u << lane) - 1u))] = (int32_t)c;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- pass reset
+__global__ void k_next_pass(int64_t nc, const int64_t *Kout, int64_t *Kp, int64_t *Sp, int32_t *Cp, uint8_t *dR,
+                            uint8_t *dS) {
+  for (int64_t c = ld_gtid(); c < nc; c += ld_gstride()) {
+    Kp[c] = Kout[c]; Sp[c] = Kout[c]; Cp[c] = (int32_t)c; dR[c] = 1; dS[c] = 0;
+  }
+}
+__global__ void k_bits_all(int64_t n, uint32_t *bm) {
+  int64_t words = (n + 31) >> 5;
+  for (int64_t w = ld_gtid(); w < words; w += ld_gstride()) {
+    int64_t rem = n - (w << 5);
+    bm[w] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+  }
+}
+__global__ void k_bits_from_flags(int64_t n, const uint8_t *flags, uint32_t *bm) {
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
+    int64_t v = base + lane;
+    uint32_t m = __ballot_sync(LD_FULL, v < n && flags[v]);
+    if (lane == 0) bm[base >> 5] = m;
+  }
+}
+__global__ void k_maxdeg(int64_t n, const int32_t *deg, DevCounters *cnt) {
+  int32_t mx = 0;
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) mx = max(mx, deg[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(LD_FULL, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&cnt->max_count, mx);
+}
+
+}  // namespace
+
+void subset_renumber(leiden_handle *h, int64_t n) {
+  cudaStream_t s = h->stream;
+  int g = grid_for(n, TB);
+  k_sr_init<<<g, TB, 0, s>>>(n, h->rep, h->S2, h->dS2, h->dR2);
+  k_sr_min<<<g, TB, 0, s>>>(n, h->Cp, h->rep);
+  k_sr_rekey<<<g, TB, 0, s>>>(n, h->rep, h->Sp, h->dS, h->dR, h->S2, h->dS2, h->dR2);
+  k_sr_remap<<<g, TB, 0, s>>>(n, h->rep, h->Cp);
+  std::swap(h->Sp, h->S2);
+  std::swap(h->dS, h->dS2);
+  std::swap(h->dR, h->dR2);
+}
+
+void split_communities(leiden_handle *h, const LevelGraph &g) {
+  cudaStream_t s = h->stream;
+  cudaMemsetAsync(&h->dcnt->split_count, 0, sizeof(int32_t), s);
+  int32_t *list = h->ibuf1;
+  k_split_init<<<grid_for(g.n, TB), TB, 0, s>>>(g.n, h->Cp, h->dS, h->dR, h->parent, list, h->dcnt);
+  k_split_hook<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
+  k_split_compress<<<h->sm_count * 4, TB, 0, s>>>(list, h->dcnt, h->parent, h->Cp);
+}
+
+void count_communities(leiden_handle *h, int64_t n) {
+  cudaStream_t s = h->stream;
+  cudaMemsetAsync(h->ibuf0, 0, (size_t)n * sizeof(int32_t), s);
+  cudaMemsetAsync(&h->dcnt->list_count, 0, sizeof(int32_t), s);
+  k_count_distinct<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0, h->dcnt);
+}
+
+void renumber_dense(leiden_handle *h, int64_t n) {
+  cudaStream_t s = h->stream;
+  cudaMemsetAsync(h->ibuf0, 0, (size_t)n * sizeof(int32_t), s);
+  k_used<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0);
+  exclusive_scan_i32_to_i64(h->ibuf0, h->lbuf0, n, h->scan_tmp, s);
+  k_rank<<<grid_for(n, TB), TB, 0, s>>>(n, h->lbuf0, h->Cp);
+}
+
+void lookup_dendrogram(leiden_handle *h) {
+  k_lookup<<<grid_for(h->n, TB), TB, 0, h->stream>>>(h->n, h->Cp, h->Ctop);
+}
+
+// Aggregate level g by its dense membership Cp into slot `out`; K'' goes to
+// h->S2.  Sets dcnt->max_count to the largest super-row capacity.
+void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
+  cudaStream_t s = h->stream;
+  int64_t n = g.n;
+  // community vertices CSR
+  cudaMemsetAsync(h->ibuf0, 0, (size_t)ncomm * sizeof(int32_t), s);
+  k_member_count<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0);
+  exclusive_scan_i32_to_i64(h->ibuf0, h->coff, ncomm, h->scan_tmp, s);
+  cudaMemcpyAsync(h->lbuf0, h->coff, (size_t)ncomm * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  k_member_fill<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->coff, (unsigned long long *)h->lbuf0, h->cverts);
+  // flat arc offsets of the members, and the super-row offsets
+  k_member_deg<<<grid_for(n, TB), TB, 0, s>>>(n, h->cverts, g.deg, h->ibuf1);
+  exclusive_scan_i32_to_i64(h->ibuf1, h->cflat, n, h->scan_tmp, s);
+  cudaMemsetAsync(&h->dcnt->max_count, 0, sizeof(int32_t), s);
+  k_yoff<<<grid_for(ncomm + 1, TB), TB, 0, s>>>(ncomm, h->coff, h->cflat, h->y_off[out], h->dcnt);
+  cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4, s);
+  k_agg_bin<<<grid_for(ncomm, TB), TB, 0, s>>>(ncomm, h->y_off[out], h->bins, h->dcnt);
+  cudaMemcpyAsync(&h->hcnt->max_count, &h->dcnt->max_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  int32_t maxc = h->hcnt->max_count;
+  AggArgs A{};
+  A.ncomm = ncomm;
+  A.off = g.off;
+  A.deg = g.deg;
+  A.col = g.col;
+  A.w = g.w;
+  A.C = h->Cp;
+  A.coff = h->coff;
+  A.cverts = h->cverts;
+  A.cflat = h->cflat;
+  A.yoff = h->y_off[out];
+  A.ydeg = h->y_deg[out];
+  A.ycol = h->y_col[out];
+  A.yw = h->y_w[out];
+  A.Kout = h->S2;
+  int sms = h->sm_count;
+  A.list = h->bins;
+  A.count = &h->dcnt->bin_count[BIN_WARP];
+  if (g.w64) k_agg_warp<int64_t><<<sms * 8, AGG_WARPS * 32, 0, s>>>(A);
+  else k_agg_warp<int32_t><<<sms * 8, AGG_WARPS * 32, 0, s>>>(A);
+  if (maxc > BIN_WARP_MAX) {
+    A.list = h->bins + ncomm;
+    A.count = &h->dcnt->bin_count[BIN_BLOCK];
+    if (g.w64) k_agg_block<int64_t><<<sms * 4, 256, 0, s>>>(A);
+    else k_agg_block<int32_t><<<sms * 4, 256, 0, s>>>(A);
+  }
+  if (maxc > BIN_BLOCK_MAX) {
+    if (!ensure_hscratch(h, maxc)) { h->fatal = LEIDEN_ERR_OOM; h->err = "global table scratch"; return; }
+    A.list = h->bins + 2 * ncomm;
+    A.count = &h->dcnt->bin_count[BIN_HUGE];
+    A.gslice = (int64_t)(h->hscratch_bytes / 12 / sms);
+    A.gkeys = (int32_t *)h->hscratch;
+    A.gvals = (int64_t *)((char *)h->hscratch + (size_t)A.gslice * sms * sizeof(int32_t));
+    if (g.w64) k_agg_huge<int64_t><<<sms, 1024, 0, s>>>(A);
+    else k_agg_huge<int32_t><<<sms, 1024, 0, s>>>(A);
+  }
+}
+
+void reset_next_pass(leiden_handle *h, int64_t ncomm, int out) {
+  (void)out;
+  cudaStream_t s = h->stream;
+  k_next_pass<<<grid_for(ncomm, TB), TB, 0, s>>>(ncomm, h->S2, h->Kp, h->Sp, h->Cp, h->dR, h->dS);
+  mark_all_unprocessed(h, ncomm);
+}
+
+void mark_all_unprocessed(leiden_handle *h, int64_t n) {
+  k_bits_all<<<grid_for((n + 31) / 32, TB), TB, 0, h->stream>>>(n, h->unproc);
+}
+
+void mark_unprocessed_from_flags(leiden_handle *h, const uint8_t *flags, int64_t n) {
+  k_bits_from_flags<<<grid_for(n, TB), TB, 0, h->stream>>>(n, flags, h->unproc);
+}
+
+void level_maxdeg(leiden_handle *h, const int32_t *deg, int64_t n) {
+  cudaMemsetAsync(&h->dcnt->max_count, 0, sizeof(int32_t), h->stream);
+  k_maxdeg<<<grid_for(n, TB), TB, 0, h->stream>>>(n, deg, h->dcnt);
+}

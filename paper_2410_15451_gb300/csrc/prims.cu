@@ -1,0 +1,238 @@
+// Device primitives: exclusive scan, stable radix sort, fills.
+#include "internal.h"
+
+namespace {
+
+constexpr int SCAN_BLOCK = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
+  int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t t = __shfl_up_sync(LD_FULL, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan over the block of one value per thread; returns the
+// thread's exclusive prefix and the block total in *total.
+__device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *total) {
+  __shared__ int64_t wsum[SCAN_BLOCK / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t incl = warp_incl_scan(v);
+  if (lane == 31) wsum[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    int nw = blockDim.x >> 5;
+    int64_t x = lane < nw ? wsum[lane] : 0;
+    int64_t xs = warp_incl_scan(x);
+    if (lane < nw) wsum[lane] = xs - x;
+    if (lane == nw - 1) wsum[31] = xs;  // total (nw <= 32)
+  }
+  __syncthreads();
+  int64_t res = incl - v + wsum[wid];
+  *total = wsum[31];
+  __syncthreads();
+  return res;
+}
+
+template <typename T>
+__global__ void scan_tile_reduce(const T *in, int64_t n, int64_t *tile_sums) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++)
+    if (base + k < n) s += (int64_t)in[base + k];
+  int64_t total;
+  block_excl_scan(s, &total);
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of the tile sums in place; writes the grand
+// total to *grand.
+__global__ void scan_tile_offsets(int64_t *tile_sums, int64_t ntiles, int64_t *grand) {
+  int64_t carry = 0;
+  for (int64_t base = 0; base < ntiles; base += SCAN_BLOCK) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = i < ntiles ? tile_sums[i] : 0;
+    int64_t total;
+    int64_t ex = block_excl_scan(v, &total);
+    if (i < ntiles) tile_sums[i] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) *grand = carry;
+}
+
+template <typename T>
+__global__ void scan_tile_apply(const T *in, int64_t *out, int64_t n, const int64_t *tile_offs) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int64_t v[SCAN_ITEMS];
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    v[k] = (base + k < n) ? (int64_t)in[base + k] : 0;
+    s += v[k];
+  }
+  int64_t total;
+  int64_t ex = block_excl_scan(s, &total) + tile_offs[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    if (base + k < n) out[base + k] = ex;
+    ex += v[k];
+  }
+}
+
+template <typename T>
+cudaError_t scan_impl(const T *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s) {
+  int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  int64_t *tile = (int64_t *)tmp;
+  if (n > 0) {
+    scan_tile_reduce<T><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, tile);
+    scan_tile_offsets<<<1, SCAN_BLOCK, 0, s>>>(tile, ntiles, out + n);
+    scan_tile_apply<T><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, n, tile);
+  } else {
+    cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- radix sort
+constexpr int RS_BLOCK = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_BLOCK * RS_ROUNDS;
+
+__global__ void rs_hist(const uint64_t *keys, int64_t n, int shift, int64_t nblocks, int64_t *hist) {
+  __shared__ int32_t cnt[256];
+  cnt[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ROUNDS; r++) {
+    int64_t i = base + (int64_t)r * RS_BLOCK + threadIdx.x;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255], 1);
+  }
+  __syncthreads();
+  hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter: elements of a tile are taken 256 at a time in index order;
+// inside a round, warp w's elements precede warp w+1's, and inside a warp the
+// lane order decides (match_any gives the peers with the same digit).
+__global__ void rs_scatter(const uint64_t *keys, const int64_t *vals, uint64_t *okeys, int64_t *ovals,
+                           int64_t n, int shift, int64_t nblocks, const int64_t *offs) {
+  __shared__ int64_t base_off[256];
+  __shared__ int32_t wcnt[RS_BLOCK / 32][256];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  base_off[threadIdx.x] = offs[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+  int64_t tile = (int64_t)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ROUNDS; r++) {
+    for (int k = threadIdx.x; k < (RS_BLOCK / 32) * 256; k += RS_BLOCK) (&wcnt[0][0])[k] = 0;
+    __syncthreads();
+    int64_t i = tile + (int64_t)r * RS_BLOCK + threadIdx.x;
+    bool valid = i < n;
+    uint64_t key = valid ? keys[i] : 0;
+    uint32_t d = valid ? (uint32_t)((key >> shift) & 255) : 256u + lane;  // invalid: unique pseudo-digit
+    uint32_t peers = __match_any_sync(LD_FULL, d);
+    uint32_t lt = peers & ((1u << lane) - 1u);
+    int rank = __popc(lt);
+    if (valid && lt == 0) wcnt[wid][d] = __popc(peers);
+    __syncthreads();
+    // per digit: exclusive prefix over warps
+    {
+      int dd = threadIdx.x;  // RS_BLOCK == 256 digits
+      int32_t run = 0;
+#pragma unroll
+      for (int w = 0; w < RS_BLOCK / 32; w++) {
+        int32_t t = wcnt[w][dd];
+        wcnt[w][dd] = run;
+        run += t;
+      }
+      // stash the round total in the slot past the prefix: reuse a register
+      __syncthreads();
+      if (valid) {
+        int64_t pos = base_off[d] + wcnt[wid][d] + rank;
+        okeys[pos] = key;
+        if (vals) ovals[pos] = vals[i];
+      }
+      __syncthreads();
+      base_off[dd] += run;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+size_t scan_tmp_bytes(int64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE + 8) * sizeof(int64_t); }
+
+cudaError_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s) {
+  return scan_impl<int64_t>(in, out, n, tmp, s);
+}
+
+cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s) {
+  return scan_impl<int32_t>(in, out, n, tmp, s);
+}
+
+size_t sort_tmp_bytes(int64_t n) {
+  int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
+  int64_t hist = 256 * nblocks + 1;
+  return (size_t)(2 * hist) * sizeof(int64_t) + scan_tmp_bytes(256 * nblocks) + 256;
+}
+
+cudaError_t radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, int64_t *vals, int64_t *vals_alt, int64_t n,
+                           int bits, void *tmp, cudaStream_t s) {
+  if (n <= 1) return cudaSuccess;
+  int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
+  int64_t hlen = 256 * nblocks;
+  int64_t *hist = (int64_t *)tmp;
+  int64_t *offs = hist + hlen + 1;
+  void *stmp = (void *)(offs + hlen + 1);
+  uint64_t *src = keys, *dst = keys_alt;
+  int64_t *vsrc = vals, *vdst = vals_alt;
+  int passes = 0;
+  for (int shift = 0; shift < bits; shift += 8) {
+    rs_hist<<<(unsigned)nblocks, RS_BLOCK, 0, s>>>(src, n, shift, nblocks, hist);
+    cudaError_t e = exclusive_scan_i64(hist, offs, hlen, stmp, s);
+    if (e != cudaSuccess) return e;
+    rs_scatter<<<(unsigned)nblocks, RS_BLOCK, 0, s>>>(src, vsrc, dst, vdst, n, shift, nblocks, offs);
+    uint64_t *t = src; src = dst; dst = t;
+    int64_t *tv = vsrc; vsrc = vdst; vdst = tv;
+    passes++;
+  }
+  if (passes & 1) {
+    cudaMemcpyAsync(keys, src, (size_t)n * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s);
+    if (vals) cudaMemcpyAsync(vals, vsrc, (size_t)n * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  }
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void k_fill_i32(int32_t *p, int32_t v, int64_t n) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) p[i] = v;
+}
+__global__ void k_fill_i64(int64_t *p, int64_t v, int64_t n) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) p[i] = v;
+}
+__global__ void k_iota_i32(int32_t *p, int64_t n) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) p[i] = (int32_t)i;
+}
+}  // namespace
+
+int grid_for(int64_t n, int block, int max_blocks) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > max_blocks) g = max_blocks;
+  return (int)g;
+}
+
+void launch_fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s) {
+  if (n > 0) k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
+}
+void launch_fill_i64(int64_t *p, int64_t v, int64_t n, cudaStream_t s) {
+  if (n > 0) k_fill_i64<<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
+}
+void launch_iota_i32(int32_t *p, int64_t n, cudaStream_t s) {
+  if (n > 0) k_iota_i32<<<grid_for(n, 256), 256, 0, s>>>(p, n);
+}

@@ -1,0 +1,193 @@
+// Community tracking (Alg. "leidentr"), Sigma recomputation and the terms of
+// modularity (Eq. 1).
+#include <climits>
+
+#include "internal.h"
+
+namespace {
+
+constexpr int TB = 256;
+constexpr uint64_t EMPTY64 = ~0ull;
+
+__device__ __forceinline__ uint64_t hash64(uint64_t k) { return ld_splitmix64(k); }
+
+// Overlap weights: sum of K over vertices with (old, new) = key.
+__global__ void k_tr_clear(int64_t cap, uint64_t *keys, int64_t *vals) {
+  for (int64_t s = ld_gtid(); s < cap; s += ld_gstride()) { keys[s] = EMPTY64; vals[s] = 0; }
+}
+__global__ void k_tr_insert(int64_t N, const int32_t *Cold, const int32_t *Cnew, const int64_t *K, int64_t cap,
+                            uint64_t *keys, int64_t *vals) {
+  uint64_t mask = (uint64_t)cap - 1;
+  for (int64_t i = ld_gtid(); i < N; i += ld_gstride()) {
+    uint64_t key = ((uint64_t)(uint32_t)Cold[i] << 32) | (uint32_t)Cnew[i];
+    uint64_t s = hash64(key) & mask;
+    while (true) {
+      unsigned long long k = atomicCAS((unsigned long long *)&keys[s], EMPTY64, key);
+      if (k == EMPTY64 || k == key) {
+        atomicAdd((unsigned long long *)&vals[s], (unsigned long long)K[i]);
+        break;
+      }
+      s = (s + 1) & mask;
+    }
+  }
+}
+// For each old community: largest overlap weight ...
+__global__ void k_tr_best_new_w(int64_t cap, const uint64_t *keys, const int64_t *vals, long long *bw) {
+  for (int64_t s = ld_gtid(); s < cap; s += ld_gstride()) {
+    if (keys[s] == EMPTY64) continue;
+    atomicMax(&bw[keys[s] >> 32], (long long)vals[s]);
+  }
+}
+// ... and the lowest new id reaching it.
+__global__ void k_tr_best_new_c(int64_t cap, const uint64_t *keys, const int64_t *vals, const long long *bw,
+                                int32_t *bc) {
+  for (int64_t s = ld_gtid(); s < cap; s += ld_gstride()) {
+    if (keys[s] == EMPTY64) continue;
+    uint32_t b = (uint32_t)(keys[s] >> 32);
+    if (vals[s] == bw[b]) atomicMin(&bc[b], (int32_t)(keys[s] & 0xffffffffu));
+  }
+}
+// For each new community: among the old communities that picked it, the
+// largest overlap, then the lowest old id.
+__global__ void k_tr_best_old_w(int64_t N, const int32_t *bc, const long long *bw, long long *ow) {
+  for (int64_t b = ld_gtid(); b < N; b += ld_gstride())
+    if (bc[b] != INT_MAX) atomicMax(&ow[bc[b]], bw[b]);
+}
+__global__ void k_tr_best_old_b(int64_t N, const int32_t *bc, const long long *bw, const long long *ow, int32_t *ob) {
+  for (int64_t b = ld_gtid(); b < N; b += ld_gstride())
+    if (bc[b] != INT_MAX && bw[b] == ow[bc[b]]) atomicMin(&ob[bc[b]], (int32_t)b);
+}
+__global__ void k_tr_new_used(int64_t N, const int32_t *Cnew, int32_t *used) {
+  for (int64_t i = ld_gtid(); i < N; i += ld_gstride()) used[Cnew[i]] = 1;
+}
+// unmatched[c] (new id used, nobody picked it); free[id] (no old vertex had id)
+__global__ void k_tr_flags(int64_t N, const int32_t *new_used, const int32_t *ob, const int32_t *bc,
+                           int32_t *unmatched, int32_t *freef) {
+  for (int64_t c = ld_gtid(); c < N; c += ld_gstride()) {
+    unmatched[c] = (new_used[c] && ob[c] == INT_MAX) ? 1 : 0;
+    freef[c] = bc[c] == INT_MAX ? 1 : 0;
+  }
+}
+__global__ void k_tr_free_list(int64_t N, const int32_t *freef, const int64_t *frank, int32_t *flist) {
+  for (int64_t id = ld_gtid(); id < N; id += ld_gstride())
+    if (freef[id]) flist[frank[id]] = (int32_t)id;
+}
+__global__ void k_tr_map(int64_t N, const int32_t *new_used, const int32_t *ob, const int64_t *urank,
+                         const int32_t *flist, int32_t *map, uint8_t *matched) {
+  for (int64_t c = ld_gtid(); c < N; c += ld_gstride()) {
+    if (!new_used[c]) continue;
+    if (ob[c] != INT_MAX) { map[c] = ob[c]; matched[ob[c]] = 1; }
+    else map[c] = flist[urank[c]];
+  }
+}
+__global__ void k_tr_relabel(int64_t N, const int32_t *Cnew, const int32_t *map, const int64_t *K, int32_t *C,
+                             int64_t *Sig) {
+  for (int64_t i = ld_gtid(); i < N; i += ld_gstride()) {
+    int32_t c = map[Cnew[i]];
+    C[i] = c;
+    atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)K[i]);
+  }
+}
+__global__ void k_tr_dsig(int64_t N, const uint8_t *matched, int64_t *dSig) {
+  for (int64_t id = ld_gtid(); id < N; id += ld_gstride())
+    if (!matched[id]) dSig[id] = 0;
+}
+
+// ---- modularity
+__global__ void k_sig_of(int64_t N, const int32_t *C, const int64_t *K, int64_t *Sig) {
+  for (int64_t i = ld_gtid(); i < N; i += ld_gstride())
+    atomicAdd((unsigned long long *)&Sig[C[i]], (unsigned long long)K[i]);
+}
+__global__ void k_sigma_intra(int64_t N, const int64_t *off, const int32_t *deg, const int32_t *col, const int32_t *w,
+                              const int32_t *C, DevCounters *cnt) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ld_gtid() >> 5, nw = ld_gstride() >> 5;
+  int64_t acc = 0;
+  for (int64_t i = warp; i < N; i += nw) {
+    int32_t c = C[i];
+    int64_t b = off[i], d = deg[i];
+    for (int64_t a = lane; a < d; a += 32)
+      if (C[col[b + a]] == c) acc += w[b + a];
+  }
+  acc = ld_warp_sum_i64(acc);
+  if (lane == 0 && acc) atomicAdd((unsigned long long *)&cnt->sigma_intra, (unsigned long long)acc);
+}
+__global__ void k_sq(int64_t N, const int64_t *Sig, DevCounters *cnt) {
+  i128 acc = 0;
+  for (int64_t c = ld_gtid(); c < N; c += ld_gstride()) acc += (i128)Sig[c] * Sig[c];
+  // warp reduce in two halves
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += ld_shfl_xor_i128(acc, o);
+  if ((threadIdx.x & 31) == 0) ld_atomic_add_i128(cnt->sq, acc);
+}
+
+__global__ void k_rowsum(int64_t N, const int64_t *off, const int32_t *deg, const int32_t *w, int64_t *K,
+                         DevCounters *cnt) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = ld_gtid() >> 5, nw = ld_gstride() >> 5;
+  int64_t tot = 0;
+  for (int64_t i = warp; i < N; i += nw) {
+    int64_t b = off[i], d = deg[i], acc = 0;
+    for (int64_t a = lane; a < d; a += 32) acc += w[b + a];
+    acc = ld_warp_sum_i64(acc);
+    if (lane == 0) K[i] = acc;
+    tot += acc;
+  }
+  if (lane == 0 && tot) atomicAdd((unsigned long long *)&cnt->m2, (unsigned long long)tot);
+}
+
+}  // namespace
+
+// C^{t-1} = h->C, final top-level membership = h->Ctop  ->  h->C, h->Sig, h->dSig.
+void track_communities(leiden_handle *h) {
+  cudaStream_t s = h->stream;
+  int64_t N = h->n;
+  int gN = grid_for(N, TB);
+  k_tr_clear<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals);
+  k_tr_insert<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, h->K, h->tr_cap, h->tr_keys, h->tr_vals);
+  long long *bw = (long long *)h->lbuf0, *ow = (long long *)h->lbuf1;
+  int32_t *bc = h->ibuf0, *ob = h->ibuf1, *used = h->ibuf2;
+  launch_fill_i64((int64_t *)bw, -1, N, s);
+  launch_fill_i32(bc, INT_MAX, N, s);
+  launch_fill_i64((int64_t *)ow, -1, N, s);
+  launch_fill_i32(ob, INT_MAX, N, s);
+  cudaMemsetAsync(used, 0, (size_t)N * sizeof(int32_t), s);
+  k_tr_best_new_w<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals, bw);
+  k_tr_best_new_c<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals, bw, bc);
+  k_tr_best_old_w<<<gN, TB, 0, s>>>(N, bc, bw, ow);
+  k_tr_best_old_b<<<gN, TB, 0, s>>>(N, bc, bw, ow, ob);
+  k_tr_new_used<<<gN, TB, 0, s>>>(N, h->Ctop, used);
+  int32_t *unmatched = h->rep, *freef = h->prop;
+  k_tr_flags<<<gN, TB, 0, s>>>(N, used, ob, bc, unmatched, freef);
+  int64_t *urank = h->lbuf2, *frank = h->lbuf3;
+  exclusive_scan_i32_to_i64(unmatched, urank, N, h->scan_tmp, s);
+  exclusive_scan_i32_to_i64(freef, frank, N, h->scan_tmp, s);
+  int32_t *flist = h->parent, *map = h->CB;
+  k_tr_free_list<<<gN, TB, 0, s>>>(N, freef, frank, flist);
+  uint8_t *matched = h->dE;
+  cudaMemsetAsync(matched, 0, (size_t)N, s);
+  k_tr_map<<<gN, TB, 0, s>>>(N, used, ob, urank, flist, map, matched);
+  cudaMemsetAsync(h->Sig, 0, (size_t)N * sizeof(int64_t), s);
+  k_tr_relabel<<<gN, TB, 0, s>>>(N, h->Ctop, map, h->K, h->C, h->Sig);
+  k_tr_dsig<<<gN, TB, 0, s>>>(N, matched, h->dSig);
+}
+
+// sigma (intra arcs) and sum Sigma_c^2 of membership C on G^t.
+void modularity_terms(leiden_handle *h, const int32_t *C) {
+  cudaStream_t s = h->stream;
+  int64_t N = h->n;
+  int64_t *Sig = h->lbuf0;
+  cudaMemsetAsync(Sig, 0, (size_t)N * sizeof(int64_t), s);
+  cudaMemsetAsync(&h->dcnt->sigma_intra, 0, sizeof(int64_t), s);
+  cudaMemsetAsync(&h->dcnt->sq[0], 0, 2 * sizeof(unsigned long long), s);
+  k_sig_of<<<grid_for(N, TB), TB, 0, s>>>(N, C, h->K, Sig);
+  k_sigma_intra<<<grid_for(N * 32, TB), TB, 0, s>>>(N, h->g_off, h->g_deg, h->g_col, h->g_w, C, h->dcnt);
+  k_sq<<<grid_for(N, TB), TB, 0, s>>>(N, Sig, h->dcnt);
+}
+
+// K = row sums of G^t and 2m.
+void recompute_weights(leiden_handle *h) {
+  cudaStream_t s = h->stream;
+  cudaMemsetAsync(&h->dcnt->m2, 0, sizeof(int64_t), s);
+  k_rowsum<<<grid_for(h->n * 32, TB), TB, 0, s>>>(h->n, h->g_off, h->g_deg, h->g_w, h->K, h->dcnt);
+}

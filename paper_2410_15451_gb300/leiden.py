@@ -1,0 +1,257 @@
+"""Python binding of the C ABI in include/leiden_gb300.h (ctypes; argument
+marshalling only -- every step of the computation runs in the CUDA library).
+
+The functions keep the C names.  Host arrays are numpy; device arrays may be
+anything exposing ``data_ptr()`` (e.g. torch CUDA tensors) or a raw int
+pointer.  Loading fails loudly when ``libleiden_gb300.so`` has not been
+built (see ``paper_2410_15451_gb300._build.build``); there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+LEIDEN_OK, LEIDEN_ERR_ARG, LEIDEN_ERR_BATCH, LEIDEN_ERR_OOM = 0, 1, 2, 3
+LEIDEN_ERR_CUDA, LEIDEN_ERR_TIMEOUT, LEIDEN_ERR_STATE = 4, 5, 6
+LEIDEN_ND, LEIDEN_DS, LEIDEN_DF = 0, 1, 2
+TRACE_WORDS = 2 + 10 * 25
+
+_lib = None
+
+
+class leiden_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("tau_drop", ctypes.c_double), ("tau_refine", ctypes.c_double),
+                ("max_iterations", ctypes.c_int32), ("max_passes", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32), ("classes", ctypes.c_int32),
+                ("slack", ctypes.c_double), ("min_slack", ctypes.c_int32), ("collect_stats", ctypes.c_int32)]
+
+
+class leiden_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "passes", "lm_iterations", "lm_vertices", "lm_arcs", "lm_moves", "refine_vertices", "refine_arcs",
+        "aggregate_arcs", "affected", "communities", "batch_arcs")] + [(k, ctypes.c_double) for k in (
+        "ms_total", "ms_batch", "ms_move", "ms_refine", "ms_aggregate", "ms_track")]
+
+
+class LeidenError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"leiden status {status}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load():
+    """Load libleiden_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB_PATH
+    if not os.path.exists(path):
+        raise OSError(f"{path} not found: build it with paper_2410_15451_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    P = ctypes.POINTER
+    lib.leiden_default_params.argtypes = [P(leiden_params)]
+    lib.leiden_default_params.restype = None
+    lib.leiden_create.argtypes = [P(leiden_params), i64, vp, vp, vp, vp, P(vp)]
+    lib.leiden_static.argtypes = [vp, vp]
+    lib.leiden_update.argtypes = [vp, vp, i64, vp, i64, ctypes.c_int, vp]
+    lib.leiden_update_device.argtypes = [vp, vp, i64, vp, i64, ctypes.c_int, vp]
+    lib.leiden_modularity.argtypes = [vp, vp, P(ctypes.c_double)]
+    lib.leiden_membership_device.argtypes = [vp, P(vp)]
+    lib.leiden_get_state.argtypes = [vp, vp, vp, vp, vp, P(i64)]
+    lib.leiden_graph_arcs.argtypes = [vp]
+    lib.leiden_graph_arcs.restype = i64
+    lib.leiden_get_graph.argtypes = [vp, vp, vp, vp]
+    lib.leiden_get_affected.argtypes = [vp, vp]
+    lib.leiden_get_trace.argtypes = [vp, vp]
+    lib.leiden_get_stats.argtypes = [vp, P(leiden_stats)]
+    lib.leiden_last_error.argtypes = [vp]
+    lib.leiden_last_error.restype = ctypes.c_char_p
+    lib.leiden_destroy.argtypes = [vp]
+    lib.leiden_destroy.restype = None
+    for f in ("leiden_create", "leiden_static", "leiden_update", "leiden_update_device", "leiden_modularity",
+              "leiden_membership_device", "leiden_get_state", "leiden_get_graph", "leiden_get_affected",
+              "leiden_get_trace", "leiden_get_stats"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _check(h, st):
+    if st != LEIDEN_OK:
+        msg = load().leiden_last_error(h)
+        raise LeidenError(st, msg.decode() if msg else "")
+
+
+# ---- C-named functions ---------------------------------------------------------------
+
+def leiden_default_params() -> leiden_params:
+    p = leiden_params()
+    load().leiden_default_params(ctypes.byref(p))
+    return p
+
+
+def leiden_create(params, n, offsets, cols, weights=None, cuda_stream=None) -> int:
+    lib = load()
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    cols = np.ascontiguousarray(cols, np.int32)
+    weights = None if weights is None else np.ascontiguousarray(weights, np.int32)
+    h = ctypes.c_void_p()
+    st = lib.leiden_create(ctypes.byref(params) if params is not None else None, int(n), _ptr(offsets), _ptr(cols),
+                           _ptr(weights), cuda_stream, ctypes.byref(h))
+    _check(None, st)
+    return h.value
+
+
+def leiden_static(h, membership_out=None):
+    _check(h, load().leiden_static(h, _ptr(membership_out)))
+
+
+def leiden_update(h, dels, ins, mode, membership_out=None):
+    dels = np.ascontiguousarray(np.asarray(dels, np.int32).reshape(-1, 3))
+    ins = np.ascontiguousarray(np.asarray(ins, np.int32).reshape(-1, 3))
+    _check(h, load().leiden_update(h, _ptr(dels), len(dels), _ptr(ins), len(ins), int(mode), _ptr(membership_out)))
+
+
+def leiden_update_device(h, d_dels, n_del, d_ins, n_ins, mode, d_membership_out=None):
+    _check(h, load().leiden_update_device(h, _ptr(d_dels), int(n_del), _ptr(d_ins), int(n_ins), int(mode),
+                                          _ptr(d_membership_out)))
+
+
+def leiden_modularity(h, membership=None) -> float:
+    q = ctypes.c_double()
+    m = None if membership is None else np.ascontiguousarray(membership, np.int32)
+    _check(h, load().leiden_modularity(h, _ptr(m), ctypes.byref(q)))
+    return q.value
+
+
+def leiden_membership_device(h) -> int:
+    p = ctypes.c_void_p()
+    _check(h, load().leiden_membership_device(h, ctypes.byref(p)))
+    return p.value
+
+
+def leiden_get_state(h, n):
+    C = np.zeros(n, np.int32)
+    K = np.zeros(n, np.int64)
+    S = np.zeros(n, np.int64)
+    dS = np.zeros(n, np.int64)
+    m2 = ctypes.c_int64()
+    _check(h, load().leiden_get_state(h, _ptr(C), _ptr(K), _ptr(S), _ptr(dS), ctypes.byref(m2)))
+    return dict(C=C, K=K, Sigma=S, dSigma=dS, m2=m2.value)
+
+
+def leiden_graph_arcs(h) -> int:
+    return int(load().leiden_graph_arcs(h))
+
+
+def leiden_get_graph(h, n):
+    arcs = leiden_graph_arcs(h)
+    off = np.zeros(n + 1, np.int64)
+    col = np.zeros(max(arcs, 1), np.int32)
+    w = np.zeros(max(arcs, 1), np.int64)
+    _check(h, load().leiden_get_graph(h, _ptr(off), _ptr(col), _ptr(w)))
+    return off, col[:arcs], w[:arcs]
+
+
+def leiden_get_affected(h, n):
+    dV = np.zeros(n, np.uint8)
+    _check(h, load().leiden_get_affected(h, _ptr(dV)))
+    return dV
+
+
+def leiden_get_trace(h) -> dict:
+    t = np.zeros(TRACE_WORDS, np.int64)
+    _check(h, load().leiden_get_trace(h, _ptr(t)))
+    passes = []
+    for p in range(int(t[0])):
+        r = t[2 + p * 25: 2 + (p + 1) * 25]
+        passes.append(dict(n=int(r[0]), iterations=int(r[1]), communities=int(r[2]), refined_any=int(r[3]),
+                           refine_rounds=int(r[4]), moves=[int(x) for x in r[5:5 + min(int(r[1]), 20)]]))
+    return dict(passes=passes, affected=int(t[1]))
+
+
+def leiden_get_stats(h) -> dict:
+    s = leiden_stats()
+    _check(h, load().leiden_get_stats(h, ctypes.byref(s)))
+    return {k: getattr(s, k) for k, _ in leiden_stats._fields_}
+
+
+def leiden_last_error(h=None) -> str:
+    m = load().leiden_last_error(h)
+    return m.decode() if m else ""
+
+
+def leiden_destroy(h):
+    if h:
+        load().leiden_destroy(h)
+
+
+class Leiden:
+    """Owning wrapper of a handle: ``Leiden(n, off, col, w).static()``, ``.update(dels, ins, mode)``."""
+
+    def __init__(self, n, off, col, w=None, deterministic=True, cuda_stream=None, **params):
+        p = leiden_default_params()
+        p.deterministic = 1 if deterministic else 0
+        for k, v in params.items():
+            setattr(p, k, v)
+        self.n = int(n)
+        self.h = leiden_create(p, n, off, col, w, cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            leiden_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def static(self) -> np.ndarray:
+        out = np.zeros(self.n, np.int32)
+        leiden_static(self.h, out)
+        return out
+
+    def update(self, dels, ins, mode) -> np.ndarray:
+        out = np.zeros(self.n, np.int32)
+        leiden_update(self.h, dels, ins, mode, out)
+        return out
+
+    def modularity(self, membership=None) -> float:
+        return leiden_modularity(self.h, membership)
+
+    def state(self):
+        return leiden_get_state(self.h, self.n)
+
+    def graph(self):
+        return leiden_get_graph(self.h, self.n)
+
+    def affected(self):
+        return leiden_get_affected(self.h, self.n)
+
+    def trace(self):
+        return leiden_get_trace(self.h)
+
+    def stats(self):
+        return leiden_get_stats(self.h)

@@ -1,0 +1,67 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every function
+declared in include/*.h (no GPU needed; no compute call is made)."""
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2410_15451_gb300 import _build
+from paper_2410_15451_gb300 import leiden as L
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b([a-z_][a-z0-9_]*)\s*\(", text):
+            name = m.group(1)
+            if name.startswith("leiden_") and name not in names:
+                names.append(name)
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return L.load()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("leiden_create", "leiden_static", "leiden_update", "leiden_modularity", "leiden_destroy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_default_params_match_the_paper(lib):
+    p = L.leiden_default_params()
+    assert p.tau == 1e-2 and p.tau_drop == 10.0 and p.tau_refine == 0.6
+    assert p.max_iterations == 20 and p.max_passes == 10
+    assert p.deterministic == 1 and p.classes == 4
+
+
+def test_struct_layouts(lib):
+    assert ctypes.sizeof(L.leiden_params) == 8 * 3 + 4 * 4 + 8 + 4 * 2
+    assert ctypes.sizeof(L.leiden_stats) == 8 * 11 + 8 * 6
+
+
+def test_create_rejects_bad_input_without_touching_the_gpu(lib):
+    import numpy as np
+
+    off = np.array([0, 1, 1], np.int64)
+    col = np.array([0], np.int32)  # self-loop
+    with pytest.raises(L.LeidenError) as e:
+        L.leiden_create(None, 2, off, col)
+    assert e.value.status == L.LEIDEN_ERR_ARG
+    assert "self-loop" in L.leiden_last_error(None)

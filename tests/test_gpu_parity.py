@@ -1,0 +1,232 @@
+"""CUDA path vs the CPU oracle, through the C ABI (needs a GB300).
+
+Deterministic mode must equal the oracle's SYNC schedule bit for bit: the
+applied CSR, the affected set, K / Sigma / Delta Sigma / 2m, the per-pass
+trace (iterations, moves per iteration, communities, refinement rounds),
+the final membership and Q (same double).  Asynchronous mode must give
+connected communities within 0.005 of the oracle's SEQ modularity.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_15451_gb300 import leiden as L
+from paper_2410_15451_gb300 import synth
+from tests.helpers import csr_from_edges, disconnected_communities
+
+pytestmark = pytest.mark.gpu
+
+MODES = [(L.LEIDEN_ND, oracle.ND), (L.LEIDEN_DS, oracle.DS), (L.LEIDEN_DF, oracle.DF)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_15451_gb300 import _build
+
+    _build.build()
+    L.load()
+
+
+def hub_graph(seed=5):
+    """Planted partition plus a hub joined to 3000 vertices (degree > 2048)
+    and a star of 40 leaves: exercises the global-table bins."""
+    g = synth.planted_partition(6000, 30, 10, 0.25, seed)
+    src = np.repeat(np.arange(g.n), np.diff(g.off))
+    keep = src < g.col
+    edges = list(zip(src[keep].tolist(), g.col[keep].tolist()))
+    rng = np.random.default_rng(seed)
+    hub = 17
+    for v in rng.choice(np.arange(200, 6000), 3000, replace=False):
+        edges.append((hub, int(v)))
+    for leaf in range(6000, 6040):
+        edges.append((6040, leaf))
+    edges = sorted({(min(a, b), max(a, b)) for a, b in edges if a != b})
+    off, col, w = csr_from_edges(6041 + 5, edges)  # 5 isolated vertices at the end
+    return synth.Graph(6046, off, col, w.astype(np.int32))
+
+
+GRAPHS = {
+    "planted10k": lambda: synth.workload_small(),
+    "rmat12": lambda: synth.rmat(12, seed=31),
+    "rmat14": lambda: synth.rmat(14, seed=32),
+    "hubs": lambda: hub_graph(),
+    "weighted": lambda: _weighted(synth.planted_partition(3000, 15, 12, 0.3, 41)),
+}
+
+
+def _weighted(g):
+    # symmetric weights 1..8 from the smaller endpoint pair
+    src = np.repeat(np.arange(g.n), np.diff(g.off)).astype(np.int64)
+    a, b = np.minimum(src, g.col), np.maximum(src, g.col)
+    w = ((a * 2654435761 + b * 40503) % 8 + 1).astype(np.int32)
+    return synth.Graph(g.n, g.off, g.col, w)
+
+
+def assert_same_state(gpu, ref):
+    gs, rs = gpu.state(), ref.state()
+    for k in ("C", "K", "Sigma", "dSigma"):
+        assert np.array_equal(gs[k], rs[k]), k
+    assert gs["m2"] == rs["m2"]
+
+
+def assert_same_trace(gpu, ref):
+    tg, tr = gpu.trace(), ref.trace()
+    assert tg["affected"] == tr["affected"]
+    assert len(tg["passes"]) == len(tr["passes"])
+    for pg, pr in zip(tg["passes"], tr["passes"]):
+        assert pg == pr, (pg, pr)
+
+
+@pytest.mark.parametrize("name", sorted(GRAPHS))
+def test_static_bit_exact(name):
+    g = GRAPHS[name]()
+    gpu = L.Leiden(g.n, g.off, g.col, g.w)
+    ref = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    cg, cr = gpu.static(), ref.static()
+    assert_same_trace(gpu, ref)
+    assert np.array_equal(cg, cr)
+    assert_same_state(gpu, ref)
+    assert gpu.modularity() == ref.modularity()
+    assert disconnected_communities(g.off, g.col, cg) == 0
+
+
+@pytest.mark.parametrize("name", ["planted10k", "rmat14", "hubs", "weighted"])
+@pytest.mark.parametrize("mode", MODES, ids=["ND", "DS", "DF"])
+def test_updates_bit_exact(name, mode):
+    gm, om = mode
+    g = GRAPHS[name]()
+    gpu = L.Leiden(g.n, g.off, g.col, g.w)
+    ref = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    gpu.static()
+    ref.static()
+    cur = g
+    for k, size in enumerate([7, 150, 1200]):
+        dels, ins = synth.random_batch(cur, size, seed=500 + k, w_lo=1, w_hi=3 if name == "weighted" else 1)
+        cg = gpu.update(dels, ins, gm)
+        cr = ref.update(dels, ins, om)
+        cur = synth.apply_batch_numpy(cur, dels, ins)
+        og, rg = gpu.graph(), ref.graph()
+        for a, b in zip(og, rg):
+            assert np.array_equal(a, b)
+        assert np.array_equal(gpu.affected(), ref.affected())
+        assert_same_trace(gpu, ref)
+        assert np.array_equal(cg, cr), f"batch {k}"
+        assert_same_state(gpu, ref)
+        assert gpu.modularity() == ref.modularity()
+
+
+def test_batch_edge_cases_bit_exact():
+    """Insertion of an existing edge (weights add), delete + reinsert of the
+    same edge, repeated insertions (add up) and repeated deletions (collapse),
+    isolating a vertex, and rows that outgrow their slack (rebuild)."""
+    g = synth.planted_partition(2000, 20, 10, 0.2, 61)
+    gpu = L.Leiden(g.n, g.off, g.col, g.w, slack=0.0, min_slack=1)
+    ref = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    gpu.static()
+    ref.static()
+    u = 5
+    nb = g.col[g.off[u]:g.off[u + 1]]
+    v0, v1 = int(nb[0]), int(nb[1])
+    dels = np.array([[u, v0, 1], [v0, u, 1], [u, v1, 9]], np.int32)          # repeated deletion
+    ins = np.array([[u, v1, 3],                                              # delete + reinsert
+                    [u, int(nb[2]), 2], [u, int(nb[2]), 1],                  # existing edge, twice
+                    [u, 1500, 1], [u, 1501, 1], [u, 1502, 1], [1500, 1501, 4]], np.int32)
+    cg = gpu.update(dels, ins, L.LEIDEN_DF)
+    cr = ref.update(dels, ins, oracle.DF)
+    for a, b in zip(gpu.graph(), ref.graph()):
+        assert np.array_equal(a, b)
+    assert np.array_equal(cg, cr)
+    assert_same_state(gpu, ref)
+    # isolate vertex 7 entirely
+    nb7 = g.col[g.off[7]:g.off[8]]
+    d2 = np.array([[7, int(v), 1] for v in nb7], np.int32)
+    cg = gpu.update(d2, np.zeros((0, 3), np.int32), L.LEIDEN_DS)
+    cr = ref.update(d2, np.zeros((0, 3), np.int32), oracle.DS)
+    assert np.array_equal(cg, cr)
+    assert_same_state(gpu, ref)
+
+
+def test_empty_batch_and_invalid_batches():
+    g = synth.planted_partition(2000, 20, 10, 0.2, 62)
+    gpu = L.Leiden(g.n, g.off, g.col, g.w)
+    gpu.static()
+    before = gpu.state()
+    c = gpu.update(np.zeros((0, 3), np.int32), np.zeros((0, 3), np.int32), L.LEIDEN_DF)
+    assert np.array_equal(c, before["C"])
+    assert gpu.affected().sum() == 0
+    absent = next(v for v in range(1, g.n) if v not in g.col[g.off[0]:g.off[1]])
+    bad = [
+        (np.array([[0, absent, 1]], np.int32), np.zeros((0, 3), np.int32)),
+        (np.zeros((0, 3), np.int32), np.array([[3, 3, 1]], np.int32)),
+        (np.zeros((0, 3), np.int32), np.array([[1, 2, 0]], np.int32)),
+        (np.zeros((0, 3), np.int32), np.array([[1, g.n, 1]], np.int32)),
+    ]
+    for d, i in bad:
+        with pytest.raises(L.LeidenError) as e:
+            gpu.update(d, i, L.LEIDEN_DF)
+        assert e.value.status == L.LEIDEN_ERR_BATCH
+        after = gpu.state()
+        for k in ("C", "K", "Sigma", "dSigma"):
+            assert np.array_equal(before[k], after[k])
+        og = gpu.graph()
+        assert np.array_equal(og[0], g.off) and np.array_equal(og[1], g.col)
+
+
+def test_update_before_static_is_rejected():
+    g = synth.planted_partition(500, 5, 8, 0.2, 63)
+    gpu = L.Leiden(g.n, g.off, g.col, g.w)
+    with pytest.raises(L.LeidenError) as e:
+        gpu.update(np.zeros((0, 3), np.int32), np.zeros((0, 3), np.int32), L.LEIDEN_DF)
+    assert e.value.status == L.LEIDEN_ERR_STATE
+
+
+@pytest.mark.parametrize("name", ["planted10k", "rmat14", "hubs"])
+def test_async_mode_quality(name):
+    """In-place moves: connected communities, Q within 0.005 of the oracle's
+    SEQ schedule (static and after a DF update)."""
+    g = GRAPHS[name]()
+    gpu = L.Leiden(g.n, g.off, g.col, g.w, deterministic=False)
+    ref = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SEQ)
+    cg = gpu.static()
+    ref.static()
+    assert disconnected_communities(g.off, g.col, cg) == 0
+    assert gpu.modularity() >= ref.modularity() - 0.005
+    dels, ins = synth.random_batch(g, 300, seed=77)
+    cg = gpu.update(dels, ins, L.LEIDEN_DF)
+    ref.update(dels, ins, oracle.DF)
+    off, col, _ = gpu.graph()
+    assert disconnected_communities(off, col, cg) == 0
+    assert gpu.modularity() >= ref.modularity() - 0.005
+
+
+def test_modularity_of_given_membership_matches_oracle():
+    g = synth.rmat(12, seed=33)
+    gpu = L.Leiden(g.n, g.off, g.col, g.w)
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        C = rng.integers(0, 50, g.n).astype(np.int32)
+        q, _ = oracle.modularity(g.off, g.col, g.w.astype(np.int64), C)
+        assert gpu.modularity(C) == q
+
+
+def test_device_entry_point_matches_host_entry_point():
+    import torch
+
+    g = synth.rmat(13, seed=34)
+    dels, ins = synth.random_batch(g, 400, seed=35)
+    a = L.Leiden(g.n, g.off, g.col, g.w)
+    b = L.Leiden(g.n, g.off, g.col, g.w)
+    a.static()
+    b.static()
+    ca = a.update(dels, ins, L.LEIDEN_DF)
+    dd = torch.from_numpy(dels).cuda()
+    di = torch.from_numpy(ins).cuda()
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    L.leiden_update_device(b.h, dd, len(dels), di, len(ins), L.LEIDEN_DF, out)
+    assert np.array_equal(out.cpu().numpy(), ca)
