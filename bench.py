@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of DF-Leiden updates on one GB300 (or N replicas under torchrun).
+
+Workload (the metric's configuration): R-MAT scale 22 (4.19M vertices, edge
+factor 16, a=0.57 b=c=0.19 d=0.05, symmetrised, deduplicated, unit weights),
+static Leiden once, then a stream of random batch updates of 1e-3|E| edges
+(80% insertions of uniform non-edges, 20% deletions of uniform existing
+edges) processed by DF Leiden through the C ABI.  A step is one update: batch
+canonicalisation and apply, DF marking, the Leiden pass loop and tracking.
+
+value   = batch edges / device time of leiden_update_device (batch resident in
+          HBM before the step; CSR ~1 GB, larger than L2; L2 is also flushed
+          between steps outside the timed intervals)
+e2e     = the same through leiden_update with host batch arrays and the
+          membership copied back to the host, wall clock
+Also reported: speedup over GPU static Leiden on the final graph and the
+modularity gap, p50/p99 latency, the batch-size sweep, the roofline of the
+local-moving kernels, the oracle timed on the host cores (bounded sample),
+and SM clocks sampled during the timed region.
+
+--impl reference times the CPU oracle (plain sequential C) on a bounded
+sample of the same workload: R-MAT scale 19 with the same generator
+parameters, DF updates of 1e-3|E| edges.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "DF-Leiden update edges/s & speedup vs GPU static Leiden at dQ<=0.005; p99 lat"
+SAMPLE_SCALE = 19
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--batch-frac", type=float, default=1e-3)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--async-mode", action="store_true", help="in-place moves instead of the snapshot schedule")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.file.name)
+        if sm:
+            out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+# ----------------------------------------------------------------------------- helpers
+def hbm_peak():
+    try:
+        with open(PEAKS_PATH) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def make_batches(g, n_batches, size, seed):
+    """n_batches batches of `size` edges with pairwise-distinct edits, valid
+    in sequence: deletions are distinct edges of G^0, insertions distinct
+    non-edges of G^0."""
+    from paper_2410_15451_gb300 import synth
+
+    n_ins = int(round(0.8 * size))
+    n_del = size - n_ins
+    dels, ins = synth.random_batch(g, n_batches * size, seed=seed, frac_ins=n_batches * n_ins / (n_batches * size))
+    out = []
+    for k in range(n_batches):
+        out.append((np.ascontiguousarray(dels[k * n_del:(k + 1) * n_del]),
+                    np.ascontiguousarray(ins[k * n_ins:(k + 1) * n_ins])))
+    return out
+
+
+def oracle_sample(steps, warmup, seed, budget_s=None):
+    """The CPU oracle (as it stands, SYNC schedule) on the bounded sample:
+    R-MAT scale 19, static once (untimed), then DF updates of 1e-3|E|."""
+    import oracle
+    from paper_2410_15451_gb300 import synth
+
+    g = synth.rmat(SAMPLE_SCALE, 16, 0.57, 0.19, 0.19, seed)
+    size = max(1, int(round(1e-3 * g.edges)))
+    batches = make_batches(g, warmup + steps, size, seed + 7)
+    o = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    o.static()
+    times = []
+    for k, (d, i) in enumerate(batches):
+        t0 = time.perf_counter()
+        o.update(d, i, oracle.DF)
+        dt = time.perf_counter() - t0
+        if k >= warmup:
+            times.append(dt)
+        if budget_s and sum(times) > budget_s and len(times) >= 1:
+            break
+    edges = size * len(times)
+    return dict(value=edges / sum(times), unit="edges/s", cores=1, kind="oracle",
+                sample=f"R-MAT scale {SAMPLE_SCALE} ({g.n} vertices, {g.edges} edges), DF updates of "
+                       f"{size} edges (1e-3|E|), {len(times)} timed after {warmup} warm-up, SYNC schedule, "
+                       f"1 host thread"), float(np.mean(times))
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    cb, mean_s = oracle_sample(args.steps, args.warmup, 2410154510 + 1)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "edges/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"R-MAT scale {SAMPLE_SCALE} DF updates of 1e-3|E| (bounded sample of the "
+                               f"R-MAT scale 22 workload)", "batch_frac": 1e-3},
+        "cpu_baseline": cb,
+        "e2e": {"value": cb["value"], "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2410_15451_gb300 import leiden as L
+    from paper_2410_15451_gb300 import synth
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    seed = synth.BASE_SEED + 1 + 1000 * rank
+    t_gen = time.time()
+    g = synth.rmat(args.scale, 16, 0.57, 0.19, 0.19, seed)
+    gen_s = time.time() - t_gen
+    E = g.edges
+    size = max(1, int(round(args.batch_frac * E)))
+    W, K = args.warmup, args.steps
+    batches = make_batches(g, W + 2 * K, size, seed + 5)
+    gpu = L.Leiden(g.n, g.off, g.col, g.w, deterministic=not args.async_mode, cuda_stream=stream.cuda_stream)
+    gpu.static()
+    dev_batches = [(torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)) for d, i in batches]
+    d_out = torch.empty(g.n, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (129 MB)
+    torch.cuda.synchronize()
+
+    def dev_step(k):
+        d, i = dev_batches[k]
+        L.leiden_update_device(gpu.h, d, d.shape[0], i, i.shape[0], L.LEIDEN_DF, d_out)
+
+    for k in range(W):
+        dev_step(k)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    times_ms, lm_stats = [], []
+    for k in range(W, W + K):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dev_step(k)
+        e1.record(stream)
+        e1.synchronize()
+        times_ms.append(e0.elapsed_time(e1))
+        lm_stats.append(gpu.stats())
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_s = sum(times_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = size * K * world / total_s
+    # e2e through the host entry point (host batches, membership to the host)
+    host_out = np.zeros(g.n, np.int32)
+    e2e_times = []
+    for k in range(W + K, W + 2 * K):
+        d, i = batches[k]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.leiden_update(gpu.h, d, i, L.LEIDEN_DF, host_out)
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_value = size * K * world / sum(e2e_times)
+    q_df = gpu.modularity()
+    # GPU static Leiden on the same final graph
+    off, col, w = gpu.graph()
+    st_times = []
+    for _ in range(2):
+        s = L.Leiden(g.n, off, col, w.astype(np.int32), deterministic=not args.async_mode,
+                     cuda_stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.leiden_static(s.h, None)
+        e1.record(stream)
+        e1.synchronize()
+        st_times.append(e0.elapsed_time(e1))
+        q_static = s.modularity()
+        s.close()
+    t_static = min(st_times)
+    mean_ms = float(np.mean(times_ms))
+    result = dict(value=value, mean_ms=mean_ms, p50=float(np.percentile(times_ms, 50)),
+                  p99=float(np.percentile(times_ms, 99)), e2e=e2e_value, q_df=q_df, q_static=q_static,
+                  t_static=t_static, clk=clk, lm_stats=lm_stats, E=E, n=g.n, size=size, gen_s=gen_s,
+                  e2e_p99=float(np.percentile(np.array(e2e_times) * 1e3, 99)))
+    # batch-size sweep (each size continues the evolving graph)
+    sweep = {}
+    if not args.no_sweep:
+        for frac in (1e-7, 1e-5, 1e-3, 1e-1):
+            sz = max(1, int(round(frac * E)))
+            nb = 3 if frac >= 0.1 else 6
+            try:
+                bs = make_batches(synth.Graph(g.n, off, col, w.astype(np.int32)), nb, sz, seed + int(1 / frac))
+            except RuntimeError:
+                continue
+            ts = []
+            for k, (d, i) in enumerate(bs):
+                dd, di = torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)
+                torch.cuda.synchronize()
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                L.leiden_update_device(gpu.h, dd, d.shape[0], di, i.shape[0], L.LEIDEN_DF, d_out)
+                e1.record(stream)
+                e1.synchronize()
+                if k > 0:
+                    ts.append(e0.elapsed_time(e1))
+            sweep[f"{frac:g}"] = dict(batch_edges=sz, ms_mean=float(np.mean(ts)), p99_ms=float(np.percentile(ts, 99)),
+                                      edges_per_s=sz / (np.mean(ts) / 1e3))
+            off, col, w = gpu.graph()
+    result["sweep"] = sweep
+    gpu.close()
+    return result
+
+
+def roofline_lm(stats_list, mean_ms):
+    """Algorithmic bytes of local moving per call (int32 col/w, int32 C, int64
+    K/Sigma): 16 B per vertex visit (offset, degree, K, C) + 12 B per scanned
+    arc (col, w, C[j]) ; achieved over the local-moving phase time."""
+    peak, src = hbm_peak()
+    vis = np.mean([s["lm_vertices"] for s in stats_list])
+    arcs = np.mean([s["lm_arcs"] for s in stats_list])
+    ms = np.mean([s["ms_move"] for s in stats_list]) if stats_list and stats_list[0]["ms_move"] > 0 else mean_ms
+    byts = 16 * vis + 12 * arcs
+    achieved = byts / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+            "kernel": "local-moving phase (k_collect + k_decide_* + k_apply_moves)"}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    r = run_ours(args, rank, world, local_rank)
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb, _ = oracle_sample(3, 1, 2410154510 + 1, budget_s=25)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": r["value"], "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["mean_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"R-MAT scale {args.scale} (n={r['n']}, |E|={r['E']}), DF updates of "
+                                   f"{r['size']} edges ({args.batch_frac:g}|E|, 80% ins / 20% del)",
+                       "parallelism": "replicas" if world > 1 else "single-gpu",
+                       "schedule": "in-place" if args.async_mode else "snapshot (deterministic)",
+                       "l2": "CSR > L2 and L2 flushed (256 MB write) between timed steps"},
+            "speedup_vs_static": r["t_static"] / r["mean_ms"], "static_ms": r["t_static"],
+            "q_df": r["q_df"], "q_static": r["q_static"], "dq": r["q_static"] - r["q_df"],
+            "quality_ok": bool(r["q_static"] - r["q_df"] <= 0.005),
+            "p50_ms": r["p50"], "p99_ms": r["p99"],
+            "e2e": {"value": r["e2e"], "unit": "edges/s", "h2d_bytes_per_step": r["size"] * 12,
+                    "d2h_bytes_per_step": r["n"] * 4, "p99_ms": r["e2e_p99"]},
+            "roofline": roofline_lm(r["lm_stats"], r["mean_ms"]),
+            "cpu_baseline": cb,
+            "clocks": r["clk"],
+            "sweep": r["sweep"],
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -111,7 +111,8 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   int64_t moves_total = 0;
   for (int lp = 0; lp < p.max_passes; lp++) {
     int64_t n = g.n;
-    int64_t *tr = &h->trace[2 + lp * 25];
+    int64_t tr_spare[25];
+    int64_t *tr = lp < 10 ? &h->trace[2 + lp * 25] : tr_spare;  // the trace keeps the first 10 passes
     passes++;
     tr[0] = n;
     mark(h, 2);

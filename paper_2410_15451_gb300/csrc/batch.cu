@@ -371,7 +371,7 @@ void release(leiden_handle *h, void *p) {
 
 cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
   BatchBuffers &b = h->b;
-  if (edges <= b.cap_edges) return cudaSuccess;
+  if (b.cap_edges > 0 && edges <= b.cap_edges) return cudaSuccess;  // the first call always allocates
   int64_t cap = std::max<int64_t>(edges, 1024);
   void *old[] = {b.dkey, b.dkey_alt, b.ikey, b.ikey_alt, b.iw, b.iw_alt, b.dw, b.flag,
                  b.pos, b.ins_state, b.ins_pos, b.row_dlo, b.row_dhi, b.row_ilo, b.row_ihi, b.row_len,

@@ -119,12 +119,11 @@ __global__ void k_count_distinct(int64_t n, const int32_t *C, int32_t *seen, Dev
 __global__ void k_member_count(int64_t n, const int32_t *C, int32_t *cnt_c) {
   for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) atomicAdd(&cnt_c[C[i]], 1);
 }
-__global__ void k_member_fill(int64_t n, const int32_t *C, const int64_t *coff, unsigned long long *cursor,
-                              int32_t *cverts) {
+// cursor[c] starts at coff[c]; each member takes the next slot of its community.
+__global__ void k_member_fill(int64_t n, const int32_t *C, unsigned long long *cursor, int32_t *cverts) {
   for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) {
-    int32_t c = C[i];
-    unsigned long long p = atomicAdd(&cursor[c], 1ull);
-    cverts[coff[c] + (int64_t)p] = (int32_t)i;
+    unsigned long long p = atomicAdd(&cursor[C[i]], 1ull);
+    cverts[(int64_t)p] = (int32_t)i;
   }
 }
 __global__ void k_member_deg(int64_t n, const int32_t *cverts, const int32_t *deg, int32_t *mdeg) {
@@ -389,7 +388,7 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
   k_member_count<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0);
   exclusive_scan_i32_to_i64(h->ibuf0, h->coff, ncomm, h->scan_tmp, s);
   cudaMemcpyAsync(h->lbuf0, h->coff, (size_t)ncomm * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-  k_member_fill<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->coff, (unsigned long long *)h->lbuf0, h->cverts);
+  k_member_fill<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, (unsigned long long *)h->lbuf0, h->cverts);
   // flat arc offsets of the members, and the super-row offsets
   k_member_deg<<<grid_for(n, TB), TB, 0, s>>>(n, h->cverts, g.deg, h->ibuf1);
   exclusive_scan_i32_to_i64(h->ibuf1, h->cflat, n, h->scan_tmp, s);

@@ -21,6 +21,7 @@ __device__ __forceinline__ int64_t warp_incl_scan(int64_t v) {
 // thread's exclusive prefix and the block total in *total.
 __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *total) {
   __shared__ int64_t wsum[SCAN_BLOCK / 32];
+  __shared__ int64_t wtotal;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int64_t incl = warp_incl_scan(v);
   if (lane == 31) wsum[wid] = incl;
@@ -30,11 +31,11 @@ __device__ __forceinline__ int64_t block_excl_scan(int64_t v, int64_t *total) {
     int64_t x = lane < nw ? wsum[lane] : 0;
     int64_t xs = warp_incl_scan(x);
     if (lane < nw) wsum[lane] = xs - x;
-    if (lane == nw - 1) wsum[31] = xs;  // total (nw <= 32)
+    if (lane == 31) wtotal = xs;  // lanes >= nw add 0, so lane 31 holds the total
   }
   __syncthreads();
   int64_t res = incl - v + wsum[wid];
-  *total = wsum[31];
+  *total = wtotal;
   __syncthreads();
   return res;
 }

@@ -21,6 +21,8 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#include <pthread.h>
+#include <unistd.h>
 
 #define GOLDEN 0x9E3779B97F4A7C15ULL
 
@@ -42,61 +44,143 @@ static inline uint64_t rng_below(uint64_t seed, uint64_t stream, uint64_t ctr, u
   return (uint64_t)(p >> 64);
 }
 
-/* ---------------------------------------------------------------- sorting */
+/* ---------------------------------------------------------------- CSR build */
 
-/* LSD radix sort of 64-bit keys on their low `bits` bits (8-bit digits). */
-static void radix_sort_u64(uint64_t *a, int64_t n, int bits) {
-  if (n <= 1) return;
-  uint64_t *tmp = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
-  uint64_t *src = a, *dst = tmp;
-  for (int shift = 0; shift < bits; shift += 8) {
-    int64_t count[257];
-    memset(count, 0, sizeof(count));
-    for (int64_t i = 0; i < n; i++) count[((src[i] >> shift) & 255) + 1]++;
-    for (int d = 0; d < 256; d++) count[d + 1] += count[d];
-    for (int64_t i = 0; i < n; i++) dst[count[(src[i] >> shift) & 255]++] = src[i];
-    uint64_t *t = src; src = dst; dst = t;
+static int cmp_i32(const void *a, const void *b) {
+  int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+  return x < y ? -1 : x > y;
+}
+
+static void sort_row(int32_t *r, int64_t len) {
+  if (len > 48) { qsort(r, (size_t)len, sizeof(int32_t), cmp_i32); return; }
+  for (int64_t i = 1; i < len; i++) { /* insertion sort for short rows */
+    int32_t x = r[i];
+    int64_t j = i - 1;
+    while (j >= 0 && r[j] > x) { r[j + 1] = r[j]; j--; }
+    r[j + 1] = x;
   }
-  if (src != a) memcpy(a, src, (size_t)n * sizeof(uint64_t));
-  free(tmp);
 }
 
-static int bits_for(int64_t n) {
-  int b = 1;
-  while (((int64_t)1 << b) < n) b++;
-  return b;
+/* ------------------------------------------------------------ threading */
+
+static int n_threads(void) {
+  long c = sysconf(_SC_NPROCESSORS_ONLN);
+  const char *e = getenv("SYNTH_THREADS");
+  if (e && atoi(e) > 0) c = atoi(e);
+  if (c < 1) c = 1;
+  if (c > 64) c = 64;
+  return (int)c;
 }
 
-/* Turn a list of undirected pairs (u, v), u != v, into a symmetric CSR with
- * unit weights.  Keys are (src << 32 | dst); duplicates collapse. */
+typedef struct {
+  int tid, nt;
+  void *ctx;
+  void (*fn)(void *ctx, int tid, int nt);
+} job_t;
+
+static void *job_main(void *p) {
+  job_t *j = (job_t *)p;
+  j->fn(j->ctx, j->tid, j->nt);
+  return NULL;
+}
+
+/* Run fn(ctx, tid, nt) on nt threads; each thread takes a fixed share. */
+static void parallel_run(void (*fn)(void *, int, int), void *ctx) {
+  int nt = n_threads();
+  pthread_t th[64];
+  job_t jobs[64];
+  for (int t = 0; t < nt; t++) {
+    jobs[t] = (job_t){t, nt, ctx, fn};
+    if (t > 0) pthread_create(&th[t], NULL, job_main, &jobs[t]);
+  }
+  job_main(&jobs[0]);
+  for (int t = 1; t < nt; t++) pthread_join(th[t], NULL);
+}
+
+static inline void span(int64_t n, int tid, int nt, int64_t *lo, int64_t *hi) {
+  *lo = n * tid / nt;
+  *hi = n * (tid + 1) / nt;
+}
+
+/* Turn a list of undirected pairs (u, v) into a symmetric CSR with unit
+ * weights: counting sort of both directions by source, then each row is
+ * sorted; self-pairs are dropped and repeated pairs collapse.  The scatter
+ * order inside a row depends on thread timing, the sorted rows do not. */
+typedef struct {
+  int64_t n, m;
+  const int64_t *u, *v;
+  int64_t *pos, *cur, *uniq;
+  int32_t *tmp, *col;
+  const int64_t *off;
+  int phase;
+} csr_ctx;
+
+static void csr_work(void *p, int tid, int nt) {
+  csr_ctx *c = (csr_ctx *)p;
+  int64_t lo, hi;
+  if (c->phase == 0) { /* degrees */
+    span(c->m, tid, nt, &lo, &hi);
+    for (int64_t e = lo; e < hi; e++) {
+      if (c->u[e] == c->v[e]) continue;
+      __atomic_fetch_add(&c->pos[c->u[e] + 1], 1, __ATOMIC_RELAXED);
+      __atomic_fetch_add(&c->pos[c->v[e] + 1], 1, __ATOMIC_RELAXED);
+    }
+  } else if (c->phase == 1) { /* scatter */
+    span(c->m, tid, nt, &lo, &hi);
+    for (int64_t e = lo; e < hi; e++) {
+      if (c->u[e] == c->v[e]) continue;
+      c->tmp[__atomic_fetch_add(&c->cur[c->u[e]], 1, __ATOMIC_RELAXED)] = (int32_t)c->v[e];
+      c->tmp[__atomic_fetch_add(&c->cur[c->v[e]], 1, __ATOMIC_RELAXED)] = (int32_t)c->u[e];
+    }
+  } else if (c->phase == 2) { /* sort and deduplicate each row in place */
+    span(c->n, tid, nt, &lo, &hi);
+    for (int64_t i = lo; i < hi; i++) {
+      int32_t *r = c->tmp + c->pos[i];
+      int64_t len = c->pos[i + 1] - c->pos[i], k = 0;
+      sort_row(r, len);
+      for (int64_t t = 0; t < len; t++)
+        if (t == 0 || r[t] != r[t - 1]) r[k++] = r[t];
+      c->uniq[i] = k;
+    }
+  } else { /* copy rows to their compact place */
+    span(c->n, tid, nt, &lo, &hi);
+    for (int64_t i = lo; i < hi; i++)
+      memcpy(c->col + c->off[i], c->tmp + c->pos[i], (size_t)c->uniq[i] * sizeof(int32_t));
+  }
+}
+
 static int build_csr_from_pairs(int64_t n, const int64_t *u, const int64_t *v, int64_t m,
                                 int64_t **off_out, int32_t **col_out, int32_t **w_out,
                                 int64_t *arcs_out) {
-  uint64_t *keys = (uint64_t *)malloc((size_t)(2 * m + 1) * sizeof(uint64_t));
-  if (!keys) return -1;
-  int64_t k = 0;
-  for (int64_t e = 0; e < m; e++) {
-    if (u[e] == v[e]) continue;
-    keys[k++] = ((uint64_t)u[e] << 32) | (uint64_t)v[e];
-    keys[k++] = ((uint64_t)v[e] << 32) | (uint64_t)u[e];
-  }
-  int vb = bits_for(n);
-  radix_sort_u64(keys, k, 32 + vb);
-  int64_t uniq = 0;
-  for (int64_t i = 0; i < k; i++)
-    if (i == 0 || keys[i] != keys[i - 1]) keys[uniq++] = keys[i];
+  csr_ctx c;
+  memset(&c, 0, sizeof(c));
+  c.n = n; c.m = m; c.u = u; c.v = v;
+  c.pos = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+  c.cur = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+  c.uniq = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
   int64_t *off = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
-  int32_t *col = (int32_t *)malloc((size_t)(uniq + 1) * sizeof(int32_t));
-  int32_t *w = (int32_t *)malloc((size_t)(uniq + 1) * sizeof(int32_t));
-  if (!off || !col || !w) { free(keys); free(off); free(col); free(w); return -1; }
-  for (int64_t i = 0; i < uniq; i++) {
-    off[(keys[i] >> 32) + 1]++;
-    col[i] = (int32_t)(keys[i] & 0xffffffffULL);
-    w[i] = 1;
-  }
-  for (int64_t i = 0; i < n; i++) off[i + 1] += off[i];
-  free(keys);
-  *off_out = off; *col_out = col; *w_out = w; *arcs_out = uniq;
+  if (!c.pos || !c.cur || !c.uniq || !off) { free(c.pos); free(c.cur); free(c.uniq); free(off); return -1; }
+  c.phase = 0;
+  parallel_run(csr_work, &c);
+  for (int64_t i = 0; i < n; i++) c.pos[i + 1] += c.pos[i];
+  c.tmp = (int32_t *)malloc((size_t)(c.pos[n] + 1) * sizeof(int32_t));
+  if (!c.tmp) { free(c.pos); free(c.cur); free(c.uniq); free(off); return -1; }
+  memcpy(c.cur, c.pos, (size_t)(n + 1) * sizeof(int64_t));
+  c.phase = 1;
+  parallel_run(csr_work, &c);
+  c.phase = 2;
+  parallel_run(csr_work, &c);
+  for (int64_t i = 0; i < n; i++) off[i + 1] = off[i] + c.uniq[i];
+  int64_t k = off[n];
+  c.col = (int32_t *)malloc((size_t)(k + 1) * sizeof(int32_t));
+  int32_t *w = (int32_t *)malloc((size_t)(k + 1) * sizeof(int32_t));
+  if (!c.col || !w) { free(c.pos); free(c.cur); free(c.uniq); free(off); free(c.tmp); free(c.col); free(w); return -1; }
+  c.off = off;
+  c.phase = 3;
+  parallel_run(csr_work, &c);
+  for (int64_t a = 0; a < k; a++) w[a] = 1;
+  free(c.pos); free(c.cur); free(c.uniq); free(c.tmp);
+  *off_out = off; *col_out = c.col; *w_out = w; *arcs_out = k;
   return 0;
 }
 
@@ -170,6 +254,38 @@ int synth_planted_partition(int64_t n, int64_t blocks, double avg_deg, double mu
 
 /* ------------------------------------------------------------------ R-MAT */
 
+typedef struct {
+  int scale;
+  int64_t m;
+  uint64_t seed;
+  uint32_t ta, tb, tc;
+  const int64_t *perm;
+  int64_t *u, *v;
+} rmat_ctx;
+
+/* Edges [lo, hi) of the R-MAT sample: edge e descends `scale` levels using
+ * 16 bits per level of the draws (seed, 8, 8e + l/4). */
+static void rmat_work(void *p, int tid, int nt) {
+  rmat_ctx *c = (rmat_ctx *)p;
+  int64_t lo, hi;
+  span(c->m, tid, nt, &lo, &hi);
+  for (int64_t e = lo; e < hi; e++) {
+    int64_t x = 0, y = 0;
+    uint64_t r = 0;
+    for (int l = 0; l < c->scale; l++) {
+      if ((l & 3) == 0) r = rng_u64(c->seed, 8, (uint64_t)e * 8 + (uint64_t)(l >> 2));
+      uint32_t q = (uint32_t)(r & 0xffff);
+      r >>= 16;
+      int bx = 0, by = 0;
+      if (q < c->ta) { } else if (q < c->tb) { by = 1; } else if (q < c->tc) { bx = 1; } else { bx = 1; by = 1; }
+      x = (x << 1) | bx;
+      y = (y << 1) | by;
+    }
+    c->u[e] = c->perm[x];
+    c->v[e] = c->perm[y];
+  }
+}
+
 /* R-MAT (Chakrabarti, Zhan, Faloutsos 2004): 2^scale vertices and
  * edge_factor * 2^scale sampled edges; each edge descends `scale` levels of
  * the adjacency quadrants with probabilities (a, b, c, 1-a-b-c).  Vertex IDs
@@ -193,21 +309,8 @@ int synth_rmat(int scale, int64_t edge_factor, double a, double b, double c, uin
     int64_t j = (int64_t)rng_below(seed, 7, (uint64_t)i, (uint64_t)(i + 1));
     int64_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
   }
-  for (int64_t e = 0; e < m; e++) {
-    int64_t x = 0, y = 0;
-    uint64_t r = 0;
-    for (int l = 0; l < scale; l++) {
-      if ((l & 3) == 0) r = rng_u64(seed, 8, (uint64_t)e * 8 + (uint64_t)(l >> 2));
-      uint32_t q = (uint32_t)(r & 0xffff);
-      r >>= 16;
-      int bx = 0, by = 0;
-      if (q < ta) { } else if (q < tb) { by = 1; } else if (q < tc) { bx = 1; } else { bx = 1; by = 1; }
-      x = (x << 1) | bx;
-      y = (y << 1) | by;
-    }
-    u[e] = perm[x];
-    v[e] = perm[y];
-  }
+  rmat_ctx rc0 = {scale, m, seed, ta, tb, tc, perm, u, v};
+  parallel_run(rmat_work, &rc0);
   free(perm);
   int rc = build_csr_from_pairs(n, u, v, m, off, col, w, arcs);
   free(u); free(v);
