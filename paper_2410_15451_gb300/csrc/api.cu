@@ -140,7 +140,9 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     refine_reset(h, g);
     int rounds = 0;
     int refined_any = 0;
-    int max_rounds = p.deterministic ? p.max_iterations : 1;
+    // Both modes repeat rounds until no move applies: in the in-place mode a
+    // singleton whose target was taken retries against the updated state.
+    int max_rounds = p.max_iterations;
     for (int r = 0; r < max_rounds; r++) {
       refine_round(h, g, r & 1);
       rounds++;
