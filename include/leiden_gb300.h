@@ -134,6 +134,32 @@ leiden_status leiden_update_device(leiden_handle *h, const leiden_edge *del, int
  * integers (2m * sum sigma_c - sum Sigma_c^2) and divided once by (2m)^2. */
 leiden_status leiden_modularity(leiden_handle *h, const int32_t *membership, double *q_out);
 
+/* Modularity Q (Eq. 1, same exact-integer arithmetic and final division as
+ * leiden_modularity) of the membership d_membership (device int32[n], ids in
+ * [0, n)) on a caller-owned device CSR: d_offsets int64[n+1], d_cols
+ * int32[d_offsets[n]], d_weights int32 or NULL for unit weights.  Work runs
+ * on cuda_stream (NULL = legacy default stream); the call returns when *q_out
+ * is written.
+ *
+ * The paper has no counterpart to this function.  It exists for callers that
+ * may not allocate device memory: a serving loop that reserved all device
+ * memory up front, code whose device memory belongs to another allocator
+ * (e.g. a framework's caching pool), or a latency-critical path where the
+ * implicit synchronisation of cudaMalloc/cudaFree is not acceptable.  It
+ * allocates nothing: no cudaMalloc, cudaFree or allocating library routine.
+ * Its scratch is one fixed array in the library's device memory, 32 MiB,
+ * which every GPU that loads the library holds until the process exits; so n
+ * may be at most 4,194,304 (larger n returns LEIDEN_ERR_ARG).  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * All calls share the one array: calls whose GPU work overlaps (other
+ * streams, other host threads) race and give wrong results; serialise them.
+ * Errors: LEIDEN_ERR_ARG (null pointer, n out of range, membership id out of
+ * range), LEIDEN_ERR_CUDA; the message is in leiden_last_error(NULL). */
+leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *d_offsets, const int32_t *d_cols,
+                                        const int32_t *d_weights, const int32_t *d_membership,
+                                        void *cuda_stream, double *q_out);
+
 /* Device pointer to the handle's current membership C^t (int32[n]); valid
  * until the next call on the handle. */
 leiden_status leiden_membership_device(leiden_handle *h, const int32_t **d_membership);

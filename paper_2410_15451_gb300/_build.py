@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libleiden_gb300.so")
-SOURCES = ["prims.cu", "batch.cu", "move.cu", "phases.cu", "track.cu", "api.cu"]
+SOURCES = ["prims.cu", "batch.cu", "move.cu", "phases.cu", "track.cu", "api.cu", "noalloc.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off"]

@@ -270,6 +270,8 @@ leiden_status check_handle(leiden_handle *h) {
 
 }  // namespace
 
+void set_handle_free_error(const std::string &msg) { g_create_error = msg; }
+
 extern "C" {
 
 void leiden_default_params(leiden_params *p) {

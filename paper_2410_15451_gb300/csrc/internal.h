@@ -124,6 +124,9 @@ struct leiden_handle {
   std::vector<void *> owned;  // every cudaMalloc of the handle
 };
 
+// Message returned by leiden_last_error(NULL) (calls without a handle).
+void set_handle_free_error(const std::string &msg);
+
 // ------------------------------------------------------------ prims.cu
 // Exclusive scan of n values; out[n] receives the total.  `tmp` must hold
 // scan_tmp_bytes(n) bytes.  in == out is allowed.

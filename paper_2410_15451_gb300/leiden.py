@@ -67,6 +67,8 @@ def load():
     lib.leiden_update_device.argtypes = [vp, vp, i64, vp, i64, ctypes.c_int, vp]
     lib.leiden_modularity.argtypes = [vp, vp, P(ctypes.c_double)]
     lib.leiden_membership_device.argtypes = [vp, P(vp)]
+    lib.leiden_modularity_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, P(ctypes.c_double)]
+    lib.leiden_modularity_noalloc.restype = ctypes.c_int
     lib.leiden_get_state.argtypes = [vp, vp, vp, vp, vp, P(i64)]
     lib.leiden_graph_arcs.argtypes = [vp]
     lib.leiden_graph_arcs.restype = i64
@@ -141,6 +143,15 @@ def leiden_modularity(h, membership=None) -> float:
     q = ctypes.c_double()
     m = None if membership is None else np.ascontiguousarray(membership, np.int32)
     _check(h, load().leiden_modularity(h, _ptr(m), ctypes.byref(q)))
+    return q.value
+
+
+def leiden_modularity_noalloc(n, d_offsets, d_cols, d_weights, d_membership, cuda_stream=None) -> float:
+    """Modularity on a caller-owned device CSR without any device allocation
+    (for callers that may not allocate; see the C header for the limits)."""
+    q = ctypes.c_double()
+    _check(None, load().leiden_modularity_noalloc(int(n), _ptr(d_offsets), _ptr(d_cols), _ptr(d_weights),
+                                                  _ptr(d_membership), cuda_stream, ctypes.byref(q)))
     return q.value
 
 
