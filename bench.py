@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--async-mode", action="store_true", help="in-place moves instead of the snapshot schedule")
+    ap.add_argument("--profile", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
 
 
@@ -220,6 +222,8 @@ def run_ours(args, rank, world, local_rank):
     clocks = ClockSampler(local_rank)
     clocks.start()
     times_ms, lm_stats = [], []
+    if args.profile:
+        torch.cuda.cudart().cudaProfilerStart()
     for k in range(W, W + K):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -231,6 +235,8 @@ def run_ours(args, rank, world, local_rank):
         times_ms.append(e0.elapsed_time(e1))
         lm_stats.append(gpu.stats())
     torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.cudart().cudaProfilerStop()
     clk = clocks.stop()
     total_s = sum(times_ms) / 1e3
     if world > 1:
