@@ -179,17 +179,89 @@ __global__ void k_merge_rows(const int32_t *rows, const int64_t *nrows_p, int vb
   }
 }
 
-__global__ void k_copy_back(const int32_t *rows, const int64_t *nrows_p, const int64_t *tmp_off, const int64_t *len,
-                            const int64_t *off, int32_t *deg, int32_t *col, int32_t *w, const int32_t *tcol,
-                            const int32_t *tw) {
-  int64_t nrows = *nrows_p;
-  int lane = threadIdx.x & 31;
-  int64_t warp = ld_gtid() >> 5, nwarps = ld_gstride() >> 5;
-  for (int64_t r = warp; r < nrows; r += nwarps) {
-    int32_t u = rows[r];
-    int64_t L = len[r], b = tmp_off[r], o = off[u];
-    for (int64_t x = lane; x < L; x += 32) { col[o + x] = tcol[b + x]; w[o + x] = tw[b + x]; }
-    if (lane == 0) deg[u] = (int32_t)L;
+// In-place merge of the touched rows that fit their capacity (no overflow).
+// Output position of an old element x at p: p - |D < x| + |I < x|; of the
+// k-th new arc y: k + |row < y| - |D < y|.  Rows of at most MERGE_SMALL
+// arcs are merged by one warp through shared memory, longer rows by one
+// block through the global merge buffer; each writes back after all its
+// reads are done, so the old row is never overwritten while still read.
+constexpr int MERGE_SMALL = 1024;
+constexpr int MERGE_WARPS = 4;
+
+struct MergeArgs {
+  const int32_t *rows;
+  const int64_t *nrows_p;
+  int vb;
+  const uint64_t *dkey, *nkey;
+  const int64_t *nw;
+  const int32_t *dlo, *dhi, *ilo, *ihi;
+  const int64_t *len, *tmp_off, *off;
+  int32_t *deg, *col, *w, *tcol, *tw;
+};
+
+__device__ __forceinline__ void merge_row_into(const MergeArgs &A, int64_t r, int t0, int stride, int32_t *ocol,
+                                               int32_t *ow) {
+  uint64_t mask = (1ull << A.vb) - 1;
+  int32_t u = A.rows[r];
+  const int32_t *row = A.col + A.off[u];
+  const int32_t *roww = A.w + A.off[u];
+  int64_t dg = A.deg[u];
+  const uint64_t *D = A.dkey + A.dlo[r];
+  int64_t nD = A.dhi[r] - A.dlo[r];
+  const uint64_t *I = A.nkey + A.ilo[r];
+  const int64_t *IW = A.nw + A.ilo[r];
+  int64_t nI = A.ihi[r] - A.ilo[r];
+  uint64_t ubase = (uint64_t)u << A.vb;
+  for (int64_t p = t0; p < dg; p += stride) {
+    int32_t x = row[p];
+    int64_t dless = nD ? lower_bound_u64(D, nD, ubase | (uint64_t)x) : 0;
+    if (dless < nD && (D[dless] & mask) == (uint64_t)x) continue;
+    int64_t iless = nI ? lower_bound_u64(I, nI, ubase | (uint64_t)x) : 0;
+    int64_t o = (p - dless) + iless;
+    ocol[o] = x;
+    ow[o] = roww[p];
+  }
+  for (int64_t k = t0; k < nI; k += stride) {
+    int32_t y = (int32_t)(I[k] & mask);
+    int64_t rless = lower_bound_i32(row, dg, y);
+    int64_t dless = nD ? lower_bound_u64(D, nD, ubase | (uint64_t)y) : 0;
+    int64_t o = k + (rless - dless);
+    ocol[o] = y;
+    ow[o] = (int32_t)IW[k];
+  }
+}
+
+__global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge_small(MergeArgs A) {
+  __shared__ int32_t scol[MERGE_WARPS][MERGE_SMALL];
+  __shared__ int32_t sw[MERGE_WARPS][MERGE_SMALL];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t nrows = *A.nrows_p;
+  for (int64_t r = (int64_t)blockIdx.x * MERGE_WARPS + wid; r < nrows; r += (int64_t)gridDim.x * MERGE_WARPS) {
+    int64_t L = A.len[r];
+    if (L > MERGE_SMALL) continue;
+    merge_row_into(A, r, lane, 32, scol[wid], sw[wid]);
+    __syncwarp();
+    int32_t u = A.rows[r];
+    int64_t o = A.off[u];
+    for (int64_t x = lane; x < L; x += 32) { A.col[o + x] = scol[wid][x]; A.w[o + x] = sw[wid][x]; }
+    if (lane == 0) A.deg[u] = (int32_t)L;
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(512) k_merge_large(MergeArgs A) {
+  int64_t nrows = *A.nrows_p;
+  for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+    int64_t L = A.len[r];
+    if (L <= MERGE_SMALL) continue;
+    int64_t b = A.tmp_off[r];
+    merge_row_into(A, r, threadIdx.x, blockDim.x, A.tcol + b, A.tw + b);
+    __syncthreads();
+    int32_t u = A.rows[r];
+    int64_t o = A.off[u];
+    for (int64_t x = threadIdx.x; x < L; x += blockDim.x) { A.col[o + x] = A.tcol[b + x]; A.w[o + x] = A.tw[b + x]; }
+    if (threadIdx.x == 0) A.deg[u] = (int32_t)L;
+    __syncthreads();
   }
 }
 
@@ -576,13 +648,16 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   // ---- apply: from here on the handle changes
   if (ni > 0) k_add_existing<<<grid_for(ni, TB), TB, 0, s>>>(b.ins_pos, b.ins_state, IW, ni, h->g_w);
   if (nrows > 0) {
-    k_merge_rows<<<grid_for(nrows * 32, TB), TB, 0, s>>>(b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo, b.row_dhi,
-                                                         b.row_ilo, b.row_ihi, b.row_tmp_off, h->g_off, h->g_deg,
-                                                         h->g_col, h->g_w, b.tmp_col, b.tmp_w);
     if (!overflow) {
-      k_copy_back<<<grid_for(nrows * 32, TB), TB, 0, s>>>(b.rows, counts + 3, b.row_tmp_off, b.row_len, h->g_off,
-                                                          h->g_deg, h->g_col, h->g_w, b.tmp_col, b.tmp_w);
+      MergeArgs M{b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo, b.row_dhi, b.row_ilo, b.row_ihi, b.row_len,
+                  b.row_tmp_off, h->g_off, h->g_deg, h->g_col, h->g_w, b.tmp_col, b.tmp_w};
+      k_merge_small<<<grid_for((nrows + MERGE_WARPS - 1) / MERGE_WARPS, 1, h->sm_count * 16), MERGE_WARPS * 32, 0,
+                      s>>>(M);
+      k_merge_large<<<h->sm_count * 2, 512, 0, s>>>(M);
     } else {
+      k_merge_rows<<<grid_for(nrows * 32, TB), TB, 0, s>>>(b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo,
+                                                           b.row_dhi, b.row_ilo, b.row_ihi, b.row_tmp_off, h->g_off,
+                                                           h->g_deg, h->g_col, h->g_w, b.tmp_col, b.tmp_w);
       leiden_status st = rebuild_graph(h, nrows, counts + 3);
       if (st != LEIDEN_OK) return st;
     }

@@ -110,6 +110,32 @@ __device__ __forceinline__ int64_t ld_warp_sum_i64(int64_t v) {
   return v;
 }
 
+// Reductions over the lanes that share a key (peers = __match_any_sync of
+// the key).  Every lane of the warp must call them (full-mask shuffles);
+// each lane receives its group's result.
+__device__ __forceinline__ int64_t ld_group_sum_i64(uint32_t peers, int64_t v) {
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < 32; k++) {
+    int64_t x = __shfl_sync(LD_FULL, v, k);
+    if ((peers >> k) & 1u) s += x;
+  }
+  return s;
+}
+__device__ __forceinline__ int32_t ld_group_min_i32(uint32_t peers, int32_t v) {
+  int32_t s = 0x7fffffff;
+#pragma unroll
+  for (int k = 0; k < 32; k++) {
+    int32_t x = __shfl_sync(LD_FULL, v, k);
+    if (((peers >> k) & 1u) && x < s) s = x;
+  }
+  return s;
+}
+// True in the lowest lane of the group.
+__device__ __forceinline__ bool ld_group_leader(uint32_t peers) {
+  return (__ffs(peers) - 1) == (int)(threadIdx.x & 31);
+}
+
 // ---------------------------------------------------------------- bitmaps
 __device__ __forceinline__ bool ld_bit_test(const uint32_t *bm, int64_t i) {
   return (bm[i >> 5] >> (i & 31)) & 1u;

@@ -354,8 +354,16 @@ __global__ void k_apply_moves(const int32_t *movers, const int32_t *target, cons
   }
 }
 
+// Community sizes; lanes with the same community add once (giant
+// communities would otherwise serialise on one counter).
 __global__ void k_sizes(const int32_t *C, int64_t n, int32_t *size) {
-  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) atomicAdd(&size[C[i]], 1);
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
+    int64_t i = base + lane;
+    int32_t c = i < n ? C[i] : -1 - lane;
+    uint32_t peers = __match_any_sync(LD_FULL, c);
+    if (i < n && ld_group_leader(peers)) atomicAdd(&size[c], __popc(peers));
+  }
 }
 
 // ---- refinement

@@ -16,7 +16,14 @@ __global__ void k_sr_init(int64_t n, int32_t *rep, int64_t *S2, uint8_t *dS2, ui
   for (int64_t c = ld_gtid(); c < n; c += ld_gstride()) { rep[c] = INT_MAX; S2[c] = 0; dS2[c] = 0; dR2[c] = 0; }
 }
 __global__ void k_sr_min(int64_t n, const int32_t *C, int32_t *rep) {
-  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) atomicMin(&rep[C[i]], (int32_t)i);
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
+    int64_t i = base + lane;
+    int32_t c = i < n ? C[i] : -1 - lane;
+    uint32_t peers = __match_any_sync(LD_FULL, c);
+    int32_t mn = ld_group_min_i32(peers, (int32_t)i);
+    if (i < n && ld_group_leader(peers)) atomicMin(&rep[c], mn);
+  }
 }
 __global__ void k_sr_rekey(int64_t n, const int32_t *rep, const int64_t *S, const uint8_t *dS, const uint8_t *dR,
                            int64_t *S2, uint8_t *dS2, uint8_t *dR2) {
@@ -74,18 +81,54 @@ __device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b) 
   }
 }
 
-__global__ void k_split_hook(const int32_t *list, const DevCounters *cnt, const int64_t *off, const int32_t *deg,
-                             const int32_t *col, const int32_t *C, int32_t *parent) {
+// Sampling round (Afforest, Sutton et al. 2018): link each listed vertex to
+// its first SPLIT_SAMPLES neighbours in the same community.
+constexpr int SPLIT_SAMPLES = 2;
+__global__ void k_split_sample(const int32_t *list, const DevCounters *cnt, const int64_t *off, const int32_t *deg,
+                               const int32_t *col, const int32_t *C, int32_t *parent) {
+  int64_t m = cnt->split_count;
+  for (int64_t t = ld_gtid(); t < m; t += ld_gstride()) {
+    int32_t i = list[t];
+    int32_t c = C[i];
+    int64_t b = off[i], d = deg[i];
+    int got = 0;
+    for (int64_t a = 0; a < d && got < SPLIT_SAMPLES; a++) {
+      int32_t j = col[b + a];
+      if (j == i || C[j] != c) continue;
+      uf_unite(parent, i, j);
+      got++;
+    }
+  }
+}
+
+__global__ void k_split_flatten(const int32_t *list, const DevCounters *cnt, int32_t *parent) {
+  int64_t m = cnt->split_count;
+  for (int64_t t = ld_gtid(); t < m; t += ld_gstride()) {
+    int32_t i = list[t];
+    parent[i] = uf_find(parent, i);
+  }
+}
+
+// Warp per listed vertex.  The community id C[i] is its smallest member,
+// which is always the root of its own component; a vertex already joined to
+// it skips its arcs, every other vertex links along all of its arcs.  An edge
+// with an endpoint outside that component is therefore always processed
+// from that endpoint, so the final components are exact.
+__global__ void k_split_link_rest(const int32_t *list, const DevCounters *cnt, const int64_t *off,
+                                  const int32_t *deg, const int32_t *col, const int32_t *C, int32_t *parent) {
   int lane = threadIdx.x & 31;
   int64_t m = cnt->split_count;
   int64_t warp = ld_gtid() >> 5, nw = ld_gstride() >> 5;
   for (int64_t t = warp; t < m; t += nw) {
     int32_t i = list[t];
     int32_t c = C[i];
+    int32_t root = 0;
+    if (lane == 0) root = uf_find(parent, i);
+    if (__shfl_sync(LD_FULL, root, 0) == c) continue;
     int64_t b = off[i], d = deg[i];
     for (int64_t a = lane; a < d; a += 32) {
       int32_t j = col[b + a];
-      if (j != i && C[j] == c && j < i) uf_unite(parent, i, j);
+      if (j != i && C[j] == c) uf_unite(parent, i, j);
     }
   }
 }
@@ -108,16 +151,27 @@ __global__ void k_rank(int64_t n, const int64_t *rank, int32_t *C) {
 __global__ void k_lookup(int64_t N, const int32_t *Cp, int32_t *Ctop) {
   for (int64_t v = ld_gtid(); v < N; v += ld_gstride()) Ctop[v] = Cp[Ctop[v]];
 }
-__global__ void k_count_distinct(int64_t n, const int32_t *C, int32_t *seen, DevCounters *cnt) {
+// After refinement every community id is one of its members and that
+// member keeps its own id (subset renumbering gives the smallest member,
+// splitting the smallest vertex of a component, refinement a stationary
+// representative), so the communities are the vertices with C[i] == i.
+__global__ void k_count_roots(int64_t n, const int32_t *C, DevCounters *cnt) {
   int32_t local = 0;
-  for (int64_t i = ld_gtid(); i < n; i += ld_gstride())
-    if (atomicExch(&seen[C[i]], 1) == 0) local++;
-  if (local) atomicAdd(&cnt->list_count, local);
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) local += C[i] == (int32_t)i;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(LD_FULL, local, o);
+  if ((threadIdx.x & 31) == 0 && local) atomicAdd(&cnt->list_count, local);
 }
 
 // ---------------------------------------------------------------- Alg. leidenag
 __global__ void k_member_count(int64_t n, const int32_t *C, int32_t *cnt_c) {
-  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) atomicAdd(&cnt_c[C[i]], 1);
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
+    int64_t i = base + lane;
+    int32_t c = i < n ? C[i] : -1 - lane;
+    uint32_t peers = __match_any_sync(LD_FULL, c);
+    if (i < n && ld_group_leader(peers)) atomicAdd(&cnt_c[c], __popc(peers));
+  }
 }
 // cursor[c] starts at coff[c]; each member takes the next slot of its community.
 __global__ void k_member_fill(int64_t n, const int32_t *C, unsigned long long *cursor, int32_t *cverts) {
@@ -355,15 +409,16 @@ void split_communities(leiden_handle *h, const LevelGraph &g) {
   cudaMemsetAsync(&h->dcnt->split_count, 0, sizeof(int32_t), s);
   int32_t *list = h->ibuf1;
   k_split_init<<<grid_for(g.n, TB), TB, 0, s>>>(g.n, h->Cp, h->dS, h->dR, h->parent, list, h->dcnt);
-  k_split_hook<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
-  k_split_compress<<<h->sm_count * 4, TB, 0, s>>>(list, h->dcnt, h->parent, h->Cp);
+  k_split_sample<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
+  k_split_flatten<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent);
+  k_split_link_rest<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
+  k_split_compress<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent, h->Cp);
 }
 
 void count_communities(leiden_handle *h, int64_t n) {
   cudaStream_t s = h->stream;
-  cudaMemsetAsync(h->ibuf0, 0, (size_t)n * sizeof(int32_t), s);
   cudaMemsetAsync(&h->dcnt->list_count, 0, sizeof(int32_t), s);
-  k_count_distinct<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0, h->dcnt);
+  k_count_roots<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->dcnt);
 }
 
 void renumber_dense(leiden_handle *h, int64_t n) {

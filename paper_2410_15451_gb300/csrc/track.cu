@@ -18,13 +18,20 @@ __global__ void k_tr_clear(int64_t cap, uint64_t *keys, int64_t *vals) {
 __global__ void k_tr_insert(int64_t N, const int32_t *Cold, const int32_t *Cnew, const int64_t *K, int64_t cap,
                             uint64_t *keys, int64_t *vals) {
   uint64_t mask = (uint64_t)cap - 1;
-  for (int64_t i = ld_gtid(); i < N; i += ld_gstride()) {
-    uint64_t key = ((uint64_t)(uint32_t)Cold[i] << 32) | (uint32_t)Cnew[i];
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < N; base += ld_gstride()) {
+    int64_t i = base + lane;
+    uint64_t key = i < N ? (((uint64_t)(uint32_t)Cold[i] << 32) | (uint32_t)Cnew[i]) : EMPTY64 - 1 - lane;
+    int64_t kw = i < N ? K[i] : 0;
+    // lanes with the same (old, new) pair insert once with their summed weight
+    uint32_t peers = __match_any_sync(LD_FULL, (unsigned long long)key);
+    int64_t sum = ld_group_sum_i64(peers, kw);
+    if (i >= N || !ld_group_leader(peers)) continue;
     uint64_t s = hash64(key) & mask;
     while (true) {
       unsigned long long k = atomicCAS((unsigned long long *)&keys[s], EMPTY64, key);
       if (k == EMPTY64 || k == key) {
-        atomicAdd((unsigned long long *)&vals[s], (unsigned long long)K[i]);
+        atomicAdd((unsigned long long *)&vals[s], (unsigned long long)sum);
         break;
       }
       s = (s + 1) & mask;
@@ -82,10 +89,15 @@ __global__ void k_tr_map(int64_t N, const int32_t *new_used, const int32_t *ob, 
 }
 __global__ void k_tr_relabel(int64_t N, const int32_t *Cnew, const int32_t *map, const int64_t *K, int32_t *C,
                              int64_t *Sig) {
-  for (int64_t i = ld_gtid(); i < N; i += ld_gstride()) {
-    int32_t c = map[Cnew[i]];
-    C[i] = c;
-    atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)K[i]);
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < N; base += ld_gstride()) {
+    int64_t i = base + lane;
+    int32_t c = -1 - lane;
+    int64_t k = 0;
+    if (i < N) { c = map[Cnew[i]]; C[i] = c; k = K[i]; }
+    uint32_t peers = __match_any_sync(LD_FULL, c);
+    int64_t s = ld_group_sum_i64(peers, k);
+    if (i < N && ld_group_leader(peers) && s) atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)s);
   }
 }
 __global__ void k_tr_dsig(int64_t N, const uint8_t *matched, int64_t *dSig) {
@@ -95,8 +107,15 @@ __global__ void k_tr_dsig(int64_t N, const uint8_t *matched, int64_t *dSig) {
 
 // ---- modularity
 __global__ void k_sig_of(int64_t N, const int32_t *C, const int64_t *K, int64_t *Sig) {
-  for (int64_t i = ld_gtid(); i < N; i += ld_gstride())
-    atomicAdd((unsigned long long *)&Sig[C[i]], (unsigned long long)K[i]);
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < N; base += ld_gstride()) {
+    int64_t i = base + lane;
+    int32_t c = i < N ? C[i] : -1 - lane;
+    int64_t k = i < N ? K[i] : 0;
+    uint32_t peers = __match_any_sync(LD_FULL, c);
+    int64_t s = ld_group_sum_i64(peers, k);
+    if (i < N && ld_group_leader(peers) && s) atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)s);
+  }
 }
 __global__ void k_sigma_intra(int64_t N, const int64_t *off, const int32_t *deg, const int32_t *col, const int32_t *w,
                               const int32_t *C, DevCounters *cnt) {
