@@ -72,6 +72,7 @@ LevelGraph level0(leiden_handle *h) {
   g.w = h->g_w;
   g.w64 = false;
   g.maxdeg = h->g_maxdeg;
+  g.huge_slots = h->g_huge_slots;
   return g;
 }
 
@@ -194,6 +195,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     y.w = h->y_w[slot];
     y.w64 = true;
     y.maxdeg = h->hcnt->max_count;
+    y.huge_slots = h->hcnt->huge_slots;
     g = y;
     slot ^= 1;
     tau /= p.tau_drop;
@@ -248,6 +250,7 @@ leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_de
   level_maxdeg(h, h->g_deg, h->n);
   sync_counters(h);
   h->g_maxdeg = h->hcnt->max_count;
+  h->g_huge_slots = h->hcnt->huge_slots;
   st = run_leiden(h, 1, mode == LEIDEN_DS ? h->dV : nullptr);
   if (st != LEIDEN_OK) return st;
   if (h->p.collect_stats) {
@@ -432,6 +435,7 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   if (h->p.collect_stats) cudaEventRecord(h->ev[0], s);
   int64_t N = h->n;
   recompute_weights(h);
+  level_maxdeg(h, h->g_deg, N);
   launch_iota_i32(h->C, N, s);
   CK(cudaMemcpyAsync(h->Sig, h->K, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(h->dSig, 0, (size_t)N * sizeof(int64_t), s));
@@ -441,6 +445,8 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   sync_counters(h);
   CK(cudaGetLastError());
   h->m2 = h->hcnt->m2;
+  h->g_maxdeg = h->hcnt->max_count;
+  h->g_huge_slots = h->hcnt->huge_slots;
   mark(h, 1);
   st = run_leiden(h, 0, nullptr);
   if (st != LEIDEN_OK) return st;

@@ -37,7 +37,8 @@ struct DevCounters {
   int64_t sigma_intra;            // modularity: intra-community arc weight
   unsigned long long sq[2];       // modularity: sum of Sigma_c^2 (int128)
   int64_t batch_dw;               // batch: change of 2m
-  int64_t pad[3];
+  int64_t huge_slots;             // table slots the vertices above the block bin need
+  int64_t pad[2];
 };
 
 // ---------------------------------------------------------------- hashing

@@ -20,6 +20,7 @@ struct LevelGraph {
   const void *w = nullptr;  // int32 at level 0, int64 above
   bool w64 = false;
   int32_t maxdeg = 0;
+  int64_t huge_slots = 0;  // sum over vertices above BIN_BLOCK_MAX of pow2 >= 2*degree
 };
 
 // Degree bins of the vertex-centric kernels (local moving, refinement).
@@ -66,6 +67,7 @@ struct leiden_handle {
   int64_t g_cap = 0;
   int64_t g_arcs = 0;
   int32_t g_maxdeg = 0;
+  int64_t g_huge_slots = 0;
   int64_t m2 = 0;            // 2m = sum of arc weights
 
   // auxiliary state {C, K, Sigma, Delta Sigma}
@@ -156,6 +158,7 @@ void refine_reset(leiden_handle *h, const LevelGraph &g);
 void refine_round(leiden_handle *h, const LevelGraph &g, int slot);
 void lm_prepare(leiden_handle *h, const LevelGraph &g);  // community sizes
 bool ensure_hscratch(leiden_handle *h, int64_t maxdeg);  // false: allocation failed
+bool ensure_hscratch_bytes(leiden_handle *h, size_t bytes);
 
 // ------------------------------------------------------------ phases.cu
 void subset_renumber(leiden_handle *h, int64_t n);

@@ -155,19 +155,12 @@ __device__ __forceinline__ i128 decide_leader(const Args &A, int64_t i, const Be
     if (A.dynamic) A.dS[d] = 1;
     return g;
   } else {
+    // Refinement runs in proposal/accept rounds in both modes: an in-place
+    // CAS scheme (pin the target, then leave) never merges mutual best
+    // pairs, because both pin each other before either can leave, and such
+    // pairs are common since the gain of joining a singleton is symmetric.
     if (A.C[b.c] != b.c) return 0;  // the representative of c* left it
-    if (!A.async_mode) {
-      A.prop[i] = b.c;
-      return g;
-    }
-    // in place: pin the target (0 -> 1, or already 1), then leave (0 -> 2)
-    int32_t t = atomicCAS(&A.prop[b.c], 0, 1);
-    if (t == 2) return 0;
-    if (atomicCAS(&A.prop[i], 0, 2) != 0) return 0;
-    A.C[i] = b.c;
-    atomicAdd((unsigned long long *)&A.S[d], (unsigned long long)(-Ki));
-    atomicAdd((unsigned long long *)&A.S[b.c], (unsigned long long)Ki);
-    atomicAdd(&A.cnt->accepted, 1);
+    A.prop[i] = b.c;
     return g;
   }
 }
@@ -309,6 +302,105 @@ __global__ void __launch_bounds__(HUGE_THREADS) k_decide_huge(Args A) {
   if (threadIdx.x == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
 }
 
+// ---------------------------------------------------------------- bin 2, split across blocks
+// Vertices above BIN_BLOCK_MAX arcs: each gets its own table of
+// pow2 >= 2*degree slots in global scratch and its arcs are cut into chunks
+// of HUGE_CHUNK that any block may take, so one hub no longer runs on one SM.
+constexpr int HUGE_CHUNK = 4096;
+
+// One block: table and chunk offsets of the listed vertices (exclusive
+// prefix sums; totals at index count).
+__global__ void __launch_bounds__(1024) k_huge_plan(const int32_t *list, const int32_t *count_p, const int32_t *deg,
+                                                     int64_t *tab_off, int64_t *ch_off) {
+  __shared__ int64_t ws[32][2];
+  __shared__ int64_t carry[2];
+  int64_t count = *count_p;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) { carry[0] = 0; carry[1] = 0; }
+  __syncthreads();
+  for (int64_t base = 0; base < count; base += blockDim.x) {
+    int64_t k = base + threadIdx.x;
+    int64_t t = 0, c = 0;
+    if (k < count) {
+      int64_t d = deg[list[k]];
+      t = 1;
+      while (t < 2 * d) t <<= 1;
+      c = (d + HUGE_CHUNK - 1) / HUGE_CHUNK;
+    }
+    int64_t it = t, ic = c;  // inclusive warp scans
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t xt = __shfl_up_sync(LD_FULL, it, o), xc = __shfl_up_sync(LD_FULL, ic, o);
+      if (lane >= o) { it += xt; ic += xc; }
+    }
+    if (lane == 31) { ws[wid][0] = it; ws[wid][1] = ic; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t a = carry[0], b = carry[1];
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+        int64_t x = ws[w][0], y = ws[w][1];
+        ws[w][0] = a; ws[w][1] = b;
+        a += x; b += y;
+      }
+      carry[0] = a; carry[1] = b;
+    }
+    __syncthreads();
+    if (k < count) { tab_off[k] = ws[wid][0] + it - t; ch_off[k] = ws[wid][1] + ic - c; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { tab_off[count] = carry[0]; ch_off[count] = carry[1]; }
+}
+
+__global__ void k_huge_clear(const int32_t *count_p, const int64_t *tab_off, int32_t *keys, int64_t *vals) {
+  int64_t total = tab_off[*count_p];
+  for (int64_t s = ld_gtid(); s < total; s += ld_gstride()) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
+}
+
+template <typename W, int KIND>
+__global__ void __launch_bounds__(256) k_huge_scan(Args A, const int64_t *tab_off, const int64_t *ch_off) {
+  int64_t count = *A.count;
+  int64_t nch = ch_off[count];
+  for (int64_t t = blockIdx.x; t < nch; t += gridDim.x) {
+    int64_t lo = 0, hi = count - 1;  // vertex k with ch_off[k] <= t < ch_off[k+1]
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) >> 1;
+      if (ch_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    int64_t i = A.list[lo];
+    int64_t first = (t - ch_off[lo]) * HUGE_CHUNK;
+    int64_t dg = A.deg[i];
+    int64_t last = first + HUGE_CHUNK < dg ? first + HUGE_CHUNK : dg;
+    int64_t T = tab_off[lo + 1] - tab_off[lo];
+    scan_arcs<W, KIND>(A, i, A.off[i] + first, last - first, threadIdx.x, blockDim.x, A.gkeys + tab_off[lo],
+                       A.gvals + tab_off[lo], (int)(T - 1));
+  }
+}
+
+template <int KIND>
+__global__ void __launch_bounds__(1024) k_huge_decide(Args A, const int64_t *tab_off) {
+  __shared__ int moved_s;
+  int64_t count = *A.count;
+  int64_t visits = 0, arcs = 0, moves = 0;
+  i128 dq = 0;
+  for (int64_t k = blockIdx.x; k < count; k += gridDim.x) {
+    int64_t i = A.list[k];
+    int64_t base = A.off[i], dg = A.deg[i];
+    int64_t T = tab_off[k + 1] - tab_off[k];
+    Best b = slot_best(A.gkeys + tab_off[k], A.gvals + tab_off[k], (int)T, threadIdx.x, blockDim.x, A.C[i],
+                       A.cnt->m2, A.K[i], A.S);
+    b = block_best(b);
+    if (threadIdx.x == 0) {
+      i128 g = decide_leader<KIND>(A, i, b);
+      moved_s = g > 0;
+      visits++; arcs += dg; moves += g > 0; dq += g;
+    }
+    __syncthreads();
+    if (KIND == KIND_MOVE && moved_s) mark_neighbours(A, i, base, dg, threadIdx.x, blockDim.x);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
+}
+
 // ---------------------------------------------------------------- collection
 // Take the unprocessed vertices of class `cls` (clearing their bits) and
 // append the in-range ones to the degree bins.
@@ -389,7 +481,7 @@ __global__ void k_refine_reset(int64_t n, const int32_t *CB, const uint8_t *dR, 
 // by degree; reset their proposals.
 __global__ void k_refine_collect(const int32_t *cand_in, const int32_t *count_in, int32_t *cand_out,
                                  int32_t *count_out, int64_t n, const int32_t *C, const int64_t *S, const int64_t *K,
-                                 const int32_t *deg, int32_t *prop, int32_t *bins, DevCounters *cnt, int async_mode) {
+                                 const int32_t *deg, int32_t *prop, int32_t *bins, DevCounters *cnt, int unused) {
   int lane = threadIdx.x & 31;
   int64_t m = *count_in;
   for (int64_t base = (ld_gtid() & ~31ll); base < m; base += ld_gstride()) {
@@ -397,7 +489,7 @@ __global__ void k_refine_collect(const int32_t *cand_in, const int32_t *count_in
     int32_t i = t < m ? cand_in[t] : -1;
     bool keep = false;
     if (i >= 0) {
-      if (!async_mode) prop[i] = -1;
+      prop[i] = -1;
       keep = S[C[i]] == K[i];
     }
     int bin = -1;
@@ -489,12 +581,18 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
       if (g.w64) k_decide_block<int64_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
       else k_decide_block<int32_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
     } else {
-      if (!ensure_hscratch(h, g.maxdeg)) { h->fatal = LEIDEN_ERR_OOM; h->err = "global table scratch"; return; }
-      A.gslice = (int64_t)(h->hscratch_bytes / 12 / sms);
+      // tables for every listed vertex at once: at most huge_slots slots
+      size_t slots = (size_t)g.huge_slots;
+      if (!ensure_hscratch_bytes(h, slots * 12)) { h->fatal = LEIDEN_ERR_OOM; h->err = "global table scratch"; return; }
       A.gkeys = (int32_t *)h->hscratch;
-      A.gvals = (int64_t *)((char *)h->hscratch + (size_t)A.gslice * sms * sizeof(int32_t));
-      if (g.w64) k_decide_huge<int64_t, KIND><<<sms, HUGE_THREADS, 0, s>>>(A);
-      else k_decide_huge<int32_t, KIND><<<sms, HUGE_THREADS, 0, s>>>(A);
+      A.gvals = (int64_t *)((char *)h->hscratch + slots * sizeof(int32_t));
+      A.gslice = 0;
+      int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
+      k_huge_plan<<<1, 1024, 0, s>>>(A.list, A.count, g.deg, tab_off, ch_off);
+      k_huge_clear<<<sms * 8, 256, 0, s>>>(A.count, tab_off, A.gkeys, A.gvals);
+      if (g.w64) k_huge_scan<int64_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
+      else k_huge_scan<int32_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
+      k_huge_decide<KIND><<<sms * 2, HUGE_THREADS, 0, s>>>(A, tab_off);
     }
   }
 }
@@ -505,7 +603,10 @@ bool ensure_hscratch(leiden_handle *h, int64_t maxdeg) {
   int64_t T = 1;
   while (T < 2 * maxdeg) T <<= 1;
   // slice = T slots, one per resident block; vals (8 B) after keys (4 B)
-  size_t need = (size_t)T * h->sm_count * 12;
+  return ensure_hscratch_bytes(h, (size_t)T * h->sm_count * 12);
+}
+
+bool ensure_hscratch_bytes(leiden_handle *h, size_t need) {
   if (need <= h->hscratch_bytes) return true;
   if (h->hscratch) {
     for (auto &q : h->owned)
@@ -559,9 +660,8 @@ void refine_round(leiden_handle *h, const LevelGraph &g, int slot) {
   cudaMemsetAsync(cout, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&h->dcnt->accepted, 0, sizeof(int32_t), s);
   k_refine_collect<<<grid_for(g.n, 256), 256, 0, s>>>(in, cin, out, cout, g.n, h->Cp, h->Sp, h->Kp, g.deg, h->prop,
-                                                      h->bins, h->dcnt, h->p.deterministic ? 0 : 1);
+                                                      h->bins, h->dcnt, 0);
   Args A = make_args(h, g);
   launch_bins<KIND_REFINE>(h, g, A);
-  if (h->p.deterministic)
-    k_refine_accept<<<h->sm_count * 4, 256, 0, s>>>(out, cout, h->prop, h->Cp, h->Sp, h->Kp, h->dcnt);
+  k_refine_accept<<<h->sm_count * 4, 256, 0, s>>>(out, cout, h->prop, h->Cp, h->Sp, h->Kp, h->dcnt);
 }

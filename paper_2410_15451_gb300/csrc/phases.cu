@@ -384,10 +384,25 @@ __global__ void k_bits_from_flags(int64_t n, const uint8_t *flags, uint32_t *bm)
 }
 __global__ void k_maxdeg(int64_t n, const int32_t *deg, DevCounters *cnt) {
   int32_t mx = 0;
-  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) mx = max(mx, deg[i]);
+  int64_t slots = 0;
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) {
+    int32_t d = deg[i];
+    mx = max(mx, d);
+    if (d > BIN_BLOCK_MAX) {
+      int64_t t = 1;
+      while (t < 2 * (int64_t)d) t <<= 1;
+      slots += t;
+    }
+  }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(LD_FULL, mx, o));
-  if ((threadIdx.x & 31) == 0 && mx) atomicMax(&cnt->max_count, mx);
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = max(mx, __shfl_xor_sync(LD_FULL, mx, o));
+    slots += __shfl_xor_sync(LD_FULL, slots, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (mx) atomicMax(&cnt->max_count, mx);
+    if (slots) atomicAdd((unsigned long long *)&cnt->huge_slots, (unsigned long long)slots);
+  }
 }
 
 }  // namespace
@@ -509,5 +524,6 @@ void mark_unprocessed_from_flags(leiden_handle *h, const uint8_t *flags, int64_t
 
 void level_maxdeg(leiden_handle *h, const int32_t *deg, int64_t n) {
   cudaMemsetAsync(&h->dcnt->max_count, 0, sizeof(int32_t), h->stream);
+  cudaMemsetAsync(&h->dcnt->huge_slots, 0, sizeof(int64_t), h->stream);
   k_maxdeg<<<grid_for(n, TB), TB, 0, h->stream>>>(n, deg, h->dcnt);
 }
