@@ -370,10 +370,15 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   };
   cudaError_t e = cudaSuccess;
   auto A = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
+  // row capacities end at `cap`; the spill arena follows for rows that grow
+  int64_t total = cap + spill_arena_size(cap);
+  std::vector<int32_t> rcap(n);
+  for (int64_t i = 0; i < n; i++) rcap[i] = (int32_t)(cap_off[i + 1] - cap_off[i]);
   A(dalloc(h, &h->g_off, n + 1));
   A(dalloc(h, &h->g_deg, n));
-  A(dalloc(h, &h->g_col, cap));
-  A(dalloc(h, &h->g_w, cap));
+  A(dalloc(h, &h->g_rcap, n));
+  A(dalloc(h, &h->g_col, total));
+  A(dalloc(h, &h->g_w, total));
   A(dalloc(h, &h->C, n));
   A(dalloc(h, &h->K, n));
   A(dalloc(h, &h->Sig, n));
@@ -388,14 +393,15 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   for (auto pp : u8s) A(dalloc(h, pp, n + 1));
   A(dalloc(h, &h->unproc, n / 32 + 2));
   A(dalloc(h, &h->bins, (int64_t)NBINS * n));
+  A(dalloc(h, &h->hocc, n + 1));
   A(dalloc(h, &h->cand, 2 * n));
   for (int k = 0; k < 2; k++) {
     A(dalloc(h, &h->y_off[k], n + 2));
     A(dalloc(h, &h->y_deg[k], n + 1));
-    A(dalloc(h, &h->y_col[k], cap));
-    A(dalloc(h, &h->y_w[k], cap));
+    A(dalloc(h, &h->y_col[k], total));
+    A(dalloc(h, &h->y_w[k], total));
   }
-  h->y_cap = cap;
+  h->y_cap = total;
   int64_t tc = 1;
   while (tc < 2 * n) tc <<= 1;
   A(dalloc(h, &h->tr_keys, tc));
@@ -416,10 +422,12 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   A(cudaMemcpyAsync(h->g_deg, deg.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   A(cudaMemcpyAsync(h->g_col, hcol.data(), (size_t)cap * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   A(cudaMemcpyAsync(h->g_w, hw.data(), (size_t)cap * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  A(cudaMemcpyAsync(h->g_rcap, rcap.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   A(cudaMemsetAsync(h->dcnt, 0, sizeof(DevCounters), s));
+  A(cudaMemcpyAsync(&h->dcnt->arena_used, &cap, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   A(cudaStreamSynchronize(s));
   if (e != cudaSuccess) return bail(LEIDEN_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));
-  h->g_cap = cap;
+  h->g_cap = total;
   h->g_arcs = arcs;
   h->g_maxdeg = maxdeg;
   ensure_hscratch(h, std::max<int64_t>(maxdeg, BIN_BLOCK_MAX + 1));

@@ -118,9 +118,14 @@ __global__ void k_compact_flags(const int32_t *flag, const int64_t *pos, int64_t
 }
 
 // New length of each touched row and its segments in the two arc lists.
+// A row that outgrows its capacity moves to the spill arena at the end of
+// the arc arrays with fresh slack (dst, newcap); if the arena is full the
+// whole CSR is rebuilt instead (overflow flag).
 __global__ void k_row_plan(const int32_t *rows, const int64_t *nrows_p, int vb, const uint64_t *dkey, int64_t nd,
                            const uint64_t *nkey, const int64_t *nn_p, const int64_t *off, const int32_t *deg,
-                           int32_t *dlo, int32_t *dhi, int32_t *ilo, int32_t *ihi, int64_t *len, DevCounters *cnt) {
+                           const int32_t *rcap, int32_t *dlo, int32_t *dhi, int32_t *ilo, int32_t *ihi, int64_t *len,
+                           int64_t *dst, int32_t *newcap, double slack, int min_slack, int64_t colcap,
+                           DevCounters *cnt) {
   int64_t nrows = *nrows_p, nn = *nn_p;
   for (int64_t r = ld_gtid(); r < nrows; r += ld_gstride()) {
     uint64_t u = (uint64_t)rows[r];
@@ -129,7 +134,17 @@ __global__ void k_row_plan(const int32_t *rows, const int64_t *nrows_p, int vb, 
     dlo[r] = (int32_t)a; dhi[r] = (int32_t)b; ilo[r] = (int32_t)c; ihi[r] = (int32_t)d;
     int64_t L = (int64_t)deg[u] - (b - a) + (d - c);
     len[r] = L;
-    if (L > off[u + 1] - off[u]) atomicExch(&cnt->overflow, 1);
+    dst[r] = off[u];
+    newcap[r] = 0;
+    if (L > rcap[u]) {
+      int64_t extra = (int64_t)((double)L * slack);
+      if (extra < min_slack) extra = min_slack;
+      int64_t cap = L + extra;
+      int64_t p = (int64_t)atomicAdd((unsigned long long *)&cnt->arena_used, (unsigned long long)cap);
+      if (p + cap > colcap) atomicExch(&cnt->overflow, 1);
+      dst[r] = p;
+      newcap[r] = (int32_t)cap;
+    }
   }
 }
 
@@ -197,18 +212,30 @@ struct MergeArgs {
   const int32_t *dlo, *dhi, *ilo, *ihi;
   const int64_t *len, *tmp_off, *off;
   int32_t *deg, *col, *w, *tcol, *tw;
+  const int64_t *dst;     // where the merged row goes (its old place unless relocated)
+  const int32_t *newcap;  // capacity of a relocated row, 0 otherwise
+  int64_t *off_w;         // row starts (written after a row is relocated)
+  int32_t *rcap;          // row capacities
 };
 
+// After the row's reads are done: record a relocation.
+__device__ __forceinline__ void finish_row(const MergeArgs &A, int64_t r, int32_t u, int64_t L) {
+  A.deg[u] = (int32_t)L;
+  if (A.newcap[r]) {
+    A.off_w[u] = A.dst[r];
+    A.rcap[u] = A.newcap[r];
+  }
+}
+
+// D, I: the row's deletion keys and new-arc keys (global or staged copies).
 __device__ __forceinline__ void merge_row_into(const MergeArgs &A, int64_t r, int t0, int stride, int32_t *ocol,
-                                               int32_t *ow) {
+                                               int32_t *ow, const uint64_t *D, const uint64_t *I) {
   uint64_t mask = (1ull << A.vb) - 1;
   int32_t u = A.rows[r];
   const int32_t *row = A.col + A.off[u];
   const int32_t *roww = A.w + A.off[u];
   int64_t dg = A.deg[u];
-  const uint64_t *D = A.dkey + A.dlo[r];
   int64_t nD = A.dhi[r] - A.dlo[r];
-  const uint64_t *I = A.nkey + A.ilo[r];
   const int64_t *IW = A.nw + A.ilo[r];
   int64_t nI = A.ihi[r] - A.ilo[r];
   uint64_t ubase = (uint64_t)u << A.vb;
@@ -239,28 +266,43 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge_small(MergeArgs A) {
   for (int64_t r = (int64_t)blockIdx.x * MERGE_WARPS + wid; r < nrows; r += (int64_t)gridDim.x * MERGE_WARPS) {
     int64_t L = A.len[r];
     if (L > MERGE_SMALL) continue;
-    merge_row_into(A, r, lane, 32, scol[wid], sw[wid]);
+    merge_row_into(A, r, lane, 32, scol[wid], sw[wid], A.dkey + A.dlo[r], A.nkey + A.ilo[r]);
     __syncwarp();
     int32_t u = A.rows[r];
-    int64_t o = A.off[u];
+    int64_t o = A.dst[r];
     for (int64_t x = lane; x < L; x += 32) { A.col[o + x] = scol[wid][x]; A.w[o + x] = sw[wid][x]; }
-    if (lane == 0) A.deg[u] = (int32_t)L;
+    if (lane == 0) finish_row(A, r, u, L);
     __syncwarp();
   }
 }
 
+// Long rows: one block per row.  The row's deletion and new-arc keys are
+// staged in shared memory when they fit, so the per-element rank searches
+// do not go to global memory.
+constexpr int MERGE_STAGE = 2048;
 __global__ void __launch_bounds__(512) k_merge_large(MergeArgs A) {
+  __shared__ uint64_t sD[MERGE_STAGE];
+  __shared__ uint64_t sI[MERGE_STAGE];
   int64_t nrows = *A.nrows_p;
   for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
     int64_t L = A.len[r];
     if (L <= MERGE_SMALL) continue;
     int64_t b = A.tmp_off[r];
-    merge_row_into(A, r, threadIdx.x, blockDim.x, A.tcol + b, A.tw + b);
+    int64_t nD = A.dhi[r] - A.dlo[r], nI = A.ihi[r] - A.ilo[r];
+    const uint64_t *D = A.dkey + A.dlo[r], *I = A.nkey + A.ilo[r];
+    if (nD <= MERGE_STAGE && nI <= MERGE_STAGE) {
+      for (int64_t k = threadIdx.x; k < nD; k += blockDim.x) sD[k] = D[k];
+      for (int64_t k = threadIdx.x; k < nI; k += blockDim.x) sI[k] = I[k];
+      __syncthreads();
+      D = sD;
+      I = sI;
+    }
+    merge_row_into(A, r, threadIdx.x, blockDim.x, A.tcol + b, A.tw + b, D, I);
     __syncthreads();
     int32_t u = A.rows[r];
-    int64_t o = A.off[u];
+    int64_t o = A.dst[r];
     for (int64_t x = threadIdx.x; x < L; x += blockDim.x) { A.col[o + x] = A.tcol[b + x]; A.w[o + x] = A.tw[b + x]; }
-    if (threadIdx.x == 0) A.deg[u] = (int32_t)L;
+    if (threadIdx.x == 0) finish_row(A, r, u, L);
     __syncthreads();
   }
 }
@@ -297,6 +339,9 @@ __global__ void k_copy_rows_rebuild(int64_t n, const int64_t *old_off, const int
     for (int64_t x = lane; x < L; x += 32) { new_col[o + x] = sc[x]; new_w[o + x] = sw[x]; }
     if (lane == 0) new_deg[u] = (int32_t)L;
   }
+}
+__global__ void k_set_rcap(const int64_t *cap, int64_t n, int32_t *rcap) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) rcap[i] = (int32_t)cap[i];
 }
 __global__ void k_rowsrc(const int32_t *rows, const int64_t *nrows_p, int32_t *rowsrc) {
   for (int64_t r = ld_gtid(); r < *nrows_p; r += ld_gstride()) rowsrc[rows[r]] = (int32_t)r;
@@ -447,7 +492,8 @@ cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
   int64_t cap = std::max<int64_t>(edges, 1024);
   void *old[] = {b.dkey, b.dkey_alt, b.ikey, b.ikey_alt, b.iw, b.iw_alt, b.dw, b.flag,
                  b.pos, b.ins_state, b.ins_pos, b.row_dlo, b.row_dhi, b.row_ilo, b.row_ihi, b.row_len,
-                 b.row_tmp_off, b.rows, b.ds_key, b.ds_key_alt, b.ds_w, b.ds_w_alt, b.ds_ukey, b.ds_uw};
+                 b.row_tmp_off, b.rows, b.ds_key, b.ds_key_alt, b.ds_w, b.ds_w_alt, b.ds_ukey, b.ds_uw,
+                 b.row_dst, b.row_newcap};
   for (void *p : old) release(h, p);
   int64_t arcs = 2 * cap;
   cudaError_t e = cudaSuccess;
@@ -471,6 +517,8 @@ cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
   chk(grow(h, &b.row_ihi, rows));
   chk(grow(h, &b.row_len, rows + 1));
   chk(grow(h, &b.row_tmp_off, rows + 1));
+  chk(grow(h, &b.row_dst, rows + 1));
+  chk(grow(h, &b.row_newcap, rows + 1));
   chk(grow(h, &b.ds_key, arcs));
   chk(grow(h, &b.ds_key_alt, arcs));
   chk(grow(h, &b.ds_w, arcs));
@@ -528,13 +576,16 @@ static leiden_status rebuild_graph(leiden_handle *h, int64_t nrows_host, const i
   if (grow(h, &new_off, n + 1) != cudaSuccess) return fail(h, LEIDEN_ERR_OOM, "rebuild: offsets");
   if (ensure_scan_tmp(h, scan_tmp_bytes(n + 1)) != cudaSuccess) return fail(h, LEIDEN_ERR_OOM, "scan tmp");
   exclusive_scan_i64(cap, new_off, n, h->scan_tmp, s);
-  int64_t total = 0;
-  cudaMemcpyAsync(&total, new_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  int64_t used = 0;
+  cudaMemcpyAsync(&used, new_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
+  int64_t total = used + spill_arena_size(used);
   int32_t *new_col = nullptr, *new_w = nullptr, *new_deg = nullptr;
   if (grow(h, &new_col, total) != cudaSuccess || grow(h, &new_w, total) != cudaSuccess ||
       grow(h, &new_deg, n) != cudaSuccess)
     return fail(h, LEIDEN_ERR_OOM, "rebuild: arcs");
+  k_set_rcap<<<grid_for(n, TB), TB, 0, s>>>(cap, n, h->g_rcap);
+  cudaMemcpyAsync(&h->dcnt->arena_used, &used, sizeof(int64_t), cudaMemcpyHostToDevice, s);
   int32_t *rowsrc = h->ibuf2;
   launch_fill_i32(rowsrc, -1, n, s);
   k_rowsrc<<<grid_for(nrows_host, TB), TB, 0, s>>>(b.rows, nrows_dev, rowsrc);
@@ -632,8 +683,8 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
     k_compact_flags<<<grid_for(n, TB), TB, 0, s>>>(touched, h->lbuf0, n, b.rows);
     cudaMemcpyAsync(counts + 3, h->lbuf0 + n, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
     k_row_plan<<<grid_for(std::min<int64_t>(n, nd + nn), TB), TB, 0, s>>>(
-        b.rows, counts + 3, vb, DK, nd, NK, counts + 2, h->g_off, h->g_deg, b.row_dlo, b.row_dhi, b.row_ilo,
-        b.row_ihi, b.row_len, cnt);
+        b.rows, counts + 3, vb, DK, nd, NK, counts + 2, h->g_off, h->g_deg, h->g_rcap, b.row_dlo, b.row_dhi,
+        b.row_ilo, b.row_ihi, b.row_len, b.row_dst, b.row_newcap, h->p.slack, h->p.min_slack, h->g_cap, cnt);
     cudaMemcpyAsync(b.hcounts + 3, counts + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     nrows = b.hcounts[3];
@@ -650,7 +701,8 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   if (nrows > 0) {
     if (!overflow) {
       MergeArgs M{b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo, b.row_dhi, b.row_ilo, b.row_ihi, b.row_len,
-                  b.row_tmp_off, h->g_off, h->g_deg, h->g_col, h->g_w, b.tmp_col, b.tmp_w};
+                  b.row_tmp_off, h->g_off, h->g_deg, h->g_col, h->g_w, b.tmp_col, b.tmp_w,
+                  b.row_dst, b.row_newcap, h->g_off, h->g_rcap};
       k_merge_small<<<grid_for((nrows + MERGE_WARPS - 1) / MERGE_WARPS, 1, h->sm_count * 16), MERGE_WARPS * 32, 0,
                       s>>>(M);
       k_merge_large<<<h->sm_count * 2, 512, 0, s>>>(M);

@@ -38,7 +38,9 @@ struct DevCounters {
   unsigned long long sq[2];       // modularity: sum of Sigma_c^2 (int128)
   int64_t batch_dw;               // batch: change of 2m
   int64_t huge_slots;             // table slots the vertices above the block bin need
-  int64_t pad[2];
+  int32_t big_count;              // splitting: long rows left to the block kernel
+  int32_t pad32;
+  int64_t arena_used;             // next free arc slot of G^t (relocated rows go here)
 };
 
 // ---------------------------------------------------------------- hashing
@@ -135,6 +137,35 @@ __device__ __forceinline__ int32_t ld_group_min_i32(uint32_t peers, int32_t v) {
 // True in the lowest lane of the group.
 __device__ __forceinline__ bool ld_group_leader(uint32_t peers) {
   return (__ffs(peers) - 1) == (int)(threadIdx.x & 31);
+}
+
+// Open-addressing insert into a global table (linear probing, key -1 =
+// empty) that records each slot it fills in `list` (count in *occ), so the
+// reader visits only filled slots and can empty them again afterwards.
+__device__ __forceinline__ void ld_gtable_insert(int32_t *keys, int64_t *vals, int32_t *list, int32_t *occ, int tmask,
+                                                 int32_t c, int64_t w) {
+  uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)tmask;
+  while (true) {
+    int32_t k = atomicCAS(&keys[s], LD_EMPTY_KEY, c);
+    if (k == LD_EMPTY_KEY) list[atomicAdd(occ, 1)] = (int32_t)s;
+    if (k == LD_EMPTY_KEY || k == c) {
+      atomicAdd((unsigned long long *)&vals[s], (unsigned long long)w);
+      return;
+    }
+    s = (s + 1) & (uint32_t)tmask;
+  }
+}
+
+// Warp-cooperative form for loops where all 32 lanes iterate together: lanes
+// with the same key add their weights first and one lane inserts the sum
+// (keys of a hub's neighbours are often few, so this removes most of the
+// atomic traffic on the hottest slots).  `valid` = this lane has an item.
+__device__ __forceinline__ void ld_gtable_insert_warp(int32_t *keys, int64_t *vals, int32_t *list, int32_t *occ,
+                                                      int tmask, bool valid, int32_t c, int64_t w) {
+  int32_t key = valid ? c : -2 - (int32_t)(threadIdx.x & 31);  // unique per invalid lane
+  uint32_t peers = __match_any_sync(LD_FULL, key);
+  int64_t sum = ld_group_sum_i64(peers, valid ? w : 0);
+  if (valid && ld_group_leader(peers)) ld_gtable_insert(keys, vals, list, occ, tmask, c, sum);
 }
 
 // ---------------------------------------------------------------- bitmaps

@@ -43,6 +43,8 @@ struct BatchBuffers {
   int32_t *row_ilo = nullptr, *row_ihi = nullptr;        // insertion arc range of a row
   int64_t *row_len = nullptr;                            // new row length
   int64_t *row_tmp_off = nullptr;                        // offset into the merge buffer
+  int64_t *row_dst = nullptr;                            // where the merged row goes
+  int32_t *row_newcap = nullptr;                         // capacity of a relocated row (0: stays)
   uint64_t *ds_key = nullptr, *ds_key_alt = nullptr, *ds_ukey = nullptr;  // DS (src, C[dst]) pairs
   int64_t *ds_w = nullptr, *ds_w_alt = nullptr, *ds_uw = nullptr;
   int64_t *counts = nullptr;                             // device counts of the batch pipeline
@@ -60,8 +62,9 @@ struct leiden_handle {
   int64_t n = 0;
 
   // G^t: device CSR with slack
-  int64_t *g_off = nullptr;  // [n+1] row starts (capacity based)
+  int64_t *g_off = nullptr;  // [n+1] row starts
   int32_t *g_deg = nullptr;  // [n]
+  int32_t *g_rcap = nullptr; // [n] row capacities (rows that outgrow them move to the spill arena)
   int32_t *g_col = nullptr;  // [g_cap]
   int32_t *g_w = nullptr;    // [g_cap]
   int64_t g_cap = 0;
@@ -98,9 +101,11 @@ struct leiden_handle {
   int64_t *y_w[2] = {nullptr, nullptr};
   int64_t y_cap = 0;
 
-  // global hash scratch for the largest vertices / communities
+  // global hash scratch for the largest vertices / communities (kept clean)
   void *hscratch = nullptr;
   size_t hscratch_bytes = 0;
+  int64_t hslots = 0;
+  int32_t *hocc = nullptr;  // [n] filled slots per listed vertex
 
   // tracking hash table of (old, new) pairs
   uint64_t *tr_keys = nullptr;
@@ -144,11 +149,17 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, int64_t *vals, in
 void launch_fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s);
 void launch_fill_i64(int64_t *p, int64_t v, int64_t n, cudaStream_t s);
 void launch_iota_i32(int32_t *p, int64_t n, cudaStream_t s);
+// Per-item global tables and work chunks for the listed items (see prims.cu).
+constexpr int TABLE_CHUNK = 4096;
+void launch_table_plan(const int32_t *list, const int32_t *count, const int32_t *deg32, const int64_t *off64,
+                       int64_t *tab_off, int64_t *ch_off, cudaStream_t s);
 int grid_for(int64_t n, int block, int max_blocks = 152 * 16);
 
 // ------------------------------------------------------------ batch.cu
 leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, int64_t n_del,
                                    const leiden_edge *d_ins, int64_t n_ins, int mode);
+// Spare arc slots kept after `used` slots for rows that outgrow their capacity.
+inline int64_t spill_arena_size(int64_t used) { return used / 8 + (int64_t)(1 << 20); }
 
 // ------------------------------------------------------------ move.cu
 // One local-moving sub-sweep of class `cls` (0 .. classes-1).
@@ -158,7 +169,10 @@ void refine_reset(leiden_handle *h, const LevelGraph &g);
 void refine_round(leiden_handle *h, const LevelGraph &g, int slot);
 void lm_prepare(leiden_handle *h, const LevelGraph &g);  // community sizes
 bool ensure_hscratch(leiden_handle *h, int64_t maxdeg);  // false: allocation failed
-bool ensure_hscratch_bytes(leiden_handle *h, size_t bytes);
+bool ensure_hslots(leiden_handle *h, int64_t slots);     // false: allocation failed
+int32_t *hs_keys(leiden_handle *h);  // global table scratch: keys, values, slot lists
+int64_t *hs_vals(leiden_handle *h);
+int32_t *hs_list(leiden_handle *h);
 
 // ------------------------------------------------------------ phases.cu
 void subset_renumber(leiden_handle *h, int64_t n);

@@ -53,6 +53,8 @@ struct Args {
   // global scratch for the huge bin
   int32_t *gkeys;
   int64_t *gvals;
+  int32_t *glist;  // filled slots of each table
+  int32_t *gocc;   // number of filled slots of each listed vertex
   int64_t gslice;
 };
 
@@ -270,90 +272,18 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Args A) {
   if (threadIdx.x == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
 }
 
-// ---------------------------------------------------------------- bin 2: block, global table
-template <typename W, int KIND>
-__global__ void __launch_bounds__(HUGE_THREADS) k_decide_huge(Args A) {
-  __shared__ int moved_s;
-  int32_t *keys = A.gkeys + (int64_t)blockIdx.x * A.gslice;
-  int64_t *vals = A.gvals + (int64_t)blockIdx.x * A.gslice;
-  int64_t count = *A.count;
-  int64_t visits = 0, arcs = 0, moves = 0;
-  i128 dq = 0;
-  for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
-    int64_t i = A.list[t];
-    int64_t base = A.off[i], dg = A.deg[i];
-    int64_t T = 1;
-    while (T < 2 * dg) T <<= 1;
-    for (int64_t s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
-    __syncthreads();
-    scan_arcs<W, KIND>(A, i, base, dg, threadIdx.x, blockDim.x, keys, vals, (int)(T - 1));
-    __syncthreads();
-    Best b = slot_best(keys, vals, (int)T, threadIdx.x, blockDim.x, A.C[i], A.cnt->m2, A.K[i], A.S);
-    b = block_best(b);
-    if (threadIdx.x == 0) {
-      i128 g = decide_leader<KIND>(A, i, b);
-      moved_s = g > 0;
-      visits++; arcs += dg; moves += g > 0; dq += g;
-    }
-    __syncthreads();
-    if (KIND == KIND_MOVE && moved_s) mark_neighbours(A, i, base, dg, threadIdx.x, blockDim.x);
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
-}
-
 // ---------------------------------------------------------------- bin 2, split across blocks
 // Vertices above BIN_BLOCK_MAX arcs: each gets its own table of
 // pow2 >= 2*degree slots in global scratch and its arcs are cut into chunks
 // of HUGE_CHUNK that any block may take, so one hub no longer runs on one SM.
-constexpr int HUGE_CHUNK = 4096;
+constexpr int HUGE_CHUNK = TABLE_CHUNK;
 
-// One block: table and chunk offsets of the listed vertices (exclusive
-// prefix sums; totals at index count).
-__global__ void __launch_bounds__(1024) k_huge_plan(const int32_t *list, const int32_t *count_p, const int32_t *deg,
-                                                     int64_t *tab_off, int64_t *ch_off) {
-  __shared__ int64_t ws[32][2];
-  __shared__ int64_t carry[2];
-  int64_t count = *count_p;
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) { carry[0] = 0; carry[1] = 0; }
-  __syncthreads();
-  for (int64_t base = 0; base < count; base += blockDim.x) {
-    int64_t k = base + threadIdx.x;
-    int64_t t = 0, c = 0;
-    if (k < count) {
-      int64_t d = deg[list[k]];
-      t = 1;
-      while (t < 2 * d) t <<= 1;
-      c = (d + HUGE_CHUNK - 1) / HUGE_CHUNK;
-    }
-    int64_t it = t, ic = c;  // inclusive warp scans
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      int64_t xt = __shfl_up_sync(LD_FULL, it, o), xc = __shfl_up_sync(LD_FULL, ic, o);
-      if (lane >= o) { it += xt; ic += xc; }
-    }
-    if (lane == 31) { ws[wid][0] = it; ws[wid][1] = ic; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int64_t a = carry[0], b = carry[1];
-      for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-        int64_t x = ws[w][0], y = ws[w][1];
-        ws[w][0] = a; ws[w][1] = b;
-        a += x; b += y;
-      }
-      carry[0] = a; carry[1] = b;
-    }
-    __syncthreads();
-    if (k < count) { tab_off[k] = ws[wid][0] + it - t; ch_off[k] = ws[wid][1] + ic - c; }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) { tab_off[count] = carry[0]; ch_off[count] = carry[1]; }
-}
-
-__global__ void k_huge_clear(const int32_t *count_p, const int64_t *tab_off, int32_t *keys, int64_t *vals) {
-  int64_t total = tab_off[*count_p];
-  for (int64_t s = ld_gtid(); s < total; s += ld_gstride()) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
+// Global tables start clean (empty keys, zero values) and are cleaned again
+// by the kernel that reads them; each records the slots it fills in a list
+// (occ[k] entries at tab_off[k] in A.glist), so the decision visits only the
+// distinct communities instead of the whole table.
+__global__ void k_huge_zero_occ(const int32_t *count_p, int32_t *occ) {
+  for (int64_t k = ld_gtid(); k < *count_p; k += ld_gstride()) occ[k] = 0;
 }
 
 template <typename W, int KIND>
@@ -368,11 +298,27 @@ __global__ void __launch_bounds__(256) k_huge_scan(Args A, const int64_t *tab_of
     }
     int64_t i = A.list[lo];
     int64_t first = (t - ch_off[lo]) * HUGE_CHUNK;
-    int64_t dg = A.deg[i];
-    int64_t last = first + HUGE_CHUNK < dg ? first + HUGE_CHUNK : dg;
+    int64_t full = A.deg[i];
+    int64_t last = first + HUGE_CHUNK < full ? first + HUGE_CHUNK : full;
     int64_t T = tab_off[lo + 1] - tab_off[lo];
-    scan_arcs<W, KIND>(A, i, A.off[i] + first, last - first, threadIdx.x, blockDim.x, A.gkeys + tab_off[lo],
-                       A.gvals + tab_off[lo], (int)(T - 1));
+    const W *w = (const W *)A.w;
+    int64_t base = A.off[i] + first, len = last - first;
+    int32_t bi = KIND == KIND_REFINE ? A.CB[i] : 0;
+    int32_t *keys = A.gkeys + tab_off[lo], *list = A.glist + tab_off[lo];
+    int64_t *vals = A.gvals + tab_off[lo];
+    int lane = threadIdx.x & 31;
+    for (int64_t a0 = threadIdx.x & ~31; a0 < len; a0 += blockDim.x) {  // warp-uniform trip count
+      int64_t a = a0 + lane;
+      bool valid = a < len;
+      int32_t c = 0;
+      int64_t wa = 0;
+      if (valid) {
+        int32_t j = A.col[base + a];
+        valid = j != i && (KIND != KIND_REFINE || A.CB[j] == bi);
+        if (valid) { c = A.C[j]; wa = (int64_t)w[base + a]; }
+      }
+      ld_gtable_insert_warp(keys, vals, list, &A.gocc[lo], (int)(T - 1), valid, c, wa);
+    }
   }
 }
 
@@ -385,10 +331,26 @@ __global__ void __launch_bounds__(1024) k_huge_decide(Args A, const int64_t *tab
   for (int64_t k = blockIdx.x; k < count; k += gridDim.x) {
     int64_t i = A.list[k];
     int64_t base = A.off[i], dg = A.deg[i];
-    int64_t T = tab_off[k + 1] - tab_off[k];
-    Best b = slot_best(A.gkeys + tab_off[k], A.gvals + tab_off[k], (int)T, threadIdx.x, blockDim.x, A.C[i],
-                       A.cnt->m2, A.K[i], A.S);
+    int32_t *keys = A.gkeys + tab_off[k], *list = A.glist + tab_off[k];
+    int64_t *vals = A.gvals + tab_off[k];
+    int32_t occ = A.gocc[k];
+    int32_t d = A.C[i];
+    int64_t m2 = A.cnt->m2, Ki = A.K[i];
+    Best b{0, -1, 0, 0};
+    for (int32_t t = threadIdx.x; t < occ; t += blockDim.x) {
+      int32_t s = list[t];
+      int32_t c = keys[s];
+      int64_t kv = vals[s];
+      if (c == d) { b.kd += kv; continue; }
+      i128 v = (i128)m2 * kv - (i128)Ki * A.S[c];
+      if (ld_better(v, c, b.v, b.c)) { b.v = v; b.c = c; b.kc = kv; }
+    }
     b = block_best(b);
+    for (int32_t t = threadIdx.x; t < occ; t += blockDim.x) {  // leave the table clean
+      int32_t s = list[t];
+      keys[s] = LD_EMPTY_KEY;
+      vals[s] = 0;
+    }
     if (threadIdx.x == 0) {
       i128 g = decide_leader<KIND>(A, i, b);
       moved_s = g > 0;
@@ -582,14 +544,15 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
       else k_decide_block<int32_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
     } else {
       // tables for every listed vertex at once: at most huge_slots slots
-      size_t slots = (size_t)g.huge_slots;
-      if (!ensure_hscratch_bytes(h, slots * 12)) { h->fatal = LEIDEN_ERR_OOM; h->err = "global table scratch"; return; }
-      A.gkeys = (int32_t *)h->hscratch;
-      A.gvals = (int64_t *)((char *)h->hscratch + slots * sizeof(int32_t));
+      if (!ensure_hslots(h, g.huge_slots)) { h->fatal = LEIDEN_ERR_OOM; h->err = "global table scratch"; return; }
+      A.gkeys = hs_keys(h);
+      A.gvals = hs_vals(h);
+      A.glist = hs_list(h);
+      A.gocc = h->hocc;
       A.gslice = 0;
       int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
-      k_huge_plan<<<1, 1024, 0, s>>>(A.list, A.count, g.deg, tab_off, ch_off);
-      k_huge_clear<<<sms * 8, 256, 0, s>>>(A.count, tab_off, A.gkeys, A.gvals);
+      launch_table_plan(A.list, A.count, g.deg, nullptr, tab_off, ch_off, s);
+      k_huge_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
       if (g.w64) k_huge_scan<int64_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
       else k_huge_scan<int32_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
       k_huge_decide<KIND><<<sms * 2, HUGE_THREADS, 0, s>>>(A, tab_off);
@@ -602,28 +565,40 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
 bool ensure_hscratch(leiden_handle *h, int64_t maxdeg) {
   int64_t T = 1;
   while (T < 2 * maxdeg) T <<= 1;
-  // slice = T slots, one per resident block; vals (8 B) after keys (4 B)
-  return ensure_hscratch_bytes(h, (size_t)T * h->sm_count * 12);
+  return ensure_hslots(h, T * h->sm_count);  // one slice of T slots per resident block
 }
 
-bool ensure_hscratch_bytes(leiden_handle *h, size_t need) {
-  if (need <= h->hscratch_bytes) return true;
+// Global table scratch of `slots` slots laid out as keys int32[S] | values
+// int64[S] | slot lists int32[S] (16 B per slot).  Every user leaves the
+// slots it touched empty again, so a new allocation is cleared once.
+bool ensure_hslots(leiden_handle *h, int64_t slots) {
+  if (slots <= h->hslots) return true;
+  int64_t S = (slots + 1023) & ~(int64_t)1023;
   if (h->hscratch) {
+    cudaStreamSynchronize(h->stream);
     for (auto &q : h->owned)
       if (q == h->hscratch) { cudaFree(q); q = nullptr; }
   }
   void *p = nullptr;
-  if (cudaMalloc(&p, need) != cudaSuccess) {
+  if (cudaMalloc(&p, (size_t)S * 16) != cudaSuccess) {
     cudaGetLastError();
     h->hscratch = nullptr;
     h->hscratch_bytes = 0;
+    h->hslots = 0;
     return false;
   }
   h->owned.push_back(p);
   h->hscratch = p;
-  h->hscratch_bytes = need;
+  h->hscratch_bytes = (size_t)S * 16;
+  h->hslots = S;
+  cudaMemsetAsync(p, 0xff, (size_t)S * 4, h->stream);                   // keys: empty
+  cudaMemsetAsync((char *)p + (size_t)S * 4, 0, (size_t)S * 8, h->stream);  // values: 0
   return true;
 }
+
+int32_t *hs_keys(leiden_handle *h) { return (int32_t *)h->hscratch; }
+int64_t *hs_vals(leiden_handle *h) { return (int64_t *)((char *)h->hscratch + (size_t)h->hslots * 4); }
+int32_t *hs_list(leiden_handle *h) { return (int32_t *)((char *)h->hscratch + (size_t)h->hslots * 12); }
 
 void lm_prepare(leiden_handle *h, const LevelGraph &g) {
   cudaMemsetAsync(h->csize, 0, (size_t)g.n * sizeof(int32_t), h->stream);

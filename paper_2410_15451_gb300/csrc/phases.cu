@@ -84,6 +84,7 @@ __device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b) 
 // Sampling round (Afforest, Sutton et al. 2018): link each listed vertex to
 // its first SPLIT_SAMPLES neighbours in the same community.
 constexpr int SPLIT_SAMPLES = 2;
+constexpr int SPLIT_SAMPLE_SCAN = 64;
 __global__ void k_split_sample(const int32_t *list, const DevCounters *cnt, const int64_t *off, const int32_t *deg,
                                const int32_t *col, const int32_t *C, int32_t *parent) {
   int64_t m = cnt->split_count;
@@ -92,6 +93,7 @@ __global__ void k_split_sample(const int32_t *list, const DevCounters *cnt, cons
     int32_t c = C[i];
     int64_t b = off[i], d = deg[i];
     int got = 0;
+    if (d > SPLIT_SAMPLE_SCAN) d = SPLIT_SAMPLE_SCAN;  // sampling looks at a short prefix only
     for (int64_t a = 0; a < d && got < SPLIT_SAMPLES; a++) {
       int32_t j = col[b + a];
       if (j == i || C[j] != c) continue;
@@ -114,8 +116,9 @@ __global__ void k_split_flatten(const int32_t *list, const DevCounters *cnt, int
 // it skips its arcs, every other vertex links along all of its arcs.  An edge
 // with an endpoint outside that component is therefore always processed
 // from that endpoint, so the final components are exact.
-__global__ void k_split_link_rest(const int32_t *list, const DevCounters *cnt, const int64_t *off,
-                                  const int32_t *deg, const int32_t *col, const int32_t *C, int32_t *parent) {
+constexpr int SPLIT_BIG = 2048;  // longer rows go to the block kernel
+__global__ void k_split_link_rest(const int32_t *list, DevCounters *cnt, const int64_t *off, const int32_t *deg,
+                                  const int32_t *col, const int32_t *C, int32_t *parent, int32_t *big) {
   int lane = threadIdx.x & 31;
   int64_t m = cnt->split_count;
   int64_t warp = ld_gtid() >> 5, nw = ld_gstride() >> 5;
@@ -126,7 +129,26 @@ __global__ void k_split_link_rest(const int32_t *list, const DevCounters *cnt, c
     if (lane == 0) root = uf_find(parent, i);
     if (__shfl_sync(LD_FULL, root, 0) == c) continue;
     int64_t b = off[i], d = deg[i];
+    if (d > SPLIT_BIG) {
+      if (lane == 0) big[atomicAdd(&cnt->big_count, 1)] = i;
+      continue;
+    }
     for (int64_t a = lane; a < d; a += 32) {
+      int32_t j = col[b + a];
+      if (j != i && C[j] == c) uf_unite(parent, i, j);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_split_link_big(const int32_t *big, const DevCounters *cnt,
+                                                        const int64_t *off, const int32_t *deg, const int32_t *col,
+                                                        const int32_t *C, int32_t *parent) {
+  int64_t m = cnt->big_count;
+  for (int64_t t = blockIdx.x; t < m; t += gridDim.x) {
+    int32_t i = big[t];
+    int32_t c = C[i];
+    int64_t b = off[i], d = deg[i];
+    for (int64_t a = threadIdx.x; a < d; a += blockDim.x) {
       int32_t j = col[b + a];
       if (j != i && C[j] == c) uf_unite(parent, i, j);
     }
@@ -190,6 +212,11 @@ __global__ void k_yoff(int64_t ncomm, const int64_t *coff, const int64_t *cflat,
     if (c < ncomm) {
       int64_t d = cflat[coff[c + 1]] - cflat[coff[c]];
       atomicMax(&cnt->max_count, (int32_t)(d < INT_MAX ? d : INT_MAX));
+      if (d > BIN_BLOCK_MAX) {  // table slots of the chunked path
+        int64_t t = 1;
+        while (t < 2 * d) t <<= 1;
+        atomicAdd((unsigned long long *)&cnt->huge_slots, (unsigned long long)t);
+      }
     }
   }
 }
@@ -225,7 +252,8 @@ struct AggArgs {
   const int32_t *count;
   int32_t *gkeys;
   int64_t *gvals;
-  int64_t gslice;
+  int32_t *glist;  // filled slots of each listed community's table
+  int32_t *gocc;   // number of filled slots
 };
 
 // Flat arcs [f0, f1) of community c, processed by `stride` threads.
@@ -249,16 +277,20 @@ __device__ __forceinline__ void agg_scan(const AggArgs &A, int64_t c, int t0, in
 }
 
 template <int GROUP>
-__device__ __forceinline__ void agg_emit(const AggArgs &A, int64_t c, int t0, int stride, const int32_t *keys,
-                                         const int64_t *vals, int T, int32_t *rowcount, int64_t *rowsum) {
+// Emit the table as the super-row of c and leave every slot empty again.
+__device__ __forceinline__ void agg_emit(const AggArgs &A, int64_t c, int t0, int stride, int32_t *keys,
+                                         int64_t *vals, int T, int32_t *rowcount, int64_t *rowsum) {
   int64_t base = A.yoff[c];
   for (int s = t0; s < T; s += stride) {
     int32_t k = keys[s];
     if (k == LD_EMPTY_KEY) continue;
+    int64_t v = vals[s];
+    keys[s] = LD_EMPTY_KEY;
+    vals[s] = 0;
     int32_t p = atomicAdd(rowcount, 1);
     A.ycol[base + p] = k;
-    A.yw[base + p] = vals[s];
-    atomicAdd((unsigned long long *)rowsum, (unsigned long long)vals[s]);
+    A.yw[base + p] = v;
+    atomicAdd((unsigned long long *)rowsum, (unsigned long long)v);
   }
 }
 
@@ -315,28 +347,81 @@ __global__ void __launch_bounds__(256) k_agg_block(AggArgs A) {
   }
 }
 
+// Communities above BIN_BLOCK_MAX flat arcs: each has its own global table
+// (tab_off) and its flat arcs are cut into chunks any block may take
+// (ch_off); the filled slots are listed so the emission visits only them.
 template <typename W>
-__global__ void __launch_bounds__(1024) k_agg_huge(AggArgs A) {
+__global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t *tab_off, const int64_t *ch_off) {
+  int64_t count = *A.count;
+  int64_t nch = ch_off[count];
+  const W *w = (const W *)A.w;
+  for (int64_t t = blockIdx.x; t < nch; t += gridDim.x) {
+    int64_t lo = 0, hi = count - 1;  // community k with ch_off[k] <= t < ch_off[k+1]
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) >> 1;
+      if (ch_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    int64_t c = A.list[lo];
+    int64_t m0 = A.coff[c], m1 = A.coff[c + 1];
+    int64_t f0 = A.cflat[m0] + (t - ch_off[lo]) * TABLE_CHUNK;
+    int64_t f1 = A.cflat[m1];
+    if (f0 + TABLE_CHUNK < f1) f1 = f0 + TABLE_CHUNK;
+    int64_t T = tab_off[lo + 1] - tab_off[lo];
+    int32_t *keys = A.gkeys + tab_off[lo], *list = A.glist + tab_off[lo];
+    int64_t *vals = A.gvals + tab_off[lo];
+    int lane = threadIdx.x & 31;
+    for (int64_t f0w = f0 + (threadIdx.x & ~31); f0w < f1; f0w += blockDim.x) {  // warp-uniform trip count
+      int64_t f = f0w + lane;
+      bool valid = f < f1;
+      int32_t c = 0;
+      int64_t wa = 0;
+      if (valid) {
+        int64_t a = m0, b = m1 - 1;  // member with cflat[a] <= f
+        while (a < b) {
+          int64_t mid = (a + b + 1) >> 1;
+          if (A.cflat[mid] <= f) a = mid; else b = mid - 1;
+        }
+        int32_t v = A.cverts[a];
+        int64_t arc = A.off[v] + (f - A.cflat[a]);
+        c = A.C[A.col[arc]];
+        wa = (int64_t)w[arc];
+      }
+      ld_gtable_insert_warp(keys, vals, list, &A.gocc[lo], (int)(T - 1), valid, c, wa);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_agg_list_emit(AggArgs A, const int64_t *tab_off) {
   __shared__ int32_t rc;
   __shared__ int64_t rs;
-  int32_t *keys = A.gkeys + (int64_t)blockIdx.x * A.gslice;
-  int64_t *vals = A.gvals + (int64_t)blockIdx.x * A.gslice;
   int64_t count = *A.count;
-  for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
-    int64_t c = A.list[t];
-    int64_t dg = A.yoff[c + 1] - A.yoff[c];
-    int64_t T = 32;
-    while (T < 2 * dg) T <<= 1;
-    for (int64_t s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
+  for (int64_t k = blockIdx.x; k < count; k += gridDim.x) {
+    int64_t c = A.list[k];
+    int32_t *keys = A.gkeys + tab_off[k], *list = A.glist + tab_off[k];
+    int64_t *vals = A.gvals + tab_off[k];
+    int32_t occ = A.gocc[k];
     if (threadIdx.x == 0) { rc = 0; rs = 0; }
     __syncthreads();
-    agg_scan<W>(A, c, threadIdx.x, blockDim.x, keys, vals, (int)(T - 1));
-    __syncthreads();
-    agg_emit<1024>(A, c, threadIdx.x, blockDim.x, keys, vals, (int)T, &rc, &rs);
+    int64_t base = A.yoff[c];
+    for (int32_t t = threadIdx.x; t < occ; t += blockDim.x) {
+      int32_t s = list[t];
+      int32_t key = keys[s];
+      int64_t v = vals[s];
+      keys[s] = LD_EMPTY_KEY;
+      vals[s] = 0;
+      int32_t p = atomicAdd(&rc, 1);
+      A.ycol[base + p] = key;
+      A.yw[base + p] = v;
+      atomicAdd((unsigned long long *)&rs, (unsigned long long)v);
+    }
     __syncthreads();
     if (threadIdx.x == 0) { A.ydeg[c] = rc; A.Kout[c] = rs; }
     __syncthreads();
   }
+}
+
+__global__ void k_zero_occ(const int32_t *count_p, int32_t *occ) {
+  for (int64_t k = ld_gtid(); k < *count_p; k += ld_gstride()) occ[k] = 0;
 }
 
 __global__ void k_agg_bin(int64_t ncomm, const int64_t *yoff, int32_t *bins, DevCounters *cnt) {
@@ -426,7 +511,9 @@ void split_communities(leiden_handle *h, const LevelGraph &g) {
   k_split_init<<<grid_for(g.n, TB), TB, 0, s>>>(g.n, h->Cp, h->dS, h->dR, h->parent, list, h->dcnt);
   k_split_sample<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
   k_split_flatten<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent);
-  k_split_link_rest<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
+  cudaMemsetAsync(&h->dcnt->big_count, 0, sizeof(int32_t), s);
+  k_split_link_rest<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent, h->ibuf2);
+  k_split_link_big<<<h->sm_count, 1024, 0, s>>>(h->ibuf2, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
   k_split_compress<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent, h->Cp);
 }
 
@@ -463,10 +550,12 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
   k_member_deg<<<grid_for(n, TB), TB, 0, s>>>(n, h->cverts, g.deg, h->ibuf1);
   exclusive_scan_i32_to_i64(h->ibuf1, h->cflat, n, h->scan_tmp, s);
   cudaMemsetAsync(&h->dcnt->max_count, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(&h->dcnt->huge_slots, 0, sizeof(int64_t), s);
   k_yoff<<<grid_for(ncomm + 1, TB), TB, 0, s>>>(ncomm, h->coff, h->cflat, h->y_off[out], h->dcnt);
   cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4, s);
   k_agg_bin<<<grid_for(ncomm, TB), TB, 0, s>>>(ncomm, h->y_off[out], h->bins, h->dcnt);
   cudaMemcpyAsync(&h->hcnt->max_count, &h->dcnt->max_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&h->hcnt->huge_slots, &h->dcnt->huge_slots, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   int32_t maxc = h->hcnt->max_count;
   AggArgs A{};
@@ -496,14 +585,20 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
     else k_agg_block<int32_t><<<sms * 4, 256, 0, s>>>(A);
   }
   if (maxc > BIN_BLOCK_MAX) {
-    if (!ensure_hscratch(h, maxc)) { h->fatal = LEIDEN_ERR_OOM; h->err = "global table scratch"; return; }
+    // a table per listed community at once: at most huge_slots slots
+    if (!ensure_hslots(h, h->hcnt->huge_slots)) { h->fatal = LEIDEN_ERR_OOM; h->err = "global table scratch"; return; }
     A.list = h->bins + 2 * ncomm;
     A.count = &h->dcnt->bin_count[BIN_HUGE];
-    A.gslice = (int64_t)(h->hscratch_bytes / 12 / sms);
-    A.gkeys = (int32_t *)h->hscratch;
-    A.gvals = (int64_t *)((char *)h->hscratch + (size_t)A.gslice * sms * sizeof(int32_t));
-    if (g.w64) k_agg_huge<int64_t><<<sms, 1024, 0, s>>>(A);
-    else k_agg_huge<int32_t><<<sms, 1024, 0, s>>>(A);
+    A.gkeys = hs_keys(h);
+    A.gvals = hs_vals(h);
+    A.glist = hs_list(h);
+    A.gocc = h->hocc;
+    int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
+    launch_table_plan(A.list, A.count, nullptr, h->y_off[out], tab_off, ch_off, s);
+    k_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
+    if (g.w64) k_agg_chunk_scan<int64_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
+    else k_agg_chunk_scan<int32_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
+    k_agg_list_emit<<<sms * 2, 1024, 0, s>>>(A, tab_off);
   }
 }
 

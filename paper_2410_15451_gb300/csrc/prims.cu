@@ -210,6 +210,53 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, int64_t *vals, in
 }
 
 namespace {
+// One block: table and chunk offsets of the listed items (exclusive prefix
+// sums, totals at index count).  An item's size is deg32[v] or
+// off64[v+1] - off64[v]; its table has pow2 >= 2*size slots and it is cut
+// into chunks of TABLE_CHUNK.
+__global__ void __launch_bounds__(1024) k_table_plan(const int32_t *list, const int32_t *count_p,
+                                                      const int32_t *deg32, const int64_t *off64, int64_t *tab_off,
+                                                      int64_t *ch_off) {
+  __shared__ int64_t ws[32][2];
+  __shared__ int64_t carry[2];
+  int64_t count = *count_p;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) { carry[0] = 0; carry[1] = 0; }
+  __syncthreads();
+  for (int64_t base = 0; base < count; base += blockDim.x) {
+    int64_t k = base + threadIdx.x;
+    int64_t t = 0, c = 0;
+    if (k < count) {
+      int32_t v = list[k];
+      int64_t d = deg32 ? (int64_t)deg32[v] : off64[v + 1] - off64[v];
+      t = 1;
+      while (t < 2 * d) t <<= 1;
+      c = (d + TABLE_CHUNK - 1) / TABLE_CHUNK;
+    }
+    int64_t it = t, ic = c;  // inclusive warp scans
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t xt = __shfl_up_sync(LD_FULL, it, o), xc = __shfl_up_sync(LD_FULL, ic, o);
+      if (lane >= o) { it += xt; ic += xc; }
+    }
+    if (lane == 31) { ws[wid][0] = it; ws[wid][1] = ic; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int64_t a = carry[0], b = carry[1];
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+        int64_t x = ws[w][0], y = ws[w][1];
+        ws[w][0] = a; ws[w][1] = b;
+        a += x; b += y;
+      }
+      carry[0] = a; carry[1] = b;
+    }
+    __syncthreads();
+    if (k < count) { tab_off[k] = ws[wid][0] + it - t; ch_off[k] = ws[wid][1] + ic - c; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { tab_off[count] = carry[0]; ch_off[count] = carry[1]; }
+}
+
 __global__ void k_fill_i32(int32_t *p, int32_t v, int64_t n) {
   for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) p[i] = v;
 }
@@ -234,6 +281,11 @@ void launch_fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s) {
 void launch_fill_i64(int64_t *p, int64_t v, int64_t n, cudaStream_t s) {
   if (n > 0) k_fill_i64<<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
 }
+void launch_table_plan(const int32_t *list, const int32_t *count, const int32_t *deg32, const int64_t *off64,
+                       int64_t *tab_off, int64_t *ch_off, cudaStream_t s) {
+  k_table_plan<<<1, 1024, 0, s>>>(list, count, deg32, off64, tab_off, ch_off);
+}
+
 void launch_iota_i32(int32_t *p, int64_t n, cudaStream_t s) {
   if (n > 0) k_iota_i32<<<grid_for(n, 256), 256, 0, s>>>(p, n);
 }
