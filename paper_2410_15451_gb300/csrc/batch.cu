@@ -9,6 +9,7 @@
 namespace {
 
 constexpr int TB = 256;
+constexpr int MERGE_SMALL = 1024;  // touched rows up to this new length merge in one warp
 
 __device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, int32_t x) {
   int64_t lo = 0, hi = n;
@@ -125,7 +126,7 @@ __global__ void k_row_plan(const int32_t *rows, const int64_t *nrows_p, int vb, 
                            const uint64_t *nkey, const int64_t *nn_p, const int64_t *off, const int32_t *deg,
                            const int32_t *rcap, int32_t *dlo, int32_t *dhi, int32_t *ilo, int32_t *ihi, int64_t *len,
                            int64_t *dst, int32_t *newcap, double slack, int min_slack, int64_t colcap,
-                           DevCounters *cnt) {
+                           int32_t *olddeg, int32_t *large, DevCounters *cnt) {
   int64_t nrows = *nrows_p, nn = *nn_p;
   for (int64_t r = ld_gtid(); r < nrows; r += ld_gstride()) {
     uint64_t u = (uint64_t)rows[r];
@@ -134,6 +135,8 @@ __global__ void k_row_plan(const int32_t *rows, const int64_t *nrows_p, int vb, 
     dlo[r] = (int32_t)a; dhi[r] = (int32_t)b; ilo[r] = (int32_t)c; ihi[r] = (int32_t)d;
     int64_t L = (int64_t)deg[u] - (b - a) + (d - c);
     len[r] = L;
+    olddeg[r] = deg[u];
+    if (L > MERGE_SMALL) large[atomicAdd(&cnt->large_count, 1)] = (int32_t)r;
     dst[r] = off[u];
     newcap[r] = 0;
     if (L > rcap[u]) {
@@ -200,7 +203,6 @@ __global__ void k_merge_rows(const int32_t *rows, const int64_t *nrows_p, int vb
 // arcs are merged by one warp through shared memory, longer rows by one
 // block through the global merge buffer; each writes back after all its
 // reads are done, so the old row is never overwritten while still read.
-constexpr int MERGE_SMALL = 1024;
 constexpr int MERGE_WARPS = 4;
 
 struct MergeArgs {
@@ -276,34 +278,79 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge_small(MergeArgs A) {
   }
 }
 
-// Long rows: one block per row.  The row's deletion and new-arc keys are
-// staged in shared memory when they fit, so the per-element rank searches
-// do not go to global memory.
-constexpr int MERGE_STAGE = 2048;
-__global__ void __launch_bounds__(512) k_merge_large(MergeArgs A) {
-  __shared__ uint64_t sD[MERGE_STAGE];
-  __shared__ uint64_t sI[MERGE_STAGE];
-  int64_t nrows = *A.nrows_p;
-  for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
-    int64_t L = A.len[r];
-    if (L <= MERGE_SMALL) continue;
-    int64_t b = A.tmp_off[r];
-    int64_t nD = A.dhi[r] - A.dlo[r], nI = A.ihi[r] - A.ilo[r];
-    const uint64_t *D = A.dkey + A.dlo[r], *I = A.nkey + A.ilo[r];
-    if (nD <= MERGE_STAGE && nI <= MERGE_STAGE) {
-      for (int64_t k = threadIdx.x; k < nD; k += blockDim.x) sD[k] = D[k];
-      for (int64_t k = threadIdx.x; k < nI; k += blockDim.x) sI[k] = I[k];
-      __syncthreads();
-      D = sD;
-      I = sI;
+// Long rows in chunks any block may take (items k of `large`, chunk offsets
+// ch_off over the old row): elements go to the merge buffer by rank; the
+// first chunk of a row also places its new arcs.
+__global__ void __launch_bounds__(256) k_merge_chunks_write(MergeArgs A, const int32_t *large,
+                                                            const int32_t *count_p, const int64_t *ch_off) {
+  int64_t count = *count_p;
+  int64_t nch = ch_off[count];
+  uint64_t mask = (1ull << A.vb) - 1;
+  for (int64_t t = blockIdx.x; t < nch; t += gridDim.x) {
+    int64_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) >> 1;
+      if (ch_off[mid] <= t) lo = mid; else hi = mid - 1;
     }
-    merge_row_into(A, r, threadIdx.x, blockDim.x, A.tcol + b, A.tw + b, D, I);
-    __syncthreads();
+    int64_t r = large[lo];
     int32_t u = A.rows[r];
-    int64_t o = A.dst[r];
-    for (int64_t x = threadIdx.x; x < L; x += blockDim.x) { A.col[o + x] = A.tcol[b + x]; A.w[o + x] = A.tw[b + x]; }
-    if (threadIdx.x == 0) finish_row(A, r, u, L);
-    __syncthreads();
+    const int32_t *row = A.col + A.off[u];
+    const int32_t *roww = A.w + A.off[u];
+    int64_t dg = A.deg[u];
+    const uint64_t *D = A.dkey + A.dlo[r];
+    int64_t nD = A.dhi[r] - A.dlo[r];
+    const uint64_t *I = A.nkey + A.ilo[r];
+    const int64_t *IW = A.nw + A.ilo[r];
+    int64_t nI = A.ihi[r] - A.ilo[r];
+    uint64_t ubase = (uint64_t)u << A.vb;
+    int32_t *ocol = A.tcol + A.tmp_off[r];
+    int32_t *ow = A.tw + A.tmp_off[r];
+    int64_t c = t - ch_off[lo];
+    int64_t p0 = c * TABLE_CHUNK, p1 = p0 + TABLE_CHUNK < dg ? p0 + TABLE_CHUNK : dg;
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+      int32_t x = row[p];
+      int64_t dless = nD ? lower_bound_u64(D, nD, ubase | (uint64_t)x) : 0;
+      if (dless < nD && (D[dless] & mask) == (uint64_t)x) continue;
+      int64_t iless = nI ? lower_bound_u64(I, nI, ubase | (uint64_t)x) : 0;
+      int64_t o = (p - dless) + iless;
+      ocol[o] = x;
+      ow[o] = roww[p];
+    }
+    if (c == 0) {
+      for (int64_t k = threadIdx.x; k < nI; k += blockDim.x) {
+        int32_t y = (int32_t)(I[k] & mask);
+        int64_t rless = lower_bound_i32(row, dg, y);
+        int64_t dless = nD ? lower_bound_u64(D, nD, ubase | (uint64_t)y) : 0;
+        int64_t o = k + (rless - dless);
+        ocol[o] = y;
+        ow[o] = (int32_t)IW[k];
+      }
+    }
+  }
+}
+
+// Copy the merged long rows back (chunks over the new length) and record
+// the new degree and any relocation.
+__global__ void __launch_bounds__(256) k_merge_chunks_copy(MergeArgs A, const int32_t *large,
+                                                           const int32_t *count_p, const int64_t *ch_off) {
+  int64_t count = *count_p;
+  int64_t nch = ch_off[count];
+  for (int64_t t = blockIdx.x; t < nch; t += gridDim.x) {
+    int64_t lo = 0, hi = count - 1;
+    while (lo < hi) {
+      int64_t mid = (lo + hi + 1) >> 1;
+      if (ch_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    int64_t r = large[lo];
+    int64_t L = A.len[r];
+    int64_t c = t - ch_off[lo];
+    int64_t x0 = c * TABLE_CHUNK, x1 = x0 + TABLE_CHUNK < L ? x0 + TABLE_CHUNK : L;
+    int64_t b = A.tmp_off[r], o = A.dst[r];
+    for (int64_t x = x0 + threadIdx.x; x < x1; x += blockDim.x) {
+      A.col[o + x] = A.tcol[b + x];
+      A.w[o + x] = A.tw[b + x];
+    }
+    if (c == 0 && threadIdx.x == 0) finish_row(A, r, A.rows[r], L);
   }
 }
 
@@ -493,7 +540,7 @@ cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
   void *old[] = {b.dkey, b.dkey_alt, b.ikey, b.ikey_alt, b.iw, b.iw_alt, b.dw, b.flag,
                  b.pos, b.ins_state, b.ins_pos, b.row_dlo, b.row_dhi, b.row_ilo, b.row_ihi, b.row_len,
                  b.row_tmp_off, b.rows, b.ds_key, b.ds_key_alt, b.ds_w, b.ds_w_alt, b.ds_ukey, b.ds_uw,
-                 b.row_dst, b.row_newcap};
+                 b.row_dst, b.row_newcap, b.row_olddeg, b.row_large};
   for (void *p : old) release(h, p);
   int64_t arcs = 2 * cap;
   cudaError_t e = cudaSuccess;
@@ -519,6 +566,8 @@ cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
   chk(grow(h, &b.row_tmp_off, rows + 1));
   chk(grow(h, &b.row_dst, rows + 1));
   chk(grow(h, &b.row_newcap, rows + 1));
+  chk(grow(h, &b.row_olddeg, rows + 1));
+  chk(grow(h, &b.row_large, rows + 1));
   chk(grow(h, &b.ds_key, arcs));
   chk(grow(h, &b.ds_key_alt, arcs));
   chk(grow(h, &b.ds_w, arcs));
@@ -627,6 +676,7 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
     return fail(h, LEIDEN_ERR_OOM, "scan tmp");
   cudaMemsetAsync(&cnt->error, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&cnt->overflow, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(&cnt->large_count, 0, sizeof(int32_t), s);
   if (n_del + n_ins > 0)
     k_expand<<<grid_for(n_del + n_ins, TB), TB, 0, s>>>(d_del, n_del, d_ins, n_ins, n, vb, b.dkey, b.ikey, b.iw, cnt);
   radix_sort_u64(b.dkey, b.dkey_alt, nullptr, nullptr, nda, 2 * vb, h->scan_tmp, s);
@@ -684,7 +734,8 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
     cudaMemcpyAsync(counts + 3, h->lbuf0 + n, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
     k_row_plan<<<grid_for(std::min<int64_t>(n, nd + nn), TB), TB, 0, s>>>(
         b.rows, counts + 3, vb, DK, nd, NK, counts + 2, h->g_off, h->g_deg, h->g_rcap, b.row_dlo, b.row_dhi,
-        b.row_ilo, b.row_ihi, b.row_len, b.row_dst, b.row_newcap, h->p.slack, h->p.min_slack, h->g_cap, cnt);
+        b.row_ilo, b.row_ihi, b.row_len, b.row_dst, b.row_newcap, h->p.slack, h->p.min_slack, h->g_cap,
+        b.row_olddeg, b.row_large, cnt);
     cudaMemcpyAsync(b.hcounts + 3, counts + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     nrows = b.hcounts[3];
@@ -705,7 +756,13 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
                   b.row_dst, b.row_newcap, h->g_off, h->g_rcap};
       k_merge_small<<<grid_for((nrows + MERGE_WARPS - 1) / MERGE_WARPS, 1, h->sm_count * 16), MERGE_WARPS * 32, 0,
                       s>>>(M);
-      k_merge_large<<<h->sm_count * 2, 512, 0, s>>>(M);
+      // long rows: chunks over the old row, then chunks over the new row
+      int32_t *large = b.row_large;
+      const int32_t *nlarge = &cnt->large_count;
+      launch_table_plan(large, nlarge, b.row_olddeg, nullptr, h->lbuf0, h->lbuf1, s);
+      k_merge_chunks_write<<<h->sm_count * 16, 256, 0, s>>>(M, large, nlarge, h->lbuf1);
+      launch_table_plan(large, nlarge, nullptr, b.row_tmp_off, h->lbuf2, h->lbuf3, s);
+      k_merge_chunks_copy<<<h->sm_count * 16, 256, 0, s>>>(M, large, nlarge, h->lbuf3);
     } else {
       k_merge_rows<<<grid_for(nrows * 32, TB), TB, 0, s>>>(b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo,
                                                            b.row_dhi, b.row_ilo, b.row_ihi, b.row_tmp_off, h->g_off,

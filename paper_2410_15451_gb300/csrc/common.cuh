@@ -39,7 +39,7 @@ struct DevCounters {
   int64_t batch_dw;               // batch: change of 2m
   int64_t huge_slots;             // table slots the vertices above the block bin need
   int32_t big_count;              // splitting: long rows left to the block kernel
-  int32_t pad32;
+  int32_t large_count;            // batch apply: touched rows merged in chunks
   int64_t arena_used;             // next free arc slot of G^t (relocated rows go here)
 };
 

@@ -45,6 +45,8 @@ struct BatchBuffers {
   int64_t *row_tmp_off = nullptr;                        // offset into the merge buffer
   int64_t *row_dst = nullptr;                            // where the merged row goes
   int32_t *row_newcap = nullptr;                         // capacity of a relocated row (0: stays)
+  int32_t *row_olddeg = nullptr;                         // degree of the row before the batch
+  int32_t *row_large = nullptr;                          // touched rows merged in chunks
   uint64_t *ds_key = nullptr, *ds_key_alt = nullptr, *ds_ukey = nullptr;  // DS (src, C[dst]) pairs
   int64_t *ds_w = nullptr, *ds_w_alt = nullptr, *ds_uw = nullptr;
   int64_t *counts = nullptr;                             // device counts of the batch pipeline

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(1024) k_table_plan(const int32_t *list, const 
       int64_t d = deg32 ? (int64_t)deg32[v] : off64[v + 1] - off64[v];
       t = 1;
       while (t < 2 * d) t <<= 1;
-      c = (d + TABLE_CHUNK - 1) / TABLE_CHUNK;
+      c = d > 0 ? (d + TABLE_CHUNK - 1) / TABLE_CHUNK : 1;  // every item gets at least one chunk
     }
     int64_t it = t, ic = c;  // inclusive warp scans
 #pragma unroll
