@@ -15,7 +15,8 @@ e2e     = the same through leiden_update with host batch arrays and the
           membership copied back to the host, wall clock
 Also reported: speedup over GPU static Leiden on the final graph and the
 modularity gap, p50/p99 latency, the batch-size sweep, the roofline of the
-local-moving kernels, the oracle timed on the host cores (bounded sample),
+dominant kernel (local moving, warp degree bin), the library's kernel
+launches in the timed steps, the oracle timed on the host cores (bounded sample),
 and SM clocks sampled during the timed region.
 
 --impl reference times the CPU oracle (plain sequential C) on a bounded
@@ -203,7 +204,10 @@ def run_ours(args, rank, world, local_rank):
     size = max(1, int(round(args.batch_frac * E)))
     W, K = args.warmup, args.steps
     batches = make_batches(g, W + 2 * K, size, seed + 5)
-    gpu = L.Leiden(g.n, g.off, g.col, g.w, deterministic=not args.async_mode, cuda_stream=stream.cuda_stream)
+    # collect_stats=2: an event pair on the stream around every launch of the
+    # local-moving warp-bin kernel (the roofline kernel); no added syncs
+    gpu = L.Leiden(g.n, g.off, g.col, g.w, deterministic=not args.async_mode, cuda_stream=stream.cuda_stream,
+                   collect_stats=2)
     gpu.static()
     dev_batches = [(torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)) for d, i in batches]
     d_out = torch.empty(g.n, dtype=torch.int32, device=dev)
@@ -224,6 +228,7 @@ def run_ours(args, rank, world, local_rank):
     times_ms, lm_stats = [], []
     if args.profile:
         torch.cuda.cudart().cudaProfilerStart()
+    launches0 = L.leiden_kernel_launches()
     for k in range(W, W + K):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -235,6 +240,7 @@ def run_ours(args, rank, world, local_rank):
         times_ms.append(e0.elapsed_time(e1))
         lm_stats.append(gpu.stats())
     torch.cuda.synchronize()
+    gpu_launches = L.leiden_kernel_launches() - launches0
     if args.profile:
         torch.cuda.cudart().cudaProfilerStop()
     clk = clocks.stop()
@@ -276,6 +282,7 @@ def run_ours(args, rank, world, local_rank):
     result = dict(value=value, mean_ms=mean_ms, p50=float(np.percentile(times_ms, 50)),
                   p99=float(np.percentile(times_ms, 99)), e2e=e2e_value, q_df=q_df, q_static=q_static,
                   t_static=t_static, clk=clk, lm_stats=lm_stats, E=E, n=g.n, size=size, gen_s=gen_s,
+                  gpu_launches=gpu_launches,
                   e2e_p99=float(np.percentile(np.array(e2e_times) * 1e3, 99)))
     # batch-size sweep (each size continues the evolving graph)
     sweep = {}
@@ -308,19 +315,51 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
-def roofline_lm(stats_list, mean_ms):
-    """Algorithmic bytes of local moving per call (int32 col/w, int32 C, int64
-    K/Sigma): 16 B per vertex visit (offset, degree, K, C) + 12 B per scanned
-    arc (col, w, C[j]) ; achieved over the local-moving phase time."""
+ROOFLINE_KERNEL = "k_decide_warp"
+ROOFLINE_PROFILE = os.path.join(ROOT, "profiles", "k_decide_warp_rmat22_df1e-3.md")
+ROOFLINE_SOURCE = os.path.join(ROOT, "paper_2410_15451_gb300", "csrc", "move.cu")
+
+
+def ncu_traffic():
+    """DRAM bytes per launch of the roofline kernel from its committed ncu
+    summary (lines `traffic_bytes_per_launch: N` and `move_cu_sha256: H`);
+    None when there is none or the kernel source changed since the capture."""
+    import hashlib
+    import re
+
+    try:
+        text = open(ROOFLINE_PROFILE).read()
+        sha = hashlib.sha256(open(ROOFLINE_SOURCE, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"move_cu_sha256:\s*([0-9a-f]{64})", text)
+    if not t or not h or h.group(1) != sha:
+        return None
+    return float(t.group(1))
+
+
+def roofline_kernel(stats_list):
+    """The dominant kernel, local moving of the warp degree bin (k_decide_warp,
+    vertices of degree <= 128): algorithmic bytes counted on the device (40 B
+    per vertex visit + 12 B per scanned arc at level 0, 16 B above) over its
+    launches in the timed steps, divided by their summed CUDA-event time (an
+    event pair around each launch on the handle's stream)."""
     peak, src = hbm_peak()
-    vis = np.mean([s["lm_vertices"] for s in stats_list])
-    arcs = np.mean([s["lm_arcs"] for s in stats_list])
-    ms = np.mean([s["ms_move"] for s in stats_list]) if stats_list and stats_list[0]["ms_move"] > 0 else mean_ms
-    byts = 16 * vis + 12 * arcs
-    achieved = byts / (ms / 1e3) / 1e9
+    byts = sum(s["lm_warp_bytes"] for s in stats_list)
+    launches = sum(s["lm_warp_launches"] for s in stats_list)
+    ms = sum(s["ms_lm_warp"] for s in stats_list)
+    if launches == 0 or ms <= 0:
+        return None
+    per_launch = byts / launches
+    achieved = per_launch / (ms / launches / 1e3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
-            "kernel": "local-moving phase (k_collect + k_decide_* + k_apply_moves)"}
+            "traffic": ncu_traffic(), "kernel": ROOFLINE_KERNEL, "launches": launches,
+            "algorithmic_bytes_per_launch": per_launch, "ms_per_launch": ms / launches,
+            "visits": sum(s["lm_warp_vertices"] for s in stats_list),
+            "arcs": sum(s["lm_warp_arcs"] for s in stats_list),
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)" if src == "measured" else
+            "fallback 6.8 TB/s"}
 
 
 def main():
@@ -357,7 +396,8 @@ def main():
             "p50_ms": r["p50"], "p99_ms": r["p99"],
             "e2e": {"value": r["e2e"], "unit": "edges/s", "h2d_bytes_per_step": r["size"] * 12,
                     "d2h_bytes_per_step": r["n"] * 4, "p99_ms": r["e2e_p99"]},
-            "roofline": roofline_lm(r["lm_stats"], r["mean_ms"]),
+            "roofline": roofline_kernel(r["lm_stats"]),
+            "gpu_launches": r["gpu_launches"],
             "cpu_baseline": cb,
             "clocks": r["clk"],
             "sweep": r["sweep"],

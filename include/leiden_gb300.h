@@ -61,7 +61,9 @@ typedef struct {
   int32_t classes;        /* sub-sweeps per local-moving iteration, power of two, 4       */
   double slack;           /* spare CSR capacity per row as a fraction of its degree, 0.25 */
   int32_t min_slack;      /* minimum spare arcs per row, 4                                */
-  int32_t collect_stats;  /* 1: time each phase with CUDA events (adds syncs)             */
+  int32_t collect_stats;  /* bit 1: time each phase with CUDA events (adds syncs);        */
+                          /* bit 2: time each launch of the local-moving warp-bin kernel  */
+                          /*    with an event pair on the stream (no added syncs); 0      */
 } leiden_params;
 
 /* Counters and phase times of the last static/update call. */
@@ -83,6 +85,14 @@ typedef struct {
   double ms_refine;            /* renumber + split + refinement (collect_stats)          */
   double ms_aggregate;         /* dense renumber + aggregation (collect_stats)           */
   double ms_track;             /* lookup + tracking (collect_stats)                      */
+  /* The local-moving kernel of the warp degree bin (vertices of degree <= 128): */
+  int64_t lm_warp_launches;    /* launches timed (collect_stats bit 2)                    */
+  int64_t lm_warp_vertices;    /* vertex visits                                          */
+  int64_t lm_warp_arcs;        /* arcs scanned                                           */
+  int64_t lm_warp_bytes;       /* algorithmic bytes: 40 per visit (list entry, offset,   */
+                               /* degree, C, K, Sigma and size of C) + per arc 8 (col,   */
+                               /* C of the neighbour) + the weight (4 at level 0, else 8)*/
+  double ms_lm_warp;           /* summed device time of the timed launches               */
 } leiden_stats;
 
 typedef struct leiden_handle leiden_handle;
@@ -187,6 +197,12 @@ leiden_status leiden_get_trace(leiden_handle *h, int64_t *trace);
 
 /* Counters and phase times of the last call. */
 leiden_status leiden_get_stats(leiden_handle *h, leiden_stats *stats);
+
+/* Number of CUDA kernels this library has launched in the process since it
+ * was loaded, over all handles and threads (a relaxed atomic counter; read
+ * it before and after a call to count that call's launches).  Library
+ * bookkeeping with no counterpart in the paper. */
+int64_t leiden_kernel_launches(void);
 
 /* Message for the last failed call on h (or for the last failed
  * leiden_create when h is NULL).  Never NULL. */

@@ -8,6 +8,39 @@
 
 #include "internal.h"
 
+#include <atomic>
+
+static std::atomic<int64_t> g_launches{0};
+
+void ld_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void kt_begin(leiden_handle *h) {
+  if (!(h->p.collect_stats & 2)) return;
+  size_t need = 2 * (size_t)(h->kt_used + 1);
+  while (h->kt_ev.size() < need) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+    h->kt_ev.push_back(e);
+  }
+  cudaEventRecord(h->kt_ev[2 * h->kt_used], h->stream);
+}
+
+void kt_end(leiden_handle *h) {
+  if (!(h->p.collect_stats & 2) || h->kt_ev.size() < 2 * (size_t)(h->kt_used + 1)) return;
+  cudaEventRecord(h->kt_ev[2 * h->kt_used + 1], h->stream);
+  h->kt_used++;
+}
+
+void kt_resolve(leiden_handle *h) {
+  for (int k = 0; k < h->kt_used; k++) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, h->kt_ev[2 * k], h->kt_ev[2 * k + 1]) == cudaSuccess) h->kt_ms += ms;
+    else cudaGetLastError();
+  }
+  h->kt_launches += h->kt_used;
+  h->kt_used = 0;
+}
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -83,7 +116,7 @@ float ev_ms(leiden_handle *h, int a, int b) {
 }
 
 void mark(leiden_handle *h, int k) {
-  if (h->p.collect_stats) cudaEventRecord(h->ev[k], h->stream);
+  if (h->p.collect_stats & 1) cudaEventRecord(h->ev[k], h->stream);
 }
 
 // Alg. leiden: passes of local moving, subset renumbering, splitting,
@@ -95,13 +128,16 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   const leiden_params &p = h->p;
   int64_t N = h->n;
   memset(h->trace, 0, sizeof(h->trace));
+  h->kt_used = 0;
+  h->kt_ms = 0;
+  h->kt_launches = 0;
   // initialisation
   mark_unprocessed_from_flags(h, h->dV, N);
   launch_iota_i32(h->Ctop, N, s);
   CK(cudaMemcpyAsync(h->Cp, h->C, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(h->Kp, h->K, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(h->Sp, h->Sig, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemsetAsync(&h->dcnt->processed, 0, 5 * sizeof(int64_t), s));
+  CK(cudaMemsetAsync(&h->dcnt->processed, 0, 8 * sizeof(int64_t), s));  // processed .. warp_bytes
   int64_t m2 = h->m2;
   LevelGraph g = level0(h);
   double tau = p.tau;
@@ -124,6 +160,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
       CK(cudaMemsetAsync(&h->dcnt->moves, 0, sizeof(int64_t), s));
       for (int cls = 0; cls < p.classes; cls++) lm_subsweep(h, g, cls, lp == 0 ? in_range : nullptr, dynamic);
       sync_counters(h);
+      kt_resolve(h);
       CK(cudaGetLastError());
       CKF();
       i128 dq = read_i128(h->hcnt->dq);
@@ -160,7 +197,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     sync_counters(h);
     tr[2] = h->hcnt->list_count;
     mark(h, 4);
-    if (h->p.collect_stats) {
+    if (h->p.collect_stats & 1) {
       cudaEventSynchronize(h->ev[4]);
       t_move += ev_ms(h, 2, 3);
       t_ref += ev_ms(h, 3, 4);
@@ -200,7 +237,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     slot ^= 1;
     tau /= p.tau_drop;
     mark(h, 5);
-    if (h->p.collect_stats) {
+    if (h->p.collect_stats & 1) {
       cudaEventSynchronize(h->ev[5]);
       t_agg += ev_ms(h, 4, 5);
     }
@@ -218,7 +255,13 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   st.lm_moves = moves_total;
   st.refine_vertices = h->hcnt->ref_processed;
   st.refine_arcs = h->hcnt->ref_arcs;
-  if (h->p.collect_stats) {
+  st.lm_warp_vertices = h->hcnt->warp_processed;
+  st.lm_warp_arcs = h->hcnt->warp_arcs;
+  st.lm_warp_bytes = h->hcnt->warp_bytes;
+  kt_resolve(h);
+  st.lm_warp_launches = h->kt_launches;
+  st.ms_lm_warp = h->kt_ms;
+  if (h->p.collect_stats & 1) {
     st.ms_move = t_move;
     st.ms_refine = t_ref;
     st.ms_aggregate = t_agg;
@@ -240,7 +283,7 @@ leiden_status finish_call(leiden_handle *h, int32_t *out, bool device_out) {
 leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_del, const leiden_edge *d_ins,
                         int64_t n_ins, leiden_mode mode) {
   h->stats = leiden_stats{};
-  if (h->p.collect_stats) cudaEventRecord(h->ev[0], h->stream);
+  if (h->p.collect_stats & 1) cudaEventRecord(h->ev[0], h->stream);
   leiden_status st = batch_apply_and_mark(h, d_del, n_del, d_ins, n_ins, (int)mode);
   if (st != LEIDEN_OK) return st;
   mark(h, 1);
@@ -253,7 +296,7 @@ leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_de
   h->g_huge_slots = h->hcnt->huge_slots;
   st = run_leiden(h, 1, mode == LEIDEN_DS ? h->dV : nullptr);
   if (st != LEIDEN_OK) return st;
-  if (h->p.collect_stats) {
+  if (h->p.collect_stats & 1) {
     cudaEventSynchronize(h->ev[7]);
     h->stats.ms_batch = ev_ms(h, 0, 1);
     h->stats.ms_total = ev_ms(h, 0, 7);
@@ -440,7 +483,7 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   if (st != LEIDEN_OK) return st;
   cudaStream_t s = h->stream;
   h->stats = leiden_stats{};
-  if (h->p.collect_stats) cudaEventRecord(h->ev[0], s);
+  if (h->p.collect_stats & 1) cudaEventRecord(h->ev[0], s);
   int64_t N = h->n;
   recompute_weights(h);
   level_maxdeg(h, h->g_deg, N);
@@ -459,7 +502,7 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   st = run_leiden(h, 0, nullptr);
   if (st != LEIDEN_OK) return st;
   h->has_static = true;
-  if (h->p.collect_stats) {
+  if (h->p.collect_stats & 1) {
     cudaEventSynchronize(h->ev[7]);
     h->stats.ms_total = ev_ms(h, 0, 7);
   }
@@ -613,6 +656,8 @@ leiden_status leiden_get_stats(leiden_handle *h, leiden_stats *stats) {
   return LEIDEN_OK;
 }
 
+int64_t leiden_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
 const char *leiden_last_error(leiden_handle *h) {
   if (!h) return g_create_error.c_str();
   return h->err.c_str();
@@ -626,6 +671,8 @@ void leiden_destroy(leiden_handle *h) {
     if (q) cudaFree(q);
   if (h->hcnt) cudaFreeHost(h->hcnt);
   for (auto &ev : h->ev)
+    if (ev) cudaEventDestroy(ev);
+  for (auto &ev : h->kt_ev)
     if (ev) cudaEventDestroy(ev);
   delete h;
 }

@@ -618,9 +618,9 @@ static leiden_status rebuild_graph(leiden_handle *h, int64_t nrows_host, const i
   int64_t n = h->n;
   BatchBuffers &b = h->b;
   int64_t *len = h->lbuf0, *cap = h->lbuf1;
-  k_row_lengths<<<grid_for(n, TB), TB, 0, s>>>(h->g_deg, n, len);
-  k_touched_lengths<<<grid_for(nrows_host, TB), TB, 0, s>>>(b.rows, nrows_dev, b.row_len, len);
-  k_capacity<<<grid_for(n, TB), TB, 0, s>>>(len, n, h->p.slack, h->p.min_slack, cap);
+  ld_note_launch(), k_row_lengths<<<grid_for(n, TB), TB, 0, s>>>(h->g_deg, n, len);
+  ld_note_launch(), k_touched_lengths<<<grid_for(nrows_host, TB), TB, 0, s>>>(b.rows, nrows_dev, b.row_len, len);
+  ld_note_launch(), k_capacity<<<grid_for(n, TB), TB, 0, s>>>(len, n, h->p.slack, h->p.min_slack, cap);
   int64_t *new_off = nullptr;
   if (grow(h, &new_off, n + 1) != cudaSuccess) return fail(h, LEIDEN_ERR_OOM, "rebuild: offsets");
   if (ensure_scan_tmp(h, scan_tmp_bytes(n + 1)) != cudaSuccess) return fail(h, LEIDEN_ERR_OOM, "scan tmp");
@@ -633,12 +633,12 @@ static leiden_status rebuild_graph(leiden_handle *h, int64_t nrows_host, const i
   if (grow(h, &new_col, total) != cudaSuccess || grow(h, &new_w, total) != cudaSuccess ||
       grow(h, &new_deg, n) != cudaSuccess)
     return fail(h, LEIDEN_ERR_OOM, "rebuild: arcs");
-  k_set_rcap<<<grid_for(n, TB), TB, 0, s>>>(cap, n, h->g_rcap);
+  ld_note_launch(), k_set_rcap<<<grid_for(n, TB), TB, 0, s>>>(cap, n, h->g_rcap);
   cudaMemcpyAsync(&h->dcnt->arena_used, &used, sizeof(int64_t), cudaMemcpyHostToDevice, s);
   int32_t *rowsrc = h->ibuf2;
   launch_fill_i32(rowsrc, -1, n, s);
-  k_rowsrc<<<grid_for(nrows_host, TB), TB, 0, s>>>(b.rows, nrows_dev, rowsrc);
-  k_copy_rows_rebuild<<<grid_for(n * 32, TB), TB, 0, s>>>(n, h->g_off, h->g_deg, h->g_col, h->g_w, rowsrc,
+  ld_note_launch(), k_rowsrc<<<grid_for(nrows_host, TB), TB, 0, s>>>(b.rows, nrows_dev, rowsrc);
+  ld_note_launch(), k_copy_rows_rebuild<<<grid_for(n * 32, TB), TB, 0, s>>>(n, h->g_off, h->g_deg, h->g_col, h->g_w, rowsrc,
                                                           b.row_tmp_off, b.row_len, b.tmp_col, b.tmp_w, new_off,
                                                           new_deg, new_col, new_w);
   cudaStreamSynchronize(s);
@@ -678,7 +678,7 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   cudaMemsetAsync(&cnt->overflow, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&cnt->large_count, 0, sizeof(int32_t), s);
   if (n_del + n_ins > 0)
-    k_expand<<<grid_for(n_del + n_ins, TB), TB, 0, s>>>(d_del, n_del, d_ins, n_ins, n, vb, b.dkey, b.ikey, b.iw, cnt);
+    ld_note_launch(), k_expand<<<grid_for(n_del + n_ins, TB), TB, 0, s>>>(d_del, n_del, d_ins, n_ins, n, vb, b.dkey, b.ikey, b.iw, cnt);
   radix_sort_u64(b.dkey, b.dkey_alt, nullptr, nullptr, nda, 2 * vb, h->scan_tmp, s);
   radix_sort_u64(b.ikey, b.ikey_alt, b.iw, b.iw_alt, nia, 2 * vb, h->scan_tmp, s);
   // deduplicate: deletions collapse (-> DK), insertions add up (-> IK, IW)
@@ -687,16 +687,16 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   uint64_t *DK = b.dkey_alt, *IK = b.ikey_alt;
   int64_t *IW = b.iw_alt, *DW = b.dw;
   if (nda > 0) {
-    k_head_flags<<<grid_for(nda, TB), TB, 0, s>>>(b.dkey, nda, b.flag);
+    ld_note_launch(), k_head_flags<<<grid_for(nda, TB), TB, 0, s>>>(b.dkey, nda, b.flag);
     exclusive_scan_i32_to_i64(b.flag, b.pos, nda, h->scan_tmp, s);
-    k_unique<<<grid_for(nda, TB), TB, 0, s>>>(b.dkey, nullptr, nda, b.flag, b.pos, DK, nullptr);
+    ld_note_launch(), k_unique<<<grid_for(nda, TB), TB, 0, s>>>(b.dkey, nullptr, nda, b.flag, b.pos, DK, nullptr);
     cudaMemcpyAsync(counts + 0, b.pos + nda, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   }
   if (nia > 0) {
-    k_head_flags<<<grid_for(nia, TB), TB, 0, s>>>(b.ikey, nia, b.flag);
+    ld_note_launch(), k_head_flags<<<grid_for(nia, TB), TB, 0, s>>>(b.ikey, nia, b.flag);
     exclusive_scan_i32_to_i64(b.flag, b.pos, nia, h->scan_tmp, s);
     cudaMemsetAsync(IW, 0, (size_t)nia * sizeof(int64_t), s);
-    k_unique<<<grid_for(nia, TB), TB, 0, s>>>(b.ikey, b.iw, nia, b.flag, b.pos, IK, IW);
+    ld_note_launch(), k_unique<<<grid_for(nia, TB), TB, 0, s>>>(b.ikey, b.iw, nia, b.flag, b.pos, IK, IW);
     cudaMemcpyAsync(counts + 1, b.pos + nia, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   }
   cudaMemcpyAsync(b.hcounts, counts, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -704,15 +704,15 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   int64_t nd = b.hcounts[0], ni = b.hcounts[1];
   // deletions must exist (stored weight -> DW); insertions: existing or new
   if (nd > 0)
-    k_check_deletions<<<grid_for(nd, TB), TB, 0, s>>>(DK, nd, vb, h->g_off, h->g_deg, h->g_col, h->g_w, DW, cnt);
+    ld_note_launch(), k_check_deletions<<<grid_for(nd, TB), TB, 0, s>>>(DK, nd, vb, h->g_off, h->g_deg, h->g_col, h->g_w, DW, cnt);
   uint64_t *NK = b.ikey;  // new insertions, compacted in sorted order
   int64_t *NW = b.iw;
   if (ni > 0) {
-    k_classify_insertions<<<grid_for(ni, TB), TB, 0, s>>>(IK, ni, DK, nd, vb, h->g_off, h->g_deg, h->g_col,
+    ld_note_launch(), k_classify_insertions<<<grid_for(ni, TB), TB, 0, s>>>(IK, ni, DK, nd, vb, h->g_off, h->g_deg, h->g_col,
                                                           b.ins_state, b.ins_pos);
-    k_new_flags<<<grid_for(ni, TB), TB, 0, s>>>(b.ins_state, ni, b.flag);
+    ld_note_launch(), k_new_flags<<<grid_for(ni, TB), TB, 0, s>>>(b.ins_state, ni, b.flag);
     exclusive_scan_i32_to_i64(b.flag, b.pos, ni, h->scan_tmp, s);
-    k_compact_new<<<grid_for(ni, TB), TB, 0, s>>>(IK, IW, ni, b.flag, b.pos, NK, NW);
+    ld_note_launch(), k_compact_new<<<grid_for(ni, TB), TB, 0, s>>>(IK, IW, ni, b.flag, b.pos, NK, NW);
     cudaMemcpyAsync(counts + 2, b.pos + ni, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   }
   cudaMemcpyAsync(b.hcounts + 2, counts + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -727,12 +727,12 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   int64_t nrows = 0, tmp_total = 0;
   if (nd + nn > 0) {
     cudaMemsetAsync(touched, 0, (size_t)n * sizeof(int32_t), s);
-    if (nd > 0) k_mark_touched<<<grid_for(nd, TB), TB, 0, s>>>(DK, nd, vb, touched);
-    if (nn > 0) k_mark_touched<<<grid_for(nn, TB), TB, 0, s>>>(NK, nn, vb, touched);
+    if (nd > 0) ld_note_launch(), k_mark_touched<<<grid_for(nd, TB), TB, 0, s>>>(DK, nd, vb, touched);
+    if (nn > 0) ld_note_launch(), k_mark_touched<<<grid_for(nn, TB), TB, 0, s>>>(NK, nn, vb, touched);
     exclusive_scan_i32_to_i64(touched, h->lbuf0, n, h->scan_tmp, s);
-    k_compact_flags<<<grid_for(n, TB), TB, 0, s>>>(touched, h->lbuf0, n, b.rows);
+    ld_note_launch(), k_compact_flags<<<grid_for(n, TB), TB, 0, s>>>(touched, h->lbuf0, n, b.rows);
     cudaMemcpyAsync(counts + 3, h->lbuf0 + n, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-    k_row_plan<<<grid_for(std::min<int64_t>(n, nd + nn), TB), TB, 0, s>>>(
+    ld_note_launch(), k_row_plan<<<grid_for(std::min<int64_t>(n, nd + nn), TB), TB, 0, s>>>(
         b.rows, counts + 3, vb, DK, nd, NK, counts + 2, h->g_off, h->g_deg, h->g_rcap, b.row_dlo, b.row_dhi,
         b.row_ilo, b.row_ihi, b.row_len, b.row_dst, b.row_newcap, h->p.slack, h->p.min_slack, h->g_cap,
         b.row_olddeg, b.row_large, cnt);
@@ -748,23 +748,23 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   bool overflow = nrows > 0 && h->hcnt->overflow != 0;
   if (ensure_tmp_rows(h, tmp_total) != cudaSuccess) return fail(h, LEIDEN_ERR_OOM, "merge buffer");
   // ---- apply: from here on the handle changes
-  if (ni > 0) k_add_existing<<<grid_for(ni, TB), TB, 0, s>>>(b.ins_pos, b.ins_state, IW, ni, h->g_w);
+  if (ni > 0) ld_note_launch(), k_add_existing<<<grid_for(ni, TB), TB, 0, s>>>(b.ins_pos, b.ins_state, IW, ni, h->g_w);
   if (nrows > 0) {
     if (!overflow) {
       MergeArgs M{b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo, b.row_dhi, b.row_ilo, b.row_ihi, b.row_len,
                   b.row_tmp_off, h->g_off, h->g_deg, h->g_col, h->g_w, b.tmp_col, b.tmp_w,
                   b.row_dst, b.row_newcap, h->g_off, h->g_rcap};
-      k_merge_small<<<grid_for((nrows + MERGE_WARPS - 1) / MERGE_WARPS, 1, h->sm_count * 16), MERGE_WARPS * 32, 0,
+      ld_note_launch(), k_merge_small<<<grid_for((nrows + MERGE_WARPS - 1) / MERGE_WARPS, 1, h->sm_count * 16), MERGE_WARPS * 32, 0,
                       s>>>(M);
       // long rows: chunks over the old row, then chunks over the new row
       int32_t *large = b.row_large;
       const int32_t *nlarge = &cnt->large_count;
       launch_table_plan(large, nlarge, b.row_olddeg, nullptr, h->lbuf0, h->lbuf1, s);
-      k_merge_chunks_write<<<h->sm_count * 16, 256, 0, s>>>(M, large, nlarge, h->lbuf1);
+      ld_note_launch(), k_merge_chunks_write<<<h->sm_count * 16, 256, 0, s>>>(M, large, nlarge, h->lbuf1);
       launch_table_plan(large, nlarge, nullptr, b.row_tmp_off, h->lbuf2, h->lbuf3, s);
-      k_merge_chunks_copy<<<h->sm_count * 16, 256, 0, s>>>(M, large, nlarge, h->lbuf3);
+      ld_note_launch(), k_merge_chunks_copy<<<h->sm_count * 16, 256, 0, s>>>(M, large, nlarge, h->lbuf3);
     } else {
-      k_merge_rows<<<grid_for(nrows * 32, TB), TB, 0, s>>>(b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo,
+      ld_note_launch(), k_merge_rows<<<grid_for(nrows * 32, TB), TB, 0, s>>>(b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo,
                                                            b.row_dhi, b.row_ilo, b.row_ihi, b.row_tmp_off, h->g_off,
                                                            h->g_deg, h->g_col, h->g_w, b.tmp_col, b.tmp_w);
       leiden_status st = rebuild_graph(h, nrows, counts + 3);
@@ -780,35 +780,35 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   } else {
     cudaMemsetAsync(dV, 0, (size_t)n, s);
     if (mode == LEIDEN_DF) {
-      if (nd + ni > 0) k_mark_df<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, dV);
+      if (nd + ni > 0) ld_note_launch(), k_mark_df<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, dV);
     } else {
       cudaMemsetAsync(h->dE, 0, (size_t)n, s);
       cudaMemsetAsync(h->dCf, 0, (size_t)n, s);
-      if (nd > 0) k_mark_ds_del<<<grid_for(nd, TB), TB, 0, s>>>(DK, nd, vb, h->C, dV, h->dE, h->dCf);
+      if (nd > 0) ld_note_launch(), k_mark_ds_del<<<grid_for(nd, TB), TB, 0, s>>>(DK, nd, vb, h->C, dV, h->dE, h->dCf);
       if (ni > 0) {
         // H of each insertion source: (src, C[dst]) pairs, sorted, runs summed
-        k_ds_keys<<<grid_for(ni, TB), TB, 0, s>>>(IK, IW, ni, vb, h->C, b.ds_key, b.ds_w);
+        ld_note_launch(), k_ds_keys<<<grid_for(ni, TB), TB, 0, s>>>(IK, IW, ni, vb, h->C, b.ds_key, b.ds_w);
         radix_sort_u64(b.ds_key, b.ds_key_alt, b.ds_w, b.ds_w_alt, ni, 64, h->scan_tmp, s);
-        k_head_flags<<<grid_for(ni, TB), TB, 0, s>>>(b.ds_key, ni, b.flag);
+        ld_note_launch(), k_head_flags<<<grid_for(ni, TB), TB, 0, s>>>(b.ds_key, ni, b.flag);
         exclusive_scan_i32_to_i64(b.flag, b.pos, ni, h->scan_tmp, s);
         cudaMemsetAsync(b.ds_uw, 0, (size_t)ni * sizeof(int64_t), s);
-        k_unique<<<grid_for(ni, TB), TB, 0, s>>>(b.ds_key, b.ds_w, ni, b.flag, b.pos, b.ds_ukey, b.ds_uw);
-        k_ds_best<<<grid_for(ni, TB), TB, 0, s>>>(b.ds_ukey, b.ds_uw, b.pos + ni, vb, h->K, h->Sig, cnt, dV, h->dE,
+        ld_note_launch(), k_unique<<<grid_for(ni, TB), TB, 0, s>>>(b.ds_key, b.ds_w, ni, b.flag, b.pos, b.ds_ukey, b.ds_uw);
+        ld_note_launch(), k_ds_best<<<grid_for(ni, TB), TB, 0, s>>>(b.ds_ukey, b.ds_uw, b.pos + ni, vb, h->K, h->Sig, cnt, dV, h->dE,
                                                   h->dCf);
       }
-      k_ds_expand_neighbours<<<grid_for(n * 32, TB), TB, 0, s>>>(h->dE, n, h->g_off, h->g_deg, h->g_col, dV);
-      k_ds_expand_communities<<<grid_for(n, TB), TB, 0, s>>>(h->dCf, h->C, n, dV);
+      ld_note_launch(), k_ds_expand_neighbours<<<grid_for(n * 32, TB), TB, 0, s>>>(h->dE, n, h->g_off, h->g_deg, h->g_col, dV);
+      ld_note_launch(), k_ds_expand_communities<<<grid_for(n, TB), TB, 0, s>>>(h->dCf, h->C, n, dV);
     }
   }
   // ---- Alg. update, then Alg. leidenmk (dS, dR; reset dSigma of refined)
   cudaMemsetAsync(h->dS, 0, (size_t)n, s);
   cudaMemsetAsync(h->dR, 0, (size_t)n, s);
   if (nd + ni > 0) {
-    k_update_weights<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, DW, nd, IK, IW, ni, vb, h->C, h->K, h->Sig, h->dSig,
+    ld_note_launch(), k_update_weights<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, DW, nd, IK, IW, ni, vb, h->C, h->K, h->Sig, h->dSig,
                                                            cnt);
-    k_mark_communities<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, h->Sig, h->dSig,
+    ld_note_launch(), k_mark_communities<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, h->Sig, h->dSig,
                                                              h->p.tau_refine, h->dS, h->dR);
-    k_reset_changes<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, h->dR, h->dSig);
+    ld_note_launch(), k_reset_changes<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, h->dR, h->dSig);
   }
   return LEIDEN_OK;
 }

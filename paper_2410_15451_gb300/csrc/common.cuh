@@ -33,6 +33,9 @@ struct DevCounters {
   int64_t moves;                  // local-moving moves
   int64_t ref_processed;          // refinement vertex visits
   int64_t ref_arcs;               // refinement arcs scanned
+  int64_t warp_processed;         // local moving, warp bin: vertex visits
+  int64_t warp_arcs;              // local moving, warp bin: arcs scanned
+  int64_t warp_bytes;             // local moving, warp bin: algorithmic bytes
   int64_t m2;                     // 2m (sum of arc weights), device copy
   int64_t sigma_intra;            // modularity: intra-community arc weight
   unsigned long long sq[2];       // modularity: sum of Sigma_c^2 (int128)

@@ -126,12 +126,28 @@ struct leiden_handle {
   int64_t up_cap = 0;
 
   cudaEvent_t ev[8] = {};
+  // Kernel timer (collect_stats bit 2): event pairs around the launches of
+  // the local-moving warp-bin kernel, resolved at the next host sync.
+  std::vector<cudaEvent_t> kt_ev;
+  int kt_used = 0;      // pairs recorded since the last resolve
+  double kt_ms = 0;     // summed device time of the resolved pairs
+  int64_t kt_launches = 0;
   leiden_stats stats{};
   int64_t trace[2 + 10 * 25] = {};
   std::string err;
   leiden_status fatal = LEIDEN_OK;  // set by a launcher that could not run
   std::vector<void *> owned;  // every cudaMalloc of the handle
 };
+
+// Every kernel launch of the library is written `ld_note_launch(), k<<<...>>>(...)`
+// so that leiden_kernel_launches() counts them.
+void ld_note_launch();
+
+// Kernel timer of the local-moving warp-bin kernel: begin/end around a launch
+// (no-ops unless collect_stats has bit 2), resolve after a stream sync.
+void kt_begin(leiden_handle *h);
+void kt_end(leiden_handle *h);
+void kt_resolve(leiden_handle *h);
 
 // Message returned by leiden_last_error(NULL) (calls without a handle).
 void set_handle_free_error(const std::string &msg);

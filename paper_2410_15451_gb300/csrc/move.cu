@@ -220,6 +220,14 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) k_decide_warp(Args A) {
     if (lane == 0) { visits++; arcs += dg; moves += moved; dq += g; }
   }
   if (lane == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
+  if (KIND == KIND_MOVE && lane == 0 && visits) {
+    // algorithmic bytes: per visit the list entry, off, deg, C[i], K[i],
+    // Sigma[C[i]], size[C[i]] (40 B); per arc col, C[j] and the weight
+    atomicAdd((unsigned long long *)&A.cnt->warp_processed, (unsigned long long)visits);
+    atomicAdd((unsigned long long *)&A.cnt->warp_arcs, (unsigned long long)arcs);
+    atomicAdd((unsigned long long *)&A.cnt->warp_bytes,
+              (unsigned long long)(40 * visits + (8 + (int64_t)sizeof(W)) * arcs));
+  }
 }
 
 // Block-wide merge of per-thread Best values (result valid in thread 0).
@@ -378,8 +386,9 @@ __global__ void k_collect(int64_t n, uint32_t *unproc, int cls, int classes_mask
     bool work = take && (!in_range || in_range[v]);
     int bin = -1;
     if (work) {
+      // a vertex without arcs has no candidate community: taking it is its visit
       int dg = deg[v];
-      bin = dg <= BIN_WARP_MAX ? BIN_WARP : (dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE);
+      bin = dg == 0 ? -1 : dg <= BIN_WARP_MAX ? BIN_WARP : (dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE);
     }
 #pragma unroll
     for (int b = 0; b < NBINS; b++) {
@@ -456,8 +465,8 @@ __global__ void k_refine_collect(const int32_t *cand_in, const int32_t *count_in
     }
     int bin = -1;
     if (keep) {
-      int dg = deg[i];
-      bin = dg <= BIN_WARP_MAX ? BIN_WARP : (dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE);
+      int dg = deg[i];  // without arcs: no proposal (prop stays -1)
+      bin = dg == 0 ? -1 : dg <= BIN_WARP_MAX ? BIN_WARP : (dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE);
     }
     uint32_t km = __ballot_sync(LD_FULL, keep);
     if (km) {
@@ -536,12 +545,14 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
     if (b == BIN_BLOCK && g.maxdeg <= BIN_WARP_MAX) continue;
     if (b == BIN_WARP) {
       int grid = sms * 8;
-      if (g.w64) k_decide_warp<int64_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
-      else k_decide_warp<int32_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
+      if (KIND == KIND_MOVE) kt_begin(h);
+      if (g.w64) ld_note_launch(), k_decide_warp<int64_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
+      else ld_note_launch(), k_decide_warp<int32_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
+      if (KIND == KIND_MOVE) kt_end(h);
     } else if (b == BIN_BLOCK) {
       int grid = sms * 4;
-      if (g.w64) k_decide_block<int64_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
-      else k_decide_block<int32_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
+      if (g.w64) ld_note_launch(), k_decide_block<int64_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
+      else ld_note_launch(), k_decide_block<int32_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
     } else {
       // tables for every listed vertex at once: at most huge_slots slots
       if (!ensure_hslots(h, g.huge_slots)) { h->fatal = LEIDEN_ERR_OOM; h->err = "global table scratch"; return; }
@@ -552,10 +563,10 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
       A.gslice = 0;
       int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
       launch_table_plan(A.list, A.count, g.deg, nullptr, tab_off, ch_off, s);
-      k_huge_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
-      if (g.w64) k_huge_scan<int64_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
-      else k_huge_scan<int32_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
-      k_huge_decide<KIND><<<sms * 2, HUGE_THREADS, 0, s>>>(A, tab_off);
+      ld_note_launch(), k_huge_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
+      if (g.w64) ld_note_launch(), k_huge_scan<int64_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
+      else ld_note_launch(), k_huge_scan<int32_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
+      ld_note_launch(), k_huge_decide<KIND><<<sms * 2, HUGE_THREADS, 0, s>>>(A, tab_off);
     }
   }
 }
@@ -602,26 +613,26 @@ int32_t *hs_list(leiden_handle *h) { return (int32_t *)((char *)h->hscratch + (s
 
 void lm_prepare(leiden_handle *h, const LevelGraph &g) {
   cudaMemsetAsync(h->csize, 0, (size_t)g.n * sizeof(int32_t), h->stream);
-  k_sizes<<<grid_for(g.n, 256), 256, 0, h->stream>>>(h->Cp, g.n, h->csize);
+  ld_note_launch(), k_sizes<<<grid_for(g.n, 256), 256, 0, h->stream>>>(h->Cp, g.n, h->csize);
 }
 
 void lm_subsweep(leiden_handle *h, const LevelGraph &g, int cls, const uint8_t *in_range, int dynamic) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4 + sizeof(int32_t), s);  // bins + movers
-  k_collect<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, h->unproc, cls, h->p.classes - 1, in_range, g.deg, h->bins,
+  ld_note_launch(), k_collect<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, h->unproc, cls, h->p.classes - 1, in_range, g.deg, h->bins,
                                                h->dcnt);
   Args A = make_args(h, g);
   A.in_range = in_range;
   A.dynamic = dynamic;
   launch_bins<KIND_MOVE>(h, g, A);
   if (h->p.deterministic)
-    k_apply_moves<<<h->sm_count * 4, 256, 0, s>>>(h->movers, h->mtarget, h->dcnt, h->Cp, h->Sp, h->Kp, h->csize);
+    ld_note_launch(), k_apply_moves<<<h->sm_count * 4, 256, 0, s>>>(h->movers, h->mtarget, h->dcnt, h->Cp, h->Sp, h->Kp, h->csize);
 }
 
 void refine_reset(leiden_handle *h, const LevelGraph &g) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->cand_count[0], 0, sizeof(int32_t), s);
-  k_refine_reset<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, h->CB, h->dR, h->Cp, h->Sp, h->Kp, h->prop, h->cand,
+  ld_note_launch(), k_refine_reset<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, h->CB, h->dR, h->Cp, h->Sp, h->Kp, h->prop, h->cand,
                                                     h->dcnt);
 }
 
@@ -634,9 +645,9 @@ void refine_round(leiden_handle *h, const LevelGraph &g, int slot) {
   cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4, s);
   cudaMemsetAsync(cout, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&h->dcnt->accepted, 0, sizeof(int32_t), s);
-  k_refine_collect<<<grid_for(g.n, 256), 256, 0, s>>>(in, cin, out, cout, g.n, h->Cp, h->Sp, h->Kp, g.deg, h->prop,
+  ld_note_launch(), k_refine_collect<<<grid_for(g.n, 256), 256, 0, s>>>(in, cin, out, cout, g.n, h->Cp, h->Sp, h->Kp, g.deg, h->prop,
                                                       h->bins, h->dcnt, 0);
   Args A = make_args(h, g);
   launch_bins<KIND_REFINE>(h, g, A);
-  k_refine_accept<<<h->sm_count * 4, 256, 0, s>>>(out, cout, h->prop, h->Cp, h->Sp, h->Kp, h->dcnt);
+  ld_note_launch(), k_refine_accept<<<h->sm_count * 4, 256, 0, s>>>(out, cout, h->prop, h->Cp, h->Sp, h->Kp, h->dcnt);
 }

@@ -116,9 +116,9 @@ extern "C" leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *d_o
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int sms = 152;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_na_clear<<<grid_for(n, 256), 256, 0, s>>>(n, scr);
-  k_na_rows<<<sms * 16, 256, 0, s>>>(n, d_offsets, d_cols, d_weights, d_membership, scr);
-  k_na_sq<<<grid_for(n, 256), 256, 0, s>>>(n, scr);
+  ld_note_launch(), k_na_clear<<<grid_for(n, 256), 256, 0, s>>>(n, scr);
+  ld_note_launch(), k_na_rows<<<sms * 16, 256, 0, s>>>(n, d_offsets, d_cols, d_weights, d_membership, scr);
+  ld_note_launch(), k_na_sq<<<grid_for(n, 256), 256, 0, s>>>(n, scr);
   int64_t cnt[5] = {0, 0, 0, 0, 0};
   e = cudaMemcpyAsync(cnt, scr + NOALLOC_MAX_VERTICES, sizeof(cnt), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -495,10 +495,10 @@ __global__ void k_maxdeg(int64_t n, const int32_t *deg, DevCounters *cnt) {
 void subset_renumber(leiden_handle *h, int64_t n) {
   cudaStream_t s = h->stream;
   int g = grid_for(n, TB);
-  k_sr_init<<<g, TB, 0, s>>>(n, h->rep, h->S2, h->dS2, h->dR2);
-  k_sr_min<<<g, TB, 0, s>>>(n, h->Cp, h->rep);
-  k_sr_rekey<<<g, TB, 0, s>>>(n, h->rep, h->Sp, h->dS, h->dR, h->S2, h->dS2, h->dR2);
-  k_sr_remap<<<g, TB, 0, s>>>(n, h->rep, h->Cp);
+  ld_note_launch(), k_sr_init<<<g, TB, 0, s>>>(n, h->rep, h->S2, h->dS2, h->dR2);
+  ld_note_launch(), k_sr_min<<<g, TB, 0, s>>>(n, h->Cp, h->rep);
+  ld_note_launch(), k_sr_rekey<<<g, TB, 0, s>>>(n, h->rep, h->Sp, h->dS, h->dR, h->S2, h->dS2, h->dR2);
+  ld_note_launch(), k_sr_remap<<<g, TB, 0, s>>>(n, h->rep, h->Cp);
   std::swap(h->Sp, h->S2);
   std::swap(h->dS, h->dS2);
   std::swap(h->dR, h->dR2);
@@ -508,31 +508,31 @@ void split_communities(leiden_handle *h, const LevelGraph &g) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->split_count, 0, sizeof(int32_t), s);
   int32_t *list = h->ibuf1;
-  k_split_init<<<grid_for(g.n, TB), TB, 0, s>>>(g.n, h->Cp, h->dS, h->dR, h->parent, list, h->dcnt);
-  k_split_sample<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
-  k_split_flatten<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent);
+  ld_note_launch(), k_split_init<<<grid_for(g.n, TB), TB, 0, s>>>(g.n, h->Cp, h->dS, h->dR, h->parent, list, h->dcnt);
+  ld_note_launch(), k_split_sample<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
+  ld_note_launch(), k_split_flatten<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent);
   cudaMemsetAsync(&h->dcnt->big_count, 0, sizeof(int32_t), s);
-  k_split_link_rest<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent, h->ibuf2);
-  k_split_link_big<<<h->sm_count, 1024, 0, s>>>(h->ibuf2, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
-  k_split_compress<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent, h->Cp);
+  ld_note_launch(), k_split_link_rest<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent, h->ibuf2);
+  ld_note_launch(), k_split_link_big<<<h->sm_count, 1024, 0, s>>>(h->ibuf2, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
+  ld_note_launch(), k_split_compress<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent, h->Cp);
 }
 
 void count_communities(leiden_handle *h, int64_t n) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->list_count, 0, sizeof(int32_t), s);
-  k_count_roots<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->dcnt);
+  ld_note_launch(), k_count_roots<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->dcnt);
 }
 
 void renumber_dense(leiden_handle *h, int64_t n) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(h->ibuf0, 0, (size_t)n * sizeof(int32_t), s);
-  k_used<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0);
+  ld_note_launch(), k_used<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0);
   exclusive_scan_i32_to_i64(h->ibuf0, h->lbuf0, n, h->scan_tmp, s);
-  k_rank<<<grid_for(n, TB), TB, 0, s>>>(n, h->lbuf0, h->Cp);
+  ld_note_launch(), k_rank<<<grid_for(n, TB), TB, 0, s>>>(n, h->lbuf0, h->Cp);
 }
 
 void lookup_dendrogram(leiden_handle *h) {
-  k_lookup<<<grid_for(h->n, TB), TB, 0, h->stream>>>(h->n, h->Cp, h->Ctop);
+  ld_note_launch(), k_lookup<<<grid_for(h->n, TB), TB, 0, h->stream>>>(h->n, h->Cp, h->Ctop);
 }
 
 // Aggregate level g by its dense membership Cp into slot `out`; K'' goes to
@@ -542,18 +542,18 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
   int64_t n = g.n;
   // community vertices CSR
   cudaMemsetAsync(h->ibuf0, 0, (size_t)ncomm * sizeof(int32_t), s);
-  k_member_count<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0);
+  ld_note_launch(), k_member_count<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0);
   exclusive_scan_i32_to_i64(h->ibuf0, h->coff, ncomm, h->scan_tmp, s);
   cudaMemcpyAsync(h->lbuf0, h->coff, (size_t)ncomm * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-  k_member_fill<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, (unsigned long long *)h->lbuf0, h->cverts);
+  ld_note_launch(), k_member_fill<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, (unsigned long long *)h->lbuf0, h->cverts);
   // flat arc offsets of the members, and the super-row offsets
-  k_member_deg<<<grid_for(n, TB), TB, 0, s>>>(n, h->cverts, g.deg, h->ibuf1);
+  ld_note_launch(), k_member_deg<<<grid_for(n, TB), TB, 0, s>>>(n, h->cverts, g.deg, h->ibuf1);
   exclusive_scan_i32_to_i64(h->ibuf1, h->cflat, n, h->scan_tmp, s);
   cudaMemsetAsync(&h->dcnt->max_count, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&h->dcnt->huge_slots, 0, sizeof(int64_t), s);
-  k_yoff<<<grid_for(ncomm + 1, TB), TB, 0, s>>>(ncomm, h->coff, h->cflat, h->y_off[out], h->dcnt);
+  ld_note_launch(), k_yoff<<<grid_for(ncomm + 1, TB), TB, 0, s>>>(ncomm, h->coff, h->cflat, h->y_off[out], h->dcnt);
   cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4, s);
-  k_agg_bin<<<grid_for(ncomm, TB), TB, 0, s>>>(ncomm, h->y_off[out], h->bins, h->dcnt);
+  ld_note_launch(), k_agg_bin<<<grid_for(ncomm, TB), TB, 0, s>>>(ncomm, h->y_off[out], h->bins, h->dcnt);
   cudaMemcpyAsync(&h->hcnt->max_count, &h->dcnt->max_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&h->hcnt->huge_slots, &h->dcnt->huge_slots, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
@@ -576,13 +576,13 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
   int sms = h->sm_count;
   A.list = h->bins;
   A.count = &h->dcnt->bin_count[BIN_WARP];
-  if (g.w64) k_agg_warp<int64_t><<<sms * 8, AGG_WARPS * 32, 0, s>>>(A);
-  else k_agg_warp<int32_t><<<sms * 8, AGG_WARPS * 32, 0, s>>>(A);
+  if (g.w64) ld_note_launch(), k_agg_warp<int64_t><<<sms * 8, AGG_WARPS * 32, 0, s>>>(A);
+  else ld_note_launch(), k_agg_warp<int32_t><<<sms * 8, AGG_WARPS * 32, 0, s>>>(A);
   if (maxc > BIN_WARP_MAX) {
     A.list = h->bins + ncomm;
     A.count = &h->dcnt->bin_count[BIN_BLOCK];
-    if (g.w64) k_agg_block<int64_t><<<sms * 4, 256, 0, s>>>(A);
-    else k_agg_block<int32_t><<<sms * 4, 256, 0, s>>>(A);
+    if (g.w64) ld_note_launch(), k_agg_block<int64_t><<<sms * 4, 256, 0, s>>>(A);
+    else ld_note_launch(), k_agg_block<int32_t><<<sms * 4, 256, 0, s>>>(A);
   }
   if (maxc > BIN_BLOCK_MAX) {
     // a table per listed community at once: at most huge_slots slots
@@ -595,30 +595,30 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
     A.gocc = h->hocc;
     int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
     launch_table_plan(A.list, A.count, nullptr, h->y_off[out], tab_off, ch_off, s);
-    k_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
-    if (g.w64) k_agg_chunk_scan<int64_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
-    else k_agg_chunk_scan<int32_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
-    k_agg_list_emit<<<sms * 2, 1024, 0, s>>>(A, tab_off);
+    ld_note_launch(), k_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
+    if (g.w64) ld_note_launch(), k_agg_chunk_scan<int64_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
+    else ld_note_launch(), k_agg_chunk_scan<int32_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
+    ld_note_launch(), k_agg_list_emit<<<sms * 2, 1024, 0, s>>>(A, tab_off);
   }
 }
 
 void reset_next_pass(leiden_handle *h, int64_t ncomm, int out) {
   (void)out;
   cudaStream_t s = h->stream;
-  k_next_pass<<<grid_for(ncomm, TB), TB, 0, s>>>(ncomm, h->S2, h->Kp, h->Sp, h->Cp, h->dR, h->dS);
+  ld_note_launch(), k_next_pass<<<grid_for(ncomm, TB), TB, 0, s>>>(ncomm, h->S2, h->Kp, h->Sp, h->Cp, h->dR, h->dS);
   mark_all_unprocessed(h, ncomm);
 }
 
 void mark_all_unprocessed(leiden_handle *h, int64_t n) {
-  k_bits_all<<<grid_for((n + 31) / 32, TB), TB, 0, h->stream>>>(n, h->unproc);
+  ld_note_launch(), k_bits_all<<<grid_for((n + 31) / 32, TB), TB, 0, h->stream>>>(n, h->unproc);
 }
 
 void mark_unprocessed_from_flags(leiden_handle *h, const uint8_t *flags, int64_t n) {
-  k_bits_from_flags<<<grid_for(n, TB), TB, 0, h->stream>>>(n, flags, h->unproc);
+  ld_note_launch(), k_bits_from_flags<<<grid_for(n, TB), TB, 0, h->stream>>>(n, flags, h->unproc);
 }
 
 void level_maxdeg(leiden_handle *h, const int32_t *deg, int64_t n) {
   cudaMemsetAsync(&h->dcnt->max_count, 0, sizeof(int32_t), h->stream);
   cudaMemsetAsync(&h->dcnt->huge_slots, 0, sizeof(int64_t), h->stream);
-  k_maxdeg<<<grid_for(n, TB), TB, 0, h->stream>>>(n, deg, h->dcnt);
+  ld_note_launch(), k_maxdeg<<<grid_for(n, TB), TB, 0, h->stream>>>(n, deg, h->dcnt);
 }

@@ -91,9 +91,9 @@ cudaError_t scan_impl(const T *in, int64_t *out, int64_t n, void *tmp, cudaStrea
   int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   int64_t *tile = (int64_t *)tmp;
   if (n > 0) {
-    scan_tile_reduce<T><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, tile);
-    scan_tile_offsets<<<1, SCAN_BLOCK, 0, s>>>(tile, ntiles, out + n);
-    scan_tile_apply<T><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, n, tile);
+    ld_note_launch(), scan_tile_reduce<T><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, tile);
+    ld_note_launch(), scan_tile_offsets<<<1, SCAN_BLOCK, 0, s>>>(tile, ntiles, out + n);
+    ld_note_launch(), scan_tile_apply<T><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, n, tile);
   } else {
     cudaMemsetAsync(out, 0, sizeof(int64_t), s);
   }
@@ -194,10 +194,10 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, int64_t *vals, in
   int64_t *vsrc = vals, *vdst = vals_alt;
   int passes = 0;
   for (int shift = 0; shift < bits; shift += 8) {
-    rs_hist<<<(unsigned)nblocks, RS_BLOCK, 0, s>>>(src, n, shift, nblocks, hist);
+    ld_note_launch(), rs_hist<<<(unsigned)nblocks, RS_BLOCK, 0, s>>>(src, n, shift, nblocks, hist);
     cudaError_t e = exclusive_scan_i64(hist, offs, hlen, stmp, s);
     if (e != cudaSuccess) return e;
-    rs_scatter<<<(unsigned)nblocks, RS_BLOCK, 0, s>>>(src, vsrc, dst, vdst, n, shift, nblocks, offs);
+    ld_note_launch(), rs_scatter<<<(unsigned)nblocks, RS_BLOCK, 0, s>>>(src, vsrc, dst, vdst, n, shift, nblocks, offs);
     uint64_t *t = src; src = dst; dst = t;
     int64_t *tv = vsrc; vsrc = vdst; vdst = tv;
     passes++;
@@ -276,16 +276,16 @@ int grid_for(int64_t n, int block, int max_blocks) {
 }
 
 void launch_fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s) {
-  if (n > 0) k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
+  if (n > 0) ld_note_launch(), k_fill_i32<<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
 }
 void launch_fill_i64(int64_t *p, int64_t v, int64_t n, cudaStream_t s) {
-  if (n > 0) k_fill_i64<<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
+  if (n > 0) ld_note_launch(), k_fill_i64<<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
 }
 void launch_table_plan(const int32_t *list, const int32_t *count, const int32_t *deg32, const int64_t *off64,
                        int64_t *tab_off, int64_t *ch_off, cudaStream_t s) {
-  k_table_plan<<<1, 1024, 0, s>>>(list, count, deg32, off64, tab_off, ch_off);
+  ld_note_launch(), k_table_plan<<<1, 1024, 0, s>>>(list, count, deg32, off64, tab_off, ch_off);
 }
 
 void launch_iota_i32(int32_t *p, int64_t n, cudaStream_t s) {
-  if (n > 0) k_iota_i32<<<grid_for(n, 256), 256, 0, s>>>(p, n);
+  if (n > 0) ld_note_launch(), k_iota_i32<<<grid_for(n, 256), 256, 0, s>>>(p, n);
 }

@@ -162,8 +162,8 @@ void track_communities(leiden_handle *h) {
   cudaStream_t s = h->stream;
   int64_t N = h->n;
   int gN = grid_for(N, TB);
-  k_tr_clear<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals);
-  k_tr_insert<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, h->K, h->tr_cap, h->tr_keys, h->tr_vals);
+  ld_note_launch(), k_tr_clear<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals);
+  ld_note_launch(), k_tr_insert<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, h->K, h->tr_cap, h->tr_keys, h->tr_vals);
   long long *bw = (long long *)h->lbuf0, *ow = (long long *)h->lbuf1;
   int32_t *bc = h->ibuf0, *ob = h->ibuf1, *used = h->ibuf2;
   launch_fill_i64((int64_t *)bw, -1, N, s);
@@ -171,24 +171,24 @@ void track_communities(leiden_handle *h) {
   launch_fill_i64((int64_t *)ow, -1, N, s);
   launch_fill_i32(ob, INT_MAX, N, s);
   cudaMemsetAsync(used, 0, (size_t)N * sizeof(int32_t), s);
-  k_tr_best_new_w<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals, bw);
-  k_tr_best_new_c<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals, bw, bc);
-  k_tr_best_old_w<<<gN, TB, 0, s>>>(N, bc, bw, ow);
-  k_tr_best_old_b<<<gN, TB, 0, s>>>(N, bc, bw, ow, ob);
-  k_tr_new_used<<<gN, TB, 0, s>>>(N, h->Ctop, used);
+  ld_note_launch(), k_tr_best_new_w<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals, bw);
+  ld_note_launch(), k_tr_best_new_c<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals, bw, bc);
+  ld_note_launch(), k_tr_best_old_w<<<gN, TB, 0, s>>>(N, bc, bw, ow);
+  ld_note_launch(), k_tr_best_old_b<<<gN, TB, 0, s>>>(N, bc, bw, ow, ob);
+  ld_note_launch(), k_tr_new_used<<<gN, TB, 0, s>>>(N, h->Ctop, used);
   int32_t *unmatched = h->rep, *freef = h->prop;
-  k_tr_flags<<<gN, TB, 0, s>>>(N, used, ob, bc, unmatched, freef);
+  ld_note_launch(), k_tr_flags<<<gN, TB, 0, s>>>(N, used, ob, bc, unmatched, freef);
   int64_t *urank = h->lbuf2, *frank = h->lbuf3;
   exclusive_scan_i32_to_i64(unmatched, urank, N, h->scan_tmp, s);
   exclusive_scan_i32_to_i64(freef, frank, N, h->scan_tmp, s);
   int32_t *flist = h->parent, *map = h->CB;
-  k_tr_free_list<<<gN, TB, 0, s>>>(N, freef, frank, flist);
+  ld_note_launch(), k_tr_free_list<<<gN, TB, 0, s>>>(N, freef, frank, flist);
   uint8_t *matched = h->dE;
   cudaMemsetAsync(matched, 0, (size_t)N, s);
-  k_tr_map<<<gN, TB, 0, s>>>(N, used, ob, urank, flist, map, matched);
+  ld_note_launch(), k_tr_map<<<gN, TB, 0, s>>>(N, used, ob, urank, flist, map, matched);
   cudaMemsetAsync(h->Sig, 0, (size_t)N * sizeof(int64_t), s);
-  k_tr_relabel<<<gN, TB, 0, s>>>(N, h->Ctop, map, h->K, h->C, h->Sig);
-  k_tr_dsig<<<gN, TB, 0, s>>>(N, matched, h->dSig);
+  ld_note_launch(), k_tr_relabel<<<gN, TB, 0, s>>>(N, h->Ctop, map, h->K, h->C, h->Sig);
+  ld_note_launch(), k_tr_dsig<<<gN, TB, 0, s>>>(N, matched, h->dSig);
 }
 
 // sigma (intra arcs) and sum Sigma_c^2 of membership C on G^t.
@@ -199,14 +199,14 @@ void modularity_terms(leiden_handle *h, const int32_t *C) {
   cudaMemsetAsync(Sig, 0, (size_t)N * sizeof(int64_t), s);
   cudaMemsetAsync(&h->dcnt->sigma_intra, 0, sizeof(int64_t), s);
   cudaMemsetAsync(&h->dcnt->sq[0], 0, 2 * sizeof(unsigned long long), s);
-  k_sig_of<<<grid_for(N, TB), TB, 0, s>>>(N, C, h->K, Sig);
-  k_sigma_intra<<<grid_for(N * 32, TB), TB, 0, s>>>(N, h->g_off, h->g_deg, h->g_col, h->g_w, C, h->dcnt);
-  k_sq<<<grid_for(N, TB), TB, 0, s>>>(N, Sig, h->dcnt);
+  ld_note_launch(), k_sig_of<<<grid_for(N, TB), TB, 0, s>>>(N, C, h->K, Sig);
+  ld_note_launch(), k_sigma_intra<<<grid_for(N * 32, TB), TB, 0, s>>>(N, h->g_off, h->g_deg, h->g_col, h->g_w, C, h->dcnt);
+  ld_note_launch(), k_sq<<<grid_for(N, TB), TB, 0, s>>>(N, Sig, h->dcnt);
 }
 
 // K = row sums of G^t and 2m.
 void recompute_weights(leiden_handle *h) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->m2, 0, sizeof(int64_t), s);
-  k_rowsum<<<grid_for(h->n * 32, TB), TB, 0, s>>>(h->n, h->g_off, h->g_deg, h->g_w, h->K, h->dcnt);
+  ld_note_launch(), k_rowsum<<<grid_for(h->n * 32, TB), TB, 0, s>>>(h->n, h->g_off, h->g_deg, h->g_w, h->K, h->dcnt);
 }

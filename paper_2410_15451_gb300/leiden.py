@@ -35,7 +35,9 @@ class leiden_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "passes", "lm_iterations", "lm_vertices", "lm_arcs", "lm_moves", "refine_vertices", "refine_arcs",
         "aggregate_arcs", "affected", "communities", "batch_arcs")] + [(k, ctypes.c_double) for k in (
-        "ms_total", "ms_batch", "ms_move", "ms_refine", "ms_aggregate", "ms_track")]
+        "ms_total", "ms_batch", "ms_move", "ms_refine", "ms_aggregate", "ms_track")] + [
+        (k, ctypes.c_int64) for k in ("lm_warp_launches", "lm_warp_vertices", "lm_warp_arcs", "lm_warp_bytes")] + [
+        ("ms_lm_warp", ctypes.c_double)]
 
 
 class LeidenError(RuntimeError):
@@ -76,6 +78,8 @@ def load():
     lib.leiden_get_affected.argtypes = [vp, vp]
     lib.leiden_get_trace.argtypes = [vp, vp]
     lib.leiden_get_stats.argtypes = [vp, P(leiden_stats)]
+    lib.leiden_kernel_launches.argtypes = []
+    lib.leiden_kernel_launches.restype = i64
     lib.leiden_last_error.argtypes = [vp]
     lib.leiden_last_error.restype = ctypes.c_char_p
     lib.leiden_destroy.argtypes = [vp]
@@ -205,6 +209,10 @@ def leiden_get_stats(h) -> dict:
     s = leiden_stats()
     _check(h, load().leiden_get_stats(h, ctypes.byref(s)))
     return {k: getattr(s, k) for k, _ in leiden_stats._fields_}
+
+
+def leiden_kernel_launches() -> int:
+    return int(load().leiden_kernel_launches())
 
 
 def leiden_last_error(h=None) -> str:

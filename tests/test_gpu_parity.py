@@ -230,3 +230,25 @@ def test_device_entry_point_matches_host_entry_point():
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
     L.leiden_update_device(b.h, dd, len(dels), di, len(ins), L.LEIDEN_DF, out)
     assert np.array_equal(out.cpu().numpy(), ca)
+
+
+def test_stats_timers_and_launch_counter_leave_results_unchanged():
+    """collect_stats (phase events, per-launch events of the warp-bin
+    local-moving kernel) only observes: the result is the same bit for bit;
+    the launch counter counts this library's kernels."""
+    g = synth.rmat(14, seed=36)
+    a = L.Leiden(g.n, g.off, g.col, g.w, collect_stats=3)
+    b = L.Leiden(g.n, g.off, g.col, g.w)
+    assert np.array_equal(a.static(), b.static())
+    dels, ins = synth.random_batch(g, 500, seed=37)
+    n0 = L.leiden_kernel_launches()
+    ca = a.update(dels, ins, L.LEIDEN_DF)
+    n1 = L.leiden_kernel_launches()
+    cb = b.update(dels, ins, L.LEIDEN_DF)
+    assert np.array_equal(ca, cb)
+    assert n1 - n0 >= 10
+    s = a.stats()
+    assert s["lm_warp_launches"] > 0 and s["ms_lm_warp"] > 0 and s["ms_move"] > 0
+    v, e = s["lm_warp_vertices"], s["lm_warp_arcs"]
+    assert 0 < v <= s["lm_vertices"] and 0 < e <= s["lm_arcs"]
+    assert 40 * v + 12 * e <= s["lm_warp_bytes"] <= 40 * v + 16 * e
