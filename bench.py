@@ -15,7 +15,7 @@ e2e     = the same through leiden_update with host batch arrays and the
           membership copied back to the host, wall clock
 Also reported: speedup over GPU static Leiden on the final graph and the
 modularity gap, p50/p99 latency, the batch-size sweep, the roofline of the
-dominant kernel (local moving, warp degree bin), the library's kernel
+dominant local-moving kernel (measured live), the library's kernel
 launches in the timed steps, the oracle timed on the host cores (bounded sample),
 and SM clocks sampled during the timed region.
 
@@ -205,7 +205,7 @@ def run_ours(args, rank, world, local_rank):
     W, K = args.warmup, args.steps
     batches = make_batches(g, W + 2 * K, size, seed + 5)
     # collect_stats=2: an event pair on the stream around every launch of the
-    # local-moving warp-bin kernel (the roofline kernel); no added syncs
+    # local-moving kernels (the roofline kernels); no added syncs
     gpu = L.Leiden(g.n, g.off, g.col, g.w, deterministic=not args.async_mode, cuda_stream=stream.cuda_stream,
                    collect_stats=2)
     gpu.static()
@@ -315,15 +315,16 @@ def run_ours(args, rank, world, local_rank):
     return result
 
 
-ROOFLINE_KERNEL = "k_decide_warp"
-ROOFLINE_PROFILE = os.path.join(ROOT, "profiles", "k_decide_warp_rmat22_df1e-3.md")
+LMK_NAMES = ("k_decide_warp", "k_decide_block", "k_huge_scan")
+ROOFLINE_PROFILE = os.path.join(ROOT, "profiles", "lm_kernels_rmat22_df1e-3.md")
 ROOFLINE_SOURCE = os.path.join(ROOT, "paper_2410_15451_gb300", "csrc", "move.cu")
 
 
-def ncu_traffic():
-    """DRAM bytes per launch of the roofline kernel from its committed ncu
-    summary (lines `traffic_bytes_per_launch: N` and `move_cu_sha256: H`);
-    None when there is none or the kernel source changed since the capture."""
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary of the
+    local-moving kernels (lines `traffic_bytes_per_launch[<kernel>]: N` and
+    `move_cu_sha256: H`); None when absent or when the kernel source changed
+    since the capture."""
     import hashlib
     import re
 
@@ -332,34 +333,38 @@ def ncu_traffic():
         sha = hashlib.sha256(open(ROOFLINE_SOURCE, "rb").read()).hexdigest()
     except OSError:
         return None
-    t = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    t = re.search(r"traffic_bytes_per_launch\[" + re.escape(kernel) + r"\]:\s*([0-9.eE+]+)", text)
     h = re.search(r"move_cu_sha256:\s*([0-9a-f]{64})", text)
     if not t or not h or h.group(1) != sha:
         return None
     return float(t.group(1))
 
 
-def roofline_kernel(stats_list):
-    """The dominant kernel, local moving of the warp degree bin (k_decide_warp,
-    vertices of degree <= 128): algorithmic bytes counted on the device (40 B
-    per vertex visit + 12 B per scanned arc at level 0, 16 B above) over its
-    launches in the timed steps, divided by their summed CUDA-event time (an
-    event pair around each launch on the handle's stream)."""
+def roofline_kernels(stats_list):
+    """Live roofline of the local-moving kernels (the dominant step): the
+    algorithmic bytes counted on the device over their launches in the timed
+    steps, divided by their summed CUDA-event time (an event pair around each
+    launch on the handle's stream).  Returns (dominant kernel's entry, all)."""
     peak, src = hbm_peak()
-    byts = sum(s["lm_warp_bytes"] for s in stats_list)
-    launches = sum(s["lm_warp_launches"] for s in stats_list)
-    ms = sum(s["ms_lm_warp"] for s in stats_list)
-    if launches == 0 or ms <= 0:
-        return None
-    per_launch = byts / launches
-    achieved = per_launch / (ms / launches / 1e3) / 1e9
-    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": ncu_traffic(), "kernel": ROOFLINE_KERNEL, "launches": launches,
-            "algorithmic_bytes_per_launch": per_launch, "ms_per_launch": ms / launches,
-            "visits": sum(s["lm_warp_vertices"] for s in stats_list),
-            "arcs": sum(s["lm_warp_arcs"] for s in stats_list),
-            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)" if src == "measured" else
-            "fallback 6.8 TB/s"}
+    out = {}
+    for k, name in enumerate(LMK_NAMES):
+        launches = sum(s["lmk_launches"][k] for s in stats_list)
+        ms = sum(s["lmk_ms"][k] for s in stats_list)
+        if launches == 0 or ms <= 0:
+            continue
+        per_launch = sum(s["lmk_bytes"][k] for s in stats_list) / launches
+        achieved = per_launch / (ms / launches / 1e3) / 1e9
+        out[name] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": ncu_traffic(name), "kernel": name, "launches": launches, "ms_total": ms,
+                     "algorithmic_bytes_per_launch": per_launch, "ms_per_launch": ms / launches,
+                     "visits": sum(s["lmk_vertices"][k] for s in stats_list),
+                     "arcs": sum(s["lmk_arcs"][k] for s in stats_list),
+                     "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)" if src == "measured"
+                     else "fallback 6.8 TB/s"}
+    if not out:
+        return None, {}
+    dom = max(out.values(), key=lambda r: r["ms_total"])
+    return dom, out
 
 
 def main():
@@ -396,7 +401,8 @@ def main():
             "p50_ms": r["p50"], "p99_ms": r["p99"],
             "e2e": {"value": r["e2e"], "unit": "edges/s", "h2d_bytes_per_step": r["size"] * 12,
                     "d2h_bytes_per_step": r["n"] * 4, "p99_ms": r["e2e_p99"]},
-            "roofline": roofline_kernel(r["lm_stats"]),
+            "roofline": roofline_kernels(r["lm_stats"])[0],
+            "roofline_lm_kernels": roofline_kernels(r["lm_stats"])[1],
             "gpu_launches": r["gpu_launches"],
             "cpu_baseline": cb,
             "clocks": r["clk"],

@@ -62,7 +62,7 @@ typedef struct {
   double slack;           /* spare CSR capacity per row as a fraction of its degree, 0.25 */
   int32_t min_slack;      /* minimum spare arcs per row, 4                                */
   int32_t collect_stats;  /* bit 1: time each phase with CUDA events (adds syncs);        */
-                          /* bit 2: time each launch of the local-moving warp-bin kernel  */
+                          /* bit 2: time each launch of the local-moving kernels          */
                           /*    with an event pair on the stream (no added syncs); 0      */
 } leiden_params;
 
@@ -85,14 +85,17 @@ typedef struct {
   double ms_refine;            /* renumber + split + refinement (collect_stats)          */
   double ms_aggregate;         /* dense renumber + aggregation (collect_stats)           */
   double ms_track;             /* lookup + tracking (collect_stats)                      */
-  /* The local-moving kernel of the warp degree bin (vertices of degree <= 128): */
-  int64_t lm_warp_launches;    /* launches timed (collect_stats bit 2)                    */
-  int64_t lm_warp_vertices;    /* vertex visits                                          */
-  int64_t lm_warp_arcs;        /* arcs scanned                                           */
-  int64_t lm_warp_bytes;       /* algorithmic bytes: 40 per visit (list entry, offset,   */
-                               /* degree, C, K, Sigma and size of C) + per arc 8 (col,   */
-                               /* C of the neighbour) + the weight (4 at level 0, else 8)*/
-  double ms_lm_warp;           /* summed device time of the timed launches               */
+  /* The local-moving kernels, [0] vertices of degree <= 128 (a warp or 8 lanes
+   * each), [1] degree 129..1024 (a block each), [2] the arc scan of vertices
+   * above 1024 arcs (chunks spread over all SMs): */
+  int64_t lmk_launches[3];     /* launches timed (collect_stats bit 2)                    */
+  int64_t lmk_vertices[3];     /* vertex visits                                          */
+  int64_t lmk_arcs[3];         /* arcs scanned                                           */
+  int64_t lmk_bytes[3];        /* algorithmic bytes: per arc 8 (col, C of the neighbour) */
+                               /* + the weight (4 at level 0, else 8); [0] and [1] add   */
+                               /* 40 per visit (list entry, offset, degree, C, K, Sigma  */
+                               /* and size of C)                                         */
+  double lmk_ms[3];            /* summed device time of the timed launches               */
 } leiden_stats;
 
 typedef struct leiden_handle leiden_handle;

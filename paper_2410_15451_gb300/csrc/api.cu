@@ -14,7 +14,7 @@ static std::atomic<int64_t> g_launches{0};
 
 void ld_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-void kt_begin(leiden_handle *h) {
+void kt_begin(leiden_handle *h, int k) {
   if (!(h->p.collect_stats & 2)) return;
   size_t need = 2 * (size_t)(h->kt_used + 1);
   while (h->kt_ev.size() < need) {
@@ -22,6 +22,8 @@ void kt_begin(leiden_handle *h) {
     if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
     h->kt_ev.push_back(e);
   }
+  if (h->kt_tag.size() < (size_t)h->kt_used + 1) h->kt_tag.resize(h->kt_used + 1);
+  h->kt_tag[h->kt_used] = k;
   cudaEventRecord(h->kt_ev[2 * h->kt_used], h->stream);
 }
 
@@ -34,10 +36,11 @@ void kt_end(leiden_handle *h) {
 void kt_resolve(leiden_handle *h) {
   for (int k = 0; k < h->kt_used; k++) {
     float ms = 0;
-    if (cudaEventElapsedTime(&ms, h->kt_ev[2 * k], h->kt_ev[2 * k + 1]) == cudaSuccess) h->kt_ms += ms;
+    int t = h->kt_tag[k];
+    if (cudaEventElapsedTime(&ms, h->kt_ev[2 * k], h->kt_ev[2 * k + 1]) == cudaSuccess) h->kt_ms[t] += ms;
     else cudaGetLastError();
+    h->kt_launches[t]++;
   }
-  h->kt_launches += h->kt_used;
   h->kt_used = 0;
 }
 
@@ -129,15 +132,14 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   int64_t N = h->n;
   memset(h->trace, 0, sizeof(h->trace));
   h->kt_used = 0;
-  h->kt_ms = 0;
-  h->kt_launches = 0;
+  for (int k = 0; k < KT_KERNELS; k++) { h->kt_ms[k] = 0; h->kt_launches[k] = 0; }
   // initialisation
   mark_unprocessed_from_flags(h, h->dV, N);
   launch_iota_i32(h->Ctop, N, s);
   CK(cudaMemcpyAsync(h->Cp, h->C, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(h->Kp, h->K, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemcpyAsync(h->Sp, h->Sig, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemsetAsync(&h->dcnt->processed, 0, 8 * sizeof(int64_t), s));  // processed .. warp_bytes
+  CK(cudaMemsetAsync(&h->dcnt->processed, 0, 14 * sizeof(int64_t), s));  // processed .. lmk_bytes
   int64_t m2 = h->m2;
   LevelGraph g = level0(h);
   double tau = p.tau;
@@ -255,12 +257,14 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   st.lm_moves = moves_total;
   st.refine_vertices = h->hcnt->ref_processed;
   st.refine_arcs = h->hcnt->ref_arcs;
-  st.lm_warp_vertices = h->hcnt->warp_processed;
-  st.lm_warp_arcs = h->hcnt->warp_arcs;
-  st.lm_warp_bytes = h->hcnt->warp_bytes;
   kt_resolve(h);
-  st.lm_warp_launches = h->kt_launches;
-  st.ms_lm_warp = h->kt_ms;
+  for (int k = 0; k < KT_KERNELS; k++) {
+    st.lmk_vertices[k] = h->hcnt->lmk_visits[k];
+    st.lmk_arcs[k] = h->hcnt->lmk_arcs[k];
+    st.lmk_bytes[k] = h->hcnt->lmk_bytes[k];
+    st.lmk_launches[k] = h->kt_launches[k];
+    st.lmk_ms[k] = h->kt_ms[k];
+  }
   if (h->p.collect_stats & 1) {
     st.ms_move = t_move;
     st.ms_refine = t_ref;
@@ -449,6 +453,7 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   while (tc < 2 * n) tc <<= 1;
   A(dalloc(h, &h->tr_keys, tc));
   A(dalloc(h, &h->tr_vals, tc));
+  A(dalloc(h, &h->tr_list, n));
   h->tr_cap = tc;
   A(dalloc(h, &h->dcnt, 1));
   size_t stb = scan_tmp_bytes(2 * n + 2);
@@ -467,6 +472,8 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   A(cudaMemcpyAsync(h->g_w, hw.data(), (size_t)cap * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   A(cudaMemcpyAsync(h->g_rcap, rcap.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, s));
   A(cudaMemsetAsync(h->dcnt, 0, sizeof(DevCounters), s));
+  A(cudaMemsetAsync(h->tr_keys, 0xff, (size_t)h->tr_cap * sizeof(uint64_t), s));  // empty pair table
+  A(cudaMemsetAsync(h->tr_vals, 0, (size_t)h->tr_cap * sizeof(int64_t), s));
   A(cudaMemcpyAsync(&h->dcnt->arena_used, &cap, sizeof(int64_t), cudaMemcpyHostToDevice, s));
   A(cudaStreamSynchronize(s));
   if (e != cudaSuccess) return bail(LEIDEN_ERR_CUDA, std::string("upload: ") + cudaGetErrorString(e));

@@ -33,9 +33,9 @@ struct DevCounters {
   int64_t moves;                  // local-moving moves
   int64_t ref_processed;          // refinement vertex visits
   int64_t ref_arcs;               // refinement arcs scanned
-  int64_t warp_processed;         // local moving, warp bin: vertex visits
-  int64_t warp_arcs;              // local moving, warp bin: arcs scanned
-  int64_t warp_bytes;             // local moving, warp bin: algorithmic bytes
+  int64_t lmk_visits[3];          // local moving per timed kernel (warp range, block bin, hub scan):
+  int64_t lmk_arcs[3];            //   vertex visits, arcs scanned and algorithmic bytes
+  int64_t lmk_bytes[3];
   int64_t m2;                     // 2m (sum of arc weights), device copy
   int64_t sigma_intra;            // modularity: intra-community arc weight
   unsigned long long sq[2];       // modularity: sum of Sigma_c^2 (int128)
@@ -43,6 +43,7 @@ struct DevCounters {
   int64_t huge_slots;             // table slots the vertices above the block bin need
   int32_t big_count;              // splitting: long rows left to the block kernel
   int32_t large_count;            // batch apply: touched rows merged in chunks
+  int32_t tr_occ;                 // tracking: filled slots of the pair table
   int64_t arena_used;             // next free arc slot of G^t (relocated rows go here)
 };
 
@@ -118,7 +119,9 @@ __device__ __forceinline__ int64_t ld_warp_sum_i64(int64_t v) {
 
 // Reductions over the lanes that share a key (peers = __match_any_sync of
 // the key).  Every lane of the warp must call them (full-mask shuffles);
-// each lane receives its group's result.
+// each lane receives its group's result.  (The warp reduction unit,
+// __reduce_add_sync with one mask per group, measured about twice as slow
+// here: it serialises over the distinct masks of a warp.)
 __device__ __forceinline__ int64_t ld_group_sum_i64(uint32_t peers, int64_t v) {
   int64_t s = 0;
 #pragma unroll
@@ -169,6 +172,136 @@ __device__ __forceinline__ void ld_gtable_insert_warp(int32_t *keys, int64_t *va
   uint32_t peers = __match_any_sync(LD_FULL, key);
   int64_t sum = ld_group_sum_i64(peers, valid ? w : 0);
   if (valid && ld_group_leader(peers)) ld_gtable_insert(keys, vals, list, occ, tmask, c, sum);
+}
+
+// Shared-memory staging table: a block adds (key, weight) pairs with
+// warp-aggregated inserts, then either reads the distinct keys from the
+// filled-slot list or flushes them into a global table (one global update
+// per distinct key instead of one per warp group).  Kept empty between uses.
+constexpr int STAGE_SLOTS = 2048;
+constexpr int STAGE_FILL = 1024;  // distinct keys per use at most (load <= 1/2)
+struct Stage {
+  int32_t keys[STAGE_SLOTS];
+  int64_t vals[STAGE_SLOTS];
+  int32_t list[STAGE_FILL];
+  int32_t count;
+};
+
+__device__ __forceinline__ void stage_init(Stage &S) {
+  for (int s = threadIdx.x; s < STAGE_SLOTS; s += blockDim.x) { S.keys[s] = LD_EMPTY_KEY; S.vals[s] = 0; }
+  if (threadIdx.x == 0) S.count = 0;
+  __syncthreads();
+}
+
+// Warp-cooperative: all 32 lanes call it; `valid` = this lane has a pair.
+__device__ __forceinline__ void stage_insert_warp(Stage &S, bool valid, int32_t c, int64_t w) {
+  int32_t key = valid ? c : -2 - (int32_t)(threadIdx.x & 31);
+  uint32_t peers = __match_any_sync(LD_FULL, key);
+  int64_t sum = ld_group_sum_i64(peers, valid ? w : 0);
+  if (!valid || !ld_group_leader(peers)) return;
+  uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(STAGE_SLOTS - 1);
+  while (true) {
+    int32_t k = atomicCAS(&S.keys[s], LD_EMPTY_KEY, c);
+    if (k == LD_EMPTY_KEY) S.list[atomicAdd(&S.count, 1)] = (int32_t)s;
+    if (k == LD_EMPTY_KEY || k == c) {
+      atomicAdd((unsigned long long *)&S.vals[s], (unsigned long long)sum);
+      return;
+    }
+    s = (s + 1) & (uint32_t)(STAGE_SLOTS - 1);
+  }
+}
+
+// Empty the listed slots (all threads of the block; ends synchronised).
+__device__ __forceinline__ void stage_clear(Stage &S) {
+  __syncthreads();
+  int n = S.count;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    int32_t s = S.list[t];
+    S.keys[s] = LD_EMPTY_KEY;
+    S.vals[s] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) S.count = 0;
+  __syncthreads();
+}
+
+// Move the staged pairs into a global table (ld_gtable_insert) and empty the
+// stage (all threads of the block).
+__device__ __forceinline__ void stage_flush(Stage &S, int32_t *gkeys, int64_t *gvals, int32_t *glist, int32_t *gocc,
+                                            int gmask) {
+  __syncthreads();
+  int n = S.count;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    int32_t s = S.list[t];
+    ld_gtable_insert(gkeys, gvals, glist, gocc, gmask, S.keys[s], S.vals[s]);
+    S.keys[s] = LD_EMPTY_KEY;
+    S.vals[s] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) S.count = 0;
+  __syncthreads();
+}
+
+// Warp-private shared table: only the lanes of one warp touch it, and after
+// __match_any_sync each key is held by one lane, so values are updated with
+// plain adds (an atomic only claims an empty slot).  Flushed into a global
+// table before it passes half full.
+constexpr int WT_SLOTS = 256;
+constexpr int WT_LIMIT = WT_SLOTS / 2 - 32;  // flush above this many keys
+struct WarpTable {
+  int32_t keys[WT_SLOTS];
+  int64_t vals[WT_SLOTS];
+  int32_t list[WT_SLOTS / 2];
+  int32_t count;
+};
+
+__device__ __forceinline__ void wt_init(WarpTable &T) {
+  int lane = threadIdx.x & 31;
+  for (int s = lane; s < WT_SLOTS; s += 32) { T.keys[s] = LD_EMPTY_KEY; T.vals[s] = 0; }
+  if (lane == 0) T.count = 0;
+  __syncwarp();
+}
+
+// All 32 lanes call it; `valid` = this lane has a pair.
+__device__ __forceinline__ void wt_insert_warp(WarpTable &T, bool valid, int32_t c, int64_t w) {
+  int32_t key = valid ? c : -2 - (int32_t)(threadIdx.x & 31);
+  uint32_t peers = __match_any_sync(LD_FULL, key);
+  int64_t sum = ld_group_sum_i64(peers, valid ? w : 0);
+  if (valid && ld_group_leader(peers)) {
+    uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(WT_SLOTS - 1);
+    while (true) {
+      int32_t k = T.keys[s];
+      if (k == LD_EMPTY_KEY) {
+        k = atomicCAS(&T.keys[s], LD_EMPTY_KEY, c);  // another lane may take it first
+        if (k == LD_EMPTY_KEY) {
+          T.vals[s] = sum;
+          T.list[atomicAdd(&T.count, 1)] = (int32_t)s;
+          break;
+        }
+      }
+      // a key already in the table lies before the first empty slot of its probe path
+      if (k == c) { T.vals[s] += sum; break; }
+      s = (s + 1) & (uint32_t)(WT_SLOTS - 1);
+    }
+  }
+  __syncwarp();
+}
+
+// All 32 lanes: move the pairs into a global table and empty the warp table.
+__device__ __forceinline__ void wt_flush(WarpTable &T, int32_t *gkeys, int64_t *gvals, int32_t *glist, int32_t *gocc,
+                                         int gmask) {
+  int lane = threadIdx.x & 31;
+  __syncwarp();
+  int n = T.count;
+  for (int q = lane; q < n; q += 32) {
+    int32_t s = T.list[q];
+    ld_gtable_insert(gkeys, gvals, glist, gocc, gmask, T.keys[s], T.vals[s]);
+    T.keys[s] = LD_EMPTY_KEY;
+    T.vals[s] = 0;
+  }
+  __syncwarp();
+  if (lane == 0) T.count = 0;
+  __syncwarp();
 }
 
 // ---------------------------------------------------------------- bitmaps

@@ -24,9 +24,12 @@ struct LevelGraph {
 };
 
 // Degree bins of the vertex-centric kernels (local moving, refinement).
-enum { BIN_WARP = 0, BIN_BLOCK = 1, BIN_HUGE = 2, NBINS = 3 };
+enum { BIN_WARP = 0, BIN_BLOCK = 1, BIN_HUGE = 2, BIN_TINY = 3, NBINS = 4 };
+constexpr int BIN_TINY_MAX = 8;      // eight lanes, one arc per lane (local moving, refinement)
 constexpr int BIN_WARP_MAX = 128;    // one warp, shared table of <= 256 slots
 constexpr int BIN_BLOCK_MAX = 1024;  // one block, shared table of 2048 slots
+// Local-moving kernels with their own timer and work counters.
+enum { KT_WARP = 0, KT_BLOCK = 1, KT_HUGE_SCAN = 2, KT_KERNELS = 3 };
 
 struct BatchBuffers {
   int64_t cap_edges = 0;  // capacity in undirected edges, per side
@@ -109,9 +112,11 @@ struct leiden_handle {
   int64_t hslots = 0;
   int32_t *hocc = nullptr;  // [n] filled slots per listed vertex
 
-  // tracking hash table of (old, new) pairs
+  // tracking hash table of (old, new) pairs (empty between calls) and the
+  // list of its filled slots
   uint64_t *tr_keys = nullptr;
   int64_t *tr_vals = nullptr;
+  int32_t *tr_list = nullptr;
   int64_t tr_cap = 0;
 
   // scan scratch
@@ -127,11 +132,12 @@ struct leiden_handle {
 
   cudaEvent_t ev[8] = {};
   // Kernel timer (collect_stats bit 2): event pairs around the launches of
-  // the local-moving warp-bin kernel, resolved at the next host sync.
+  // the local-moving kernels, resolved at the next host sync.
   std::vector<cudaEvent_t> kt_ev;
-  int kt_used = 0;      // pairs recorded since the last resolve
-  double kt_ms = 0;     // summed device time of the resolved pairs
-  int64_t kt_launches = 0;
+  std::vector<int> kt_tag;  // timed kernel of each recorded pair
+  int kt_used = 0;          // pairs recorded since the last resolve
+  double kt_ms[KT_KERNELS] = {};
+  int64_t kt_launches[KT_KERNELS] = {};
   leiden_stats stats{};
   int64_t trace[2 + 10 * 25] = {};
   std::string err;
@@ -143,9 +149,10 @@ struct leiden_handle {
 // so that leiden_kernel_launches() counts them.
 void ld_note_launch();
 
-// Kernel timer of the local-moving warp-bin kernel: begin/end around a launch
-// (no-ops unless collect_stats has bit 2), resolve after a stream sync.
-void kt_begin(leiden_handle *h);
+// Kernel timer of the local-moving kernels: begin/end around a launch of
+// kernel `k` (no-ops unless collect_stats has bit 2), resolve after a
+// stream sync.
+void kt_begin(leiden_handle *h, int k);
 void kt_end(leiden_handle *h);
 void kt_resolve(leiden_handle *h);
 

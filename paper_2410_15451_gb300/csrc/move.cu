@@ -46,6 +46,9 @@ struct Args {
   int32_t *movers, *mtarget;
   const int32_t *list;   // bin list
   const int32_t *count;  // bin count (device)
+  const int32_t *list_tiny;   // bin 3 list (degree <= 8), used with bin 0
+  const int32_t *count_tiny;
+  int64_t m2;                 // 2m of the level graph
   DevCounters *cnt;
   int dynamic;
   int async_mode;
@@ -137,7 +140,7 @@ template <int KIND>
 __device__ __forceinline__ i128 decide_leader(const Args &A, int64_t i, const Best &b) {
   int32_t d = A.C[i];
   int64_t Ki = A.K[i];
-  int64_t m2 = A.cnt->m2;
+  int64_t m2 = A.m2;
   if (b.c < 0) return 0;
   i128 g = (i128)m2 * (b.kc - b.kd) - (i128)Ki * ((i128)Ki + A.S[b.c] - A.S[d]);
   if (g <= 0) return 0;
@@ -190,44 +193,250 @@ __device__ __forceinline__ void add_counters(DevCounters *cnt, int kind, int64_t
   }
 }
 
-// ---------------------------------------------------------------- bin 0: warp per vertex
+// Work counters of the timed local-moving kernels (algorithmic bytes as
+// stated in the C header).
+__device__ __forceinline__ void add_lmk(DevCounters *cnt, int k, int64_t visits, int64_t arcs, int64_t bytes) {
+  if (visits) atomicAdd((unsigned long long *)&cnt->lmk_visits[k], (unsigned long long)visits);
+  if (arcs) atomicAdd((unsigned long long *)&cnt->lmk_arcs[k], (unsigned long long)arcs);
+  if (bytes) atomicAdd((unsigned long long *)&cnt->lmk_bytes[k], (unsigned long long)bytes);
+}
+
+// ---------------------------------------------------------------- bins 3 and 0: warp range
+// Candidate with the values the decision needs carried along, so that the
+// winner's Sigma and size are not loaded again after the reduction.
+struct BestX {
+  i128 v;
+  int32_t c;
+  int32_t szc;  // size of c (local moving)
+  int64_t kc;
+  int64_t kd;
+  int64_t sc;   // Sigma of c
+};
+
+__device__ __forceinline__ void bestx_merge(BestX &a, const BestX &b) {
+  if (ld_better(b.v, b.c, a.v, a.c)) { a.v = b.v; a.c = b.c; a.kc = b.kc; a.sc = b.sc; a.szc = b.szc; }
+  a.kd += b.kd;
+}
+
+__device__ __forceinline__ int64_t shfl_xor_i64(int64_t v, int o) { return __shfl_xor_sync(LD_FULL, v, o); }
+
+// Reduction over lanes that differ in the bits of `width` - 1 (width 8:
+// within aligned groups of 8 lanes; 32: the whole warp).
+template <int WIDTH>
+__device__ __forceinline__ BestX bestx_reduce(BestX b) {
+#pragma unroll
+  for (int o = WIDTH / 2; o > 0; o >>= 1) {
+    BestX t;
+    t.v = ld_shfl_xor_i128(b.v, o);
+    t.c = __shfl_xor_sync(LD_FULL, b.c, o);
+    t.szc = __shfl_xor_sync(LD_FULL, b.szc, o);
+    t.kc = shfl_xor_i64(b.kc, o);
+    t.kd = shfl_xor_i64(b.kd, o);
+    t.sc = shfl_xor_i64(b.sc, o);
+    bestx_merge(b, t);
+  }
+  return b;
+}
+
+// The decision of vertex i in community d (K_i, Sigma_d, size_d given) for
+// the reduced candidate b.  Returns the gain (Eq. 2 times 2m^2) when i moves
+// (local moving) or proposes (refinement), else 0; the caller records a
+// deferred move.
+template <int KIND>
+__device__ __forceinline__ i128 decide_x(const Args &A, int64_t i, int32_t d, int64_t Ki, int64_t Sd, int32_t szd,
+                                         BestX b) {
+  if (b.c < 0) return 0;
+  if (KIND == KIND_MOVE && A.async_mode) {
+    // in-place moves: read the totals again, as late as possible
+    Sd = A.S[d];
+    b.sc = A.S[b.c];
+    szd = A.size[d];
+    b.szc = A.size[b.c];
+  }
+  i128 g = (i128)A.m2 * (b.kc - b.kd) - (i128)Ki * ((i128)Ki + b.sc - Sd);
+  if (g <= 0) return 0;
+  if (KIND == KIND_MOVE) {
+    if (szd == 1 && b.szc == 1 && b.c > d) return 0;
+    if (A.async_mode) {
+      A.C[i] = b.c;
+      atomicAdd((unsigned long long *)&A.S[d], (unsigned long long)(-Ki));
+      atomicAdd((unsigned long long *)&A.S[b.c], (unsigned long long)Ki);
+      atomicSub(&A.size[d], 1);
+      atomicAdd(&A.size[b.c], 1);
+    }
+    if (A.dynamic) A.dS[d] = 1;
+    return g;
+  } else {
+    if (A.C[b.c] != b.c) return 0;  // the representative of c* left it
+    A.prop[i] = b.c;
+    return g;
+  }
+}
+
+// Deferred moves of the lanes with `mv` set (snapshot schedule): one
+// counter update per warp.
+__device__ __forceinline__ void record_movers(const Args &A, bool mv, int32_t i, int32_t c) {
+  uint32_t m = __ballot_sync(LD_FULL, mv);
+  if (!m) return;
+  int lane = threadIdx.x & 31;
+  int32_t p0 = 0;
+  if (lane == __ffs(m) - 1) p0 = atomicAdd(&A.cnt->movers, __popc(m));
+  p0 = __shfl_sync(LD_FULL, p0, __ffs(m) - 1);
+  if (mv) {
+    int32_t slot = p0 + __popc(m & ((1u << lane) - 1u));
+    A.movers[slot] = i;
+    A.mtarget[slot] = c;
+  }
+}
+
+struct Tally {
+  int64_t visits = 0, arcs = 0, moves = 0;
+  i128 dq = 0;
+};
+
+// Per-block sums of the lanes' tallies, then one set of counter updates.
+template <typename W, int KIND>
+__device__ __forceinline__ void flush_tally(const Args &A, Tally t) {
+  __shared__ unsigned long long sacc[6];
+  if (threadIdx.x < 6) sacc[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t v = ld_warp_sum_i64(t.visits), a = ld_warp_sum_i64(t.arcs), m = ld_warp_sum_i64(t.moves);
+  i128 q = t.dq;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) q += ld_shfl_xor_i128(q, o);
+  if ((threadIdx.x & 31) == 0 && v) {
+    atomicAdd(&sacc[0], (unsigned long long)v);
+    atomicAdd(&sacc[1], (unsigned long long)a);
+    atomicAdd(&sacc[2], (unsigned long long)m);
+    ld_atomic_add_i128(&sacc[3], q);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && sacc[0]) {
+    i128 dq = (i128)(((u128)sacc[4] << 64) | (u128)sacc[3]);
+    add_counters(A.cnt, KIND, (int64_t)sacc[0], (int64_t)sacc[1], (int64_t)sacc[2], dq);
+    if (KIND == KIND_MOVE) {
+      // algorithmic bytes: per visit the list entry, off, deg, C[i], K[i],
+      // Sigma[C[i]], size[C[i]] (40 B); per arc col, C[j] and the weight
+      add_lmk(A.cnt, KT_WARP, (int64_t)sacc[0], (int64_t)sacc[1], 40 * (int64_t)sacc[0] + (8 + (int64_t)sizeof(W)) * (int64_t)sacc[1]);
+    }
+  }
+}
+
+constexpr int TINY_LANES = 8;  // lanes per vertex of degree <= BIN_TINY_MAX (one arc each)
+
+// Four vertices of degree <= 8 per warp, one arc per lane: lanes whose
+// neighbours share a community find each other with __match_any_sync, so
+// no table is built; each group's leader lanes hold K_{i->c} and Sigma_c.
+template <typename W, int KIND>
+__device__ __forceinline__ void tiny_step(const Args &A, int64_t item, int64_t ntiny, int lane, Tally &tl) {
+  const W *w = (const W *)A.w;
+  int grp = lane >> 3, sub = lane & 7, gl = lane & ~7;
+  int64_t k = item * 4 + grp;
+  bool has = k < ntiny;
+  int32_t i = has ? A.list_tiny[k] : 0;
+  int64_t base = 0, Ki = 0, Sd = 0, wj = 0;
+  int32_t dg = 0, d = 0, szd = 0, bi = 0, j = -1;
+  if (has) {
+    base = A.off[i];
+    dg = A.deg[i];
+    d = A.C[i];
+    Ki = A.K[i];
+    if (KIND == KIND_REFINE) bi = A.CB[i];
+  }
+  bool arc = has && sub < dg;
+  if (arc) { j = A.col[base + sub]; wj = (int64_t)w[base + sub]; }
+  if (has) {
+    Sd = A.S[d];
+    if (KIND == KIND_MOVE) szd = A.size[d];
+  }
+  bool valid = arc && j != i && (KIND != KIND_REFINE || A.CB[j] == bi);
+  int32_t c = valid ? A.C[j] : 0;
+  unsigned long long key = valid ? (((unsigned long long)grp << 32) | (uint32_t)c)
+                                 : (0xffffffff00000000ull | (unsigned)lane);
+  uint32_t peers = __match_any_sync(LD_FULL, key);
+  int64_t kv = 0;  // peers lie within the lane's group of eight
+#pragma unroll
+  for (int q = 0; q < TINY_LANES; q++) {
+    int64_t x = __shfl_sync(LD_FULL, wj, gl + q);
+    if ((peers >> (gl + q)) & 1u) kv += x;
+  }
+  BestX b{0, -1, 0, 0, 0, 0};
+  if (valid && ld_group_leader(peers)) {
+    if (c == d) {
+      b.kd = kv;
+    } else {
+      b.sc = A.S[c];
+      if (KIND == KIND_MOVE) b.szc = A.size[c];
+      b.v = (i128)A.m2 * kv - (i128)Ki * b.sc;
+      b.c = c;
+      b.kc = kv;
+    }
+  }
+  b = bestx_reduce<TINY_LANES>(b);
+  i128 g = 0;
+  if (has && sub == 0) g = decide_x<KIND>(A, i, d, Ki, Sd, szd, b);
+  bool mv = g > 0;
+  if (KIND == KIND_MOVE && !A.async_mode) record_movers(A, mv, i, b.c);
+  int moved = __shfl_sync(LD_FULL, mv ? 1 : 0, gl);
+  if (KIND == KIND_MOVE && moved && arc && j != i && (!A.in_range || A.in_range[j])) ld_bit_set(A.unproc, j);
+  if (has && sub == 0) { tl.visits++; tl.arcs += dg; tl.moves += mv; tl.dq += g; }
+}
+
+// One vertex of degree 9..128 per warp with a shared-memory table; every
+// per-vertex load is issued before the arc scan.
+template <typename W, int KIND>
+__device__ __forceinline__ void warp_step(const Args &A, int32_t i, int lane, int32_t *keys, int64_t *vals,
+                                          Tally &tl) {
+  int64_t base = A.off[i];
+  int32_t dg = A.deg[i];
+  int32_t d = A.C[i];
+  int64_t Ki = A.K[i];
+  int64_t Sd = A.S[d];
+  int32_t szd = KIND == KIND_MOVE ? A.size[d] : 0;
+  int T = max(32, next_pow2(2 * dg));
+  for (int s = lane; s < T; s += 32) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
+  __syncwarp();
+  scan_arcs<W, KIND>(A, i, base, dg, lane, 32, keys, vals, T - 1);
+  __syncwarp();
+  BestX b{0, -1, 0, 0, 0, 0};
+  for (int s = lane; s < T; s += 32) {
+    int32_t c = keys[s];
+    if (c == LD_EMPTY_KEY) continue;
+    int64_t kv = vals[s];
+    if (c == d) { b.kd += kv; continue; }
+    int64_t sc = A.S[c];
+    i128 v = (i128)A.m2 * kv - (i128)Ki * sc;
+    if (ld_better(v, c, b.v, b.c)) { b.v = v; b.c = c; b.kc = kv; b.sc = sc; }
+  }
+  if (KIND == KIND_MOVE && b.c >= 0) b.szc = A.size[b.c];
+  b = bestx_reduce<32>(b);
+  __syncwarp();
+  i128 g = 0;
+  if (lane == 0) g = decide_x<KIND>(A, i, d, Ki, Sd, szd, b);
+  bool mv = g > 0;
+  if (KIND == KIND_MOVE && !A.async_mode) record_movers(A, mv, i, b.c);
+  int moved = __shfl_sync(LD_FULL, mv ? 1 : 0, 0);
+  if (KIND == KIND_MOVE && moved) mark_neighbours(A, i, base, dg, lane, 32);
+  if (lane == 0) { tl.visits++; tl.arcs += dg; tl.moves += mv; tl.dq += g; }
+}
+
+// Bins 3 (degree <= 8, groups of 8 lanes) and 0 (degree <= 128, a warp
+// each) in one launch: items [0, ceil(n3/4)) are groups of four tiny
+// vertices, the rest one warp-bin vertex each.
 template <typename W, int KIND>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) k_decide_warp(Args A) {
   __shared__ int32_t skeys[WARPS_PER_BLOCK][WARP_TABLE];
   __shared__ int64_t svals[WARPS_PER_BLOCK][WARP_TABLE];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int32_t *keys = skeys[wid];
-  int64_t *vals = svals[wid];
-  int64_t count = *A.count;
+  int64_t ntiny = *A.count_tiny, nwarp = *A.count;
+  int64_t ngroups = (ntiny + 3) / 4, total = ngroups + nwarp;
   int64_t gw = (int64_t)blockIdx.x * WARPS_PER_BLOCK + wid, nw = (int64_t)gridDim.x * WARPS_PER_BLOCK;
-  int64_t visits = 0, arcs = 0, moves = 0;
-  i128 dq = 0;
-  for (int64_t t = gw; t < count; t += nw) {
-    int64_t i = A.list[t];
-    int64_t base = A.off[i], dg = A.deg[i];
-    int T = max(32, next_pow2(2 * (int)dg));
-    for (int s = lane; s < T; s += 32) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
-    __syncwarp();
-    scan_arcs<W, KIND>(A, i, base, dg, lane, 32, keys, vals, T - 1);
-    __syncwarp();
-    Best b = slot_best(keys, vals, T, lane, 32, A.C[i], A.cnt->m2, A.K[i], A.S);
-    b = warp_best(b);
-    __syncwarp();
-    i128 g = 0;
-    if (lane == 0) g = decide_leader<KIND>(A, i, b);
-    int moved = __shfl_sync(LD_FULL, g > 0 ? 1 : 0, 0);
-    if (KIND == KIND_MOVE && moved) mark_neighbours(A, i, base, dg, lane, 32);
-    if (lane == 0) { visits++; arcs += dg; moves += moved; dq += g; }
+  Tally tl;
+  for (int64_t t = gw; t < total; t += nw) {
+    if (t < ngroups) tiny_step<W, KIND>(A, t, ntiny, lane, tl);
+    else warp_step<W, KIND>(A, A.list[t - ngroups], lane, skeys[wid], svals[wid], tl);
   }
-  if (lane == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
-  if (KIND == KIND_MOVE && lane == 0 && visits) {
-    // algorithmic bytes: per visit the list entry, off, deg, C[i], K[i],
-    // Sigma[C[i]], size[C[i]] (40 B); per arc col, C[j] and the weight
-    atomicAdd((unsigned long long *)&A.cnt->warp_processed, (unsigned long long)visits);
-    atomicAdd((unsigned long long *)&A.cnt->warp_arcs, (unsigned long long)arcs);
-    atomicAdd((unsigned long long *)&A.cnt->warp_bytes,
-              (unsigned long long)(40 * visits + (8 + (int64_t)sizeof(W)) * arcs));
-  }
+  flush_tally<W, KIND>(A, tl);
 }
 
 // Block-wide merge of per-thread Best values (result valid in thread 0).
@@ -248,36 +457,92 @@ __device__ __forceinline__ Best block_best(Best b) {
   return r;
 }
 
-// ---------------------------------------------------------------- bin 1: block, shared table
+// ---------------------------------------------------------------- bin 1: block, shared stage
+// Block-wide merge of per-thread BestX values (result valid in every thread).
+__device__ __forceinline__ BestX block_bestx(BestX b) {
+  __shared__ BestX sb[32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  b = bestx_reduce<32>(b);
+  if (lane == 0) sb[wid] = b;
+  __syncthreads();
+  if (wid == 0) {
+    BestX x = lane < nw ? sb[lane] : BestX{0, -1, 0, 0, 0, 0};
+    x = bestx_reduce<32>(x);
+    if (lane == 0) sb[0] = x;
+  }
+  __syncthreads();
+  BestX r = sb[0];
+  __syncthreads();
+  return r;
+}
+
+// One vertex of degree 129..1024 per block: warp-aggregated inserts into a
+// shared stage, then the candidates are read from its filled-slot list (the
+// distinct neighbour communities only) and the slots emptied again.
 template <typename W, int KIND>
 __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Args A) {
-  __shared__ int32_t keys[BLOCK_TABLE];
-  __shared__ int64_t vals[BLOCK_TABLE];
+  __shared__ Stage S;
   __shared__ int moved_s;
+  stage_init(S);
+  const W *w = (const W *)A.w;
+  int lane = threadIdx.x & 31;
   int64_t count = *A.count;
   int64_t visits = 0, arcs = 0, moves = 0;
   i128 dq = 0;
   for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
-    int64_t i = A.list[t];
-    int64_t base = A.off[i], dg = A.deg[i];
-    int T = next_pow2(2 * (int)dg);
-    if (T > BLOCK_TABLE) T = BLOCK_TABLE;
-    for (int s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
+    int32_t i = A.list[t];
+    int64_t base = A.off[i];
+    int32_t dg = A.deg[i];
+    int32_t d = A.C[i];
+    int64_t Ki = A.K[i];
+    int64_t Sd = A.S[d];
+    int32_t szd = KIND == KIND_MOVE ? A.size[d] : 0;
+    int32_t bi = KIND == KIND_REFINE ? A.CB[i] : 0;
+    for (int a0 = threadIdx.x & ~31; a0 < dg; a0 += blockDim.x) {  // warp-uniform trip count
+      int a = a0 + lane;
+      bool valid = a < dg;
+      int32_t c = 0;
+      int64_t wa = 0;
+      if (valid) {
+        int32_t j = A.col[base + a];
+        valid = j != i && (KIND != KIND_REFINE || A.CB[j] == bi);
+        if (valid) { c = A.C[j]; wa = (int64_t)w[base + a]; }
+      }
+      stage_insert_warp(S, valid, c, wa);
+    }
     __syncthreads();
-    scan_arcs<W, KIND>(A, i, base, dg, threadIdx.x, blockDim.x, keys, vals, T - 1);
-    __syncthreads();
-    Best b = slot_best(keys, vals, T, threadIdx.x, blockDim.x, A.C[i], A.cnt->m2, A.K[i], A.S);
-    b = block_best(b);
+    int n = S.count;
+    BestX b{0, -1, 0, 0, 0, 0};
+    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+      int32_t sl = S.list[q];
+      int32_t c = S.keys[sl];
+      int64_t kv = S.vals[sl];
+      if (c == d) { b.kd += kv; continue; }
+      int64_t sc = A.S[c];
+      i128 v = (i128)A.m2 * kv - (i128)Ki * sc;
+      if (ld_better(v, c, b.v, b.c)) { b.v = v; b.c = c; b.kc = kv; b.sc = sc; }
+    }
+    if (KIND == KIND_MOVE && b.c >= 0) b.szc = A.size[b.c];
+    b = block_bestx(b);
+    stage_clear(S);
     if (threadIdx.x == 0) {
-      i128 g = decide_leader<KIND>(A, i, b);
-      moved_s = g > 0;
-      visits++; arcs += dg; moves += g > 0; dq += g;
+      i128 g = decide_x<KIND>(A, i, d, Ki, Sd, szd, b);
+      bool mv = g > 0;
+      if (KIND == KIND_MOVE && mv && !A.async_mode) {
+        int32_t slot = atomicAdd(&A.cnt->movers, 1);
+        A.movers[slot] = i;
+        A.mtarget[slot] = b.c;
+      }
+      moved_s = mv;
+      visits++; arcs += dg; moves += mv; dq += g;
     }
     __syncthreads();
     if (KIND == KIND_MOVE && moved_s) mark_neighbours(A, i, base, dg, threadIdx.x, blockDim.x);
     __syncthreads();
   }
   if (threadIdx.x == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
+  if (KIND == KIND_MOVE && threadIdx.x == 0)
+    add_lmk(A.cnt, KT_BLOCK, visits, arcs, 40 * visits + (8 + (int64_t)sizeof(W)) * arcs);
 }
 
 // ---------------------------------------------------------------- bin 2, split across blocks
@@ -296,6 +561,12 @@ __global__ void k_huge_zero_occ(const int32_t *count_p, int32_t *occ) {
 
 template <typename W, int KIND>
 __global__ void __launch_bounds__(256) k_huge_scan(Args A, const int64_t *tab_off, const int64_t *ch_off) {
+  // Each warp sums its arcs per community in a private shared table first
+  // (the neighbours of a hub fall into few communities), then each distinct
+  // community updates the vertex's global table once per flush.
+  __shared__ WarpTable WT[8];
+  WarpTable &T8 = WT[threadIdx.x >> 5];
+  wt_init(T8);
   int64_t count = *A.count;
   int64_t nch = ch_off[count];
   for (int64_t t = blockIdx.x; t < nch; t += gridDim.x) {
@@ -325,8 +596,12 @@ __global__ void __launch_bounds__(256) k_huge_scan(Args A, const int64_t *tab_of
         valid = j != i && (KIND != KIND_REFINE || A.CB[j] == bi);
         if (valid) { c = A.C[j]; wa = (int64_t)w[base + a]; }
       }
-      ld_gtable_insert_warp(keys, vals, list, &A.gocc[lo], (int)(T - 1), valid, c, wa);
+      if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+      wt_insert_warp(T8, valid, c, wa);
     }
+    wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+    if (KIND == KIND_MOVE && threadIdx.x == 0)
+      add_lmk(A.cnt, KT_HUGE_SCAN, first == 0 ? 1 : 0, len, (8 + (int64_t)sizeof(W)) * len);
   }
 }
 
@@ -343,7 +618,7 @@ __global__ void __launch_bounds__(1024) k_huge_decide(Args A, const int64_t *tab
     int64_t *vals = A.gvals + tab_off[k];
     int32_t occ = A.gocc[k];
     int32_t d = A.C[i];
-    int64_t m2 = A.cnt->m2, Ki = A.K[i];
+    int64_t m2 = A.m2, Ki = A.K[i];
     Best b{0, -1, 0, 0};
     for (int32_t t = threadIdx.x; t < occ; t += blockDim.x) {
       int32_t s = list[t];
@@ -376,28 +651,38 @@ __global__ void __launch_bounds__(1024) k_huge_decide(Args A, const int64_t *tab
 // append the in-range ones to the degree bins.
 __global__ void k_collect(int64_t n, uint32_t *unproc, int cls, int classes_mask, const uint8_t *in_range,
                           const int32_t *deg, int32_t *bins, DevCounters *cnt) {
+  // Each warp reads 32 bitmap words at once and visits only the non-zero
+  // ones (a frontier is usually sparse), one vertex per lane.
   int lane = threadIdx.x & 31;
-  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
-    int64_t v = base + lane;
-    uint32_t word = unproc[base >> 5];
-    bool take = v < n && ((word >> lane) & 1u) && ld_class_of(v, classes_mask) == cls;
-    uint32_t taken = __ballot_sync(LD_FULL, take);
-    if (lane == 0 && taken) atomicAnd(&unproc[base >> 5], ~taken);
-    bool work = take && (!in_range || in_range[v]);
-    int bin = -1;
-    if (work) {
-      // a vertex without arcs has no candidate community: taking it is its visit
-      int dg = deg[v];
-      bin = dg == 0 ? -1 : dg <= BIN_WARP_MAX ? BIN_WARP : (dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE);
-    }
+  int64_t nwords = (n + 31) >> 5;
+  int64_t warp = ld_gtid() >> 5, nwarps = ld_gstride() >> 5;
+  for (int64_t w0 = warp * 32; w0 < nwords; w0 += nwarps * 32) {
+    uint32_t word = w0 + lane < nwords ? unproc[w0 + lane] : 0u;
+    uint32_t nz = __ballot_sync(LD_FULL, word != 0u);
+    while (nz) {
+      int src = __ffs(nz) - 1;
+      nz &= nz - 1;
+      uint32_t wd = __shfl_sync(LD_FULL, word, src);
+      int64_t v = ((w0 + src) << 5) + lane;
+      bool take = v < n && ((wd >> lane) & 1u) && ld_class_of(v, classes_mask) == cls;
+      uint32_t taken = __ballot_sync(LD_FULL, take);
+      if (lane == 0 && taken) atomicAnd(&unproc[w0 + src], ~taken);
+      bool work = take && (!in_range || in_range[v]);
+      int bin = -1;
+      if (work) {
+        // a vertex without arcs has no candidate community: taking it is its visit
+        int dg = deg[v];
+        bin = dg == 0 ? -1 : dg <= BIN_TINY_MAX ? BIN_TINY : dg <= BIN_WARP_MAX ? BIN_WARP : dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE;
+      }
 #pragma unroll
-    for (int b = 0; b < NBINS; b++) {
-      uint32_t m = __ballot_sync(LD_FULL, bin == b);
-      if (!m) continue;
-      int32_t pos0 = 0;
-      if (lane == __ffs(m) - 1) pos0 = atomicAdd(&cnt->bin_count[b], __popc(m));
-      pos0 = __shfl_sync(LD_FULL, pos0, __ffs(m) - 1);
-      if (bin == b) bins[(int64_t)b * n + pos0 + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
+      for (int b = 0; b < NBINS; b++) {
+        uint32_t m = __ballot_sync(LD_FULL, bin == b);
+        if (!m) continue;
+        int32_t pos0 = 0;
+        if (lane == __ffs(m) - 1) pos0 = atomicAdd(&cnt->bin_count[b], __popc(m));
+        pos0 = __shfl_sync(LD_FULL, pos0, __ffs(m) - 1);
+        if (bin == b) bins[(int64_t)b * n + pos0 + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
+      }
     }
   }
 }
@@ -466,7 +751,7 @@ __global__ void k_refine_collect(const int32_t *cand_in, const int32_t *count_in
     int bin = -1;
     if (keep) {
       int dg = deg[i];  // without arcs: no proposal (prop stays -1)
-      bin = dg == 0 ? -1 : dg <= BIN_WARP_MAX ? BIN_WARP : (dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE);
+      bin = dg == 0 ? -1 : dg <= BIN_TINY_MAX ? BIN_TINY : dg <= BIN_WARP_MAX ? BIN_WARP : dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE;
     }
     uint32_t km = __ballot_sync(LD_FULL, keep);
     if (km) {
@@ -529,6 +814,7 @@ Args make_args(leiden_handle *h, const LevelGraph &g) {
   A.movers = h->movers;
   A.mtarget = h->mtarget;
   A.cnt = h->dcnt;
+  A.m2 = h->m2;
   A.async_mode = h->p.deterministic ? 0 : 1;
   A.classes_mask = h->p.classes - 1;
   return A;
@@ -538,21 +824,26 @@ template <int KIND>
 void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
   cudaStream_t s = h->stream;
   int sms = h->sm_count;
+  A.list_tiny = h->bins + (int64_t)BIN_TINY * g.n;
+  A.count_tiny = &h->dcnt->bin_count[BIN_TINY];
   for (int b = 0; b < NBINS; b++) {
     A.list = h->bins + (int64_t)b * g.n;
     A.count = &h->dcnt->bin_count[b];
+    if (b == BIN_TINY) continue;  // with the warp bin
     if (b == BIN_HUGE && g.maxdeg <= BIN_BLOCK_MAX) continue;
     if (b == BIN_BLOCK && g.maxdeg <= BIN_WARP_MAX) continue;
     if (b == BIN_WARP) {
-      int grid = sms * 8;
-      if (KIND == KIND_MOVE) kt_begin(h);
+      int grid = sms * 4;  // one wave at four resident blocks per SM
+      if (KIND == KIND_MOVE) kt_begin(h, KT_WARP);
       if (g.w64) ld_note_launch(), k_decide_warp<int64_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
       else ld_note_launch(), k_decide_warp<int32_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
       if (KIND == KIND_MOVE) kt_end(h);
     } else if (b == BIN_BLOCK) {
       int grid = sms * 4;
+      if (KIND == KIND_MOVE) kt_begin(h, KT_BLOCK);
       if (g.w64) ld_note_launch(), k_decide_block<int64_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
       else ld_note_launch(), k_decide_block<int32_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
+      if (KIND == KIND_MOVE) kt_end(h);
     } else {
       // tables for every listed vertex at once: at most huge_slots slots
       if (!ensure_hslots(h, g.huge_slots)) { h->fatal = LEIDEN_ERR_OOM; h->err = "global table scratch"; return; }
@@ -564,8 +855,10 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
       int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
       launch_table_plan(A.list, A.count, g.deg, nullptr, tab_off, ch_off, s);
       ld_note_launch(), k_huge_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
+      if (KIND == KIND_MOVE) kt_begin(h, KT_HUGE_SCAN);
       if (g.w64) ld_note_launch(), k_huge_scan<int64_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
       else ld_note_launch(), k_huge_scan<int32_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
+      if (KIND == KIND_MOVE) kt_end(h);
       ld_note_launch(), k_huge_decide<KIND><<<sms * 2, HUGE_THREADS, 0, s>>>(A, tab_off);
     }
   }
@@ -619,7 +912,7 @@ void lm_prepare(leiden_handle *h, const LevelGraph &g) {
 void lm_subsweep(leiden_handle *h, const LevelGraph &g, int cls, const uint8_t *in_range, int dynamic) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4 + sizeof(int32_t), s);  // bins + movers
-  ld_note_launch(), k_collect<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, h->unproc, cls, h->p.classes - 1, in_range, g.deg, h->bins,
+  ld_note_launch(), k_collect<<<grid_for((g.n + 31) / 32, 256), 256, 0, s>>>(g.n, h->unproc, cls, h->p.classes - 1, in_range, g.deg, h->bins,
                                                h->dcnt);
   Args A = make_args(h, g);
   A.in_range = in_range;

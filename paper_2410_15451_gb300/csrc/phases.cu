@@ -352,6 +352,9 @@ __global__ void __launch_bounds__(256) k_agg_block(AggArgs A) {
 // (ch_off); the filled slots are listed so the emission visits only them.
 template <typename W>
 __global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t *tab_off, const int64_t *ch_off) {
+  __shared__ WarpTable WT[8];  // per-warp sums by community, flushed into the global table
+  WarpTable &T8 = WT[threadIdx.x >> 5];
+  wt_init(T8);
   int64_t count = *A.count;
   int64_t nch = ch_off[count];
   const W *w = (const W *)A.w;
@@ -386,8 +389,10 @@ __global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t
         c = A.C[A.col[arc]];
         wa = (int64_t)w[arc];
       }
-      ld_gtable_insert_warp(keys, vals, list, &A.gocc[lo], (int)(T - 1), valid, c, wa);
+      if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+      wt_insert_warp(T8, valid, c, wa);
     }
+    wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
   }
 }
 

@@ -11,47 +11,107 @@ constexpr uint64_t EMPTY64 = ~0ull;
 
 __device__ __forceinline__ uint64_t hash64(uint64_t k) { return ld_splitmix64(k); }
 
-// Overlap weights: sum of K over vertices with (old, new) = key.
-__global__ void k_tr_clear(int64_t cap, uint64_t *keys, int64_t *vals) {
-  for (int64_t s = ld_gtid(); s < cap; s += ld_gstride()) { keys[s] = EMPTY64; vals[s] = 0; }
+// Best successor of each old community o: the new community with the largest
+// overlap weight W(o, c) = sum of K_i over i with C^{t-1}_i = o and C_i = c,
+// ties to the lowest new id.  Most communities keep a strict majority of
+// their weight in one new community, and that one is then the unique
+// argmax: a candidate (the new label of any member) is checked with two
+// coalesced sweeps, and only communities without a majority go through the
+// pair table.
+__global__ void k_trc_cand(int64_t N, const int32_t *Cold, const int32_t *Cnew, int32_t *cand) {
+  for (int64_t i = ld_gtid(); i < N; i += ld_gstride()) cand[Cold[i]] = Cnew[i];  // any member will do
 }
-__global__ void k_tr_insert(int64_t N, const int32_t *Cold, const int32_t *Cnew, const int64_t *K, int64_t cap,
-                            uint64_t *keys, int64_t *vals) {
+__global__ void k_trc_overlap(int64_t N, const int32_t *Cold, const int32_t *Cnew, const int64_t *K,
+                              const int32_t *cand, int64_t *tot, int64_t *ov) {
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < N; base += ld_gstride()) {
+    int64_t i = base + lane;
+    int32_t o = i < N ? Cold[i] : -1 - lane;
+    int64_t k = 0, kin = 0;
+    if (i < N) {
+      k = K[i];
+      kin = Cnew[i] == cand[o] ? k : 0;
+    }
+    uint32_t peers = __match_any_sync(LD_FULL, o);
+    int64_t st = ld_group_sum_i64(peers, k), so = ld_group_sum_i64(peers, kin);
+    if (i < N && ld_group_leader(peers)) {
+      if (st) atomicAdd((unsigned long long *)&tot[o], (unsigned long long)st);
+      if (so) atomicAdd((unsigned long long *)&ov[o], (unsigned long long)so);
+    }
+  }
+}
+// bw/bc of the majority communities; the others are flagged: 1 = through
+// the pair table, 2 = weight 0 (every member has K = 0, e.g. isolated
+// vertices): every pair weighs 0, so the lowest new label of a member wins.
+__global__ void k_trc_majority(int64_t N, const int32_t *cand, const int64_t *tot, const int64_t *ov,
+                               long long *bw, int32_t *bc, int32_t *flag) {
+  for (int64_t o = ld_gtid(); o < N; o += ld_gstride()) {
+    int f = 0;
+    if (cand[o] >= 0) {
+      if (tot[o] == 0) { bw[o] = 0; f = 2; }
+      else if (2 * ov[o] > tot[o]) { bw[o] = ov[o]; bc[o] = cand[o]; }
+      else f = 1;
+    }
+    flag[o] = f;
+  }
+}
+// Pair weights of the flagged communities.  The table is empty between
+// calls; each filled slot is listed (count in *occ) and emptied by its reader.
+__global__ void k_trc_insert(int64_t N, const int32_t *Cold, const int32_t *Cnew, const int64_t *K,
+                             const int32_t *flag, int32_t *bc, int64_t cap, uint64_t *keys, int64_t *vals,
+                             int32_t *list, int32_t *occ) {
   uint64_t mask = (uint64_t)cap - 1;
   int lane = threadIdx.x & 31;
   for (int64_t base = (ld_gtid() & ~31ll); base < N; base += ld_gstride()) {
     int64_t i = base + lane;
-    uint64_t key = i < N ? (((uint64_t)(uint32_t)Cold[i] << 32) | (uint32_t)Cnew[i]) : EMPTY64 - 1 - lane;
-    int64_t kw = i < N ? K[i] : 0;
-    // lanes with the same (old, new) pair insert once with their summed weight
+    bool take = false;
+    uint64_t key = EMPTY64 - 1 - lane;
+    int64_t kw = 0;
+    if (i < N) {
+      int32_t o = Cold[i];
+      int f = flag[o];
+      if (f == 1) {
+        take = true;
+        key = ((uint64_t)(uint32_t)o << 32) | (uint32_t)Cnew[i];
+        kw = K[i];
+      } else if (f == 2) {
+        atomicMin(&bc[o], Cnew[i]);
+      }
+    }
+    if (!__any_sync(LD_FULL, take)) continue;
     uint32_t peers = __match_any_sync(LD_FULL, (unsigned long long)key);
     int64_t sum = ld_group_sum_i64(peers, kw);
-    if (i >= N || !ld_group_leader(peers)) continue;
-    uint64_t s = hash64(key) & mask;
+    if (!take || !ld_group_leader(peers)) continue;
+    uint64_t sl = hash64(key) & mask;
     while (true) {
-      unsigned long long k = atomicCAS((unsigned long long *)&keys[s], EMPTY64, key);
+      unsigned long long k = atomicCAS((unsigned long long *)&keys[sl], EMPTY64, key);
+      if (k == EMPTY64) list[atomicAdd(occ, 1)] = (int32_t)sl;
       if (k == EMPTY64 || k == key) {
-        atomicAdd((unsigned long long *)&vals[s], (unsigned long long)sum);
+        atomicAdd((unsigned long long *)&vals[sl], (unsigned long long)sum);
         break;
       }
-      s = (s + 1) & mask;
+      sl = (sl + 1) & mask;
     }
   }
 }
-// For each old community: largest overlap weight ...
-__global__ void k_tr_best_new_w(int64_t cap, const uint64_t *keys, const int64_t *vals, long long *bw) {
-  for (int64_t s = ld_gtid(); s < cap; s += ld_gstride()) {
-    if (keys[s] == EMPTY64) continue;
-    atomicMax(&bw[keys[s] >> 32], (long long)vals[s]);
+__global__ void k_trc_best_w(const int32_t *occ, const int32_t *list, const uint64_t *keys, const int64_t *vals,
+                             long long *bw) {
+  int64_t m = *occ;
+  for (int64_t t = ld_gtid(); t < m; t += ld_gstride()) {
+    int32_t sl = list[t];
+    atomicMax(&bw[keys[sl] >> 32], (long long)vals[sl]);
   }
 }
-// ... and the lowest new id reaching it.
-__global__ void k_tr_best_new_c(int64_t cap, const uint64_t *keys, const int64_t *vals, const long long *bw,
-                                int32_t *bc) {
-  for (int64_t s = ld_gtid(); s < cap; s += ld_gstride()) {
-    if (keys[s] == EMPTY64) continue;
-    uint32_t b = (uint32_t)(keys[s] >> 32);
-    if (vals[s] == bw[b]) atomicMin(&bc[b], (int32_t)(keys[s] & 0xffffffffu));
+__global__ void k_trc_best_c(const int32_t *occ, const int32_t *list, uint64_t *keys, int64_t *vals,
+                             const long long *bw, int32_t *bc) {
+  int64_t m = *occ;
+  for (int64_t t = ld_gtid(); t < m; t += ld_gstride()) {
+    int32_t sl = list[t];
+    uint64_t key = keys[sl];
+    uint32_t o = (uint32_t)(key >> 32);
+    if (vals[sl] == bw[o]) atomicMin(&bc[o], (int32_t)(key & 0xffffffffu));
+    keys[sl] = EMPTY64;  // leave the table empty
+    vals[sl] = 0;
   }
 }
 // For each new community: among the old communities that picked it, the
@@ -162,17 +222,27 @@ void track_communities(leiden_handle *h) {
   cudaStream_t s = h->stream;
   int64_t N = h->n;
   int gN = grid_for(N, TB);
-  ld_note_launch(), k_tr_clear<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals);
-  ld_note_launch(), k_tr_insert<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, h->K, h->tr_cap, h->tr_keys, h->tr_vals);
   long long *bw = (long long *)h->lbuf0, *ow = (long long *)h->lbuf1;
   int32_t *bc = h->ibuf0, *ob = h->ibuf1, *used = h->ibuf2;
+  int32_t *cand = h->mtarget, *flag = h->movers;
+  int64_t *tot = h->Kp, *ov = h->Sp;
   launch_fill_i64((int64_t *)bw, -1, N, s);
   launch_fill_i32(bc, INT_MAX, N, s);
   launch_fill_i64((int64_t *)ow, -1, N, s);
   launch_fill_i32(ob, INT_MAX, N, s);
+  launch_fill_i32(cand, -1, N, s);
   cudaMemsetAsync(used, 0, (size_t)N * sizeof(int32_t), s);
-  ld_note_launch(), k_tr_best_new_w<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals, bw);
-  ld_note_launch(), k_tr_best_new_c<<<grid_for(h->tr_cap, TB), TB, 0, s>>>(h->tr_cap, h->tr_keys, h->tr_vals, bw, bc);
+  cudaMemsetAsync(tot, 0, (size_t)N * sizeof(int64_t), s);
+  cudaMemsetAsync(ov, 0, (size_t)N * sizeof(int64_t), s);
+  cudaMemsetAsync(&h->dcnt->tr_occ, 0, sizeof(int32_t), s);
+  ld_note_launch(), k_trc_cand<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, cand);
+  ld_note_launch(), k_trc_overlap<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, h->K, cand, tot, ov);
+  ld_note_launch(), k_trc_majority<<<gN, TB, 0, s>>>(N, cand, tot, ov, bw, bc, flag);
+  int32_t *occ = &h->dcnt->tr_occ;
+  ld_note_launch(), k_trc_insert<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, h->K, flag, bc, h->tr_cap, h->tr_keys, h->tr_vals,
+                                                   h->tr_list, occ);
+  ld_note_launch(), k_trc_best_w<<<h->sm_count * 8, TB, 0, s>>>(occ, h->tr_list, h->tr_keys, h->tr_vals, bw);
+  ld_note_launch(), k_trc_best_c<<<h->sm_count * 8, TB, 0, s>>>(occ, h->tr_list, h->tr_keys, h->tr_vals, bw, bc);
   ld_note_launch(), k_tr_best_old_w<<<gN, TB, 0, s>>>(N, bc, bw, ow);
   ld_note_launch(), k_tr_best_old_b<<<gN, TB, 0, s>>>(N, bc, bw, ow, ob);
   ld_note_launch(), k_tr_new_used<<<gN, TB, 0, s>>>(N, h->Ctop, used);

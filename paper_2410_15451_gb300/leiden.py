@@ -36,8 +36,8 @@ class leiden_stats(ctypes.Structure):
         "passes", "lm_iterations", "lm_vertices", "lm_arcs", "lm_moves", "refine_vertices", "refine_arcs",
         "aggregate_arcs", "affected", "communities", "batch_arcs")] + [(k, ctypes.c_double) for k in (
         "ms_total", "ms_batch", "ms_move", "ms_refine", "ms_aggregate", "ms_track")] + [
-        (k, ctypes.c_int64) for k in ("lm_warp_launches", "lm_warp_vertices", "lm_warp_arcs", "lm_warp_bytes")] + [
-        ("ms_lm_warp", ctypes.c_double)]
+        (k, ctypes.c_int64 * 3) for k in ("lmk_launches", "lmk_vertices", "lmk_arcs", "lmk_bytes")] + [
+        ("lmk_ms", ctypes.c_double * 3)]
 
 
 class LeidenError(RuntimeError):
@@ -208,7 +208,11 @@ def leiden_get_trace(h) -> dict:
 def leiden_get_stats(h) -> dict:
     s = leiden_stats()
     _check(h, load().leiden_get_stats(h, ctypes.byref(s)))
-    return {k: getattr(s, k) for k, _ in leiden_stats._fields_}
+    out = {}
+    for k, _ in leiden_stats._fields_:
+        v = getattr(s, k)
+        out[k] = list(v) if isinstance(v, ctypes.Array) else v
+    return out
 
 
 def leiden_kernel_launches() -> int:
