@@ -201,6 +201,36 @@ leiden_status leiden_get_trace(leiden_handle *h, int64_t *trace);
 /* Counters and phase times of the last call. */
 leiden_status leiden_get_stats(leiden_handle *h, leiden_stats *stats);
 
+/* ---- Batched handles: many graphs, one launch per kernel for all of them ----
+ *
+ * leiden_create_batched() takes G graphs concatenated with vertex offsets:
+ * graph g owns the vertices vertex_offsets[g] .. vertex_offsets[g+1]-1 of one
+ * symmetric CSR (offsets[n+1], cols, weights as in leiden_create, with
+ * n = vertex_offsets[G]); no arc may join two graphs (LEIDEN_ERR_ARG).  Every
+ * call on the handle then processes all graphs at once, each exactly as a
+ * handle of its own would (Section 4: same passes, iterations, tau, 2m and
+ * tracking per graph; the deterministic schedule gives the same memberships
+ * bit for bit, offset by vertex_offsets[g]).  Batches passed to
+ * leiden_update use the concatenated vertex ids; an edge between two graphs
+ * is LEIDEN_ERR_BATCH.  Community ids of graph g stay in its vertex range.
+ * Batched handles with G > 1 run the deterministic schedule only
+ * (params->deterministic = 0 is LEIDEN_ERR_ARG).  Library extension: the
+ * paper processes one graph at a time. */
+leiden_status leiden_create_batched(const leiden_params *params, int32_t graphs, const int64_t *vertex_offsets,
+                                    const int64_t *offsets, const int32_t *cols, const int32_t *weights,
+                                    void *cuda_stream, leiden_handle **out);
+
+/* Number of graphs of the handle (1 for leiden_create handles). */
+int32_t leiden_batch_graphs(const leiden_handle *h);
+
+/* Per-graph trace of the last call, same layout as leiden_get_trace ([1] is
+ * |dV| of that graph). */
+leiden_status leiden_batch_trace(leiden_handle *h, int32_t graph, int64_t *trace);
+
+/* Modularity (Eq. 1) of each graph's current membership, q_out[G], with its
+ * own 2m. */
+leiden_status leiden_batch_modularity(leiden_handle *h, double *q_out);
+
 /* Number of CUDA kernels this library has launched in the process since it
  * was loaded, over all handles and threads (a relaxed atomic counter; read
  * it before and after a call to count that call's launches).  Library

@@ -14,6 +14,25 @@ static std::atomic<int64_t> g_launches{0};
 
 void ld_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+GraphCounters gc_layout(void *base, int G) {
+  char *q = (char *)base;
+  GraphCounters c;
+  c.dq = (unsigned long long *)q;  q += 16 * (size_t)G;
+  c.sq = (unsigned long long *)q;  q += 16 * (size_t)G;
+  c.moves = (int64_t *)q;          q += 8 * (size_t)G;
+  c.m2 = (int64_t *)q;             q += 8 * (size_t)G;
+  c.sigma = (int64_t *)q;          q += 8 * (size_t)G;
+  c.accepted = (int32_t *)q;       q += 4 * (size_t)G;
+  c.ncomm = (int32_t *)q;          q += 4 * (size_t)G;
+  c.refined = (uint8_t *)q;        q += (size_t)G;
+  c.lm_on = (uint8_t *)q;          q += (size_t)G;
+  c.cont = (uint8_t *)q;
+  return c;
+}
+
+// 16+16+8+8+8+4+4+1+1+1 = 67 bytes per graph, rounded up.
+size_t gc_block_bytes(int G) { return 72 * (size_t)G + 64; }
+
 void kt_begin(leiden_handle *h, int k) {
   if (!(h->p.collect_stats & 2)) return;
   size_t need = 2 * (size_t)(h->kt_used + 1);
@@ -101,6 +120,7 @@ void sync_counters(leiden_handle *h) {
 
 LevelGraph level0(leiden_handle *h) {
   LevelGraph g;
+  g.gid = h->gid0;
   g.n = h->n;
   g.off = h->g_off;
   g.deg = h->g_deg;
@@ -122,10 +142,25 @@ void mark(leiden_handle *h, int k) {
   if (h->p.collect_stats & 1) cudaEventRecord(h->ev[k], h->stream);
 }
 
+constexpr int TRACE_WORDS = 2 + 10 * 25;
+
+// Copies the per-graph counter block of a batched handle to its pinned host
+// mirror (with the device counters) and waits.
+void sync_all(leiden_handle *h) {
+  cudaMemcpyAsync(h->hcnt, h->dcnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, h->stream);
+  if (h->G > 1) cudaMemcpyAsync(h->gc_host, h->gc.dq, h->gc_bytes, cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+}
+
 // Alg. leiden: passes of local moving, subset renumbering, splitting,
 // refinement, then renumbering, lookup and aggregation; finally lookup and
 // tracking.  Expects: Cp = C^{t-1} copy source in h->C, Kp/Sp from h->K,
 // h->Sig, dS/dR marked, dV = affected.
+//
+// A batched handle runs the same loop over all its graphs at once; each
+// graph keeps its own iteration count and stops iterating when its own dQ
+// reaches tau, keeps its own refinement rounds, and leaves the pass loop at
+// its own break (its final lookup is done then and it is not aggregated).
 leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range) {
   cudaStream_t s = h->stream;
   const leiden_params &p = h->p;
@@ -133,6 +168,26 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   memset(h->trace, 0, sizeof(h->trace));
   h->kt_used = 0;
   for (int k = 0; k < KT_KERNELS; k++) { h->kt_ms[k] = 0; h->kt_launches[k] = 0; }
+  const bool B = h->G > 1;
+  const int G = h->G;
+  GraphCounters hg = B ? gc_layout(h->gc_host, G) : GraphCounters{};
+  std::vector<int64_t> loff_h;
+  std::vector<int> li_g, rounds_g;
+  std::vector<char> inlvl, lmon, refany, refdone, cont;
+  if (B) {
+    h->gtrace.assign((size_t)G * TRACE_WORDS, 0);
+    loff_h = h->voff;
+    h->d_loff = h->d_loffb[0];
+    CK(cudaMemcpyAsync(h->d_loff, h->d_voff, (size_t)(G + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    inlvl.assign(G, 1);
+    li_g.assign(G, 0);
+    rounds_g.assign(G, 0);
+    lmon.assign(G, 0);
+    refany.assign(G, 0);
+    refdone.assign(G, 0);
+    cont.assign(G, 0);
+  }
+  auto gtr = [&](int gi, int lp) -> int64_t * { return &h->gtrace[(size_t)gi * TRACE_WORDS + 2 + lp * 25]; };
   // initialisation
   mark_unprocessed_from_flags(h, h->dV, N);
   launch_iota_i32(h->Ctop, N, s);
@@ -145,6 +200,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   double tau = p.tau;
   int slot = 0;
   int passes = 0;
+  bool looked_up = false;  // batched: every graph had its final lookup
   leiden_stats &st = h->stats;
   float t_move = 0, t_ref = 0, t_agg = 0;
   int64_t moves_total = 0;
@@ -154,14 +210,33 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     int64_t *tr = lp < 10 ? &h->trace[2 + lp * 25] : tr_spare;  // the trace keeps the first 10 passes
     passes++;
     tr[0] = n;
+    if (B) {
+      for (int gi = 0; gi < G; gi++) {
+        lmon[gi] = inlvl[gi];
+        li_g[gi] = p.max_iterations;
+        rounds_g[gi] = 0;
+        refany[gi] = 0;
+        refdone[gi] = !inlvl[gi];
+        if (inlvl[gi] && lp < 10) {
+          gtr(gi, lp)[0] = loff_h[gi + 1] - loff_h[gi];
+          h->gtrace[(size_t)gi * TRACE_WORDS] = lp + 1;
+        }
+      }
+      memcpy(hg.lm_on, lmon.data(), (size_t)G);
+      CK(cudaMemcpyAsync(h->gc.lm_on, hg.lm_on, (size_t)G, cudaMemcpyHostToDevice, s));
+    }
     mark(h, 2);
     lm_prepare(h, g);
     int li = p.max_iterations;
     for (int it = 0; it < p.max_iterations; it++) {
       CK(cudaMemsetAsync(&h->dcnt->dq[0], 0, 2 * sizeof(unsigned long long), s));
       CK(cudaMemsetAsync(&h->dcnt->moves, 0, sizeof(int64_t), s));
+      if (B) {
+        CK(cudaMemsetAsync(h->gc.dq, 0, (size_t)G * 2 * sizeof(unsigned long long), s));
+        CK(cudaMemsetAsync(h->gc.moves, 0, (size_t)G * sizeof(int64_t), s));
+      }
       for (int cls = 0; cls < p.classes; cls++) lm_subsweep(h, g, cls, lp == 0 ? in_range : nullptr, dynamic);
-      sync_counters(h);
+      sync_all(h);
       kt_resolve(h);
       CK(cudaGetLastError());
       CKF();
@@ -170,33 +245,62 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
       if (it < 20) tr[5 + it] = mv;
       moves_total += mv;
       st.lm_iterations++;
-      if (gains_to_dq(dq, m2) <= tau) { li = it + 1; break; }
+      if (!B) {
+        if (gains_to_dq(dq, m2) <= tau) { li = it + 1; break; }
+        continue;
+      }
+      bool any = false;
+      for (int gi = 0; gi < G; gi++) {
+        if (!lmon[gi]) continue;
+        if (lp < 10 && it < 20) gtr(gi, lp)[5 + it] = hg.moves[gi];
+        if (gains_to_dq(read_i128(&hg.dq[2 * gi]), h->m2g[gi]) <= tau) {
+          li_g[gi] = it + 1;
+          lmon[gi] = 0;
+        } else {
+          any = true;
+        }
+      }
+      if (!any) { li = it + 1; break; }
+      memcpy(hg.lm_on, lmon.data(), (size_t)G);
+      CK(cudaMemcpyAsync(h->gc.lm_on, hg.lm_on, (size_t)G, cudaMemcpyHostToDevice, s));
     }
     tr[1] = li;
     mark(h, 3);
     subset_renumber(h, n);
     split_communities(h, g);
     CK(cudaMemcpyAsync(h->CB, h->Cp, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+    if (B) CK(cudaMemsetAsync(h->gc.refined, 0, (size_t)G, s));
     refine_reset(h, g);
     int rounds = 0;
     int refined_any = 0;
     // Both modes repeat rounds until no move applies: in the in-place mode a
     // singleton whose target was taken retries against the updated state.
+    // A graph of a batch counts the rounds up to its first round without a
+    // move (its state does not change after that).
     int max_rounds = p.max_iterations;
     for (int r = 0; r < max_rounds; r++) {
+      if (B) CK(cudaMemsetAsync(h->gc.accepted, 0, (size_t)G * sizeof(int32_t), s));
       refine_round(h, g, r & 1);
       rounds++;
-      sync_counters(h);
+      sync_all(h);
       CK(cudaGetLastError());
       CKF();
       if (r == 0) refined_any = h->hcnt->cand_count[0] > 0;
+      if (B) {
+        for (int gi = 0; gi < G; gi++) {
+          if (r == 0) refany[gi] = hg.refined[gi];
+          if (refdone[gi]) continue;
+          rounds_g[gi]++;
+          if (hg.accepted[gi] == 0) refdone[gi] = 1;
+        }
+      }
       if (h->hcnt->accepted == 0) break;
     }
-    if (max_rounds == 0) { sync_counters(h); refined_any = h->hcnt->cand_count[0] > 0; }
     tr[3] = refined_any;
     tr[4] = rounds;
-    count_communities(h, n);
-    sync_counters(h);
+    if (B) CK(cudaMemsetAsync(h->gc.ncomm, 0, (size_t)G * sizeof(int32_t), s));
+    count_communities(h, n, g.gid);
+    sync_all(h);
     tr[2] = h->hcnt->list_count;
     mark(h, 4);
     if (h->p.collect_stats & 1) {
@@ -204,18 +308,42 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
       t_move += ev_ms(h, 2, 3);
       t_ref += ev_ms(h, 3, 4);
     }
-    if (li <= 1 && !refined_any) break;
-    if (li <= 1 && lp > 0) break;
-    if (lp == p.max_passes - 1) {
-      // the pass limit is reached: lookup with C' below, as when breaking
-      break;
+    if (!B) {
+      if (li <= 1 && !refined_any) break;
+      if (li <= 1 && lp > 0) break;
+      if (lp == p.max_passes - 1) {
+        // the pass limit is reached: lookup with C' below, as when breaking
+        break;
+      }
+    } else {
+      bool any_cont = false;
+      for (int gi = 0; gi < G; gi++) {
+        cont[gi] = 0;
+        if (!inlvl[gi]) continue;
+        if (lp < 10) {
+          int64_t *t = gtr(gi, lp);
+          t[1] = li_g[gi];
+          t[2] = hg.ncomm[gi];
+          t[3] = refany[gi];
+          t[4] = rounds_g[gi];
+        }
+        bool brk = (li_g[gi] <= 1 && !refany[gi]) || (li_g[gi] <= 1 && lp > 0) || lp == p.max_passes - 1;
+        cont[gi] = !brk;
+        any_cont = any_cont || !brk;
+      }
+      memcpy(hg.cont, cont.data(), (size_t)G);
+      CK(cudaMemcpyAsync(h->gc.cont, hg.cont, (size_t)G, cudaMemcpyHostToDevice, s));
+      break_lookup(h);
+      if (!any_cont) { looked_up = true; break; }
     }
-    renumber_dense(h, n);
-    sync_counters(h);
+    renumber_dense(h, n, g.gid);
+    int64_t *loff_next = B ? (h->d_loff == h->d_loffb[0] ? h->d_loffb[1] : h->d_loffb[0]) : nullptr;
+    if (B) next_level_ids(h, n, g.gid, h->gidL[slot], loff_next);
     int64_t ncomm = 0;
     {
       int64_t tot = 0;
       CK(cudaMemcpyAsync(&tot, h->lbuf0 + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+      if (B) CK(cudaMemcpyAsync(loff_h.data(), loff_next, (size_t)(G + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       ncomm = tot;
     }
@@ -235,6 +363,11 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     y.w64 = true;
     y.maxdeg = h->hcnt->max_count;
     y.huge_slots = h->hcnt->huge_slots;
+    if (B) {
+      y.gid = h->gidL[slot];
+      h->d_loff = loff_next;
+      for (int gi = 0; gi < G; gi++) inlvl[gi] = cont[gi];
+    }
     g = y;
     slot ^= 1;
     tau /= p.tau_drop;
@@ -245,7 +378,8 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     }
   }
   mark(h, 6);
-  lookup_dendrogram(h);
+  if (!B) lookup_dendrogram(h);
+  else if (!looked_up) { h->err = "batched pass loop ended without a final lookup"; return LEIDEN_ERR_STATE; }
   track_communities(h);
   mark(h, 7);
   sync_counters(h);
@@ -291,9 +425,13 @@ leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_de
   leiden_status st = batch_apply_and_mark(h, d_del, n_del, d_ins, n_ins, (int)mode);
   if (st != LEIDEN_OK) return st;
   mark(h, 1);
-  sync_counters(h);
+  sync_all(h);
   CK(cudaGetLastError());
   h->m2 = h->hcnt->m2;
+  if (h->G > 1) {
+    GraphCounters hg = gc_layout(h->gc_host, h->G);
+    for (int gi = 0; gi < h->G; gi++) h->m2g[gi] = hg.m2[gi];
+  }
   level_maxdeg(h, h->g_deg, h->n);
   sync_counters(h);
   h->g_maxdeg = h->hcnt->max_count;
@@ -485,6 +623,109 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   return LEIDEN_OK;
 }
 
+leiden_status leiden_create_batched(const leiden_params *params, int32_t graphs, const int64_t *vertex_offsets,
+                                    const int64_t *offsets, const int32_t *cols, const int32_t *weights,
+                                    void *cuda_stream, leiden_handle **out) {
+  g_create_error.clear();
+  if (!out) { g_create_error = "out is NULL"; return LEIDEN_ERR_ARG; }
+  *out = nullptr;
+  if (graphs < 1 || !vertex_offsets || vertex_offsets[0] != 0) {
+    g_create_error = "invalid graph count or vertex offsets";
+    return LEIDEN_ERR_ARG;
+  }
+  for (int32_t gi = 0; gi < graphs; gi++)
+    if (vertex_offsets[gi + 1] <= vertex_offsets[gi]) {
+      g_create_error = "every graph needs at least one vertex (vertex offsets strictly increasing)";
+      return LEIDEN_ERR_ARG;
+    }
+  if (params && !params->deterministic && graphs > 1) {
+    g_create_error = "batched handles run the deterministic (snapshot) schedule";
+    return LEIDEN_ERR_ARG;
+  }
+  int64_t n = vertex_offsets[graphs];
+  if (n < 1 || n > 0x7ffffffe || !offsets) { g_create_error = "invalid vertex count"; return LEIDEN_ERR_ARG; }
+  std::vector<int32_t> gid((size_t)n);
+  for (int32_t gi = 0; gi < graphs; gi++)
+    for (int64_t v = vertex_offsets[gi]; v < vertex_offsets[gi + 1]; v++) gid[v] = gi;
+  for (int64_t v = 0; v < n; v++)
+    for (int64_t a = offsets[v]; a < offsets[v + 1]; a++)
+      if (cols && cols[a] >= 0 && cols[a] < n && gid[cols[a]] != gid[v]) {
+        g_create_error = "an arc joins two graphs of the batch";
+        return LEIDEN_ERR_ARG;
+      }
+  leiden_handle *h = nullptr;
+  leiden_status st = leiden_create(params, n, offsets, cols, weights, cuda_stream, &h);
+  if (st != LEIDEN_OK) return st;
+  if (graphs == 1) { *out = h; return LEIDEN_OK; }
+  h->G = graphs;
+  h->voff.assign(vertex_offsets, vertex_offsets + graphs + 1);
+  h->m2g.assign(graphs, 0);
+  h->gc_bytes = gc_block_bytes(graphs);
+  cudaError_t e = cudaSuccess;
+  auto A = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
+  void *gcd = nullptr;
+  A(cudaMalloc(&gcd, h->gc_bytes));
+  if (gcd) h->owned.push_back(gcd);
+  A(cudaMallocHost(&h->gc_host, h->gc_bytes));
+  A(dalloc(h, &h->d_voff, graphs + 1));
+  A(dalloc(h, &h->d_loffb[0], graphs + 1));
+  A(dalloc(h, &h->d_loffb[1], graphs + 1));
+  A(dalloc(h, &h->gid0, n));
+  A(dalloc(h, &h->gidL[0], n));
+  A(dalloc(h, &h->gidL[1], n));
+  A(dalloc(h, &h->mgain, 2 * n));
+  if (e == cudaSuccess) {
+    h->gc = gc_layout(gcd, graphs);
+    h->d_loff = h->d_loffb[0];
+    A(cudaMemsetAsync(gcd, 0, h->gc_bytes, h->stream));
+    A(cudaMemcpyAsync(h->d_voff, vertex_offsets, (size_t)(graphs + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                      h->stream));
+    A(cudaMemcpyAsync(h->gid0, gid.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    A(cudaStreamSynchronize(h->stream));
+  }
+  if (e != cudaSuccess) {
+    g_create_error = std::string("batched allocation: ") + cudaGetErrorString(e);
+    leiden_destroy(h);
+    return e == cudaErrorMemoryAllocation ? LEIDEN_ERR_OOM : LEIDEN_ERR_CUDA;
+  }
+  *out = h;
+  return LEIDEN_OK;
+}
+
+int32_t leiden_batch_graphs(const leiden_handle *h) { return h ? h->G : 0; }
+
+leiden_status leiden_batch_trace(leiden_handle *h, int32_t graph, int64_t *trace) {
+  if (!h || !trace || graph < 0 || graph >= h->G) return LEIDEN_ERR_ARG;
+  if (h->G == 1) return leiden_get_trace(h, trace);
+  if (h->gtrace.size() < (size_t)h->G * TRACE_WORDS) { memset(trace, 0, TRACE_WORDS * sizeof(int64_t)); return LEIDEN_OK; }
+  memcpy(trace, &h->gtrace[(size_t)graph * TRACE_WORDS], TRACE_WORDS * sizeof(int64_t));
+  std::vector<uint8_t> dV((size_t)h->n);
+  if (leiden_get_affected(h, dV.data()) == LEIDEN_OK) {
+    int64_t k = 0;
+    for (int64_t v = h->voff[graph]; v < h->voff[graph + 1]; v++) k += dV[v];
+    trace[1] = k;
+  }
+  return LEIDEN_OK;
+}
+
+leiden_status leiden_batch_modularity(leiden_handle *h, double *q_out) {
+  leiden_status st = check_handle(h);
+  if (st != LEIDEN_OK) return st;
+  if (!q_out) return LEIDEN_ERR_ARG;
+  if (h->G == 1) return leiden_modularity(h, nullptr, q_out);
+  modularity_terms(h, h->C);
+  sync_all(h);
+  CK(cudaGetLastError());
+  GraphCounters hg = gc_layout(h->gc_host, h->G);
+  for (int gi = 0; gi < h->G; gi++) {
+    int64_t m2 = h->m2g[gi];
+    if (m2 == 0) { q_out[gi] = 0.0; continue; }
+    i128 num = (i128)m2 * hg.sigma[gi] - read_i128(&hg.sq[2 * gi]);
+    q_out[gi] = i128_to_double(num) / ((double)m2 * (double)m2);
+  }
+  return LEIDEN_OK;
+}
+
 leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   leiden_status st = check_handle(h);
   if (st != LEIDEN_OK) return st;
@@ -500,9 +741,13 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   CK(cudaMemsetAsync(h->dV, 1, (size_t)N, s));
   CK(cudaMemsetAsync(h->dS, 0, (size_t)N, s));
   CK(cudaMemsetAsync(h->dR, 1, (size_t)N, s));
-  sync_counters(h);
+  sync_all(h);
   CK(cudaGetLastError());
   h->m2 = h->hcnt->m2;
+  if (h->G > 1) {
+    GraphCounters hg = gc_layout(h->gc_host, h->G);
+    for (int gi = 0; gi < h->G; gi++) h->m2g[gi] = hg.m2[gi];
+  }
   h->g_maxdeg = h->hcnt->max_count;
   h->g_huge_slots = h->hcnt->huge_slots;
   mark(h, 1);
@@ -677,6 +922,7 @@ void leiden_destroy(leiden_handle *h) {
   for (void *q : h->owned)
     if (q) cudaFree(q);
   if (h->hcnt) cudaFreeHost(h->hcnt);
+  if (h->gc_host) cudaFreeHost(h->gc_host);
   for (auto &ev : h->ev)
     if (ev) cudaEventDestroy(ev);
   for (auto &ev : h->kt_ev)

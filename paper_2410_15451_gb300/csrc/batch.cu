@@ -31,11 +31,13 @@ __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *a, int64_t n,
 // Mirror each undirected edge into two arcs keyed (src << vb) | dst and
 // validate it.  error := 1 on any violation.
 __global__ void k_expand(const leiden_edge *del, int64_t n_del, const leiden_edge *ins, int64_t n_ins,
-                         int64_t n, int vb, uint64_t *dkey, uint64_t *ikey, int64_t *iw, DevCounters *cnt) {
+                         int64_t n, int vb, uint64_t *dkey, uint64_t *ikey, int64_t *iw, DevCounters *cnt,
+                         const int32_t *gid0) {
   for (int64_t e = ld_gtid(); e < n_del + n_ins; e += ld_gstride()) {
     bool is_del = e < n_del;
     leiden_edge x = is_del ? del[e] : ins[e - n_del];
     bool bad = x.u < 0 || x.u >= n || x.v < 0 || x.v >= n || x.u == x.v || (!is_del && x.w <= 0);
+    if (!bad && gid0 && gid0[x.u] != gid0[x.v]) bad = true;  // batched: an edge between two graphs
     if (bad) {
       atomicExch(&cnt->error, 1);
       x.u = 0; x.v = 1 % (int32_t)(n > 1 ? n : 1); x.w = 1;
@@ -431,14 +433,15 @@ __global__ void k_ds_keys(const uint64_t *ikey, const int64_t *iw, int64_t ni, i
 // Sorted unique (src, c) pairs with summed weights H; warp per source run:
 // c* = argmax 2m*H[c] - K_src*Sigma_c, ties to the lowest c.
 __global__ void k_ds_best(const uint64_t *pkey, const int64_t *pw, const int64_t *np_p, int vb, const int64_t *K,
-                          const int64_t *Sig, const DevCounters *cnt, uint8_t *dV, uint8_t *dE, uint8_t *dCf) {
+                          const int64_t *Sig, const DevCounters *cnt, uint8_t *dV, uint8_t *dE, uint8_t *dCf,
+                          const int32_t *gid0, const int64_t *m2g) {
   int64_t np = *np_p;
   uint64_t mask = (1ull << vb) - 1;
-  int64_t m2 = cnt->m2;
   for (int64_t i = ld_gtid(); i < np; i += ld_gstride()) {
     if (pkey[i] == ~0ull) continue;
     uint64_t src = pkey[i] >> vb;
     if (i > 0 && (pkey[i - 1] >> vb) == src) continue;  // only the run head works
+    int64_t m2 = gid0 ? m2g[gid0[src]] : cnt->m2;  // 2m^{t-1} of the source's graph
     int32_t best = -1;
     i128 bv = 0;
     for (int64_t j = i; j < np && pkey[j] != ~0ull && (pkey[j] >> vb) == src; j++) {
@@ -468,19 +471,27 @@ __global__ void k_ds_expand_communities(const uint8_t *dCf, const int32_t *C, in
 // Alg. update (updateWeights, updateChanges) on both arc lists.
 __global__ void k_update_weights(const uint64_t *dkey, const int64_t *dw, int64_t nd, const uint64_t *ikey,
                                  const int64_t *iw, int64_t ni, int vb, const int32_t *C, int64_t *K, int64_t *Sig,
-                                 int64_t *dSig, DevCounters *cnt) {
+                                 int64_t *dSig, DevCounters *cnt, const int32_t *gid0, int64_t *m2g) {
   int64_t acc = 0;
-  for (int64_t i = ld_gtid(); i < nd + ni; i += ld_gstride()) {
-    bool del = i < nd;
-    uint64_t k = del ? dkey[i] : ikey[i - nd];
-    int64_t w = del ? dw[i] : iw[i - nd];
-    int32_t u = (int32_t)(k >> vb);
-    int32_t c = C[u];
-    int64_t s = del ? -w : w;
-    atomicAdd((unsigned long long *)&K[u], (unsigned long long)s);
-    atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)s);
-    atomicAdd((unsigned long long *)&dSig[c], (unsigned long long)w);
-    acc += s;
+  for (int64_t i0 = (ld_gtid() & ~31ll); i0 < nd + ni; i0 += ld_gstride()) {  // warp-uniform trip count
+    int64_t i = i0 + (threadIdx.x & 31);
+    bool has = i < nd + ni;
+    int64_t s = 0;
+    int32_t u = 0;
+    if (has) {
+      bool del = i < nd;
+      uint64_t k = del ? dkey[i] : ikey[i - nd];
+      int64_t w = del ? dw[i] : iw[i - nd];
+      u = (int32_t)(k >> vb);
+      int32_t c = C[u];
+      s = del ? -w : w;
+      atomicAdd((unsigned long long *)&K[u], (unsigned long long)s);
+      atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)s);
+      atomicAdd((unsigned long long *)&dSig[c], (unsigned long long)w);
+      acc += s;
+    }
+    // batched: 2m per graph (a signed sum; the helper adds two's-complement values)
+    if (gid0) ld_graph_add_i64(m2g, has, has ? gid0[u] : 0, s);
   }
   acc = ld_warp_sum_i64(acc);
   if ((threadIdx.x & 31) == 0 && acc) atomicAdd((unsigned long long *)&cnt->m2, (unsigned long long)acc);
@@ -678,7 +689,8 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   cudaMemsetAsync(&cnt->overflow, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&cnt->large_count, 0, sizeof(int32_t), s);
   if (n_del + n_ins > 0)
-    ld_note_launch(), k_expand<<<grid_for(n_del + n_ins, TB), TB, 0, s>>>(d_del, n_del, d_ins, n_ins, n, vb, b.dkey, b.ikey, b.iw, cnt);
+    ld_note_launch(), k_expand<<<grid_for(n_del + n_ins, TB), TB, 0, s>>>(d_del, n_del, d_ins, n_ins, n, vb, b.dkey, b.ikey,
+                                                                          b.iw, cnt, h->gid0);
   radix_sort_u64(b.dkey, b.dkey_alt, nullptr, nullptr, nda, 2 * vb, h->scan_tmp, s);
   radix_sort_u64(b.ikey, b.ikey_alt, b.iw, b.iw_alt, nia, 2 * vb, h->scan_tmp, s);
   // deduplicate: deletions collapse (-> DK), insertions add up (-> IK, IW)
@@ -794,7 +806,7 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
         cudaMemsetAsync(b.ds_uw, 0, (size_t)ni * sizeof(int64_t), s);
         ld_note_launch(), k_unique<<<grid_for(ni, TB), TB, 0, s>>>(b.ds_key, b.ds_w, ni, b.flag, b.pos, b.ds_ukey, b.ds_uw);
         ld_note_launch(), k_ds_best<<<grid_for(ni, TB), TB, 0, s>>>(b.ds_ukey, b.ds_uw, b.pos + ni, vb, h->K, h->Sig, cnt, dV, h->dE,
-                                                  h->dCf);
+                                                  h->dCf, h->gid0, h->gc.m2);
       }
       ld_note_launch(), k_ds_expand_neighbours<<<grid_for(n * 32, TB), TB, 0, s>>>(h->dE, n, h->g_off, h->g_deg, h->g_col, dV);
       ld_note_launch(), k_ds_expand_communities<<<grid_for(n, TB), TB, 0, s>>>(h->dCf, h->C, n, dV);
@@ -805,7 +817,7 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   cudaMemsetAsync(h->dR, 0, (size_t)n, s);
   if (nd + ni > 0) {
     ld_note_launch(), k_update_weights<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, DW, nd, IK, IW, ni, vb, h->C, h->K, h->Sig, h->dSig,
-                                                           cnt);
+                                                           cnt, h->gid0, h->gc.m2);
     ld_note_launch(), k_mark_communities<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, h->Sig, h->dSig,
                                                              h->p.tau_refine, h->dS, h->dR);
     ld_note_launch(), k_reset_changes<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, h->dR, h->dSig);

@@ -304,6 +304,43 @@ __device__ __forceinline__ void wt_flush(WarpTable &T, int32_t *gkeys, int64_t *
   __syncwarp();
 }
 
+// Per-graph sums of a batched handle: every lane of the warp calls these;
+// lanes with `has` add v into arr[g].  When the whole warp is on one graph
+// (the common case: lists follow vertex order) one lane adds the warp's sum.
+__device__ __forceinline__ void ld_graph_add_i64(int64_t *arr, bool has, int32_t g, int64_t v) {
+  int32_t g0 = __shfl_sync(LD_FULL, has ? g : -1, __ffs(__ballot_sync(LD_FULL, has) | 0x80000000u) - 1);
+  if (__all_sync(LD_FULL, !has || g == g0)) {
+    int64_t s = has ? v : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(LD_FULL, s, o);
+    if ((threadIdx.x & 31) == 0 && g0 >= 0 && s) atomicAdd((unsigned long long *)&arr[g0], (unsigned long long)s);
+  } else if (has && v) {
+    atomicAdd((unsigned long long *)&arr[g], (unsigned long long)v);
+  }
+}
+__device__ __forceinline__ void ld_graph_add_i32(int32_t *arr, bool has, int32_t g, int32_t v) {
+  int32_t g0 = __shfl_sync(LD_FULL, has ? g : -1, __ffs(__ballot_sync(LD_FULL, has) | 0x80000000u) - 1);
+  if (__all_sync(LD_FULL, !has || g == g0)) {
+    int32_t s = has ? v : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(LD_FULL, s, o);
+    if ((threadIdx.x & 31) == 0 && g0 >= 0 && s) atomicAdd(&arr[g0], s);
+  } else if (has && v) {
+    atomicAdd(&arr[g], v);
+  }
+}
+__device__ __forceinline__ void ld_graph_add_i128(unsigned long long *arr, bool has, int32_t g, i128 v) {
+  int32_t g0 = __shfl_sync(LD_FULL, has ? g : -1, __ffs(__ballot_sync(LD_FULL, has) | 0x80000000u) - 1);
+  if (__all_sync(LD_FULL, !has || g == g0)) {
+    i128 s = has ? v : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += ld_shfl_xor_i128(s, o);
+    if ((threadIdx.x & 31) == 0 && g0 >= 0 && s != 0) ld_atomic_add_i128(&arr[2 * g0], s);
+  } else if (has && v != 0) {
+    ld_atomic_add_i128(&arr[2 * g], v);
+  }
+}
+
 // ---------------------------------------------------------------- bitmaps
 __device__ __forceinline__ bool ld_bit_test(const uint32_t *bm, int64_t i) {
   return (bm[i >> 5] >> (i & 31)) & 1u;

@@ -21,6 +21,21 @@ struct LevelGraph {
   bool w64 = false;
   int32_t maxdeg = 0;
   int64_t huge_slots = 0;  // sum over vertices above BIN_BLOCK_MAX of pow2 >= 2*degree
+  const int32_t *gid = nullptr;  // batched handles: graph of each vertex (null: one graph)
+};
+
+// Per-graph device counters of a batched handle (G graphs), one allocation.
+struct GraphCounters {
+  unsigned long long *dq = nullptr;  // [2G] local-moving gains of the iteration (int128)
+  int64_t *moves = nullptr;          // [G] local-moving moves of the iteration
+  int64_t *m2 = nullptr;             // [G] 2m of each graph
+  int32_t *accepted = nullptr;       // [G] refinement moves accepted in the round
+  int32_t *ncomm = nullptr;          // [G] communities after refinement
+  int64_t *sigma = nullptr;          // [G] modularity: intra-community arc weight
+  unsigned long long *sq = nullptr;  // [2G] modularity: sum of Sigma_c^2 (int128)
+  uint8_t *refined = nullptr;        // [G] a vertex of the graph lies in a refined bound
+  uint8_t *lm_on = nullptr;          // [G] still iterating local moving (host-written)
+  uint8_t *cont = nullptr;           // [G] continues to the next pass (host-written)
 };
 
 // Degree bins of the vertex-centric kernels (local moving, refinement).
@@ -126,6 +141,25 @@ struct leiden_handle {
   DevCounters *dcnt = nullptr;  // device
   DevCounters *hcnt = nullptr;  // pinned host mirror
 
+  // Batched handles: G graphs concatenated with vertex offsets voff (graph g
+  // owns vertices and community ids [voff[g], voff[g+1])).  Every kernel
+  // covers all graphs in one launch; 2m, convergence, pass breaks, tracking
+  // ranges and traces are per graph.  G == 1: the single-graph path, and
+  // gid0 / gidL / gc stay null.
+  int G = 1;
+  std::vector<int64_t> voff;          // host [G+1]
+  int64_t *d_voff = nullptr;          // device [G+1]
+  int32_t *gid0 = nullptr;            // device [n] graph of each vertex of G^t
+  int32_t *gidL[2] = {nullptr, nullptr};  // graph of each super-vertex (ping-pong with y_*)
+  int64_t *d_loff = nullptr;          // device [G+1] level offsets of the current level
+  int64_t *d_loffb[2] = {nullptr, nullptr};  // the two buffers d_loff alternates between
+  int64_t *mgain = nullptr;           // device [2n] gain (lo, hi) of each deferred move
+  GraphCounters gc;                   // device
+  void *gc_host = nullptr;            // pinned host copy of the gc block
+  size_t gc_bytes = 0;
+  std::vector<int64_t> m2g;           // host 2m of each graph
+  std::vector<int64_t> gtrace;        // host per-graph traces, G x (2 + 10*25)
+
   BatchBuffers b;
   leiden_edge *up_del = nullptr, *up_ins = nullptr;  // staging of host batches
   int64_t up_cap = 0;
@@ -155,6 +189,11 @@ void ld_note_launch();
 void kt_begin(leiden_handle *h, int k);
 void kt_end(leiden_handle *h);
 void kt_resolve(leiden_handle *h);
+
+// Layout of the per-graph counter block (device or its host mirror) at
+// `base`; gc_block_bytes(G) bytes in all.
+GraphCounters gc_layout(void *base, int G);
+size_t gc_block_bytes(int G);
 
 // Message returned by leiden_last_error(NULL) (calls without a handle).
 void set_handle_free_error(const std::string &msg);
@@ -202,9 +241,15 @@ int32_t *hs_list(leiden_handle *h);
 // ------------------------------------------------------------ phases.cu
 void subset_renumber(leiden_handle *h, int64_t n);
 void split_communities(leiden_handle *h, const LevelGraph &g);
-void renumber_dense(leiden_handle *h, int64_t n);  // ranks in lbuf0, count in lbuf0[n]
-void count_communities(leiden_handle *h, int64_t n);  // distinct ids of Cp -> dcnt->list_count
-void lookup_dendrogram(leiden_handle *h);
+// Ranks in lbuf0, count in lbuf0[n]; batched (gid non-null): only the
+// graphs flagged in gc.cont, the others mapped to the spare id lbuf0[n].
+void renumber_dense(leiden_handle *h, int64_t n, const int32_t *gid);
+// Distinct ids of Cp -> dcnt->list_count (and gc.ncomm per graph when batched).
+void count_communities(leiden_handle *h, int64_t n, const int32_t *gid);
+void lookup_dendrogram(leiden_handle *h);  // batched: the continuing graphs only
+void break_lookup(leiden_handle *h);       // batched: final lookup of the stopping graphs
+// Batched: graph ids of the next level's super-vertices and its graph ranges.
+void next_level_ids(leiden_handle *h, int64_t n, const int32_t *gid, int32_t *gid_next, int64_t *loff_next);
 void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out_slot);
 void reset_next_pass(leiden_handle *h, int64_t ncomm, int out_slot);
 void mark_all_unprocessed(leiden_handle *h, int64_t n);

@@ -48,7 +48,15 @@ struct Args {
   const int32_t *count;  // bin count (device)
   const int32_t *list_tiny;   // bin 3 list (degree <= 8), used with bin 0
   const int32_t *count_tiny;
-  int64_t m2;                 // 2m of the level graph
+  int64_t m2;                 // 2m of the level graph (one graph)
+  // batched handles (null otherwise): graph of each vertex, 2m per graph,
+  // the gain of each deferred move, per-graph refinement counters
+  const int32_t *gid;
+  const int64_t *m2g;
+  const uint8_t *lm_on;
+  int64_t *mgain;
+  int32_t *accg;
+  uint8_t *refg;
   DevCounters *cnt;
   int dynamic;
   int async_mode;
@@ -60,6 +68,9 @@ struct Args {
   int32_t *gocc;   // number of filled slots of each listed vertex
   int64_t gslice;
 };
+
+// 2m of the graph vertex i belongs to.
+__device__ __forceinline__ int64_t m2_of(const Args &A, int64_t i) { return A.gid ? A.m2g[A.gid[i]] : A.m2; }
 
 __device__ __forceinline__ int next_pow2(int x) {
   int p = 1;
@@ -140,7 +151,7 @@ template <int KIND>
 __device__ __forceinline__ i128 decide_leader(const Args &A, int64_t i, const Best &b) {
   int32_t d = A.C[i];
   int64_t Ki = A.K[i];
-  int64_t m2 = A.m2;
+  int64_t m2 = m2_of(A, i);
   if (b.c < 0) return 0;
   i128 g = (i128)m2 * (b.kc - b.kd) - (i128)Ki * ((i128)Ki + A.S[b.c] - A.S[d]);
   if (g <= 0) return 0;
@@ -156,6 +167,7 @@ __device__ __forceinline__ i128 decide_leader(const Args &A, int64_t i, const Be
       int32_t slot = atomicAdd(&A.cnt->movers, 1);
       A.movers[slot] = (int32_t)i;
       A.mtarget[slot] = b.c;
+      if (A.mgain) { A.mgain[2 * slot] = (int64_t)(u128)g; A.mgain[2 * slot + 1] = (int64_t)((u128)g >> 64); }
     }
     if (A.dynamic) A.dS[d] = 1;
     return g;
@@ -244,7 +256,7 @@ __device__ __forceinline__ BestX bestx_reduce(BestX b) {
 // deferred move.
 template <int KIND>
 __device__ __forceinline__ i128 decide_x(const Args &A, int64_t i, int32_t d, int64_t Ki, int64_t Sd, int32_t szd,
-                                         BestX b) {
+                                         int64_t m2, BestX b) {
   if (b.c < 0) return 0;
   if (KIND == KIND_MOVE && A.async_mode) {
     // in-place moves: read the totals again, as late as possible
@@ -253,7 +265,7 @@ __device__ __forceinline__ i128 decide_x(const Args &A, int64_t i, int32_t d, in
     szd = A.size[d];
     b.szc = A.size[b.c];
   }
-  i128 g = (i128)A.m2 * (b.kc - b.kd) - (i128)Ki * ((i128)Ki + b.sc - Sd);
+  i128 g = (i128)m2 * (b.kc - b.kd) - (i128)Ki * ((i128)Ki + b.sc - Sd);
   if (g <= 0) return 0;
   if (KIND == KIND_MOVE) {
     if (szd == 1 && b.szc == 1 && b.c > d) return 0;
@@ -275,7 +287,7 @@ __device__ __forceinline__ i128 decide_x(const Args &A, int64_t i, int32_t d, in
 
 // Deferred moves of the lanes with `mv` set (snapshot schedule): one
 // counter update per warp.
-__device__ __forceinline__ void record_movers(const Args &A, bool mv, int32_t i, int32_t c) {
+__device__ __forceinline__ void record_movers(const Args &A, bool mv, int32_t i, int32_t c, i128 g) {
   uint32_t m = __ballot_sync(LD_FULL, mv);
   if (!m) return;
   int lane = threadIdx.x & 31;
@@ -286,6 +298,7 @@ __device__ __forceinline__ void record_movers(const Args &A, bool mv, int32_t i,
     int32_t slot = p0 + __popc(m & ((1u << lane) - 1u));
     A.movers[slot] = i;
     A.mtarget[slot] = c;
+    if (A.mgain) { A.mgain[2 * slot] = (int64_t)(u128)g; A.mgain[2 * slot + 1] = (int64_t)((u128)g >> 64); }
   }
 }
 
@@ -334,13 +347,14 @@ __device__ __forceinline__ void tiny_step(const Args &A, int64_t item, int64_t n
   int64_t k = item * 4 + grp;
   bool has = k < ntiny;
   int32_t i = has ? A.list_tiny[k] : 0;
-  int64_t base = 0, Ki = 0, Sd = 0, wj = 0;
+  int64_t base = 0, Ki = 0, Sd = 0, wj = 0, m2 = A.m2;
   int32_t dg = 0, d = 0, szd = 0, bi = 0, j = -1;
   if (has) {
     base = A.off[i];
     dg = A.deg[i];
     d = A.C[i];
     Ki = A.K[i];
+    if (A.gid) m2 = A.m2g[A.gid[i]];
     if (KIND == KIND_REFINE) bi = A.CB[i];
   }
   bool arc = has && sub < dg;
@@ -367,16 +381,16 @@ __device__ __forceinline__ void tiny_step(const Args &A, int64_t item, int64_t n
     } else {
       b.sc = A.S[c];
       if (KIND == KIND_MOVE) b.szc = A.size[c];
-      b.v = (i128)A.m2 * kv - (i128)Ki * b.sc;
+      b.v = (i128)m2 * kv - (i128)Ki * b.sc;
       b.c = c;
       b.kc = kv;
     }
   }
   b = bestx_reduce<TINY_LANES>(b);
   i128 g = 0;
-  if (has && sub == 0) g = decide_x<KIND>(A, i, d, Ki, Sd, szd, b);
+  if (has && sub == 0) g = decide_x<KIND>(A, i, d, Ki, Sd, szd, m2, b);
   bool mv = g > 0;
-  if (KIND == KIND_MOVE && !A.async_mode) record_movers(A, mv, i, b.c);
+  if (KIND == KIND_MOVE && !A.async_mode) record_movers(A, mv, i, b.c, g);
   int moved = __shfl_sync(LD_FULL, mv ? 1 : 0, gl);
   if (KIND == KIND_MOVE && moved && arc && j != i && (!A.in_range || A.in_range[j])) ld_bit_set(A.unproc, j);
   if (has && sub == 0) { tl.visits++; tl.arcs += dg; tl.moves += mv; tl.dq += g; }
@@ -393,6 +407,7 @@ __device__ __forceinline__ void warp_step(const Args &A, int32_t i, int lane, in
   int64_t Ki = A.K[i];
   int64_t Sd = A.S[d];
   int32_t szd = KIND == KIND_MOVE ? A.size[d] : 0;
+  int64_t m2 = m2_of(A, i);
   int T = max(32, next_pow2(2 * dg));
   for (int s = lane; s < T; s += 32) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
   __syncwarp();
@@ -405,16 +420,16 @@ __device__ __forceinline__ void warp_step(const Args &A, int32_t i, int lane, in
     int64_t kv = vals[s];
     if (c == d) { b.kd += kv; continue; }
     int64_t sc = A.S[c];
-    i128 v = (i128)A.m2 * kv - (i128)Ki * sc;
+    i128 v = (i128)m2 * kv - (i128)Ki * sc;
     if (ld_better(v, c, b.v, b.c)) { b.v = v; b.c = c; b.kc = kv; b.sc = sc; }
   }
   if (KIND == KIND_MOVE && b.c >= 0) b.szc = A.size[b.c];
   b = bestx_reduce<32>(b);
   __syncwarp();
   i128 g = 0;
-  if (lane == 0) g = decide_x<KIND>(A, i, d, Ki, Sd, szd, b);
+  if (lane == 0) g = decide_x<KIND>(A, i, d, Ki, Sd, szd, m2, b);
   bool mv = g > 0;
-  if (KIND == KIND_MOVE && !A.async_mode) record_movers(A, mv, i, b.c);
+  if (KIND == KIND_MOVE && !A.async_mode) record_movers(A, mv, i, b.c, g);
   int moved = __shfl_sync(LD_FULL, mv ? 1 : 0, 0);
   if (KIND == KIND_MOVE && moved) mark_neighbours(A, i, base, dg, lane, 32);
   if (lane == 0) { tl.visits++; tl.arcs += dg; tl.moves += mv; tl.dq += g; }
@@ -498,6 +513,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Args A) {
     int64_t Sd = A.S[d];
     int32_t szd = KIND == KIND_MOVE ? A.size[d] : 0;
     int32_t bi = KIND == KIND_REFINE ? A.CB[i] : 0;
+    int64_t m2 = m2_of(A, i);
     for (int a0 = threadIdx.x & ~31; a0 < dg; a0 += blockDim.x) {  // warp-uniform trip count
       int a = a0 + lane;
       bool valid = a < dg;
@@ -519,19 +535,20 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Args A) {
       int64_t kv = S.vals[sl];
       if (c == d) { b.kd += kv; continue; }
       int64_t sc = A.S[c];
-      i128 v = (i128)A.m2 * kv - (i128)Ki * sc;
+      i128 v = (i128)m2 * kv - (i128)Ki * sc;
       if (ld_better(v, c, b.v, b.c)) { b.v = v; b.c = c; b.kc = kv; b.sc = sc; }
     }
     if (KIND == KIND_MOVE && b.c >= 0) b.szc = A.size[b.c];
     b = block_bestx(b);
     stage_clear(S);
     if (threadIdx.x == 0) {
-      i128 g = decide_x<KIND>(A, i, d, Ki, Sd, szd, b);
+      i128 g = decide_x<KIND>(A, i, d, Ki, Sd, szd, m2, b);
       bool mv = g > 0;
       if (KIND == KIND_MOVE && mv && !A.async_mode) {
         int32_t slot = atomicAdd(&A.cnt->movers, 1);
         A.movers[slot] = i;
         A.mtarget[slot] = b.c;
+        if (A.mgain) { A.mgain[2 * slot] = (int64_t)(u128)g; A.mgain[2 * slot + 1] = (int64_t)((u128)g >> 64); }
       }
       moved_s = mv;
       visits++; arcs += dg; moves += mv; dq += g;
@@ -618,7 +635,7 @@ __global__ void __launch_bounds__(1024) k_huge_decide(Args A, const int64_t *tab
     int64_t *vals = A.gvals + tab_off[k];
     int32_t occ = A.gocc[k];
     int32_t d = A.C[i];
-    int64_t m2 = A.m2, Ki = A.K[i];
+    int64_t m2 = m2_of(A, i), Ki = A.K[i];
     Best b{0, -1, 0, 0};
     for (int32_t t = threadIdx.x; t < occ; t += blockDim.x) {
       int32_t s = list[t];
@@ -650,7 +667,8 @@ __global__ void __launch_bounds__(1024) k_huge_decide(Args A, const int64_t *tab
 // Take the unprocessed vertices of class `cls` (clearing their bits) and
 // append the in-range ones to the degree bins.
 __global__ void k_collect(int64_t n, uint32_t *unproc, int cls, int classes_mask, const uint8_t *in_range,
-                          const int32_t *deg, int32_t *bins, DevCounters *cnt) {
+                          const int32_t *deg, int32_t *bins, DevCounters *cnt, const int32_t *gid,
+                          const uint8_t *lm_on, const int64_t *loff) {
   // Each warp reads 32 bitmap words at once and visits only the non-zero
   // ones (a frontier is usually sparse), one vertex per lane.
   int lane = threadIdx.x & 31;
@@ -664,7 +682,11 @@ __global__ void k_collect(int64_t n, uint32_t *unproc, int cls, int classes_mask
       nz &= nz - 1;
       uint32_t wd = __shfl_sync(LD_FULL, word, src);
       int64_t v = ((w0 + src) << 5) + lane;
-      bool take = v < n && ((wd >> lane) & 1u) && ld_class_of(v, classes_mask) == cls;
+      // batched handles: the class of a vertex is taken on its id within its
+      // graph, and graphs whose iterations ended are skipped
+      int64_t vl = v < n && gid ? v - loff[gid[v]] : v;
+      bool take = v < n && ((wd >> lane) & 1u) && ld_class_of(vl, classes_mask) == cls &&
+                  (!gid || lm_on[gid[v]]);
       uint32_t taken = __ballot_sync(LD_FULL, take);
       if (lane == 0 && taken) atomicAnd(&unproc[w0 + src], ~taken);
       bool work = take && (!in_range || in_range[v]);
@@ -688,17 +710,34 @@ __global__ void k_collect(int64_t n, uint32_t *unproc, int cls, int classes_mask
 }
 
 // Deferred moves of a sub-sweep (deterministic mode).
+// Batched handles also sum the gains and moves per graph (gid non-null).
 __global__ void k_apply_moves(const int32_t *movers, const int32_t *target, const DevCounters *cnt_c, int32_t *C,
-                              int64_t *S, const int64_t *K, int32_t *size) {
+                              int64_t *S, const int64_t *K, int32_t *size, const int32_t *gid, const int64_t *mgain,
+                              unsigned long long *dqg, int64_t *movesg) {
   int64_t m = cnt_c->movers;
-  for (int64_t t = ld_gtid(); t < m; t += ld_gstride()) {
-    int32_t i = movers[t], c = target[t];
-    int32_t d = C[i];
-    C[i] = c;
-    atomicAdd((unsigned long long *)&S[d], (unsigned long long)(-K[i]));
-    atomicAdd((unsigned long long *)&S[c], (unsigned long long)K[i]);
-    atomicSub(&size[d], 1);
-    atomicAdd(&size[c], 1);
+  for (int64_t t0 = (ld_gtid() & ~31ll); t0 < m; t0 += ld_gstride()) {  // warp-uniform trip count
+    int64_t t = t0 + (threadIdx.x & 31);
+    bool has = t < m;
+    int32_t i = 0, gi = 0;
+    i128 gain = 0;
+    if (has) {
+      i = movers[t];
+      int32_t c = target[t];
+      int32_t d = C[i];
+      C[i] = c;
+      atomicAdd((unsigned long long *)&S[d], (unsigned long long)(-K[i]));
+      atomicAdd((unsigned long long *)&S[c], (unsigned long long)K[i]);
+      atomicSub(&size[d], 1);
+      atomicAdd(&size[c], 1);
+      if (gid) {
+        gi = gid[i];
+        gain = (i128)(((u128)(uint64_t)mgain[2 * t + 1] << 64) | (u128)(uint64_t)mgain[2 * t]);
+      }
+    }
+    if (gid) {
+      ld_graph_add_i128(dqg, has, gi, gain);
+      ld_graph_add_i64(movesg, has, gi, 1);
+    }
   }
 }
 
@@ -717,13 +756,15 @@ __global__ void k_sizes(const int32_t *C, int64_t n, int32_t *size) {
 // ---- refinement
 // Reset the vertices of refined bounds to singletons and list them.
 __global__ void k_refine_reset(int64_t n, const int32_t *CB, const uint8_t *dR, int32_t *C, int64_t *S,
-                               const int64_t *K, int32_t *prop, int32_t *cand, DevCounters *cnt) {
+                               const int64_t *K, int32_t *prop, int32_t *cand, DevCounters *cnt, const int32_t *gid,
+                               uint8_t *refg) {
   int lane = threadIdx.x & 31;
   for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
     int64_t i = base + lane;
     bool r = i < n && dR[CB[i]];
     if (i < n) prop[i] = r ? 0 : -1;
     if (r) { C[i] = (int32_t)i; S[i] = K[i]; }
+    if (r && gid) refg[gid[i]] = 1;  // the graph has a vertex in a refined bound
     uint32_t m = __ballot_sync(LD_FULL, r);
     if (!m) continue;
     int32_t p0 = 0;
@@ -780,18 +821,26 @@ __device__ __forceinline__ bool holds(const int32_t *prop, int32_t v) {
   return t < 0 || (prop[t] == v && v < t);
 }
 __global__ void k_refine_accept(const int32_t *cand, const int32_t *count, const int32_t *prop, int32_t *C, int64_t *S,
-                                const int64_t *K, DevCounters *cnt) {
+                                const int64_t *K, DevCounters *cnt, const int32_t *gid, int32_t *accg) {
   int64_t m = *count;
   int32_t acc = 0;
-  for (int64_t t = ld_gtid(); t < m; t += ld_gstride()) {
-    int32_t i = cand[t];
-    int32_t c = prop[i];
-    if (c < 0 || holds(prop, i) || !holds(prop, c)) continue;
-    int32_t d = C[i];
-    C[i] = c;
-    atomicAdd((unsigned long long *)&S[d], (unsigned long long)(-K[i]));
-    atomicAdd((unsigned long long *)&S[c], (unsigned long long)K[i]);
-    acc++;
+  for (int64_t t0 = (ld_gtid() & ~31ll); t0 < m; t0 += ld_gstride()) {  // warp-uniform trip count
+    int64_t t = t0 + (threadIdx.x & 31);
+    bool took = false;
+    int32_t i = 0;
+    if (t < m) {
+      i = cand[t];
+      int32_t c = prop[i];
+      if (c >= 0 && !holds(prop, i) && holds(prop, c)) {
+        int32_t d = C[i];
+        C[i] = c;
+        atomicAdd((unsigned long long *)&S[d], (unsigned long long)(-K[i]));
+        atomicAdd((unsigned long long *)&S[c], (unsigned long long)K[i]);
+        acc++;
+        took = true;
+      }
+    }
+    if (gid) ld_graph_add_i32(accg, took, took ? gid[i] : 0, 1);
   }
   if (acc) atomicAdd(&cnt->accepted, acc);
 }
@@ -815,6 +864,13 @@ Args make_args(leiden_handle *h, const LevelGraph &g) {
   A.mtarget = h->mtarget;
   A.cnt = h->dcnt;
   A.m2 = h->m2;
+  if (g.gid) {
+    A.gid = g.gid;
+    A.m2g = h->gc.m2;
+    A.mgain = h->mgain;
+    A.accg = h->gc.accepted;
+    A.refg = h->gc.refined;
+  }
   A.async_mode = h->p.deterministic ? 0 : 1;
   A.classes_mask = h->p.classes - 1;
   return A;
@@ -912,21 +968,22 @@ void lm_prepare(leiden_handle *h, const LevelGraph &g) {
 void lm_subsweep(leiden_handle *h, const LevelGraph &g, int cls, const uint8_t *in_range, int dynamic) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4 + sizeof(int32_t), s);  // bins + movers
-  ld_note_launch(), k_collect<<<grid_for((g.n + 31) / 32, 256), 256, 0, s>>>(g.n, h->unproc, cls, h->p.classes - 1, in_range, g.deg, h->bins,
-                                               h->dcnt);
+  ld_note_launch(), k_collect<<<grid_for((g.n + 31) / 32, 256), 256, 0, s>>>(
+      g.n, h->unproc, cls, h->p.classes - 1, in_range, g.deg, h->bins, h->dcnt, g.gid, h->gc.lm_on, h->d_loff);
   Args A = make_args(h, g);
   A.in_range = in_range;
   A.dynamic = dynamic;
   launch_bins<KIND_MOVE>(h, g, A);
   if (h->p.deterministic)
-    ld_note_launch(), k_apply_moves<<<h->sm_count * 4, 256, 0, s>>>(h->movers, h->mtarget, h->dcnt, h->Cp, h->Sp, h->Kp, h->csize);
+    ld_note_launch(), k_apply_moves<<<h->sm_count * 4, 256, 0, s>>>(h->movers, h->mtarget, h->dcnt, h->Cp, h->Sp, h->Kp,
+                                                                    h->csize, g.gid, h->mgain, h->gc.dq, h->gc.moves);
 }
 
 void refine_reset(leiden_handle *h, const LevelGraph &g) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->cand_count[0], 0, sizeof(int32_t), s);
   ld_note_launch(), k_refine_reset<<<grid_for(g.n, 256), 256, 0, s>>>(g.n, h->CB, h->dR, h->Cp, h->Sp, h->Kp, h->prop, h->cand,
-                                                    h->dcnt);
+                                                    h->dcnt, g.gid, h->gc.refined);
 }
 
 // One round on the candidates of list `slot` (cand + slot*n, count
@@ -942,5 +999,6 @@ void refine_round(leiden_handle *h, const LevelGraph &g, int slot) {
                                                       h->bins, h->dcnt, 0);
   Args A = make_args(h, g);
   launch_bins<KIND_REFINE>(h, g, A);
-  ld_note_launch(), k_refine_accept<<<h->sm_count * 4, 256, 0, s>>>(out, cout, h->prop, h->Cp, h->Sp, h->Kp, h->dcnt);
+  ld_note_launch(), k_refine_accept<<<h->sm_count * 4, 256, 0, s>>>(out, cout, h->prop, h->Cp, h->Sp, h->Kp, h->dcnt,
+                                                                     g.gid, h->gc.accepted);
 }

@@ -164,22 +164,52 @@ __global__ void k_split_compress(const int32_t *list, const DevCounters *cnt, in
 }
 
 // ---------------------------------------------------------------- renumber / lookup
-__global__ void k_used(int64_t n, const int32_t *C, int32_t *used) {
-  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) used[C[i]] = 1;
+// Batched handles (gid non-null): only the graphs that continue to the next
+// pass are renumbered; the others are mapped to one spare id past the dense
+// range (rank[n]), which aggregation leaves out.
+__global__ void k_used(int64_t n, const int32_t *C, int32_t *used, const int32_t *gid, const uint8_t *cont) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride())
+    if (!gid || cont[gid[i]]) used[C[i]] = 1;
 }
-__global__ void k_rank(int64_t n, const int64_t *rank, int32_t *C) {
-  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) C[i] = (int32_t)rank[C[i]];
+__global__ void k_rank(int64_t n, const int64_t *rank, int32_t *C, const int32_t *gid, const uint8_t *cont) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride())
+    C[i] = (int32_t)((!gid || cont[gid[i]]) ? rank[C[i]] : rank[n]);
 }
-__global__ void k_lookup(int64_t N, const int32_t *Cp, int32_t *Ctop) {
-  for (int64_t v = ld_gtid(); v < N; v += ld_gstride()) Ctop[v] = Cp[Ctop[v]];
+__global__ void k_lookup(int64_t N, const int32_t *Cp, int32_t *Ctop, const int32_t *gid0, const uint8_t *cont) {
+  for (int64_t v = ld_gtid(); v < N; v += ld_gstride())
+    if (!gid0 || cont[gid0[v]]) Ctop[v] = Cp[Ctop[v]];
+}
+// Final lookup of the graphs that stop at this pass, with the community id
+// moved from the level's range of the graph into its own vertex range (the
+// order within the graph, all that tracking uses, is kept).
+__global__ void k_break_lookup(int64_t N, const int32_t *Cp, int32_t *Ctop, const int32_t *gid0, const uint8_t *cont,
+                               const int64_t *loff, const int64_t *voff) {
+  for (int64_t v = ld_gtid(); v < N; v += ld_gstride()) {
+    int32_t g = gid0[v];
+    if (loff[g + 1] > loff[g] && !cont[g]) Ctop[v] = (int32_t)(Cp[Ctop[v]] - loff[g] + voff[g]);
+  }
+}
+// Graph of each super-vertex and the graphs' ranges at the next level.
+__global__ void k_level_ids(int64_t n, const int32_t *Cdense, const int32_t *gid, const uint8_t *cont,
+                            int32_t *gid_next) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride())
+    if (cont[gid[i]]) gid_next[Cdense[i]] = gid[i];
+}
+__global__ void k_level_off(int G, const int64_t *loff, const int64_t *rank, int64_t *loff_next) {
+  for (int64_t g = ld_gtid(); g <= G; g += ld_gstride()) loff_next[g] = rank[loff[g]];
 }
 // After refinement every community id is one of its members and that
 // member keeps its own id (subset renumbering gives the smallest member,
 // splitting the smallest vertex of a component, refinement a stationary
 // representative), so the communities are the vertices with C[i] == i.
-__global__ void k_count_roots(int64_t n, const int32_t *C, DevCounters *cnt) {
+__global__ void k_count_roots(int64_t n, const int32_t *C, DevCounters *cnt, const int32_t *gid, int32_t *ncg) {
   int32_t local = 0;
-  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) local += C[i] == (int32_t)i;
+  for (int64_t b = (ld_gtid() & ~31ll); b < n; b += ld_gstride()) {  // warp-uniform trip count
+    int64_t i = b + (threadIdx.x & 31);
+    bool root = i < n && C[i] == (int32_t)i;
+    local += root;
+    if (gid) ld_graph_add_i32(ncg, root, root ? gid[i] : 0, 1);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(LD_FULL, local, o);
   if ((threadIdx.x & 31) == 0 && local) atomicAdd(&cnt->list_count, local);
@@ -522,22 +552,35 @@ void split_communities(leiden_handle *h, const LevelGraph &g) {
   ld_note_launch(), k_split_compress<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent, h->Cp);
 }
 
-void count_communities(leiden_handle *h, int64_t n) {
+void count_communities(leiden_handle *h, int64_t n, const int32_t *gid) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->list_count, 0, sizeof(int32_t), s);
-  ld_note_launch(), k_count_roots<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->dcnt);
+  ld_note_launch(), k_count_roots<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->dcnt, gid, h->gc.ncomm);
 }
 
-void renumber_dense(leiden_handle *h, int64_t n) {
+void renumber_dense(leiden_handle *h, int64_t n, const int32_t *gid) {
   cudaStream_t s = h->stream;
+  const uint8_t *cont = gid ? h->gc.cont : nullptr;
   cudaMemsetAsync(h->ibuf0, 0, (size_t)n * sizeof(int32_t), s);
-  ld_note_launch(), k_used<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0);
+  ld_note_launch(), k_used<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0, gid, cont);
   exclusive_scan_i32_to_i64(h->ibuf0, h->lbuf0, n, h->scan_tmp, s);
-  ld_note_launch(), k_rank<<<grid_for(n, TB), TB, 0, s>>>(n, h->lbuf0, h->Cp);
+  ld_note_launch(), k_rank<<<grid_for(n, TB), TB, 0, s>>>(n, h->lbuf0, h->Cp, gid, cont);
 }
 
 void lookup_dendrogram(leiden_handle *h) {
-  ld_note_launch(), k_lookup<<<grid_for(h->n, TB), TB, 0, h->stream>>>(h->n, h->Cp, h->Ctop);
+  const uint8_t *cont = h->gid0 ? h->gc.cont : nullptr;
+  ld_note_launch(), k_lookup<<<grid_for(h->n, TB), TB, 0, h->stream>>>(h->n, h->Cp, h->Ctop, h->gid0, cont);
+}
+
+void break_lookup(leiden_handle *h) {
+  ld_note_launch(), k_break_lookup<<<grid_for(h->n, TB), TB, 0, h->stream>>>(h->n, h->Cp, h->Ctop, h->gid0, h->gc.cont,
+                                                                               h->d_loff, h->d_voff);
+}
+
+void next_level_ids(leiden_handle *h, int64_t n, const int32_t *gid, int32_t *gid_next, int64_t *loff_next) {
+  cudaStream_t s = h->stream;
+  ld_note_launch(), k_level_ids<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, gid, h->gc.cont, gid_next);
+  ld_note_launch(), k_level_off<<<grid_for(h->G + 1, TB), TB, 0, s>>>(h->G, h->d_loff, h->lbuf0, loff_next);
 }
 
 // Aggregate level g by its dense membership Cp into slot `out`; K'' goes to
@@ -545,11 +588,13 @@ void lookup_dendrogram(leiden_handle *h) {
 void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
   cudaStream_t s = h->stream;
   int64_t n = g.n;
-  // community vertices CSR
-  cudaMemsetAsync(h->ibuf0, 0, (size_t)ncomm * sizeof(int32_t), s);
+  // community vertices CSR; batched handles carry the stopped graphs'
+  // vertices in one spare community ncomm, listed last and not aggregated
+  int64_t nc = ncomm + (g.gid ? 1 : 0);
+  cudaMemsetAsync(h->ibuf0, 0, (size_t)nc * sizeof(int32_t), s);
   ld_note_launch(), k_member_count<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, h->ibuf0);
-  exclusive_scan_i32_to_i64(h->ibuf0, h->coff, ncomm, h->scan_tmp, s);
-  cudaMemcpyAsync(h->lbuf0, h->coff, (size_t)ncomm * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  exclusive_scan_i32_to_i64(h->ibuf0, h->coff, nc, h->scan_tmp, s);
+  cudaMemcpyAsync(h->lbuf0, h->coff, (size_t)nc * sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   ld_note_launch(), k_member_fill<<<grid_for(n, TB), TB, 0, s>>>(n, h->Cp, (unsigned long long *)h->lbuf0, h->cverts);
   // flat arc offsets of the members, and the super-row offsets
   ld_note_launch(), k_member_deg<<<grid_for(n, TB), TB, 0, s>>>(n, h->cverts, g.deg, h->ibuf1);

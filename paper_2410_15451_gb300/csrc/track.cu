@@ -139,12 +139,22 @@ __global__ void k_tr_free_list(int64_t N, const int32_t *freef, const int64_t *f
   for (int64_t id = ld_gtid(); id < N; id += ld_gstride())
     if (freef[id]) flist[frank[id]] = (int32_t)id;
 }
+// The k-th unmatched new community of a graph takes the k-th free id of that
+// graph (batched handles: ranks counted from the graph's first id).
 __global__ void k_tr_map(int64_t N, const int32_t *new_used, const int32_t *ob, const int64_t *urank,
-                         const int32_t *flist, int32_t *map, uint8_t *matched) {
+                         const int64_t *frank, const int32_t *flist, int32_t *map, uint8_t *matched,
+                         const int32_t *gid0, const int64_t *voff) {
   for (int64_t c = ld_gtid(); c < N; c += ld_gstride()) {
     if (!new_used[c]) continue;
-    if (ob[c] != INT_MAX) { map[c] = ob[c]; matched[ob[c]] = 1; }
-    else map[c] = flist[urank[c]];
+    if (ob[c] != INT_MAX) {
+      map[c] = ob[c];
+      matched[ob[c]] = 1;
+    } else if (!gid0) {
+      map[c] = flist[urank[c]];
+    } else {
+      int64_t v0 = voff[gid0[c]];
+      map[c] = flist[frank[v0] + urank[c] - urank[v0]];
+    }
   }
 }
 __global__ void k_tr_relabel(int64_t N, const int32_t *Cnew, const int32_t *map, const int64_t *K, int32_t *C,
@@ -177,23 +187,34 @@ __global__ void k_sig_of(int64_t N, const int32_t *C, const int64_t *K, int64_t 
     if (i < N && ld_group_leader(peers) && s) atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)s);
   }
 }
+// Batched handles (gid0 non-null) also sum per graph: sigg, sqg, m2g.
 __global__ void k_sigma_intra(int64_t N, const int64_t *off, const int32_t *deg, const int32_t *col, const int32_t *w,
-                              const int32_t *C, DevCounters *cnt) {
+                              const int32_t *C, DevCounters *cnt, const int32_t *gid0, int64_t *sigg) {
   int lane = threadIdx.x & 31;
   int64_t warp = ld_gtid() >> 5, nw = ld_gstride() >> 5;
   int64_t acc = 0;
   for (int64_t i = warp; i < N; i += nw) {
     int32_t c = C[i];
-    int64_t b = off[i], d = deg[i];
+    int64_t b = off[i], d = deg[i], vi = 0;
     for (int64_t a = lane; a < d; a += 32)
-      if (C[col[b + a]] == c) acc += w[b + a];
+      if (C[col[b + a]] == c) vi += w[b + a];
+    acc += vi;
+    if (gid0) {
+      vi = ld_warp_sum_i64(vi);
+      if (lane == 0 && vi) atomicAdd((unsigned long long *)&sigg[gid0[i]], (unsigned long long)vi);
+    }
   }
   acc = ld_warp_sum_i64(acc);
   if (lane == 0 && acc) atomicAdd((unsigned long long *)&cnt->sigma_intra, (unsigned long long)acc);
 }
-__global__ void k_sq(int64_t N, const int64_t *Sig, DevCounters *cnt) {
+__global__ void k_sq(int64_t N, const int64_t *Sig, DevCounters *cnt, const int32_t *gid0, unsigned long long *sqg) {
   i128 acc = 0;
-  for (int64_t c = ld_gtid(); c < N; c += ld_gstride()) acc += (i128)Sig[c] * Sig[c];
+  for (int64_t c0 = (ld_gtid() & ~31ll); c0 < N; c0 += ld_gstride()) {  // warp-uniform trip count
+    int64_t c = c0 + (threadIdx.x & 31);
+    i128 v = c < N ? (i128)Sig[c] * Sig[c] : 0;
+    acc += v;
+    if (gid0) ld_graph_add_i128(sqg, c < N && v != 0, c < N ? gid0[c] : 0, v);
+  }
   // warp reduce in two halves
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += ld_shfl_xor_i128(acc, o);
@@ -201,7 +222,7 @@ __global__ void k_sq(int64_t N, const int64_t *Sig, DevCounters *cnt) {
 }
 
 __global__ void k_rowsum(int64_t N, const int64_t *off, const int32_t *deg, const int32_t *w, int64_t *K,
-                         DevCounters *cnt) {
+                         DevCounters *cnt, const int32_t *gid0, int64_t *m2g) {
   int lane = threadIdx.x & 31;
   int64_t warp = ld_gtid() >> 5, nw = ld_gstride() >> 5;
   int64_t tot = 0;
@@ -210,6 +231,7 @@ __global__ void k_rowsum(int64_t N, const int64_t *off, const int32_t *deg, cons
     for (int64_t a = lane; a < d; a += 32) acc += w[b + a];
     acc = ld_warp_sum_i64(acc);
     if (lane == 0) K[i] = acc;
+    if (lane == 0 && gid0 && acc) atomicAdd((unsigned long long *)&m2g[gid0[i]], (unsigned long long)acc);
     tot += acc;
   }
   if (lane == 0 && tot) atomicAdd((unsigned long long *)&cnt->m2, (unsigned long long)tot);
@@ -255,7 +277,7 @@ void track_communities(leiden_handle *h) {
   ld_note_launch(), k_tr_free_list<<<gN, TB, 0, s>>>(N, freef, frank, flist);
   uint8_t *matched = h->dE;
   cudaMemsetAsync(matched, 0, (size_t)N, s);
-  ld_note_launch(), k_tr_map<<<gN, TB, 0, s>>>(N, used, ob, urank, flist, map, matched);
+  ld_note_launch(), k_tr_map<<<gN, TB, 0, s>>>(N, used, ob, urank, frank, flist, map, matched, h->gid0, h->d_voff);
   cudaMemsetAsync(h->Sig, 0, (size_t)N * sizeof(int64_t), s);
   ld_note_launch(), k_tr_relabel<<<gN, TB, 0, s>>>(N, h->Ctop, map, h->K, h->C, h->Sig);
   ld_note_launch(), k_tr_dsig<<<gN, TB, 0, s>>>(N, matched, h->dSig);
@@ -270,13 +292,20 @@ void modularity_terms(leiden_handle *h, const int32_t *C) {
   cudaMemsetAsync(&h->dcnt->sigma_intra, 0, sizeof(int64_t), s);
   cudaMemsetAsync(&h->dcnt->sq[0], 0, 2 * sizeof(unsigned long long), s);
   ld_note_launch(), k_sig_of<<<grid_for(N, TB), TB, 0, s>>>(N, C, h->K, Sig);
-  ld_note_launch(), k_sigma_intra<<<grid_for(N * 32, TB), TB, 0, s>>>(N, h->g_off, h->g_deg, h->g_col, h->g_w, C, h->dcnt);
-  ld_note_launch(), k_sq<<<grid_for(N, TB), TB, 0, s>>>(N, Sig, h->dcnt);
+  if (h->gid0) {
+    cudaMemsetAsync(h->gc.sigma, 0, (size_t)h->G * sizeof(int64_t), s);
+    cudaMemsetAsync(h->gc.sq, 0, (size_t)h->G * 2 * sizeof(unsigned long long), s);
+  }
+  ld_note_launch(), k_sigma_intra<<<grid_for(N * 32, TB), TB, 0, s>>>(N, h->g_off, h->g_deg, h->g_col, h->g_w, C, h->dcnt,
+                                                                      h->gid0, h->gc.sigma);
+  ld_note_launch(), k_sq<<<grid_for(N, TB), TB, 0, s>>>(N, Sig, h->dcnt, h->gid0, h->gc.sq);
 }
 
 // K = row sums of G^t and 2m.
 void recompute_weights(leiden_handle *h) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->m2, 0, sizeof(int64_t), s);
-  ld_note_launch(), k_rowsum<<<grid_for(h->n * 32, TB), TB, 0, s>>>(h->n, h->g_off, h->g_deg, h->g_w, h->K, h->dcnt);
+  if (h->gid0) cudaMemsetAsync(h->gc.m2, 0, (size_t)h->G * sizeof(int64_t), s);
+  ld_note_launch(), k_rowsum<<<grid_for(h->n * 32, TB), TB, 0, s>>>(h->n, h->g_off, h->g_deg, h->g_w, h->K, h->dcnt,
+                                                                    h->gid0, h->gc.m2);
 }

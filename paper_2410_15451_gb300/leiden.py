@@ -78,6 +78,14 @@ def load():
     lib.leiden_get_affected.argtypes = [vp, vp]
     lib.leiden_get_trace.argtypes = [vp, vp]
     lib.leiden_get_stats.argtypes = [vp, P(leiden_stats)]
+    lib.leiden_create_batched.argtypes = [P(leiden_params), i32, vp, vp, vp, vp, vp, P(vp)]
+    lib.leiden_create_batched.restype = ctypes.c_int
+    lib.leiden_batch_graphs.argtypes = [vp]
+    lib.leiden_batch_graphs.restype = i32
+    lib.leiden_batch_trace.argtypes = [vp, i32, vp]
+    lib.leiden_batch_trace.restype = ctypes.c_int
+    lib.leiden_batch_modularity.argtypes = [vp, vp]
+    lib.leiden_batch_modularity.restype = ctypes.c_int
     lib.leiden_kernel_launches.argtypes = []
     lib.leiden_kernel_launches.restype = i64
     lib.leiden_last_error.argtypes = [vp]
@@ -197,6 +205,10 @@ def leiden_get_affected(h, n):
 def leiden_get_trace(h) -> dict:
     t = np.zeros(TRACE_WORDS, np.int64)
     _check(h, load().leiden_get_trace(h, _ptr(t)))
+    return _trace_dict(t)
+
+
+def _trace_dict(t) -> dict:
     passes = []
     for p in range(int(t[0])):
         r = t[2 + p * 25: 2 + (p + 1) * 25]
@@ -213,6 +225,35 @@ def leiden_get_stats(h) -> dict:
         v = getattr(s, k)
         out[k] = list(v) if isinstance(v, ctypes.Array) else v
     return out
+
+
+def leiden_create_batched(params, vertex_offsets, offsets, cols, weights=None, cuda_stream=None) -> int:
+    lib = load()
+    vo = np.ascontiguousarray(vertex_offsets, np.int64)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    cols = np.ascontiguousarray(cols, np.int32)
+    weights = None if weights is None else np.ascontiguousarray(weights, np.int32)
+    h = ctypes.c_void_p()
+    st = lib.leiden_create_batched(ctypes.byref(params) if params is not None else None, len(vo) - 1, _ptr(vo),
+                                   _ptr(offsets), _ptr(cols), _ptr(weights), cuda_stream, ctypes.byref(h))
+    _check(None, st)
+    return h.value
+
+
+def leiden_batch_graphs(h) -> int:
+    return int(load().leiden_batch_graphs(h))
+
+
+def leiden_batch_trace(h, graph) -> dict:
+    t = np.zeros(TRACE_WORDS, np.int64)
+    _check(h, load().leiden_batch_trace(h, int(graph), _ptr(t)))
+    return _trace_dict(t)
+
+
+def leiden_batch_modularity(h) -> np.ndarray:
+    q = np.zeros(leiden_batch_graphs(h), np.float64)
+    _check(h, load().leiden_batch_modularity(h, _ptr(q)))
+    return q
 
 
 def leiden_kernel_launches() -> int:
@@ -278,3 +319,74 @@ class Leiden:
 
     def stats(self):
         return leiden_get_stats(self.h)
+
+
+class LeidenBatch:
+    """G graphs in one batched handle (``leiden_create_batched``).
+
+    ``graphs`` is a list of ``(n, off, col, w)`` CSRs; they are concatenated
+    with vertex offsets ``self.voff``.  Memberships and batches use the
+    concatenated ids; ``local(arr, g)`` gives graph g's slice shifted back to
+    its own ids.
+    """
+
+    def __init__(self, graphs, cuda_stream=None, **params):
+        p = leiden_default_params()
+        for k, v in params.items():
+            setattr(p, k, v)
+        sizes = [int(g[0]) for g in graphs]
+        self.voff = np.zeros(len(graphs) + 1, np.int64)
+        self.voff[1:] = np.cumsum(sizes)
+        offs, cols, ws = [np.zeros(1, np.int64)], [], []
+        arc_base = 0
+        for (n, off, col, w), v0 in zip(graphs, self.voff[:-1]):
+            off = np.asarray(off, np.int64)
+            offs.append(off[1:] + arc_base)
+            arc_base += int(off[-1])
+            cols.append(np.asarray(col, np.int64) + v0)
+            ws.append(np.ones(int(off[-1]), np.int32) if w is None else np.asarray(w, np.int32))
+        self.n = int(self.voff[-1])
+        self.off = np.concatenate(offs)
+        self.col = np.concatenate(cols).astype(np.int32) if cols else np.zeros(0, np.int32)
+        self.w = np.concatenate(ws) if ws else np.zeros(0, np.int32)
+        self.h = leiden_create_batched(p, self.voff, self.off, self.col, self.w, cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            leiden_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def to_global(self, edges, g):
+        """Edge triples of graph g in its own ids -> concatenated ids."""
+        e = np.array(edges, np.int32).reshape(-1, 3)
+        e[:, :2] += self.voff[g]
+        return e
+
+    def local(self, arr, g):
+        a, b = int(self.voff[g]), int(self.voff[g + 1])
+        return np.asarray(arr)[a:b] - a
+
+    def static(self) -> np.ndarray:
+        out = np.zeros(self.n, np.int32)
+        leiden_static(self.h, out)
+        return out
+
+    def update(self, dels, ins, mode) -> np.ndarray:
+        out = np.zeros(self.n, np.int32)
+        leiden_update(self.h, dels, ins, mode, out)
+        return out
+
+    def modularity(self) -> np.ndarray:
+        return leiden_batch_modularity(self.h)
+
+    def trace(self, g) -> dict:
+        return leiden_batch_trace(self.h, g)
+
+    def state(self):
+        return leiden_get_state(self.h, self.n)

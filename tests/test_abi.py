@@ -65,3 +65,23 @@ def test_create_rejects_bad_input_without_touching_the_gpu(lib):
         L.leiden_create(None, 2, off, col)
     assert e.value.status == L.LEIDEN_ERR_ARG
     assert "self-loop" in L.leiden_last_error(None)
+
+
+def test_create_batched_rejects_bad_input_without_touching_the_gpu(lib):
+    import numpy as np
+
+    # two graphs of 2 vertices; an arc from graph 0 into graph 1
+    off = np.array([0, 1, 2, 3, 4], np.int64)
+    col = np.array([2, 0, 0, 2], np.int32)
+    with pytest.raises(L.LeidenError) as e:
+        L.leiden_create_batched(None, np.array([0, 2, 4], np.int64), off, col)
+    assert e.value.status == L.LEIDEN_ERR_ARG
+    assert "two graphs" in L.leiden_last_error(None)
+    with pytest.raises(L.LeidenError) as e:  # an empty graph
+        L.leiden_create_batched(None, np.array([0, 2, 2, 4], np.int64), off, col)
+    assert e.value.status == L.LEIDEN_ERR_ARG
+    p = L.leiden_default_params()
+    p.deterministic = 0
+    with pytest.raises(L.LeidenError) as e:  # batched handles run the snapshot schedule
+        L.leiden_create_batched(p, np.array([0, 2, 4], np.int64), off, np.array([1, 0, 3, 2], np.int32))
+    assert e.value.status == L.LEIDEN_ERR_ARG
