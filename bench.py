@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--async-mode", action="store_true", help="in-place moves instead of the snapshot schedule")
+    ap.add_argument("--batched", action="store_true",
+                    help="the batched configuration: many planted-partition graphs in one handle vs one call each")
+    ap.add_argument("--graphs", type=int, default=512, help="graphs of the batched configuration")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -367,6 +370,115 @@ def roofline_kernels(stats_list):
     return dom, out
 
 
+# ----------------------------------------------------------------------------- batched configuration
+def batched_graphs(count, seed):
+    """`count` planted-partition graphs: vertex counts log-uniform in [1e3, 2e5],
+    mean degree log-uniform in [4, 64], blocks of 100 vertices, mixing 0.2,
+    unit weights (seeded)."""
+    from paper_2410_15451_gb300 import synth
+
+    rng = np.random.default_rng(seed)
+    ns = np.exp(rng.uniform(np.log(1e3), np.log(2e5), count)).astype(np.int64)
+    ds = np.exp(rng.uniform(np.log(4.0), np.log(64.0), count))
+    return [synth.planted_partition(int(n), max(1, int(n) // 100), float(d), 0.2, seed + 1 + k)
+            for k, (n, d) in enumerate(zip(ns, ds))]
+
+
+def run_batched(args):
+    """DF updates of every graph (1e-3 of its edges, 80/20) processed by one
+    batched call versus one call per graph, both on device-resident batches;
+    the memberships of the two must be equal graph by graph."""
+    import torch
+
+    from paper_2410_15451_gb300 import leiden as L
+    from paper_2410_15451_gb300 import synth
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    seed = synth.BASE_SEED + 3
+    t0 = time.time()
+    gs = batched_graphs(args.graphs, seed)
+    W, K = args.warmup, args.steps
+    sizes = [max(1, int(round(1e-3 * g.off[-1] / 2))) for g in gs]
+    per_graph = [make_batches(g, W + K, sz, seed + 1000 + k) for k, (g, sz) in enumerate(zip(gs, sizes))]
+    gen_s = time.time() - t0
+    edges_per_step = int(sum(sizes))
+
+    def ev_time(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    # one handle per graph, one call per graph and step
+    seq_ms = np.zeros(K)
+    seq_lat = []
+    seq_out = []
+    d_out = torch.empty(max(g.n for g in gs), dtype=torch.int32, device=dev)
+    for k, g in enumerate(gs):
+        h = L.Leiden(g.n, g.off, g.col, g.w, cuda_stream=stream.cuda_stream)
+        h.static()
+        outs = []
+        for step, (d, i) in enumerate(per_graph[k]):
+            dd, di = torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)
+            torch.cuda.synchronize()
+            ms = ev_time(lambda: L.leiden_update_device(h.h, dd, d.shape[0], di, i.shape[0], L.LEIDEN_DF, d_out))
+            if step >= W:
+                seq_ms[step - W] += ms
+                seq_lat.append(ms)
+                outs.append(d_out[:g.n].cpu().numpy().copy())
+        seq_out.append(outs)
+        h.close()
+    # all graphs in one batched handle, one call per step
+    batch = L.LeidenBatch([(g.n, g.off, g.col, g.w) for g in gs], cuda_stream=stream.cuda_stream)
+    t_static0 = time.time()
+    batch.static()
+    static_s = time.time() - t_static0
+    b_out = torch.empty(batch.n, dtype=torch.int32, device=dev)
+    bat_ms = []
+    parity = True
+    launches = 0
+    for step in range(W + K):
+        d = np.concatenate([batch.to_global(per_graph[k][step][0], k) for k in range(len(gs))])
+        i = np.concatenate([batch.to_global(per_graph[k][step][1], k) for k in range(len(gs))])
+        dd, di = torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)
+        torch.cuda.synchronize()
+        l0 = L.leiden_kernel_launches()
+        ms = ev_time(lambda: L.leiden_update_device(batch.h, dd, d.shape[0], di, i.shape[0], L.LEIDEN_DF, b_out))
+        if step >= W:
+            bat_ms.append(ms)
+            launches += L.leiden_kernel_launches() - l0
+            out = b_out.cpu().numpy()
+            for k in range(len(gs)):
+                if not np.array_equal(batch.local(out, k), seq_out[k][step - W]):
+                    parity = False
+    batch.close()
+    bat_total = float(np.sum(bat_ms))
+    seq_total = float(np.sum(seq_ms))
+    line = {
+        "metric": "batched DF update edges/s (all graphs in one call) vs one call per graph", "impl": "batched",
+        "value": edges_per_step * K / (bat_total / 1e3), "unit": "edges/s", "n_gpus": 1, "steps": K, "warmup": W,
+        "ms_per_step": bat_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{len(gs)} planted-partition graphs, n log-uniform in [1e3, 2e5], mean degree "
+                               f"log-uniform in [4, 64], blocks of 100, mixing 0.2; DF updates of 1e-3 of each "
+                               f"graph's edges (80/20)", "graphs": len(gs), "vertices": int(sum(g.n for g in gs)),
+                   "edges": int(sum(g.off[-1] for g in gs) // 2), "batch_edges_per_step": edges_per_step},
+        "sequential": {"value": edges_per_step * K / (seq_total / 1e3), "ms_per_step": seq_total / K,
+                       "p50_ms_per_graph": float(np.percentile(seq_lat, 50)),
+                       "p99_ms_per_graph": float(np.percentile(seq_lat, 99))},
+        "speedup_vs_sequential": seq_total / bat_total,
+        "batched_p99_ms": float(np.percentile(bat_ms, 99)),
+        "parity_with_sequential": parity, "gpu_launches": launches, "static_s_batched": static_s,
+        "setup_s": gen_s,
+    }
+    print(json.dumps(line), flush=True)
+    return 0 if parity else 1
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -381,6 +493,8 @@ def main():
     import __graft_entry__
 
     __graft_entry__.build()
+    if args.batched:
+        return run_batched(args) if rank == 0 else 0
     r = run_ours(args, rank, world, local_rank)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
