@@ -220,6 +220,12 @@ leiden_status leiden_create_batched(const leiden_params *params, int32_t graphs,
                                     const int64_t *offsets, const int32_t *cols, const int32_t *weights,
                                     void *cuda_stream, leiden_handle **out);
 
+/* Device bytes a handle for this graph (CSR offsets[n+1]) is expected to
+ * hold: the allocations of leiden_create plus an allowance for batch buffers
+ * and aggregated-level hash tables that grow on demand.  -1 on bad input.
+ * Used by the server below to admit graphs by footprint. */
+int64_t leiden_footprint_bytes(const leiden_params *params, int64_t n, const int64_t *offsets);
+
 /* Number of graphs of the handle (1 for leiden_create handles). */
 int32_t leiden_batch_graphs(const leiden_handle *h);
 
@@ -230,6 +236,60 @@ leiden_status leiden_batch_trace(leiden_handle *h, int32_t graph, int64_t *trace
 /* Modularity (Eq. 1) of each graph's current membership, q_out[G], with its
  * own 2m. */
 leiden_status leiden_batch_modularity(leiden_handle *h, double *q_out);
+
+/* ---- Serving: many tracked graphs resident on the device ----
+ *
+ * A server keeps every admitted graph's state (CSR with slack, C, K, Sigma,
+ * Delta Sigma) on the device, each graph with a CUDA stream of its own, and
+ * runs update requests on `slots` worker threads as soon as a slot is free.
+ * Admission is by footprint (leiden_footprint_bytes): a graph waits until it
+ * fits in the remaining `device_bytes` budget (graphs leave with
+ * leiden_server_remove_graph), then gets its static Leiden.  Requests of one
+ * graph run one at a time in submission order, so every result equals the
+ * one the graph gets alone (bit for bit in the deterministic schedule);
+ * requests of different graphs overlap on the device.  All functions are
+ * thread-safe.  Library extension: the paper has no serving layer. */
+typedef struct leiden_server leiden_server;
+
+typedef struct {
+  int64_t graphs_resident;   /* admitted and on the device                         */
+  int64_t graphs_waiting;    /* waiting for device memory, or being admitted       */
+  int64_t requests_queued;   /* submitted, not started                             */
+  int64_t requests_running;  /* on a slot now (admissions included)                */
+  int64_t requests_done;     /* finished                                           */
+  int64_t bytes_used;        /* footprint of the resident graphs                   */
+  int64_t bytes_budget;      /* device_bytes                                       */
+} leiden_server_stats;
+
+/* params as for leiden_create (shared by all graphs); 1 <= slots <= 256. */
+leiden_status leiden_server_create(const leiden_params *params, int64_t device_bytes, int32_t slots,
+                                   leiden_server **out);
+/* Register a graph (host CSR as for leiden_create, copied); *graph_out is its
+ * id.  LEIDEN_ERR_OOM if its footprint alone exceeds the budget.  A graph
+ * that fails admission answers its requests with LEIDEN_ERR_OOM. */
+leiden_status leiden_server_add_graph(leiden_server *s, int64_t n, const int64_t *offsets, const int32_t *cols,
+                                      const int32_t *weights, int32_t *graph_out);
+/* Queue an update of `graph` (batch copied); keep_membership != 0 keeps a host
+ * copy of the resulting membership for leiden_server_wait. */
+leiden_status leiden_server_submit(leiden_server *s, int32_t graph, const leiden_edge *del, int64_t n_del,
+                                   const leiden_edge *ins, int64_t n_ins, leiden_mode mode, int32_t keep_membership,
+                                   int64_t *ticket_out);
+/* Wait for a request: its status; membership_out (n of the graph, or NULL),
+ * latency from submission to completion and service time (ms, or NULL).
+ * Each ticket is waited for once. */
+leiden_status leiden_server_wait(leiden_server *s, int64_t ticket, int32_t *membership_out, double *latency_ms,
+                                 double *service_ms);
+/* Current membership of a resident graph (after its queued requests). */
+leiden_status leiden_server_membership(leiden_server *s, int32_t graph, int32_t *membership_out);
+/* Remove a graph once its queued requests are done; its memory is freed and
+ * waiting graphs may be admitted. */
+leiden_status leiden_server_remove_graph(leiden_server *s, int32_t graph);
+leiden_status leiden_server_get_stats(leiden_server *s, leiden_server_stats *out);
+/* Message of the last failure on s (NULL: of the last failed create). */
+const char *leiden_server_last_error(leiden_server *s);
+/* Wait for running work, stop the workers, free everything (queued requests
+ * are dropped). */
+void leiden_server_destroy(leiden_server *s);
 
 /* Number of CUDA kernels this library has launched in the process since it
  * was loaded, over all handles and threads (a relaxed atomic counter; read

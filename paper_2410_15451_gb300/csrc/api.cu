@@ -33,6 +33,18 @@ GraphCounters gc_layout(void *base, int G) {
 // 16+16+8+8+8+4+4+1+1+1 = 67 bytes per graph, rounded up.
 size_t gc_block_bytes(int G) { return 72 * (size_t)G + 64; }
 
+// Global table slots the vertices above the block bin need at level 0.
+int64_t level0_huge_slots(const std::vector<int32_t> &deg) {
+  int64_t slots = 1 << 16;
+  for (int32_t d : deg)
+    if (d > BIN_BLOCK_MAX) {
+      int64_t t = 1;
+      while (t < 2 * (int64_t)d) t <<= 1;
+      slots += t;
+    }
+  return slots;
+}
+
 void kt_begin(leiden_handle *h, int k) {
   if (!(h->p.collect_stats & 2)) return;
   size_t need = 2 * (size_t)(h->kt_used + 1);
@@ -618,7 +630,7 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   h->g_cap = total;
   h->g_arcs = arcs;
   h->g_maxdeg = maxdeg;
-  ensure_hscratch(h, std::max<int64_t>(maxdeg, BIN_BLOCK_MAX + 1));
+  ensure_hslots(h, level0_huge_slots(deg));  // grows on demand for aggregated levels
   *out = h;
   return LEIDEN_OK;
 }
@@ -693,6 +705,34 @@ leiden_status leiden_create_batched(const leiden_params *params, int32_t graphs,
 }
 
 int32_t leiden_batch_graphs(const leiden_handle *h) { return h ? h->G : 0; }
+
+int64_t leiden_footprint_bytes(const leiden_params *params, int64_t n, const int64_t *offsets) {
+  if (n < 1 || !offsets) return -1;
+  leiden_params p;
+  leiden_default_params(&p);
+  if (params) p = *params;
+  int64_t cap = 0;
+  std::vector<int32_t> deg((size_t)n);
+  for (int64_t i = 0; i < n; i++) {
+    int64_t d = offsets[i + 1] - offsets[i];
+    deg[i] = (int32_t)d;
+    cap += d + std::max<int64_t>((int64_t)((double)d * p.slack), p.min_slack);
+  }
+  int64_t total = cap + spill_arena_size(cap);
+  int64_t tc = 1;
+  while (tc < 2 * n) tc <<= 1;
+  int64_t hs = (level0_huge_slots(deg) + 1023) & ~(int64_t)1023;
+  int64_t b = 0;
+  b += 8 * (n + 1) + 8 * n + 8 * total;                              // G^t: off, deg, rcap, col, w
+  b += 4 * n + 24 * n + n;                                            // C, K, Sigma, dSigma, dV
+  b += 52 * (n + 1) + 72 * (n + 2) + 6 * (n + 1);                     // per-pass work arrays
+  b += 4 * (n / 32 + 2) + 16 * n + 4 * (n + 1) + 8 * n;               // frontier, bins, hocc, cand
+  b += 2 * (8 * (n + 2) + 4 * (n + 1) + 12 * total);                  // aggregated levels
+  b += 16 * tc + 4 * n + (int64_t)scan_tmp_bytes(2 * n + 2);          // tracking, scans
+  b += 16 * hs;                                                       // hub tables at level 0
+  b += 8 * n + ((int64_t)32 << 20);                                   // batch buffers (grow with batches)
+  return b;
+}
 
 leiden_status leiden_batch_trace(leiden_handle *h, int32_t graph, int64_t *trace) {
   if (!h || !trace || graph < 0 || graph >= h->G) return LEIDEN_ERR_ARG;

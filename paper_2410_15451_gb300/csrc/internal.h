@@ -194,6 +194,7 @@ void kt_resolve(leiden_handle *h);
 // `base`; gc_block_bytes(G) bytes in all.
 GraphCounters gc_layout(void *base, int G);
 size_t gc_block_bytes(int G);
+int64_t level0_huge_slots(const std::vector<int32_t> &deg);
 
 // Message returned by leiden_last_error(NULL) (calls without a handle).
 void set_handle_free_error(const std::string &msg);
@@ -232,7 +233,6 @@ void lm_subsweep(leiden_handle *h, const LevelGraph &g, int cls, const uint8_t *
 void refine_reset(leiden_handle *h, const LevelGraph &g);
 void refine_round(leiden_handle *h, const LevelGraph &g, int slot);
 void lm_prepare(leiden_handle *h, const LevelGraph &g);  // community sizes
-bool ensure_hscratch(leiden_handle *h, int64_t maxdeg);  // false: allocation failed
 bool ensure_hslots(leiden_handle *h, int64_t slots);     // false: allocation failed
 int32_t *hs_keys(leiden_handle *h);  // global table scratch: keys, values, slot lists
 int64_t *hs_vals(leiden_handle *h);

@@ -66,7 +66,6 @@ struct Args {
   int64_t *gvals;
   int32_t *glist;  // filled slots of each table
   int32_t *gocc;   // number of filled slots of each listed vertex
-  int64_t gslice;
 };
 
 // 2m of the graph vertex i belongs to.
@@ -907,7 +906,6 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
       A.gvals = hs_vals(h);
       A.glist = hs_list(h);
       A.gocc = h->hocc;
-      A.gslice = 0;
       int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
       launch_table_plan(A.list, A.count, g.deg, nullptr, tab_off, ch_off, s);
       ld_note_launch(), k_huge_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
@@ -921,12 +919,6 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
 }
 
 }  // namespace
-
-bool ensure_hscratch(leiden_handle *h, int64_t maxdeg) {
-  int64_t T = 1;
-  while (T < 2 * maxdeg) T <<= 1;
-  return ensure_hslots(h, T * h->sm_count);  // one slice of T slots per resident block
-}
 
 // Global table scratch of `slots` slots laid out as keys int32[S] | values
 // int64[S] | slot lists int32[S] (16 B per slot).  Every user leaves the

@@ -40,6 +40,12 @@ class leiden_stats(ctypes.Structure):
         ("lmk_ms", ctypes.c_double * 3)]
 
 
+class leiden_server_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in (
+        "graphs_resident", "graphs_waiting", "requests_queued", "requests_running", "requests_done", "bytes_used",
+        "bytes_budget")]
+
+
 class LeidenError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"leiden status {status}: {message}")
@@ -86,6 +92,22 @@ def load():
     lib.leiden_batch_trace.restype = ctypes.c_int
     lib.leiden_batch_modularity.argtypes = [vp, vp]
     lib.leiden_batch_modularity.restype = ctypes.c_int
+    lib.leiden_footprint_bytes.argtypes = [P(leiden_params), i64, vp]
+    lib.leiden_footprint_bytes.restype = i64
+    d = ctypes.c_double
+    for name, args in (("leiden_server_create", [P(leiden_params), i64, i32, P(vp)]),
+                       ("leiden_server_add_graph", [vp, i64, vp, vp, vp, P(i32)]),
+                       ("leiden_server_submit", [vp, i32, vp, i64, vp, i64, ctypes.c_int, i32, P(i64)]),
+                       ("leiden_server_wait", [vp, i64, vp, P(d), P(d)]),
+                       ("leiden_server_membership", [vp, i32, vp]),
+                       ("leiden_server_remove_graph", [vp, i32]),
+                       ("leiden_server_get_stats", [vp, P(leiden_server_stats)])):
+        getattr(lib, name).argtypes = args
+        getattr(lib, name).restype = ctypes.c_int
+    lib.leiden_server_last_error.argtypes = [vp]
+    lib.leiden_server_last_error.restype = ctypes.c_char_p
+    lib.leiden_server_destroy.argtypes = [vp]
+    lib.leiden_server_destroy.restype = None
     lib.leiden_kernel_launches.argtypes = []
     lib.leiden_kernel_launches.restype = i64
     lib.leiden_last_error.argtypes = [vp]
@@ -390,3 +412,78 @@ class LeidenBatch:
 
     def state(self):
         return leiden_get_state(self.h, self.n)
+
+
+def leiden_footprint_bytes(n, offsets, params=None) -> int:
+    off = np.ascontiguousarray(offsets, np.int64)
+    return int(load().leiden_footprint_bytes(ctypes.byref(params) if params is not None else None, int(n), _ptr(off)))
+
+
+class LeidenServer:
+    """Resident graphs and concurrent update requests (``leiden_server_*``)."""
+
+    def __init__(self, device_bytes, slots=4, **params):
+        p = leiden_default_params()
+        for k, v in params.items():
+            setattr(p, k, v)
+        self.p = p
+        s = ctypes.c_void_p()
+        self._check(load().leiden_server_create(ctypes.byref(p), int(device_bytes), int(slots), ctypes.byref(s)),
+                    None)
+        self.s = s.value
+        self.sizes = {}
+
+    def _check(self, st, s):
+        if st != LEIDEN_OK:
+            msg = load().leiden_server_last_error(s)
+            raise LeidenError(st, msg.decode() if msg else "")
+
+    def add_graph(self, n, off, col, w=None) -> int:
+        off = np.ascontiguousarray(off, np.int64)
+        col = np.ascontiguousarray(col, np.int32)
+        w = None if w is None else np.ascontiguousarray(w, np.int32)
+        g = ctypes.c_int32()
+        self._check(load().leiden_server_add_graph(self.s, int(n), _ptr(off), _ptr(col), _ptr(w), ctypes.byref(g)),
+                    self.s)
+        self.sizes[g.value] = int(n)
+        return g.value
+
+    def submit(self, graph, dels, ins, mode=LEIDEN_DF, keep_membership=False) -> int:
+        dels = np.ascontiguousarray(np.asarray(dels, np.int32).reshape(-1, 3))
+        ins = np.ascontiguousarray(np.asarray(ins, np.int32).reshape(-1, 3))
+        t = ctypes.c_int64()
+        self._check(load().leiden_server_submit(self.s, int(graph), _ptr(dels), len(dels), _ptr(ins), len(ins),
+                                                int(mode), 1 if keep_membership else 0, ctypes.byref(t)), self.s)
+        return (t.value, int(graph), bool(keep_membership))
+
+    def wait(self, ticket):
+        """-> (membership or None, latency ms, service ms)"""
+        t, graph, keep = ticket
+        out = np.zeros(self.sizes[graph], np.int32) if keep else None
+        lat, svc = ctypes.c_double(), ctypes.c_double()
+        self._check(load().leiden_server_wait(self.s, t, _ptr(out), ctypes.byref(lat), ctypes.byref(svc)), self.s)
+        return out, lat.value, svc.value
+
+    def membership(self, graph) -> np.ndarray:
+        out = np.zeros(self.sizes[graph], np.int32)
+        self._check(load().leiden_server_membership(self.s, int(graph), _ptr(out)), self.s)
+        return out
+
+    def remove_graph(self, graph):
+        self._check(load().leiden_server_remove_graph(self.s, int(graph)), self.s)
+
+    def stats(self) -> dict:
+        st = leiden_server_stats()
+        self._check(load().leiden_server_get_stats(self.s, ctypes.byref(st)), self.s)
+        return {k: getattr(st, k) for k, _ in leiden_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "s", None):
+            load().leiden_server_destroy(self.s)
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

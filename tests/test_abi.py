@@ -85,3 +85,14 @@ def test_create_batched_rejects_bad_input_without_touching_the_gpu(lib):
     with pytest.raises(L.LeidenError) as e:  # batched handles run the snapshot schedule
         L.leiden_create_batched(p, np.array([0, 2, 4], np.int64), off, np.array([1, 0, 3, 2], np.int32))
     assert e.value.status == L.LEIDEN_ERR_ARG
+
+
+def test_footprint_estimate_grows_with_the_graph(lib):
+    import numpy as np
+
+    small = L.leiden_footprint_bytes(1000, np.arange(0, 10 * 1001, 10, dtype=np.int64))
+    big = L.leiden_footprint_bytes(100000, np.arange(0, 10 * 100001, 10, dtype=np.int64))
+    assert 0 < small < big
+    # at least the CSR with slack: 8 bytes per arc
+    assert big > 8 * 10 * 100000
+    assert L.load().leiden_footprint_bytes(None, 0, None) == -1
