@@ -60,6 +60,14 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="the batched configuration: many planted-partition graphs in one handle vs one call each")
     ap.add_argument("--graphs", type=int, default=512, help="graphs of the batched configuration")
+    ap.add_argument("--serve", action="store_true",
+                    help="the serving configuration: resident R-MAT graphs, Poisson arrivals of update requests")
+    ap.add_argument("--serve-graphs", type=int, default=64)
+    ap.add_argument("--serve-scales", default="17,23", help="R-MAT scales drawn uniformly from lo,hi")
+    ap.add_argument("--requests", type=int, default=10000)
+    ap.add_argument("--mean-gap-us", type=float, default=200.0)
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=200.0)
     ap.add_argument("--profile", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -479,6 +487,104 @@ def run_batched(args):
     return 0 if parity else 1
 
 
+# ----------------------------------------------------------------------------- serving configuration
+def run_serve(args):
+    """Resident R-MAT graphs in a server; update requests (sizes log-uniform in
+    [10, 1e5] edges, 80/20, graph uniform) arrive with exponential gaps and
+    run on `slots` workers.  Latency = submission to completion."""
+    import threading
+
+    from paper_2410_15451_gb300 import leiden as L
+    from paper_2410_15451_gb300 import synth
+
+    rng = np.random.default_rng(synth.BASE_SEED + 4)
+    lo, hi = (int(x) for x in args.serve_scales.split(","))
+    t0 = time.time()
+    scales = rng.integers(lo, hi + 1, args.serve_graphs)
+    gs = [synth.rmat(int(sc), 16, 0.57, 0.19, 0.19, synth.BASE_SEED + 4 + 17 * k) for k, sc in enumerate(scales)]
+    R = args.requests
+    which = rng.integers(0, len(gs), R)
+    sizes = np.exp(rng.uniform(np.log(10.0), np.log(1e5), R)).astype(np.int64)
+    gaps = rng.exponential(args.mean_gap_us * 1e-6, R)
+    # per graph: all its edits drawn at once (distinct, valid in sequence), then cut into its requests
+    batches = [None] * R
+    for k, g in enumerate(gs):
+        mine = np.nonzero(which == k)[0]
+        if len(mine) == 0:
+            continue
+        tot = int(sizes[mine].sum())
+        dels, ins = synth.random_batch(g, tot, seed=synth.BASE_SEED + 5000 + k)
+        di = ii = 0
+        for r in mine:
+            n_ins = int(round(0.8 * sizes[r]))
+            n_del = int(sizes[r]) - n_ins
+            batches[r] = (dels[di:di + n_del], ins[ii:ii + n_ins])
+            di += n_del
+            ii += n_ins
+    gen_s = time.time() - t0
+    srv = L.LeidenServer(int(args.serve_budget_gb * 2**30), slots=args.slots)
+    ids = [srv.add_graph(g.n, g.off, g.col, g.w) for g in gs]
+    t1 = time.time()
+    while srv.stats()["graphs_resident"] + 0 < len(gs):
+        st = srv.stats()
+        if st["graphs_waiting"] == 0 and st["graphs_resident"] < len(gs):
+            raise RuntimeError("some graphs failed admission")
+        time.sleep(0.05)
+    admit_s = time.time() - t1
+    tickets = [None] * R
+    submit_at = np.zeros(R)
+    lat = np.zeros(R)
+    svc = np.zeros(R)
+    done = threading.Event()
+
+    def waiter():
+        for r in range(R):
+            while tickets[r] is None:
+                time.sleep(0.0002)
+            _, lat[r], svc[r] = srv.wait(tickets[r])
+        done.set()
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = L.leiden_kernel_launches()
+    start = time.perf_counter()
+    due = start
+    for r in range(R):
+        due += gaps[r]
+        while time.perf_counter() < due:
+            pass
+        submit_at[r] = time.perf_counter()
+        d, i = batches[r]
+        tickets[r] = srv.submit(ids[which[r]], d, i, L.LEIDEN_DF)
+    done.wait()
+    th.join()
+    launches = L.leiden_kernel_launches() - launches0
+    clk = clocks.stop()
+    end = float(np.max(submit_at + lat / 1e3))
+    wall = end - start
+    edges = int(sizes.sum())
+    srv.close()
+    line = {
+        "metric": "served DF update latency p50/p99 and edges/s (resident R-MAT graphs, Poisson arrivals)",
+        "impl": "served", "value": edges / wall, "unit": "edges/s", "n_gpus": 1, "steps": R, "warmup": 0,
+        "ms_per_step": float(np.mean(lat)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"{len(gs)} R-MAT graphs (scales uniform in {lo}..{hi}, edge factor 16), {R} DF "
+                               f"update requests, exponential gaps of mean {args.mean_gap_us:g} us, sizes "
+                               f"log-uniform in [10, 1e5] edges (80/20), graph uniform",
+                   "slots": args.slots, "budget_gb": args.serve_budget_gb,
+                   "vertices": int(sum(g.n for g in gs)), "edges": int(sum(g.off[-1] for g in gs) // 2)},
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "service_p50_ms": float(np.percentile(svc, 50)), "service_p99_ms": float(np.percentile(svc, 99)),
+        "arrival_span_s": float(submit_at[-1] - start), "wall_s": wall, "batch_edges": edges,
+        "gpu_launches": launches, "clocks": clk, "setup_s": gen_s, "admission_s": admit_s,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -495,6 +601,8 @@ def main():
     __graft_entry__.build()
     if args.batched:
         return run_batched(args) if rank == 0 else 0
+    if args.serve:
+        return run_serve(args) if rank == 0 else 0
     r = run_ours(args, rank, world, local_rank)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

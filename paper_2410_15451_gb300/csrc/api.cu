@@ -813,6 +813,7 @@ leiden_status leiden_update(leiden_handle *h, const leiden_edge *del, int64_t n_
   // stage the host batch in device memory (upload buffers grow on demand)
   int64_t need = std::max<int64_t>(std::max(n_del, n_ins), 1);
   if (need > h->up_cap) {
+    need = std::max<int64_t>(need, 2 * h->up_cap);  // geometric growth (fewer device-wide frees)
     for (auto &q : h->owned)
       if (q && (q == h->up_del || q == h->up_ins)) { cudaFree(q); q = nullptr; }
     h->up_del = h->up_ins = nullptr;

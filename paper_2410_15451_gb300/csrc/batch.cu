@@ -547,7 +547,9 @@ void release(leiden_handle *h, void *p) {
 cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
   BatchBuffers &b = h->b;
   if (b.cap_edges > 0 && edges <= b.cap_edges) return cudaSuccess;  // the first call always allocates
-  int64_t cap = std::max<int64_t>(edges, 1024);
+  // geometric growth: a freed buffer synchronises the whole device, which
+  // stalls every other stream of a serving process
+  int64_t cap = std::max<int64_t>({edges, 2 * b.cap_edges, (int64_t)1024});
   void *old[] = {b.dkey, b.dkey_alt, b.ikey, b.ikey_alt, b.iw, b.iw_alt, b.dw, b.flag,
                  b.pos, b.ins_state, b.ins_pos, b.row_dlo, b.row_dhi, b.row_ilo, b.row_ihi, b.row_len,
                  b.row_tmp_off, b.rows, b.ds_key, b.ds_key_alt, b.ds_w, b.ds_w_alt, b.ds_ukey, b.ds_uw,
@@ -607,7 +609,7 @@ cudaError_t ensure_tmp_rows(leiden_handle *h, int64_t arcs) {
   if (arcs <= b.tmp_cap) return cudaSuccess;
   release(h, b.tmp_col);
   release(h, b.tmp_w);
-  int64_t cap = std::max<int64_t>(arcs, 4096);
+  int64_t cap = std::max<int64_t>({arcs, 2 * b.tmp_cap, (int64_t)4096});
   cudaError_t e = grow(h, &b.tmp_col, cap);
   if (e == cudaSuccess) e = grow(h, &b.tmp_w, cap);
   if (e == cudaSuccess) b.tmp_cap = cap;
