@@ -211,6 +211,27 @@ __device__ __forceinline__ void stage_insert_warp(Stage &S, bool valid, int32_t 
   }
 }
 
+// Lane-wise form: every thread with a pair adds it with shared atomics.
+__device__ __forceinline__ void stage_insert_lanes(Stage &S, bool valid, int32_t c, int64_t w) {
+  if (!valid) return;
+  uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(STAGE_SLOTS - 1);
+  while (true) {
+    int32_t k = S.keys[s];
+    if (k == LD_EMPTY_KEY) {
+      k = atomicCAS(&S.keys[s], LD_EMPTY_KEY, c);
+      if (k == LD_EMPTY_KEY) {
+        S.list[atomicAdd(&S.count, 1)] = (int32_t)s;
+        k = c;
+      }
+    }
+    if (k == c) {
+      atomicAdd((unsigned long long *)&S.vals[s], (unsigned long long)w);
+      return;
+    }
+    s = (s + 1) & (uint32_t)(STAGE_SLOTS - 1);
+  }
+}
+
 // Empty the listed slots (all threads of the block; ends synchronised).
 __device__ __forceinline__ void stage_clear(Stage &S) {
   __syncthreads();
@@ -281,6 +302,32 @@ __device__ __forceinline__ void wt_insert_warp(WarpTable &T, bool valid, int32_t
       }
       // a key already in the table lies before the first empty slot of its probe path
       if (k == c) { T.vals[s] += sum; break; }
+      s = (s + 1) & (uint32_t)(WT_SLOTS - 1);
+    }
+  }
+  __syncwarp();
+}
+
+// All 32 lanes call it; each lane with a pair adds it on its own with a
+// shared-memory atomic (lanes of one warp only, so the only contention is
+// between lanes with the same key, which the atomic unit serialises) -- no
+// key grouping and no shuffles.
+__device__ __forceinline__ void wt_insert_lanes(WarpTable &T, bool valid, int32_t c, int64_t w) {
+  if (valid) {
+    uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(WT_SLOTS - 1);
+    while (true) {
+      int32_t k = T.keys[s];
+      if (k == LD_EMPTY_KEY) {
+        k = atomicCAS(&T.keys[s], LD_EMPTY_KEY, c);
+        if (k == LD_EMPTY_KEY) {
+          T.list[atomicAdd(&T.count, 1)] = (int32_t)s;
+          k = c;
+        }
+      }
+      if (k == c) {
+        atomicAdd((unsigned long long *)&T.vals[s], (unsigned long long)w);
+        break;
+      }
       s = (s + 1) & (uint32_t)(WT_SLOTS - 1);
     }
   }

@@ -523,7 +523,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Args A) {
         valid = j != i && (KIND != KIND_REFINE || A.CB[j] == bi);
         if (valid) { c = A.C[j]; wa = (int64_t)w[base + a]; }
       }
-      stage_insert_warp(S, valid, c, wa);
+      stage_insert_lanes(S, valid, c, wa);
     }
     __syncthreads();
     int n = S.count;
@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(256) k_huge_scan(Args A, const int64_t *tab_of
         if (valid) { c = A.C[j]; wa = (int64_t)w[base + a]; }
       }
       if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
-      wt_insert_warp(T8, valid, c, wa);
+      wt_insert_lanes(T8, valid, c, wa);
     }
     wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
     if (KIND == KIND_MOVE && threadIdx.x == 0)

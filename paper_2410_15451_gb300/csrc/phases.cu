@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t
         wa = (int64_t)w[arc];
       }
       if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
-      wt_insert_warp(T8, valid, c, wa);
+      wt_insert_lanes(T8, valid, c, wa);
     }
     wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
   }
