@@ -9,7 +9,8 @@
 namespace {
 
 constexpr int TB = 256;
-constexpr int MERGE_SMALL = 1024;  // touched rows up to this new length merge in one warp
+constexpr int MERGE_SMALL = 256;  // touched rows up to this new length merge in one warp (8 KB of
+                                  // shared staging per block keeps many rows in flight)
 
 __device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, int32_t x) {
   int64_t lo = 0, hi = n;

@@ -85,20 +85,39 @@ __device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b) 
 // its first SPLIT_SAMPLES neighbours in the same community.
 constexpr int SPLIT_SAMPLES = 2;
 constexpr int SPLIT_SAMPLE_SCAN = 64;
+// Eight lanes per vertex read its row prefix eight arcs at a time and the
+// lanes holding the first SPLIT_SAMPLES same-community neighbours link.
 __global__ void k_split_sample(const int32_t *list, const DevCounters *cnt, const int64_t *off, const int32_t *deg,
                                const int32_t *col, const int32_t *C, int32_t *parent) {
   int64_t m = cnt->split_count;
-  for (int64_t t = ld_gtid(); t < m; t += ld_gstride()) {
-    int32_t i = list[t];
-    int32_t c = C[i];
-    int64_t b = off[i], d = deg[i];
+  int lane = threadIdx.x & 31, grp = lane >> 3, sub = lane & 7;
+  uint32_t gmask = 0xffu << (grp * 8);
+  int64_t ngroups = ld_gstride() >> 3;
+  for (int64_t t0 = (ld_gtid() >> 5) * 4; t0 < m; t0 += ngroups) {  // warp-uniform trip count
+    int64_t t = t0 + grp;
+    bool has = t < m;
+    int32_t i = 0, c = 0;
+    int64_t b = 0, d = 0;
+    if (has) {
+      i = list[t];
+      c = C[i];
+      b = off[i];
+      d = deg[i];
+      if (d > SPLIT_SAMPLE_SCAN) d = SPLIT_SAMPLE_SCAN;  // sampling looks at a short prefix only
+    }
     int got = 0;
-    if (d > SPLIT_SAMPLE_SCAN) d = SPLIT_SAMPLE_SCAN;  // sampling looks at a short prefix only
-    for (int64_t a = 0; a < d && got < SPLIT_SAMPLES; a++) {
-      int32_t j = col[b + a];
-      if (j == i || C[j] != c) continue;
-      uf_unite(parent, i, j);
-      got++;
+    for (int64_t a0 = 0; a0 < SPLIT_SAMPLE_SCAN; a0 += 8) {
+      bool live = has && got < SPLIT_SAMPLES && a0 < d;
+      if (!__any_sync(LD_FULL, live)) break;
+      int32_t j = -1;
+      bool hit = false;
+      if (live && a0 + sub < d) {
+        j = col[b + a0 + sub];
+        hit = j != i && C[j] == c;
+      }
+      uint32_t hits = __ballot_sync(LD_FULL, hit) & gmask;
+      if (hit && __popc(hits & ((1u << lane) - 1u)) < SPLIT_SAMPLES - got) uf_unite(parent, i, j);
+      if (live) got += __popc(hits);
     }
   }
 }
@@ -544,7 +563,7 @@ void split_communities(leiden_handle *h, const LevelGraph &g) {
   cudaMemsetAsync(&h->dcnt->split_count, 0, sizeof(int32_t), s);
   int32_t *list = h->ibuf1;
   ld_note_launch(), k_split_init<<<grid_for(g.n, TB), TB, 0, s>>>(g.n, h->Cp, h->dS, h->dR, h->parent, list, h->dcnt);
-  ld_note_launch(), k_split_sample<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
+  ld_note_launch(), k_split_sample<<<h->sm_count * 16, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
   ld_note_launch(), k_split_flatten<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent);
   cudaMemsetAsync(&h->dcnt->big_count, 0, sizeof(int32_t), s);
   ld_note_launch(), k_split_link_rest<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent, h->ibuf2);
