@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="the batched configuration: many planted-partition graphs in one handle vs one call each")
     ap.add_argument("--graphs", type=int, default=512, help="graphs of the batched configuration")
+    ap.add_argument("--stability", action="store_true",
+                    help="delete a random batch, insert it back (DF both times); fraction of memberships kept")
     ap.add_argument("--serve", action="store_true",
                     help="the serving configuration: resident R-MAT graphs, Poisson arrivals of update requests")
     ap.add_argument("--serve-graphs", type=int, default=64)
@@ -487,6 +489,42 @@ def run_batched(args):
     return 0 if parity else 1
 
 
+# ----------------------------------------------------------------------------- stability protocol
+def run_stability(args):
+    """Delete a batch of random existing edges, then insert the same edges
+    back, each step a DF update; report the fraction of vertices whose
+    community id after the round trip equals the one before it."""
+    from paper_2410_15451_gb300 import leiden as L
+    from paper_2410_15451_gb300 import synth
+
+    seed = synth.BASE_SEED + 6
+    g = synth.rmat(args.scale, 16, 0.57, 0.19, 0.19, seed)
+    h = L.Leiden(g.n, g.off, g.col, g.w)
+    h.static()
+    src = np.repeat(np.arange(g.n), np.diff(g.off))
+    keep = src < g.col
+    edges = np.stack([src[keep], g.col[keep], g.w[keep]], 1).astype(np.int32)
+    rng = np.random.default_rng(seed)
+    none = np.zeros((0, 3), np.int32)
+    out = {}
+    for frac in (1e-7, 1e-5, 1e-3, 1e-1):
+        size = max(1, int(round(frac * len(edges))))
+        kept = []
+        for trial in range(3):
+            c0 = h.state()["C"]  # current membership
+            batch = edges[rng.choice(len(edges), size, replace=False)]
+            h.update(batch, none, L.LEIDEN_DF)
+            c2 = h.update(none, batch, L.LEIDEN_DF)
+            kept.append(float(np.mean(c2 == c0)))
+        out[f"{frac:g}"] = {"batch_edges": size, "memberships_kept": float(np.mean(kept)), "trials": kept}
+    line = {"metric": "memberships kept after delete + reinsert of a random batch (DF)", "impl": "stability",
+            "unit": "fraction", "data": "synthetic", "dtype": "int64",
+            "config": {"workload": f"R-MAT scale {args.scale} (n={g.n}, |E|={len(edges)}), 3 trials per size"},
+            "result": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- serving configuration
 def run_serve(args):
     """Resident R-MAT graphs in a server; update requests (sizes log-uniform in
@@ -603,6 +641,8 @@ def main():
         return run_batched(args) if rank == 0 else 0
     if args.serve:
         return run_serve(args) if rank == 0 else 0
+    if args.stability:
+        return run_stability(args) if rank == 0 else 0
     r = run_ours(args, rank, world, local_rank)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

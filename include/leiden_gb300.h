@@ -173,6 +173,15 @@ leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *d_offsets, con
                                         const int32_t *d_weights, const int32_t *d_membership,
                                         void *cuda_stream, double *q_out);
 
+/* Resume from an exported state: a handle created from the exported graph
+ * (leiden_get_graph) takes the exported membership C (int32[n]) and Delta
+ * Sigma (int64[n], indexed by community id); K, Sigma and 2m are recomputed
+ * from the graph (they are functions of it and of C).  The handle then
+ * behaves as the exporting one did: leiden_update may follow directly, with
+ * no leiden_static.  LEIDEN_ERR_ARG on ids out of range (or outside their
+ * graph's range on a batched handle).  Library extension (checkpointing). */
+leiden_status leiden_import_state(leiden_handle *h, const int32_t *C, const int64_t *dSigma);
+
 /* Device pointer to the handle's current membership C^t (int32[n]); valid
  * until the next call on the handle. */
 leiden_status leiden_membership_device(leiden_handle *h, const int32_t **d_membership);

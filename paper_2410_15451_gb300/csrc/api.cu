@@ -894,6 +894,44 @@ leiden_status leiden_get_state(leiden_handle *h, int32_t *C, int64_t *K, int64_t
   return LEIDEN_OK;
 }
 
+leiden_status leiden_import_state(leiden_handle *h, const int32_t *C, const int64_t *dSigma) {
+  leiden_status st = check_handle(h);
+  if (st != LEIDEN_OK) return st;
+  if (!C || !dSigma) return LEIDEN_ERR_ARG;
+  int64_t N = h->n;
+  for (int64_t i = 0; i < N; i++)
+    if (C[i] < 0 || C[i] >= N) { h->err = "membership id out of range"; return LEIDEN_ERR_ARG; }
+  if (h->G > 1)
+    for (int32_t gi = 0; gi < h->G; gi++)
+      for (int64_t i = h->voff[gi]; i < h->voff[gi + 1]; i++)
+        if (C[i] < h->voff[gi] || C[i] >= h->voff[gi + 1]) {
+          h->err = "membership id outside its graph's range";
+          return LEIDEN_ERR_ARG;
+        }
+  cudaStream_t s = h->stream;
+  // K and 2m from G^t, Sigma from K and C (Section 4.1: the auxiliary
+  // information is a function of the graph and the membership, plus the
+  // accumulated Delta Sigma)
+  recompute_weights(h);
+  CK(cudaMemcpyAsync(h->C, C, (size_t)N * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(h->dSig, dSigma, (size_t)N * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // the host arrays may be freed on return
+  recompute_sigma(h);
+  sync_all(h);
+  CK(cudaGetLastError());
+  h->m2 = h->hcnt->m2;
+  if (h->G > 1) {
+    GraphCounters hg = gc_layout(h->gc_host, h->G);
+    for (int gi = 0; gi < h->G; gi++) h->m2g[gi] = hg.m2[gi];
+  }
+  level_maxdeg(h, h->g_deg, N);
+  sync_counters(h);
+  h->g_maxdeg = h->hcnt->max_count;
+  h->g_huge_slots = h->hcnt->huge_slots;
+  h->has_static = true;
+  return LEIDEN_OK;
+}
+
 int64_t leiden_graph_arcs(leiden_handle *h) { return h ? h->g_arcs : -1; }
 
 leiden_status leiden_get_graph(leiden_handle *h, int64_t *off, int32_t *col, int64_t *w) {

@@ -260,3 +260,4 @@ void level_maxdeg(leiden_handle *h, const int32_t *deg, int64_t n);  // into dcn
 void track_communities(leiden_handle *h);  // Ctop vs C -> C, Sig, dSig
 void modularity_terms(leiden_handle *h, const int32_t *C);  // into dcnt->sigma_intra / sq
 void recompute_weights(leiden_handle *h);  // K = row sums, m2 (device)
+void recompute_sigma(leiden_handle *h);    // Sigma from K and C

@@ -301,6 +301,13 @@ void modularity_terms(leiden_handle *h, const int32_t *C) {
   ld_note_launch(), k_sq<<<grid_for(N, TB), TB, 0, s>>>(N, Sig, h->dcnt, h->gid0, h->gc.sq);
 }
 
+// Sigma = per-community sums of K for membership h->C.
+void recompute_sigma(leiden_handle *h) {
+  cudaStream_t s = h->stream;
+  cudaMemsetAsync(h->Sig, 0, (size_t)h->n * sizeof(int64_t), s);
+  ld_note_launch(), k_sig_of<<<grid_for(h->n, TB), TB, 0, s>>>(h->n, h->C, h->K, h->Sig);
+}
+
 // K = row sums of G^t and 2m.
 void recompute_weights(leiden_handle *h) {
   cudaStream_t s = h->stream;

@@ -78,6 +78,8 @@ def load():
     lib.leiden_modularity_noalloc.argtypes = [i64, vp, vp, vp, vp, vp, P(ctypes.c_double)]
     lib.leiden_modularity_noalloc.restype = ctypes.c_int
     lib.leiden_get_state.argtypes = [vp, vp, vp, vp, vp, P(i64)]
+    lib.leiden_import_state.argtypes = [vp, vp, vp]
+    lib.leiden_import_state.restype = ctypes.c_int
     lib.leiden_graph_arcs.argtypes = [vp]
     lib.leiden_graph_arcs.restype = i64
     lib.leiden_get_graph.argtypes = [vp, vp, vp, vp]
@@ -203,6 +205,12 @@ def leiden_get_state(h, n):
     m2 = ctypes.c_int64()
     _check(h, load().leiden_get_state(h, _ptr(C), _ptr(K), _ptr(S), _ptr(dS), ctypes.byref(m2)))
     return dict(C=C, K=K, Sigma=S, dSigma=dS, m2=m2.value)
+
+
+def leiden_import_state(h, C, dSigma):
+    C = np.ascontiguousarray(C, np.int32)
+    dS = np.ascontiguousarray(dSigma, np.int64)
+    _check(h, load().leiden_import_state(h, _ptr(C), _ptr(dS)))
 
 
 def leiden_graph_arcs(h) -> int:
