@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="the batched configuration: many planted-partition graphs in one handle vs one call each")
     ap.add_argument("--graphs", type=int, default=512, help="graphs of the batched configuration")
+    ap.add_argument("--ablation", action="store_true",
+                    help="DF updates under the ablation switches: split all, OR convergence, tau_re sweep")
     ap.add_argument("--stability", action="store_true",
                     help="delete a random batch, insert it back (DF both times); fraction of memberships kept")
     ap.add_argument("--serve", action="store_true",
@@ -489,6 +491,49 @@ def run_batched(args):
     return 0 if parity else 1
 
 
+# ----------------------------------------------------------------------------- ablations
+def run_ablation(args):
+    """The same DF update stream (R-MAT, 1e-3|E| batches) under each switch:
+    mean update time and the final modularity."""
+    import torch
+
+    from paper_2410_15451_gb300 import leiden as L
+    from paper_2410_15451_gb300 import synth
+
+    seed = synth.BASE_SEED + 7
+    g = synth.rmat(args.scale, 16, 0.57, 0.19, 0.19, seed)
+    size = max(1, int(round(args.batch_frac * g.edges)))
+    W, K = args.warmup, args.steps
+    batches = make_batches(g, W + K, size, seed + 1)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    dev_batches = [(torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)) for d, i in batches]
+    out = {}
+    for name, flags in (("default", {}), ("split_all", dict(split_all=1)), ("converge_any", dict(converge_any=1)),
+                        ("tau_re=0.2", dict(tau_refine=0.2)), ("tau_re=1.0", dict(tau_refine=1.0)),
+                        ("tau_re=2.0", dict(tau_refine=2.0))):
+        h = L.Leiden(g.n, g.off, g.col, g.w, cuda_stream=stream.cuda_stream, **flags)
+        h.static()
+        ms = []
+        for k, (d, i) in enumerate(dev_batches):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.leiden_update_device(h.h, d, d.shape[0], i, i.shape[0], L.LEIDEN_DF, None)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= W:
+                ms.append(e0.elapsed_time(e1))
+        out[name] = {"ms_mean": float(np.mean(ms)), "p99_ms": float(np.percentile(ms, 99)), "q": h.modularity()}
+        h.close()
+    line = {"metric": "DF update time and modularity under ablation switches", "impl": "ablation",
+            "unit": "ms", "data": "synthetic", "dtype": "int64",
+            "config": {"workload": f"R-MAT scale {args.scale} (n={g.n}, |E|={g.edges}), DF updates of {size} "
+                                   f"edges, {K} timed after {W} warm-up"}, "result": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- stability protocol
 def run_stability(args):
     """Delete a batch of random existing edges, then insert the same edges
@@ -643,6 +688,8 @@ def main():
         return run_serve(args) if rank == 0 else 0
     if args.stability:
         return run_stability(args) if rank == 0 else 0
+    if args.ablation:
+        return run_ablation(args) if rank == 0 else 0
     r = run_ours(args, rank, world, local_rank)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -64,6 +64,11 @@ typedef struct {
   int32_t collect_stats;  /* bit 1: time each phase with CUDA events (adds syncs);        */
                           /* bit 2: time each launch of the local-moving kernels          */
                           /*    with an event pair on the stream (no added syncs); 0      */
+  int32_t split_all;      /* ablation: split every community that is not refined, not     */
+                          /*    only the changed ones (Section 4.1.3 splits changed); 0   */
+  int32_t converge_any;   /* ablation: leave the pass loop when l_i <= 1 OR no community  */
+                          /*    was refined (the text's reading; the pseudocode's AND     */
+                          /*    is the default); 0                                        */
 } leiden_params;
 
 /* Counters and phase times of the last static/update call. */

@@ -39,7 +39,8 @@ def build(force: bool = False) -> str:
 class _Params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("tau_drop", ctypes.c_double), ("tau_refine", ctypes.c_double),
                 ("max_iterations", ctypes.c_int32), ("max_passes", ctypes.c_int32),
-                ("schedule", ctypes.c_int32), ("classes", ctypes.c_int32)]
+                ("schedule", ctypes.c_int32), ("classes", ctypes.c_int32),
+                ("split_all", ctypes.c_int32), ("converge_any", ctypes.c_int32)]
 
 
 def _load():
@@ -74,8 +75,8 @@ def _p(a):
 
 
 def params(schedule=SYNC, tau=1e-2, tau_drop=10.0, tau_refine=0.6, max_iterations=20, max_passes=10,
-           classes=4):
-    return _Params(tau, tau_drop, tau_refine, max_iterations, max_passes, schedule, classes)
+           classes=4, split_all=0, converge_any=0):
+    return _Params(tau, tau_drop, tau_refine, max_iterations, max_passes, schedule, classes, split_all, converge_any)
 
 
 def _i128(lo, hi) -> int:

@@ -679,9 +679,10 @@ static int leiden_run(oracle_state *s, const int32_t *Cprev, uint8_t *dSp, uint8
                            m2, p, &H, tr + 5);
     tr[1] = li;
     subset_renumber(n, Cp, Sp, dSp, dR);
-    /* split communities marked in dS and not in dR */
+    /* split communities marked in dS and not in dR (or, as an ablation, every
+       community not in dR) */
     uint8_t *split_c = (uint8_t *)xcalloc((size_t)n, 1);
-    for (int64_t c = 0; c < n; c++) split_c[c] = dSp[c] && !dR[c];
+    for (int64_t c = 0; c < n; c++) split_c[c] = (p->split_all || dSp[c]) && !dR[c];
     split_components(&G, Cp, split_c);
     free(split_c);
     memcpy(CB, Cp, (size_t)n * sizeof(int32_t)); /* community bounds */
@@ -701,8 +702,12 @@ static int leiden_run(oracle_state *s, const int32_t *Cprev, uint8_t *dSp, uint8
       free(seen);
       tr[2] = k;
     }
-    if (li <= 1 && !refined_any) break;
-    if (li <= 1 && lp > 0) break;
+    if (p->converge_any) {
+      if (li <= 1 || !refined_any) break;
+    } else {
+      if (li <= 1 && !refined_any) break;
+      if (li <= 1 && lp > 0) break;
+    }
     int64_t ncomm = renumber_dense(n, Cp);
     for (int64_t v = 0; v < N; v++) Ctop[v] = Cp[Ctop[v]]; /* dendrogram lookup */
     ograph Y;

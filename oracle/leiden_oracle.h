@@ -36,6 +36,9 @@ typedef struct {
   int32_t max_passes;      /* 10 */
   int32_t schedule;        /* ORACLE_SEQ or ORACLE_SYNC */
   int32_t classes;         /* SYNC: sub-sweeps per local-moving iteration, 4 */
+  int32_t split_all;       /* ablation: split every community not refined (not only changed ones), 0 */
+  int32_t converge_any;    /* ablation: leave the pass loop when l_i <= 1 OR nothing was refined
+                              (the text's reading of the convergence test), 0 */
 } oracle_params;
 
 typedef struct oracle_state oracle_state;

@@ -321,8 +321,9 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
       t_ref += ev_ms(h, 3, 4);
     }
     if (!B) {
+      if (p.converge_any && (li <= 1 || !refined_any)) break;
       if (li <= 1 && !refined_any) break;
-      if (li <= 1 && lp > 0) break;
+      if (li <= 1 && lp > 0 && !p.converge_any) break;
       if (lp == p.max_passes - 1) {
         // the pass limit is reached: lookup with C' below, as when breaking
         break;
@@ -339,7 +340,9 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
           t[3] = refany[gi];
           t[4] = rounds_g[gi];
         }
-        bool brk = (li_g[gi] <= 1 && !refany[gi]) || (li_g[gi] <= 1 && lp > 0) || lp == p.max_passes - 1;
+        bool brk = p.converge_any ? (li_g[gi] <= 1 || !refany[gi])
+                                  : ((li_g[gi] <= 1 && !refany[gi]) || (li_g[gi] <= 1 && lp > 0));
+        brk = brk || lp == p.max_passes - 1;
         cont[gi] = !brk;
         any_cont = any_cont || !brk;
       }
@@ -486,6 +489,8 @@ void leiden_default_params(leiden_params *p) {
   p->slack = 0.25;
   p->min_slack = 4;
   p->collect_stats = 0;
+  p->split_all = 0;
+  p->converge_any = 0;
 }
 
 leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_t *offsets, const int32_t *cols,

@@ -42,14 +42,14 @@ __global__ void k_sr_remap(int64_t n, const int32_t *rep, int32_t *C) {
 // only ever hooked under a smaller root, so every component ends with its
 // smallest vertex as root -- the label a BFS from the lowest vertex gives.
 __global__ void k_split_init(int64_t n, const int32_t *C, const uint8_t *dS, const uint8_t *dR, int32_t *parent,
-                             int32_t *list, DevCounters *cnt) {
+                             int32_t *list, DevCounters *cnt, int split_all) {
   int lane = threadIdx.x & 31;
   for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
     int64_t i = base + lane;
     bool f = false;
     if (i < n) {
       int32_t c = C[i];
-      f = dS[c] && !dR[c];
+      f = (split_all || dS[c]) && !dR[c];
       if (f) parent[i] = (int32_t)i;
     }
     uint32_t m = __ballot_sync(LD_FULL, f);
@@ -562,7 +562,8 @@ void split_communities(leiden_handle *h, const LevelGraph &g) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->split_count, 0, sizeof(int32_t), s);
   int32_t *list = h->ibuf1;
-  ld_note_launch(), k_split_init<<<grid_for(g.n, TB), TB, 0, s>>>(g.n, h->Cp, h->dS, h->dR, h->parent, list, h->dcnt);
+  ld_note_launch(), k_split_init<<<grid_for(g.n, TB), TB, 0, s>>>(g.n, h->Cp, h->dS, h->dR, h->parent, list, h->dcnt,
+                                                                               h->p.split_all);
   ld_note_launch(), k_split_sample<<<h->sm_count * 16, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
   ld_note_launch(), k_split_flatten<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent);
   cudaMemsetAsync(&h->dcnt->big_count, 0, sizeof(int32_t), s);

@@ -28,7 +28,8 @@ class leiden_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("tau_drop", ctypes.c_double), ("tau_refine", ctypes.c_double),
                 ("max_iterations", ctypes.c_int32), ("max_passes", ctypes.c_int32),
                 ("deterministic", ctypes.c_int32), ("classes", ctypes.c_int32),
-                ("slack", ctypes.c_double), ("min_slack", ctypes.c_int32), ("collect_stats", ctypes.c_int32)]
+                ("slack", ctypes.c_double), ("min_slack", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
+                ("split_all", ctypes.c_int32), ("converge_any", ctypes.c_int32)]
 
 
 class leiden_stats(ctypes.Structure):

@@ -255,3 +255,23 @@ def test_stats_timers_and_launch_counter_leave_results_unchanged():
     for k in range(3):
         lo = (40 * v[k] if k < 2 else 0) + 12 * e[k]
         assert lo <= s["lmk_bytes"][k] <= lo + 4 * e[k]
+
+
+@pytest.mark.parametrize("flags", [dict(split_all=1), dict(converge_any=1), dict(tau_refine=0.2),
+                                   dict(tau_refine=2.0)], ids=["split_all", "converge_any", "tau_re0.2", "tau_re2"])
+def test_ablation_switches_bit_exact(flags):
+    """The ablation switches (split every unrefined community, the OR reading
+    of the convergence test, other tau_re) match the oracle bit for bit."""
+    g = synth.rmat(13, seed=306)
+    gpu = L.Leiden(g.n, g.off, g.col, g.w, **flags)
+    ref = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC, **flags)
+    assert np.array_equal(gpu.static(), ref.static())
+    assert_same_trace(gpu, ref)
+    cur = g
+    for k in range(2):
+        d, i = synth.random_batch(cur, 400, seed=307 + k)
+        cg, cr = gpu.update(d, i, L.LEIDEN_DF), ref.update(d, i, oracle.DF)
+        cur = synth.apply_batch_numpy(cur, d, i)
+        assert_same_trace(gpu, ref)
+        assert np.array_equal(cg, cr)
+        assert_same_state(gpu, ref)

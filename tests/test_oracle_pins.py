@@ -422,3 +422,41 @@ def test_sync_and_seq_agree_in_quality():
         q[sch] = o.modularity()
         assert disconnected_communities(g.off, g.col, C) == 0
     assert abs(q[oracle.SEQ] - q[oracle.SYNC]) < 0.01
+
+
+# ---- ablation switches (Section 4.1.3 splitting of changed communities; the
+# convergence test of Alg. "leiden" read with AND, as printed, or OR)
+
+def test_split_all_changes_nothing_in_static_leiden():
+    """Static Leiden refines every community, and a refined community is
+    never split, so splitting 'all' communities is the same computation."""
+    g = synth.planted_partition(2000, 20, 10, 0.3, 301)
+    a = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    b = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC, split_all=1)
+    assert np.array_equal(a.static(), b.static())
+    assert a.trace() == b.trace()
+
+
+def test_split_all_keeps_communities_connected_after_updates():
+    g = synth.rmat(11, seed=302)
+    o = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC, split_all=1)
+    o.static()
+    cur = g
+    for k in range(2):
+        d, i = synth.random_batch(cur, 150, seed=303 + k)
+        C = o.update(d, i, oracle.DF)
+        cur = synth.apply_batch_numpy(cur, d, i)
+        assert disconnected_communities(cur.off, cur.col, C) == 0
+
+
+def test_converge_any_stops_no_later_than_the_printed_test():
+    """OR is implied by AND at every pass, so the text's reading never runs
+    more passes; the first pass is identical."""
+    for g in (synth.planted_partition(2000, 20, 10, 0.3, 304), synth.rmat(11, seed=305)):
+        a = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+        b = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC, converge_any=1)
+        a.static()
+        b.static()
+        ta, tb = a.trace(), b.trace()
+        assert len(tb["passes"]) <= len(ta["passes"])
+        assert ta["passes"][0] == tb["passes"][0]
