@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="the batched configuration: many planted-partition graphs in one handle vs one call each")
     ap.add_argument("--graphs", type=int, default=512, help="graphs of the batched configuration")
+    ap.add_argument("--large", action="store_true",
+                    help="the large web-like configuration: degree-corrected planted partition, 20 DF batches, "
+                         "checked at full size")
+    ap.add_argument("--large-n", type=int, default=30_000_000)
     ap.add_argument("--ablation", action="store_true",
                     help="DF updates under the ablation switches: split all, OR convergence, tau_re sweep")
     ap.add_argument("--stability", action="store_true",
@@ -491,6 +495,132 @@ def run_batched(args):
     return 0 if parity else 1
 
 
+# ----------------------------------------------------------------------------- large configuration
+def run_large(args):
+    """Degree-corrected planted partition (power-law degrees, exponent 2.1, max
+    1e6; community sizes power-law, exponent 1.5, in [10, 1e5]; mixing 0.3;
+    weights 1..8), static Leiden, then 20 DF batches of 1e-4|E| (80/20).
+    Checked at full size by properties and sampled outputs: K, Sigma and 2m
+    against the final graph; the applied CSR rows of sampled touched vertices
+    against the batches; every community connected (oracle split); Q equal to
+    the oracle's Eq. 1 on the same membership; Q_static - Q_DF <= 0.005."""
+    import gc
+
+    import torch
+
+    import oracle
+    from paper_2410_15451_gb300 import leiden as L
+    from paper_2410_15451_gb300 import synth
+
+    seed = synth.BASE_SEED + 2
+    rep = {}
+    t0 = time.time()
+    g = synth.dcpp(args.large_n, avg_deg=84.0, deg_exp=2.1, max_deg=1e6, comm_exp=1.5, cmin=10, cmax=100000,
+                   mu=0.3, wmax=8, seed=seed)
+    rep["gen_s"] = time.time() - t0
+    E = g.edges
+    deg0 = np.diff(g.off)
+    rep.update(n=g.n, edges=int(E), mean_degree=float(deg0.mean()), max_degree=int(deg0.max()))
+    size = max(1, int(round(1e-4 * E)))
+    nb = 20
+    dels, ins = synth.random_batch(g, nb * size, seed=seed + 11, w_lo=1, w_hi=8)
+    n_ins = int(round(0.8 * size))
+    n_del = size - n_ins
+    batches = [(dels[k * n_del:(k + 1) * n_del], ins[k * n_ins:(k + 1) * n_ins]) for k in range(nb)]
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.time()
+    h = L.Leiden(g.n, g.off, g.col, g.w, cuda_stream=stream.cuda_stream)
+    rep["create_s"] = time.time() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    L.leiden_static(h.h, None)
+    e1.record(stream)
+    e1.synchronize()
+    rep["static_ms"] = e0.elapsed_time(e1)
+    # sampled rows: touched vertices and their rows in G^0
+    touched = np.unique(np.concatenate([dels[:, 0], dels[:, 1], ins[:, 0], ins[:, 1]]))
+    rng = np.random.default_rng(seed)
+    sample = rng.choice(touched, min(2000, len(touched)), replace=False)
+    rows0 = {int(v): dict(zip(g.col[g.off[v]:g.off[v + 1]].tolist(), g.w[g.off[v]:g.off[v + 1]].tolist()))
+             for v in sample}
+    del g
+    gc.collect()
+    ms = []
+    d_out = torch.empty(rep["n"], dtype=torch.int32, device=dev)
+    for d, i in batches:
+        dd, di = torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        L.leiden_update_device(h.h, dd, d.shape[0], di, i.shape[0], L.LEIDEN_DF, d_out)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    rep.update(batch_edges=size, df_ms_mean=float(np.mean(ms)), df_ms_p99=float(np.percentile(ms, 99)),
+               df_edges_per_s=size / (np.mean(ms) / 1e3))
+    q_df = h.modularity()
+    st = h.state()
+    off, col, w = h.graph()
+    h.close()
+    gc.collect()
+    checks = {}
+    # K, Sigma, 2m against the final graph
+    K = np.add.reduceat(np.append(w, 0), off[:-1])  # rows sums; the pad keeps every start in range
+    K[np.diff(off) == 0] = 0
+    checks["K"] = bool(np.array_equal(K, st["K"]))
+    checks["m2"] = bool(int(K.sum()) == st["m2"])
+    checks["Sigma"] = bool(np.array_equal(np.bincount(st["C"], K.astype(np.float64), rep["n"]).astype(np.int64),
+                                          st["Sigma"]))  # sums below 2^53: exact in float64
+    # applied rows of sampled touched vertices
+    for d, i in batches:
+        for (u, v, wt) in d.tolist():
+            for a, b in ((u, v), (v, u)):
+                if a in rows0:
+                    rows0[a].pop(b, None)
+        for (u, v, wt) in i.tolist():
+            for a, b in ((u, v), (v, u)):
+                if a in rows0:
+                    rows0[a][b] = rows0[a].get(b, 0) + wt
+    ok = True
+    for v, row in rows0.items():
+        got = dict(zip(col[off[v]:off[v + 1]].tolist(), w[off[v]:off[v + 1]].tolist()))
+        ok = ok and got == row
+    checks["sampled_rows"] = ok
+    checks["sampled_rows_count"] = len(rows0)
+    # connected communities (components of every community by the oracle's BFS)
+    labels = oracle.split(off, col, st["C"], np.ones(rep["n"], np.uint8))
+    checks["communities"] = int(len(np.unique(st["C"])))
+    checks["connected"] = bool(len(np.unique(labels)) == checks["communities"])
+    # Eq. 1 by the oracle on the same membership
+    q_or, _ = oracle.modularity(off, col, w, st["C"])
+    checks["modularity_equal"] = bool(q_or == q_df)
+    # GPU static Leiden on the final graph
+    del labels, K
+    gc.collect()
+    s = L.Leiden(rep["n"], off, col, w.astype(np.int32), cuda_stream=stream.cuda_stream)
+    del off, col, w
+    gc.collect()
+    e0.record(stream)
+    L.leiden_static(s.h, None)
+    e1.record(stream)
+    e1.synchronize()
+    rep["static_final_ms"] = e0.elapsed_time(e1)
+    q_static = s.modularity()
+    s.close()
+    rep.update(q_df=q_df, q_static=q_static, dq=q_static - q_df)
+    checks["quality"] = bool(q_static - q_df <= 0.005)
+    rep["speedup_vs_static"] = rep["static_final_ms"] / rep["df_ms_mean"]
+    rep["checks"] = checks
+    rep["all_ok"] = all(v for k, v in checks.items() if isinstance(v, bool))
+    line = {"metric": "DF updates on the large web-like graph, checked at full size", "impl": "large",
+            "data": "synthetic", "dtype": "int64",
+            "config": {"workload": f"degree-corrected planted partition, n={rep['n']}, |E|={rep['edges']}, "
+                                   f"20 DF batches of {size} edges (1e-4|E|, 80/20, weights 1..8)"},
+            "result": rep}
+    print(json.dumps(line), flush=True)
+    return 0 if rep["all_ok"] else 1
+
+
 # ----------------------------------------------------------------------------- ablations
 def run_ablation(args):
     """The same DF update stream (R-MAT, 1e-3|E| batches) under each switch:
@@ -690,6 +820,8 @@ def main():
         return run_stability(args) if rank == 0 else 0
     if args.ablation:
         return run_ablation(args) if rank == 0 else 0
+    if args.large:
+        return run_large(args) if rank == 0 else 0
     r = run_ours(args, rank, world, local_rank)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -9,6 +9,7 @@
 #include "internal.h"
 
 #include <atomic>
+#include <thread>
 
 static std::atomic<int64_t> g_launches{0};
 
@@ -78,6 +79,16 @@ void kt_resolve(leiden_handle *h) {
 namespace {
 
 thread_local std::string g_create_error;
+
+// fn(lo, hi) over [0, n) split across the host's threads (small n: one call).
+template <typename F>
+void host_parallel(int64_t n, F fn) {
+  int nt = (int)std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+  if (n < (1 << 16) || nt == 1) { fn(0, n); return; }
+  std::vector<std::thread> ts;
+  for (int t = 0; t < nt; t++) ts.emplace_back([&, t] { fn(n * t / nt, n * (t + 1) / nt); });
+  for (auto &th : ts) th.join();
+}
 
 // int128 -> double in a fixed order (|x| = hi*2^64 + lo, then the sign).
 double i128_to_double(i128 x) {
@@ -524,40 +535,48 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   }
   int64_t cap = cap_off[n];
   std::vector<int32_t> hcol((size_t)std::max<int64_t>(cap, 1), 0), hw((size_t)std::max<int64_t>(cap, 1), 0);
-  std::vector<std::pair<int32_t, int32_t>> row;
   int32_t maxdeg = 0;
-  for (int64_t i = 0; i < n; i++) {
-    row.clear();
-    for (int64_t a = offsets[i]; a < offsets[i + 1]; a++) {
-      int32_t j = cols[a];
-      int32_t w = weights ? weights[a] : 1;
-      if (j < 0 || j >= n || j == i || w <= 0) {
-        g_create_error = "column out of range, self-loop or weight <= 0";
-        return LEIDEN_ERR_ARG;
+  for (int64_t i = 0; i < n; i++) maxdeg = std::max<int32_t>(maxdeg, deg[i]);
+  // rows canonicalised (sorted by neighbour) and checked on all host threads
+  std::atomic<int> bad{0};  // 1 range/self-loop/weight, 2 repeated arc, 3 not symmetric
+  host_parallel(n, [&](int64_t lo, int64_t hi) {
+    std::vector<std::pair<int32_t, int32_t>> row;
+    for (int64_t i = lo; i < hi && !bad.load(std::memory_order_relaxed); i++) {
+      row.clear();
+      bool sorted = true;
+      for (int64_t a = offsets[i]; a < offsets[i + 1]; a++) {
+        int32_t j = cols[a];
+        int32_t w = weights ? weights[a] : 1;
+        if (j < 0 || j >= n || j == i || w <= 0) { bad = 1; return; }
+        if (!row.empty() && j <= row.back().first) sorted = false;
+        row.emplace_back(j, w);
       }
-      row.emplace_back(j, w);
+      if (!sorted) std::sort(row.begin(), row.end());
+      for (size_t k = 1; k < row.size(); k++)
+        if (row[k].first == row[k - 1].first) { bad = 2; return; }
+      for (size_t k = 0; k < row.size(); k++) {
+        hcol[cap_off[i] + k] = row[k].first;
+        hw[cap_off[i] + k] = row[k].second;
+      }
     }
-    std::sort(row.begin(), row.end());
-    for (size_t k = 1; k < row.size(); k++)
-      if (row[k].first == row[k - 1].first) { g_create_error = "repeated arc"; return LEIDEN_ERR_ARG; }
-    for (size_t k = 0; k < row.size(); k++) {
-      hcol[cap_off[i] + k] = row[k].first;
-      hw[cap_off[i] + k] = row[k].second;
-    }
-    maxdeg = std::max<int32_t>(maxdeg, deg[i]);
-  }
+  });
   // symmetry: every arc (i, j, w) must have (j, i, w)
-  for (int64_t i = 0; i < n; i++) {
-    for (int64_t k = 0; k < deg[i]; k++) {
-      int32_t j = hcol[cap_off[i] + k];
-      const int32_t *rb = hcol.data() + cap_off[j];
-      const int32_t *re = rb + deg[j];
-      const int32_t *it = std::lower_bound(rb, re, (int32_t)i);
-      if (it == re || *it != i || hw[cap_off[j] + (it - rb)] != hw[cap_off[i] + k]) {
-        g_create_error = "graph is not symmetric";
-        return LEIDEN_ERR_ARG;
+  if (!bad)
+    host_parallel(n, [&](int64_t lo, int64_t hi) {
+      for (int64_t i = lo; i < hi && !bad.load(std::memory_order_relaxed); i++) {
+        for (int64_t k = 0; k < deg[i]; k++) {
+          int32_t j = hcol[cap_off[i] + k];
+          const int32_t *rb = hcol.data() + cap_off[j];
+          const int32_t *re = rb + deg[j];
+          const int32_t *it = std::lower_bound(rb, re, (int32_t)i);
+          if (it == re || *it != i || hw[cap_off[j] + (it - rb)] != hw[cap_off[i] + k]) { bad = 3; return; }
+        }
       }
-    }
+    });
+  if (bad) {
+    g_create_error = bad == 1 ? "column out of range, self-loop or weight <= 0"
+                     : bad == 2 ? "repeated arc" : "graph is not symmetric";
+    return LEIDEN_ERR_ARG;
   }
   leiden_handle *h = new leiden_handle();
   h->p = p;

@@ -48,6 +48,8 @@ def _load():
         lib.synth_planted_partition.restype = ctypes.c_int
         lib.synth_rmat.argtypes = [ctypes.c_int, i64, dbl, dbl, dbl, u64] + out_args
         lib.synth_rmat.restype = ctypes.c_int
+        lib.synth_dcpp.argtypes = [i64, dbl, dbl, dbl, dbl, i64, i64, dbl, i32, u64] + out_args
+        lib.synth_dcpp.restype = ctypes.c_int
         lib.synth_batch.argtypes = [i64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, i64, i64,
                                     i32, i32, u64, ctypes.c_void_p, ctypes.c_void_p]
         lib.synth_batch.restype = ctypes.c_int
@@ -109,6 +111,16 @@ def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c:
     """R-MAT graph, symmetrised and deduplicated, vertex IDs randomly permuted, unit weights."""
     lib = _load()
     return _csr_call(lib.synth_rmat, 1 << scale, scale, edge_factor, float(a), float(b), float(c), seed)
+
+
+def dcpp(n: int, avg_deg: float = 66.7, deg_exp: float = 2.1, max_deg: float = 1e6, comm_exp: float = 1.5,
+         cmin: int = 10, cmax: int = 100000, mu: float = 0.3, wmax: int = 8, seed: int = BASE_SEED + 2) -> Graph:
+    """Degree-corrected planted partition: power-law expected degrees (exponent
+    deg_exp, bounded by max_deg, mean avg_deg), power-law community sizes
+    (exponent comm_exp in [cmin, cmax]), mixing mu, weights 1..wmax."""
+    lib = _load()
+    return _csr_call(lib.synth_dcpp, n, n, float(avg_deg), float(deg_exp), float(max_deg), float(comm_exp),
+                     int(cmin), int(cmax), float(mu), int(wmax), seed)
 
 
 def random_batch(g: Graph, n_edges: int, seed: int, frac_ins: float = 0.8,

@@ -317,6 +317,140 @@ int synth_rmat(int scale, int64_t edge_factor, double a, double b, double c, uin
   return rc;
 }
 
+/* ------------------------------------ degree-corrected planted partition */
+
+/* Expected value of min(X, cap) for X Pareto with shape a > 1 and scale xm
+ * (density a xm^a / x^(a+1), x >= xm). */
+static double pareto_capped_mean(double a, double xm, double cap) {
+  if (cap <= xm) return cap;
+  double t = pow(xm / cap, a);
+  return xm * a / (a - 1.0) * (1.0 - pow(xm / cap, a - 1.0)) + cap * t;
+}
+
+/* Inverse-CDF draw from a Pareto(shape a, scale xm) bounded to [xm, cap]
+ * (the tail above cap folded onto cap). */
+static double pareto_draw(double a, double xm, double cap, uint64_t r) {
+  double u = ((double)(r >> 11) + 0.5) * (1.0 / 9007199254740992.0); /* (0, 1) */
+  double x = xm * pow(u, -1.0 / a);
+  return x < cap ? x : cap;
+}
+
+typedef struct {
+  int64_t n;
+  uint64_t seed;
+  double mu;
+  const int64_t *deg, *cstart, *comm, *perm;
+  const double *gcdf, *ccdf; /* cumulative degree: global, and inside each community */
+  const int64_t *eoff;       /* first edge index of each vertex */
+  int64_t *u, *v;
+} dcpp_ctx;
+
+static int64_t cdf_pick(const double *cdf, int64_t lo, int64_t hi, double x) {
+  /* smallest i in [lo, hi) with cdf[i] > x */
+  while (lo < hi - 1) {
+    int64_t mid = (lo + hi) >> 1;
+    if (cdf[mid - 1] > x) hi = mid; else lo = mid;
+  }
+  return lo;
+}
+
+static void dcpp_work(void *p, int tid, int nt) {
+  dcpp_ctx *c = (dcpp_ctx *)p;
+  int64_t lo, hi;
+  span(c->n, tid, nt, &lo, &hi);
+  for (int64_t x = lo; x < hi; x++) {
+    int64_t k = c->comm[x], a = c->cstart[k], b = c->cstart[k + 1];
+    double cbase = a > 0 ? c->ccdf[a - 1] : 0.0, ctot = c->ccdf[b - 1] - cbase;
+    double gtot = c->gcdf[c->n - 1];
+    for (int64_t e = c->eoff[x]; e < c->eoff[x + 1]; e++) {
+      uint64_t r1 = rng_u64(c->seed, 21, 2 * (uint64_t)e), r2 = rng_u64(c->seed, 21, 2 * (uint64_t)e + 1);
+      double coin = ((double)(r1 >> 11)) * (1.0 / 9007199254740992.0);
+      double pick = ((double)(r2 >> 11)) * (1.0 / 9007199254740992.0);
+      int64_t y;
+      if (coin >= c->mu && b - a > 1) y = cdf_pick(c->ccdf, a, b, cbase + pick * ctot);
+      else y = cdf_pick(c->gcdf, 0, c->n, pick * gtot);
+      c->u[e] = c->perm[x];
+      c->v[e] = c->perm[y];
+    }
+  }
+}
+
+/* Degree-corrected planted partition: expected degrees from a Pareto law of
+ * exponent deg_exp (density ~ d^-deg_exp) bounded by max_deg, its scale set
+ * so the mean is avg_deg; community sizes from a Pareto law of exponent
+ * comm_exp bounded to [cmin, cmax], filled in order; each vertex x draws
+ * ceil(d_x/2) edges whose other end is, with probability 1-mu, a member of
+ * x's community and otherwise any vertex, chosen in proportion to expected
+ * degree (Chung-Lu style).  Vertex ids are then randomly permuted.  Weights
+ * are 1..wmax from a hash of the unordered pair, so both directions agree;
+ * repeated pairs collapse and self-pairs are dropped. */
+int synth_dcpp(int64_t n, double avg_deg, double deg_exp, double max_deg, double comm_exp, int64_t cmin,
+               int64_t cmax, double mu, int32_t wmax, uint64_t seed, int64_t **off, int32_t **col, int32_t **w,
+               int64_t *arcs) {
+  if (n < 2 || deg_exp <= 2.0 || comm_exp <= 1.0 || cmin < 1 || cmax < cmin || wmax < 1) return -1;
+  double a = deg_exp - 1.0, lo = 1e-3, hi = avg_deg;
+  for (int it = 0; it < 200; it++) { /* scale of the degree law for the requested mean */
+    double mid = 0.5 * (lo + hi);
+    if (pareto_capped_mean(a, mid, max_deg) < avg_deg) lo = mid; else hi = mid;
+  }
+  double xm = 0.5 * (lo + hi);
+  int64_t *deg = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  int64_t *comm = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  int64_t *cstart = (int64_t *)malloc((size_t)(n + 2) * sizeof(int64_t));
+  int64_t *perm = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+  int64_t *eoff = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+  double *gcdf = (double *)malloc((size_t)n * sizeof(double));
+  double *ccdf = (double *)malloc((size_t)n * sizeof(double));
+  if (!deg || !comm || !cstart || !perm || !eoff || !gcdf || !ccdf) {
+    free(deg); free(comm); free(cstart); free(perm); free(eoff); free(gcdf); free(ccdf);
+    return -1;
+  }
+  int64_t nc = 0, pos = 0;
+  for (uint64_t t = 0; pos < n; t++) {
+    int64_t sz = (int64_t)pareto_draw(comm_exp - 1.0, (double)cmin, (double)cmax, rng_u64(seed, 22, t));
+    if (sz < cmin) sz = cmin;
+    if (pos + sz > n) sz = n - pos;
+    cstart[nc++] = pos;
+    for (int64_t x = pos; x < pos + sz; x++) comm[x] = nc - 1;
+    pos += sz;
+  }
+  cstart[nc] = n;
+  eoff[0] = 0;
+  for (int64_t x = 0; x < n; x++) {
+    double d = pareto_draw(a, xm, max_deg, rng_u64(seed, 23, (uint64_t)x));
+    deg[x] = (int64_t)llround(d) < 1 ? 1 : (int64_t)llround(d);
+    gcdf[x] = (x ? gcdf[x - 1] : 0.0) + (double)deg[x];
+    ccdf[x] = gcdf[x];
+    eoff[x + 1] = eoff[x] + (deg[x] + 1) / 2;
+  }
+  for (int64_t i = 0; i < n; i++) perm[i] = i;
+  for (int64_t i = n - 1; i > 0; i--) {
+    int64_t j = (int64_t)rng_below(seed, 24, (uint64_t)i, (uint64_t)(i + 1));
+    int64_t t = perm[i]; perm[i] = perm[j]; perm[j] = t;
+  }
+  int64_t m = eoff[n];
+  int64_t *u = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+  int64_t *v = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+  int rc = -1;
+  if (u && v) {
+    dcpp_ctx c = {n, seed, mu, deg, cstart, comm, perm, gcdf, ccdf, eoff, u, v};
+    parallel_run(dcpp_work, &c);
+    rc = build_csr_from_pairs(n, u, v, m, off, col, w, arcs);
+  }
+  free(u); free(v);
+  free(deg); free(comm); free(cstart); free(perm); free(eoff); free(gcdf); free(ccdf);
+  if (rc == 0) { /* weights from the unordered pair */
+    int64_t nn = n;
+    for (int64_t x = 0; x < nn; x++)
+      for (int64_t e = (*off)[x]; e < (*off)[x + 1]; e++) {
+        int64_t y = (*col)[e];
+        uint64_t key = x < y ? ((uint64_t)x << 32) | (uint64_t)y : ((uint64_t)y << 32) | (uint64_t)x;
+        (*w)[e] = 1 + (int32_t)(mix64(key ^ (seed * 0x9E3779B97F4A7C15ULL)) % (uint64_t)wmax);
+      }
+  }
+  return rc;
+}
+
 /* ---------------------------------------------------------- batch updates */
 
 static int has_edge(const int64_t *off, const int32_t *col, int64_t u, int64_t v) {

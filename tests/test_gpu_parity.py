@@ -57,6 +57,8 @@ GRAPHS = {
     "rmat14": lambda: synth.rmat(14, seed=32),
     "hubs": lambda: hub_graph(),
     "weighted": lambda: _weighted(synth.planted_partition(3000, 15, 12, 0.3, 41)),
+    # degree-corrected planted partition: power-law degrees and community sizes, weights 1..8
+    "dcpp": lambda: synth.dcpp(20000, avg_deg=30, max_deg=3000, cmax=3000, seed=42),
 }
 
 
@@ -96,7 +98,7 @@ def test_static_bit_exact(name):
     assert disconnected_communities(g.off, g.col, cg) == 0
 
 
-@pytest.mark.parametrize("name", ["planted10k", "rmat14", "hubs", "weighted"])
+@pytest.mark.parametrize("name", ["planted10k", "rmat14", "hubs", "weighted", "dcpp"])
 @pytest.mark.parametrize("mode", MODES, ids=["ND", "DS", "DF"])
 def test_updates_bit_exact(name, mode):
     gm, om = mode
@@ -107,7 +109,7 @@ def test_updates_bit_exact(name, mode):
     ref.static()
     cur = g
     for k, size in enumerate([7, 150, 1200]):
-        dels, ins = synth.random_batch(cur, size, seed=500 + k, w_lo=1, w_hi=3 if name == "weighted" else 1)
+        dels, ins = synth.random_batch(cur, size, seed=500 + k, w_lo=1, w_hi=8 if name in ("weighted", "dcpp") else 1)
         cg = gpu.update(dels, ins, gm)
         cr = ref.update(dels, ins, om)
         cur = synth.apply_batch_numpy(cur, dels, ins)

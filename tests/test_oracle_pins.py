@@ -460,3 +460,17 @@ def test_converge_any_stops_no_later_than_the_printed_test():
         ta, tb = a.trace(), b.trace()
         assert len(tb["passes"]) <= len(ta["passes"])
         assert ta["passes"][0] == tb["passes"][0]
+
+
+def test_dcpp_generator_shape():
+    """The degree-corrected planted-partition input: symmetric, weights 1..8
+    from the unordered pair, a heavy degree tail, seeded bytes."""
+    g = synth.dcpp(30000, avg_deg=40, max_deg=5000, cmax=5000, seed=7)
+    d = np.diff(g.off)
+    src = np.repeat(np.arange(g.n), d)
+    fwd = dict(zip(zip(src.tolist(), g.col.tolist()), g.w.tolist()))
+    assert all(fwd[(v, u)] == w for (u, v), w in list(fwd.items())[:20000])
+    assert g.w.min() >= 1 and g.w.max() <= 8
+    assert d.max() > 20 * d.mean()
+    h = synth.dcpp(30000, avg_deg=40, max_deg=5000, cmax=5000, seed=7)
+    assert np.array_equal(g.col, h.col) and np.array_equal(g.w, h.w)
