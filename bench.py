@@ -515,7 +515,7 @@ def run_large(args):
     seed = synth.BASE_SEED + 2
     rep = {}
     t0 = time.time()
-    g = synth.dcpp(args.large_n, avg_deg=84.0, deg_exp=2.1, max_deg=1e6, comm_exp=1.5, cmin=10, cmax=100000,
+    g = synth.dcpp(args.large_n, avg_deg=93.0, deg_exp=2.1, max_deg=1e6, comm_exp=1.5, cmin=10, cmax=100000,
                    mu=0.3, wmax=8, seed=seed)
     rep["gen_s"] = time.time() - t0
     E = g.edges
