@@ -249,7 +249,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
       CK(cudaMemcpyAsync(h->gc.lm_on, hg.lm_on, (size_t)G, cudaMemcpyHostToDevice, s));
     }
     mark(h, 2);
-    lm_prepare(h, g);
+    lm_prepare(h, g, lp > 0 || !dynamic ? SIZES_ONES : SIZES_KEPT);
     int li = p.max_iterations;
     for (int it = 0; it < p.max_iterations; it++) {
       CK(cudaMemsetAsync(&h->dcnt->dq[0], 0, 2 * sizeof(unsigned long long), s));
@@ -605,7 +605,7 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   A(dalloc(h, &h->Sig, n));
   A(dalloc(h, &h->dSig, n));
   A(dalloc(h, &h->dV, n));
-  int32_t **i32s[] = {&h->Cp, &h->CB, &h->Ctop, &h->csize, &h->rep, &h->prop, &h->parent,
+  int32_t **i32s[] = {&h->Cp, &h->CB, &h->Ctop, &h->csize, &h->csize0, &h->rep, &h->prop, &h->parent,
                       &h->ibuf0, &h->ibuf1, &h->ibuf2, &h->movers, &h->mtarget, &h->cverts};
   for (auto pp : i32s) A(dalloc(h, pp, n + 1));
   int64_t **i64s[] = {&h->Kp, &h->Sp, &h->S2, &h->lbuf0, &h->lbuf1, &h->lbuf2, &h->lbuf3, &h->coff, &h->cflat};
@@ -749,7 +749,7 @@ int64_t leiden_footprint_bytes(const leiden_params *params, int64_t n, const int
   int64_t b = 0;
   b += 8 * (n + 1) + 8 * n + 8 * total;                              // G^t: off, deg, rcap, col, w
   b += 4 * n + 24 * n + n;                                            // C, K, Sigma, dSigma, dV
-  b += 52 * (n + 1) + 72 * (n + 2) + 6 * (n + 1);                     // per-pass work arrays
+  b += 56 * (n + 1) + 72 * (n + 2) + 6 * (n + 1);                     // per-pass work arrays
   b += 4 * (n / 32 + 2) + 16 * n + 4 * (n + 1) + 8 * n;               // frontier, bins, hocc, cand
   b += 2 * (8 * (n + 2) + 4 * (n + 1) + 12 * total);                  // aggregated levels
   b += 16 * tc + 4 * n + (int64_t)scan_tmp_bytes(2 * n + 2);          // tracking, scans
@@ -941,6 +941,7 @@ leiden_status leiden_import_state(leiden_handle *h, const int32_t *C, const int6
   CK(cudaMemcpyAsync(h->dSig, dSigma, (size_t)N * sizeof(int64_t), cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));  // the host arrays may be freed on return
   recompute_sigma(h);
+  count_sizes(h, h->C, N, h->csize0);
   sync_all(h);
   CK(cudaGetLastError());
   h->m2 = h->hcnt->m2;

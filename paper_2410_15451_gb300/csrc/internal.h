@@ -101,6 +101,7 @@ struct leiden_handle {
 
   // per-vertex work arrays (length n or n+1)
   int32_t *Cp = nullptr, *CB = nullptr, *Ctop = nullptr, *csize = nullptr, *rep = nullptr;
+  int32_t *csize0 = nullptr;  // [n] member counts of C^t (kept by tracking for the next call)
   int32_t *prop = nullptr, *parent = nullptr, *ibuf0 = nullptr, *ibuf1 = nullptr, *ibuf2 = nullptr;
   int64_t *Kp = nullptr, *Sp = nullptr, *S2 = nullptr, *lbuf0 = nullptr, *lbuf1 = nullptr;
   int64_t *lbuf2 = nullptr, *lbuf3 = nullptr;
@@ -232,7 +233,11 @@ void lm_subsweep(leiden_handle *h, const LevelGraph &g, int cls, const uint8_t *
 // Refinement: reset, then one round (SYNC) or one sweep (async) of moves.
 void refine_reset(leiden_handle *h, const LevelGraph &g);
 void refine_round(leiden_handle *h, const LevelGraph &g, int slot);
-void lm_prepare(leiden_handle *h, const LevelGraph &g);  // community sizes
+// Community sizes of C' for the singleton rule: all ones (C' the identity),
+// the sizes kept by the last tracking (C' = C^{t-1}), or counted.
+enum { SIZES_ONES = 0, SIZES_KEPT = 1, SIZES_COUNT = 2 };
+void lm_prepare(leiden_handle *h, const LevelGraph &g, int sizes_from);
+void count_sizes(leiden_handle *h, const int32_t *C, int64_t n, int32_t *size);
 bool ensure_hslots(leiden_handle *h, int64_t slots);     // false: allocation failed
 int32_t *hs_keys(leiden_handle *h);  // global table scratch: keys, values, slot lists
 int64_t *hs_vals(leiden_handle *h);

@@ -952,9 +952,20 @@ int32_t *hs_keys(leiden_handle *h) { return (int32_t *)h->hscratch; }
 int64_t *hs_vals(leiden_handle *h) { return (int64_t *)((char *)h->hscratch + (size_t)h->hslots * 4); }
 int32_t *hs_list(leiden_handle *h) { return (int32_t *)((char *)h->hscratch + (size_t)h->hslots * 12); }
 
-void lm_prepare(leiden_handle *h, const LevelGraph &g) {
-  cudaMemsetAsync(h->csize, 0, (size_t)g.n * sizeof(int32_t), h->stream);
-  ld_note_launch(), k_sizes<<<grid_for(g.n, 256), 256, 0, h->stream>>>(h->Cp, g.n, h->csize);
+void lm_prepare(leiden_handle *h, const LevelGraph &g, int sizes_from) {
+  if (sizes_from == SIZES_ONES) {  // C' is the identity: every community is one vertex
+    launch_fill_i32(h->csize, 1, g.n, h->stream);
+  } else if (sizes_from == SIZES_KEPT) {  // C' = C^{t-1}: sizes kept by the last tracking
+    cudaMemcpyAsync(h->csize, h->csize0, (size_t)g.n * sizeof(int32_t), cudaMemcpyDeviceToDevice, h->stream);
+  } else {
+    cudaMemsetAsync(h->csize, 0, (size_t)g.n * sizeof(int32_t), h->stream);
+    ld_note_launch(), k_sizes<<<grid_for(g.n, 256), 256, 0, h->stream>>>(h->Cp, g.n, h->csize);
+  }
+}
+
+void count_sizes(leiden_handle *h, const int32_t *C, int64_t n, int32_t *size) {
+  cudaMemsetAsync(size, 0, (size_t)n * sizeof(int32_t), h->stream);
+  ld_note_launch(), k_sizes<<<grid_for(n, 256), 256, 0, h->stream>>>(C, n, size);
 }
 
 void lm_subsweep(leiden_handle *h, const LevelGraph &g, int cls, const uint8_t *in_range, int dynamic) {

@@ -102,7 +102,7 @@ cudaError_t scan_impl(const T *in, int64_t *out, int64_t n, void *tmp, cudaStrea
 
 // ---------------------------------------------------------------- radix sort
 constexpr int RS_BLOCK = 256;
-constexpr int RS_ROUNDS = 16;
+constexpr int RS_ROUNDS = 4;  // short tiles: a batch of 1e5 keys still spreads over ~100 blocks
 constexpr int RS_TILE = RS_BLOCK * RS_ROUNDS;
 
 __global__ void rs_hist(const uint64_t *keys, int64_t n, int shift, int64_t nblocks, int64_t *hist) {

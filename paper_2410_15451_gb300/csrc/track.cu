@@ -158,7 +158,7 @@ __global__ void k_tr_map(int64_t N, const int32_t *new_used, const int32_t *ob, 
   }
 }
 __global__ void k_tr_relabel(int64_t N, const int32_t *Cnew, const int32_t *map, const int64_t *K, int32_t *C,
-                             int64_t *Sig) {
+                             int64_t *Sig, int32_t *size) {
   int lane = threadIdx.x & 31;
   for (int64_t base = (ld_gtid() & ~31ll); base < N; base += ld_gstride()) {
     int64_t i = base + lane;
@@ -167,7 +167,10 @@ __global__ void k_tr_relabel(int64_t N, const int32_t *Cnew, const int32_t *map,
     if (i < N) { c = map[Cnew[i]]; C[i] = c; k = K[i]; }
     uint32_t peers = __match_any_sync(LD_FULL, c);
     int64_t s = ld_group_sum_i64(peers, k);
-    if (i < N && ld_group_leader(peers) && s) atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)s);
+    if (i < N && ld_group_leader(peers)) {
+      if (s) atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)s);
+      atomicAdd(&size[c], __popc(peers));  // member counts of C^t, for the next call
+    }
   }
 }
 __global__ void k_tr_dsig(int64_t N, const uint8_t *matched, int64_t *dSig) {
@@ -279,7 +282,8 @@ void track_communities(leiden_handle *h) {
   cudaMemsetAsync(matched, 0, (size_t)N, s);
   ld_note_launch(), k_tr_map<<<gN, TB, 0, s>>>(N, used, ob, urank, frank, flist, map, matched, h->gid0, h->d_voff);
   cudaMemsetAsync(h->Sig, 0, (size_t)N * sizeof(int64_t), s);
-  ld_note_launch(), k_tr_relabel<<<gN, TB, 0, s>>>(N, h->Ctop, map, h->K, h->C, h->Sig);
+  cudaMemsetAsync(h->csize0, 0, (size_t)N * sizeof(int32_t), s);
+  ld_note_launch(), k_tr_relabel<<<gN, TB, 0, s>>>(N, h->Ctop, map, h->K, h->C, h->Sig, h->csize0);
   ld_note_launch(), k_tr_dsig<<<gN, TB, 0, s>>>(N, matched, h->dSig);
 }
 
