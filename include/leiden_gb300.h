@@ -59,6 +59,7 @@ typedef struct {
                           /* 0: moves applied in place as vertices decide (the paper's    */
                           /*    asynchronous style; results may vary between runs)        */
   int32_t classes;        /* sub-sweeps per local-moving iteration, power of two, 4       */
+                          /*    (the in-place schedule uses at least 16)                  */
   double slack;           /* spare CSR capacity per row as a fraction of its degree, 0.25 */
   int32_t min_slack;      /* minimum spare arcs per row, 4                                */
   int32_t collect_stats;  /* bit 1: time each phase with CUDA events (adds syncs);        */

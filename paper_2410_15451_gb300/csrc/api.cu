@@ -258,7 +258,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
         CK(cudaMemsetAsync(h->gc.dq, 0, (size_t)G * 2 * sizeof(unsigned long long), s));
         CK(cudaMemsetAsync(h->gc.moves, 0, (size_t)G * sizeof(int64_t), s));
       }
-      for (int cls = 0; cls < p.classes; cls++) lm_subsweep(h, g, cls, lp == 0 ? in_range : nullptr, dynamic);
+      for (int cls = 0; cls < lm_classes(h); cls++) lm_subsweep(h, g, cls, lp == 0 ? in_range : nullptr, dynamic);
       sync_all(h);
       kt_resolve(h);
       CK(cudaGetLastError());

@@ -11,6 +11,7 @@ namespace {
 constexpr int TB = 256;
 constexpr int MERGE_SMALL = 256;  // touched rows up to this new length merge in one warp (8 KB of
                                   // shared staging per block keeps many rows in flight)
+constexpr int MERGE_MID = 4096;   // up to this length: one block, staged in shared memory, in place
 
 __device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, int32_t x) {
   int64_t lo = 0, hi = n;
@@ -129,7 +130,7 @@ __global__ void k_row_plan(const int32_t *rows, const int64_t *nrows_p, int vb, 
                            const uint64_t *nkey, const int64_t *nn_p, const int64_t *off, const int32_t *deg,
                            const int32_t *rcap, int32_t *dlo, int32_t *dhi, int32_t *ilo, int32_t *ihi, int64_t *len,
                            int64_t *dst, int32_t *newcap, double slack, int min_slack, int64_t colcap,
-                           int32_t *olddeg, int32_t *large, DevCounters *cnt) {
+                           int32_t *olddeg, int32_t *large, int32_t *mid, DevCounters *cnt) {
   int64_t nrows = *nrows_p, nn = *nn_p;
   for (int64_t r = ld_gtid(); r < nrows; r += ld_gstride()) {
     uint64_t u = (uint64_t)rows[r];
@@ -139,7 +140,8 @@ __global__ void k_row_plan(const int32_t *rows, const int64_t *nrows_p, int vb, 
     int64_t L = (int64_t)deg[u] - (b - a) + (d - c);
     len[r] = L;
     olddeg[r] = deg[u];
-    if (L > MERGE_SMALL) large[atomicAdd(&cnt->large_count, 1)] = (int32_t)r;
+    if (L > MERGE_MID) large[atomicAdd(&cnt->large_count, 1)] = (int32_t)r;
+    else if (L > MERGE_SMALL) mid[atomicAdd(&cnt->mid_count, 1)] = (int32_t)r;
     dst[r] = off[u];
     newcap[r] = 0;
     if (L > rcap[u]) {
@@ -278,6 +280,25 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge_small(MergeArgs A) {
     for (int64_t x = lane; x < L; x += 32) { A.col[o + x] = scol[wid][x]; A.w[o + x] = sw[wid][x]; }
     if (lane == 0) finish_row(A, r, u, L);
     __syncwarp();
+  }
+}
+
+// Rows of MERGE_SMALL..MERGE_MID arcs: one block each, staged in shared
+// memory and written back after all of the row's reads.
+__global__ void __launch_bounds__(256) k_merge_mid(MergeArgs A, const int32_t *mid, const int32_t *count_p) {
+  __shared__ int32_t scol[MERGE_MID];
+  __shared__ int32_t sw[MERGE_MID];
+  int64_t count = *count_p;
+  for (int64_t k = blockIdx.x; k < count; k += gridDim.x) {
+    int64_t r = mid[k];
+    int64_t L = A.len[r];
+    merge_row_into(A, r, threadIdx.x, blockDim.x, scol, sw, A.dkey + A.dlo[r], A.nkey + A.ilo[r]);
+    __syncthreads();
+    int32_t u = A.rows[r];
+    int64_t o = A.dst[r];
+    for (int64_t x = threadIdx.x; x < L; x += blockDim.x) { A.col[o + x] = scol[x]; A.w[o + x] = sw[x]; }
+    if (threadIdx.x == 0) finish_row(A, r, u, L);
+    __syncthreads();
   }
 }
 
@@ -554,7 +575,7 @@ cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
   void *old[] = {b.dkey, b.dkey_alt, b.ikey, b.ikey_alt, b.iw, b.iw_alt, b.dw, b.flag,
                  b.pos, b.ins_state, b.ins_pos, b.row_dlo, b.row_dhi, b.row_ilo, b.row_ihi, b.row_len,
                  b.row_tmp_off, b.rows, b.ds_key, b.ds_key_alt, b.ds_w, b.ds_w_alt, b.ds_ukey, b.ds_uw,
-                 b.row_dst, b.row_newcap, b.row_olddeg, b.row_large};
+                 b.row_dst, b.row_newcap, b.row_olddeg, b.row_large, b.row_mid};
   for (void *p : old) release(h, p);
   int64_t arcs = 2 * cap;
   cudaError_t e = cudaSuccess;
@@ -582,6 +603,7 @@ cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
   chk(grow(h, &b.row_newcap, rows + 1));
   chk(grow(h, &b.row_olddeg, rows + 1));
   chk(grow(h, &b.row_large, rows + 1));
+  chk(grow(h, &b.row_mid, rows + 1));
   chk(grow(h, &b.ds_key, arcs));
   chk(grow(h, &b.ds_key_alt, arcs));
   chk(grow(h, &b.ds_w, arcs));
@@ -691,6 +713,7 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   cudaMemsetAsync(&cnt->error, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&cnt->overflow, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&cnt->large_count, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(&cnt->mid_count, 0, sizeof(int32_t), s);
   if (n_del + n_ins > 0)
     ld_note_launch(), k_expand<<<grid_for(n_del + n_ins, TB), TB, 0, s>>>(d_del, n_del, d_ins, n_ins, n, vb, b.dkey, b.ikey,
                                                                           b.iw, cnt, h->gid0);
@@ -750,7 +773,7 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
     ld_note_launch(), k_row_plan<<<grid_for(std::min<int64_t>(n, nd + nn), TB), TB, 0, s>>>(
         b.rows, counts + 3, vb, DK, nd, NK, counts + 2, h->g_off, h->g_deg, h->g_rcap, b.row_dlo, b.row_dhi,
         b.row_ilo, b.row_ihi, b.row_len, b.row_dst, b.row_newcap, h->p.slack, h->p.min_slack, h->g_cap,
-        b.row_olddeg, b.row_large, cnt);
+        b.row_olddeg, b.row_large, b.row_mid, cnt);
     cudaMemcpyAsync(b.hcounts + 3, counts + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
     nrows = b.hcounts[3];
@@ -771,6 +794,7 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
                   b.row_dst, b.row_newcap, h->g_off, h->g_rcap};
       ld_note_launch(), k_merge_small<<<grid_for((nrows + MERGE_WARPS - 1) / MERGE_WARPS, 1, h->sm_count * 16), MERGE_WARPS * 32, 0,
                       s>>>(M);
+      ld_note_launch(), k_merge_mid<<<h->sm_count * 4, 256, 0, s>>>(M, b.row_mid, &cnt->mid_count);
       // long rows: chunks over the old row, then chunks over the new row
       int32_t *large = b.row_large;
       const int32_t *nlarge = &cnt->large_count;

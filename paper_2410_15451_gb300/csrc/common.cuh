@@ -44,6 +44,7 @@ struct DevCounters {
   int32_t big_count;              // splitting: long rows left to the block kernel
   int32_t large_count;            // batch apply: touched rows merged in chunks
   int32_t tr_occ;                 // tracking: filled slots of the pair table
+  int32_t mid_count;              // batch apply: touched rows merged by one block each
   int64_t arena_used;             // next free arc slot of G^t (relocated rows go here)
 };
 

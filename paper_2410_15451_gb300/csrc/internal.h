@@ -65,6 +65,7 @@ struct BatchBuffers {
   int32_t *row_newcap = nullptr;                         // capacity of a relocated row (0: stays)
   int32_t *row_olddeg = nullptr;                         // degree of the row before the batch
   int32_t *row_large = nullptr;                          // touched rows merged in chunks
+  int32_t *row_mid = nullptr;                            // touched rows merged by one block each
   uint64_t *ds_key = nullptr, *ds_key_alt = nullptr, *ds_ukey = nullptr;  // DS (src, C[dst]) pairs
   int64_t *ds_w = nullptr, *ds_w_alt = nullptr, *ds_uw = nullptr;
   int64_t *counts = nullptr;                             // device counts of the batch pipeline
@@ -226,6 +227,13 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
                                    const leiden_edge *d_ins, int64_t n_ins, int mode);
 // Spare arc slots kept after `used` slots for rows that outgrow their capacity.
 inline int64_t spill_arena_size(int64_t used) { return used / 8 + (int64_t)(1 << 20); }
+
+// Sub-sweeps per local-moving iteration: params.classes in the snapshot
+// schedule; the in-place schedule uses at least 16 (fewer vertices move at
+// once, so fewer decisions act on totals that other moves are changing).
+inline int lm_classes(const leiden_handle *h) {
+  return h->p.deterministic ? h->p.classes : (h->p.classes > 16 ? h->p.classes : 16);
+}
 
 // ------------------------------------------------------------ move.cu
 // One local-moving sub-sweep of class `cls` (0 .. classes-1).

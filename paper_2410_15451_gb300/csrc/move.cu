@@ -871,7 +871,7 @@ Args make_args(leiden_handle *h, const LevelGraph &g) {
     A.refg = h->gc.refined;
   }
   A.async_mode = h->p.deterministic ? 0 : 1;
-  A.classes_mask = h->p.classes - 1;
+  A.classes_mask = lm_classes(h) - 1;
   return A;
 }
 
@@ -972,7 +972,7 @@ void lm_subsweep(leiden_handle *h, const LevelGraph &g, int cls, const uint8_t *
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4 + sizeof(int32_t), s);  // bins + movers
   ld_note_launch(), k_collect<<<grid_for((g.n + 31) / 32, 256), 256, 0, s>>>(
-      g.n, h->unproc, cls, h->p.classes - 1, in_range, g.deg, h->bins, h->dcnt, g.gid, h->gc.lm_on, h->d_loff);
+      g.n, h->unproc, cls, lm_classes(h) - 1, in_range, g.deg, h->bins, h->dcnt, g.gid, h->gc.lm_on, h->d_loff);
   Args A = make_args(h, g);
   A.in_range = in_range;
   A.dynamic = dynamic;

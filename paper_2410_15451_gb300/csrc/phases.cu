@@ -402,6 +402,8 @@ __global__ void __launch_bounds__(256) k_agg_block(AggArgs A) {
 template <typename W>
 __global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t *tab_off, const int64_t *ch_off) {
   __shared__ WarpTable WT[8];  // per-warp sums by community, flushed into the global table
+  __shared__ int64_t longm[TABLE_CHUNK / 256 + 1];  // members with a long segment in the chunk
+  __shared__ int nlong;
   WarpTable &T8 = WT[threadIdx.x >> 5];
   wt_init(T8);
   int64_t count = *A.count;
@@ -421,27 +423,61 @@ __global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t
     int64_t T = tab_off[lo + 1] - tab_off[lo];
     int32_t *keys = A.gkeys + tab_off[lo], *list = A.glist + tab_off[lo];
     int64_t *vals = A.gvals + tab_off[lo];
-    int lane = threadIdx.x & 31;
-    for (int64_t f0w = f0 + (threadIdx.x & ~31); f0w < f1; f0w += blockDim.x) {  // warp-uniform trip count
-      int64_t f = f0w + lane;
-      bool valid = f < f1;
-      int32_t c = 0;
-      int64_t wa = 0;
-      if (valid) {
-        int64_t a = m0, b = m1 - 1;  // member with cflat[a] <= f
-        while (a < b) {
-          int64_t mid = (a + b + 1) >> 1;
-          if (A.cflat[mid] <= f) a = mid; else b = mid - 1;
-        }
-        int32_t v = A.cverts[a];
-        int64_t arc = A.off[v] + (f - A.cflat[a]);
-        c = A.C[A.col[arc]];
-        wa = (int64_t)w[arc];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    // the chunk's first member (one search per chunk), then each warp walks
+    // the members whose arcs meet [f0, f1), a member's arcs at a time
+    int64_t a0 = m0, b0 = m1 - 1;
+    while (a0 < b0) {
+      int64_t mid = (a0 + b0 + 1) >> 1;
+      if (A.cflat[mid] <= f0) a0 = mid; else b0 = mid - 1;
+    }
+    if (threadIdx.x == 0) nlong = 0;
+    __syncthreads();
+    // segments of at most 256 arcs: a warp per member; longer ones: listed
+    // and shared by all the block's warps below
+    for (int64_t a = a0 + wid; a < m1; a += nwarps) {  // warp-uniform
+      int64_t fa = A.cflat[a], fb = A.cflat[a + 1];
+      if (fa >= f1) break;
+      int64_t s0 = fa > f0 ? fa : f0, s1 = fb < f1 ? fb : f1;
+      if (s0 >= s1) continue;
+      if (s1 - s0 > 256) {
+        if (lane == 0) longm[atomicAdd(&nlong, 1)] = a;
+        continue;
       }
-      if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
-      wt_insert_lanes(T8, valid, c, wa);
+      int64_t row = A.off[A.cverts[a]] - fa;
+      for (int64_t g0 = s0; g0 < s1; g0 += 32) {
+        int64_t f = g0 + lane;
+        bool valid = f < s1;
+        int32_t c = 0;
+        int64_t wa = 0;
+        if (valid) {
+          c = A.C[A.col[row + f]];
+          wa = (int64_t)w[row + f];
+        }
+        if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+        wt_insert_lanes(T8, valid, c, wa);
+      }
+    }
+    __syncthreads();
+    for (int q = 0; q < nlong; q++) {
+      int64_t a = longm[q], fa = A.cflat[a], fb = A.cflat[a + 1];
+      int64_t s0 = fa > f0 ? fa : f0, s1 = fb < f1 ? fb : f1;
+      int64_t row = A.off[A.cverts[a]] - fa;
+      for (int64_t g0 = s0 + 32 * wid; g0 < s1; g0 += 32 * nwarps) {  // warp-uniform
+        int64_t f = g0 + lane;
+        bool valid = f < s1;
+        int32_t c = 0;
+        int64_t wa = 0;
+        if (valid) {
+          c = A.C[A.col[row + f]];
+          wa = (int64_t)w[row + f];
+        }
+        if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+        wt_insert_lanes(T8, valid, c, wa);
+      }
     }
     wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+    __syncthreads();  // nlong and longm are rewritten by the next chunk
   }
 }
 
