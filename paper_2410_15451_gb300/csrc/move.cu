@@ -22,7 +22,7 @@ constexpr int WARP_TABLE = 256;   // slots per warp (bin 0)
 constexpr int WARPS_PER_BLOCK = 8;
 constexpr int BLOCK_TABLE = 2048;  // slots per block (bin 1)
 constexpr int BLOCK_THREADS = 256;
-constexpr int HUGE_THREADS = 1024;
+constexpr int HUGE_THREADS = 256;  // a hub's decision reads only its distinct communities
 
 enum Kind { KIND_MOVE = 0, KIND_REFINE = 1 };
 
@@ -622,7 +622,7 @@ __global__ void __launch_bounds__(256) k_huge_scan(Args A, const int64_t *tab_of
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(1024) k_huge_decide(Args A, const int64_t *tab_off) {
+__global__ void __launch_bounds__(HUGE_THREADS) k_huge_decide(Args A, const int64_t *tab_off) {
   __shared__ int moved_s;
   int64_t count = *A.count;
   int64_t visits = 0, arcs = 0, moves = 0;
@@ -894,7 +894,7 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
       else ld_note_launch(), k_decide_warp<int32_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
       if (KIND == KIND_MOVE) kt_end(h);
     } else if (b == BIN_BLOCK) {
-      int grid = sms * 4;
+      int grid = sms * 7;  // every resident slot (shared stage ~30 KB: 7 blocks per SM)
       if (KIND == KIND_MOVE) kt_begin(h, KT_BLOCK);
       if (g.w64) ld_note_launch(), k_decide_block<int64_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
       else ld_note_launch(), k_decide_block<int32_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
@@ -913,7 +913,7 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
       if (g.w64) ld_note_launch(), k_huge_scan<int64_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
       else ld_note_launch(), k_huge_scan<int32_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
       if (KIND == KIND_MOVE) kt_end(h);
-      ld_note_launch(), k_huge_decide<KIND><<<sms * 2, HUGE_THREADS, 0, s>>>(A, tab_off);
+      ld_note_launch(), k_huge_decide<KIND><<<sms * 8, HUGE_THREADS, 0, s>>>(A, tab_off);
     }
   }
 }

@@ -140,21 +140,31 @@ __global__ void k_split_link_rest(const int32_t *list, DevCounters *cnt, const i
                                   const int32_t *col, const int32_t *C, int32_t *parent, int32_t *big) {
   int lane = threadIdx.x & 31;
   int64_t m = cnt->split_count;
-  int64_t warp = ld_gtid() >> 5, nw = ld_gstride() >> 5;
-  for (int64_t t = warp; t < m; t += nw) {
-    int32_t i = list[t];
-    int32_t c = C[i];
-    int32_t root = 0;
-    if (lane == 0) root = uf_find(parent, i);
-    if (__shfl_sync(LD_FULL, root, 0) == c) continue;
-    int64_t b = off[i], d = deg[i];
-    if (d > SPLIT_BIG) {
-      if (lane == 0) big[atomicAdd(&cnt->big_count, 1)] = i;
-      continue;
+  // 32 listed vertices per warp: the root lookups run a lane each, then the
+  // warp scans the arcs of the vertices that are not joined yet, one by one
+  for (int64_t base = (ld_gtid() & ~31ll); base < m; base += ld_gstride()) {
+    int64_t t = base + lane;
+    int32_t i = 0, c = 0;
+    bool need = false;
+    if (t < m) {
+      i = list[t];
+      c = C[i];
+      need = uf_find(parent, i) != c;
     }
-    for (int64_t a = lane; a < d; a += 32) {
-      int32_t j = col[b + a];
-      if (j != i && C[j] == c) uf_unite(parent, i, j);
+    uint32_t todo = __ballot_sync(LD_FULL, need);
+    while (todo) {
+      int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      int32_t vi = __shfl_sync(LD_FULL, i, src), vc = __shfl_sync(LD_FULL, c, src);
+      int64_t b = off[vi], d = deg[vi];
+      if (d > SPLIT_BIG) {
+        if (lane == 0) big[atomicAdd(&cnt->big_count, 1)] = vi;
+        continue;
+      }
+      for (int64_t a = lane; a < d; a += 32) {
+        int32_t j = col[b + a];
+        if (j != vi && C[j] == vc) uf_unite(parent, vi, j);
+      }
     }
   }
 }
