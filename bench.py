@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--batched", action="store_true",
                     help="the batched configuration: many planted-partition graphs in one handle vs one call each")
     ap.add_argument("--graphs", type=int, default=512, help="graphs of the batched configuration")
+    ap.add_argument("--autotune", action="store_true",
+                    help="search the launch shapes (bin thresholds, blocks per SM) on the DF workload")
     ap.add_argument("--large", action="store_true",
                     help="the large web-like configuration: degree-corrected planted partition, 20 DF batches, "
                          "checked at full size")
@@ -495,6 +497,82 @@ def run_batched(args):
     return 0 if parity else 1
 
 
+# ----------------------------------------------------------------------------- autotuner
+TUNING_SPACE = {
+    "tiny_max": (0, 4, 8),
+    "warp_max": (32, 64, 128),
+    "block_max": (256, 512, 1024),
+    "warp_blocks_per_sm": (2, 4, 8),
+    "block_blocks_per_sm": (2, 4, 7),
+    "hub_blocks_per_sm": (4, 8, 16, 32),
+}
+
+
+def run_autotune(args):
+    """Coordinate search over the launch shapes.  Every candidate runs the
+    same work: a fresh handle takes the state exported after static Leiden
+    (leiden_import_state) and applies the same DF batches, so candidates
+    differ only in launch shapes, which never change a result."""
+    import torch
+
+    from paper_2410_15451_gb300 import leiden as L
+    from paper_2410_15451_gb300 import synth
+
+    seed = synth.BASE_SEED + 8
+    g = synth.rmat(args.scale, 16, 0.57, 0.19, 0.19, seed)
+    size = max(1, int(round(args.batch_frac * g.edges)))
+    W, K = args.warmup, max(3, args.steps)
+    batches = make_batches(g, W + K, size, seed + 1)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    h0 = L.Leiden(g.n, g.off, g.col, g.w, cuda_stream=stream.cuda_stream)
+    h0.static()
+    snap = h0.state()
+    h0.close()
+    dbat = [(torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)) for d, i in batches]
+
+    def evaluate(tuning):
+        x = L.Leiden(g.n, g.off, g.col, g.w, cuda_stream=stream.cuda_stream)
+        L.leiden_set_tuning(x.h, **tuning)
+        L.leiden_import_state(x.h, snap["C"], snap["dSigma"])
+        ms = []
+        for k, (dd, di) in enumerate(dbat):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L.leiden_update_device(x.h, dd, dd.shape[0], di, di.shape[0], L.LEIDEN_DF, None)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= W:
+                ms.append(e0.elapsed_time(e1))
+        x.close()
+        return float(np.mean(ms))
+
+    default = {k: getattr(L.leiden_default_tuning(), k) for k in TUNING_SPACE}
+    best, best_ms = dict(default), evaluate(default)
+    default_ms = best_ms
+    tried = []
+    for key, values in TUNING_SPACE.items():
+        for v in values:
+            cand = dict(best, **{key: v})
+            if cand == best or not (cand["tiny_max"] <= cand["warp_max"] <= cand["block_max"]):
+                continue
+            ms = evaluate(cand)
+            tried.append({"tuning": cand, "ms": ms})
+            if ms < best_ms:
+                best, best_ms = cand, ms
+    recheck_default, recheck_best = evaluate(default), evaluate(best)
+    line = {"metric": "DF update time over launch shapes (coordinate search on identical work)",
+            "impl": "autotune", "unit": "ms", "data": "synthetic", "dtype": "int64",
+            "config": {"workload": f"R-MAT scale {args.scale}, the same {K} DF updates of {size} edges after "
+                                   f"{W} warm-up from the same static state, per candidate"},
+            "default": default, "default_ms": default_ms, "best": best, "best_ms": best_ms,
+            "recheck_default_ms": recheck_default, "recheck_best_ms": recheck_best,
+            "candidates": len(tried), "tried": tried}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- large configuration
 def run_large(args):
     """Degree-corrected planted partition (power-law degrees, exponent 2.1, max
@@ -822,6 +900,8 @@ def main():
         return run_ablation(args) if rank == 0 else 0
     if args.large:
         return run_large(args) if rank == 0 else 0
+    if args.autotune:
+        return run_autotune(args) if rank == 0 else 0
     r = run_ours(args, rank, world, local_rank)
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -106,8 +106,27 @@ typedef struct {
 
 typedef struct leiden_handle leiden_handle;
 
+/* Launch shapes of the local-moving and refinement kernels.  They change how
+ * the work is spread over the GPU, never a result (the deterministic schedule
+ * gives the same bits for every valid setting). */
+typedef struct {
+  int32_t tiny_max;           /* degree <= this: eight lanes per vertex; 0 or 1..8, 8       */
+  int32_t warp_max;           /* degree <= this: a warp per vertex; tiny_max..128, 128      */
+  int32_t block_max;          /* degree <= this: a block per vertex, above: spread over all */
+                              /*    SMs; warp_max..1024, 1024                               */
+  int32_t warp_blocks_per_sm; /* grid of the warp-range kernel, 1..8, 4                     */
+  int32_t block_blocks_per_sm;/* grid of the block-bin kernel, 1..8, 7                      */
+  int32_t hub_blocks_per_sm;  /* grid of the hub arc scan, 1..32, 16                        */
+} leiden_tuning;
+
 /* Fill *p with the defaults listed above. */
 void leiden_default_params(leiden_params *p);
+
+/* Defaults of leiden_tuning; set a handle's with leiden_set_tuning
+ * (LEIDEN_ERR_ARG outside the ranges above).  `python bench.py --autotune`
+ * searches them on a workload. */
+void leiden_default_tuning(leiden_tuning *t);
+leiden_status leiden_set_tuning(leiden_handle *h, const leiden_tuning *t);
 
 /* Create a handle for the graph G^0 given as symmetric CSR on the host:
  * offsets[n+1] (int64, offsets[0] = 0), cols[offsets[n]] (int32, in [0, n)),

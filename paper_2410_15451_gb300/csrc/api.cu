@@ -957,6 +957,28 @@ leiden_status leiden_import_state(leiden_handle *h, const int32_t *C, const int6
   return LEIDEN_OK;
 }
 
+void leiden_default_tuning(leiden_tuning *t) {
+  if (t) *t = leiden_tuning{8, BIN_WARP_MAX, BIN_BLOCK_MAX, 4, 7, 16};
+}
+
+leiden_status leiden_set_tuning(leiden_handle *h, const leiden_tuning *t) {
+  if (!h || !t) return LEIDEN_ERR_ARG;
+  if (t->tiny_max < 0 || t->tiny_max > 8 || t->warp_max < t->tiny_max || t->warp_max > BIN_WARP_MAX ||
+      t->block_max < t->warp_max || t->block_max > BIN_BLOCK_MAX || t->warp_blocks_per_sm < 1 ||
+      t->warp_blocks_per_sm > 8 || t->block_blocks_per_sm < 1 || t->block_blocks_per_sm > 8 ||
+      t->hub_blocks_per_sm < 1 || t->hub_blocks_per_sm > 32) {
+    h->err = "tuning outside its ranges";
+    return LEIDEN_ERR_ARG;
+  }
+  h->tune = *t;
+  // hub tables are sized for the vertices above block_max
+  level_maxdeg(h, h->g_deg, h->n);
+  sync_counters(h);
+  h->g_maxdeg = h->hcnt->max_count;
+  h->g_huge_slots = h->hcnt->huge_slots;
+  return LEIDEN_OK;
+}
+
 int64_t leiden_graph_arcs(leiden_handle *h) { return h ? h->g_arcs : -1; }
 
 leiden_status leiden_get_graph(leiden_handle *h, int64_t *off, int32_t *col, int64_t *w) {

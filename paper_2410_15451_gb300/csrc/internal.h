@@ -77,6 +77,7 @@ struct BatchBuffers {
 
 struct leiden_handle {
   leiden_params p{};
+  leiden_tuning tune{8, BIN_WARP_MAX, BIN_BLOCK_MAX, 4, 7, 16};
   cudaStream_t stream = nullptr;
   int device = 0;
   int sm_count = 152;

@@ -667,7 +667,7 @@ __global__ void __launch_bounds__(HUGE_THREADS) k_huge_decide(Args A, const int6
 // append the in-range ones to the degree bins.
 __global__ void k_collect(int64_t n, uint32_t *unproc, int cls, int classes_mask, const uint8_t *in_range,
                           const int32_t *deg, int32_t *bins, DevCounters *cnt, const int32_t *gid,
-                          const uint8_t *lm_on, const int64_t *loff) {
+                          const uint8_t *lm_on, const int64_t *loff, leiden_tuning tn) {
   // Each warp reads 32 bitmap words at once and visits only the non-zero
   // ones (a frontier is usually sparse), one vertex per lane.
   int lane = threadIdx.x & 31;
@@ -693,7 +693,7 @@ __global__ void k_collect(int64_t n, uint32_t *unproc, int cls, int classes_mask
       if (work) {
         // a vertex without arcs has no candidate community: taking it is its visit
         int dg = deg[v];
-        bin = dg == 0 ? -1 : dg <= BIN_TINY_MAX ? BIN_TINY : dg <= BIN_WARP_MAX ? BIN_WARP : dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE;
+        bin = dg == 0 ? -1 : dg <= tn.tiny_max ? BIN_TINY : dg <= tn.warp_max ? BIN_WARP : dg <= tn.block_max ? BIN_BLOCK : BIN_HUGE;
       }
 #pragma unroll
       for (int b = 0; b < NBINS; b++) {
@@ -777,7 +777,7 @@ __global__ void k_refine_reset(int64_t n, const int32_t *CB, const uint8_t *dR, 
 // by degree; reset their proposals.
 __global__ void k_refine_collect(const int32_t *cand_in, const int32_t *count_in, int32_t *cand_out,
                                  int32_t *count_out, int64_t n, const int32_t *C, const int64_t *S, const int64_t *K,
-                                 const int32_t *deg, int32_t *prop, int32_t *bins, DevCounters *cnt, int unused) {
+                                 const int32_t *deg, int32_t *prop, int32_t *bins, DevCounters *cnt, leiden_tuning tn) {
   int lane = threadIdx.x & 31;
   int64_t m = *count_in;
   for (int64_t base = (ld_gtid() & ~31ll); base < m; base += ld_gstride()) {
@@ -791,7 +791,7 @@ __global__ void k_refine_collect(const int32_t *cand_in, const int32_t *count_in
     int bin = -1;
     if (keep) {
       int dg = deg[i];  // without arcs: no proposal (prop stays -1)
-      bin = dg == 0 ? -1 : dg <= BIN_TINY_MAX ? BIN_TINY : dg <= BIN_WARP_MAX ? BIN_WARP : dg <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE;
+      bin = dg == 0 ? -1 : dg <= tn.tiny_max ? BIN_TINY : dg <= tn.warp_max ? BIN_WARP : dg <= tn.block_max ? BIN_BLOCK : BIN_HUGE;
     }
     uint32_t km = __ballot_sync(LD_FULL, keep);
     if (km) {
@@ -885,16 +885,16 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
     A.list = h->bins + (int64_t)b * g.n;
     A.count = &h->dcnt->bin_count[b];
     if (b == BIN_TINY) continue;  // with the warp bin
-    if (b == BIN_HUGE && g.maxdeg <= BIN_BLOCK_MAX) continue;
-    if (b == BIN_BLOCK && g.maxdeg <= BIN_WARP_MAX) continue;
+    if (b == BIN_HUGE && g.maxdeg <= h->tune.block_max) continue;
+    if (b == BIN_BLOCK && g.maxdeg <= h->tune.warp_max) continue;
     if (b == BIN_WARP) {
-      int grid = sms * 4;  // one wave at four resident blocks per SM
+      int grid = sms * h->tune.warp_blocks_per_sm;  // default 4: one wave at four resident blocks per SM
       if (KIND == KIND_MOVE) kt_begin(h, KT_WARP);
       if (g.w64) ld_note_launch(), k_decide_warp<int64_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
       else ld_note_launch(), k_decide_warp<int32_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
       if (KIND == KIND_MOVE) kt_end(h);
     } else if (b == BIN_BLOCK) {
-      int grid = sms * 7;  // every resident slot (shared stage ~30 KB: 7 blocks per SM)
+      int grid = sms * h->tune.block_blocks_per_sm;  // default 7: every slot (shared stage ~30 KB)
       if (KIND == KIND_MOVE) kt_begin(h, KT_BLOCK);
       if (g.w64) ld_note_launch(), k_decide_block<int64_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
       else ld_note_launch(), k_decide_block<int32_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
@@ -910,8 +910,9 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
       launch_table_plan(A.list, A.count, g.deg, nullptr, tab_off, ch_off, s);
       ld_note_launch(), k_huge_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
       if (KIND == KIND_MOVE) kt_begin(h, KT_HUGE_SCAN);
-      if (g.w64) ld_note_launch(), k_huge_scan<int64_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
-      else ld_note_launch(), k_huge_scan<int32_t, KIND><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
+      int hg = sms * h->tune.hub_blocks_per_sm;
+      if (g.w64) ld_note_launch(), k_huge_scan<int64_t, KIND><<<hg, 256, 0, s>>>(A, tab_off, ch_off);
+      else ld_note_launch(), k_huge_scan<int32_t, KIND><<<hg, 256, 0, s>>>(A, tab_off, ch_off);
       if (KIND == KIND_MOVE) kt_end(h);
       ld_note_launch(), k_huge_decide<KIND><<<sms * 8, HUGE_THREADS, 0, s>>>(A, tab_off);
     }
@@ -972,7 +973,8 @@ void lm_subsweep(leiden_handle *h, const LevelGraph &g, int cls, const uint8_t *
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4 + sizeof(int32_t), s);  // bins + movers
   ld_note_launch(), k_collect<<<grid_for((g.n + 31) / 32, 256), 256, 0, s>>>(
-      g.n, h->unproc, cls, lm_classes(h) - 1, in_range, g.deg, h->bins, h->dcnt, g.gid, h->gc.lm_on, h->d_loff);
+      g.n, h->unproc, cls, lm_classes(h) - 1, in_range, g.deg, h->bins, h->dcnt, g.gid, h->gc.lm_on, h->d_loff,
+      h->tune);
   Args A = make_args(h, g);
   A.in_range = in_range;
   A.dynamic = dynamic;
@@ -999,7 +1001,7 @@ void refine_round(leiden_handle *h, const LevelGraph &g, int slot) {
   cudaMemsetAsync(cout, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&h->dcnt->accepted, 0, sizeof(int32_t), s);
   ld_note_launch(), k_refine_collect<<<grid_for(g.n, 256), 256, 0, s>>>(in, cin, out, cout, g.n, h->Cp, h->Sp, h->Kp, g.deg, h->prop,
-                                                      h->bins, h->dcnt, 0);
+                                                      h->bins, h->dcnt, h->tune);
   Args A = make_args(h, g);
   launch_bins<KIND_REFINE>(h, g, A);
   ld_note_launch(), k_refine_accept<<<h->sm_count * 4, 256, 0, s>>>(out, cout, h->prop, h->Cp, h->Sp, h->Kp, h->dcnt,

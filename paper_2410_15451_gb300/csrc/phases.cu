@@ -567,13 +567,13 @@ __global__ void k_bits_from_flags(int64_t n, const uint8_t *flags, uint32_t *bm)
     if (lane == 0) bm[base >> 5] = m;
   }
 }
-__global__ void k_maxdeg(int64_t n, const int32_t *deg, DevCounters *cnt) {
+__global__ void k_maxdeg(int64_t n, const int32_t *deg, DevCounters *cnt, int block_max) {
   int32_t mx = 0;
   int64_t slots = 0;
   for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) {
     int32_t d = deg[i];
     mx = max(mx, d);
-    if (d > BIN_BLOCK_MAX) {
+    if (d > block_max) {
       int64_t t = 1;
       while (t < 2 * (int64_t)d) t <<= 1;
       slots += t;
@@ -736,5 +736,5 @@ void mark_unprocessed_from_flags(leiden_handle *h, const uint8_t *flags, int64_t
 void level_maxdeg(leiden_handle *h, const int32_t *deg, int64_t n) {
   cudaMemsetAsync(&h->dcnt->max_count, 0, sizeof(int32_t), h->stream);
   cudaMemsetAsync(&h->dcnt->huge_slots, 0, sizeof(int64_t), h->stream);
-  ld_note_launch(), k_maxdeg<<<grid_for(n, TB), TB, 0, h->stream>>>(n, deg, h->dcnt);
+  ld_note_launch(), k_maxdeg<<<grid_for(n, TB), TB, 0, h->stream>>>(n, deg, h->dcnt, h->tune.block_max);
 }

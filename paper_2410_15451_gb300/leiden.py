@@ -41,6 +41,11 @@ class leiden_stats(ctypes.Structure):
         ("lmk_ms", ctypes.c_double * 3)]
 
 
+class leiden_tuning(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int32) for k in ("tiny_max", "warp_max", "block_max", "warp_blocks_per_sm",
+                                              "block_blocks_per_sm", "hub_blocks_per_sm")]
+
+
 class leiden_server_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in (
         "graphs_resident", "graphs_waiting", "requests_queued", "requests_running", "requests_done", "bytes_used",
@@ -95,6 +100,10 @@ def load():
     lib.leiden_batch_trace.restype = ctypes.c_int
     lib.leiden_batch_modularity.argtypes = [vp, vp]
     lib.leiden_batch_modularity.restype = ctypes.c_int
+    lib.leiden_default_tuning.argtypes = [P(leiden_tuning)]
+    lib.leiden_default_tuning.restype = None
+    lib.leiden_set_tuning.argtypes = [vp, P(leiden_tuning)]
+    lib.leiden_set_tuning.restype = ctypes.c_int
     lib.leiden_footprint_bytes.argtypes = [P(leiden_params), i64, vp]
     lib.leiden_footprint_bytes.restype = i64
     d = ctypes.c_double
@@ -285,6 +294,20 @@ def leiden_batch_modularity(h) -> np.ndarray:
     q = np.zeros(leiden_batch_graphs(h), np.float64)
     _check(h, load().leiden_batch_modularity(h, _ptr(q)))
     return q
+
+
+def leiden_default_tuning() -> leiden_tuning:
+    t = leiden_tuning()
+    load().leiden_default_tuning(ctypes.byref(t))
+    return t
+
+
+def leiden_set_tuning(h, **fields):
+    """Set launch shapes (defaults for the fields not given)."""
+    t = leiden_default_tuning()
+    for k, v in fields.items():
+        setattr(t, k, int(v))
+    _check(h, load().leiden_set_tuning(h, ctypes.byref(t)))
 
 
 def leiden_kernel_launches() -> int:

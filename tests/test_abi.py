@@ -96,3 +96,9 @@ def test_footprint_estimate_grows_with_the_graph(lib):
     # at least the CSR with slack: 8 bytes per arc
     assert big > 8 * 10 * 100000
     assert L.load().leiden_footprint_bytes(None, 0, None) == -1
+
+
+def test_default_tuning(lib):
+    t = L.leiden_default_tuning()
+    assert (t.tiny_max, t.warp_max, t.block_max) == (8, 128, 1024)
+    assert ctypes.sizeof(L.leiden_tuning) == 6 * 4

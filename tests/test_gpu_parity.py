@@ -277,3 +277,22 @@ def test_ablation_switches_bit_exact(flags):
         assert_same_trace(gpu, ref)
         assert np.array_equal(cg, cr)
         assert_same_state(gpu, ref)
+
+
+@pytest.mark.parametrize("tuning", [dict(tiny_max=0), dict(tiny_max=4, warp_max=32, block_max=256),
+                                    dict(warp_max=64, block_max=512, warp_blocks_per_sm=2, block_blocks_per_sm=3,
+                                         hub_blocks_per_sm=4)], ids=["no-tiny", "small-bins", "mixed"])
+def test_launch_shapes_do_not_change_results(tuning):
+    """Bin thresholds and grid sizes only move work between kernels."""
+    g = GRAPHS["hubs"]()
+    a = L.Leiden(g.n, g.off, g.col, g.w)
+    b = L.Leiden(g.n, g.off, g.col, g.w)
+    L.leiden_set_tuning(b.h, **tuning)
+    assert np.array_equal(a.static(), b.static())
+    for k in range(2):
+        d, i = synth.random_batch(synth.Graph(g.n, *a.graph()[:2], a.graph()[2].astype(np.int32)), 300,
+                                  seed=311 + k)
+        assert np.array_equal(a.update(d, i, L.LEIDEN_DF), b.update(d, i, L.LEIDEN_DF))
+        assert a.trace()["passes"] == b.trace()["passes"]
+    with pytest.raises(L.LeidenError):
+        L.leiden_set_tuning(b.h, warp_max=200)
