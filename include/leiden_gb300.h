@@ -70,6 +70,9 @@ typedef struct {
   int32_t converge_any;   /* ablation: leave the pass loop when l_i <= 1 OR no community  */
                           /*    was refined (the text's reading; the pseudocode's AND     */
                           /*    is the default); 0                                        */
+  int32_t arena_log2;     /* spill arena for rows that outgrow their slack: used/8 +     */
+                          /*    2^arena_log2 arc slots (0..30); when it is full the CSR   */
+                          /*    is rebuilt with fresh slack; 20                           */
 } leiden_params;
 
 /* Counters and phase times of the last static/update call. */
@@ -102,6 +105,7 @@ typedef struct {
                                /* 40 per visit (list entry, offset, degree, C, K, Sigma  */
                                /* and size of C)                                         */
   double lmk_ms[3];            /* summed device time of the timed launches               */
+  int64_t rebuilds;            /* full CSR rebuilds (the spill arena was full)           */
 } leiden_stats;
 
 typedef struct leiden_handle leiden_handle;

@@ -434,12 +434,37 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   return LEIDEN_OK;
 }
 
+// Pinned host staging of at least `bytes` (grows geometrically); false if it
+// cannot be had, and the caller copies from pageable memory instead.
+bool ensure_pinned(leiden_handle *h, size_t bytes) {
+  if (bytes <= h->pin_bytes) return true;
+  size_t want = std::max(bytes, 2 * h->pin_bytes);
+  if (h->pin) {
+    cudaStreamSynchronize(h->stream);
+    cudaFreeHost(h->pin);
+    h->pin = nullptr;
+    h->pin_bytes = 0;
+  }
+  if (cudaMallocHost(&h->pin, want) != cudaSuccess) {
+    cudaGetLastError();
+    h->pin = nullptr;
+    return false;
+  }
+  h->pin_bytes = want;
+  return true;
+}
+
 leiden_status finish_call(leiden_handle *h, int32_t *out, bool device_out) {
   cudaStream_t s = h->stream;
-  if (out) {
-    CK(cudaMemcpyAsync(out, h->C, (size_t)h->n * sizeof(int32_t),
-                       device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  size_t bytes = (size_t)h->n * sizeof(int32_t);
+  if (out && !device_out && ensure_pinned(h, bytes)) {
+    // device -> pinned at full link speed, then one host copy
+    CK(cudaMemcpyAsync(h->pin, h->C, bytes, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    memcpy(out, h->pin, bytes);
+    return LEIDEN_OK;
   }
+  if (out) CK(cudaMemcpyAsync(out, h->C, bytes, device_out ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return LEIDEN_OK;
 }
@@ -502,6 +527,7 @@ void leiden_default_params(leiden_params *p) {
   p->collect_stats = 0;
   p->split_all = 0;
   p->converge_any = 0;
+  p->arena_log2 = 20;
 }
 
 leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_t *offsets, const int32_t *cols,
@@ -517,7 +543,7 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   leiden_default_params(&p);
   if (params) p = *params;
   if (p.classes < 1 || (p.classes & (p.classes - 1)) || p.max_iterations < 1 || p.max_passes < 1 || p.slack < 0 ||
-      p.min_slack < 0 || p.tau_drop <= 0) {
+      p.min_slack < 0 || p.tau_drop <= 0 || p.arena_log2 < 0 || p.arena_log2 > 30) {
     g_create_error = "invalid parameters (classes must be a power of two)";
     return LEIDEN_ERR_ARG;
   }
@@ -592,7 +618,7 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   cudaError_t e = cudaSuccess;
   auto A = [&](cudaError_t x) { if (x != cudaSuccess && e == cudaSuccess) e = x; };
   // row capacities end at `cap`; the spill arena follows for rows that grow
-  int64_t total = cap + spill_arena_size(cap);
+  int64_t total = cap + spill_arena_size(cap, p.arena_log2);
   std::vector<int32_t> rcap(n);
   for (int64_t i = 0; i < n; i++) rcap[i] = (int32_t)(cap_off[i + 1] - cap_off[i]);
   A(dalloc(h, &h->g_off, n + 1));
@@ -742,7 +768,7 @@ int64_t leiden_footprint_bytes(const leiden_params *params, int64_t n, const int
     deg[i] = (int32_t)d;
     cap += d + std::max<int64_t>((int64_t)((double)d * p.slack), p.min_slack);
   }
-  int64_t total = cap + spill_arena_size(cap);
+  int64_t total = cap + spill_arena_size(cap, p.arena_log2);
   int64_t tc = 1;
   while (tc < 2 * n) tc <<= 1;
   int64_t hs = (level0_huge_slots(deg) + 1023) & ~(int64_t)1023;
@@ -847,8 +873,17 @@ leiden_status leiden_update(leiden_handle *h, const leiden_edge *del, int64_t n_
     h->up_cap = need;
   }
   leiden_edge *dd = h->up_del, *di = h->up_ins;
-  if (n_del) CK(cudaMemcpyAsync(dd, del, (size_t)n_del * sizeof(leiden_edge), cudaMemcpyHostToDevice, h->stream));
-  if (n_ins) CK(cudaMemcpyAsync(di, ins, (size_t)n_ins * sizeof(leiden_edge), cudaMemcpyHostToDevice, h->stream));
+  size_t bd = (size_t)n_del * sizeof(leiden_edge), bi = (size_t)n_ins * sizeof(leiden_edge);
+  CK(cudaStreamSynchronize(h->stream));  // the pinned buffer may still feed an earlier copy
+  if (ensure_pinned(h, bd + bi)) {
+    // host -> pinned, then one asynchronous copy each at full link speed
+    char *pp = (char *)h->pin;
+    if (n_del) { memcpy(pp, del, bd); CK(cudaMemcpyAsync(dd, pp, bd, cudaMemcpyHostToDevice, h->stream)); }
+    if (n_ins) { memcpy(pp + bd, ins, bi); CK(cudaMemcpyAsync(di, pp + bd, bi, cudaMemcpyHostToDevice, h->stream)); }
+  } else {
+    if (n_del) CK(cudaMemcpyAsync(dd, del, bd, cudaMemcpyHostToDevice, h->stream));
+    if (n_ins) CK(cudaMemcpyAsync(di, ins, bi, cudaMemcpyHostToDevice, h->stream));
+  }
   st = do_update(h, dd, n_del, di, n_ins, mode);
   if (st != LEIDEN_OK) return st;
   return finish_call(h, membership_out, false);
@@ -1049,6 +1084,7 @@ void leiden_destroy(leiden_handle *h) {
     if (q) cudaFree(q);
   if (h->hcnt) cudaFreeHost(h->hcnt);
   if (h->gc_host) cudaFreeHost(h->gc_host);
+  if (h->pin) cudaFreeHost(h->pin);
   for (auto &ev : h->ev)
     if (ev) cudaEventDestroy(ev);
   for (auto &ev : h->kt_ev)

@@ -664,7 +664,7 @@ static leiden_status rebuild_graph(leiden_handle *h, int64_t nrows_host, const i
   int64_t used = 0;
   cudaMemcpyAsync(&used, new_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
-  int64_t total = used + spill_arena_size(used);
+  int64_t total = used + spill_arena_size(used, h->p.arena_log2);
   int32_t *new_col = nullptr, *new_w = nullptr, *new_deg = nullptr;
   if (grow(h, &new_col, total) != cudaSuccess || grow(h, &new_w, total) != cudaSuccess ||
       grow(h, &new_deg, n) != cudaSuccess)
@@ -807,6 +807,7 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
                                                            b.row_dhi, b.row_ilo, b.row_ihi, b.row_tmp_off, h->g_off,
                                                            h->g_deg, h->g_col, h->g_w, b.tmp_col, b.tmp_w);
       leiden_status st = rebuild_graph(h, nrows, counts + 3);
+      h->stats.rebuilds++;
       if (st != LEIDEN_OK) return st;
     }
   }

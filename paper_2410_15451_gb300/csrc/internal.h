@@ -166,6 +166,8 @@ struct leiden_handle {
   BatchBuffers b;
   leiden_edge *up_del = nullptr, *up_ins = nullptr;  // staging of host batches
   int64_t up_cap = 0;
+  void *pin = nullptr;      // pinned host staging: batches in, membership out
+  size_t pin_bytes = 0;
 
   cudaEvent_t ev[8] = {};
   // Kernel timer (collect_stats bit 2): event pairs around the launches of
@@ -227,7 +229,7 @@ int grid_for(int64_t n, int block, int max_blocks = 152 * 16);
 leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, int64_t n_del,
                                    const leiden_edge *d_ins, int64_t n_ins, int mode);
 // Spare arc slots kept after `used` slots for rows that outgrow their capacity.
-inline int64_t spill_arena_size(int64_t used) { return used / 8 + (int64_t)(1 << 20); }
+inline int64_t spill_arena_size(int64_t used, int log2_min) { return used / 8 + ((int64_t)1 << log2_min); }
 
 // Sub-sweeps per local-moving iteration: params.classes in the snapshot
 // schedule; the in-place schedule uses at least 16 (fewer vertices move at

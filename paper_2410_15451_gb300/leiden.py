@@ -29,7 +29,7 @@ class leiden_params(ctypes.Structure):
                 ("max_iterations", ctypes.c_int32), ("max_passes", ctypes.c_int32),
                 ("deterministic", ctypes.c_int32), ("classes", ctypes.c_int32),
                 ("slack", ctypes.c_double), ("min_slack", ctypes.c_int32), ("collect_stats", ctypes.c_int32),
-                ("split_all", ctypes.c_int32), ("converge_any", ctypes.c_int32)]
+                ("split_all", ctypes.c_int32), ("converge_any", ctypes.c_int32), ("arena_log2", ctypes.c_int32)]
 
 
 class leiden_stats(ctypes.Structure):
@@ -38,7 +38,7 @@ class leiden_stats(ctypes.Structure):
         "aggregate_arcs", "affected", "communities", "batch_arcs")] + [(k, ctypes.c_double) for k in (
         "ms_total", "ms_batch", "ms_move", "ms_refine", "ms_aggregate", "ms_track")] + [
         (k, ctypes.c_int64 * 3) for k in ("lmk_launches", "lmk_vertices", "lmk_arcs", "lmk_bytes")] + [
-        ("lmk_ms", ctypes.c_double * 3)]
+        ("lmk_ms", ctypes.c_double * 3), ("rebuilds", ctypes.c_int64)]
 
 
 class leiden_tuning(ctypes.Structure):

@@ -52,8 +52,8 @@ def test_default_params_match_the_paper(lib):
 
 
 def test_struct_layouts(lib):
-    assert ctypes.sizeof(L.leiden_params) == 8 * 3 + 4 * 4 + 8 + 4 * 4
-    assert ctypes.sizeof(L.leiden_stats) == 8 * 11 + 8 * 6 + 8 * 3 * 5
+    assert ctypes.sizeof(L.leiden_params) == 8 * 3 + 4 * 4 + 8 + 4 * 5 + 4  # + tail padding
+    assert ctypes.sizeof(L.leiden_stats) == 8 * 11 + 8 * 6 + 8 * 3 * 5 + 8
 
 
 def test_create_rejects_bad_input_without_touching_the_gpu(lib):

@@ -296,3 +296,24 @@ def test_launch_shapes_do_not_change_results(tuning):
         assert a.trace()["passes"] == b.trace()["passes"]
     with pytest.raises(L.LeidenError):
         L.leiden_set_tuning(b.h, warp_max=200)
+
+
+def test_full_rebuild_when_the_spill_arena_fills():
+    """Rows that outgrow their slack move to the spill arena; once it is full
+    the whole CSR is rebuilt.  Both paths keep the result bit-exact."""
+    g = synth.planted_partition(2000, 20, 10, 0.2, 62)
+    gpu = L.Leiden(g.n, g.off, g.col, g.w, slack=0.0, min_slack=1, arena_log2=0)
+    ref = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    gpu.static()
+    ref.static()
+    cur, rebuilds = g, 0
+    for k in range(4):
+        dels, ins = synth.random_batch(cur, 800, seed=600 + k)
+        cg, cr = gpu.update(dels, ins, L.LEIDEN_DF), ref.update(dels, ins, oracle.DF)
+        rebuilds += gpu.stats()["rebuilds"]
+        cur = synth.apply_batch_numpy(cur, dels, ins)
+        for a, b in zip(gpu.graph(), ref.graph()):
+            assert np.array_equal(a, b)
+        assert np.array_equal(cg, cr)
+        assert_same_state(gpu, ref)
+    assert rebuilds >= 1
