@@ -826,6 +826,7 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   recompute_weights(h);
   level_maxdeg(h, h->g_deg, N);
   launch_iota_i32(h->C, N, s);
+  launch_fill_i32(h->csize0, 1, N, s);  // singletons: tracking updates the counts by the vertices that move
   CK(cudaMemcpyAsync(h->Sig, h->K, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
   CK(cudaMemsetAsync(h->dSig, 0, (size_t)N * sizeof(int64_t), s));
   CK(cudaMemsetAsync(h->dV, 1, (size_t)N, s));

@@ -21,35 +21,30 @@ __device__ __forceinline__ uint64_t hash64(uint64_t k) { return ld_splitmix64(k)
 __global__ void k_trc_cand(int64_t N, const int32_t *Cold, const int32_t *Cnew, int32_t *cand) {
   for (int64_t i = ld_gtid(); i < N; i += ld_gstride()) cand[Cold[i]] = Cnew[i];  // any member will do
 }
-__global__ void k_trc_overlap(int64_t N, const int32_t *Cold, const int32_t *Cnew, const int64_t *K,
-                              const int32_t *cand, int64_t *tot, int64_t *ov) {
-  int lane = threadIdx.x & 31;
-  for (int64_t base = (ld_gtid() & ~31ll); base < N; base += ld_gstride()) {
-    int64_t i = base + lane;
-    int32_t o = i < N ? Cold[i] : -1 - lane;
-    int64_t k = 0, kin = 0;
-    if (i < N) {
-      k = K[i];
-      kin = Cnew[i] == cand[o] ? k : 0;
-    }
-    uint32_t peers = __match_any_sync(LD_FULL, o);
-    int64_t st = ld_group_sum_i64(peers, k), so = ld_group_sum_i64(peers, kin);
-    if (i < N && ld_group_leader(peers)) {
-      if (st) atomicAdd((unsigned long long *)&tot[o], (unsigned long long)st);
-      if (so) atomicAdd((unsigned long long *)&ov[o], (unsigned long long)so);
+// The weight of an old community is Sigma^{t-1} with K^t (the batch kept it
+// current), so only the members whose new label differs from the candidate
+// (the deviants) need adding up: ov = tot - deviant weight.
+__global__ void k_trc_deviants(int64_t N, const int32_t *Cold, const int32_t *Cnew, const int64_t *K,
+                               const int32_t *cand, int64_t *dev) {
+  for (int64_t i = ld_gtid(); i < N; i += ld_gstride()) {
+    int32_t o = Cold[i];
+    if (Cnew[i] != cand[o]) {
+      int64_t k = K[i];
+      if (k) atomicAdd((unsigned long long *)&dev[o], (unsigned long long)k);
     }
   }
 }
 // bw/bc of the majority communities; the others are flagged: 1 = through
 // the pair table, 2 = weight 0 (every member has K = 0, e.g. isolated
 // vertices): every pair weighs 0, so the lowest new label of a member wins.
-__global__ void k_trc_majority(int64_t N, const int32_t *cand, const int64_t *tot, const int64_t *ov,
+__global__ void k_trc_majority(int64_t N, const int32_t *cand, const int64_t *tot, const int64_t *dev,
                                long long *bw, int32_t *bc, int32_t *flag) {
   for (int64_t o = ld_gtid(); o < N; o += ld_gstride()) {
     int f = 0;
     if (cand[o] >= 0) {
+      int64_t ov = tot[o] - dev[o];
       if (tot[o] == 0) { bw[o] = 0; f = 2; }
-      else if (2 * ov[o] > tot[o]) { bw[o] = ov[o]; bc[o] = cand[o]; }
+      else if (2 * ov > tot[o]) { bw[o] = ov; bc[o] = cand[o]; }
       else f = 1;
     }
     flag[o] = f;
@@ -157,20 +152,22 @@ __global__ void k_tr_map(int64_t N, const int32_t *new_used, const int32_t *ob, 
     }
   }
 }
+// C^t = map[new label]; Sigma and the member counts follow the vertices
+// whose id changes (Sigma^{t-1} is current with K^t, so the others add
+// nothing).
 __global__ void k_tr_relabel(int64_t N, const int32_t *Cnew, const int32_t *map, const int64_t *K, int32_t *C,
                              int64_t *Sig, int32_t *size) {
-  int lane = threadIdx.x & 31;
-  for (int64_t base = (ld_gtid() & ~31ll); base < N; base += ld_gstride()) {
-    int64_t i = base + lane;
-    int32_t c = -1 - lane;
-    int64_t k = 0;
-    if (i < N) { c = map[Cnew[i]]; C[i] = c; k = K[i]; }
-    uint32_t peers = __match_any_sync(LD_FULL, c);
-    int64_t s = ld_group_sum_i64(peers, k);
-    if (i < N && ld_group_leader(peers)) {
-      if (s) atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)s);
-      atomicAdd(&size[c], __popc(peers));  // member counts of C^t, for the next call
+  for (int64_t i = ld_gtid(); i < N; i += ld_gstride()) {
+    int32_t c = map[Cnew[i]], o = C[i];
+    if (c == o) continue;
+    C[i] = c;
+    int64_t k = K[i];
+    if (k) {
+      atomicAdd((unsigned long long *)&Sig[o], (unsigned long long)(-k));
+      atomicAdd((unsigned long long *)&Sig[c], (unsigned long long)k);
     }
+    atomicSub(&size[o], 1);  // member counts of C^t, for the next call
+    atomicAdd(&size[c], 1);
   }
 }
 __global__ void k_tr_dsig(int64_t N, const uint8_t *matched, int64_t *dSig) {
@@ -250,19 +247,18 @@ void track_communities(leiden_handle *h) {
   long long *bw = (long long *)h->lbuf0, *ow = (long long *)h->lbuf1;
   int32_t *bc = h->ibuf0, *ob = h->ibuf1, *used = h->ibuf2;
   int32_t *cand = h->mtarget, *flag = h->movers;
-  int64_t *tot = h->Kp, *ov = h->Sp;
+  int64_t *dev = h->Sp;
   launch_fill_i64((int64_t *)bw, -1, N, s);
   launch_fill_i32(bc, INT_MAX, N, s);
   launch_fill_i64((int64_t *)ow, -1, N, s);
   launch_fill_i32(ob, INT_MAX, N, s);
   launch_fill_i32(cand, -1, N, s);
   cudaMemsetAsync(used, 0, (size_t)N * sizeof(int32_t), s);
-  cudaMemsetAsync(tot, 0, (size_t)N * sizeof(int64_t), s);
-  cudaMemsetAsync(ov, 0, (size_t)N * sizeof(int64_t), s);
+  cudaMemsetAsync(dev, 0, (size_t)N * sizeof(int64_t), s);
   cudaMemsetAsync(&h->dcnt->tr_occ, 0, sizeof(int32_t), s);
   ld_note_launch(), k_trc_cand<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, cand);
-  ld_note_launch(), k_trc_overlap<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, h->K, cand, tot, ov);
-  ld_note_launch(), k_trc_majority<<<gN, TB, 0, s>>>(N, cand, tot, ov, bw, bc, flag);
+  ld_note_launch(), k_trc_deviants<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, h->K, cand, dev);
+  ld_note_launch(), k_trc_majority<<<gN, TB, 0, s>>>(N, cand, h->Sig, dev, bw, bc, flag);
   int32_t *occ = &h->dcnt->tr_occ;
   ld_note_launch(), k_trc_insert<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, h->K, flag, bc, h->tr_cap, h->tr_keys, h->tr_vals,
                                                    h->tr_list, occ);
@@ -281,8 +277,6 @@ void track_communities(leiden_handle *h) {
   uint8_t *matched = h->dE;
   cudaMemsetAsync(matched, 0, (size_t)N, s);
   ld_note_launch(), k_tr_map<<<gN, TB, 0, s>>>(N, used, ob, urank, frank, flist, map, matched, h->gid0, h->d_voff);
-  cudaMemsetAsync(h->Sig, 0, (size_t)N * sizeof(int64_t), s);
-  cudaMemsetAsync(h->csize0, 0, (size_t)N * sizeof(int32_t), s);
   ld_note_launch(), k_tr_relabel<<<gN, TB, 0, s>>>(N, h->Ctop, map, h->K, h->C, h->Sig, h->csize0);
   ld_note_launch(), k_tr_dsig<<<gN, TB, 0, s>>>(N, matched, h->dSig);
 }
