@@ -794,7 +794,7 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
                   b.row_dst, b.row_newcap, h->g_off, h->g_rcap};
       ld_note_launch(), k_merge_small<<<grid_for((nrows + MERGE_WARPS - 1) / MERGE_WARPS, 1, h->sm_count * 16), MERGE_WARPS * 32, 0,
                       s>>>(M);
-      ld_note_launch(), k_merge_mid<<<h->sm_count * 4, 256, 0, s>>>(M, b.row_mid, &cnt->mid_count);
+      ld_note_launch(), k_merge_mid<<<h->sm_count * 7, 256, 0, s>>>(M, b.row_mid, &cnt->mid_count);  // 32 KB: 7 per SM
       // long rows: chunks over the old row, then chunks over the new row
       int32_t *large = b.row_large;
       const int32_t *nlarge = &cnt->large_count;

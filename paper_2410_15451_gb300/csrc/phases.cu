@@ -15,14 +15,12 @@ constexpr int TB = 256;
 __global__ void k_sr_init(int64_t n, int32_t *rep, int64_t *S2, uint8_t *dS2, uint8_t *dR2) {
   for (int64_t c = ld_gtid(); c < n; c += ld_gstride()) { rep[c] = INT_MAX; S2[c] = 0; dS2[c] = 0; dR2[c] = 0; }
 }
+// rep[c] = smallest member; a vertex only competes while it is below the
+// value already there (a plain read first spares most atomics).
 __global__ void k_sr_min(int64_t n, const int32_t *C, int32_t *rep) {
-  int lane = threadIdx.x & 31;
-  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
-    int64_t i = base + lane;
-    int32_t c = i < n ? C[i] : -1 - lane;
-    uint32_t peers = __match_any_sync(LD_FULL, c);
-    int32_t mn = ld_group_min_i32(peers, (int32_t)i);
-    if (i < n && ld_group_leader(peers)) atomicMin(&rep[c], mn);
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) {
+    int32_t c = C[i];
+    if ((int32_t)i < rep[c]) atomicMin(&rep[c], (int32_t)i);
   }
 }
 __global__ void k_sr_rekey(int64_t n, const int32_t *rep, const int64_t *S, const uint8_t *dS, const uint8_t *dR,
