@@ -138,6 +138,23 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- helpers
+def max_over_ranks(seconds, world, device=None):
+    """The slowest rank's time (every rank gets it); one process: unchanged."""
+    if world <= 1:
+        return seconds
+    import torch
+
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank, world, seconds):
+    """Whole-job units per second: every rank (replica) did `units_per_rank`
+    in at most `seconds`."""
+    return units_per_rank * world / seconds
+
+
 def hbm_peak():
     try:
         with open(PEAKS_PATH) as f:
@@ -265,12 +282,8 @@ def run_ours(args, rank, world, local_rank):
     if args.profile:
         torch.cuda.cudart().cudaProfilerStop()
     clk = clocks.stop()
-    total_s = sum(times_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = size * K * world / total_s
+    total_s = max_over_ranks(sum(times_ms) / 1e3, world, dev)
+    value = replica_throughput(size * K, world, total_s)
     # e2e through the host entry point (host batches, membership to the host)
     host_out = np.zeros(g.n, np.int32)
     e2e_times = []

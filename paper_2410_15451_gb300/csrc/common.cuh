@@ -86,14 +86,6 @@ __device__ __forceinline__ i128 ld_shfl_xor_i128(i128 v, int mask) {
   return (i128)(((u128)(unsigned long long)hi << 64) | (u128)(unsigned long long)lo);
 }
 
-__device__ __forceinline__ i128 ld_shfl_i128(i128 v, int src) {
-  long long lo = (long long)(unsigned long long)(u128)v;
-  long long hi = (long long)((u128)v >> 64);
-  lo = __shfl_sync(LD_FULL, lo, src);
-  hi = __shfl_sync(LD_FULL, hi, src);
-  return (i128)(((u128)(unsigned long long)hi << 64) | (u128)(unsigned long long)lo);
-}
-
 // Candidate (value, community) ordered by larger value, then smaller id.
 // c < 0 means "no candidate".
 __device__ __forceinline__ bool ld_better(i128 v1, int32_t c1, i128 v2, int32_t c2) {
@@ -102,42 +94,23 @@ __device__ __forceinline__ bool ld_better(i128 v1, int32_t c1, i128 v2, int32_t 
   return v1 > v2 || (v1 == v2 && c1 < c2);
 }
 
-// Warp-wide argmax of (v, c); every lane receives the winner.
-__device__ __forceinline__ void ld_warp_argmax(i128 &v, int32_t &c) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    i128 v2 = ld_shfl_xor_i128(v, o);
-    int32_t c2 = __shfl_xor_sync(LD_FULL, c, o);
-    if (ld_better(v2, c2, v, c)) { v = v2; c = c2; }
-  }
-}
-
 __device__ __forceinline__ int64_t ld_warp_sum_i64(int64_t v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(LD_FULL, v, o);
   return v;
 }
 
-// Reductions over the lanes that share a key (peers = __match_any_sync of
-// the key).  Every lane of the warp must call them (full-mask shuffles);
-// each lane receives its group's result.  (The warp reduction unit,
-// __reduce_add_sync with one mask per group, measured about twice as slow
-// here: it serialises over the distinct masks of a warp.)
+// Sum over the lanes that share a key (peers = __match_any_sync of the
+// key).  Every lane of the warp must call it (full-mask shuffles); each
+// lane receives its group's sum.  (The warp reduction unit, __reduce_add_sync
+// with one mask per group, measured about twice as slow here: it serialises
+// over the distinct masks of a warp.)
 __device__ __forceinline__ int64_t ld_group_sum_i64(uint32_t peers, int64_t v) {
   int64_t s = 0;
 #pragma unroll
   for (int k = 0; k < 32; k++) {
     int64_t x = __shfl_sync(LD_FULL, v, k);
     if ((peers >> k) & 1u) s += x;
-  }
-  return s;
-}
-__device__ __forceinline__ int32_t ld_group_min_i32(uint32_t peers, int32_t v) {
-  int32_t s = 0x7fffffff;
-#pragma unroll
-  for (int k = 0; k < 32; k++) {
-    int32_t x = __shfl_sync(LD_FULL, v, k);
-    if (((peers >> k) & 1u) && x < s) s = x;
   }
   return s;
 }
@@ -163,22 +136,9 @@ __device__ __forceinline__ void ld_gtable_insert(int32_t *keys, int64_t *vals, i
   }
 }
 
-// Warp-cooperative form for loops where all 32 lanes iterate together: lanes
-// with the same key add their weights first and one lane inserts the sum
-// (keys of a hub's neighbours are often few, so this removes most of the
-// atomic traffic on the hottest slots).  `valid` = this lane has an item.
-__device__ __forceinline__ void ld_gtable_insert_warp(int32_t *keys, int64_t *vals, int32_t *list, int32_t *occ,
-                                                      int tmask, bool valid, int32_t c, int64_t w) {
-  int32_t key = valid ? c : -2 - (int32_t)(threadIdx.x & 31);  // unique per invalid lane
-  uint32_t peers = __match_any_sync(LD_FULL, key);
-  int64_t sum = ld_group_sum_i64(peers, valid ? w : 0);
-  if (valid && ld_group_leader(peers)) ld_gtable_insert(keys, vals, list, occ, tmask, c, sum);
-}
-
-// Shared-memory staging table: a block adds (key, weight) pairs with
-// warp-aggregated inserts, then either reads the distinct keys from the
-// filled-slot list or flushes them into a global table (one global update
-// per distinct key instead of one per warp group).  Kept empty between uses.
+// Shared-memory staging table of one block: (key, weight) pairs are added
+// with shared atomics and the distinct keys read back from the filled-slot
+// list.  Kept empty between uses.
 constexpr int STAGE_SLOTS = 2048;
 constexpr int STAGE_FILL = 1024;  // distinct keys per use at most (load <= 1/2)
 struct Stage {
@@ -192,24 +152,6 @@ __device__ __forceinline__ void stage_init(Stage &S) {
   for (int s = threadIdx.x; s < STAGE_SLOTS; s += blockDim.x) { S.keys[s] = LD_EMPTY_KEY; S.vals[s] = 0; }
   if (threadIdx.x == 0) S.count = 0;
   __syncthreads();
-}
-
-// Warp-cooperative: all 32 lanes call it; `valid` = this lane has a pair.
-__device__ __forceinline__ void stage_insert_warp(Stage &S, bool valid, int32_t c, int64_t w) {
-  int32_t key = valid ? c : -2 - (int32_t)(threadIdx.x & 31);
-  uint32_t peers = __match_any_sync(LD_FULL, key);
-  int64_t sum = ld_group_sum_i64(peers, valid ? w : 0);
-  if (!valid || !ld_group_leader(peers)) return;
-  uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(STAGE_SLOTS - 1);
-  while (true) {
-    int32_t k = atomicCAS(&S.keys[s], LD_EMPTY_KEY, c);
-    if (k == LD_EMPTY_KEY) S.list[atomicAdd(&S.count, 1)] = (int32_t)s;
-    if (k == LD_EMPTY_KEY || k == c) {
-      atomicAdd((unsigned long long *)&S.vals[s], (unsigned long long)sum);
-      return;
-    }
-    s = (s + 1) & (uint32_t)(STAGE_SLOTS - 1);
-  }
 }
 
 // Lane-wise form: every thread with a pair adds it with shared atomics.
@@ -247,27 +189,9 @@ __device__ __forceinline__ void stage_clear(Stage &S) {
   __syncthreads();
 }
 
-// Move the staged pairs into a global table (ld_gtable_insert) and empty the
-// stage (all threads of the block).
-__device__ __forceinline__ void stage_flush(Stage &S, int32_t *gkeys, int64_t *gvals, int32_t *glist, int32_t *gocc,
-                                            int gmask) {
-  __syncthreads();
-  int n = S.count;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    int32_t s = S.list[t];
-    ld_gtable_insert(gkeys, gvals, glist, gocc, gmask, S.keys[s], S.vals[s]);
-    S.keys[s] = LD_EMPTY_KEY;
-    S.vals[s] = 0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) S.count = 0;
-  __syncthreads();
-}
-
-// Warp-private shared table: only the lanes of one warp touch it, and after
-// __match_any_sync each key is held by one lane, so values are updated with
-// plain adds (an atomic only claims an empty slot).  Flushed into a global
-// table before it passes half full.
+// Warp-private shared table: only the lanes of one warp touch it, so the
+// only contention on a slot is between lanes with the same key.  Flushed
+// into a global table before it passes half full.
 constexpr int WT_SLOTS = 256;
 constexpr int WT_LIMIT = WT_SLOTS / 2 - 32;  // flush above this many keys
 struct WarpTable {
@@ -281,31 +205,6 @@ __device__ __forceinline__ void wt_init(WarpTable &T) {
   int lane = threadIdx.x & 31;
   for (int s = lane; s < WT_SLOTS; s += 32) { T.keys[s] = LD_EMPTY_KEY; T.vals[s] = 0; }
   if (lane == 0) T.count = 0;
-  __syncwarp();
-}
-
-// All 32 lanes call it; `valid` = this lane has a pair.
-__device__ __forceinline__ void wt_insert_warp(WarpTable &T, bool valid, int32_t c, int64_t w) {
-  int32_t key = valid ? c : -2 - (int32_t)(threadIdx.x & 31);
-  uint32_t peers = __match_any_sync(LD_FULL, key);
-  int64_t sum = ld_group_sum_i64(peers, valid ? w : 0);
-  if (valid && ld_group_leader(peers)) {
-    uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(WT_SLOTS - 1);
-    while (true) {
-      int32_t k = T.keys[s];
-      if (k == LD_EMPTY_KEY) {
-        k = atomicCAS(&T.keys[s], LD_EMPTY_KEY, c);  // another lane may take it first
-        if (k == LD_EMPTY_KEY) {
-          T.vals[s] = sum;
-          T.list[atomicAdd(&T.count, 1)] = (int32_t)s;
-          break;
-        }
-      }
-      // a key already in the table lies before the first empty slot of its probe path
-      if (k == c) { T.vals[s] += sum; break; }
-      s = (s + 1) & (uint32_t)(WT_SLOTS - 1);
-    }
-  }
   __syncwarp();
 }
 

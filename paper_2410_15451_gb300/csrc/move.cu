@@ -116,20 +116,6 @@ __device__ __forceinline__ Best warp_best(Best b) {
   return b;
 }
 
-__device__ __forceinline__ Best slot_best(const int32_t *keys, const int64_t *vals, int T, int start, int stride,
-                                          int32_t d, int64_t m2, int64_t Ki, const int64_t *S) {
-  Best b{0, -1, 0, 0};
-  for (int s = start; s < T; s += stride) {
-    int32_t c = keys[s];
-    if (c == LD_EMPTY_KEY) continue;
-    int64_t kv = vals[s];
-    if (c == d) { b.kd += kv; continue; }
-    i128 v = (i128)m2 * kv - (i128)Ki * S[c];
-    if (ld_better(v, c, b.v, b.c)) { b.v = v; b.c = c; b.kc = kv; }
-  }
-  return b;
-}
-
 // Scan arcs [lo, hi) of vertex i with `stride` threads starting at `t0`.
 template <typename W, int KIND>
 __device__ __forceinline__ void scan_arcs(const Args &A, int64_t i, int64_t base, int64_t dg, int t0, int stride,
