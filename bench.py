@@ -354,17 +354,30 @@ ROOFLINE_PROFILE = os.path.join(ROOT, "profiles", "lm_kernels_rmat22_df1e-3.md")
 ROOFLINE_SOURCE = os.path.join(ROOT, "paper_2410_15451_gb300", "csrc", "move.cu")
 
 
+def source_code_sha256(path):
+    """sha256 of a CUDA source with its // comments and blank lines removed,
+    so that a comment edit does not read as a kernel change."""
+    import hashlib
+    import re
+
+    lines = []
+    for line in open(path).read().splitlines():
+        line = re.sub(r"//.*$", "", line).rstrip()
+        if line:
+            lines.append(line)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def ncu_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu summary of the
     local-moving kernels (lines `traffic_bytes_per_launch[<kernel>]: N` and
-    `move_cu_sha256: H`); None when absent or when the kernel source changed
-    since the capture."""
-    import hashlib
+    `move_cu_sha256: H`, H from source_code_sha256); None when absent or when
+    the kernel source changed since the capture."""
     import re
 
     try:
         text = open(ROOFLINE_PROFILE).read()
-        sha = hashlib.sha256(open(ROOFLINE_SOURCE, "rb").read()).hexdigest()
+        sha = source_code_sha256(ROOFLINE_SOURCE)
     except OSError:
         return None
     t = re.search(r"traffic_bytes_per_launch\[" + re.escape(kernel) + r"\]:\s*([0-9.eE+]+)", text)

@@ -476,9 +476,9 @@ __device__ __forceinline__ BestX block_bestx(BestX b) {
   return r;
 }
 
-// One vertex of degree 129..1024 per block: warp-aggregated inserts into a
-// shared stage, then the candidates are read from its filled-slot list (the
-// distinct neighbour communities only) and the slots emptied again.
+// One vertex of degree 129..1024 per block: lane-wise shared-atomic inserts
+// into a shared stage, then the candidates are read from its filled-slot
+// list (the distinct neighbour communities only) and the slots emptied again.
 template <typename W, int KIND>
 __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Args A) {
   __shared__ Stage S;
