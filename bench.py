@@ -206,6 +206,16 @@ def oracle_sample(steps, warmup, seed, budget_s=None):
                        f"1 host thread"), float(np.mean(times))
 
 
+def main_config(args, world):
+    """The workload of the main line, shared by both arms (the reference arm
+    times the oracle on a bounded sample of it, described in its cpu_baseline)."""
+    return {"workload": f"R-MAT scale {args.scale} (n={1 << args.scale}, edge factor 16, a=0.57 b=c=0.19, "
+                        f"symmetrised, deduplicated), DF updates of {args.batch_frac:g}|E| edges (80% ins / 20% del)",
+            "parallelism": "replicas" if world > 1 else "single-gpu",
+            "schedule": "in-place" if args.async_mode else "snapshot (deterministic)",
+            "l2": "CSR > L2 and L2 flushed (256 MB write) between timed steps"}
+
+
 # ----------------------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
@@ -215,8 +225,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "edges/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"R-MAT scale {SAMPLE_SCALE} DF updates of 1e-3|E| (bounded sample of the "
-                               f"R-MAT scale 22 workload)", "batch_frac": 1e-3},
+        "config": main_config(args, world),
         "cpu_baseline": cb,
         "e2e": {"value": cb["value"], "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -937,11 +946,8 @@ def main():
             "metric": METRIC, "value": r["value"], "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["mean_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": f"R-MAT scale {args.scale} (n={r['n']}, |E|={r['E']}), DF updates of "
-                                   f"{r['size']} edges ({args.batch_frac:g}|E|, 80% ins / 20% del)",
-                       "parallelism": "replicas" if world > 1 else "single-gpu",
-                       "schedule": "in-place" if args.async_mode else "snapshot (deterministic)",
-                       "l2": "CSR > L2 and L2 flushed (256 MB write) between timed steps"},
+            "config": main_config(args, world),
+            "graph": {"n": r["n"], "edges": r["E"], "batch_edges": r["size"]},
             "speedup_vs_static": r["t_static"] / r["mean_ms"], "static_ms": r["t_static"],
             "q_df": r["q_df"], "q_static": r["q_static"], "dq": r["q_static"] - r["q_df"],
             "quality_ok": bool(r["q_static"] - r["q_df"] <= 0.005),
