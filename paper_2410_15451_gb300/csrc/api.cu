@@ -321,10 +321,18 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     }
     tr[3] = refined_any;
     tr[4] = rounds;
-    if (B) CK(cudaMemsetAsync(h->gc.ncomm, 0, (size_t)G * sizeof(int32_t), s));
-    count_communities(h, n, g.gid);
-    sync_all(h);
-    tr[2] = h->hcnt->list_count;
+    if (B) {
+      CK(cudaMemsetAsync(h->gc.ncomm, 0, (size_t)G * sizeof(int32_t), s));
+      count_communities(h, n, g.gid);
+      sync_all(h);
+      tr[2] = h->hcnt->list_count;
+    } else {
+      // only the trace needs the count: it is read with the next host sync
+      count_communities(h, n, g.gid);
+      if (lp < 10)
+        CK(cudaMemcpyAsync(&h->dcnt->pass_ncomm[lp], &h->dcnt->list_count, sizeof(int32_t),
+                           cudaMemcpyDeviceToDevice, s));
+    }
     mark(h, 4);
     if (h->p.collect_stats & 1) {
       cudaEventSynchronize(h->ev[4]);
@@ -411,6 +419,8 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   sync_counters(h);
   CK(cudaGetLastError());
   h->trace[0] = passes;
+  if (!B)
+    for (int lp = 0; lp < passes && lp < 10; lp++) h->trace[2 + lp * 25 + 2] = h->hcnt->pass_ncomm[lp];
   st.passes = passes;
   st.lm_vertices = h->hcnt->processed;
   st.lm_arcs = h->hcnt->arcs;
@@ -476,6 +486,7 @@ leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_de
   leiden_status st = batch_apply_and_mark(h, d_del, n_del, d_ins, n_ins, (int)mode);
   if (st != LEIDEN_OK) return st;
   mark(h, 1);
+  level_maxdeg(h, h->g_deg, h->n);
   sync_all(h);
   CK(cudaGetLastError());
   h->m2 = h->hcnt->m2;
@@ -483,8 +494,6 @@ leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_de
     GraphCounters hg = gc_layout(h->gc_host, h->G);
     for (int gi = 0; gi < h->G; gi++) h->m2g[gi] = hg.m2[gi];
   }
-  level_maxdeg(h, h->g_deg, h->n);
-  sync_counters(h);
   h->g_maxdeg = h->hcnt->max_count;
   h->g_huge_slots = h->hcnt->huge_slots;
   st = run_leiden(h, 1, mode == LEIDEN_DS ? h->dV : nullptr);
@@ -780,7 +789,7 @@ int64_t leiden_footprint_bytes(const leiden_params *params, int64_t n, const int
   b += 2 * (8 * (n + 2) + 4 * (n + 1) + 12 * total);                  // aggregated levels
   b += 16 * tc + 4 * n + (int64_t)scan_tmp_bytes(2 * n + 2);          // tracking, scans
   b += 16 * hs;                                                       // hub tables at level 0
-  b += 8 * n + ((int64_t)32 << 20);                                   // batch buffers (grow with batches)
+  b += 8 * n + n / 8 + ((int64_t)32 << 20);                          // batch buffers, touched-row bits
   return b;
 }
 

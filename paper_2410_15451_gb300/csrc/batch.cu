@@ -71,9 +71,11 @@ __global__ void k_unique(const uint64_t *key, const int64_t *w, int64_t n, const
 }
 
 // Deletions must name existing arcs; record the stored weight.
-__global__ void k_check_deletions(const uint64_t *dkey, int64_t nd, int vb, const int64_t *off, const int32_t *deg,
-                                  const int32_t *col, const int32_t *w, int64_t *dw, DevCounters *cnt) {
+__global__ void k_check_deletions(const uint64_t *dkey, const int64_t *nd_p, int vb, const int64_t *off,
+                                  const int32_t *deg, const int32_t *col, const int32_t *w, int64_t *dw,
+                                  DevCounters *cnt) {
   uint64_t mask = (1ull << vb) - 1;
+  int64_t nd = *nd_p;
   for (int64_t i = ld_gtid(); i < nd; i += ld_gstride()) {
     int32_t u = (int32_t)(dkey[i] >> vb), v = (int32_t)(dkey[i] & mask);
     const int32_t *row = col + off[u];
@@ -85,10 +87,11 @@ __global__ void k_check_deletions(const uint64_t *dkey, int64_t nd, int vb, cons
 
 // Insertions: existing arc (not deleted in this batch) -> state 1, position;
 // otherwise state 0 (a new arc).
-__global__ void k_classify_insertions(const uint64_t *ikey, int64_t ni, const uint64_t *dkey, int64_t nd, int vb,
-                                      const int64_t *off, const int32_t *deg, const int32_t *col, int32_t *state,
-                                      int64_t *ipos) {
+__global__ void k_classify_insertions(const uint64_t *ikey, const int64_t *ni_p, const uint64_t *dkey,
+                                      const int64_t *nd_p, int vb, const int64_t *off, const int32_t *deg,
+                                      const int32_t *col, int32_t *state, int64_t *ipos) {
   uint64_t mask = (1ull << vb) - 1;
+  int64_t ni = *ni_p, nd = *nd_p;
   for (int64_t i = ld_gtid(); i < ni; i += ld_gstride()) {
     int32_t u = (int32_t)(ikey[i] >> vb), v = (int32_t)(ikey[i] & mask);
     const int32_t *row = col + off[u];
@@ -103,8 +106,10 @@ __global__ void k_classify_insertions(const uint64_t *ikey, int64_t ni, const ui
   }
 }
 
-__global__ void k_new_flags(const int32_t *state, int64_t ni, int32_t *flag) {
-  for (int64_t i = ld_gtid(); i < ni; i += ld_gstride()) flag[i] = state[i] == 0 ? 1 : 0;
+// Flags of the new arcs over the bound nb >= ni (zero past ni).
+__global__ void k_new_flags(const int32_t *state, const int64_t *ni_p, int64_t nb, int32_t *flag) {
+  int64_t ni = *ni_p;
+  for (int64_t i = ld_gtid(); i < nb; i += ld_gstride()) flag[i] = i < ni && state[i] == 0 ? 1 : 0;
 }
 
 __global__ void k_compact_new(const uint64_t *ikey, const int64_t *iw, int64_t ni, const int32_t *flag,
@@ -113,26 +118,47 @@ __global__ void k_compact_new(const uint64_t *ikey, const int64_t *iw, int64_t n
     if (flag[i]) { okey[pos[i]] = ikey[i]; ow[pos[i]] = iw[i]; }
 }
 
-__global__ void k_mark_touched(const uint64_t *key, int64_t nk, int vb, int32_t *touched) {
-  for (int64_t i = ld_gtid(); i < nk; i += ld_gstride()) touched[key[i] >> vb] = 1;
+// Rows whose structure changes (sources of deletions and of new arcs), each
+// listed once, in no particular order: the first arc of a source's run in
+// either sorted list sets the source's bit, and the arc that found it clear
+// appends the row.  Work is O(batch), not O(n).
+__global__ void k_touched_rows(const uint64_t *dkey, const int64_t *nd_p, const uint64_t *nkey, const int64_t *nn_p,
+                               int vb, uint32_t *bits, int32_t *rows, int64_t *nrows) {
+  int64_t nd = *nd_p, nn = *nn_p;
+  for (int64_t t = ld_gtid(); t < nd + nn; t += ld_gstride()) {
+    bool del = t < nd;
+    const uint64_t *K = del ? dkey : nkey;
+    int64_t k = del ? t : t - nd;
+    uint64_t u = K[k] >> vb;
+    if (k > 0 && (K[k - 1] >> vb) == u) continue;
+    uint32_t bit = 1u << (u & 31);
+    if (!(atomicOr(&bits[u >> 5], bit) & bit))
+      rows[atomicAdd((unsigned long long *)nrows, 1ull)] = (int32_t)u;
+  }
 }
 
-__global__ void k_compact_flags(const int32_t *flag, const int64_t *pos, int64_t n, int32_t *out) {
-  for (int64_t i = ld_gtid(); i < n; i += ld_gstride())
-    if (flag[i]) out[pos[i]] = (int32_t)i;
+// Leaves the row bitmap clear for the next call (every set bit belongs to a
+// listed row).
+__global__ void k_clear_row_bits(const int32_t *rows, const int64_t *nrows_p, uint32_t *bits) {
+  int64_t nrows = *nrows_p;
+  for (int64_t r = ld_gtid(); r < nrows; r += ld_gstride()) bits[rows[r] >> 5] = 0;
 }
 
 // New length of each touched row and its segments in the two arc lists.
 // A row that outgrows its capacity moves to the spill arena at the end of
 // the arc arrays with fresh slack (dst, newcap); if the arena is full the
-// whole CSR is rebuilt instead (overflow flag).
-__global__ void k_row_plan(const int32_t *rows, const int64_t *nrows_p, int vb, const uint64_t *dkey, int64_t nd,
-                           const uint64_t *nkey, const int64_t *nn_p, const int64_t *off, const int32_t *deg,
-                           const int32_t *rcap, int32_t *dlo, int32_t *dhi, int32_t *ilo, int32_t *ihi, int64_t *len,
-                           int64_t *dst, int32_t *newcap, double slack, int min_slack, int64_t colcap,
-                           int32_t *olddeg, int32_t *large, int32_t *mid, DevCounters *cnt) {
-  int64_t nrows = *nrows_p, nn = *nn_p;
-  for (int64_t r = ld_gtid(); r < nrows; r += ld_gstride()) {
+// whole CSR is rebuilt instead (overflow flag).  Lengths are written up to
+// the bound nb >= nrows (zero past nrows) so that their scan needs no host
+// count.  A batch already found invalid takes no arena space.
+__global__ void k_row_plan(const int32_t *rows, const int64_t *nrows_p, int64_t nb, int vb, const uint64_t *dkey,
+                           const int64_t *nd_p, const uint64_t *nkey, const int64_t *nn_p, const int64_t *off,
+                           const int32_t *deg, const int32_t *rcap, int32_t *dlo, int32_t *dhi, int32_t *ilo,
+                           int32_t *ihi, int64_t *len, int64_t *dst, int32_t *newcap, double slack, int min_slack,
+                           int64_t colcap, int32_t *olddeg, int32_t *large, int32_t *mid, DevCounters *cnt) {
+  int64_t nrows = *nrows_p, nd = *nd_p, nn = *nn_p;
+  bool invalid = cnt->error != 0;
+  for (int64_t r = ld_gtid(); r < nb; r += ld_gstride()) {
+    if (r >= nrows) { len[r] = 0; continue; }
     uint64_t u = (uint64_t)rows[r];
     int64_t a = lower_bound_u64(dkey, nd, u << vb), b = lower_bound_u64(dkey, nd, (u + 1) << vb);
     int64_t c = lower_bound_u64(nkey, nn, u << vb), d = lower_bound_u64(nkey, nn, (u + 1) << vb);
@@ -144,7 +170,7 @@ __global__ void k_row_plan(const int32_t *rows, const int64_t *nrows_p, int vb, 
     else if (L > MERGE_SMALL) mid[atomicAdd(&cnt->mid_count, 1)] = (int32_t)r;
     dst[r] = off[u];
     newcap[r] = 0;
-    if (L > rcap[u]) {
+    if (L > rcap[u] && !invalid) {
       int64_t extra = (int64_t)((double)L * slack);
       if (extra < min_slack) extra = min_slack;
       int64_t cap = L + extra;
@@ -610,7 +636,12 @@ cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
   chk(grow(h, &b.ds_w_alt, arcs));
   chk(grow(h, &b.ds_ukey, arcs));
   chk(grow(h, &b.ds_uw, arcs));
-  if (!b.counts) chk(grow(h, &b.counts, 8));
+  b.counts = h->dcnt->bcounts;
+  if (!b.row_bits) {
+    int64_t words = (h->n + 31) / 32;
+    chk(grow(h, &b.row_bits, words));
+    if (b.row_bits) chk(cudaMemsetAsync(b.row_bits, 0, (size_t)std::max<int64_t>(words, 1) * sizeof(uint32_t), h->stream));
+  }
   if (e == cudaSuccess) b.cap_edges = cap;
   return e;
 }
@@ -719,9 +750,11 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
                                                                           b.iw, cnt, h->gid0);
   radix_sort_u64(b.dkey, b.dkey_alt, nullptr, nullptr, nda, 2 * vb, h->scan_tmp, s);
   radix_sort_u64(b.ikey, b.ikey_alt, b.iw, b.iw_alt, nia, 2 * vb, h->scan_tmp, s);
-  // deduplicate: deletions collapse (-> DK), insertions add up (-> IK, IW)
-  int64_t *counts = b.counts;  // [0] nd, [1] ni, [2] new insertions
-  cudaMemsetAsync(counts, 0, 4 * sizeof(int64_t), s);
+  // deduplicate: deletions collapse (-> DK), insertions add up (-> IK, IW).
+  // The counts stay on the device until the one host read below: launches
+  // are sized by the bounds nda, nia and read the counts themselves.
+  int64_t *counts = b.counts;  // [0] nd, [1] ni, [2] new arcs, [3] touched rows, [4] merge-buffer arcs
+  cudaMemsetAsync(counts, 0, 8 * sizeof(int64_t), s);
   uint64_t *DK = b.dkey_alt, *IK = b.ikey_alt;
   int64_t *IW = b.iw_alt, *DW = b.dw;
   if (nda > 0) {
@@ -737,52 +770,42 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
     ld_note_launch(), k_unique<<<grid_for(nia, TB), TB, 0, s>>>(b.ikey, b.iw, nia, b.flag, b.pos, IK, IW);
     cudaMemcpyAsync(counts + 1, b.pos + nia, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   }
-  cudaMemcpyAsync(b.hcounts, counts, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-  cudaStreamSynchronize(s);
-  int64_t nd = b.hcounts[0], ni = b.hcounts[1];
   // deletions must exist (stored weight -> DW); insertions: existing or new
-  if (nd > 0)
-    ld_note_launch(), k_check_deletions<<<grid_for(nd, TB), TB, 0, s>>>(DK, nd, vb, h->g_off, h->g_deg, h->g_col, h->g_w, DW, cnt);
+  if (nda > 0)
+    ld_note_launch(), k_check_deletions<<<grid_for(nda, TB), TB, 0, s>>>(DK, counts + 0, vb, h->g_off, h->g_deg,
+                                                                         h->g_col, h->g_w, DW, cnt);
   uint64_t *NK = b.ikey;  // new insertions, compacted in sorted order
   int64_t *NW = b.iw;
-  if (ni > 0) {
-    ld_note_launch(), k_classify_insertions<<<grid_for(ni, TB), TB, 0, s>>>(IK, ni, DK, nd, vb, h->g_off, h->g_deg, h->g_col,
-                                                          b.ins_state, b.ins_pos);
-    ld_note_launch(), k_new_flags<<<grid_for(ni, TB), TB, 0, s>>>(b.ins_state, ni, b.flag);
-    exclusive_scan_i32_to_i64(b.flag, b.pos, ni, h->scan_tmp, s);
-    ld_note_launch(), k_compact_new<<<grid_for(ni, TB), TB, 0, s>>>(IK, IW, ni, b.flag, b.pos, NK, NW);
-    cudaMemcpyAsync(counts + 2, b.pos + ni, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  if (nia > 0) {
+    ld_note_launch(), k_classify_insertions<<<grid_for(nia, TB), TB, 0, s>>>(IK, counts + 1, DK, counts + 0, vb,
+                                                                             h->g_off, h->g_deg, h->g_col,
+                                                                             b.ins_state, b.ins_pos);
+    ld_note_launch(), k_new_flags<<<grid_for(nia, TB), TB, 0, s>>>(b.ins_state, counts + 1, nia, b.flag);
+    exclusive_scan_i32_to_i64(b.flag, b.pos, nia, h->scan_tmp, s);
+    ld_note_launch(), k_compact_new<<<grid_for(nia, TB), TB, 0, s>>>(IK, IW, nia, b.flag, b.pos, NK, NW);
+    cudaMemcpyAsync(counts + 2, b.pos + nia, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   }
-  cudaMemcpyAsync(b.hcounts + 2, counts + 2, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(&h->hcnt->error, &cnt->error, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  // rows whose structure changes: sources of deletions and of new arcs
+  int64_t nb = std::min<int64_t>(n, nda + nia);  // bound on the touched rows
+  if (nb > 0) {
+    ld_note_launch(), k_touched_rows<<<grid_for(nda + nia, TB), TB, 0, s>>>(DK, counts + 0, NK, counts + 2, vb,
+                                                                            b.row_bits, b.rows, counts + 3);
+    ld_note_launch(), k_clear_row_bits<<<grid_for(nb, TB), TB, 0, s>>>(b.rows, counts + 3, b.row_bits);
+    ld_note_launch(), k_row_plan<<<grid_for(nb, TB), TB, 0, s>>>(
+        b.rows, counts + 3, nb, vb, DK, counts + 0, NK, counts + 2, h->g_off, h->g_deg, h->g_rcap, b.row_dlo,
+        b.row_dhi, b.row_ilo, b.row_ihi, b.row_len, b.row_dst, b.row_newcap, h->p.slack, h->p.min_slack, h->g_cap,
+        b.row_olddeg, b.row_large, b.row_mid, cnt);
+    exclusive_scan_i64(b.row_len, b.row_tmp_off, nb, h->scan_tmp, s);
+    cudaMemcpyAsync(counts + 4, b.row_tmp_off + nb, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
+  }
+  // the one host read before the graph changes: counts, validation, overflow
+  cudaMemcpyAsync(h->hcnt, h->dcnt, sizeof(DevCounters), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
   if (h->hcnt->error)
     return fail(h, LEIDEN_ERR_BATCH, h->hcnt->error == 2 ? "batch deletes an edge that does not exist"
                                                          : "batch edge out of range, self-loop or weight <= 0");
-  int64_t nn = b.hcounts[2];
-  // rows whose structure changes: sources of deletions and of new arcs
-  int32_t *touched = h->ibuf0;
-  int64_t nrows = 0, tmp_total = 0;
-  if (nd + nn > 0) {
-    cudaMemsetAsync(touched, 0, (size_t)n * sizeof(int32_t), s);
-    if (nd > 0) ld_note_launch(), k_mark_touched<<<grid_for(nd, TB), TB, 0, s>>>(DK, nd, vb, touched);
-    if (nn > 0) ld_note_launch(), k_mark_touched<<<grid_for(nn, TB), TB, 0, s>>>(NK, nn, vb, touched);
-    exclusive_scan_i32_to_i64(touched, h->lbuf0, n, h->scan_tmp, s);
-    ld_note_launch(), k_compact_flags<<<grid_for(n, TB), TB, 0, s>>>(touched, h->lbuf0, n, b.rows);
-    cudaMemcpyAsync(counts + 3, h->lbuf0 + n, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
-    ld_note_launch(), k_row_plan<<<grid_for(std::min<int64_t>(n, nd + nn), TB), TB, 0, s>>>(
-        b.rows, counts + 3, vb, DK, nd, NK, counts + 2, h->g_off, h->g_deg, h->g_rcap, b.row_dlo, b.row_dhi,
-        b.row_ilo, b.row_ihi, b.row_len, b.row_dst, b.row_newcap, h->p.slack, h->p.min_slack, h->g_cap,
-        b.row_olddeg, b.row_large, b.row_mid, cnt);
-    cudaMemcpyAsync(b.hcounts + 3, counts + 3, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    nrows = b.hcounts[3];
-    exclusive_scan_i64(b.row_len, b.row_tmp_off, nrows, h->scan_tmp, s);
-    cudaMemcpyAsync(&b.hcounts[4], b.row_tmp_off + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(&h->hcnt->overflow, &cnt->overflow, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    tmp_total = b.hcounts[4];
-  }
+  const int64_t *hc = h->hcnt->bcounts;
+  int64_t nd = hc[0], ni = hc[1], nn = hc[2], nrows = hc[3], tmp_total = hc[4];
   bool overflow = nrows > 0 && h->hcnt->overflow != 0;
   if (ensure_tmp_rows(h, tmp_total) != cudaSuccess) return fail(h, LEIDEN_ERR_OOM, "merge buffer");
   // ---- apply: from here on the handle changes

@@ -46,6 +46,9 @@ struct DevCounters {
   int32_t tr_occ;                 // tracking: filled slots of the pair table
   int32_t mid_count;              // batch apply: touched rows merged by one block each
   int64_t arena_used;             // next free arc slot of G^t (relocated rows go here)
+  int64_t bcounts[8];             // batch apply: unique deletions, unique insertions, new arcs,
+                                  //   touched rows, merge-buffer arcs
+  int32_t pass_ncomm[10];         // communities after refinement, per pass (trace)
 };
 
 // ---------------------------------------------------------------- hashing

@@ -68,8 +68,8 @@ struct BatchBuffers {
   int32_t *row_mid = nullptr;                            // touched rows merged by one block each
   uint64_t *ds_key = nullptr, *ds_key_alt = nullptr, *ds_ukey = nullptr;  // DS (src, C[dst]) pairs
   int64_t *ds_w = nullptr, *ds_w_alt = nullptr, *ds_uw = nullptr;
-  int64_t *counts = nullptr;                             // device counts of the batch pipeline
-  int64_t hcounts[8] = {};                               // host copies
+  int64_t *counts = nullptr;                             // device counts of the batch pipeline (in DevCounters)
+  uint32_t *row_bits = nullptr;                          // one bit per vertex, all clear between calls
   int32_t *tmp_col = nullptr;                            // merged rows
   int32_t *tmp_w = nullptr;
   int64_t tmp_cap = 0;
@@ -210,9 +210,10 @@ void set_handle_free_error(const std::string &msg);
 size_t scan_tmp_bytes(int64_t n);
 cudaError_t exclusive_scan_i64(const int64_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s);
 cudaError_t exclusive_scan_i32_to_i64(const int32_t *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s);
-// Stable LSD radix sort of 64-bit keys on their low `bits` bits, with an
-// optional int64 payload.  Buffers are ping-ponged; the result is written
-// back to keys/vals.  `tmp` must hold sort_tmp_bytes(n) bytes.
+// Stable sort of 64-bit keys on their low `bits` bits, with an optional
+// int64 payload: one block for at most 2048 keys, otherwise an LSD radix
+// sort whose buffers are ping-ponged.  The result is written back to
+// keys/vals.  `tmp` must hold sort_tmp_bytes(n) bytes.
 size_t sort_tmp_bytes(int64_t n);
 cudaError_t radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, int64_t *vals, int64_t *vals_alt, int64_t n,
                            int bits, void *tmp, cudaStream_t s);

@@ -86,16 +86,80 @@ __global__ void scan_tile_apply(const T *in, int64_t *out, int64_t n, const int6
   }
 }
 
+// Second step of the two-launch scan: each block adds up the sums of the
+// tiles before its own (at most SCAN_PREFIX_MAX of them, read from L2) in
+// place of a separate offsets launch; the last block writes the total.
+constexpr int64_t SCAN_PREFIX_MAX = 4096;
+template <typename T>
+__global__ void scan_tile_apply_prefix(const T *in, int64_t *out, int64_t n, const int64_t *tile_sums) {
+  __shared__ int64_t red[SCAN_BLOCK / 32];
+  int64_t b = blockIdx.x;
+  int64_t p = 0;
+  for (int64_t k = threadIdx.x; k < b; k += blockDim.x) p += tile_sums[k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(LD_FULL, p, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = p;
+  __syncthreads();
+  int64_t prefix = 0;
+#pragma unroll 4
+  for (int w = 0; w < SCAN_BLOCK / 32; w++) prefix += red[w];
+  int64_t base = b * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int64_t v[SCAN_ITEMS];
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    v[k] = (base + k < n) ? (int64_t)in[base + k] : 0;
+    s += v[k];
+  }
+  int64_t total;
+  int64_t ex = block_excl_scan(s, &total) + prefix;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    if (base + k < n) out[base + k] = ex;
+    ex += v[k];
+  }
+  if (b == gridDim.x - 1 && threadIdx.x == 0) out[n] = prefix + total;
+}
+
+// One block over all n <= SCAN_TILE values (the loads finish before the
+// first barrier, so in == out is safe).
+template <typename T>
+__global__ void scan_single_tile(const T *in, int64_t *out, int64_t n) {
+  int64_t base = (int64_t)threadIdx.x * SCAN_ITEMS;
+  int64_t v[SCAN_ITEMS];
+  int64_t s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    v[k] = (base + k < n) ? (int64_t)in[base + k] : 0;
+    s += v[k];
+  }
+  int64_t total;
+  int64_t ex = block_excl_scan(s, &total);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; k++) {
+    if (base + k < n) out[base + k] = ex;
+    ex += v[k];
+  }
+  if (threadIdx.x == 0) out[n] = total;
+}
+
+// One launch for a single tile, two while a block can add up the tile sums
+// before it, three (reduce, offsets, apply) beyond that.
 template <typename T>
 cudaError_t scan_impl(const T *in, int64_t *out, int64_t n, void *tmp, cudaStream_t s) {
   int64_t ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
   int64_t *tile = (int64_t *)tmp;
-  if (n > 0) {
+  if (n <= 0) {
+    cudaMemsetAsync(out, 0, sizeof(int64_t), s);
+  } else if (ntiles == 1) {
+    ld_note_launch(), scan_single_tile<T><<<1, SCAN_BLOCK, 0, s>>>(in, out, n);
+  } else if (ntiles <= SCAN_PREFIX_MAX) {
+    ld_note_launch(), scan_tile_reduce<T><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, tile);
+    ld_note_launch(), scan_tile_apply_prefix<T><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, n, tile);
+  } else {
     ld_note_launch(), scan_tile_reduce<T><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, n, tile);
     ld_note_launch(), scan_tile_offsets<<<1, SCAN_BLOCK, 0, s>>>(tile, ntiles, out + n);
     ld_note_launch(), scan_tile_apply<T><<<(unsigned)ntiles, SCAN_BLOCK, 0, s>>>(in, out, n, tile);
-  } else {
-    cudaMemsetAsync(out, 0, sizeof(int64_t), s);
   }
   return cudaGetLastError();
 }
@@ -164,6 +228,49 @@ __global__ void rs_scatter(const uint64_t *keys, const int64_t *vals, uint64_t *
   }
 }
 
+// Stable sort of at most SMALL_SORT_MAX keys (on their low bits) in one
+// block: a bitonic network over (key, position) pairs, then the keys and
+// values are gathered by position.  Equal keys keep their input order, so
+// the output equals the radix sort's.
+constexpr int SMALL_SORT_MAX = 2048;
+__global__ void __launch_bounds__(1024) k_small_sort(uint64_t *keys, int64_t *vals, int n, uint64_t mask) {
+  __shared__ uint64_t sk[SMALL_SORT_MAX];
+  __shared__ int32_t si[SMALL_SORT_MAX];
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int t = threadIdx.x; t < P; t += blockDim.x) {
+    sk[t] = t < n ? (keys[t] & mask) : ~0ull;  // padding sorts last (its positions are larger)
+    si[t] = t;
+  }
+  __syncthreads();
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int t = threadIdx.x; t < P; t += blockDim.x) {
+        int u = t ^ j;
+        if (u <= t) continue;
+        uint64_t a = sk[t], b = sk[u];
+        int32_t ia = si[t], ib = si[u];
+        bool greater = a > b || (a == b && ia > ib);
+        if (greater == ((t & k) == 0)) { sk[t] = b; sk[u] = a; si[t] = ib; si[u] = ia; }
+      }
+      __syncthreads();
+    }
+  constexpr int PER = SMALL_SORT_MAX / 1024;
+  uint64_t kk[PER];
+  int64_t vv[PER];
+#pragma unroll
+  for (int r = 0; r < PER; r++) {
+    int t = threadIdx.x + r * (int)blockDim.x;
+    if (t < n) { kk[r] = keys[si[t]]; vv[r] = vals ? vals[si[t]] : 0; }
+  }
+  __syncthreads();  // every read of the input is done before it is overwritten
+#pragma unroll
+  for (int r = 0; r < PER; r++) {
+    int t = threadIdx.x + r * (int)blockDim.x;
+    if (t < n) { keys[t] = kk[r]; if (vals) vals[t] = vv[r]; }
+  }
+}
+
 }  // namespace
 
 size_t scan_tmp_bytes(int64_t n) { return (size_t)((n + SCAN_TILE - 1) / SCAN_TILE + 8) * sizeof(int64_t); }
@@ -185,6 +292,11 @@ size_t sort_tmp_bytes(int64_t n) {
 cudaError_t radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, int64_t *vals, int64_t *vals_alt, int64_t n,
                            int bits, void *tmp, cudaStream_t s) {
   if (n <= 1) return cudaSuccess;
+  if (n <= SMALL_SORT_MAX) {
+    uint64_t mask = bits >= 64 ? ~0ull : ((1ull << bits) - 1);
+    ld_note_launch(), k_small_sort<<<1, 1024, 0, s>>>(keys, vals, (int)n, mask);
+    return cudaGetLastError();
+  }
   int64_t nblocks = (n + RS_TILE - 1) / RS_TILE;
   int64_t hlen = 256 * nblocks;
   int64_t *hist = (int64_t *)tmp;

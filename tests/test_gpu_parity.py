@@ -108,7 +108,7 @@ def test_updates_bit_exact(name, mode):
     gpu.static()
     ref.static()
     cur = g
-    for k, size in enumerate([7, 150, 1200]):
+    for k, size in enumerate([7, 150, 1200, 4000]):  # the last sorts > 2048 arcs by radix passes
         dels, ins = synth.random_batch(cur, size, seed=500 + k, w_lo=1, w_hi=8 if name in ("weighted", "dcpp") else 1)
         cg = gpu.update(dels, ins, gm)
         cr = ref.update(dels, ins, om)
