@@ -13,6 +13,7 @@
 // the state at the start of the sub-sweep.  Asynchronous mode applies each
 // move as soon as it is found.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -20,7 +21,6 @@ namespace {
 
 constexpr int WARP_TABLE = 256;   // slots per warp (bin 0)
 constexpr int WARPS_PER_BLOCK = 8;
-constexpr int BLOCK_TABLE = 2048;  // slots per block (bin 1)
 constexpr int BLOCK_THREADS = 256;
 constexpr int HUGE_THREADS = 256;  // a hub's decision reads only its distinct communities
 
@@ -561,13 +561,74 @@ __global__ void k_huge_zero_occ(const int32_t *count_p, int32_t *occ) {
   for (int64_t k = ld_gtid(); k < *count_p; k += ld_gstride()) occ[k] = 0;
 }
 
+// Warp table with 32-bit sums, for 32-bit arc weights: 64-bit shared atomics
+// cost more than twice as much, and the smaller table and register footprint
+// leave room for more resident warps.  A lane whose add carries the slot past
+// 2^32 adds the carry straight into the vertex's global table, so the sums
+// stay exact for any weights (a weight below 2^31 carries at most once).
+struct WarpTable32 {
+  int32_t keys[WT_SLOTS];
+  uint32_t vals[WT_SLOTS];
+  int32_t list[WT_SLOTS / 2];
+  int32_t count;
+};
+
+__device__ __forceinline__ void wt_init(WarpTable32 &T) {
+  int lane = threadIdx.x & 31;
+  for (int s = lane; s < WT_SLOTS; s += 32) { T.keys[s] = LD_EMPTY_KEY; T.vals[s] = 0; }
+  if (lane == 0) T.count = 0;
+  __syncwarp();
+}
+
+__device__ __forceinline__ void wt_insert_lanes(WarpTable32 &T, bool valid, int32_t c, int64_t w, int32_t *gkeys,
+                                                int64_t *gvals, int32_t *glist, int32_t *gocc, int gmask) {
+  if (valid) {
+    uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(WT_SLOTS - 1);
+    while (true) {
+      int32_t k = T.keys[s];
+      if (k == LD_EMPTY_KEY) {
+        k = atomicCAS(&T.keys[s], LD_EMPTY_KEY, c);
+        if (k == LD_EMPTY_KEY) {
+          T.list[atomicAdd(&T.count, 1)] = (int32_t)s;
+          k = c;
+        }
+      }
+      if (k == c) {
+        uint32_t add = (uint32_t)w;
+        uint32_t old = atomicAdd(&T.vals[s], add);
+        if (old + add < old) ld_gtable_insert(gkeys, gvals, glist, gocc, gmask, c, (int64_t)1 << 32);
+        break;
+      }
+      s = (s + 1) & (uint32_t)(WT_SLOTS - 1);
+    }
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void wt_flush(WarpTable32 &T, int32_t *gkeys, int64_t *gvals, int32_t *glist, int32_t *gocc,
+                                         int gmask) {
+  int lane = threadIdx.x & 31;
+  __syncwarp();
+  int n = T.count;
+  for (int q = lane; q < n; q += 32) {
+    int32_t s = T.list[q];
+    ld_gtable_insert(gkeys, gvals, glist, gocc, gmask, T.keys[s], (int64_t)T.vals[s]);
+    T.keys[s] = LD_EMPTY_KEY;
+    T.vals[s] = 0;
+  }
+  __syncwarp();
+  if (lane == 0) T.count = 0;
+  __syncwarp();
+}
+
 template <typename W, int KIND>
 __global__ void __launch_bounds__(256) k_huge_scan(Args A, const int64_t *tab_off, const int64_t *ch_off) {
   // Each warp sums its arcs per community in a private shared table first
   // (the neighbours of a hub fall into few communities), then each distinct
   // community updates the vertex's global table once per flush.
-  __shared__ WarpTable WT[8];
-  WarpTable &T8 = WT[threadIdx.x >> 5];
+  using Table = typename std::conditional<sizeof(W) == 4, WarpTable32, WarpTable>::type;
+  __shared__ Table WT[8];
+  Table &T8 = WT[threadIdx.x >> 5];
   wt_init(T8);
   int64_t count = *A.count;
   int64_t nch = ch_off[count];
@@ -599,7 +660,8 @@ __global__ void __launch_bounds__(256) k_huge_scan(Args A, const int64_t *tab_of
         if (valid) { c = A.C[j]; wa = (int64_t)w[base + a]; }
       }
       if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
-      wt_insert_lanes(T8, valid, c, wa);
+      if constexpr (sizeof(W) == 4) wt_insert_lanes(T8, valid, c, wa, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+      else wt_insert_lanes(T8, valid, c, wa);
     }
     wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
     if (KIND == KIND_MOVE && threadIdx.x == 0)

@@ -70,6 +70,15 @@ def _weighted(g):
     return synth.Graph(g.n, g.off, g.col, w)
 
 
+def _heavy(g):
+    # symmetric weights just below 2^30: one warp's sum for one community
+    # passes 2^32 in the hub scan's 32-bit tables
+    src = np.repeat(np.arange(g.n), np.diff(g.off)).astype(np.int64)
+    a, b = np.minimum(src, g.col), np.maximum(src, g.col)
+    w = ((1 << 30) - (a * 2654435761 + b * 40503) % 4096).astype(np.int32)
+    return synth.Graph(g.n, g.off, g.col, w)
+
+
 def assert_same_state(gpu, ref):
     gs, rs = gpu.state(), ref.state()
     for k in ("C", "K", "Sigma", "dSigma"):
@@ -119,6 +128,25 @@ def test_updates_bit_exact(name, mode):
         assert np.array_equal(gpu.affected(), ref.affected())
         assert_same_trace(gpu, ref)
         assert np.array_equal(cg, cr), f"batch {k}"
+        assert_same_state(gpu, ref)
+        assert gpu.modularity() == ref.modularity()
+
+
+def test_heavy_weights_bit_exact():
+    """Weights near 2^30 on the hub graph: the 32-bit warp sums of the hub
+    scan carry past 2^32 and must stay exact, in static Leiden (local moving
+    and refinement) and in a DF update with heavy insertions."""
+    g = _heavy(hub_graph())
+    gpu = L.Leiden(g.n, g.off, g.col, g.w)
+    ref = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    for step in range(2):
+        if step == 0:
+            cg, cr = gpu.static(), ref.static()
+        else:
+            dels, ins = synth.random_batch(g, 300, seed=91, w_lo=1 << 29, w_hi=1 << 30)
+            cg, cr = gpu.update(dels, ins, L.LEIDEN_DF), ref.update(dels, ins, oracle.DF)
+        assert_same_trace(gpu, ref)
+        assert np.array_equal(cg, cr), f"step {step}"
         assert_same_state(gpu, ref)
         assert gpu.modularity() == ref.modularity()
 
