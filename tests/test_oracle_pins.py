@@ -474,3 +474,30 @@ def test_dcpp_generator_shape():
     assert d.max() > 20 * d.mean()
     h = synth.dcpp(30000, avg_deg=40, max_deg=5000, cmax=5000, seed=7)
     assert np.array_equal(g.col, h.col) and np.array_equal(g.w, h.w)
+
+
+@pytest.mark.parametrize("schedule", [oracle.SEQ, oracle.SYNC])
+def test_graphs_without_edges(schedule):
+    """2m = 0: no vertex has a positive gain, so every vertex stays alone and
+    Q is 0 by convention; an update that deletes every edge of a community
+    leaves its vertices alone, with K, Sigma and 2m all zero."""
+    off = np.zeros(6, np.int64)
+    o = oracle.Oracle(5, off, np.zeros(0, np.int32), np.zeros(0, np.int64), schedule=schedule)
+    assert np.array_equal(o.static(), np.arange(5))
+    assert o.modularity() == 0.0
+    # one edge: joining gives Q = 0 against -1/2 apart, so the pair merges
+    off, col, w = csr_from_edges(2, [(0, 1)])
+    o = oracle.Oracle(2, off, col, w, schedule=schedule)
+    assert np.array_equal(o.static(), [0, 0])
+    assert o.modularity() == 0.0
+    # a triangle and an isolated vertex; then every edge deleted
+    off, col, w = csr_from_edges(4, [(0, 1), (1, 2), (0, 2)])
+    o = oracle.Oracle(4, off, col, w, schedule=schedule)
+    assert np.array_equal(o.static(), [0, 0, 0, 3])
+    dels = np.array([[0, 1, 1], [1, 2, 1], [0, 2, 1]], np.int32)
+    c = o.update(dels, np.zeros((0, 3), np.int32), oracle.DF)
+    assert len(np.unique(c)) == 4
+    assert c[0] == 0 and c[3] == 3  # the old ids stay with their vertices where they can
+    st = o.state()
+    assert st["m2"] == 0 and not st["K"].any() and not st["Sigma"].any()
+    assert o.modularity() == 0.0
