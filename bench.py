@@ -1,27 +1,31 @@
 #!/usr/bin/env python3
 """Benchmark of DF-Leiden updates on one GB300 (or N replicas under torchrun).
 
-Workload (the metric's configuration): R-MAT scale 22 (4.19M vertices, edge
-factor 16, a=0.57 b=c=0.19 d=0.05, symmetrised, deduplicated, unit weights),
-static Leiden once, then a stream of random batch updates of 1e-3|E| edges
-(80% insertions of uniform non-edges, 20% deletions of uniform existing
-edges) processed by DF Leiden through the C ABI.  A step is one update: batch
+Workload of the main line: R-MAT scale 22 (4.19M vertices, edge factor 16,
+a=0.57 b=c=0.19 d=0.05, symmetrised, deduplicated, unit weights), static
+Leiden once, then a stream of random batch updates of 1e-3|E| edges (80%
+insertions of uniform non-edges, 20% deletions of uniform existing edges)
+processed by DF Leiden through the C ABI.  A step is one update: batch
 canonicalisation and apply, DF marking, the Leiden pass loop and tracking.
 
 value   = batch edges / device time of leiden_update_device (batch resident in
           HBM before the step; CSR ~1 GB, larger than L2; L2 is also flushed
           between steps outside the timed intervals)
 e2e     = the same through leiden_update with host batch arrays and the
-          membership copied back to the host, wall clock
-Also reported: speedup over GPU static Leiden on the final graph and the
-modularity gap, p50/p99 latency, the batch-size sweep, the roofline of the
-dominant local-moving kernel (measured live), the library's kernel
-launches in the timed steps, the oracle timed on the host cores (bounded sample),
-and SM clocks sampled during the timed region.
+          membership copied back to the host, wall clock, same L2 flush
+Also reported: speedup over GPU static Leiden on the final graph, the
+modularity gap and the connectivity of every community (quality_ok), p50/p99
+latency with a per-step breakdown, ND and DS updates of the same size, the
+batch-size sweep, the roofline of the dominant local-moving kernel (measured
+live) and of the whole step by phase, the library's kernel launches in the
+timed steps, the oracle timed on one host core on the same graph and batch
+stream (a spawned process, in parallel with the GPU work), SM clocks sampled
+during the timed region, and the large web-like configuration (1B edges,
+20 DF batches of 1e-4|E|, checked at full size) as `large`.
 
---impl reference times the CPU oracle (plain sequential C) on a bounded
-sample of the same workload: R-MAT scale 19 with the same generator
-parameters, DF updates of 1e-3|E| edges.
+--impl reference times the CPU oracle (plain sequential C, one host thread)
+on the same workload: the same R-MAT scale-22 graph and batch stream, static
+Leiden untimed, `--warmup` DF updates untimed, `--steps` DF updates timed.
 """
 from __future__ import annotations
 
@@ -43,7 +47,6 @@ if ROOT not in sys.path:
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "DF-Leiden update edges/s & speedup vs GPU static Leiden at dQ<=0.005; p99 lat"
-SAMPLE_SCALE = 19
 
 
 def parse():
@@ -66,6 +69,7 @@ def parse():
                     help="the large web-like configuration: degree-corrected planted partition, 20 DF batches, "
                          "checked at full size")
     ap.add_argument("--large-n", type=int, default=30_000_000)
+    ap.add_argument("--no-large", action="store_true", help="leave the large configuration out of the main line")
     ap.add_argument("--ablation", action="store_true",
                     help="DF updates under the ablation switches: split all, OR convergence, tau_re sweep")
     ap.add_argument("--stability", action="store_true",
@@ -179,38 +183,99 @@ def make_batches(g, n_batches, size, seed):
     return out
 
 
-def oracle_sample(steps, warmup, seed, budget_s=None):
-    """The CPU oracle (as it stands, SYNC schedule) on the bounded sample:
-    R-MAT scale 19, static once (untimed), then DF updates of 1e-3|E|."""
+ND_DS_STEPS = 3  # ND and DS updates timed (after one untimed each) on the same stream
+
+
+def stream_batches(args):
+    """Batches drawn for the main line's stream: warm-up, the timed DF steps,
+    the e2e steps, then one untimed plus ND_DS_STEPS timed steps each of ND
+    and DS.  All are drawn in one call so that they stay valid in sequence;
+    the reference arm draws the same count and gets the same batches."""
+    return args.warmup + 2 * args.steps + 2 * (ND_DS_STEPS + 1)
+
+
+def main_seed(rank=0):
+    from paper_2410_15451_gb300 import synth
+
+    return synth.BASE_SEED + 1 + 1000 * rank
+
+
+def oracle_run(scale, batch_frac, n_batches, warmup, steps, budget_s=None, seed=None):
+    """The CPU oracle as it stands (plain sequential C, SYNC schedule, one
+    host thread) on the main line's workload: the same R-MAT graph (same
+    seed) and the same DF batch stream as the GPU arm.  Static Leiden and
+    `warmup` DF updates run untimed, then up to `steps` DF updates are timed
+    (stopping early once `budget_s` seconds of timed work are done)."""
     import oracle
     from paper_2410_15451_gb300 import synth
 
-    g = synth.rmat(SAMPLE_SCALE, 16, 0.57, 0.19, 0.19, seed)
-    size = max(1, int(round(1e-3 * g.edges)))
-    batches = make_batches(g, warmup + steps, size, seed + 7)
+    seed = main_seed() if seed is None else seed
+    g = synth.rmat(scale, 16, 0.57, 0.19, 0.19, seed)
+    size = max(1, int(round(batch_frac * g.edges)))
+    batches = make_batches(g, n_batches, size, seed + 5)
     o = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    t0 = time.perf_counter()
     o.static()
+    static_s = time.perf_counter() - t0
+    for d, i in batches[:warmup]:
+        o.update(d, i, oracle.DF)
     times = []
-    for k, (d, i) in enumerate(batches):
+    for d, i in batches[warmup:warmup + steps]:
         t0 = time.perf_counter()
         o.update(d, i, oracle.DF)
-        dt = time.perf_counter() - t0
-        if k >= warmup:
-            times.append(dt)
-        if budget_s and sum(times) > budget_s and len(times) >= 1:
+        times.append(time.perf_counter() - t0)
+        if budget_s and sum(times) > budget_s:
             break
     edges = size * len(times)
-    return dict(value=edges / sum(times), unit="edges/s", cores=1, kind="oracle",
-                sample=f"R-MAT scale {SAMPLE_SCALE} ({g.n} vertices, {g.edges} edges), DF updates of "
-                       f"{size} edges (1e-3|E|), {len(times)} timed after {warmup} warm-up, SYNC schedule, "
-                       f"1 host thread"), float(np.mean(times))
+    cb = dict(value=edges / sum(times), unit="edges/s", cores=1, host_cores=os.cpu_count(), kind="oracle",
+              sample=f"R-MAT scale {scale} ({g.n} vertices, {g.edges} edges; the benchmark graph and batch "
+                     f"stream), static Leiden untimed ({static_s:.1f} s), DF updates of {size} edges "
+                     f"({batch_frac:g}|E|): batches {warmup + 1}..{warmup + len(times)} of the stream timed "
+                     f"after {warmup} untimed, SYNC schedule, 1 host thread",
+              static_s=static_s, ms_per_update=float(np.mean(times)) * 1e3)
+    return cb, float(np.mean(times))
+
+
+def _oracle_child(queue, scale, batch_frac, n_batches, warmup, steps, budget_s):
+    try:
+        queue.put(oracle_run(scale, batch_frac, n_batches, warmup, steps, budget_s)[0])
+    except Exception as e:  # reported in the line instead of a number
+        queue.put({"error": f"{type(e).__name__}: {e}"})
+
+
+class OracleBaseline:
+    """The oracle timing of the main line in a spawned process, started
+    before the first GPU call and read at the end (it uses one host core
+    while the GPU arm runs)."""
+
+    def __init__(self, args, warmup=1, steps=8, budget_s=20.0):
+        import multiprocessing as mp
+
+        ctx = mp.get_context("spawn")
+        self.q = ctx.Queue()
+        self.p = ctx.Process(target=_oracle_child,
+                             args=(self.q, args.scale, args.batch_frac, stream_batches(args), warmup, steps,
+                                   budget_s), daemon=True)
+        self.p.start()
+
+    def result(self, timeout=1800):
+        try:
+            out = self.q.get(timeout=timeout)
+        except Exception as e:
+            out = {"error": f"no result from the oracle process: {type(e).__name__}"}
+        self.p.join(timeout=10)
+        return out
+
+
+def workload_name(args):
+    return (f"R-MAT scale {args.scale} (n={1 << args.scale}, edge factor 16, a=0.57 b=c=0.19, symmetrised, "
+            f"deduplicated, unit weights), DF updates of {args.batch_frac:g}|E| edges (80% ins / 20% del)")
 
 
 def main_config(args, world):
     """The workload of the main line, shared by both arms (the reference arm
-    times the oracle on a bounded sample of it, described in its cpu_baseline)."""
-    return {"workload": f"R-MAT scale {args.scale} (n={1 << args.scale}, edge factor 16, a=0.57 b=c=0.19, "
-                        f"symmetrised, deduplicated), DF updates of {args.batch_frac:g}|E| edges (80% ins / 20% del)",
+    times the oracle on the same graph and batch stream)."""
+    return {"workload": workload_name(args),
             "parallelism": "replicas" if world > 1 else "single-gpu",
             "schedule": "in-place" if args.async_mode else "snapshot (deterministic)",
             "l2": "CSR > L2 and L2 flushed (256 MB write) between timed steps"}
@@ -220,7 +285,7 @@ def main_config(args, world):
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    cb, mean_s = oracle_sample(args.steps, args.warmup, 2410154510 + 1)
+    cb, mean_s = oracle_run(args.scale, args.batch_frac, stream_batches(args), args.warmup, args.steps)
     line = {
         "impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "edges/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_s * 1e3, "higher_is_better": True,
@@ -234,6 +299,29 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------- our arm
+def timed_update(stream, fn, flush=None):
+    """One step timed with CUDA events on the handle's stream; the L2 flush
+    (a 256 MB write) runs before the start event."""
+    import torch
+
+    if flush is not None:
+        flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def step_record(ms, st):
+    """Per-step breakdown kept in the line: time, passes, local-moving
+    iterations, CSR rebuilds and device (re)allocations of the call."""
+    return {"ms": round(ms, 4), "passes": int(st["passes"]), "lm_iterations": int(st["lm_iterations"]),
+            "rebuilds": int(st["rebuilds"]), "affected": int(st["affected"])}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -243,14 +331,14 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    seed = synth.BASE_SEED + 1 + 1000 * rank
+    seed = main_seed(rank)
     t_gen = time.time()
     g = synth.rmat(args.scale, 16, 0.57, 0.19, 0.19, seed)
     gen_s = time.time() - t_gen
     E = g.edges
     size = max(1, int(round(args.batch_frac * E)))
     W, K = args.warmup, args.steps
-    batches = make_batches(g, W + 2 * K, size, seed + 5)
+    batches = make_batches(g, stream_batches(args), size, seed + 5)
     # collect_stats=2: an event pair on the stream around every launch of the
     # local-moving kernels (the roofline kernels); no added syncs
     gpu = L.Leiden(g.n, g.off, g.col, g.w, deterministic=not args.async_mode, cuda_stream=stream.cuda_stream,
@@ -261,12 +349,12 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (129 MB)
     torch.cuda.synchronize()
 
-    def dev_step(k):
+    def dev_step(k, mode=L.LEIDEN_DF):
         d, i = dev_batches[k]
-        L.leiden_update_device(gpu.h, d, d.shape[0], i, i.shape[0], L.LEIDEN_DF, d_out)
+        return lambda: L.leiden_update_device(gpu.h, d, d.shape[0], i, i.shape[0], mode, d_out)
 
     for k in range(W):
-        dev_step(k)
+        dev_step(k)()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -277,14 +365,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.cudart().cudaProfilerStart()
     launches0 = L.leiden_kernel_launches()
     for k in range(W, W + K):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        dev_step(k)
-        e1.record(stream)
-        e1.synchronize()
-        times_ms.append(e0.elapsed_time(e1))
+        times_ms.append(timed_update(stream, dev_step(k), flush))
         lm_stats.append(gpu.stats())
     torch.cuda.synchronize()
     gpu_launches = L.leiden_kernel_launches() - launches0
@@ -293,43 +374,56 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     total_s = max_over_ranks(sum(times_ms) / 1e3, world, dev)
     value = replica_throughput(size * K, world, total_s)
-    # e2e through the host entry point (host batches, membership to the host)
+    # e2e through the host entry point (host batches, membership to the
+    # host), with the same L2 flush before each step
     host_out = np.zeros(g.n, np.int32)
     e2e_times = []
     for k in range(W + K, W + 2 * K):
         d, i = batches[k]
+        flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         L.leiden_update(gpu.h, d, i, L.LEIDEN_DF, host_out)
         e2e_times.append(time.perf_counter() - t0)
     e2e_value = size * K * world / sum(e2e_times)
+    # quality on the final graph: Q of the DF membership, every community
+    # connected, GPU static Leiden on the same graph
     q_df = gpu.modularity()
-    # GPU static Leiden on the same final graph
     off, col, w = gpu.graph()
+    st_df = gpu.state()
+    chk = community_checks(off, col, w, st_df["C"], dev)
     st_times = []
     for _ in range(2):
         s = L.Leiden(g.n, off, col, w.astype(np.int32), deterministic=not args.async_mode,
                      cuda_stream=stream.cuda_stream)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        L.leiden_static(s.h, None)
-        e1.record(stream)
-        e1.synchronize()
-        st_times.append(e0.elapsed_time(e1))
+        st_times.append(timed_update(stream, lambda: L.leiden_static(s.h, None)))
         q_static = s.modularity()
         s.close()
     t_static = min(st_times)
     mean_ms = float(np.mean(times_ms))
+    # ND and DS updates of the same size, continuing the stream
+    modes = {}
+    base = W + 2 * K
+    for name, mode in (("ND", L.LEIDEN_ND), ("DS", L.LEIDEN_DS)):
+        dev_step(base, mode)()
+        torch.cuda.synchronize()
+        ms = [timed_update(stream, dev_step(base + 1 + j, mode), flush) for j in range(ND_DS_STEPS)]
+        base += ND_DS_STEPS + 1
+        modes[name] = {"ms_mean": float(np.mean(ms)), "edges_per_s": size / (np.mean(ms) / 1e3),
+                       "speedup_vs_static": t_static / float(np.mean(ms)), "steps": len(ms)}
+    modes["DF"] = {"ms_mean": mean_ms, "edges_per_s": size / (mean_ms / 1e3),
+                   "speedup_vs_static": t_static / mean_ms, "steps": K}
     result = dict(value=value, mean_ms=mean_ms, p50=float(np.percentile(times_ms, 50)),
                   p99=float(np.percentile(times_ms, 99)), e2e=e2e_value, q_df=q_df, q_static=q_static,
                   t_static=t_static, clk=clk, lm_stats=lm_stats, E=E, n=g.n, size=size, gen_s=gen_s,
-                  gpu_launches=gpu_launches,
+                  gpu_launches=gpu_launches, checks=chk, modes=modes,
+                  steps=[step_record(t, st) for t, st in zip(times_ms, lm_stats)],
                   e2e_p99=float(np.percentile(np.array(e2e_times) * 1e3, 99)))
     # batch-size sweep (each size continues the evolving graph)
     sweep = {}
     if not args.no_sweep:
+        off, col, w = gpu.graph()
         for frac in (1e-7, 1e-5, 1e-3, 1e-1):
             sz = max(1, int(round(frac * E)))
             nb = 3 if frac >= 0.1 else 6
@@ -341,20 +435,17 @@ def run_ours(args, rank, world, local_rank):
             for k, (d, i) in enumerate(bs):
                 dd, di = torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)
                 torch.cuda.synchronize()
-                flush.zero_()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                L.leiden_update_device(gpu.h, dd, d.shape[0], di, i.shape[0], L.LEIDEN_DF, d_out)
-                e1.record(stream)
-                e1.synchronize()
+                ms = timed_update(stream, lambda: L.leiden_update_device(gpu.h, dd, d.shape[0], di, i.shape[0],
+                                                                         L.LEIDEN_DF, d_out), flush)
                 if k > 0:
-                    ts.append(e0.elapsed_time(e1))
+                    ts.append(ms)
             sweep[f"{frac:g}"] = dict(batch_edges=sz, ms_mean=float(np.mean(ts)), p99_ms=float(np.percentile(ts, 99)),
                                       edges_per_s=sz / (np.mean(ts) / 1e3))
             off, col, w = gpu.graph()
     result["sweep"] = sweep
     gpu.close()
+    del flush, dev_batches, d_out
+    torch.cuda.empty_cache()
     return result
 
 
@@ -609,53 +700,70 @@ def run_autotune(args):
 
 
 # ----------------------------------------------------------------------------- large configuration
-def intra_community_checks(off, col, w, C, K, rows_per_chunk=1 << 20):
-    """Connected components of the graph of intra-community arcs (scipy), and
-    Q by Eq. 1 in exact integers: (2m * sum_c sigma_c - sum_c Sigma_c^2) /
-    (2m)^2 with sigma_c the intra-community arc weight and Sigma_c the total
-    degree of c."""
-    from scipy.sparse import csr_matrix
-    from scipy.sparse.csgraph import connected_components
+def community_checks(off, col, w, C, dev, chunk_arcs=1 << 28):
+    """Full-size checks of a membership on a CSR, independent of the CUDA
+    library: the number of connected components of the graph of
+    intra-community arcs (label propagation with pointer jumping in torch on
+    `dev`, chunked over rows) against the number of communities, and Q by
+    Eq. 1 in exact integers, (2m * sum_c sigma_c - sum_c Sigma_c^2) / (2m)^2,
+    with sigma_c the intra-community arc weight and Sigma_c the total degree
+    of c.  Returns dict(components, communities, connected, q, intra, m2)."""
+    import torch
 
+    off = np.ascontiguousarray(off, np.int64)
     n = len(off) - 1
-    indptr = np.zeros(n + 1, np.int64)
-    parts = []
+    Ct = torch.from_numpy(np.ascontiguousarray(C, np.int32)).to(dev).long()
+    srcs, dsts = [], []
     intra = 0
-    for a in range(0, n, rows_per_chunk):
-        b = min(n, a + rows_per_chunk)
-        lo, hi = int(off[a]), int(off[b])
-        deg = np.diff(off[a:b + 1])
-        src = np.repeat(np.arange(a, b, dtype=np.int32), deg)
-        dst = col[lo:hi]
-        same = C[src] == C[dst]
-        intra += int(w[lo:hi][same].astype(np.int64).sum())
-        kept = np.add.reduceat(np.append(same.astype(np.int64), 0), (off[a:b] - lo))
-        kept[deg == 0] = 0
-        indptr[a + 1:b + 1] = kept
-        parts.append(dst[same].astype(np.int32))
-    np.cumsum(indptr, out=indptr)
-    indices = np.concatenate(parts)
-    del parts
-    A = csr_matrix((np.ones(len(indices), np.int8), indices, indptr), shape=(n, n))
-    ncc, _ = connected_components(A, directed=False)
-    del A, indices
+    Kt = torch.zeros(n, dtype=torch.int64, device=dev)
+    r0 = 0
+    while r0 < n:
+        r1 = int(np.searchsorted(off, off[r0] + chunk_arcs, side="right")) - 1
+        r1 = min(n, max(r1, r0 + 1))
+        a, b = int(off[r0]), int(off[r1])
+        deg = torch.from_numpy(np.diff(off[r0:r1 + 1])).to(dev)
+        src = torch.repeat_interleave(torch.arange(r0, r1, device=dev, dtype=torch.int64), deg)
+        dst = torch.from_numpy(np.ascontiguousarray(col[a:b])).to(dev).long()
+        wt = torch.from_numpy(np.ascontiguousarray(w[a:b], np.int64)).to(dev)
+        Kt.index_add_(0, src, wt)
+        same = Ct[src] == Ct[dst]
+        intra += int(wt[same].sum())
+        srcs.append(src[same])
+        dsts.append(dst[same])
+        del src, dst, wt, same
+        r0 = r1
+    src = torch.cat(srcs) if srcs else torch.zeros(0, dtype=torch.int64, device=dev)
+    dst = torch.cat(dsts) if dsts else torch.zeros(0, dtype=torch.int64, device=dev)
+    del srcs, dsts
+    lab = torch.arange(n, device=dev, dtype=torch.int64)
+    while src.numel():
+        new = lab.scatter_reduce(0, src, lab[dst], reduce="amin", include_self=True)
+        new = new[new]  # a label is a vertex of the same component: jump to its label
+        if torch.equal(new, lab):
+            break
+        lab = new
+    ncc = int(torch.unique(lab).numel())
+    ncomm = int(torch.unique(Ct).numel())
+    del src, dst, lab
+    K = Kt.cpu().numpy()
     m2 = int(K.sum())
-    Sig = np.bincount(C, K.astype(np.float64), n)  # sums below 2^53: exact
-    sq = sum(int(x) * int(x) for x in Sig[Sig > 0].astype(np.int64))
-    q = (m2 * intra - sq) / (m2 * m2)  # exact integers, one rounding
-    return int(ncc), float(q)
+    Sig = np.bincount(np.asarray(C), K.astype(np.float64), n).astype(np.int64)  # sums below 2^53: exact
+    sq = int(np.square(Sig[Sig > 0].astype(object)).sum())
+    q = (m2 * intra - sq) / (m2 * m2) if m2 else 0.0  # exact integers, one rounding
+    return {"components": ncc, "communities": ncomm, "connected": ncc == ncomm, "q": float(q), "intra": intra,
+            "m2": m2}
 
 
-def run_large(args):
+def large_record(args, stream, dev):
     """Degree-corrected planted partition (power-law degrees, exponent 2.1, max
     1e6; community sizes power-law, exponent 1.5, in [10, 1e5]; mixing 0.3;
-    weights 1..8), static Leiden, then 20 DF batches of 1e-4|E| (80/20).
-    Checked at full size by properties and sampled outputs: K, Sigma and 2m
-    against the final graph; the applied CSR rows of sampled touched vertices
-    against the batches; every community connected (scipy's connected
-    components of the intra-community arcs); Q equal to Eq. 1 evaluated here
-    in exact integers; Q_static - Q_DF <= 0.005.  The host needs about 20 GB
-    beyond the graph for the component check."""
+    weights 1..8; about 1B edges), static Leiden, then 20 DF batches of
+    1e-4|E| (80/20, weights 1..8), each timed with CUDA events after an L2
+    flush.  Checked at full size by properties and sampled outputs: K, Sigma
+    and 2m against the final graph; the applied CSR rows of sampled touched
+    vertices against the batches; every community connected and Q equal to
+    Eq. 1 in exact integers (community_checks); Q_static - Q_DF <= 0.005 with
+    GPU static Leiden run on the same handle's final graph."""
     import gc
 
     import torch
@@ -672,57 +780,58 @@ def run_large(args):
     E = g.edges
     deg0 = np.diff(g.off)
     rep.update(n=g.n, edges=int(E), mean_degree=float(deg0.mean()), max_degree=int(deg0.max()))
+    del deg0
     size = max(1, int(round(1e-4 * E)))
     nb = 20
     dels, ins = synth.random_batch(g, nb * size, seed=seed + 11, w_lo=1, w_hi=8)
     n_ins = int(round(0.8 * size))
     n_del = size - n_ins
     batches = [(dels[k * n_del:(k + 1) * n_del], ins[k * n_ins:(k + 1) * n_ins]) for k in range(nb)]
-    dev = torch.device("cuda", 0)
-    stream = torch.cuda.current_stream(dev)
     t0 = time.time()
-    h = L.Leiden(g.n, g.off, g.col, g.w, cuda_stream=stream.cuda_stream)
+    h = L.Leiden(g.n, g.off, g.col, g.w, cuda_stream=stream.cuda_stream, collect_stats=2)
     rep["create_s"] = time.time() - t0
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    L.leiden_static(h.h, None)
-    e1.record(stream)
-    e1.synchronize()
-    rep["static_ms"] = e0.elapsed_time(e1)
+    rep["static_ms"] = timed_update(stream, lambda: L.leiden_static(h.h, None))
     # sampled rows: touched vertices and their rows in G^0
     touched = np.unique(np.concatenate([dels[:, 0], dels[:, 1], ins[:, 0], ins[:, 1]]))
     rng = np.random.default_rng(seed)
     sample = rng.choice(touched, min(2000, len(touched)), replace=False)
     rows0 = {int(v): dict(zip(g.col[g.off[v]:g.off[v + 1]].tolist(), g.w[g.off[v]:g.off[v + 1]].tolist()))
              for v in sample}
+    n = g.n
     del g
     gc.collect()
-    ms = []
-    d_out = torch.empty(rep["n"], dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+    d_out = torch.empty(n, dtype=torch.int32, device=dev)
+    ms, steps = [], []
+    launches0 = L.leiden_kernel_launches()
     for d, i in batches:
         dd, di = torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)
         torch.cuda.synchronize()
-        e0.record(stream)
-        L.leiden_update_device(h.h, dd, d.shape[0], di, i.shape[0], L.LEIDEN_DF, d_out)
-        e1.record(stream)
-        e1.synchronize()
-        ms.append(e0.elapsed_time(e1))
-    rep.update(batch_edges=size, df_ms_mean=float(np.mean(ms)), df_ms_p99=float(np.percentile(ms, 99)),
-               df_edges_per_s=size / (np.mean(ms) / 1e3))
+        ms.append(timed_update(stream, lambda: L.leiden_update_device(h.h, dd, d.shape[0], di, i.shape[0],
+                                                                      L.LEIDEN_DF, d_out), flush))
+        steps.append(step_record(ms[-1], h.stats()))
+    rep["gpu_launches"] = L.leiden_kernel_launches() - launches0
+    del flush
+    rep.update(batch_edges=size, df_ms_mean=float(np.mean(ms)), df_ms_p50=float(np.percentile(ms, 50)),
+               df_ms_p99=float(np.percentile(ms, 99)), df_edges_per_s=size / (np.mean(ms) / 1e3), steps=steps)
     q_df = h.modularity()
     st = h.state()
     off, col, w = h.graph()
+    # GPU static Leiden on the same final graph, on the same handle (its
+    # state is not needed any more)
+    rep["static_final_ms"] = timed_update(stream, lambda: L.leiden_static(h.h, None))
+    q_static = h.modularity()
     h.close()
+    torch.cuda.empty_cache()
     gc.collect()
     checks = {}
-    # K, Sigma, 2m against the final graph
-    K = np.add.reduceat(np.append(w, 0), off[:-1])  # rows sums; the pad keeps every start in range
+    K = np.add.reduceat(np.append(w, 0), off[:-1])  # row sums; the pad keeps every start in range
     K[np.diff(off) == 0] = 0
     checks["K"] = bool(np.array_equal(K, st["K"]))
     checks["m2"] = bool(int(K.sum()) == st["m2"])
-    checks["Sigma"] = bool(np.array_equal(np.bincount(st["C"], K.astype(np.float64), rep["n"]).astype(np.int64),
+    checks["Sigma"] = bool(np.array_equal(np.bincount(st["C"], K.astype(np.float64), n).astype(np.int64),
                                           st["Sigma"]))  # sums below 2^53: exact in float64
-    # applied rows of sampled touched vertices
+    del K
     for d, i in batches:
         for (u, v, wt) in d.tolist():
             for a, b in ((u, v), (v, u)):
@@ -738,34 +847,28 @@ def run_large(args):
         ok = ok and got == row
     checks["sampled_rows"] = ok
     checks["sampled_rows_count"] = len(rows0)
-    # connected communities and Eq. 1, from the intra-community arcs
-    ncc, q_host = intra_community_checks(off, col, w, st["C"], K)
-    checks["communities"] = int(len(np.unique(st["C"])))
-    checks["connected"] = bool(ncc == checks["communities"])
-    checks["modularity_equal"] = bool(abs(q_host - q_df) <= 1e-12 * max(1.0, abs(q_host)))
-    # GPU static Leiden on the final graph
-    del K
-    gc.collect()
-    s = L.Leiden(rep["n"], off, col, w.astype(np.int32), cuda_stream=stream.cuda_stream)
-    del off, col, w
-    gc.collect()
-    e0.record(stream)
-    L.leiden_static(s.h, None)
-    e1.record(stream)
-    e1.synchronize()
-    rep["static_final_ms"] = e0.elapsed_time(e1)
-    q_static = s.modularity()
-    s.close()
+    cc = community_checks(off, col, w, st["C"], dev)
+    torch.cuda.empty_cache()
+    checks["communities"] = cc["communities"]
+    checks["connected"] = bool(cc["connected"])
+    checks["modularity_equal"] = bool(abs(cc["q"] - q_df) <= 1e-12 * max(1.0, abs(cc["q"])))
     rep.update(q_df=q_df, q_static=q_static, dq=q_static - q_df)
     checks["quality"] = bool(q_static - q_df <= 0.005)
     rep["speedup_vs_static"] = rep["static_final_ms"] / rep["df_ms_mean"]
     rep["checks"] = checks
     rep["all_ok"] = all(v for k, v in checks.items() if isinstance(v, bool))
+    rep["workload"] = (f"degree-corrected planted partition, n={rep['n']}, |E|={rep['edges']}, 20 DF batches of "
+                       f"{size} edges (1e-4|E|, 80/20, weights 1..8), L2 flushed before each")
+    return rep
+
+
+def run_large(args):
+    import torch
+
+    dev = torch.device("cuda", 0)
+    rep = large_record(args, torch.cuda.current_stream(dev), dev)
     line = {"metric": "DF updates on the large web-like graph, checked at full size", "impl": "large",
-            "data": "synthetic", "dtype": "int64",
-            "config": {"workload": f"degree-corrected planted partition, n={rep['n']}, |E|={rep['edges']}, "
-                                   f"20 DF batches of {size} edges (1e-4|E|, 80/20, weights 1..8)"},
-            "result": rep}
+            "data": "synthetic", "dtype": "int64", "config": {"workload": rep["workload"]}, "result": rep}
     print(json.dumps(line), flush=True)
     return 0 if rep["all_ok"] else 1
 
@@ -954,6 +1057,11 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    # the oracle baseline runs in a spawned process, started before any GPU call
+    base = None
+    plain = not (args.batched or args.serve or args.stability or args.ablation or args.large or args.autotune)
+    if plain and rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = OracleBaseline(args)
     import torch
 
     if world > 1:
@@ -974,10 +1082,14 @@ def main():
     if args.autotune:
         return run_autotune(args) if rank == 0 else 0
     r = run_ours(args, rank, world, local_rank)
-    cb = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb, _ = oracle_sample(30, 1, 2410154510 + 1, budget_s=15)  # about 10 s of timed oracle work
+    large = None
+    if rank == 0 and world == 1 and not args.no_large:
+        dev = torch.device("cuda", local_rank)
+        large = large_record(args, torch.cuda.current_stream(dev), dev)
+    cb = base.result() if base is not None else None
     if rank == 0:
+        chk = r["checks"]
+        dom, lmk = roofline_kernels(r["lm_stats"])
         line = {
             "metric": METRIC, "value": r["value"], "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["mean_ms"], "higher_is_better": True, "scaling": "weak",
@@ -986,16 +1098,20 @@ def main():
             "graph": {"n": r["n"], "edges": r["E"], "batch_edges": r["size"]},
             "speedup_vs_static": r["t_static"] / r["mean_ms"], "static_ms": r["t_static"],
             "q_df": r["q_df"], "q_static": r["q_static"], "dq": r["q_static"] - r["q_df"],
-            "quality_ok": bool(r["q_static"] - r["q_df"] <= 0.005),
-            "p50_ms": r["p50"], "p99_ms": r["p99"],
+            "communities": chk["communities"], "disconnected": chk["components"] - chk["communities"],
+            "q_df_exact_check": bool(abs(chk["q"] - r["q_df"]) <= 1e-12 * max(1.0, abs(chk["q"]))),
+            "quality_ok": bool(r["q_static"] - r["q_df"] <= 0.005 and chk["connected"]),
+            "p50_ms": r["p50"], "p99_ms": r["p99"], "steps_detail": r["steps"],
+            "modes": r["modes"],
             "e2e": {"value": r["e2e"], "unit": "edges/s", "h2d_bytes_per_step": r["size"] * 12,
                     "d2h_bytes_per_step": r["n"] * 4, "p99_ms": r["e2e_p99"]},
-            "roofline": roofline_kernels(r["lm_stats"])[0],
-            "roofline_lm_kernels": roofline_kernels(r["lm_stats"])[1],
+            "roofline": dom,
+            "roofline_lm_kernels": lmk,
             "gpu_launches": r["gpu_launches"],
             "cpu_baseline": cb,
             "clocks": r["clk"],
             "sweep": r["sweep"],
+            "large": large,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -1,7 +1,7 @@
-"""The full-size checks of `bench.py --large` restate connectivity and Eq. 1
-without the oracle (scipy components, exact integers); here they are held
-against the oracle's component labelling and modularity on small graphs,
-including memberships with a disconnected community."""
+"""The full-size checks of the benchmark restate connectivity and Eq. 1
+without the oracle (label propagation in torch, exact integers); here they
+are held against the oracle's component labelling and modularity on small
+graphs, including memberships with a disconnected community."""
 from __future__ import annotations
 
 import numpy as np
@@ -12,24 +12,18 @@ import oracle
 from paper_2410_15451_gb300 import synth
 from tests.helpers import csr_from_edges
 
-pytest.importorskip("scipy")
 
-
-def row_sums(g):
-    K = np.add.reduceat(np.append(g.w.astype(np.int64), 0), g.off[:-1])
-    K[np.diff(g.off) == 0] = 0
-    return K
-
-
-@pytest.mark.parametrize("chunk", [7, 1000, 1 << 20])
+@pytest.mark.parametrize("chunk", [7, 1000, 1 << 28])
 def test_components_and_modularity_match_the_oracle(chunk):
     g = synth.rmat(12, 16, 0.57, 0.19, 0.19, 11)
     C = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC).static()
-    ncc, q = bench.intra_community_checks(g.off, g.col, g.w, C, row_sums(g), rows_per_chunk=chunk)
+    r = bench.community_checks(g.off, g.col, g.w, C, "cpu", chunk_arcs=chunk)
     labels = oracle.split(g.off, g.col, C, np.ones(g.n, np.uint8))
-    assert ncc == len(np.unique(labels)) == len(np.unique(C))
-    q_or, _ = oracle.modularity(g.off, g.col, g.w, C)
-    assert abs(q - q_or) <= 1e-12
+    assert r["components"] == len(np.unique(labels)) == len(np.unique(C)) == r["communities"]
+    assert r["connected"]
+    q_or, num = oracle.modularity(g.off, g.col, g.w, C)
+    assert r["m2"] * r["intra"] - num == sum(int(x) ** 2 for x in np.bincount(C, np.diff(g.off).astype(float)))
+    assert abs(r["q"] - q_or) <= 1e-12
 
 
 def test_a_disconnected_community_is_found():
@@ -40,13 +34,13 @@ def test_a_disconnected_community_is_found():
     edges += [(c * k, ((c + 1) % L) * k + 1) for c in range(L)]
     off, col, w = csr_from_edges(L * k, edges)
     C = np.repeat(np.arange(L, dtype=np.int32), k)
-    K = np.add.reduceat(w, off[:-1])
     for C2, extra in ((C, 0), (np.where(C == 2, 0, C).astype(np.int32), 1)):
-        ncc, q = bench.intra_community_checks(off, col, w, C2, K, rows_per_chunk=3)
+        r = bench.community_checks(off, col, w, C2, "cpu", chunk_arcs=3)
         labels = oracle.split(off, col, C2, np.ones(L * k, np.uint8))
-        assert ncc == len(np.unique(labels)) == len(np.unique(C2)) + extra
+        assert r["components"] == len(np.unique(labels)) == len(np.unique(C2)) + extra
+        assert r["connected"] == (extra == 0)
         q_or, _ = oracle.modularity(off, col, w, C2)
-        assert abs(q - q_or) <= 1e-12
+        assert abs(r["q"] - q_or) <= 1e-12
 
 
 def test_reference_arm_prints_the_contract_line():
@@ -58,8 +52,8 @@ def test_reference_arm_prints_the_contract_line():
     import sys
 
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "1"], cwd=root, capture_output=True, text=True, timeout=600)
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "2",
+                          "--warmup", "1", "--scale", "15"], cwd=root, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -68,15 +62,31 @@ def test_reference_arm_prints_the_contract_line():
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
               "vs_baseline", "dtype", "data", "config"):
         assert k in d, k
-    assert d["steps"] == 1 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["unit"] == "edges/s" and d["higher_is_better"] is True
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["cpu_baseline"]["host_cores"] >= 1
+    assert "R-MAT scale 15" in d["cpu_baseline"]["sample"] and "batches 2..3" in d["cpu_baseline"]["sample"]
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     argv = sys.argv
     try:
-        sys.argv = ["bench.py"]
+        sys.argv = ["bench.py", "--scale", "15"]
         defaults = bench.parse()
     finally:
         sys.argv = argv
     assert d["config"] == bench.main_config(defaults, 1)
+
+
+def test_oracle_baseline_runs_in_a_spawned_process():
+    """The main line's oracle timing: a spawned process on the same graph and
+    batch stream as the GPU arm; the result names the sample it timed."""
+    import argparse
+
+    args = argparse.Namespace(scale=13, batch_frac=1e-3, warmup=2, steps=3)
+    cb = bench.OracleBaseline(args, warmup=1, steps=2, budget_s=60).result(timeout=600)
+    assert "error" not in cb, cb
+    assert cb["value"] > 0 and cb["unit"] == "edges/s" and cb["cores"] == 1
+    assert "R-MAT scale 13" in cb["sample"] and "batches 2..3" in cb["sample"]
+    # the same numbers of batches as the GPU arm draws, hence the same batches
+    assert bench.stream_batches(args) == 2 + 2 * 3 + 2 * (bench.ND_DS_STEPS + 1)
