@@ -179,9 +179,10 @@ leiden_status leiden_modularity(leiden_handle *h, const int32_t *membership, dou
 /* Modularity Q (Eq. 1, same exact-integer arithmetic and final division as
  * leiden_modularity) of the membership d_membership (device int32[n], ids in
  * [0, n)) on a caller-owned device CSR: d_offsets int64[n+1], d_cols
- * int32[d_offsets[n]], d_weights int32 or NULL for unit weights.  Work runs
- * on cuda_stream (NULL = legacy default stream); the call returns when *q_out
- * is written.
+ * int32[d_offsets[n]] with ids in [0, n) (non-NULL even for a graph without
+ * arcs), d_weights int32 or NULL for unit weights.  Work runs on cuda_stream
+ * (NULL = legacy default stream); the call returns when *q_out is written.
+ * A graph without arcs has Q = 0.
  *
  * The paper has no counterpart to this function.  It exists for callers that
  * may not allocate device memory: a serving loop that reserved all device
@@ -196,8 +197,10 @@ leiden_status leiden_modularity(leiden_handle *h, const int32_t *membership, dou
  * with that device current; make that first call before any stream capture.
  * All calls share the one array: calls whose GPU work overlaps (other
  * streams, other host threads) race and give wrong results; serialise them.
- * Errors: LEIDEN_ERR_ARG (null pointer, n out of range, membership id out of
- * range), LEIDEN_ERR_CUDA; the message is in leiden_last_error(NULL). */
+ * Errors: LEIDEN_ERR_ARG (null pointer, n out of range, a membership or
+ * column id outside [0, n): found by the kernels, reported after the GPU
+ * work, with no other effect), LEIDEN_ERR_CUDA; the message is in
+ * leiden_last_error(NULL). */
 leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *d_offsets, const int32_t *d_cols,
                                         const int32_t *d_weights, const int32_t *d_membership,
                                         void *cuda_stream, double *q_out);

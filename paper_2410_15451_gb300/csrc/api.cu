@@ -15,6 +15,16 @@ static std::atomic<int64_t> g_launches{0};
 
 void ld_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// int128 -> double in a fixed order (|x| = hi*2^64 + lo, then the sign).
+double i128_to_double(i128 x) {
+  bool neg = x < 0;
+  u128 u = neg ? (u128)(-(x + 1)) + 1 : (u128)x;
+  double hi = (double)(uint64_t)(u >> 64);
+  double lo = (double)(uint64_t)u;
+  double r = hi * 18446744073709551616.0 + lo;
+  return neg ? -r : r;
+}
+
 GraphCounters gc_layout(void *base, int G) {
   char *q = (char *)base;
   GraphCounters c;
@@ -88,16 +98,6 @@ void host_parallel(int64_t n, F fn) {
   std::vector<std::thread> ts;
   for (int t = 0; t < nt; t++) ts.emplace_back([&, t] { fn(n * t / nt, n * (t + 1) / nt); });
   for (auto &th : ts) th.join();
-}
-
-// int128 -> double in a fixed order (|x| = hi*2^64 + lo, then the sign).
-double i128_to_double(i128 x) {
-  bool neg = x < 0;
-  u128 u = neg ? (u128)(-(x + 1)) + 1 : (u128)x;
-  double hi = (double)(uint64_t)(u >> 64);
-  double lo = (double)(uint64_t)u;
-  double r = hi * 18446744073709551616.0 + lo;
-  return neg ? -r : r;
 }
 
 i128 read_i128(const unsigned long long *p) { return (i128)(((u128)p[1] << 64) | (u128)p[0]); }

@@ -139,58 +139,10 @@ __device__ __forceinline__ void ld_gtable_insert(int32_t *keys, int64_t *vals, i
   }
 }
 
-// Shared-memory staging table of one block: (key, weight) pairs are added
-// with shared atomics and the distinct keys read back from the filled-slot
-// list.  Kept empty between uses.
+// Shared staging table of one block (local moving and refinement of the
+// block bin): STAGE_SLOTS open-addressing slots, at most STAGE_FILL keys.
 constexpr int STAGE_SLOTS = 2048;
 constexpr int STAGE_FILL = 1024;  // distinct keys per use at most (load <= 1/2)
-struct Stage {
-  int32_t keys[STAGE_SLOTS];
-  int64_t vals[STAGE_SLOTS];
-  int32_t list[STAGE_FILL];
-  int32_t count;
-};
-
-__device__ __forceinline__ void stage_init(Stage &S) {
-  for (int s = threadIdx.x; s < STAGE_SLOTS; s += blockDim.x) { S.keys[s] = LD_EMPTY_KEY; S.vals[s] = 0; }
-  if (threadIdx.x == 0) S.count = 0;
-  __syncthreads();
-}
-
-// Lane-wise form: every thread with a pair adds it with shared atomics.
-__device__ __forceinline__ void stage_insert_lanes(Stage &S, bool valid, int32_t c, int64_t w) {
-  if (!valid) return;
-  uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(STAGE_SLOTS - 1);
-  while (true) {
-    int32_t k = S.keys[s];
-    if (k == LD_EMPTY_KEY) {
-      k = atomicCAS(&S.keys[s], LD_EMPTY_KEY, c);
-      if (k == LD_EMPTY_KEY) {
-        S.list[atomicAdd(&S.count, 1)] = (int32_t)s;
-        k = c;
-      }
-    }
-    if (k == c) {
-      atomicAdd((unsigned long long *)&S.vals[s], (unsigned long long)w);
-      return;
-    }
-    s = (s + 1) & (uint32_t)(STAGE_SLOTS - 1);
-  }
-}
-
-// Empty the listed slots (all threads of the block; ends synchronised).
-__device__ __forceinline__ void stage_clear(Stage &S) {
-  __syncthreads();
-  int n = S.count;
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    int32_t s = S.list[t];
-    S.keys[s] = LD_EMPTY_KEY;
-    S.vals[s] = 0;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) S.count = 0;
-  __syncthreads();
-}
 
 // Warp-private shared table: only the lanes of one warp touch it, so the
 // only contention on a slot is between lanes with the same key.  Flushed

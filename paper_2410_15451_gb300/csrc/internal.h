@@ -184,6 +184,10 @@ struct leiden_handle {
   std::vector<void *> owned;  // every cudaMalloc of the handle
 };
 
+// int128 -> double in a fixed order (|x| = hi*2^64 + lo, then the sign), so
+// that every entry point turns the same exact numerator into the same double.
+double i128_to_double(i128 x);
+
 // Every kernel launch of the library is written `ld_note_launch(), k<<<...>>>(...)`
 // so that leiden_kernel_launches() counts them.
 void ld_note_launch();

@@ -13,15 +13,15 @@
 // the state at the start of the sub-sweep.  Asynchronous mode applies each
 // move as soon as it is found.
 #include <algorithm>
+#include <atomic>
 #include <type_traits>
 
 #include "internal.h"
 
 namespace {
 
-constexpr int WARP_TABLE = 256;   // slots per warp (bin 0)
 constexpr int WARPS_PER_BLOCK = 8;
-constexpr int BLOCK_THREADS = 256;
+constexpr int BLOCK_THREADS = 128;
 constexpr int HUGE_THREADS = 256;  // a hub's decision reads only its distinct communities
 
 enum Kind { KIND_MOVE = 0, KIND_REFINE = 1 };
@@ -270,6 +270,17 @@ __device__ __forceinline__ i128 decide_x(const Args &A, int64_t i, int32_t d, in
   }
 }
 
+// The outcome of decide_x<KIND_MOVE> in the snapshot schedule, without its
+// writes: a pure function of the sub-sweep's starting state, so every
+// thread of a group can evaluate it.
+__device__ __forceinline__ bool would_move(int32_t d, int64_t Ki, int64_t Sd, int32_t szd, int64_t m2,
+                                           const BestX &b) {
+  if (b.c < 0) return false;
+  i128 g = (i128)m2 * (b.kc - b.kd) - (i128)Ki * ((i128)Ki + b.sc - Sd);
+  if (g <= 0) return false;
+  return !(szd == 1 && b.szc == 1 && b.c > d);
+}
+
 // Deferred moves of the lanes with `mv` set (snapshot schedule): one
 // counter update per warp.
 __device__ __forceinline__ void record_movers(const Args &A, bool mv, int32_t i, int32_t c, i128 g) {
@@ -365,7 +376,6 @@ __device__ __forceinline__ void tiny_step(const Args &A, int64_t item, int64_t n
       b.kd = kv;
     } else {
       b.sc = A.S[c];
-      if (KIND == KIND_MOVE) b.szc = A.size[c];
       b.v = (i128)m2 * kv - (i128)Ki * b.sc;
       b.c = c;
       b.kc = kv;
@@ -373,7 +383,11 @@ __device__ __forceinline__ void tiny_step(const Args &A, int64_t item, int64_t n
   }
   b = bestx_reduce<TINY_LANES>(b);
   i128 g = 0;
-  if (has && sub == 0) g = decide_x<KIND>(A, i, d, Ki, Sd, szd, m2, b);
+  if (has && sub == 0) {
+    // the winner's size matters only to the singleton rule (size_d == 1)
+    if (KIND == KIND_MOVE && !A.async_mode && b.c > d && szd == 1) b.szc = A.size[b.c];
+    g = decide_x<KIND>(A, i, d, Ki, Sd, szd, m2, b);
+  }
   bool mv = g > 0;
   if (KIND == KIND_MOVE && !A.async_mode) record_movers(A, mv, i, b.c, g);
   int moved = __shfl_sync(LD_FULL, mv ? 1 : 0, gl);
@@ -381,38 +395,79 @@ __device__ __forceinline__ void tiny_step(const Args &A, int64_t item, int64_t n
   if (has && sub == 0) { tl.visits++; tl.arcs += dg; tl.moves += mv; tl.dq += g; }
 }
 
-// One vertex of degree 9..128 per warp with a shared-memory table; every
-// per-vertex load is issued before the arc scan.
+// One vertex of degree 9..128 per warp with a warp-private shared table that
+// records its filled slots and is emptied by the reads (so it is cleared
+// once per launch, not per vertex).  Every lane keeps its up to four arcs in
+// flight: their col, weight and C[j] loads are independent, and so are the
+// Sigma loads of the up to four candidates each lane reads back.
+constexpr int WARP_UNROLL = BIN_WARP_MAX / 32;
+
 template <typename W, int KIND>
-__device__ __forceinline__ void warp_step(const Args &A, int32_t i, int lane, int32_t *keys, int64_t *vals,
-                                          Tally &tl) {
+__device__ __forceinline__ void warp_step(const Args &A, int32_t i, int lane, WarpTable &T, Tally &tl) {
+  const W *w = (const W *)A.w;
   int64_t base = A.off[i];
   int32_t dg = A.deg[i];
   int32_t d = A.C[i];
   int64_t Ki = A.K[i];
   int64_t Sd = A.S[d];
   int32_t szd = KIND == KIND_MOVE ? A.size[d] : 0;
+  int32_t bi = KIND == KIND_REFINE ? A.CB[i] : 0;
   int64_t m2 = m2_of(A, i);
-  int T = max(32, next_pow2(2 * dg));
-  for (int s = lane; s < T; s += 32) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
-  __syncwarp();
-  scan_arcs<W, KIND>(A, i, base, dg, lane, 32, keys, vals, T - 1);
-  __syncwarp();
-  BestX b{0, -1, 0, 0, 0, 0};
-  for (int s = lane; s < T; s += 32) {
-    int32_t c = keys[s];
-    if (c == LD_EMPTY_KEY) continue;
-    int64_t kv = vals[s];
-    if (c == d) { b.kd += kv; continue; }
-    int64_t sc = A.S[c];
-    i128 v = (i128)m2 * kv - (i128)Ki * sc;
-    if (ld_better(v, c, b.v, b.c)) { b.v = v; b.c = c; b.kc = kv; b.sc = sc; }
+  int32_t j[WARP_UNROLL], c[WARP_UNROLL];
+  int64_t wa[WARP_UNROLL];
+  bool v[WARP_UNROLL];
+#pragma unroll
+  for (int u = 0; u < WARP_UNROLL; u++) {
+    int a = lane + 32 * u;
+    v[u] = a < dg;
+    j[u] = v[u] ? A.col[base + a] : i;
+    wa[u] = v[u] ? (int64_t)w[base + a] : 0;
   }
-  if (KIND == KIND_MOVE && b.c >= 0) b.szc = A.size[b.c];
-  b = bestx_reduce<32>(b);
+#pragma unroll
+  for (int u = 0; u < WARP_UNROLL; u++) {
+    v[u] = v[u] && j[u] != i;
+    if (KIND == KIND_REFINE) v[u] = v[u] && A.CB[j[u]] == bi;
+  }
+#pragma unroll
+  for (int u = 0; u < WARP_UNROLL; u++) c[u] = v[u] ? A.C[j[u]] : 0;
+#pragma unroll
+  for (int u = 0; u < WARP_UNROLL; u++) wt_insert_lanes(T, v[u], c[u], wa[u]);
+  int n = T.count;
+  int32_t cc[WARP_UNROLL];
+  int64_t kv[WARP_UNROLL], sc[WARP_UNROLL];
+#pragma unroll
+  for (int u = 0; u < WARP_UNROLL; u++) {
+    int q = lane + 32 * u;
+    cc[u] = -1;
+    kv[u] = 0;
+    if (q < n) {
+      int32_t sl = T.list[q];
+      cc[u] = T.keys[sl];
+      kv[u] = T.vals[sl];
+      T.keys[sl] = LD_EMPTY_KEY;
+      T.vals[sl] = 0;
+    }
+  }
   __syncwarp();
+  if (lane == 0) T.count = 0;
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < WARP_UNROLL; u++) sc[u] = cc[u] >= 0 && cc[u] != d ? A.S[cc[u]] : 0;
+  BestX b{0, -1, 0, 0, 0, 0};
+#pragma unroll
+  for (int u = 0; u < WARP_UNROLL; u++) {
+    if (cc[u] < 0) continue;
+    if (cc[u] == d) { b.kd += kv[u]; continue; }
+    i128 val = (i128)m2 * kv[u] - (i128)Ki * sc[u];
+    if (ld_better(val, cc[u], b.v, b.c)) { b.v = val; b.c = cc[u]; b.kc = kv[u]; b.sc = sc[u]; }
+  }
+  b = bestx_reduce<32>(b);
   i128 g = 0;
-  if (lane == 0) g = decide_x<KIND>(A, i, d, Ki, Sd, szd, m2, b);
+  if (lane == 0) {
+    // the winner's size matters only to the singleton rule (size_d == 1)
+    if (KIND == KIND_MOVE && !A.async_mode && b.c > d && szd == 1) b.szc = A.size[b.c];
+    g = decide_x<KIND>(A, i, d, Ki, Sd, szd, m2, b);
+  }
   bool mv = g > 0;
   if (KIND == KIND_MOVE && !A.async_mode) record_movers(A, mv, i, b.c, g);
   int moved = __shfl_sync(LD_FULL, mv ? 1 : 0, 0);
@@ -424,17 +479,17 @@ __device__ __forceinline__ void warp_step(const Args &A, int32_t i, int lane, in
 // each) in one launch: items [0, ceil(n3/4)) are groups of four tiny
 // vertices, the rest one warp-bin vertex each.
 template <typename W, int KIND>
-__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) k_decide_warp(Args A) {
-  __shared__ int32_t skeys[WARPS_PER_BLOCK][WARP_TABLE];
-  __shared__ int64_t svals[WARPS_PER_BLOCK][WARP_TABLE];
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, 4) k_decide_warp(Args A) {
+  __shared__ WarpTable WT[WARPS_PER_BLOCK];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  wt_init(WT[wid]);
   int64_t ntiny = *A.count_tiny, nwarp = *A.count;
   int64_t ngroups = (ntiny + 3) / 4, total = ngroups + nwarp;
   int64_t gw = (int64_t)blockIdx.x * WARPS_PER_BLOCK + wid, nw = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   Tally tl;
   for (int64_t t = gw; t < total; t += nw) {
     if (t < ngroups) tiny_step<W, KIND>(A, t, ntiny, lane, tl);
-    else warp_step<W, KIND>(A, A.list[t - ngroups], lane, skeys[wid], svals[wid], tl);
+    else warp_step<W, KIND>(A, A.list[t - ngroups], lane, WT[wid], tl);
   }
   flush_tally<W, KIND>(A, tl);
 }
@@ -458,38 +513,63 @@ __device__ __forceinline__ Best block_best(Best b) {
 }
 
 // ---------------------------------------------------------------- bin 1: block, shared stage
-// Block-wide merge of per-thread BestX values (result valid in every thread).
-__device__ __forceinline__ BestX block_bestx(BestX b) {
-  __shared__ BestX sb[32];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  b = bestx_reduce<32>(b);
-  if (lane == 0) sb[wid] = b;
-  __syncthreads();
-  if (wid == 0) {
-    BestX x = lane < nw ? sb[lane] : BestX{0, -1, 0, 0, 0, 0};
-    x = bestx_reduce<32>(x);
-    if (lane == 0) sb[0] = x;
+// One vertex of degree 129..1024 per block of BLOCK_THREADS.  Each thread
+// keeps BLOCK_UNROLL arcs in flight (their col, weight and C[j] loads are
+// independent), adds them into a shared open-addressing stage with shared
+// atomics, and the block then reads the candidates from the stage's
+// filled-slot list (the distinct neighbour communities only), emptying
+// each slot as it reads it.
+//
+// Two barriers per vertex: B1 after the inserts, B2 after the per-warp
+// candidates are posted.  The filled-slot count alternates between two
+// words by vertex parity: the count of vertex k is read between B1(k) and
+// B2(k) and reset by thread 0 after B2(k); it is next used by vertex k+2,
+// whose inserts begin after B2(k+1).  The slots read (and emptied) for
+// vertex k are all emptied before B2(k), so the inserts of vertex k+1 find
+// the stage empty.
+constexpr int BLOCK_UNROLL = 4;
+struct BlockStage {
+  int32_t keys[STAGE_SLOTS];
+  int64_t vals[STAGE_SLOTS];
+  int32_t list[STAGE_FILL];
+  int32_t count[2];
+};
+
+__device__ __forceinline__ void bstage_insert(BlockStage &S, int32_t *count, bool valid, int32_t c, int64_t w) {
+  if (!valid) return;
+  uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(STAGE_SLOTS - 1);
+  while (true) {
+    int32_t k = S.keys[s];
+    if (k == LD_EMPTY_KEY) {
+      k = atomicCAS(&S.keys[s], LD_EMPTY_KEY, c);
+      if (k == LD_EMPTY_KEY) {
+        S.list[atomicAdd(count, 1)] = (int32_t)s;
+        k = c;
+      }
+    }
+    if (k == c) {
+      atomicAdd((unsigned long long *)&S.vals[s], (unsigned long long)w);
+      return;
+    }
+    s = (s + 1) & (uint32_t)(STAGE_SLOTS - 1);
   }
-  __syncthreads();
-  BestX r = sb[0];
-  __syncthreads();
-  return r;
 }
 
-// One vertex of degree 129..1024 per block: lane-wise shared-atomic inserts
-// into a shared stage, then the candidates are read from its filled-slot
-// list (the distinct neighbour communities only) and the slots emptied again.
 template <typename W, int KIND>
 __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Args A) {
-  __shared__ Stage S;
+  __shared__ BlockStage S;
+  __shared__ BestX sb[BLOCK_THREADS / 32];
   __shared__ int moved_s;
-  stage_init(S);
+  for (int s = threadIdx.x; s < STAGE_SLOTS; s += BLOCK_THREADS) { S.keys[s] = LD_EMPTY_KEY; S.vals[s] = 0; }
+  if (threadIdx.x < 2) S.count[threadIdx.x] = 0;
+  __syncthreads();
   const W *w = (const W *)A.w;
-  int lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   int64_t count = *A.count;
   int64_t visits = 0, arcs = 0, moves = 0;
   i128 dq = 0;
-  for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
+  int par = 0;
+  for (int64_t t = blockIdx.x; t < count; t += gridDim.x, par ^= 1) {
     int32_t i = A.list[t];
     int64_t base = A.off[i];
     int32_t dg = A.deg[i];
@@ -499,51 +579,98 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Args A) {
     int32_t szd = KIND == KIND_MOVE ? A.size[d] : 0;
     int32_t bi = KIND == KIND_REFINE ? A.CB[i] : 0;
     int64_t m2 = m2_of(A, i);
-    for (int a0 = threadIdx.x & ~31; a0 < dg; a0 += blockDim.x) {  // warp-uniform trip count
-      int a = a0 + lane;
-      bool valid = a < dg;
-      int32_t c = 0;
-      int64_t wa = 0;
-      if (valid) {
-        int32_t j = A.col[base + a];
-        valid = j != i && (KIND != KIND_REFINE || A.CB[j] == bi);
-        if (valid) { c = A.C[j]; wa = (int64_t)w[base + a]; }
+    int32_t *cnt = &S.count[par];
+    for (int r0 = 0; r0 < dg; r0 += BLOCK_THREADS * BLOCK_UNROLL) {
+      int32_t j[BLOCK_UNROLL], c[BLOCK_UNROLL];
+      int64_t wa[BLOCK_UNROLL];
+      bool v[BLOCK_UNROLL];
+#pragma unroll
+      for (int u = 0; u < BLOCK_UNROLL; u++) {
+        int a = r0 + u * BLOCK_THREADS + tid;
+        v[u] = a < dg;
+        j[u] = v[u] ? A.col[base + a] : i;
+        wa[u] = v[u] ? (int64_t)w[base + a] : 0;
       }
-      stage_insert_lanes(S, valid, c, wa);
+#pragma unroll
+      for (int u = 0; u < BLOCK_UNROLL; u++) {
+        v[u] = v[u] && j[u] != i;
+        if (KIND == KIND_REFINE) v[u] = v[u] && A.CB[j[u]] == bi;
+      }
+#pragma unroll
+      for (int u = 0; u < BLOCK_UNROLL; u++) c[u] = v[u] ? A.C[j[u]] : 0;
+#pragma unroll
+      for (int u = 0; u < BLOCK_UNROLL; u++) bstage_insert(S, cnt, v[u], c[u], wa[u]);
     }
-    __syncthreads();
-    int n = S.count;
+    __syncthreads();  // B1: the stage holds K_{i->c} for every neighbour community c
+    int n = *cnt;
     BestX b{0, -1, 0, 0, 0, 0};
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
-      int32_t sl = S.list[q];
-      int32_t c = S.keys[sl];
-      int64_t kv = S.vals[sl];
-      if (c == d) { b.kd += kv; continue; }
-      int64_t sc = A.S[c];
-      i128 v = (i128)m2 * kv - (i128)Ki * sc;
-      if (ld_better(v, c, b.v, b.c)) { b.v = v; b.c = c; b.kc = kv; b.sc = sc; }
-    }
-    if (KIND == KIND_MOVE && b.c >= 0) b.szc = A.size[b.c];
-    b = block_bestx(b);
-    stage_clear(S);
-    if (threadIdx.x == 0) {
-      i128 g = decide_x<KIND>(A, i, d, Ki, Sd, szd, m2, b);
-      bool mv = g > 0;
-      if (KIND == KIND_MOVE && mv && !A.async_mode) {
-        int32_t slot = atomicAdd(&A.cnt->movers, 1);
-        A.movers[slot] = i;
-        A.mtarget[slot] = b.c;
-        if (A.mgain) { A.mgain[2 * slot] = (int64_t)(u128)g; A.mgain[2 * slot + 1] = (int64_t)((u128)g >> 64); }
+    for (int q0 = 0; q0 < n; q0 += BLOCK_THREADS * BLOCK_UNROLL) {
+      int32_t cc[BLOCK_UNROLL];
+      int64_t kv[BLOCK_UNROLL], sc[BLOCK_UNROLL];
+#pragma unroll
+      for (int u = 0; u < BLOCK_UNROLL; u++) {
+        int q = q0 + u * BLOCK_THREADS + tid;
+        cc[u] = -1;
+        kv[u] = 0;
+        if (q < n) {
+          int32_t sl = S.list[q];
+          cc[u] = S.keys[sl];
+          kv[u] = S.vals[sl];
+          S.keys[sl] = LD_EMPTY_KEY;
+          S.vals[sl] = 0;
+        }
       }
-      moved_s = mv;
-      visits++; arcs += dg; moves += mv; dq += g;
+#pragma unroll
+      for (int u = 0; u < BLOCK_UNROLL; u++) sc[u] = cc[u] >= 0 && cc[u] != d ? A.S[cc[u]] : 0;
+#pragma unroll
+      for (int u = 0; u < BLOCK_UNROLL; u++) {
+        if (cc[u] < 0) continue;
+        if (cc[u] == d) { b.kd += kv[u]; continue; }
+        i128 val = (i128)m2 * kv[u] - (i128)Ki * sc[u];
+        if (ld_better(val, cc[u], b.v, b.c)) { b.v = val; b.c = cc[u]; b.kc = kv[u]; b.sc = sc[u]; }
+      }
     }
-    __syncthreads();
-    if (KIND == KIND_MOVE && moved_s) mark_neighbours(A, i, base, dg, threadIdx.x, blockDim.x);
-    __syncthreads();
+    b = bestx_reduce<32>(b);
+    if (lane == 0) sb[wid] = b;
+    __syncthreads();  // B2: every warp's best is posted, every read slot emptied
+    if (tid == 0) S.count[par] = 0;
+    BestX r = sb[0];
+#pragma unroll
+    for (int k = 1; k < BLOCK_THREADS / 32; k++) bestx_merge(r, sb[k]);
+    // the winner's size matters only to the singleton rule (size_d == 1)
+    if (KIND == KIND_MOVE && !A.async_mode && r.c > d && szd == 1) r.szc = A.size[r.c];
+    bool mv;
+    if (A.async_mode) {
+      // in-place moves change the totals under the decision: one thread
+      // decides and applies, the block learns the outcome
+      if (tid == 0) {
+        i128 g = decide_x<KIND>(A, i, d, Ki, Sd, szd, m2, r);
+        moved_s = g > 0;
+        visits++; arcs += dg; moves += g > 0; dq += g;
+      }
+      __syncthreads();
+      mv = moved_s;
+    } else {
+      // snapshot schedule: the decision reads only the state at the start
+      // of the sub-sweep, so every thread reaches the same one; thread 0
+      // writes it
+      i128 g = 0;
+      if (tid == 0) {
+        g = decide_x<KIND>(A, i, d, Ki, Sd, szd, m2, r);
+        if (KIND == KIND_MOVE && g > 0) {
+          int32_t slot = atomicAdd(&A.cnt->movers, 1);
+          A.movers[slot] = i;
+          A.mtarget[slot] = r.c;
+          if (A.mgain) { A.mgain[2 * slot] = (int64_t)(u128)g; A.mgain[2 * slot + 1] = (int64_t)((u128)g >> 64); }
+        }
+        visits++; arcs += dg; moves += g > 0; dq += g;
+      }
+      mv = KIND == KIND_MOVE && would_move(d, Ki, Sd, szd, m2, r);
+    }
+    if (KIND == KIND_MOVE && mv) mark_neighbours(A, i, base, dg, tid, BLOCK_THREADS);
   }
-  if (threadIdx.x == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
-  if (KIND == KIND_MOVE && threadIdx.x == 0)
+  if (tid == 0) add_counters(A.cnt, KIND, visits, arcs, moves, dq);
+  if (KIND == KIND_MOVE && tid == 0)
     add_lmk(A.cnt, KT_BLOCK, visits, arcs, 40 * visits + (8 + (int64_t)sizeof(W)) * arcs);
 }
 
@@ -923,6 +1050,22 @@ Args make_args(leiden_handle *h, const LevelGraph &g) {
   return A;
 }
 
+// The block-bin kernels ask for the largest shared-memory carveout, so that
+// seven 29 KB stages fit on an SM (set once per device of the process).
+void block_kernel_carveout() {
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev >= 64) { cudaGetLastError(); return; }
+  if (done.load(std::memory_order_relaxed) & (1ull << dev)) return;
+  int co = cudaSharedmemCarveoutMaxShared;
+  cudaFuncSetAttribute(k_decide_block<int32_t, KIND_MOVE>, cudaFuncAttributePreferredSharedMemoryCarveout, co);
+  cudaFuncSetAttribute(k_decide_block<int64_t, KIND_MOVE>, cudaFuncAttributePreferredSharedMemoryCarveout, co);
+  cudaFuncSetAttribute(k_decide_block<int32_t, KIND_REFINE>, cudaFuncAttributePreferredSharedMemoryCarveout, co);
+  cudaFuncSetAttribute(k_decide_block<int64_t, KIND_REFINE>, cudaFuncAttributePreferredSharedMemoryCarveout, co);
+  cudaGetLastError();
+  done.fetch_or(1ull << dev, std::memory_order_relaxed);
+}
+
 template <int KIND>
 void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
   cudaStream_t s = h->stream;
@@ -942,7 +1085,10 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
       else ld_note_launch(), k_decide_warp<int32_t, KIND><<<grid, WARPS_PER_BLOCK * 32, 0, s>>>(A);
       if (KIND == KIND_MOVE) kt_end(h);
     } else if (b == BIN_BLOCK) {
-      int grid = sms * h->tune.block_blocks_per_sm;  // default 7: every slot (shared stage ~30 KB)
+      // default 7 blocks per SM: the shared stage (29 KB) and 71 registers
+      // for 128 threads admit 7, with the carveout set to favour shared memory
+      block_kernel_carveout();
+      int grid = sms * h->tune.block_blocks_per_sm;
       if (KIND == KIND_MOVE) kt_begin(h, KT_BLOCK);
       if (g.w64) ld_note_launch(), k_decide_block<int64_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
       else ld_note_launch(), k_decide_block<int32_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);

@@ -9,9 +9,10 @@
 namespace {
 
 // Largest vertex count the entry point accepts: the scratch holds one int64
-// community total per vertex id (32 MiB) plus five int64 counters.
+// community total per vertex id (32 MiB) plus NOALLOC_COUNTERS int64 words.
 constexpr int64_t NOALLOC_MAX_VERTICES = (int64_t)1 << 22;
-constexpr int64_t NOALLOC_WORDS = NOALLOC_MAX_VERTICES + 5;
+constexpr int64_t NOALLOC_COUNTERS = 6;
+constexpr int64_t NOALLOC_WORDS = NOALLOC_MAX_VERTICES + NOALLOC_COUNTERS;
 
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) int64_t g_noalloc_scratch[NOALLOC_WORDS];
@@ -24,15 +25,17 @@ int64_t *g_scratch_ptr[MAX_DEVICES] = {};
 std::mutex g_scratch_mu;
 
 // counters after the per-vertex totals
-enum { C_M2 = 0, C_SIGMA = 1, C_SQ_LO = 2, C_SQ_HI = 3, C_BAD = 4 };
+enum { C_M2 = 0, C_SIGMA = 1, C_SQ_LO = 2, C_SQ_HI = 3, C_BAD = 4, C_BADCOL = 5 };
 
 __global__ void k_na_clear(int64_t n, int64_t *scr) {
   for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) scr[i] = 0;
-  if (ld_gtid() < 5) scr[NOALLOC_MAX_VERTICES + ld_gtid()] = 0;
+  if (ld_gtid() < NOALLOC_COUNTERS) scr[NOALLOC_MAX_VERTICES + ld_gtid()] = 0;
 }
 
 // Warp per vertex: K_i (row sum) into Sigma[C_i]; intra-community weight; 2m.
-// A membership id outside [0, n) sets the C_BAD word and the vertex is skipped.
+// A membership id outside [0, n) sets the C_BAD word and the vertex is
+// skipped; a column outside [0, n) sets C_BADCOL (and is not read through).
+// Either one turns the call into LEIDEN_ERR_ARG.
 __global__ void k_na_rows(int64_t n, const int64_t *off, const int32_t *col, const int32_t *w, const int32_t *C,
                           int64_t *scr) {
   int lane = threadIdx.x & 31;
@@ -49,7 +52,11 @@ __global__ void k_na_rows(int64_t n, const int64_t *off, const int32_t *col, con
       int64_t wa = w ? (int64_t)w[a] : 1;
       k += wa;
       int32_t j = col[a];
-      if (j >= 0 && j < n && C[j] == c) intra += wa;
+      if (j < 0 || j >= n) {
+        atomicExch((unsigned long long *)&scr[NOALLOC_MAX_VERTICES + C_BADCOL], 1ull);
+        continue;
+      }
+      if (C[j] == c) intra += wa;
     }
     k = ld_warp_sum_i64(k);
     if (lane == 0 && k) atomicAdd((unsigned long long *)&scr[c], (unsigned long long)k);
@@ -70,22 +77,13 @@ __global__ void k_na_sq(int64_t n, int64_t *scr) {
   if ((threadIdx.x & 31) == 0) ld_atomic_add_i128((unsigned long long *)&scr[NOALLOC_MAX_VERTICES + C_SQ_LO], acc);
 }
 
-double na_i128_to_double(i128 x) {
-  bool neg = x < 0;
-  u128 u = neg ? (u128)(-(x + 1)) + 1 : (u128)x;
-  double hi = (double)(uint64_t)(u >> 64);
-  double lo = (double)(uint64_t)u;
-  double r = hi * 18446744073709551616.0 + lo;
-  return neg ? -r : r;
-}
-
 }  // namespace
 
 
 extern "C" leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *d_offsets, const int32_t *d_cols,
                                                    const int32_t *d_weights, const int32_t *d_membership,
                                                    void *cuda_stream, double *q_out) {
-  if (!q_out || n < 1 || !d_offsets || !d_membership) {
+  if (!q_out || n < 1 || !d_offsets || !d_cols || !d_membership) {
     set_handle_free_error("leiden_modularity_noalloc: null pointer or n < 1");
     return LEIDEN_ERR_ARG;
   }
@@ -95,8 +93,13 @@ extern "C" leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *d_o
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
+  if (e != cudaSuccess) {
     set_handle_free_error(std::string("leiden_modularity_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+    return LEIDEN_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= MAX_DEVICES) {
+    set_handle_free_error("leiden_modularity_noalloc: device ordinal " + std::to_string(dev) +
+                          " is beyond the 64 devices whose scratch address is cached");
     return LEIDEN_ERR_CUDA;
   }
   int64_t *scr = nullptr;
@@ -119,7 +122,7 @@ extern "C" leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *d_o
   ld_note_launch(), k_na_clear<<<grid_for(n, 256), 256, 0, s>>>(n, scr);
   ld_note_launch(), k_na_rows<<<sms * 16, 256, 0, s>>>(n, d_offsets, d_cols, d_weights, d_membership, scr);
   ld_note_launch(), k_na_sq<<<grid_for(n, 256), 256, 0, s>>>(n, scr);
-  int64_t cnt[5] = {0, 0, 0, 0, 0};
+  int64_t cnt[NOALLOC_COUNTERS] = {};
   e = cudaMemcpyAsync(cnt, scr + NOALLOC_MAX_VERTICES, sizeof(cnt), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -130,6 +133,10 @@ extern "C" leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *d_o
     set_handle_free_error("leiden_modularity_noalloc: membership id outside [0, n)");
     return LEIDEN_ERR_ARG;
   }
+  if (cnt[C_BADCOL]) {
+    set_handle_free_error("leiden_modularity_noalloc: column id outside [0, n)");
+    return LEIDEN_ERR_ARG;
+  }
   int64_t m2 = cnt[C_M2];
   if (m2 == 0) {
     *q_out = 0.0;
@@ -137,7 +144,7 @@ extern "C" leiden_status leiden_modularity_noalloc(int64_t n, const int64_t *d_o
   }
   i128 sq = (i128)(((u128)(uint64_t)cnt[C_SQ_HI] << 64) | (u128)(uint64_t)cnt[C_SQ_LO]);
   i128 num = (i128)m2 * cnt[C_SIGMA] - sq;
-  *q_out = na_i128_to_double(num) / ((double)m2 * (double)m2);
+  *q_out = i128_to_double(num) / ((double)m2 * (double)m2);
   return LEIDEN_OK;
 }
 

@@ -345,3 +345,145 @@ def test_full_rebuild_when_the_spill_arena_fills():
         assert np.array_equal(cg, cr)
         assert_same_state(gpu, ref)
     assert rebuilds >= 1
+
+
+def long_rows_graph(seed=8):
+    """Planted partition plus two hubs of degree 7000 and 5000, longer than
+    the 4096 arcs a block merges in shared memory, so batches that touch them
+    take the chunked merge over all SMs (and, without slack, the move of a
+    long row to the spill arena)."""
+    g = synth.planted_partition(12000, 60, 10, 0.25, seed)
+    src = np.repeat(np.arange(g.n), np.diff(g.off))
+    keep = src < g.col
+    edges = set(zip(src[keep].tolist(), g.col[keep].tolist()))
+    rng = np.random.default_rng(seed)
+    for hub, deg in ((3, 7000), (11000, 5000)):
+        for v in rng.choice(np.arange(100, 11900), deg, replace=False):
+            if int(v) != hub:
+                edges.add((min(hub, int(v)), max(hub, int(v))))
+    off, col, w = csr_from_edges(g.n, sorted(edges))
+    return synth.Graph(g.n, off, col, w.astype(np.int32))
+
+
+@pytest.mark.parametrize("slack", [0.25, 0.0])
+@pytest.mark.parametrize("mode", MODES, ids=["ND", "DS", "DF"])
+def test_long_rows_merge_bit_exact(slack, mode):
+    """Batches that delete and insert arcs of rows longer than 4096: the
+    chunked merge must give the oracle's CSR exactly, and the update the
+    oracle's membership, trace and state."""
+    gm, om = mode
+    g = long_rows_graph()
+    gpu = L.Leiden(g.n, g.off, g.col, g.w, slack=slack, min_slack=1)
+    ref = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    gpu.static()
+    ref.static()
+    cur = g
+    rng = np.random.default_rng(9)
+    for k in range(3):
+        dels, ins = synth.random_batch(cur, 600, seed=700 + k)
+        # plus edits on the hubs: delete 300 of their arcs, insert 400 new ones
+        extra_d, extra_i = [], []
+        for hub in (3, 11000):
+            nb = cur.col[cur.off[hub]:cur.off[hub + 1]]
+            taken = set(map(tuple, np.sort(dels[:, :2], axis=1).tolist())) | set(
+                map(tuple, np.sort(ins[:, :2], axis=1).tolist()))
+            for v in rng.choice(nb, 150, replace=False):
+                e = (min(hub, int(v)), max(hub, int(v)))
+                if e not in taken:
+                    extra_d.append([hub, int(v), 1])
+                    taken.add(e)
+            non = np.setdiff1d(np.arange(cur.n), np.append(nb, hub))
+            for v in rng.choice(non, 200, replace=False):
+                e = (min(hub, int(v)), max(hub, int(v)))
+                if e not in taken:
+                    extra_i.append([int(v), hub, 1])
+                    taken.add(e)
+        dels = np.concatenate([dels, np.array(extra_d, np.int32).reshape(-1, 3)])
+        ins = np.concatenate([ins, np.array(extra_i, np.int32).reshape(-1, 3)])
+        cg = gpu.update(dels, ins, gm)
+        cr = ref.update(dels, ins, om)
+        cur = synth.apply_batch_numpy(cur, dels, ins)
+        for a, b in zip(gpu.graph(), ref.graph()):
+            assert np.array_equal(a, b), f"batch {k}"
+        assert np.array_equal(gpu.affected(), ref.affected())
+        assert_same_trace(gpu, ref)
+        assert np.array_equal(cg, cr), f"batch {k}"
+        assert_same_state(gpu, ref)
+    assert np.diff(cur.off)[3] > 4096
+
+
+@pytest.mark.parametrize("case", ["gain_order", "state_before_batch", "tie"])
+def test_ds_best_community_pin_graphs_bit_exact(case):
+    """The hand-derived Delta-screening cases of the oracle pins (the
+    community c* a source of insertions marks) on the CUDA path."""
+    from tests.test_oracle_pins import _ds_graph
+
+    k, a, b, ha, hb = {"gain_order": (10, 10, 3, 2, 1), "state_before_batch": (4, 5, 4, 11, 10),
+                       "tie": (4, 5, 5, 1, 1)}[case]
+    n, off, col, w, blocks = _ds_graph(k, a, b)
+    gpu = L.Leiden(n, off, col, w)
+    ref = oracle.Oracle(n, off, col, w, schedule=oracle.SYNC)
+    assert np.array_equal(gpu.static(), ref.static())
+    ins = np.array([[0, blocks[0][2], ha], [0, blocks[1][2], hb]], np.int32)
+    cg = gpu.update(np.zeros((0, 3), np.int32), ins, L.LEIDEN_DS)
+    cr = ref.update(np.zeros((0, 3), np.int32), ins, oracle.DS)
+    assert np.array_equal(gpu.affected(), ref.affected())
+    assert np.array_equal(cg, cr)
+    assert_same_state(gpu, ref)
+
+
+@pytest.mark.parametrize("mode", MODES, ids=["ND", "DS", "DF"])
+def test_tracking_pin_graph_bit_exact(mode):
+    """The hand-derived tracking case of the oracle pins (a merge that keeps
+    the larger overlap's id, a split whose unmatched parts take the smallest
+    free ids in ascending order) on the CUDA path."""
+    from tests.test_oracle_pins import _tracking_graph
+
+    gm, om = mode
+    off, col, w, bridges = _tracking_graph()
+    gpu = L.Leiden(27, off, col, w, tau_refine=2.0)
+    ref = oracle.Oracle(27, off, col, w, schedule=oracle.SYNC, tau_refine=2.0)
+    assert np.array_equal(gpu.static(), ref.static())
+    dels = np.array([[u, v, 1] for u, v in bridges], np.int32)
+    ins = np.array([[u, v, 1] for u in range(0, 3) for v in range(21, 27)], np.int32)
+    cg = gpu.update(dels, ins, gm)
+    assert np.array_equal(cg, ref.update(dels, ins, om))
+    assert cg.tolist() == [21] * 3 + [4] * 5 + [8] * 6 + [1] * 3 + [2] * 4 + [21] * 6
+
+
+def _async_run(g, ref, updates=3):
+    """Static Leiden and `updates` DF updates of 1e-3|E| in the in-place mode
+    and in the oracle; yields (GPU Q, oracle Q) after each step, with every
+    community checked for connectivity."""
+    gpu = L.Leiden(g.n, g.off, g.col, g.w, deterministic=False)
+    cg = gpu.static()
+    ref.static()
+    assert disconnected_communities(g.off, g.col, cg) == 0
+    yield gpu.modularity(), ref.modularity()
+    cur = g
+    for k in range(updates):
+        dels, ins = synth.random_batch(cur, int(1e-3 * cur.edges), seed=78 + k)
+        cg = gpu.update(dels, ins, L.LEIDEN_DF)
+        ref.update(dels, ins, oracle.DF)
+        cur = synth.apply_batch_numpy(cur, dels, ins)
+        assert disconnected_communities(cur.off, cur.col, cg) == 0
+        yield gpu.modularity(), ref.modularity()
+
+
+def test_async_mode_quality_rmat17_against_the_sequential_oracle():
+    """In-place moves on R-MAT scale 17: connected communities and Q within
+    0.005 of the oracle's SEQ schedule (the paper's loop order), for static
+    Leiden and three DF updates."""
+    g = synth.rmat(17, seed=41)
+    for q_gpu, q_seq in _async_run(g, oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SEQ)):
+        assert q_gpu >= q_seq - 0.005
+
+
+@pytest.mark.parametrize("seed", [38, 39, 40])
+def test_async_mode_quality_rmat16_against_the_snapshot_oracle(seed):
+    """In-place moves on R-MAT scale 16: connected communities and Q within
+    0.005 of the oracle's snapshot schedule (the schedule the deterministic
+    mode reproduces bit for bit), for static Leiden and three DF updates."""
+    g = synth.rmat(16, seed=seed)
+    for q_gpu, q_sync in _async_run(g, oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)):
+        assert q_gpu >= q_sync - 0.005
