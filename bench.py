@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--mean-gap-us", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=200.0)
+    ap.add_argument("--ncu-summary", default=None, metavar="CSV",
+                    help="write the machine-read DRAM-traffic summary and the launch list from an ncu CSV")
+    ap.add_argument("--ncu-command", default="", help="the ncu command line that made the CSV (recorded)")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     return ap.parse_args()
@@ -317,9 +320,43 @@ def timed_update(stream, fn, flush=None):
 
 def step_record(ms, st):
     """Per-step breakdown kept in the line: time, passes, local-moving
-    iterations, CSR rebuilds and device (re)allocations of the call."""
-    return {"ms": round(ms, 4), "passes": int(st["passes"]), "lm_iterations": int(st["lm_iterations"]),
-            "rebuilds": int(st["rebuilds"]), "affected": int(st["affected"])}
+    iterations, refinement visits, CSR rebuilds, the affected set and the
+    device time of each phase."""
+    from paper_2410_15451_gb300 import leiden as L
+
+    rec = {"ms": round(ms, 4), "passes": int(st["passes"]), "lm_iterations": int(st["lm_iterations"]),
+           "refine_visits": int(st["refine_vertices"]), "rebuilds": int(st["rebuilds"]),
+           "affected": int(st["affected"])}
+    if any(st["phase_ms"]):
+        rec["phase_ms"] = {k: round(v, 4) for k, v in zip(L.PHASES, st["phase_ms"])}
+    return rec
+
+
+def roofline_step(stats_list, ms_per_step):
+    """Roofline of the whole step: the algorithmic bytes the library counts
+    per phase (leiden_stats.phase_bytes), summed, over the event-timed step;
+    and per phase its bytes over its own device time (phase_ms)."""
+    from paper_2410_15451_gb300 import leiden as L
+
+    peak, src = hbm_peak()
+    k = len(stats_list)
+    if not k:
+        return None
+    phases = {}
+    for j, name in enumerate(L.PHASES):
+        b = sum(s["phase_bytes"][j] for s in stats_list) / k
+        ms = sum(s["phase_ms"][j] for s in stats_list) / k
+        gbs = b / (ms / 1e3) / 1e9 if ms > 0 else None
+        phases[name] = {"bytes": b, "ms": ms, "achieved": gbs, "frac": gbs / peak if gbs else None}
+    tot = sum(p["bytes"] for p in phases.values())
+    ach = tot / (ms_per_step / 1e3) / 1e9
+    ph_ms = sum(p["ms"] for p in phases.values())
+    for p in phases.values():
+        p["share_of_time"] = p["ms"] / ph_ms if ph_ms > 0 else None
+    return {"bound": "hbm", "bytes_per_step": tot, "ms_per_step": ms_per_step, "achieved": ach, "peak": peak,
+            "unit": "GB/s", "frac": ach / peak, "phases": phases,
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)" if src == "measured"
+            else "fallback 6.8 TB/s"}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -339,10 +376,11 @@ def run_ours(args, rank, world, local_rank):
     size = max(1, int(round(args.batch_frac * E)))
     W, K = args.warmup, args.steps
     batches = make_batches(g, stream_batches(args), size, seed + 5)
-    # collect_stats=2: an event pair on the stream around every launch of the
-    # local-moving kernels (the roofline kernels); no added syncs
+    # collect_stats=3: events at the phase boundaries (the step roofline) and
+    # an event pair around every launch of the local-moving kernels (the
+    # kernel roofline); neither adds a host sync
     gpu = L.Leiden(g.n, g.off, g.col, g.w, deterministic=not args.async_mode, cuda_stream=stream.cuda_stream,
-                   collect_stats=2)
+                   collect_stats=3)
     gpu.static()
     dev_batches = [(torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)) for d, i in batches]
     d_out = torch.empty(g.n, dtype=torch.int32, device=dev)
@@ -450,8 +488,8 @@ def run_ours(args, rank, world, local_rank):
 
 
 LMK_NAMES = ("k_decide_warp", "k_decide_block", "k_huge_scan")
-ROOFLINE_PROFILE = os.path.join(ROOT, "profiles", "lm_kernels_rmat22_df1e-3.md")
-ROOFLINE_SOURCE = os.path.join(ROOT, "paper_2410_15451_gb300", "csrc", "move.cu")
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "kernels_dram_rmat22_df1e-3.json")
+CSRC = os.path.join(ROOT, "paper_2410_15451_gb300", "csrc")
 
 
 def source_code_sha256(path):
@@ -469,22 +507,88 @@ def source_code_sha256(path):
 
 
 def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary of the
-    local-moving kernels (lines `traffic_bytes_per_launch[<kernel>]: N` and
-    `move_cu_sha256: H`, H from source_code_sha256); None when absent or when
-    the kernel source changed since the capture."""
+    """DRAM bytes per launch of the local-moving launches of `kernel` from the
+    machine-written summary of one ncu capture (written by --ncu-summary);
+    None when absent or when move.cu changed since the capture."""
+    try:
+        d = json.load(open(TRAFFIC_JSON))
+        sha = source_code_sha256(os.path.join(CSRC, "move.cu"))
+    except (OSError, ValueError):
+        return None
+    if d.get("source_sha256", {}).get("move.cu") != sha:
+        return None
+    k = d.get("local_moving", {}).get(kernel)
+    return float(k["traffic_bytes_per_launch"]) if k else None
+
+
+def ncu_summary(csv_path, command, out_json=TRAFFIC_JSON,
+                out_md=os.path.join(ROOT, "profiles", "launches_df_update_rmat22_batch1e-3.md")):
+    """Reads the CSV of one `ncu --metrics gpu__time_duration.sum,
+    dram__bytes_read.sum,dram__bytes_write.sum --csv` capture and writes
+    profiles/kernels_dram_rmat22_df1e-3.json (machine-read by the roofline)
+    and profiles/launches_df_update_rmat22_batch1e-3.md (the launch list)."""
+    import csv
     import re
 
-    try:
-        text = open(ROOFLINE_PROFILE).read()
-        sha = source_code_sha256(ROOFLINE_SOURCE)
-    except OSError:
-        return None
-    t = re.search(r"traffic_bytes_per_launch\[" + re.escape(kernel) + r"\]:\s*([0-9.eE+]+)", text)
-    h = re.search(r"move_cu_sha256:\s*([0-9a-f]{64})", text)
-    if not t or not h or h.group(1) != sha:
-        return None
-    return float(t.group(1))
+    lines = open(csv_path).read().splitlines()
+    start = next(i for i, ln in enumerate(lines) if ln.startswith('"ID"'))
+    rows = list(csv.DictReader(lines[start:]))
+    launches = {}
+    for r in rows:
+        ent = launches.setdefault(r["ID"], {"name": r["Kernel Name"]})
+        v = r["Metric Value"].replace(",", "")
+        unit = r["Metric Unit"]
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9,
+                 "nsecond": 1e-3, "ns": 1e-3, "usecond": 1.0, "us": 1.0, "msecond": 1e3, "ms": 1e3}[unit]
+        ent[r["Metric Name"]] = float(v) * scale
+
+    def base(name):
+        name = re.sub(r"\(.*$", "", name.replace("void ", "").replace("<unnamed>::", "")
+                      .replace("(anonymous namespace)::", ""))
+        return name.strip()
+
+    per = {}
+    for ent in launches.values():
+        k = base(ent["name"])
+        p = per.setdefault(k, {"launches": 0, "us": 0.0, "read": 0.0, "write": 0.0})
+        p["launches"] += 1
+        p["us"] += ent.get("gpu__time_duration.sum", 0.0)
+        p["read"] += ent.get("dram__bytes_read.sum", 0.0)
+        p["write"] += ent.get("dram__bytes_write.sum", 0.0)
+    tot_us = sum(p["us"] for p in per.values())
+    lm = {}
+    for name in LMK_NAMES:
+        sel = [p for k, p in per.items() if re.match(re.escape(name) + r"<[^,]+, 0>$", k)]
+        n = sum(p["launches"] for p in sel)
+        if n:
+            rd, wr = sum(p["read"] for p in sel), sum(p["write"] for p in sel)
+            lm[name] = {"launches": n, "dram_read_bytes_per_launch": rd / n, "dram_write_bytes_per_launch": wr / n,
+                        "traffic_bytes_per_launch": (rd + wr) / n, "ncu_us_per_launch": sum(p["us"] for p in sel) / n}
+    out = {"command": command, "workload": "R-MAT scale 22, DF updates of 1e-3|E| (the benchmark's timed steps)",
+           "note": "one pass per launch (three metrics); ncu times are serialised and cold-cache: compare shares",
+           "source_sha256": {f: source_code_sha256(os.path.join(CSRC, f)) for f in sorted(os.listdir(CSRC))},
+           "local_moving": lm,
+           "kernels": {k: {"launches": p["launches"], "ncu_us": p["us"], "share": p["us"] / tot_us,
+                           "dram_read_bytes": p["read"], "dram_write_bytes": p["write"]}
+                       for k, p in sorted(per.items(), key=lambda kv: -kv[1]["us"])},
+           "total_ncu_us": tot_us, "total_dram_bytes": sum(p["read"] + p["write"] for p in per.values())}
+    with open(out_json, "w") as f:
+        json.dump(out, f, indent=1)
+    md = ["# Launch list: DF updates on R-MAT scale 22, batches of 1e-3|E|", "",
+          "Written by `python bench.py --ncu-summary <csv>` from one capture of the benchmark's timed steps",
+          "(one pass per launch; times are serialised and cold-cache under ncu, so compare shares).", "",
+          "Command (repository root, one GB300):", "", "    " + command, "",
+          f"{len(launches)} launches, {tot_us / 1e3:.2f} ms summed, "
+          f"{out['total_dram_bytes'] / 1e6:.1f} MB of DRAM traffic.", "",
+          "| kernel | launches | total ms | share | DRAM MB |", "|---|---:|---:|---:|---:|"]
+    for k, p in out["kernels"].items():
+        if p["share"] < 0.004:
+            continue
+        md.append(f"| {k} | {p['launches']} | {p['ncu_us'] / 1e3:.3f} | {100 * p['share']:.1f}% | "
+                  f"{(p['dram_read_bytes'] + p['dram_write_bytes']) / 1e6:.1f} |")
+    with open(out_md, "w") as f:
+        f.write("\n".join(md) + "\n")
+    return out
 
 
 def roofline_kernels(stats_list):
@@ -528,7 +632,7 @@ def batched_graphs(count, seed):
             for k, (n, d) in enumerate(zip(ns, ds))]
 
 
-def run_batched(args):
+def batched_record(args, warmup=None, steps=None):
     """DF updates of every graph (1e-3 of its edges, 80/20) processed by one
     batched call versus one call per graph, both on device-resident batches;
     the memberships of the two must be equal graph by graph."""
@@ -542,7 +646,8 @@ def run_batched(args):
     seed = synth.BASE_SEED + 3
     t0 = time.time()
     gs = batched_graphs(args.graphs, seed)
-    W, K = args.warmup, args.steps
+    W = args.warmup if warmup is None else warmup
+    K = args.steps if steps is None else steps
     sizes = [max(1, int(round(1e-3 * g.off[-1] / 2))) for g in gs]
     per_graph = [make_batches(g, W + K, sz, seed + 1000 + k) for k, (g, sz) in enumerate(zip(gs, sizes))]
     gen_s = time.time() - t0
@@ -602,25 +707,31 @@ def run_batched(args):
     batch.close()
     bat_total = float(np.sum(bat_ms))
     seq_total = float(np.sum(seq_ms))
-    line = {
-        "metric": "batched DF update edges/s (all graphs in one call) vs one call per graph", "impl": "batched",
-        "value": edges_per_step * K / (bat_total / 1e3), "unit": "edges/s", "n_gpus": 1, "steps": K, "warmup": W,
-        "ms_per_step": bat_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"{len(gs)} planted-partition graphs, n log-uniform in [1e3, 2e5], mean degree "
-                               f"log-uniform in [4, 64], blocks of 100, mixing 0.2; DF updates of 1e-3 of each "
-                               f"graph's edges (80/20)", "graphs": len(gs), "vertices": int(sum(g.n for g in gs)),
-                   "edges": int(sum(g.off[-1] for g in gs) // 2), "batch_edges_per_step": edges_per_step},
-        "sequential": {"value": edges_per_step * K / (seq_total / 1e3), "ms_per_step": seq_total / K,
+    return {
+        "workload": f"{len(gs)} planted-partition graphs, n log-uniform in [1e3, 2e5], mean degree log-uniform in "
+                    f"[4, 64], blocks of 100, mixing 0.2; DF updates of 1e-3 of each graph's edges (80/20)",
+        "graphs": len(gs), "vertices": int(sum(g.n for g in gs)), "edges": int(sum(g.off[-1] for g in gs) // 2),
+        "batch_edges_per_step": edges_per_step, "steps": K, "warmup": W,
+        "edges_per_s": edges_per_step * K / (bat_total / 1e3), "ms_per_step": bat_total / K,
+        "p50_ms": float(np.percentile(bat_ms, 50)), "p99_ms": float(np.percentile(bat_ms, 99)),
+        "sequential": {"edges_per_s": edges_per_step * K / (seq_total / 1e3), "ms_per_step": seq_total / K,
                        "p50_ms_per_graph": float(np.percentile(seq_lat, 50)),
                        "p99_ms_per_graph": float(np.percentile(seq_lat, 99))},
         "speedup_vs_sequential": seq_total / bat_total,
-        "batched_p99_ms": float(np.percentile(bat_ms, 99)),
         "parity_with_sequential": parity, "gpu_launches": launches, "static_s_batched": static_s,
         "setup_s": gen_s,
     }
+
+
+def run_batched(args):
+    rep = batched_record(args)
+    line = {
+        "metric": "batched DF update edges/s (all graphs in one call) vs one call per graph", "impl": "batched",
+        "value": rep["edges_per_s"], "unit": "edges/s", "n_gpus": 1, "steps": rep["steps"], "warmup": rep["warmup"],
+        "ms_per_step": rep["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int64", "data": "synthetic", "config": {"workload": rep["workload"]}, "result": rep}
     print(json.dumps(line), flush=True)
-    return 0 if parity else 1
+    return 0 if rep["parity_with_sequential"] else 1
 
 
 # ----------------------------------------------------------------------------- autotuner
@@ -788,7 +899,7 @@ def large_record(args, stream, dev):
     n_del = size - n_ins
     batches = [(dels[k * n_del:(k + 1) * n_del], ins[k * n_ins:(k + 1) * n_ins]) for k in range(nb)]
     t0 = time.time()
-    h = L.Leiden(g.n, g.off, g.col, g.w, cuda_stream=stream.cuda_stream, collect_stats=2)
+    h = L.Leiden(g.n, g.off, g.col, g.w, cuda_stream=stream.cuda_stream, collect_stats=3)
     rep["create_s"] = time.time() - t0
     rep["static_ms"] = timed_update(stream, lambda: L.leiden_static(h.h, None))
     # sampled rows: touched vertices and their rows in G^0
@@ -802,15 +913,18 @@ def large_record(args, stream, dev):
     gc.collect()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
     d_out = torch.empty(n, dtype=torch.int32, device=dev)
-    ms, steps = [], []
+    ms, steps, stats_list = [], [], []
     launches0 = L.leiden_kernel_launches()
     for d, i in batches:
         dd, di = torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)
         torch.cuda.synchronize()
         ms.append(timed_update(stream, lambda: L.leiden_update_device(h.h, dd, d.shape[0], di, i.shape[0],
                                                                       L.LEIDEN_DF, d_out), flush))
-        steps.append(step_record(ms[-1], h.stats()))
+        st_k = h.stats()
+        steps.append(step_record(ms[-1], st_k))
+        stats_list.append(st_k)
     rep["gpu_launches"] = L.leiden_kernel_launches() - launches0
+    rep["roofline_step"] = roofline_step(stats_list, float(np.mean(ms)))
     del flush
     rep.update(batch_edges=size, df_ms_mean=float(np.mean(ms)), df_ms_p50=float(np.percentile(ms, 50)),
                df_ms_p99=float(np.percentile(ms, 99)), df_edges_per_s=size / (np.mean(ms) / 1e3), steps=steps)
@@ -953,10 +1067,15 @@ def run_stability(args):
 
 
 # ----------------------------------------------------------------------------- serving configuration
-def run_serve(args):
-    """Resident R-MAT graphs in a server; update requests (sizes log-uniform in
-    [10, 1e5] edges, 80/20, graph uniform) arrive with exponential gaps and
-    run on `slots` workers.  Latency = submission to completion."""
+def serve_record(args):
+    """Resident R-MAT graphs in a server (scales uniform in --serve-scales);
+    update requests (sizes log-uniform in [10, 1e5] edges, 80/20, graph
+    uniform) arrive with exponential gaps and run on `slots` workers.
+    Latency = submission to completion; service = start to completion.
+    Phase 1 is the configuration's arrival process (mean gap --mean-gap-us);
+    phase 2 offers half of the throughput phase 1 measured, so that its
+    latencies show service rather than queueing."""
+    import gc
     import threading
 
     from paper_2410_15451_gb300 import leiden as L
@@ -967,10 +1086,12 @@ def run_serve(args):
     t0 = time.time()
     scales = rng.integers(lo, hi + 1, args.serve_graphs)
     gs = [synth.rmat(int(sc), 16, 0.57, 0.19, 0.19, synth.BASE_SEED + 4 + 17 * k) for k, sc in enumerate(scales)]
-    R = args.requests
+    R1, R2 = args.requests, max(1, args.requests // 5)
+    R = R1 + R2
     which = rng.integers(0, len(gs), R)
     sizes = np.exp(rng.uniform(np.log(10.0), np.log(1e5), R)).astype(np.int64)
-    gaps = rng.exponential(args.mean_gap_us * 1e-6, R)
+    gaps1 = rng.exponential(args.mean_gap_us * 1e-6, R1)
+    unit_gaps2 = rng.exponential(1.0, R2)
     # per graph: all its edits drawn at once (distinct, valid in sequence), then cut into its requests
     batches = [None] * R
     for k, g in enumerate(gs):
@@ -987,65 +1108,80 @@ def run_serve(args):
             di += n_del
             ii += n_ins
     gen_s = time.time() - t0
+    nv, ne = int(sum(g.n for g in gs)), int(sum(g.off[-1] for g in gs) // 2)
     srv = L.LeidenServer(int(args.serve_budget_gb * 2**30), slots=args.slots)
     ids = [srv.add_graph(g.n, g.off, g.col, g.w) for g in gs]
+    del gs
+    gc.collect()
     t1 = time.time()
-    while srv.stats()["graphs_resident"] + 0 < len(gs):
+    while srv.stats()["graphs_resident"] < len(ids):
         st = srv.stats()
-        if st["graphs_waiting"] == 0 and st["graphs_resident"] < len(gs):
+        if st["graphs_waiting"] == 0 and st["graphs_resident"] < len(ids):
             raise RuntimeError("some graphs failed admission")
         time.sleep(0.05)
     admit_s = time.time() - t1
-    tickets = [None] * R
-    submit_at = np.zeros(R)
-    lat = np.zeros(R)
-    svc = np.zeros(R)
-    done = threading.Event()
 
-    def waiter():
-        for r in range(R):
-            while tickets[r] is None:
-                time.sleep(0.0002)
-            _, lat[r], svc[r] = srv.wait(tickets[r])
-        done.set()
+    def arrivals(first, gaps):
+        """Submit requests first.. with the given gaps; wait for all of them."""
+        n = len(gaps)
+        tickets = [None] * n
+        submit_at = np.zeros(n)
+        lat = np.zeros(n)
+        svc = np.zeros(n)
 
-    th = threading.Thread(target=waiter)
-    th.start()
+        def waiter():
+            for r in range(n):
+                while tickets[r] is None:
+                    time.sleep(0.0002)
+                _, lat[r], svc[r] = srv.wait(tickets[r])
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        start = time.perf_counter()
+        due = start
+        for r in range(n):
+            due += gaps[r]
+            while time.perf_counter() < due:
+                pass
+            submit_at[r] = time.perf_counter()
+            d, i = batches[first + r]
+            tickets[r] = srv.submit(ids[which[first + r]], d, i, L.LEIDEN_DF)
+        th.join()
+        wall = float(np.max(submit_at + lat / 1e3)) - start
+        edges = int(sizes[first:first + n].sum())
+        return {"requests": n, "edges": edges, "edges_per_s": edges / wall, "wall_s": wall,
+                "arrival_span_s": float(submit_at[-1] - start),
+                "offered_edges_per_s": edges / max(float(np.sum(gaps)), 1e-9),
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "service_p50_ms": float(np.percentile(svc, 50)), "service_p99_ms": float(np.percentile(svc, 99))}
+
     clocks = ClockSampler(0)
     clocks.start()
     launches0 = L.leiden_kernel_launches()
-    start = time.perf_counter()
-    due = start
-    for r in range(R):
-        due += gaps[r]
-        while time.perf_counter() < due:
-            pass
-        submit_at[r] = time.perf_counter()
-        d, i = batches[r]
-        tickets[r] = srv.submit(ids[which[r]], d, i, L.LEIDEN_DF)
-    done.wait()
-    th.join()
+    p1 = arrivals(0, gaps1)
+    cap = p1["edges_per_s"]
+    gap2 = float(np.mean(sizes[R1:])) / (0.5 * cap)
+    p2 = arrivals(R1, unit_gaps2 * gap2)
     launches = L.leiden_kernel_launches() - launches0
     clk = clocks.stop()
-    end = float(np.max(submit_at + lat / 1e3))
-    wall = end - start
-    edges = int(sizes.sum())
     srv.close()
+    return {"workload": f"{len(ids)} R-MAT graphs (scales uniform in {lo}..{hi}, edge factor 16), DF update "
+                        f"requests with exponential gaps, sizes log-uniform in [10, 1e5] edges (80/20), graph "
+                        f"uniform: {R1} at a mean gap of {args.mean_gap_us:g} us, then {R2} at half the "
+                        f"measured capacity",
+            "graphs": len(ids), "vertices": nv, "edges": ne, "slots": args.slots, "budget_gb": args.serve_budget_gb,
+            "configured_load": p1, "half_capacity_load": dict(p2, mean_gap_us=gap2 * 1e6),
+            "gpu_launches": launches, "clocks": clk, "setup_s": gen_s, "admission_s": admit_s}
+
+
+def run_serve(args):
+    rep = serve_record(args)
+    p1 = rep["configured_load"]
     line = {
         "metric": "served DF update latency p50/p99 and edges/s (resident R-MAT graphs, Poisson arrivals)",
-        "impl": "served", "value": edges / wall, "unit": "edges/s", "n_gpus": 1, "steps": R, "warmup": 0,
-        "ms_per_step": float(np.mean(lat)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"{len(gs)} R-MAT graphs (scales uniform in {lo}..{hi}, edge factor 16), {R} DF "
-                               f"update requests, exponential gaps of mean {args.mean_gap_us:g} us, sizes "
-                               f"log-uniform in [10, 1e5] edges (80/20), graph uniform",
-                   "slots": args.slots, "budget_gb": args.serve_budget_gb,
-                   "vertices": int(sum(g.n for g in gs)), "edges": int(sum(g.off[-1] for g in gs) // 2)},
-        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-        "service_p50_ms": float(np.percentile(svc, 50)), "service_p99_ms": float(np.percentile(svc, 99)),
-        "arrival_span_s": float(submit_at[-1] - start), "wall_s": wall, "batch_edges": edges,
-        "gpu_launches": launches, "clocks": clk, "setup_s": gen_s, "admission_s": admit_s,
-    }
+        "impl": "served", "value": p1["edges_per_s"], "unit": "edges/s", "n_gpus": 1, "steps": p1["requests"],
+        "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": {"workload": rep["workload"]}, "result": rep}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -1057,6 +1193,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.ncu_summary:
+        ncu_summary(args.ncu_summary, args.ncu_command)
+        return 0
     # the oracle baseline runs in a spawned process, started before any GPU call
     base = None
     plain = not (args.batched or args.serve or args.stability or args.ablation or args.large or args.autotune)
@@ -1107,6 +1246,7 @@ def main():
                     "d2h_bytes_per_step": r["n"] * 4, "p99_ms": r["e2e_p99"]},
             "roofline": dom,
             "roofline_lm_kernels": lmk,
+            "roofline_step": roofline_step(r["lm_stats"], r["mean_ms"]),
             "gpu_launches": r["gpu_launches"],
             "cpu_baseline": cb,
             "clocks": r["clk"],

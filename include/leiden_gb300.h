@@ -15,7 +15,7 @@
  *  - Host pointers unless the name ends in _device; the library copies host
  *    inputs before returning and never keeps a caller pointer.
  *  - Vertex ids are int32 in [0, n); n is fixed for the life of a handle
- *    (the paper adds or removes no vertices, Section 4.1.3).  Edge weights
+ *    (the paper adds or removes no vertices: Evaluation, "Batch generation").  Edge weights
  *    are positive int32; degrees and community totals are exact int64.
  *  - Errors are reported by status code only; no exception or abort crosses
  *    the ABI.  leiden_last_error() gives a message for the last failure.
@@ -37,7 +37,7 @@ typedef enum {
   LEIDEN_ERR_BATCH = 2,    /* invalid batch; the handle is left unchanged        */
   LEIDEN_ERR_OOM = 3,      /* device memory exhausted                            */
   LEIDEN_ERR_CUDA = 4,     /* a CUDA call failed (the message names it)          */
-  LEIDEN_ERR_TIMEOUT = 5,  /* a bounded device wait gave up                      */
+  LEIDEN_ERR_TIMEOUT = 5,  /* a bounded wait gave up (leiden_server_wait_for)    */
   LEIDEN_ERR_STATE = 6     /* call order violated (update before static)         */
 } leiden_status;
 
@@ -50,9 +50,10 @@ typedef struct {
 } leiden_edge;
 
 typedef struct {
-  double tau;             /* iteration tolerance of local moving, 1e-2 (Section 4.1.2)   */
+  double tau;             /* iteration tolerance of local moving, 1e-2 (Evaluation, "Configuration") */
   double tau_drop;        /* TOLERANCE_DECLINE_FACTOR, 10                                 */
-  double tau_refine;      /* refinement tolerance tau_re, 0.6 (Section 3.3)               */
+  double tau_refine;      /* refinement tolerance tau_re, 0.6 (Approach, "Minimizing     */
+                          /*    communities to refine")                                  */
   int32_t max_iterations; /* MAX_ITERATIONS per pass, 20                                  */
   int32_t max_passes;     /* MAX_PASSES, 10                                               */
   int32_t deterministic;  /* 1: snapshot schedule, bit-identical run to run (default);    */
@@ -62,11 +63,14 @@ typedef struct {
                           /*    (the in-place schedule uses at least 16)                  */
   double slack;           /* spare CSR capacity per row as a fraction of its degree, 0.25 */
   int32_t min_slack;      /* minimum spare arcs per row, 4                                */
-  int32_t collect_stats;  /* bit 1: time each phase with CUDA events (adds syncs);        */
+  int32_t collect_stats;  /* bit 1: time each phase with CUDA events recorded at the     */
+                          /*    phase boundaries, read after the call's last host sync    */
+                          /*    (no added syncs);                                         */
                           /* bit 2: time each launch of the local-moving kernels          */
                           /*    with an event pair on the stream (no added syncs); 0      */
   int32_t split_all;      /* ablation: split every community that is not refined, not     */
-                          /*    only the changed ones (Section 4.1.3 splits changed); 0   */
+                          /*    only the changed ones (Approach, "Minimizing communities */
+                          /*    to split", splits the changed ones); 0                   */
   int32_t converge_any;   /* ablation: leave the pass loop when l_i <= 1 OR no community  */
                           /*    was refined (the text's reading; the pseudocode's AND     */
                           /*    is the default); 0                                        */
@@ -85,15 +89,17 @@ typedef struct {
   int64_t refine_vertices;     /* vertex visits in refinement                            */
   int64_t refine_arcs;         /* arcs scanned in refinement                             */
   int64_t aggregate_arcs;      /* arcs read by aggregation                               */
-  int64_t affected;            /* |dV| after marking (pass 1 affected set)               */
+  int64_t affected;            /* |dV|: the affected set of pass 1 (all n for static/ND) */
   int64_t communities;         /* communities in C^t                                     */
   int64_t batch_arcs;          /* arcs applied (both directions, after deduplication)    */
-  double ms_total;             /* wall time of the call on the stream                    */
-  double ms_batch;             /* batch canonicalisation, apply, marking (collect_stats) */
-  double ms_move;              /* local moving (collect_stats)                           */
-  double ms_refine;            /* renumber + split + refinement (collect_stats)          */
-  double ms_aggregate;         /* dense renumber + aggregation (collect_stats)           */
-  double ms_track;             /* lookup + tracking (collect_stats)                      */
+  /* Phase times (collect_stats bit 1; device time on the stream between the
+   * phase boundaries, ms): */
+  double ms_total;             /* the whole call: the sum of the six phases below        */
+  double ms_batch;             /* phase_ms[LEIDEN_PHASE_BATCH]                           */
+  double ms_move;              /* phase_ms[LEIDEN_PHASE_MOVE]                            */
+  double ms_refine;            /* phase_ms[LEIDEN_PHASE_REFINE]                          */
+  double ms_aggregate;         /* phase_ms[LEIDEN_PHASE_AGGREGATE]                       */
+  double ms_track;             /* phase_ms[LEIDEN_PHASE_TRACK]                           */
   /* The local-moving kernels, [0] vertices of degree <= 128 (a warp or 8 lanes
    * each), [1] degree 129..1024 (a block each), [2] the arc scan of vertices
    * above 1024 arcs (chunks spread over all SMs): */
@@ -106,7 +112,25 @@ typedef struct {
                                /* and size of C)                                         */
   double lmk_ms[3];            /* summed device time of the timed launches               */
   int64_t rebuilds;            /* full CSR rebuilds (the spill arena was full)           */
+  /* Per phase (index: leiden_phase): device time (collect_stats bit 1, else 0)
+   * and algorithmic bytes (always), the bytes each phase must move as counted
+   * from its work counters: per vertex of a level, per arc scanned, per batch
+   * arc, per move, with the per-unit sizes of each phase's arrays (the byte
+   * model is documented with the kernels).  Bytes / time is the phase's
+   * achieved bandwidth for a roofline of the whole call. */
+  double phase_ms[6];
+  int64_t phase_bytes[6];
 } leiden_stats;
+
+/* Phases of a call, as timed and counted in leiden_stats. */
+typedef enum {
+  LEIDEN_PHASE_BATCH = 0,     /* batch canonicalisation, sort, merge-apply, marking, weights */
+  LEIDEN_PHASE_MOVE = 1,      /* local moving (Alg. leidenlm), all passes                     */
+  LEIDEN_PHASE_SPLIT = 2,     /* subset renumbering and splitting (Alg. leidensr, leidensp)   */
+  LEIDEN_PHASE_REFINE = 3,    /* refinement (Alg. leidenre)                                   */
+  LEIDEN_PHASE_AGGREGATE = 4, /* community count, dense renumbering, lookup, aggregation      */
+  LEIDEN_PHASE_TRACK = 5      /* final lookup and tracking (Alg. leidentr)                    */
+} leiden_phase;
 
 typedef struct leiden_handle leiden_handle;
 
@@ -132,7 +156,9 @@ void leiden_default_params(leiden_params *p);
 void leiden_default_tuning(leiden_tuning *t);
 leiden_status leiden_set_tuning(leiden_handle *h, const leiden_tuning *t);
 
-/* Create a handle for the graph G^0 given as symmetric CSR on the host:
+/* Create a handle for the graph G^0 -- the graph before the first batch in
+ * the problem statement of Alg. "naive", "delta" and "frontier" (Appendix
+ * A.1-A.3, whose G^{t-1} it is at t = 1) -- given as symmetric CSR on the host:
  * offsets[n+1] (int64, offsets[0] = 0), cols[offsets[n]] (int32, in [0, n)),
  * weights[offsets[n]] (int32 > 0, NULL = unit).  Rows need not be sorted;
  * self-loops and repeated arcs are rejected (LEIDEN_ERR_ARG).  The graph is
@@ -143,7 +169,7 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
                             const int32_t *cols, const int32_t *weights, void *cuda_stream,
                             leiden_handle **out);
 
-/* Static Leiden (Section 4.1.4 baseline, Alg. "leiden" with C^{t-1} = singletons,
+/* Static Leiden (the baseline of Evaluation, "Measurement"; Alg. "leiden" with C^{t-1} = singletons,
  * every vertex affected, every community refined) on the current graph.
  * Resets the auxiliary state: C^t = result, K^t = weighted degrees,
  * Sigma^t = community totals, Delta Sigma^t = 0.  membership_out: host
@@ -239,7 +265,11 @@ leiden_status leiden_get_affected(leiden_handle *h, uint8_t *dV);
  * local-moving iterations 0..19. */
 leiden_status leiden_get_trace(leiden_handle *h, int64_t *trace);
 
-/* Counters and phase times of the last call. */
+/* Counters and phase times of the last call: the work of the phases of
+ * Alg. "leiden" (Appendix A.4: local moving, splitting, refinement,
+ * aggregation), the affected set |dV| the evaluation reports per approach
+ * (Evaluation, "Affected vertices and Marked communities"), and the phase times behind its runtime split.  Library
+ * instrumentation; the paper measures with its own timers. */
 leiden_status leiden_get_stats(leiden_handle *h, leiden_stats *stats);
 
 /* ---- Batched handles: many graphs, one launch per kernel for all of them ----
@@ -249,7 +279,7 @@ leiden_status leiden_get_stats(leiden_handle *h, leiden_stats *stats);
  * symmetric CSR (offsets[n+1], cols, weights as in leiden_create, with
  * n = vertex_offsets[G]); no arc may join two graphs (LEIDEN_ERR_ARG).  Every
  * call on the handle then processes all graphs at once, each exactly as a
- * handle of its own would (Section 4: same passes, iterations, tau, 2m and
+ * handle of its own would (Alg. "leiden": same passes, iterations, tau, 2m and
  * tracking per graph; the deterministic schedule gives the same memberships
  * bit for bit, offset by vertex_offsets[g]).  Batches passed to
  * leiden_update use the concatenated vertex ids; an edge between two graphs
@@ -320,6 +350,12 @@ leiden_status leiden_server_submit(leiden_server *s, int32_t graph, const leiden
  * Each ticket is waited for once. */
 leiden_status leiden_server_wait(leiden_server *s, int64_t ticket, int32_t *membership_out, double *latency_ms,
                                  double *service_ms);
+/* The same with a limit: if the request is not done within timeout_ms
+ * (< 0: no limit) the call returns LEIDEN_ERR_TIMEOUT and the ticket stays
+ * valid, so it may be waited for again -- a caller's deadline, e.g. for a
+ * request of a graph still waiting for memory, never blocks it for good. */
+leiden_status leiden_server_wait_for(leiden_server *s, int64_t ticket, double timeout_ms, int32_t *membership_out,
+                                     double *latency_ms, double *service_ms);
 /* Current membership of a resident graph (after its queued requests). */
 leiden_status leiden_server_membership(leiden_server *s, int32_t graph, int32_t *membership_out);
 /* Remove a graph once its queued requests are done; its memory is freed and
@@ -337,6 +373,19 @@ void leiden_server_destroy(leiden_server *s);
  * it before and after a call to count that call's launches).  Library
  * bookkeeping with no counterpart in the paper. */
 int64_t leiden_kernel_launches(void);
+
+/* Checked build.  Compiled with -DLEIDEN_CHECKED, the kernels test the
+ * invariants the algorithm guarantees (an open-addressing probe ends within
+ * its table; neighbour and community ids lie in [0, n)); a failed test is
+ * recorded in a device word, the access is skipped, and the call returns
+ * LEIDEN_ERR_STATE -- no trap, no fault, no endless loop.  The default build
+ * compiles the tests away.  leiden_checked_build() is 1 in the checked build,
+ * else 0.  leiden_check_selftest() launches one kernel that fails a test on
+ * purpose and returns the code the host reads back (and clears): 0x5e1f in
+ * the checked build, 0 in the default one.  Library diagnostics with no
+ * counterpart in the paper. */
+int32_t leiden_checked_build(void);
+int32_t leiden_check_selftest(void *cuda_stream);
 
 /* Message for the last failed call on h (or for the last failed
  * leiden_create when h is NULL).  Never NULL. */

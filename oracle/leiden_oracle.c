@@ -5,7 +5,7 @@
  * integer arithmetic.  Section and algorithm names are the paper's; where the
  * paper is silent or garbled the reading taken is stated beside the code.
  *
- * Notation (Section 3): K_i weighted degree, Sigma_c total weight of the arcs
+ * Notation (Preliminaries): K_i weighted degree, Sigma_c total weight of the arcs
  * leaving community c, K_{i->c} weight from i to the members of c other than
  * i, M2 = 2m = sum of all arc weights.  Delta-modularity (Eq. 2) is kept as
  * the integer g = M2 (K_{i->c} - K_{i->d}) - K_i (K_i + Sigma_c - Sigma_d),
@@ -54,7 +54,7 @@ static void graph_free(ograph *g) {
   memset(g, 0, sizeof(*g));
 }
 
-/* The paper's "collision-free" per-thread hashtable (Section 4.3): a dense
+/* The paper's "collision-free" per-thread hashtable (Approach, "Implementation details"): a dense
  * value array over all keys plus the list of keys touched. */
 typedef struct {
   int64_t *val;

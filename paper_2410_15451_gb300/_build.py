@@ -1,5 +1,8 @@
 """Build of libleiden_gb300.so: nvcc for sm_103a, one process per .cu file,
-objects under _build/, the shared library next to this file."""
+objects under _build/, the shared library next to this file.  build(checked=True)
+makes the checked variant libleiden_gb300_checked.so (-DLEIDEN_CHECKED: the
+kernels test their invariants and report a failed test as a status), with its
+objects under _build/checked/."""
 from __future__ import annotations
 
 import os
@@ -9,6 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB_PATH = os.path.join(HERE, "libleiden_gb300.so")
+LIB_PATH_CHECKED = os.path.join(HERE, "libleiden_gb300_checked.so")
 SOURCES = ["prims.cu", "batch.cu", "move.cu", "phases.cu", "track.cu", "api.cu", "noalloc.cu", "server.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -21,16 +25,19 @@ def _inputs():
     return files
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    lib_path = LIB_PATH_CHECKED if checked else LIB_PATH
+    out_dir = os.path.join(OUT_DIR, "checked") if checked else OUT_DIR
     newest = max(os.path.getmtime(f) for f in _inputs())
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
-        return LIB_PATH
-    os.makedirs(OUT_DIR, exist_ok=True)
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= newest:
+        return lib_path
+    os.makedirs(out_dir, exist_ok=True)
     procs, objs = [], []
     for src in SOURCES:
-        obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [NVCC, *ARCH, *FLAGS, *(["-DLEIDEN_CHECKED"] if checked else []), "-c", os.path.join(CSRC, src),
+               "-o", obj]
         if verbose:
             print(" ".join(cmd))
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -41,10 +48,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
             errors.append(f"{src}:\n{out.decode(errors='replace')}")
     if errors:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     subprocess.check_call([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-pthread"])
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

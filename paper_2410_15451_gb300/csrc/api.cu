@@ -56,6 +56,37 @@ int64_t level0_huge_slots(const std::vector<int32_t> &deg) {
   return slots;
 }
 
+void ph_mark(leiden_handle *h, int tag) {
+  if (!(h->p.collect_stats & 1)) return;
+  if (h->ph_ev.size() < (size_t)h->ph_used + 1) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+    h->ph_ev.push_back(e);
+  }
+  if (h->ph_tag.size() < (size_t)h->ph_used + 1) h->ph_tag.resize(h->ph_used + 1);
+  h->ph_tag[h->ph_used] = tag;
+  cudaEventRecord(h->ph_ev[h->ph_used], h->stream);
+  h->ph_used++;
+}
+
+void ph_resolve(leiden_handle *h) {
+  for (int k = 0; k + 1 < h->ph_used; k++) {
+    float ms = 0;
+    if (h->ph_tag[k] >= PHASE_END) continue;
+    if (cudaEventElapsedTime(&ms, h->ph_ev[k], h->ph_ev[k + 1]) == cudaSuccess) h->stats.phase_ms[h->ph_tag[k]] += ms;
+    else cudaGetLastError();
+  }
+  h->ph_used = 0;
+  leiden_stats &st = h->stats;
+  st.ms_batch = st.phase_ms[LEIDEN_PHASE_BATCH];
+  st.ms_move = st.phase_ms[LEIDEN_PHASE_MOVE];
+  st.ms_refine = st.phase_ms[LEIDEN_PHASE_REFINE];
+  st.ms_aggregate = st.phase_ms[LEIDEN_PHASE_AGGREGATE];
+  st.ms_track = st.phase_ms[LEIDEN_PHASE_TRACK];
+  st.ms_total = 0;
+  for (int k = 0; k < 6; k++) st.ms_total += st.phase_ms[k];
+}
+
 void kt_begin(leiden_handle *h, int k) {
   if (!(h->p.collect_stats & 2)) return;
   size_t need = 2 * (size_t)(h->kt_used + 1);
@@ -155,16 +186,6 @@ LevelGraph level0(leiden_handle *h) {
   return g;
 }
 
-float ev_ms(leiden_handle *h, int a, int b) {
-  float ms = 0;
-  cudaEventElapsedTime(&ms, h->ev[a], h->ev[b]);
-  return ms;
-}
-
-void mark(leiden_handle *h, int k) {
-  if (h->p.collect_stats & 1) cudaEventRecord(h->ev[k], h->stream);
-}
-
 constexpr int TRACE_WORDS = 2 + 10 * 25;
 
 // Copies the per-graph counter block of a batched handle to its pinned host
@@ -212,6 +233,11 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   }
   auto gtr = [&](int gi, int lp) -> int64_t * { return &h->gtrace[(size_t)gi * TRACE_WORDS + 2 + lp * 25]; };
   // initialisation
+  // Phase bytes below follow the algorithmic byte model: the bytes a phase
+  // must move per unit of its work (vertex of the level, arc scanned, move,
+  // listed vertex), with the sizes of the arrays it reads and writes.
+  ph_mark(h, LEIDEN_PHASE_MOVE);
+  ph_bytes(h, LEIDEN_PHASE_MOVE, 45 * N + N / 8);  // dV -> frontier bits; Ctop; copies of C', K', Sigma'
   mark_unprocessed_from_flags(h, h->dV, N);
   launch_iota_i32(h->Ctop, N, s);
   CK(cudaMemcpyAsync(h->Cp, h->C, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
@@ -225,8 +251,9 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   int passes = 0;
   bool looked_up = false;  // batched: every graph had its final lookup
   leiden_stats &st = h->stats;
-  float t_move = 0, t_ref = 0, t_agg = 0;
   int64_t moves_total = 0;
+  int64_t subsweep_words = 0;     // frontier words read by the collection kernels
+  int64_t level_arcs = h->g_arcs;  // arcs of the current level
   for (int lp = 0; lp < p.max_passes; lp++) {
     int64_t n = g.n;
     int64_t tr_spare[25];
@@ -248,7 +275,8 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
       memcpy(hg.lm_on, lmon.data(), (size_t)G);
       CK(cudaMemcpyAsync(h->gc.lm_on, hg.lm_on, (size_t)G, cudaMemcpyHostToDevice, s));
     }
-    mark(h, 2);
+    if (lp > 0) ph_mark(h, LEIDEN_PHASE_MOVE);
+    ph_bytes(h, LEIDEN_PHASE_MOVE, (lp > 0 || !dynamic ? 4 : 8) * n);  // community sizes
     lm_prepare(h, g, lp > 0 || !dynamic ? SIZES_ONES : SIZES_KEPT);
     int li = p.max_iterations;
     for (int it = 0; it < p.max_iterations; it++) {
@@ -259,6 +287,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
         CK(cudaMemsetAsync(h->gc.moves, 0, (size_t)G * sizeof(int64_t), s));
       }
       for (int cls = 0; cls < lm_classes(h); cls++) lm_subsweep(h, g, cls, lp == 0 ? in_range : nullptr, dynamic);
+      subsweep_words += (int64_t)lm_classes(h) * ((n + 31) / 32);
       sync_all(h);
       kt_resolve(h);
       CK(cudaGetLastError());
@@ -288,9 +317,12 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
       CK(cudaMemcpyAsync(h->gc.lm_on, hg.lm_on, (size_t)G, cudaMemcpyHostToDevice, s));
     }
     tr[1] = li;
-    mark(h, 3);
+    ph_mark(h, LEIDEN_PHASE_SPLIT);
+    ph_bytes(h, LEIDEN_PHASE_SPLIT, 64 * n);  // subset renumbering (58 B per vertex), split flags (6 B)
     subset_renumber(h, n);
     split_communities(h, g);
+    ph_mark(h, LEIDEN_PHASE_REFINE);
+    ph_bytes(h, LEIDEN_PHASE_REFINE, 29 * n);  // bounds C'_B, reset of the refined bounds
     CK(cudaMemcpyAsync(h->CB, h->Cp, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
     if (B) CK(cudaMemsetAsync(h->gc.refined, 0, (size_t)G, s));
     refine_reset(h, g);
@@ -321,6 +353,10 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     }
     tr[3] = refined_any;
     tr[4] = rounds;
+    // listed vertices (parent, list, compress: 24 B) and their arcs (col, C: 8 B)
+    ph_bytes(h, LEIDEN_PHASE_SPLIT, 24 * (int64_t)h->hcnt->split_count + 8 * h->hcnt->split_arcs);
+    ph_mark(h, LEIDEN_PHASE_AGGREGATE);
+    ph_bytes(h, LEIDEN_PHASE_AGGREGATE, 4 * n);  // community count
     if (B) {
       CK(cudaMemsetAsync(h->gc.ncomm, 0, (size_t)G * sizeof(int32_t), s));
       count_communities(h, n, g.gid);
@@ -332,12 +368,6 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
       if (lp < 10)
         CK(cudaMemcpyAsync(&h->dcnt->pass_ncomm[lp], &h->dcnt->list_count, sizeof(int32_t),
                            cudaMemcpyDeviceToDevice, s));
-    }
-    mark(h, 4);
-    if (h->p.collect_stats & 1) {
-      cudaEventSynchronize(h->ev[4]);
-      t_move += ev_ms(h, 2, 3);
-      t_ref += ev_ms(h, 3, 4);
     }
     if (!B) {
       if (p.converge_any && (li <= 1 || !refined_any)) break;
@@ -388,6 +418,17 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     sync_counters(h);
     CK(cudaGetLastError());
     CKF();
+    {
+      // dense renumbering (36 B per vertex), lookup (12 B per vertex of G),
+      // community-vertex lists (56 B per vertex), per community offsets,
+      // bins, K'' and the next pass's state (81 B + a frontier bit); per arc
+      // in: col, C of the neighbour and the weight; per super-arc out: col
+      // and an 8-byte weight
+      int64_t super_arcs = h->hcnt->deg_sum;
+      ph_bytes(h, LEIDEN_PHASE_AGGREGATE, 92 * n + 12 * N + 81 * ncomm + ncomm / 8 +
+                                              (8 + (g.w64 ? 8 : 4)) * level_arcs + 12 * super_arcs);
+      level_arcs = super_arcs;
+    }
     LevelGraph y;
     y.n = ncomm;
     y.off = h->y_off[slot];
@@ -405,19 +446,20 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     g = y;
     slot ^= 1;
     tau /= p.tau_drop;
-    mark(h, 5);
-    if (h->p.collect_stats & 1) {
-      cudaEventSynchronize(h->ev[5]);
-      t_agg += ev_ms(h, 4, 5);
-    }
   }
-  mark(h, 6);
+  ph_mark(h, LEIDEN_PHASE_TRACK);
+  ph_bytes(h, LEIDEN_PHASE_TRACK, (B ? 0 : 12 * N) + 234 * N);  // final lookup; tracking's sweeps
   if (!B) lookup_dendrogram(h);
   else if (!looked_up) { h->err = "batched pass loop ended without a final lookup"; return LEIDEN_ERR_STATE; }
   track_communities(h);
-  mark(h, 7);
+  ph_mark(h, PHASE_END);
   sync_counters(h);
   CK(cudaGetLastError());
+  ph_resolve(h);
+  if (unsigned int code = check_word_move() | check_word_phases() | check_word_track()) {
+    h->err = "a device-side check of the checked build failed (code " + std::to_string(code) + ")";
+    return LEIDEN_ERR_STATE;
+  }
   h->trace[0] = passes;
   if (!B)
     for (int lp = 0; lp < passes && lp < 10; lp++) h->trace[2 + lp * 25 + 2] = h->hcnt->pass_ncomm[lp];
@@ -428,19 +470,23 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   st.refine_vertices = h->hcnt->ref_processed;
   st.refine_arcs = h->hcnt->ref_arcs;
   kt_resolve(h);
+  int64_t visits = 0, decide_bytes = 0;
   for (int k = 0; k < KT_KERNELS; k++) {
     st.lmk_vertices[k] = h->hcnt->lmk_visits[k];
     st.lmk_arcs[k] = h->hcnt->lmk_arcs[k];
     st.lmk_bytes[k] = h->hcnt->lmk_bytes[k];
     st.lmk_launches[k] = h->kt_launches[k];
     st.lmk_ms[k] = h->kt_ms[k];
+    visits += h->hcnt->lmk_visits[k];
+    decide_bytes += h->hcnt->lmk_bytes[k];
   }
-  if (h->p.collect_stats & 1) {
-    st.ms_move = t_move;
-    st.ms_refine = t_ref;
-    st.ms_aggregate = t_agg;
-    st.ms_track = ev_ms(h, 6, 7);
-  }
+  // local moving: frontier words, the decide kernels' own count, 8 B per
+  // visit to bin it (degree, list entry), 44 B per applied move
+  ph_bytes(h, LEIDEN_PHASE_MOVE, 4 * subsweep_words + decide_bytes + 8 * visits + 44 * moves_total);
+  // refinement: per visit 40 B of vertex state plus 40 B to list, bin and
+  // accept it; per arc col, C, C'_B of the neighbour and the weight
+  ph_bytes(h, LEIDEN_PHASE_REFINE, 80 * st.refine_vertices + 16 * st.refine_arcs);
+  st.affected = h->hcnt->affected;
   return LEIDEN_OK;
 }
 
@@ -482,10 +528,11 @@ leiden_status finish_call(leiden_handle *h, int32_t *out, bool device_out) {
 leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_del, const leiden_edge *d_ins,
                         int64_t n_ins, leiden_mode mode) {
   h->stats = leiden_stats{};
-  if (h->p.collect_stats & 1) cudaEventRecord(h->ev[0], h->stream);
+  h->ph_used = 0;
+  ph_mark(h, LEIDEN_PHASE_BATCH);
   leiden_status st = batch_apply_and_mark(h, d_del, n_del, d_ins, n_ins, (int)mode);
   if (st != LEIDEN_OK) return st;
-  mark(h, 1);
+  ph_bytes(h, LEIDEN_PHASE_BATCH, 4 * h->n);  // degrees scanned for the bins
   level_maxdeg(h, h->g_deg, h->n);
   sync_all(h);
   CK(cudaGetLastError());
@@ -496,14 +543,7 @@ leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_de
   }
   h->g_maxdeg = h->hcnt->max_count;
   h->g_huge_slots = h->hcnt->huge_slots;
-  st = run_leiden(h, 1, mode == LEIDEN_DS ? h->dV : nullptr);
-  if (st != LEIDEN_OK) return st;
-  if (h->p.collect_stats & 1) {
-    cudaEventSynchronize(h->ev[7]);
-    h->stats.ms_batch = ev_ms(h, 0, 1);
-    h->stats.ms_total = ev_ms(h, 0, 7);
-  }
-  return LEIDEN_OK;
+  return run_leiden(h, 1, mode == LEIDEN_DS ? h->dV : nullptr);
 }
 
 leiden_status check_handle(leiden_handle *h) {
@@ -670,7 +710,6 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   A(cudaMalloc(&stp, stb));
   if (stp) { h->owned.push_back(stp); h->scan_tmp = stp; h->scan_tmp_bytes = stb; }
   A(cudaMallocHost((void **)&h->hcnt, sizeof(DevCounters)));
-  for (auto &ev : h->ev) A(cudaEventCreate(&ev));
   if (e != cudaSuccess)
     return bail(e == cudaErrorMemoryAllocation ? LEIDEN_ERR_OOM : LEIDEN_ERR_CUDA,
                 std::string("device allocation: ") + cudaGetErrorString(e));
@@ -830,8 +869,12 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   if (st != LEIDEN_OK) return st;
   cudaStream_t s = h->stream;
   h->stats = leiden_stats{};
-  if (h->p.collect_stats & 1) cudaEventRecord(h->ev[0], s);
+  h->ph_used = 0;
+  ph_mark(h, LEIDEN_PHASE_BATCH);
   int64_t N = h->n;
+  // row sums (offsets, degree, K: 20 B per vertex; a weight per arc), degree
+  // scan, C, sizes, Sigma, Delta Sigma and the flags
+  ph_bytes(h, LEIDEN_PHASE_BATCH, 59 * N + 4 * h->g_arcs);
   recompute_weights(h);
   level_maxdeg(h, h->g_deg, N);
   launch_iota_i32(h->C, N, s);
@@ -850,14 +893,9 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   }
   h->g_maxdeg = h->hcnt->max_count;
   h->g_huge_slots = h->hcnt->huge_slots;
-  mark(h, 1);
   st = run_leiden(h, 0, nullptr);
   if (st != LEIDEN_OK) return st;
   h->has_static = true;
-  if (h->p.collect_stats & 1) {
-    cudaEventSynchronize(h->ev[7]);
-    h->stats.ms_total = ev_ms(h, 0, 7);
-  }
   return finish_call(h, membership_out, false);
 }
 
@@ -978,7 +1016,7 @@ leiden_status leiden_import_state(leiden_handle *h, const int32_t *C, const int6
           return LEIDEN_ERR_ARG;
         }
   cudaStream_t s = h->stream;
-  // K and 2m from G^t, Sigma from K and C (Section 4.1: the auxiliary
+  // K and 2m from G^t, Sigma from K and C (Approach: the auxiliary
   // information is a function of the graph and the membership, plus the
   // accumulated Delta Sigma)
   recompute_weights(h);
@@ -1081,6 +1119,16 @@ leiden_status leiden_get_stats(leiden_handle *h, leiden_stats *stats) {
 
 int64_t leiden_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int32_t leiden_checked_build(void) {
+#ifdef LEIDEN_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int32_t leiden_check_selftest(void *cuda_stream) { return (int32_t)check_selftest((cudaStream_t)cuda_stream); }
+
 const char *leiden_last_error(leiden_handle *h) {
   if (!h) return g_create_error.c_str();
   return h->err.c_str();
@@ -1095,7 +1143,7 @@ void leiden_destroy(leiden_handle *h) {
   if (h->hcnt) cudaFreeHost(h->hcnt);
   if (h->gc_host) cudaFreeHost(h->gc_host);
   if (h->pin) cudaFreeHost(h->pin);
-  for (auto &ev : h->ev)
+  for (auto &ev : h->ph_ev)
     if (ev) cudaEventDestroy(ev);
   for (auto &ev : h->kt_ev)
     if (ev) cudaEventDestroy(ev);

@@ -873,5 +873,22 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
                                                              h->p.tau_refine, h->dS, h->dR);
     ld_note_launch(), k_reset_changes<<<grid_for(nd + ni, TB), TB, 0, s>>>(DK, nd, IK, ni, vb, h->C, h->dR, h->dSig);
   }
+  // Algorithmic bytes of the batch phase: the edge triples read (12 B per
+  // edge); per raw arc its expansion and sort (48 B: key and weight written,
+  // then read and written once more) and deduplication (24 B); per unique
+  // arc the existence check or classification (16 B) and the updates of K,
+  // Sigma, Delta Sigma, 2m and the flags (40 B); per touched row its plan
+  // (40 B) and per arc of a merged row its read and write (16 B); a full
+  // rebuild copies every arc (16 B); marking: dV (1 B per vertex) plus, for
+  // DF, both endpoints' communities per unique arc (16 B), for DS the
+  // (source, community) pairs of the insertions and their sort (48 B per
+  // arc), dE and the community sweep (7 B per vertex); dS and dR (2 B per
+  // vertex).
+  int64_t A = nda + nia, U = nd + ni;
+  int64_t bytes = 12 * (n_del + n_ins) + 72 * A + 56 * U + 40 * nrows + 16 * tmp_total + 3 * n;
+  if (overflow) bytes += 16 * h->g_arcs;
+  if (mode == LEIDEN_DF) bytes += 16 * U;
+  if (mode == LEIDEN_DS) bytes += 48 * ni + 7 * n;
+  ph_bytes(h, LEIDEN_PHASE_BATCH, bytes);
   return LEIDEN_OK;
 }

@@ -49,7 +49,39 @@ struct DevCounters {
   int64_t bcounts[8];             // batch apply: unique deletions, unique insertions, new arcs,
                                   //   touched rows, merge-buffer arcs
   int32_t pass_ncomm[10];         // communities after refinement, per pass (trace)
+  int64_t affected;               // |dV|: vertices flagged affected (counted into the frontier)
+  int64_t split_arcs;             // splitting: arcs of the vertices listed for splitting
+  int64_t deg_sum;                // degree sum of the level scanned by level_maxdeg (its arcs)
 };
+
+// ---------------------------------------------------------------- checked build
+// Built with -DLEIDEN_CHECKED, the kernels test conditions the algorithm
+// guarantees -- an open-addressing probe ends within its table, neighbour and
+// community ids lie in [0, n), a union-find chain is shorter than n -- and
+// where one fails they record its code in a device word of their source
+// file, skip the access and go on.  A broken invariant then ends the call
+// with LEIDEN_ERR_STATE instead of a fault, a trap or an endless loop.  The
+// default build compiles every test away (ld_ok is then always true).
+enum { LD_CHK_PROBE = 1, LD_CHK_COL = 2, LD_CHK_COMM = 3, LD_CHK_CHAIN = 4, LD_CHK_SELFTEST = 0x5e1f };
+#ifdef LEIDEN_CHECKED
+static __device__ unsigned int ld_check_word;
+__device__ __forceinline__ bool ld_ok(bool cond, unsigned int code) {
+  if (!cond) atomicCAS(&ld_check_word, 0u, code);
+  return cond;
+}
+// Host: the file's check word (after a stream sync), reset to 0.
+#define LD_CHECK_WORD_READER(fn)                                      \
+  unsigned int fn() {                                                 \
+    unsigned int v = 0, z = 0;                                        \
+    if (cudaMemcpyFromSymbol(&v, ld_check_word, sizeof(v)) != cudaSuccess) { cudaGetLastError(); return 0; } \
+    cudaMemcpyToSymbol(ld_check_word, &z, sizeof(z));                 \
+    return v;                                                         \
+  }
+#else
+__device__ __forceinline__ bool ld_ok(bool, unsigned int) { return true; }
+#define LD_CHECK_WORD_READER(fn) \
+  unsigned int fn() { return 0; }
+#endif
 
 // ---------------------------------------------------------------- hashing
 // SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014).
@@ -128,7 +160,7 @@ __device__ __forceinline__ bool ld_group_leader(uint32_t peers) {
 __device__ __forceinline__ void ld_gtable_insert(int32_t *keys, int64_t *vals, int32_t *list, int32_t *occ, int tmask,
                                                  int32_t c, int64_t w) {
   uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)tmask;
-  while (true) {
+  for (uint32_t probe = 0; ld_ok(probe <= (uint32_t)tmask, LD_CHK_PROBE); probe++) {
     int32_t k = atomicCAS(&keys[s], LD_EMPTY_KEY, c);
     if (k == LD_EMPTY_KEY) list[atomicAdd(occ, 1)] = (int32_t)s;
     if (k == LD_EMPTY_KEY || k == c) {
@@ -170,7 +202,7 @@ __device__ __forceinline__ void wt_init(WarpTable &T) {
 __device__ __forceinline__ void wt_insert_lanes(WarpTable &T, bool valid, int32_t c, int64_t w) {
   if (valid) {
     uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(WT_SLOTS - 1);
-    while (true) {
+    for (int probe = 0; ld_ok(probe < WT_SLOTS, LD_CHK_PROBE); probe++) {
       int32_t k = T.keys[s];
       if (k == LD_EMPTY_KEY) {
         k = atomicCAS(&T.keys[s], LD_EMPTY_KEY, c);

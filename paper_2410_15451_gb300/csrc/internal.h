@@ -169,7 +169,12 @@ struct leiden_handle {
   void *pin = nullptr;      // pinned host staging: batches in, membership out
   size_t pin_bytes = 0;
 
-  cudaEvent_t ev[8] = {};
+  // Phase timer (collect_stats bit 1): an event recorded on the stream at
+  // each phase boundary, tagged with the phase that starts there, and read
+  // after the call's last host sync.
+  std::vector<cudaEvent_t> ph_ev;
+  std::vector<int> ph_tag;
+  int ph_used = 0;
   // Kernel timer (collect_stats bit 2): event pairs around the launches of
   // the local-moving kernels, resolved at the next host sync.
   std::vector<cudaEvent_t> kt_ev;
@@ -195,6 +200,14 @@ void ld_note_launch();
 // Kernel timer of the local-moving kernels: begin/end around a launch of
 // kernel `k` (no-ops unless collect_stats has bit 2), resolve after a
 // stream sync.
+// Phase boundaries (tag: a leiden_phase, or PHASE_END after the last one)
+// and their resolution after a stream sync into stats.phase_ms.
+constexpr int PHASE_END = 6;
+void ph_mark(leiden_handle *h, int tag);
+void ph_resolve(leiden_handle *h);
+// Adds algorithmic bytes to stats.phase_bytes[phase].
+inline void ph_bytes(leiden_handle *h, int phase, int64_t bytes) { h->stats.phase_bytes[phase] += bytes; }
+
 void kt_begin(leiden_handle *h, int k);
 void kt_end(leiden_handle *h);
 void kt_resolve(leiden_handle *h);
@@ -207,6 +220,14 @@ int64_t level0_huge_slots(const std::vector<int32_t> &deg);
 
 // Message returned by leiden_last_error(NULL) (calls without a handle).
 void set_handle_free_error(const std::string &msg);
+
+// Checked build: each file's device check word (0 = every check held), read
+// after a stream sync and reset; check_selftest records LD_CHK_SELFTEST on
+// purpose and returns what the host reads back (0 in the default build).
+unsigned int check_word_move();
+unsigned int check_word_phases();
+unsigned int check_word_track();
+unsigned int check_selftest(cudaStream_t s);
 
 // ------------------------------------------------------------ prims.cu
 // Exclusive scan of n values; out[n] receives the total.  `tmp` must hold

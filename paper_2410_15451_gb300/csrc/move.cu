@@ -79,7 +79,7 @@ __device__ __forceinline__ int next_pow2(int x) {
 
 __device__ __forceinline__ void table_insert(int32_t *keys, int64_t *vals, int tmask, int32_t c, int64_t w) {
   uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)tmask;
-  while (true) {
+  for (uint32_t probe = 0; ld_ok(probe <= (uint32_t)tmask, LD_CHK_PROBE); probe++) {
     int32_t k = atomicCAS(&keys[s], LD_EMPTY_KEY, c);
     if (k == LD_EMPTY_KEY || k == c) {
       atomicAdd((unsigned long long *)&vals[s], (unsigned long long)w);
@@ -355,12 +355,14 @@ __device__ __forceinline__ void tiny_step(const Args &A, int64_t item, int64_t n
   }
   bool arc = has && sub < dg;
   if (arc) { j = A.col[base + sub]; wj = (int64_t)w[base + sub]; }
+  arc = arc && ld_ok((uint64_t)j < (uint64_t)A.n, LD_CHK_COL);
   if (has) {
     Sd = A.S[d];
     if (KIND == KIND_MOVE) szd = A.size[d];
   }
   bool valid = arc && j != i && (KIND != KIND_REFINE || A.CB[j] == bi);
   int32_t c = valid ? A.C[j] : 0;
+  valid = valid && ld_ok((uint64_t)c < (uint64_t)A.n, LD_CHK_COMM);
   unsigned long long key = valid ? (((unsigned long long)grp << 32) | (uint32_t)c)
                                  : (0xffffffff00000000ull | (unsigned)lane);
   uint32_t peers = __match_any_sync(LD_FULL, key);
@@ -425,11 +427,14 @@ __device__ __forceinline__ void warp_step(const Args &A, int32_t i, int lane, Wa
   }
 #pragma unroll
   for (int u = 0; u < WARP_UNROLL; u++) {
-    v[u] = v[u] && j[u] != i;
+    v[u] = v[u] && j[u] != i && ld_ok((uint64_t)j[u] < (uint64_t)A.n, LD_CHK_COL);
     if (KIND == KIND_REFINE) v[u] = v[u] && A.CB[j[u]] == bi;
   }
 #pragma unroll
-  for (int u = 0; u < WARP_UNROLL; u++) c[u] = v[u] ? A.C[j[u]] : 0;
+  for (int u = 0; u < WARP_UNROLL; u++) {
+    c[u] = v[u] ? A.C[j[u]] : 0;
+    v[u] = v[u] && ld_ok((uint64_t)c[u] < (uint64_t)A.n, LD_CHK_COMM);
+  }
 #pragma unroll
   for (int u = 0; u < WARP_UNROLL; u++) wt_insert_lanes(T, v[u], c[u], wa[u]);
   int n = T.count;
@@ -538,7 +543,7 @@ struct BlockStage {
 __device__ __forceinline__ void bstage_insert(BlockStage &S, int32_t *count, bool valid, int32_t c, int64_t w) {
   if (!valid) return;
   uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(STAGE_SLOTS - 1);
-  while (true) {
+  for (int probe = 0; ld_ok(probe < STAGE_SLOTS, LD_CHK_PROBE); probe++) {
     int32_t k = S.keys[s];
     if (k == LD_EMPTY_KEY) {
       k = atomicCAS(&S.keys[s], LD_EMPTY_KEY, c);
@@ -593,11 +598,14 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Args A) {
       }
 #pragma unroll
       for (int u = 0; u < BLOCK_UNROLL; u++) {
-        v[u] = v[u] && j[u] != i;
+        v[u] = v[u] && j[u] != i && ld_ok((uint64_t)j[u] < (uint64_t)A.n, LD_CHK_COL);
         if (KIND == KIND_REFINE) v[u] = v[u] && A.CB[j[u]] == bi;
       }
 #pragma unroll
-      for (int u = 0; u < BLOCK_UNROLL; u++) c[u] = v[u] ? A.C[j[u]] : 0;
+      for (int u = 0; u < BLOCK_UNROLL; u++) {
+        c[u] = v[u] ? A.C[j[u]] : 0;
+        v[u] = v[u] && ld_ok((uint64_t)c[u] < (uint64_t)A.n, LD_CHK_COMM);
+      }
 #pragma unroll
       for (int u = 0; u < BLOCK_UNROLL; u++) bstage_insert(S, cnt, v[u], c[u], wa[u]);
     }
@@ -679,6 +687,7 @@ __global__ void __launch_bounds__(BLOCK_THREADS) k_decide_block(Args A) {
 // pow2 >= 2*degree slots in global scratch and its arcs are cut into chunks
 // of HUGE_CHUNK that any block may take, so one hub no longer runs on one SM.
 constexpr int HUGE_CHUNK = TABLE_CHUNK;
+constexpr int HUGE_UNROLL = 4;
 
 // Global tables start clean (empty keys, zero values) and are cleaned again
 // by the kernel that reads them; each records the slots it fills in a list
@@ -711,7 +720,7 @@ __device__ __forceinline__ void wt_insert_lanes(WarpTable32 &T, bool valid, int3
                                                 int64_t *gvals, int32_t *glist, int32_t *gocc, int gmask) {
   if (valid) {
     uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)(WT_SLOTS - 1);
-    while (true) {
+    for (int probe = 0; ld_ok(probe < WT_SLOTS, LD_CHK_PROBE); probe++) {
       int32_t k = T.keys[s];
       if (k == LD_EMPTY_KEY) {
         k = atomicCAS(&T.keys[s], LD_EMPTY_KEY, c);
@@ -776,19 +785,36 @@ __global__ void __launch_bounds__(256) k_huge_scan(Args A, const int64_t *tab_of
     int32_t *keys = A.gkeys + tab_off[lo], *list = A.glist + tab_off[lo];
     int64_t *vals = A.gvals + tab_off[lo];
     int lane = threadIdx.x & 31;
-    for (int64_t a0 = threadIdx.x & ~31; a0 < len; a0 += blockDim.x) {  // warp-uniform trip count
-      int64_t a = a0 + lane;
-      bool valid = a < len;
-      int32_t c = 0;
-      int64_t wa = 0;
-      if (valid) {
-        int32_t j = A.col[base + a];
-        valid = j != i && (KIND != KIND_REFINE || A.CB[j] == bi);
-        if (valid) { c = A.C[j]; wa = (int64_t)w[base + a]; }
+    // HUGE_UNROLL arcs per lane in flight: their col, weight and C[j] loads
+    // are independent; the inserts follow one by one
+    for (int64_t a0 = threadIdx.x & ~31; a0 < len; a0 += (int64_t)blockDim.x * HUGE_UNROLL) {  // warp-uniform
+      int32_t j[HUGE_UNROLL], c[HUGE_UNROLL];
+      int64_t wa[HUGE_UNROLL];
+      bool valid[HUGE_UNROLL];
+#pragma unroll
+      for (int u = 0; u < HUGE_UNROLL; u++) {
+        int64_t a = a0 + (int64_t)u * blockDim.x + lane;
+        valid[u] = a < len;
+        j[u] = valid[u] ? A.col[base + a] : (int32_t)i;
+        wa[u] = valid[u] ? (int64_t)w[base + a] : 0;
       }
-      if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
-      if constexpr (sizeof(W) == 4) wt_insert_lanes(T8, valid, c, wa, keys, vals, list, &A.gocc[lo], (int)(T - 1));
-      else wt_insert_lanes(T8, valid, c, wa);
+#pragma unroll
+      for (int u = 0; u < HUGE_UNROLL; u++) {
+        valid[u] = valid[u] && j[u] != i && ld_ok((uint64_t)j[u] < (uint64_t)A.n, LD_CHK_COL);
+        if (KIND == KIND_REFINE) valid[u] = valid[u] && A.CB[j[u]] == bi;
+      }
+#pragma unroll
+      for (int u = 0; u < HUGE_UNROLL; u++) {
+        c[u] = valid[u] ? A.C[j[u]] : 0;
+        valid[u] = valid[u] && ld_ok((uint64_t)c[u] < (uint64_t)A.n, LD_CHK_COMM);
+      }
+#pragma unroll
+      for (int u = 0; u < HUGE_UNROLL; u++) {
+        if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+        if constexpr (sizeof(W) == 4)
+          wt_insert_lanes(T8, valid[u], c[u], wa[u], keys, vals, list, &A.gocc[lo], (int)(T - 1));
+        else wt_insert_lanes(T8, valid[u], c[u], wa[u]);
+      }
     }
     wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
     if (KIND == KIND_MOVE && threadIdx.x == 0)
@@ -1019,6 +1045,10 @@ __global__ void k_refine_accept(const int32_t *cand, const int32_t *count, const
   if (acc) atomicAdd(&cnt->accepted, acc);
 }
 
+__global__ void k_check_selftest() {
+  if (threadIdx.x == 0) ld_ok(false, LD_CHK_SELFTEST);
+}
+
 Args make_args(leiden_handle *h, const LevelGraph &g) {
   Args A{};
   A.n = g.n;
@@ -1200,4 +1230,12 @@ void refine_round(leiden_handle *h, const LevelGraph &g, int slot) {
   launch_bins<KIND_REFINE>(h, g, A);
   ld_note_launch(), k_refine_accept<<<h->sm_count * 4, 256, 0, s>>>(out, cout, h->prop, h->Cp, h->Sp, h->Kp, h->dcnt,
                                                                      g.gid, h->gc.accepted);
+}
+
+LD_CHECK_WORD_READER(check_word_move)
+
+unsigned int check_selftest(cudaStream_t s) {
+  ld_note_launch(), k_check_selftest<<<1, 32, 0, s>>>();
+  cudaStreamSynchronize(s);
+  return check_word_move();
 }

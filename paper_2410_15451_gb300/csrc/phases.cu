@@ -39,16 +39,17 @@ __global__ void k_sr_remap(int64_t n, const int32_t *rep, int32_t *C) {
 // Components of the flagged communities by lock-free union-find: a root is
 // only ever hooked under a smaller root, so every component ends with its
 // smallest vertex as root -- the label a BFS from the lowest vertex gives.
-__global__ void k_split_init(int64_t n, const int32_t *C, const uint8_t *dS, const uint8_t *dR, int32_t *parent,
-                             int32_t *list, DevCounters *cnt, int split_all) {
+__global__ void k_split_init(int64_t n, const int32_t *C, const uint8_t *dS, const uint8_t *dR, const int32_t *deg,
+                             int32_t *parent, int32_t *list, DevCounters *cnt, int split_all) {
   int lane = threadIdx.x & 31;
+  int64_t arcs = 0;  // arcs of the listed vertices (work counter)
   for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
     int64_t i = base + lane;
     bool f = false;
     if (i < n) {
       int32_t c = C[i];
       f = (split_all || dS[c]) && !dR[c];
-      if (f) parent[i] = (int32_t)i;
+      if (f) { parent[i] = (int32_t)i; arcs += deg[i]; }
     }
     uint32_t m = __ballot_sync(LD_FULL, f);
     if (!m) continue;
@@ -57,6 +58,8 @@ __global__ void k_split_init(int64_t n, const int32_t *C, const uint8_t *dS, con
     p0 = __shfl_sync(LD_FULL, p0, 0);
     if (f) list[p0 + __popc(m & ((1u << lane) - 1u))] = (int32_t)i;
   }
+  arcs = ld_warp_sum_i64(arcs);
+  if (lane == 0 && arcs) atomicAdd((unsigned long long *)&cnt->split_arcs, (unsigned long long)arcs);
 }
 
 __device__ __forceinline__ int32_t uf_find(int32_t *parent, int32_t x) {
@@ -252,11 +255,21 @@ __global__ void k_member_count(int64_t n, const int32_t *C, int32_t *cnt_c) {
     if (i < n && ld_group_leader(peers)) atomicAdd(&cnt_c[c], __popc(peers));
   }
 }
-// cursor[c] starts at coff[c]; each member takes the next slot of its community.
+// cursor[c] starts at coff[c]; each member takes the next slot of its
+// community.  Lanes of a warp in the same community claim their slots with
+// one atomic (giant communities would otherwise serialise on one cursor);
+// the order of members within a community does not matter downstream.
 __global__ void k_member_fill(int64_t n, const int32_t *C, unsigned long long *cursor, int32_t *cverts) {
-  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) {
-    unsigned long long p = atomicAdd(&cursor[C[i]], 1ull);
-    cverts[(int64_t)p] = (int32_t)i;
+  int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {  // warp-uniform trip count
+    int64_t i = base + lane;
+    int32_t c = i < n ? C[i] : -1 - lane;
+    uint32_t peers = __match_any_sync(LD_FULL, c);
+    int leader = __ffs(peers) - 1;
+    unsigned long long p0 = 0;
+    if (i < n && lane == leader) p0 = atomicAdd(&cursor[c], (unsigned long long)__popc(peers));
+    p0 = __shfl_sync(LD_FULL, p0, leader);
+    if (i < n) cverts[(int64_t)p0 + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
   }
 }
 __global__ void k_member_deg(int64_t n, const int32_t *cverts, const int32_t *deg, int32_t *mdeg) {
@@ -280,7 +293,7 @@ __global__ void k_yoff(int64_t ncomm, const int64_t *coff, const int64_t *cflat,
 
 __device__ __forceinline__ void agg_insert(int32_t *keys, int64_t *vals, int tmask, int32_t c, int64_t w) {
   uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)tmask;
-  while (true) {
+  for (uint32_t probe = 0; ld_ok(probe <= (uint32_t)tmask, LD_CHK_PROBE); probe++) {
     int32_t k = atomicCAS(&keys[s], LD_EMPTY_KEY, c);
     if (k == LD_EMPTY_KEY || k == c) {
       atomicAdd((unsigned long long *)&vals[s], (unsigned long long)w);
@@ -404,6 +417,37 @@ __global__ void __launch_bounds__(256) k_agg_block(AggArgs A) {
   }
 }
 
+// AGG_UNROLL groups of 32 flat arcs, `gap` apart, from f = g0 + lane: the
+// col and weight loads of all of them, then the C loads, then the inserts
+// into the warp table (flushed to the community's global table when full).
+constexpr int AGG_UNROLL = 4;
+template <typename W>
+__device__ __forceinline__ void agg_chunk_step(const AggArgs &A, WarpTable &T8, int64_t row, int64_t g0, int64_t gap,
+                                               int64_t s1, int32_t *keys, int64_t *vals, int32_t *list,
+                                               int32_t *occ, int tmask) {
+  const W *w = (const W *)A.w;
+  int lane = threadIdx.x & 31;
+  int32_t j[AGG_UNROLL], c[AGG_UNROLL];
+  int64_t wa[AGG_UNROLL];
+  bool valid[AGG_UNROLL];
+#pragma unroll
+  for (int u = 0; u < AGG_UNROLL; u++) {
+    int64_t f = g0 + u * gap + lane;
+    valid[u] = f < s1;
+    j[u] = valid[u] ? A.col[row + f] : 0;
+    wa[u] = valid[u] ? (int64_t)w[row + f] : 0;
+  }
+#pragma unroll
+  for (int u = 0; u < AGG_UNROLL; u++) {
+    c[u] = valid[u] ? A.C[j[u]] : 0;
+  }
+#pragma unroll
+  for (int u = 0; u < AGG_UNROLL; u++) {
+    if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, occ, tmask);
+    wt_insert_lanes(T8, valid[u], c[u], wa[u]);
+  }
+}
+
 // Communities above BIN_BLOCK_MAX flat arcs: each has its own global table
 // (tab_off) and its flat arcs are cut into chunks any block may take
 // (ch_off); the filled slots are listed so the emission visits only them.
@@ -453,36 +497,16 @@ __global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t
         continue;
       }
       int64_t row = A.off[A.cverts[a]] - fa;
-      for (int64_t g0 = s0; g0 < s1; g0 += 32) {
-        int64_t f = g0 + lane;
-        bool valid = f < s1;
-        int32_t c = 0;
-        int64_t wa = 0;
-        if (valid) {
-          c = A.C[A.col[row + f]];
-          wa = (int64_t)w[row + f];
-        }
-        if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
-        wt_insert_lanes(T8, valid, c, wa);
-      }
+      for (int64_t g0 = s0; g0 < s1; g0 += 32 * AGG_UNROLL)
+        agg_chunk_step<W>(A, T8, row, g0, 32, s1, keys, vals, list, &A.gocc[lo], (int)(T - 1));
     }
     __syncthreads();
     for (int q = 0; q < nlong; q++) {
       int64_t a = longm[q], fa = A.cflat[a], fb = A.cflat[a + 1];
       int64_t s0 = fa > f0 ? fa : f0, s1 = fb < f1 ? fb : f1;
       int64_t row = A.off[A.cverts[a]] - fa;
-      for (int64_t g0 = s0 + 32 * wid; g0 < s1; g0 += 32 * nwarps) {  // warp-uniform
-        int64_t f = g0 + lane;
-        bool valid = f < s1;
-        int32_t c = 0;
-        int64_t wa = 0;
-        if (valid) {
-          c = A.C[A.col[row + f]];
-          wa = (int64_t)w[row + f];
-        }
-        if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
-        wt_insert_lanes(T8, valid, c, wa);
-      }
+      for (int64_t g0 = s0 + 32 * wid; g0 < s1; g0 += 32 * nwarps * AGG_UNROLL)  // warp-uniform
+        agg_chunk_step<W>(A, T8, row, g0, 32 * nwarps, s1, keys, vals, list, &A.gocc[lo], (int)(T - 1));
     }
     wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
     __syncthreads();  // nlong and longm are rewritten by the next chunk
@@ -557,20 +581,23 @@ __global__ void k_bits_all(int64_t n, uint32_t *bm) {
     bm[w] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
   }
 }
-__global__ void k_bits_from_flags(int64_t n, const uint8_t *flags, uint32_t *bm) {
+__global__ void k_bits_from_flags(int64_t n, const uint8_t *flags, uint32_t *bm, DevCounters *cnt) {
   int lane = threadIdx.x & 31;
+  int64_t set = 0;
   for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
     int64_t v = base + lane;
     uint32_t m = __ballot_sync(LD_FULL, v < n && flags[v]);
-    if (lane == 0) bm[base >> 5] = m;
+    if (lane == 0) { bm[base >> 5] = m; set += __popc(m); }
   }
+  if (lane == 0 && set) atomicAdd((unsigned long long *)&cnt->affected, (unsigned long long)set);
 }
 __global__ void k_maxdeg(int64_t n, const int32_t *deg, DevCounters *cnt, int block_max) {
   int32_t mx = 0;
-  int64_t slots = 0;
+  int64_t slots = 0, sum = 0;
   for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) {
     int32_t d = deg[i];
     mx = max(mx, d);
+    sum += d;
     if (d > block_max) {
       int64_t t = 1;
       while (t < 2 * (int64_t)d) t <<= 1;
@@ -581,10 +608,12 @@ __global__ void k_maxdeg(int64_t n, const int32_t *deg, DevCounters *cnt, int bl
   for (int o = 16; o > 0; o >>= 1) {
     mx = max(mx, __shfl_xor_sync(LD_FULL, mx, o));
     slots += __shfl_xor_sync(LD_FULL, slots, o);
+    sum += __shfl_xor_sync(LD_FULL, sum, o);
   }
   if ((threadIdx.x & 31) == 0) {
     if (mx) atomicMax(&cnt->max_count, mx);
     if (slots) atomicAdd((unsigned long long *)&cnt->huge_slots, (unsigned long long)slots);
+    if (sum) atomicAdd((unsigned long long *)&cnt->deg_sum, (unsigned long long)sum);
   }
 }
 
@@ -605,9 +634,10 @@ void subset_renumber(leiden_handle *h, int64_t n) {
 void split_communities(leiden_handle *h, const LevelGraph &g) {
   cudaStream_t s = h->stream;
   cudaMemsetAsync(&h->dcnt->split_count, 0, sizeof(int32_t), s);
+  cudaMemsetAsync(&h->dcnt->split_arcs, 0, sizeof(int64_t), s);
   int32_t *list = h->ibuf1;
-  ld_note_launch(), k_split_init<<<grid_for(g.n, TB), TB, 0, s>>>(g.n, h->Cp, h->dS, h->dR, h->parent, list, h->dcnt,
-                                                                               h->p.split_all);
+  ld_note_launch(), k_split_init<<<grid_for(g.n, TB), TB, 0, s>>>(g.n, h->Cp, h->dS, h->dR, g.deg, h->parent, list,
+                                                                  h->dcnt, h->p.split_all);
   ld_note_launch(), k_split_sample<<<h->sm_count * 16, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
   ld_note_launch(), k_split_flatten<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent);
   cudaMemsetAsync(&h->dcnt->big_count, 0, sizeof(int32_t), s);
@@ -728,11 +758,15 @@ void mark_all_unprocessed(leiden_handle *h, int64_t n) {
 }
 
 void mark_unprocessed_from_flags(leiden_handle *h, const uint8_t *flags, int64_t n) {
-  ld_note_launch(), k_bits_from_flags<<<grid_for(n, TB), TB, 0, h->stream>>>(n, flags, h->unproc);
+  cudaMemsetAsync(&h->dcnt->affected, 0, sizeof(int64_t), h->stream);
+  ld_note_launch(), k_bits_from_flags<<<grid_for(n, TB), TB, 0, h->stream>>>(n, flags, h->unproc, h->dcnt);
 }
 
 void level_maxdeg(leiden_handle *h, const int32_t *deg, int64_t n) {
   cudaMemsetAsync(&h->dcnt->max_count, 0, sizeof(int32_t), h->stream);
   cudaMemsetAsync(&h->dcnt->huge_slots, 0, sizeof(int64_t), h->stream);
+  cudaMemsetAsync(&h->dcnt->deg_sum, 0, sizeof(int64_t), h->stream);
   ld_note_launch(), k_maxdeg<<<grid_for(n, TB), TB, 0, h->stream>>>(n, deg, h->dcnt, h->tune.block_max);
 }
+
+LD_CHECK_WORD_READER(check_word_phases)

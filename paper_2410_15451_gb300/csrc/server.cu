@@ -258,14 +258,19 @@ leiden_status leiden_server_submit(leiden_server *S, int32_t graph, const leiden
   return LEIDEN_OK;
 }
 
-leiden_status leiden_server_wait(leiden_server *S, int64_t ticket, int32_t *membership_out, double *latency_ms,
-                                 double *service_ms) {
+leiden_status leiden_server_wait_for(leiden_server *S, int64_t ticket, double timeout_ms, int32_t *membership_out,
+                                     double *latency_ms, double *service_ms) {
   if (!S) return LEIDEN_ERR_ARG;
   std::unique_lock<std::mutex> lk(S->mu);
   auto it = S->reqs.find(ticket);
   if (it == S->reqs.end()) { S->err = "unknown ticket"; return LEIDEN_ERR_ARG; }
   ServerRequest *r = it->second;
-  S->cv_done.wait(lk, [&] { return r->done; });
+  if (timeout_ms < 0) {
+    S->cv_done.wait(lk, [&] { return r->done; });
+  } else if (!S->cv_done.wait_for(lk, std::chrono::duration<double, std::milli>(timeout_ms), [&] { return r->done; })) {
+    S->err = "request not done within the time limit (the ticket stays valid)";
+    return LEIDEN_ERR_TIMEOUT;
+  }
   S->reqs.erase(it);
   lk.unlock();
   if (membership_out && r->keep && !r->membership.empty())
@@ -280,6 +285,11 @@ leiden_status leiden_server_wait(leiden_server *S, int64_t ticket, int32_t *memb
   }
   delete r;
   return st;
+}
+
+leiden_status leiden_server_wait(leiden_server *S, int64_t ticket, int32_t *membership_out, double *latency_ms,
+                                 double *service_ms) {
+  return leiden_server_wait_for(S, ticket, -1.0, membership_out, latency_ms, service_ms);
 }
 
 leiden_status leiden_server_remove_graph(leiden_server *S, int32_t graph) {

@@ -78,7 +78,7 @@ __global__ void k_trc_insert(int64_t N, const int32_t *Cold, const int32_t *Cnew
     int64_t sum = ld_group_sum_i64(peers, kw);
     if (!take || !ld_group_leader(peers)) continue;
     uint64_t sl = hash64(key) & mask;
-    while (true) {
+    for (uint64_t probe = 0; ld_ok(probe <= mask, LD_CHK_PROBE); probe++) {
       unsigned long long k = atomicCAS((unsigned long long *)&keys[sl], EMPTY64, key);
       if (k == EMPTY64) list[atomicAdd(occ, 1)] = (int32_t)sl;
       if (k == EMPTY64 || k == key) {
@@ -314,3 +314,5 @@ void recompute_weights(leiden_handle *h) {
   ld_note_launch(), k_rowsum<<<grid_for(h->n * 32, TB), TB, 0, s>>>(h->n, h->g_off, h->g_deg, h->g_w, h->K, h->dcnt,
                                                                     h->gid0, h->gc.m2);
 }
+
+LD_CHECK_WORD_READER(check_word_track)

@@ -38,7 +38,10 @@ class leiden_stats(ctypes.Structure):
         "aggregate_arcs", "affected", "communities", "batch_arcs")] + [(k, ctypes.c_double) for k in (
         "ms_total", "ms_batch", "ms_move", "ms_refine", "ms_aggregate", "ms_track")] + [
         (k, ctypes.c_int64 * 3) for k in ("lmk_launches", "lmk_vertices", "lmk_arcs", "lmk_bytes")] + [
-        ("lmk_ms", ctypes.c_double * 3), ("rebuilds", ctypes.c_int64)]
+        ("lmk_ms", ctypes.c_double * 3), ("rebuilds", ctypes.c_int64), ("phase_ms", ctypes.c_double * 6),
+        ("phase_bytes", ctypes.c_int64 * 6)]
+
+PHASES = ("batch", "move", "split", "refine", "aggregate", "track")
 
 
 class leiden_tuning(ctypes.Structure):
@@ -59,15 +62,17 @@ class LeidenError(RuntimeError):
 
 
 def library_path() -> str:
-    return _build.LIB_PATH
+    """The library this process loads: libleiden_gb300.so, or the checked
+    build libleiden_gb300_checked.so when LEIDEN_GB300_CHECKED=1."""
+    return _build.LIB_PATH_CHECKED if os.environ.get("LEIDEN_GB300_CHECKED") == "1" else _build.LIB_PATH
 
 
 def load():
-    """Load libleiden_gb300.so (raises if it has not been built)."""
+    """Load the library (raises if it has not been built)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB_PATH
+    path = library_path()
     if not os.path.exists(path):
         raise OSError(f"{path} not found: build it with paper_2410_15451_gb300._build.build()")
     lib = ctypes.CDLL(path)
@@ -111,6 +116,7 @@ def load():
                        ("leiden_server_add_graph", [vp, i64, vp, vp, vp, P(i32)]),
                        ("leiden_server_submit", [vp, i32, vp, i64, vp, i64, ctypes.c_int, i32, P(i64)]),
                        ("leiden_server_wait", [vp, i64, vp, P(d), P(d)]),
+                       ("leiden_server_wait_for", [vp, i64, d, vp, P(d), P(d)]),
                        ("leiden_server_membership", [vp, i32, vp]),
                        ("leiden_server_remove_graph", [vp, i32]),
                        ("leiden_server_get_stats", [vp, P(leiden_server_stats)])):
@@ -122,6 +128,10 @@ def load():
     lib.leiden_server_destroy.restype = None
     lib.leiden_kernel_launches.argtypes = []
     lib.leiden_kernel_launches.restype = i64
+    lib.leiden_checked_build.argtypes = []
+    lib.leiden_checked_build.restype = i32
+    lib.leiden_check_selftest.argtypes = [vp]
+    lib.leiden_check_selftest.restype = i32
     lib.leiden_last_error.argtypes = [vp]
     lib.leiden_last_error.restype = ctypes.c_char_p
     lib.leiden_destroy.argtypes = [vp]
@@ -314,6 +324,14 @@ def leiden_kernel_launches() -> int:
     return int(load().leiden_kernel_launches())
 
 
+def leiden_checked_build() -> bool:
+    return bool(load().leiden_checked_build())
+
+
+def leiden_check_selftest(cuda_stream=None) -> int:
+    return int(load().leiden_check_selftest(cuda_stream))
+
+
 def leiden_last_error(h=None) -> str:
     m = load().leiden_last_error(h)
     return m.decode() if m else ""
@@ -494,6 +512,16 @@ class LeidenServer:
         out = np.zeros(self.sizes[graph], np.int32) if keep else None
         lat, svc = ctypes.c_double(), ctypes.c_double()
         self._check(load().leiden_server_wait(self.s, t, _ptr(out), ctypes.byref(lat), ctypes.byref(svc)), self.s)
+        return out, lat.value, svc.value
+
+    def wait_for(self, ticket, timeout_ms):
+        """-> (membership or None, latency ms, service ms); LeidenError with
+        LEIDEN_ERR_TIMEOUT if not done in time (the ticket stays valid)."""
+        t, graph, keep = ticket
+        out = np.zeros(self.sizes[graph], np.int32) if keep else None
+        lat, svc = ctypes.c_double(), ctypes.c_double()
+        self._check(load().leiden_server_wait_for(self.s, t, float(timeout_ms), _ptr(out), ctypes.byref(lat),
+                                                  ctypes.byref(svc)), self.s)
         return out, lat.value, svc.value
 
     def membership(self, graph) -> np.ndarray:

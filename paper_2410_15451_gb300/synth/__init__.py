@@ -1,7 +1,7 @@
 """Seeded synthetic graphs and batch updates (no community-detection arithmetic).
 
 The workloads stand in for the paper's SuiteSparse graphs and random batch
-updates (Section 4.1.3 "Batch generation": 80% insertions of uniformly chosen
+updates (Evaluation, "Batch generation": 80% insertions of uniformly chosen
 vertex pairs, 20% deletions of uniformly chosen existing edges, unit weights,
 undirected, no new vertices).  Generation runs in ``libsynth.so`` (plain C,
 SplitMix64 counter-based draws), so the same seed gives the same bytes on any

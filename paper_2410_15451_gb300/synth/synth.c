@@ -4,7 +4,7 @@
  * This module holds no part of the community-detection arithmetic.  It only
  * draws graphs and edge batches whose shapes follow the paper's workloads
  * (random batch updates with an 80:20 insertion:deletion mix, unit weights,
- * undirected, no new vertices -- Section 4.1.3 "Batch generation"), and it is
+ * undirected, no new vertices -- Evaluation, "Batch generation"), and it is
  * the one piece of code shared by the CUDA path's tests and the CPU oracle's.
  *
  * Every random number is a pure function of (seed, stream, counter): the

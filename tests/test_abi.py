@@ -51,9 +51,36 @@ def test_default_params_match_the_paper(lib):
     assert p.deterministic == 1 and p.classes == 4
 
 
-def test_struct_layouts(lib):
-    assert ctypes.sizeof(L.leiden_params) == 8 * 3 + 4 * 4 + 8 + 4 * 5 + 4  # + tail padding
-    assert ctypes.sizeof(L.leiden_stats) == 8 * 11 + 8 * 6 + 8 * 3 * 5 + 8
+def _c_layout(struct, fields):
+    """sizeof and offsetof of a struct of include/leiden_gb300.h as a C
+    compiler lays it out (gcc, host ABI)."""
+    import subprocess
+    import tempfile
+
+    src = "#include <stddef.h>\n#include <stdio.h>\n#include \"leiden_gb300.h\"\nint main(void) {\n"
+    src += f'  printf("%zu\\n", sizeof({struct}));\n'
+    for f in fields:
+        src += f'  printf("%zu\\n", offsetof({struct}, {f}));\n'
+    src += "  return 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c, exe = os.path.join(d, "t.c"), os.path.join(d, "t")
+        open(c, "w").write(src)
+        subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        out = [int(x) for x in subprocess.check_output([exe]).split()]
+    return out[0], out[1:]
+
+
+@pytest.mark.parametrize("struct,cls", [("leiden_params", "leiden_params"), ("leiden_stats", "leiden_stats"),
+                                        ("leiden_tuning", "leiden_tuning"),
+                                        ("leiden_server_stats", "leiden_server_stats")])
+def test_struct_layouts_match_the_c_header(struct, cls):
+    """The binding's ctypes structures have the header's size and field
+    offsets (compiled with gcc)."""
+    ct = getattr(L, cls)
+    names = [f for f, _ in ct._fields_]
+    size, offsets = _c_layout(struct, names)
+    assert ctypes.sizeof(ct) == size
+    assert [getattr(ct, f).offset for f in names] == offsets
 
 
 def test_create_rejects_bad_input_without_touching_the_gpu(lib):

@@ -4,6 +4,8 @@ are held against the oracle's component labelling and modularity on small
 graphs, including memberships with a disconnected community."""
 from __future__ import annotations
 
+import os
+
 import numpy as np
 import pytest
 
@@ -90,3 +92,35 @@ def test_oracle_baseline_runs_in_a_spawned_process():
     assert "R-MAT scale 13" in cb["sample"] and "batches 2..3" in cb["sample"]
     # the same numbers of batches as the GPU arm draws, hence the same batches
     assert bench.stream_batches(args) == 2 + 2 * 3 + 2 * (bench.ND_DS_STEPS + 1)
+
+
+def test_ncu_summary_reads_the_capture_csv(tmp_path):
+    """--ncu-summary: per-kernel launches, time and DRAM bytes from an ncu
+    CSV (units normalised), the local-moving launches (template kind 0) per
+    launch, and the source hashes the roofline's traffic is keyed to."""
+    import json
+
+    hdr = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size",'
+           '"Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"')
+    rows = []
+    launches = [("void <unnamed>::k_decide_block<int, 0>(<unnamed>::Args)", 10.0, 2.0, 0.5),
+                ("void <unnamed>::k_decide_block<long, 0>(<unnamed>::Args)", 20.0, 4.0, 1.5),
+                ("void <unnamed>::k_decide_block<int, 1>(<unnamed>::Args)", 5.0, 1.0, 0.0),
+                ("void <unnamed>::k_expand(const leiden_edge *, long)", 3.0, 0.25, 0.25)]
+    for i, (name, us, rd, wr) in enumerate(launches):
+        for metric, unit, val in (("dram__bytes_read.sum", "Mbyte", rd), ("dram__bytes_write.sum", "Mbyte", wr),
+                                  ("gpu__time_duration.sum", "usecond", us)):
+            rows.append(f'"{i}","1","python","h","{name}","1","7","(128, 1, 1)","(1064, 1, 1)","0","10.3",'
+                        f'"Command line profiler metrics","{metric}","{unit}","{val:,}"')
+    csv_path = tmp_path / "launches.csv"
+    csv_path.write_text("==PROF== Connected\n" + hdr + "\n" + "\n".join(rows) + "\n")
+    out = bench.ncu_summary(str(csv_path), "ncu ...", out_json=str(tmp_path / "t.json"),
+                            out_md=str(tmp_path / "t.md"))
+    lm = out["local_moving"]["k_decide_block"]
+    assert lm["launches"] == 2
+    assert lm["traffic_bytes_per_launch"] == (2.5e6 + 5.5e6) / 2
+    assert out["kernels"]["k_decide_block<int, 1>"]["launches"] == 1
+    assert abs(sum(k["share"] for k in out["kernels"].values()) - 1) < 1e-12
+    assert json.loads((tmp_path / "t.json").read_text())["source_sha256"]["move.cu"] == \
+        bench.source_code_sha256(os.path.join(bench.CSRC, "move.cu"))
+    assert "| k_expand | 1 |" in (tmp_path / "t.md").read_text()

@@ -279,6 +279,13 @@ def test_stats_timers_and_launch_counter_leave_results_unchanged():
     assert n1 - n0 >= 10
     s = a.stats()
     assert s["lmk_launches"][0] > 0 and s["lmk_ms"][0] > 0 and s["ms_move"] > 0
+    # phase times from events at the phase boundaries, bytes from the counters
+    assert all(x >= 0 for x in s["phase_ms"]) and s["phase_ms"][L.PHASES.index("move")] == s["ms_move"]
+    assert abs(sum(s["phase_ms"]) - s["ms_total"]) < 1e-9 * max(1.0, s["ms_total"])
+    assert all(b > 0 for b in s["phase_bytes"])
+    assert s["phase_bytes"][L.PHASES.index("move")] >= sum(s["lmk_bytes"])
+    assert s["affected"] == a.trace()["affected"]
+    assert b.stats()["phase_bytes"] == s["phase_bytes"] and b.stats()["phase_ms"] == [0.0] * 6
     v, e = s["lmk_vertices"], s["lmk_arcs"]
     # every visit of a vertex with arcs goes through one of the three kernels
     assert v[0] + v[1] + v[2] <= s["lm_vertices"] and e[0] + e[1] + e[2] == s["lm_arcs"]

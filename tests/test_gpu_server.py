@@ -1,6 +1,6 @@
 """Serving runtime (needs a GB300): resident graphs, footprint admission,
 requests from several threads at once; every result must equal the one the
-graph gets alone, bit for bit (deterministic schedule)."""
+graph gets alone and the CPU oracle's, bit for bit (deterministic schedule)."""
 from __future__ import annotations
 
 import threading
@@ -9,6 +9,7 @@ import time
 import numpy as np
 import pytest
 
+import oracle
 from paper_2410_15451_gb300 import leiden as L
 from paper_2410_15451_gb300 import synth
 
@@ -57,9 +58,21 @@ def _alone(g, lst):
     return out
 
 
+ORACLE_MODE = {L.LEIDEN_ND: oracle.ND, L.LEIDEN_DS: oracle.DS, L.LEIDEN_DF: oracle.DF}
+
+
+def _oracle(g, lst):
+    o = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    o.static()
+    return [o.update(d, i, ORACLE_MODE[m]) for d, i, m in lst]
+
+
 def test_server_results_equal_results_alone():
     gs, reqs = _workload()
-    expected = [_alone(g, lst) for g, lst in zip(gs, reqs)]
+    expected = [_oracle(g, lst) for g, lst in zip(gs, reqs)]
+    for k, (g, lst) in enumerate(zip(gs, reqs)):  # each graph alone on the GPU equals the oracle
+        for step, c in enumerate(_alone(g, lst)):
+            assert np.array_equal(c, expected[k][step]), (k, step)
     fp = [L.leiden_footprint_bytes(g.n, g.off) for g in gs]
     budget = sum(fp[:4]) + 1  # graphs 4 and 5 wait for memory
     srv = L.LeidenServer(budget, slots=3)
@@ -115,5 +128,32 @@ def test_server_bad_batch_leaves_the_graph_unchanged():
     assert np.array_equal(srv.membership(gid), before)
     d, i = synth.random_batch(g, 50, seed=92)
     memb, _, _ = srv.wait(srv.submit(gid, d, i, L.LEIDEN_DF, keep_membership=True))
-    assert np.array_equal(memb, _alone(g, [(d, i, L.LEIDEN_DF)])[0])
+    assert np.array_equal(memb, _oracle(g, [(d, i, L.LEIDEN_DF)])[0])
+    srv.close()
+
+
+def test_server_wait_for_times_out_then_the_ticket_completes():
+    """A bounded wait on a request of a graph still waiting for memory gives
+    up with LEIDEN_ERR_TIMEOUT and leaves the ticket valid; once memory is
+    freed the graph is admitted and the same ticket completes with the
+    oracle's result.  The failure is made on the host (no GPU fault)."""
+    g1 = synth.planted_partition(1200, 12, 10, 0.2, 93)
+    g2 = synth.planted_partition(1500, 15, 10, 0.2, 94)
+    fp1 = L.leiden_footprint_bytes(g1.n, g1.off)
+    srv = L.LeidenServer(fp1 + 1, slots=2)  # g2 does not fit while g1 is resident
+    id1 = srv.add_graph(g1.n, g1.off, g1.col, g1.w)
+    while srv.stats()["graphs_resident"] < 1:
+        time.sleep(0.01)
+    id2 = srv.add_graph(g2.n, g2.off, g2.col, g2.w)
+    d, i = synth.random_batch(g2, 40, seed=95)
+    t = srv.submit(id2, d, i, L.LEIDEN_DF, keep_membership=True)
+    for _ in range(2):
+        with pytest.raises(L.LeidenError) as e:
+            srv.wait_for(t, 50.0)
+        assert e.value.status == L.LEIDEN_ERR_TIMEOUT
+    assert srv.stats()["graphs_waiting"] == 1
+    srv.remove_graph(id1)
+    memb, lat, svc = srv.wait_for(t, 120000.0)
+    assert lat >= svc >= 0.0
+    assert np.array_equal(memb, _oracle(g2, [(d, i, L.LEIDEN_DF)])[0])
     srv.close()

@@ -71,7 +71,7 @@ def test_modularity_matches_newman_pairwise_form(seed):
     C = rng.integers(0, 4, n).astype(np.int32)
     q, num = oracle.modularity(off, col, w, C)
     assert num == newman_numerator(off, col, w, C)
-    assert -0.5 <= q <= 1.0  # range stated in Section 3.2
+    assert -0.5 <= q <= 1.0  # range stated in Preliminaries, "Modularity"
 
 
 # ---------------------------------------------------------------- Eq. 2
@@ -310,7 +310,7 @@ def test_marking_set_algebra(schedule):
 @pytest.mark.parametrize("schedule", SCHEDULES)
 def test_empty_batch_changes_nothing(mode, schedule):
     """DS and DF mark nothing on an empty batch and return C^{t-1} unchanged;
-    ND re-processes every vertex (Section 2.4.1), so it may still improve Q."""
+    ND re-processes every vertex (Preliminaries, the Naive-dynamic approach), so it may still improve Q."""
     g, o, _, _ = _dyn_setup(schedule=schedule)
     before = o.state()
     q0 = o.modularity()
@@ -329,7 +329,7 @@ def test_empty_batch_changes_nothing(mode, schedule):
 
 @pytest.mark.parametrize("schedule", SCHEDULES)
 def test_delete_then_reinsert_tracks_ids(schedule):
-    """The stability protocol of Section 3.1: delete a batch, reinsert it; with
+    """The stability protocol of Approach, "Improving stability": delete a batch, reinsert it; with
     tracking, most vertices keep the community id they had before."""
     g = synth.planted_partition(3000, 30, 14, 0.2, 77)
     o = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=schedule)
@@ -344,7 +344,7 @@ def test_delete_then_reinsert_tracks_ids(schedule):
 
 @pytest.mark.parametrize("schedule", SCHEDULES)
 def test_refinement_threshold_rule(schedule):
-    """Alg. leidenmk with tau_re = 0.6 (Section 3.3): deletions inside a
+    """Alg. leidenmk with tau_re = 0.6 (Approach, "Minimizing communities to refine"): deletions inside a
     community add to its cumulative change dSigma (both directions count);
     the community is marked for refinement in the batch where
     dSigma/Sigma first exceeds 0.6, and its dSigma then resets to 0."""
@@ -396,7 +396,7 @@ def test_invalid_batches_rejected_without_change():
 
 @pytest.mark.parametrize("schedule", SCHEDULES)
 def test_dynamic_quality_close_to_static(schedule):
-    """Section 4.2: the dynamic result stays close to static Leiden's Q."""
+    """Evaluation, "Performance comparison": the dynamic result stays close to static Leiden's Q."""
     g = synth.planted_partition(4000, 40, 14, 0.3, 55)
     dels, ins = synth.random_batch(g, 400, seed=56)
     g2 = synth.apply_batch_numpy(g, dels, ins)
@@ -439,7 +439,7 @@ def test_sync_and_seq_agree_on_planted_partition():
     assert abs(q[oracle.SEQ] - q[oracle.SYNC]) < 0.002
 
 
-# ---- ablation switches (Section 4.1.3 splitting of changed communities; the
+# ---- ablation switches (Approach, "Minimizing communities to split": the
 # convergence test of Alg. "leiden" read with AND, as printed, or OR)
 
 def test_split_all_changes_nothing_in_static_leiden():
