@@ -21,7 +21,9 @@ live) and of the whole step by phase, the library's kernel launches in the
 timed steps, the oracle timed on one host core on the same graph and batch
 stream (a spawned process, in parallel with the GPU work), SM clocks sampled
 during the timed region, and the large web-like configuration (1B edges,
-20 DF batches of 1e-4|E|, checked at full size) as `large`.
+20 DF batches of 1e-4|E|, checked at full size) as `large`, and the batched
+configuration (512 planted-partition graphs in one handle against one call
+per graph, memberships compared graph by graph) as `batched`.
 
 --impl reference times the CPU oracle (plain sequential C, one host thread)
 on the same workload: the same R-MAT scale-22 graph and batch stream, static
@@ -69,7 +71,8 @@ def parse():
                     help="the large web-like configuration: degree-corrected planted partition, 20 DF batches, "
                          "checked at full size")
     ap.add_argument("--large-n", type=int, default=30_000_000)
-    ap.add_argument("--no-large", action="store_true", help="leave the large configuration out of the main line")
+    ap.add_argument("--no-large", action="store_true",
+                    help="leave the large and the batched configurations out of the main line")
     ap.add_argument("--ablation", action="store_true",
                     help="DF updates under the ablation switches: split all, OR convergence, tau_re sweep")
     ap.add_argument("--stability", action="store_true",
@@ -81,7 +84,7 @@ def parse():
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--mean-gap-us", type=float, default=200.0)
     ap.add_argument("--slots", type=int, default=8)
-    ap.add_argument("--serve-budget-gb", type=float, default=200.0)
+    ap.add_argument("--serve-budget-gb", type=float, default=250.0)
     ap.add_argument("--ncu-summary", default=None, metavar="CSV",
                     help="write the machine-read DRAM-traffic summary and the launch list from an ncu CSV")
     ap.add_argument("--ncu-command", default="", help="the ncu command line that made the CSV (recorded)")
@@ -469,7 +472,7 @@ def run_ours(args, rank, world, local_rank):
                 bs = make_batches(synth.Graph(g.n, off, col, w.astype(np.int32)), nb, sz, seed + int(1 / frac))
             except RuntimeError:
                 continue
-            ts = []
+            ts, phases = [], []
             for k, (d, i) in enumerate(bs):
                 dd, di = torch.from_numpy(d).to(dev), torch.from_numpy(i).to(dev)
                 torch.cuda.synchronize()
@@ -477,8 +480,10 @@ def run_ours(args, rank, world, local_rank):
                                                                          L.LEIDEN_DF, d_out), flush)
                 if k > 0:
                     ts.append(ms)
+                    phases.append(gpu.stats()["phase_ms"])
             sweep[f"{frac:g}"] = dict(batch_edges=sz, ms_mean=float(np.mean(ts)), p99_ms=float(np.percentile(ts, 99)),
-                                      edges_per_s=sz / (np.mean(ts) / 1e3))
+                                      edges_per_s=sz / (np.mean(ts) / 1e3),
+                                      phase_ms={k: float(v) for k, v in zip(L.PHASES, np.mean(phases, axis=0))})
             off, col, w = gpu.graph()
     result["sweep"] = sweep
     gpu.close()
@@ -506,19 +511,35 @@ def source_code_sha256(path):
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
+# The timed kernels: name -> (source file, pattern of its timed launches in
+# the ncu launch list).  The local-moving kernels are timed in their move
+# instantiations (template kind 0), the others in all of theirs.
+TIMED_KERNELS = {"k_decide_warp": ("move.cu", r"k_decide_warp<[^,]+, 0>$"),
+                 "k_decide_block": ("move.cu", r"k_decide_block<[^,]+, 0>$"),
+                 "k_huge_scan": ("move.cu", r"k_huge_scan<[^,]+, 0>$"),
+                 "k_split_sample": ("phases.cu", r"k_split_sample$"),
+                 "k_agg_chunk_scan": ("phases.cu", r"k_agg_chunk_scan<[^>]+>$"),
+                 "k_merge_mid": ("batch.cu", r"k_merge_mid$")}
+
+
 def ncu_traffic(kernel):
-    """DRAM bytes per launch of the local-moving launches of `kernel` from the
+    """DRAM bytes per launch of `kernel`'s timed launches from the
     machine-written summary of one ncu capture (written by --ncu-summary);
-    None when absent or when move.cu changed since the capture."""
+    None when absent or when the kernel's source file changed since the
+    capture (comments aside)."""
+    import re
+
+    src, pat = TIMED_KERNELS[kernel]
     try:
         d = json.load(open(TRAFFIC_JSON))
-        sha = source_code_sha256(os.path.join(CSRC, "move.cu"))
+        sha = source_code_sha256(os.path.join(CSRC, src))
     except (OSError, ValueError):
         return None
-    if d.get("source_sha256", {}).get("move.cu") != sha:
+    if d.get("source_sha256", {}).get(src) != sha:
         return None
-    k = d.get("local_moving", {}).get(kernel)
-    return float(k["traffic_bytes_per_launch"]) if k else None
+    sel = [k for name, k in d.get("kernels", {}).items() if re.match(pat, name)]
+    n = sum(k["launches"] for k in sel)
+    return sum(k["dram_read_bytes"] + k["dram_write_bytes"] for k in sel) / n if n else None
 
 
 def ncu_summary(csv_path, command, out_json=TRAFFIC_JSON,
@@ -591,27 +612,36 @@ def ncu_summary(csv_path, command, out_json=TRAFFIC_JSON,
     return out
 
 
+XK_NAMES = ("k_split_sample", "k_agg_chunk_scan", "k_merge_mid")
+
+
 def roofline_kernels(stats_list):
-    """Live roofline of the local-moving kernels (the dominant step): the
-    algorithmic bytes counted on the device over their launches in the timed
-    steps, divided by their summed CUDA-event time (an event pair around each
-    launch on the handle's stream).  Returns (dominant kernel's entry, all)."""
+    """Live roofline of the timed kernels -- the three local-moving kernels
+    and the largest kernels of splitting, aggregation and the batch merge,
+    the top of the ncu launch list: the algorithmic bytes counted on the
+    device over their launches in the timed steps, divided by their summed
+    CUDA-event time (an event pair around each launch on the handle's
+    stream).  Returns (entry of the kernel with the largest summed time,
+    all entries)."""
     peak, src = hbm_peak()
     out = {}
-    for k, name in enumerate(LMK_NAMES):
-        launches = sum(s["lmk_launches"][k] for s in stats_list)
-        ms = sum(s["lmk_ms"][k] for s in stats_list)
+    rows = [(name, "lmk_launches", "lmk_ms", "lmk_bytes", k) for k, name in enumerate(LMK_NAMES)]
+    rows += [(name, "xk_launches", "xk_ms", "xk_bytes", k) for k, name in enumerate(XK_NAMES)]
+    for name, kl, km, kb, k in rows:
+        launches = sum(s[kl][k] for s in stats_list)
+        ms = sum(s[km][k] for s in stats_list)
         if launches == 0 or ms <= 0:
             continue
-        per_launch = sum(s["lmk_bytes"][k] for s in stats_list) / launches
+        per_launch = sum(s[kb][k] for s in stats_list) / launches
         achieved = per_launch / (ms / launches / 1e3) / 1e9
         out[name] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": ncu_traffic(name), "kernel": name, "launches": launches, "ms_total": ms,
                      "algorithmic_bytes_per_launch": per_launch, "ms_per_launch": ms / launches,
-                     "visits": sum(s["lmk_vertices"][k] for s in stats_list),
-                     "arcs": sum(s["lmk_arcs"][k] for s in stats_list),
                      "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)" if src == "measured"
                      else "fallback 6.8 TB/s"}
+        if kl == "lmk_launches":
+            out[name]["visits"] = sum(s["lmk_vertices"][k] for s in stats_list)
+            out[name]["arcs"] = sum(s["lmk_arcs"][k] for s in stats_list)
     if not out:
         return None, {}
     dom = max(out.values(), key=lambda r: r["ms_total"])
@@ -1109,17 +1139,30 @@ def serve_record(args):
             ii += n_ins
     gen_s = time.time() - t0
     nv, ne = int(sum(g.n for g in gs)), int(sum(g.off[-1] for g in gs) // 2)
+    need = sum(L.leiden_footprint_bytes(g.n, g.off) for g in gs)
+    need += args.slots * max(L.leiden_transient_bytes(g.n, g.off) for g in gs)
+    print(f"serve: {len(gs)} graphs, {nv} vertices, {ne} edges generated in {gen_s:.0f} s; resident footprint "
+          f"with {args.slots} slots' aggregation room {need / 2**30:.1f} GiB of a {args.serve_budget_gb:g} GiB "
+          f"budget", file=sys.stderr, flush=True)
+    if need > args.serve_budget_gb * 2**30:
+        raise RuntimeError(f"the graphs need {need / 2**30:.1f} GiB, above the {args.serve_budget_gb:g} GiB budget")
     srv = L.LeidenServer(int(args.serve_budget_gb * 2**30), slots=args.slots)
     ids = [srv.add_graph(g.n, g.off, g.col, g.w) for g in gs]
     del gs
     gc.collect()
     t1 = time.time()
+    last, last_t = -1, time.time()
     while srv.stats()["graphs_resident"] < len(ids):
         st = srv.stats()
-        if st["graphs_waiting"] == 0 and st["graphs_resident"] < len(ids):
+        if st["graphs_waiting"] == 0 and st["graphs_resident"] < len(ids) and st["requests_running"] == 0:
             raise RuntimeError("some graphs failed admission")
+        if st["graphs_resident"] != last:
+            last, last_t = st["graphs_resident"], time.time()
+        elif time.time() - last_t > 600:
+            raise RuntimeError(f"admission made no progress for 10 minutes ({last} of {len(ids)} resident)")
         time.sleep(0.05)
     admit_s = time.time() - t1
+    print(f"serve: all graphs resident after {admit_s:.0f} s", file=sys.stderr, flush=True)
 
     def arrivals(first, gaps):
         """Submit requests first.. with the given gaps; wait for all of them."""
@@ -1221,10 +1264,12 @@ def main():
     if args.autotune:
         return run_autotune(args) if rank == 0 else 0
     r = run_ours(args, rank, world, local_rank)
-    large = None
+    large = batched = None
     if rank == 0 and world == 1 and not args.no_large:
         dev = torch.device("cuda", local_rank)
         large = large_record(args, torch.cuda.current_stream(dev), dev)
+        torch.cuda.empty_cache()
+        batched = batched_record(args, warmup=1, steps=3)
     cb = base.result() if base is not None else None
     if rank == 0:
         chk = r["checks"]
@@ -1245,13 +1290,14 @@ def main():
             "e2e": {"value": r["e2e"], "unit": "edges/s", "h2d_bytes_per_step": r["size"] * 12,
                     "d2h_bytes_per_step": r["n"] * 4, "p99_ms": r["e2e_p99"]},
             "roofline": dom,
-            "roofline_lm_kernels": lmk,
+            "roofline_kernels": lmk,
             "roofline_step": roofline_step(r["lm_stats"], r["mean_ms"]),
             "gpu_launches": r["gpu_launches"],
             "cpu_baseline": cb,
             "clocks": r["clk"],
             "sweep": r["sweep"],
             "large": large,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

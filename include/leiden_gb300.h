@@ -120,6 +120,16 @@ typedef struct {
    * achieved bandwidth for a roofline of the whole call. */
   double phase_ms[6];
   int64_t phase_bytes[6];
+  /* The largest kernels of the other phases, timed like the local-moving
+   * ones: [0] split sampling (per listed vertex 20 B: list entry, C, offset,
+   * degree; per arc read 8 B: col, C of the neighbour), [1] the chunked scan
+   * of communities above 1024 member arcs in aggregation (per arc: col, C of
+   * the neighbour and the weight), [2] the block merge of touched rows of
+   * 257..4096 arcs (per arc: the old row read and the new row written,
+   * 16 B; per batch arc 16 B). */
+  int64_t xk_launches[3];
+  int64_t xk_bytes[3];
+  double xk_ms[3];
 } leiden_stats;
 
 /* Phases of a call, as timed and counted in leiden_stats. */
@@ -294,8 +304,16 @@ leiden_status leiden_create_batched(const leiden_params *params, int32_t graphs,
 /* Device bytes a handle for this graph (CSR offsets[n+1]) is expected to
  * hold: the allocations of leiden_create plus an allowance for batch buffers
  * and aggregated-level hash tables that grow on demand.  -1 on bad input.
- * Used by the server below to admit graphs by footprint. */
+ * Used by the server below to admit graphs by footprint.  Not included: the
+ * arcs of the aggregated levels, which a call draws from the device's
+ * stream-ordered memory pool only while it aggregates (see the next). */
 int64_t leiden_footprint_bytes(const leiden_params *params, int64_t n, const int64_t *offsets);
+
+/* Device bytes a call on this graph draws from the stream-ordered pool while
+ * it aggregates (two levels of arcs, 24 B per arc of the graph), returned at
+ * the end of the call; -1 on bad input.  The server keeps room for `slots`
+ * of these (the largest admitted graph's).  Library extension. */
+int64_t leiden_transient_bytes(int64_t n, const int64_t *offsets);
 
 /* Number of graphs of the handle (1 for leiden_create handles). */
 int32_t leiden_batch_graphs(const leiden_handle *h);

@@ -56,6 +56,29 @@ int64_t level0_huge_slots(const std::vector<int32_t> &deg) {
   return slots;
 }
 
+bool acquire_agg_buffers(leiden_handle *h) {
+  if (h->y_col[0]) return true;
+  size_t slots = (size_t)h->g_arcs + 1;
+  for (int k = 0; k < 2; k++) {
+    if (cudaMallocAsync((void **)&h->y_col[k], slots * sizeof(int32_t), h->stream) != cudaSuccess ||
+        cudaMallocAsync((void **)&h->y_w[k], slots * sizeof(int64_t), h->stream) != cudaSuccess) {
+      cudaGetLastError();
+      release_agg_buffers(h);
+      return false;
+    }
+  }
+  return true;
+}
+
+void release_agg_buffers(leiden_handle *h) {
+  for (int k = 0; k < 2; k++) {
+    if (h->y_col[k]) cudaFreeAsync(h->y_col[k], h->stream);
+    if (h->y_w[k]) cudaFreeAsync(h->y_w[k], h->stream);
+    h->y_col[k] = nullptr;
+    h->y_w[k] = nullptr;
+  }
+}
+
 void ph_mark(leiden_handle *h, int tag) {
   if (!(h->p.collect_stats & 1)) return;
   if (h->ph_ev.size() < (size_t)h->ph_used + 1) {
@@ -104,6 +127,12 @@ void kt_end(leiden_handle *h) {
   if (!(h->p.collect_stats & 2) || h->kt_ev.size() < 2 * (size_t)(h->kt_used + 1)) return;
   cudaEventRecord(h->kt_ev[2 * h->kt_used + 1], h->stream);
   h->kt_used++;
+}
+
+void kt_reset(leiden_handle *h) {
+  h->kt_used = 0;
+  for (int k = 0; k < KT_KERNELS; k++) { h->kt_ms[k] = 0; h->kt_launches[k] = 0; }
+  cudaMemsetAsync(h->dcnt->xk_bytes, 0, sizeof(h->dcnt->xk_bytes), h->stream);
 }
 
 void kt_resolve(leiden_handle *h) {
@@ -210,8 +239,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   const leiden_params &p = h->p;
   int64_t N = h->n;
   memset(h->trace, 0, sizeof(h->trace));
-  h->kt_used = 0;
-  for (int k = 0; k < KT_KERNELS; k++) { h->kt_ms[k] = 0; h->kt_launches[k] = 0; }
+  release_agg_buffers(h);  // a call that failed part-way may have left them
   const bool B = h->G > 1;
   const int G = h->G;
   GraphCounters hg = B ? gc_layout(h->gc_host, G) : GraphCounters{};
@@ -238,11 +266,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   // listed vertex), with the sizes of the arrays it reads and writes.
   ph_mark(h, LEIDEN_PHASE_MOVE);
   ph_bytes(h, LEIDEN_PHASE_MOVE, 45 * N + N / 8);  // dV -> frontier bits; Ctop; copies of C', K', Sigma'
-  mark_unprocessed_from_flags(h, h->dV, N);
-  launch_iota_i32(h->Ctop, N, s);
-  CK(cudaMemcpyAsync(h->Cp, h->C, (size_t)N * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(h->Kp, h->K, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(h->Sp, h->Sig, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+  pass_init(h);
   CK(cudaMemsetAsync(&h->dcnt->processed, 0, 14 * sizeof(int64_t), s));  // processed .. lmk_bytes
   int64_t m2 = h->m2;
   LevelGraph g = level0(h);
@@ -412,6 +436,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
       ncomm = tot;
     }
     lookup_dendrogram(h);
+    if (!acquire_agg_buffers(h)) { h->err = "aggregation buffers (stream-ordered pool)"; return LEIDEN_ERR_OOM; }
     aggregate(h, g, ncomm, slot);
     reset_next_pass(h, ncomm, slot);
     level_maxdeg(h, h->y_deg[slot], ncomm);
@@ -453,6 +478,7 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   else if (!looked_up) { h->err = "batched pass loop ended without a final lookup"; return LEIDEN_ERR_STATE; }
   track_communities(h);
   ph_mark(h, PHASE_END);
+  release_agg_buffers(h);
   sync_counters(h);
   CK(cudaGetLastError());
   ph_resolve(h);
@@ -471,7 +497,12 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   st.refine_arcs = h->hcnt->ref_arcs;
   kt_resolve(h);
   int64_t visits = 0, decide_bytes = 0;
-  for (int k = 0; k < KT_KERNELS; k++) {
+  for (int k = 0; k < 3; k++) {
+    st.xk_launches[k] = h->kt_launches[KT_SPLIT_SAMPLE + k];
+    st.xk_ms[k] = h->kt_ms[KT_SPLIT_SAMPLE + k];
+    st.xk_bytes[k] = h->hcnt->xk_bytes[k];
+  }
+  for (int k = 0; k < 3; k++) {
     st.lmk_vertices[k] = h->hcnt->lmk_visits[k];
     st.lmk_arcs[k] = h->hcnt->lmk_arcs[k];
     st.lmk_bytes[k] = h->hcnt->lmk_bytes[k];
@@ -529,6 +560,7 @@ leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_de
                         int64_t n_ins, leiden_mode mode) {
   h->stats = leiden_stats{};
   h->ph_used = 0;
+  kt_reset(h);
   ph_mark(h, LEIDEN_PHASE_BATCH);
   leiden_status st = batch_apply_and_mark(h, d_del, n_del, d_ins, n_ins, (int)mode);
   if (st != LEIDEN_OK) return st;
@@ -694,10 +726,17 @@ leiden_status leiden_create(const leiden_params *params, int64_t n, const int64_
   for (int k = 0; k < 2; k++) {
     A(dalloc(h, &h->y_off[k], n + 2));
     A(dalloc(h, &h->y_deg[k], n + 1));
-    A(dalloc(h, &h->y_col[k], total));
-    A(dalloc(h, &h->y_w[k], total));
   }
-  h->y_cap = total;
+  {
+    // keep the pool's memory cached between calls instead of returning it
+    // to the driver at every synchronisation
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    cudaGetLastError();
+  }
   int64_t tc = 1;
   while (tc < 2 * n) tc <<= 1;
   A(dalloc(h, &h->tr_keys, tc));
@@ -825,7 +864,7 @@ int64_t leiden_footprint_bytes(const leiden_params *params, int64_t n, const int
   b += 4 * n + 24 * n + n;                                            // C, K, Sigma, dSigma, dV
   b += 56 * (n + 1) + 72 * (n + 2) + 6 * (n + 1);                     // per-pass work arrays
   b += 4 * (n / 32 + 2) + 16 * n + 4 * (n + 1) + 8 * n;               // frontier, bins, hocc, cand
-  b += 2 * (8 * (n + 2) + 4 * (n + 1) + 12 * total);                  // aggregated levels
+  b += 2 * (8 * (n + 2) + 4 * (n + 1));                              // aggregated levels' offsets, degrees
   b += 16 * tc + 4 * n + (int64_t)scan_tmp_bytes(2 * n + 2);          // tracking, scans
   b += 16 * hs;                                                       // hub tables at level 0
   b += 8 * n + n / 8 + ((int64_t)32 << 20);                          // batch buffers, touched-row bits
@@ -870,6 +909,7 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   cudaStream_t s = h->stream;
   h->stats = leiden_stats{};
   h->ph_used = 0;
+  kt_reset(h);
   ph_mark(h, LEIDEN_PHASE_BATCH);
   int64_t N = h->n;
   // row sums (offsets, degree, K: 20 B per vertex; a weight per arc), degree
@@ -1117,6 +1157,11 @@ leiden_status leiden_get_stats(leiden_handle *h, leiden_stats *stats) {
   return LEIDEN_OK;
 }
 
+int64_t leiden_transient_bytes(int64_t n, const int64_t *offsets) {
+  if (n < 1 || !offsets) return -1;
+  return agg_buffer_bytes(offsets[n]);
+}
+
 int64_t leiden_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
 int32_t leiden_checked_build(void) {
@@ -1137,6 +1182,7 @@ const char *leiden_last_error(leiden_handle *h) {
 void leiden_destroy(leiden_handle *h) {
   if (!h) return;
   cudaSetDevice(h->device);
+  release_agg_buffers(h);
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void *q : h->owned)
     if (q) cudaFree(q);

@@ -311,21 +311,25 @@ __global__ void __launch_bounds__(MERGE_WARPS * 32) k_merge_small(MergeArgs A) {
 
 // Rows of MERGE_SMALL..MERGE_MID arcs: one block each, staged in shared
 // memory and written back after all of the row's reads.
-__global__ void __launch_bounds__(256) k_merge_mid(MergeArgs A, const int32_t *mid, const int32_t *count_p) {
+__global__ void __launch_bounds__(256) k_merge_mid(MergeArgs A, const int32_t *mid, const int32_t *count_p,
+                                                   int64_t *xk_bytes) {
   __shared__ int32_t scol[MERGE_MID];
   __shared__ int32_t sw[MERGE_MID];
   int64_t count = *count_p;
+  int64_t bytes = 0;  // algorithmic bytes (thread 0): old row read, new row written, the row's batch arcs
   for (int64_t k = blockIdx.x; k < count; k += gridDim.x) {
     int64_t r = mid[k];
     int64_t L = A.len[r];
+    int32_t u = A.rows[r];
+    if (threadIdx.x == 0) bytes += 8 * ((int64_t)A.deg[u] + L) + 16 * (A.dhi[r] - A.dlo[r] + A.ihi[r] - A.ilo[r]);
     merge_row_into(A, r, threadIdx.x, blockDim.x, scol, sw, A.dkey + A.dlo[r], A.nkey + A.ilo[r]);
     __syncthreads();
-    int32_t u = A.rows[r];
     int64_t o = A.dst[r];
     for (int64_t x = threadIdx.x; x < L; x += blockDim.x) { A.col[o + x] = scol[x]; A.w[o + x] = sw[x]; }
     if (threadIdx.x == 0) finish_row(A, r, u, L);
     __syncthreads();
   }
+  if (threadIdx.x == 0 && bytes) atomicAdd((unsigned long long *)xk_bytes, (unsigned long long)bytes);
 }
 
 // Long rows in chunks any block may take (items k of `large`, chunk offsets
@@ -678,8 +682,7 @@ leiden_status fail(leiden_handle *h, leiden_status st, const std::string &msg) {
 }  // namespace
 
 // Rebuild G^t with new capacities: rows keep their content (touched rows
-// come from the merge buffer).  Reallocates the aggregation buffers when the
-// arc capacity grows.
+// come from the merge buffer).
 static leiden_status rebuild_graph(leiden_handle *h, int64_t nrows_host, const int64_t *nrows_dev) {
   cudaStream_t s = h->stream;
   int64_t n = h->n;
@@ -718,15 +721,6 @@ static leiden_status rebuild_graph(leiden_handle *h, int64_t nrows_host, const i
   h->g_w = new_w;
   h->g_deg = new_deg;
   h->g_cap = total;
-  if (total > h->y_cap) {
-    for (int k = 0; k < 2; k++) {
-      release(h, h->y_col[k]);
-      release(h, h->y_w[k]);
-      if (grow(h, &h->y_col[k], total) != cudaSuccess || grow(h, &h->y_w[k], total) != cudaSuccess)
-        return fail(h, LEIDEN_ERR_OOM, "rebuild: aggregation buffers");
-    }
-    h->y_cap = total;
-  }
   return LEIDEN_OK;
 }
 
@@ -817,7 +811,10 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
                   b.row_dst, b.row_newcap, h->g_off, h->g_rcap};
       ld_note_launch(), k_merge_small<<<grid_for((nrows + MERGE_WARPS - 1) / MERGE_WARPS, 1, h->sm_count * 16), MERGE_WARPS * 32, 0,
                       s>>>(M);
-      ld_note_launch(), k_merge_mid<<<h->sm_count * 7, 256, 0, s>>>(M, b.row_mid, &cnt->mid_count);  // 32 KB: 7 per SM
+      kt_begin(h, KT_MERGE_MID);
+      ld_note_launch(), k_merge_mid<<<h->sm_count * 7, 256, 0, s>>>(M, b.row_mid, &cnt->mid_count,  // 32 KB: 7 per SM
+                                                                   &cnt->xk_bytes[2]);
+      kt_end(h);
       // long rows: chunks over the old row, then chunks over the new row
       int32_t *large = b.row_large;
       const int32_t *nlarge = &cnt->large_count;

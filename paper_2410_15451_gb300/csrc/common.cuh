@@ -52,6 +52,8 @@ struct DevCounters {
   int64_t affected;               // |dV|: vertices flagged affected (counted into the frontier)
   int64_t split_arcs;             // splitting: arcs of the vertices listed for splitting
   int64_t deg_sum;                // degree sum of the level scanned by level_maxdeg (its arcs)
+  int64_t xk_bytes[3];            // algorithmic bytes of the other timed kernels (split sampling,
+                                  //   giant-community aggregation scan, block merge of touched rows)
 };
 
 // ---------------------------------------------------------------- checked build

@@ -43,8 +43,12 @@ enum { BIN_WARP = 0, BIN_BLOCK = 1, BIN_HUGE = 2, BIN_TINY = 3, NBINS = 4 };
 constexpr int BIN_TINY_MAX = 8;      // eight lanes, one arc per lane (local moving, refinement)
 constexpr int BIN_WARP_MAX = 128;    // one warp, shared table of <= 256 slots
 constexpr int BIN_BLOCK_MAX = 1024;  // one block, shared table of 2048 slots
-// Local-moving kernels with their own timer and work counters.
-enum { KT_WARP = 0, KT_BLOCK = 1, KT_HUGE_SCAN = 2, KT_KERNELS = 3 };
+// Kernels with their own live timer (event pairs, collect_stats bit 2) and
+// algorithmic-byte counters: the three local-moving kernels, and the
+// largest kernels of the other phases (split sampling, the chunked scan of
+// giant communities in aggregation, the block merge of touched rows).
+enum { KT_WARP = 0, KT_BLOCK = 1, KT_HUGE_SCAN = 2, KT_SPLIT_SAMPLE = 3, KT_AGG_CHUNK = 4, KT_MERGE_MID = 5,
+       KT_KERNELS = 6 };
 
 struct BatchBuffers {
   int64_t cap_edges = 0;  // capacity in undirected edges, per side
@@ -120,9 +124,12 @@ struct leiden_handle {
   int64_t *cflat = nullptr;  // [n+1] flat arc offsets in cverts order
   int64_t *y_off[2] = {nullptr, nullptr};
   int32_t *y_deg[2] = {nullptr, nullptr};
+  // The arcs of the two aggregated levels (y_col, y_w: 12 B per arc of G^t
+  // each) are drawn from the device's stream-ordered memory pool when a call
+  // first aggregates and returned at its end, so a resident graph does not
+  // hold them between calls (most DF updates never aggregate).
   int32_t *y_col[2] = {nullptr, nullptr};
   int64_t *y_w[2] = {nullptr, nullptr};
-  int64_t y_cap = 0;
 
   // global hash scratch for the largest vertices / communities (kept clean)
   void *hscratch = nullptr;
@@ -203,6 +210,15 @@ void ld_note_launch();
 // Phase boundaries (tag: a leiden_phase, or PHASE_END after the last one)
 // and their resolution after a stream sync into stats.phase_ms.
 constexpr int PHASE_END = 6;
+// Aggregation arcs from the stream-ordered pool (false: out of memory) and
+// their return at the end of a call (a no-op when none are held).
+bool acquire_agg_buffers(leiden_handle *h);
+void release_agg_buffers(leiden_handle *h);
+// Bytes of those buffers for a graph of `arcs` arcs: every aggregated level
+// has at most the arcs of G^t, and its rows are laid out by the members'
+// degrees, so arcs + 1 slots per buffer suffice.
+inline int64_t agg_buffer_bytes(int64_t arcs) { return 2 * 12 * (arcs + 1); }
+
 void ph_mark(leiden_handle *h, int tag);
 void ph_resolve(leiden_handle *h);
 // Adds algorithmic bytes to stats.phase_bytes[phase].
@@ -211,6 +227,7 @@ inline void ph_bytes(leiden_handle *h, int phase, int64_t bytes) { h->stats.phas
 void kt_begin(leiden_handle *h, int k);
 void kt_end(leiden_handle *h);
 void kt_resolve(leiden_handle *h);
+void kt_reset(leiden_handle *h);  // at the start of a call
 
 // Layout of the per-graph counter block (device or its host mirror) at
 // `base`; gc_block_bytes(G) bytes in all.
@@ -295,7 +312,9 @@ void next_level_ids(leiden_handle *h, int64_t n, const int32_t *gid, int32_t *gi
 void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out_slot);
 void reset_next_pass(leiden_handle *h, int64_t ncomm, int out_slot);
 void mark_all_unprocessed(leiden_handle *h, int64_t n);
-void mark_unprocessed_from_flags(leiden_handle *h, const uint8_t *flags, int64_t n);
+// Pass-loop start: frontier from dV (counted into affected), Ctop = identity,
+// C' = C, K' = K, Sigma' = Sigma.
+void pass_init(leiden_handle *h);
 void level_maxdeg(leiden_handle *h, const int32_t *deg, int64_t n);  // into dcnt->max_count
 
 // ------------------------------------------------------------ track.cu

@@ -88,12 +88,13 @@ constexpr int SPLIT_SAMPLES = 2;
 constexpr int SPLIT_SAMPLE_SCAN = 64;
 // Eight lanes per vertex read its row prefix eight arcs at a time and the
 // lanes holding the first SPLIT_SAMPLES same-community neighbours link.
-__global__ void k_split_sample(const int32_t *list, const DevCounters *cnt, const int64_t *off, const int32_t *deg,
+__global__ void k_split_sample(const int32_t *list, DevCounters *cnt, const int64_t *off, const int32_t *deg,
                                const int32_t *col, const int32_t *C, int32_t *parent) {
   int64_t m = cnt->split_count;
   int lane = threadIdx.x & 31, grp = lane >> 3, sub = lane & 7;
   uint32_t gmask = 0xffu << (grp * 8);
   int64_t ngroups = ld_gstride() >> 3;
+  int64_t bytes = 0;  // algorithmic bytes (lane 0 of each group of eight)
   for (int64_t t0 = (ld_gtid() >> 5) * 4; t0 < m; t0 += ngroups) {  // warp-uniform trip count
     int64_t t = t0 + grp;
     bool has = t < m;
@@ -119,8 +120,12 @@ __global__ void k_split_sample(const int32_t *list, const DevCounters *cnt, cons
       uint32_t hits = __ballot_sync(LD_FULL, hit) & gmask;
       if (hit && __popc(hits & ((1u << lane) - 1u)) < SPLIT_SAMPLES - got) uf_unite(parent, i, j);
       if (live) got += __popc(hits);
+      if (live && sub == 0) bytes += 8 * (d - a0 < 8 ? d - a0 : 8);  // col and C of the arcs read
     }
+    if (has && sub == 0) bytes += 20;  // list entry, C, offset, degree
   }
+  bytes = ld_warp_sum_i64(bytes);
+  if (lane == 0 && bytes) atomicAdd((unsigned long long *)&cnt->xk_bytes[0], (unsigned long long)bytes);
 }
 
 __global__ void k_split_flatten(const int32_t *list, const DevCounters *cnt, int32_t *parent) {
@@ -324,6 +329,7 @@ struct AggArgs {
   int64_t *gvals;
   int32_t *glist;  // filled slots of each listed community's table
   int32_t *gocc;   // number of filled slots
+  int64_t *xk_bytes;  // algorithmic bytes of the chunked scan
 };
 
 // Flat arcs [f0, f1) of community c, processed by `stride` threads.
@@ -509,6 +515,8 @@ __global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t
         agg_chunk_step<W>(A, T8, row, g0, 32 * nwarps, s1, keys, vals, list, &A.gocc[lo], (int)(T - 1));
     }
     wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+    if (threadIdx.x == 0)  // per flat arc: col, C of the neighbour and the weight
+      atomicAdd((unsigned long long *)A.xk_bytes, (unsigned long long)((8 + sizeof(W)) * (f1 - f0)));
     __syncthreads();  // nlong and longm are rewritten by the next chunk
   }
 }
@@ -581,16 +589,28 @@ __global__ void k_bits_all(int64_t n, uint32_t *bm) {
     bm[w] = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
   }
 }
-__global__ void k_bits_from_flags(int64_t n, const uint8_t *flags, uint32_t *bm, DevCounters *cnt) {
+// Start of the pass loop in one sweep: the affected flags become the
+// frontier bitmap (and are counted), Ctop = identity, C' = C, K' = K,
+// Sigma' = Sigma.
+__global__ void k_pass_init(int64_t n, const uint8_t *dV, uint32_t *bm, int32_t *Ctop, const int32_t *C, int32_t *Cp,
+                            const int64_t *K, int64_t *Kp, const int64_t *Sig, int64_t *Sp, DevCounters *cnt) {
   int lane = threadIdx.x & 31;
   int64_t set = 0;
-  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
+  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {  // warp-uniform trip count
     int64_t v = base + lane;
-    uint32_t m = __ballot_sync(LD_FULL, v < n && flags[v]);
+    bool in = v < n;
+    uint32_t m = __ballot_sync(LD_FULL, in && dV[v]);
     if (lane == 0) { bm[base >> 5] = m; set += __popc(m); }
+    if (in) {
+      Ctop[v] = (int32_t)v;
+      Cp[v] = C[v];
+      Kp[v] = K[v];
+      Sp[v] = Sig[v];
+    }
   }
   if (lane == 0 && set) atomicAdd((unsigned long long *)&cnt->affected, (unsigned long long)set);
 }
+
 __global__ void k_maxdeg(int64_t n, const int32_t *deg, DevCounters *cnt, int block_max) {
   int32_t mx = 0;
   int64_t slots = 0, sum = 0;
@@ -638,7 +658,9 @@ void split_communities(leiden_handle *h, const LevelGraph &g) {
   int32_t *list = h->ibuf1;
   ld_note_launch(), k_split_init<<<grid_for(g.n, TB), TB, 0, s>>>(g.n, h->Cp, h->dS, h->dR, g.deg, h->parent, list,
                                                                   h->dcnt, h->p.split_all);
+  kt_begin(h, KT_SPLIT_SAMPLE);
   ld_note_launch(), k_split_sample<<<h->sm_count * 16, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent);
+  kt_end(h);
   ld_note_launch(), k_split_flatten<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, h->parent);
   cudaMemsetAsync(&h->dcnt->big_count, 0, sizeof(int32_t), s);
   ld_note_launch(), k_split_link_rest<<<h->sm_count * 8, TB, 0, s>>>(list, h->dcnt, g.off, g.deg, g.col, h->Cp, h->parent, h->ibuf2);
@@ -740,8 +762,11 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
     int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
     launch_table_plan(A.list, A.count, nullptr, h->y_off[out], tab_off, ch_off, s);
     ld_note_launch(), k_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
+    A.xk_bytes = &h->dcnt->xk_bytes[1];
+    kt_begin(h, KT_AGG_CHUNK);
     if (g.w64) ld_note_launch(), k_agg_chunk_scan<int64_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
     else ld_note_launch(), k_agg_chunk_scan<int32_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
+    kt_end(h);
     ld_note_launch(), k_agg_list_emit<<<sms * 2, 1024, 0, s>>>(A, tab_off);
   }
 }
@@ -757,9 +782,10 @@ void mark_all_unprocessed(leiden_handle *h, int64_t n) {
   ld_note_launch(), k_bits_all<<<grid_for((n + 31) / 32, TB), TB, 0, h->stream>>>(n, h->unproc);
 }
 
-void mark_unprocessed_from_flags(leiden_handle *h, const uint8_t *flags, int64_t n) {
+void pass_init(leiden_handle *h) {
   cudaMemsetAsync(&h->dcnt->affected, 0, sizeof(int64_t), h->stream);
-  ld_note_launch(), k_bits_from_flags<<<grid_for(n, TB), TB, 0, h->stream>>>(n, flags, h->unproc, h->dcnt);
+  ld_note_launch(), k_pass_init<<<grid_for(h->n, TB), TB, 0, h->stream>>>(h->n, h->dV, h->unproc, h->Ctop, h->C, h->Cp,
+                                                                          h->K, h->Kp, h->Sig, h->Sp, h->dcnt);
 }
 
 void level_maxdeg(leiden_handle *h, const int32_t *deg, int64_t n) {

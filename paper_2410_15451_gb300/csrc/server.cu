@@ -6,7 +6,9 @@
 // threads ("slots") takes work as soon as a slot is free:
 //   * admission: the oldest waiting graph whose footprint
 //     (leiden_footprint_bytes) fits in the remaining device budget is
-//     created and gets its static Leiden;
+//     created and gets its static Leiden; the budget also keeps room for
+//     the aggregation buffers that `slots` concurrent calls draw from the
+//     stream-ordered pool (slots times the largest admitted graph's);
 //   * requests: among admitted graphs that are not busy, the one whose next
 //     request is oldest runs that request (leiden_update on its stream).
 // Requests of one graph run one at a time in submission order, so each
@@ -34,6 +36,7 @@ struct ServerGraph {
   std::vector<int64_t> off;  // host copy until admitted
   std::vector<int32_t> col, w;
   int64_t bytes = 0;
+  int64_t agg_bytes = 0;  // aggregation buffers a call on it draws from the pool
   leiden_handle *h = nullptr;
   cudaStream_t stream = nullptr;
   State state = PENDING;
@@ -60,6 +63,7 @@ struct leiden_server {
   leiden_params p{};
   int device = 0;
   int64_t budget = 0, used = 0;
+  int64_t max_agg = 0;  // largest agg_bytes of the graphs admitted so far
   std::vector<std::thread> workers;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -143,11 +147,17 @@ void worker_loop(leiden_server *S) {
       }
     // admission by footprint, oldest graph first among those that fit
     ServerGraph *adm = nullptr;
+    int64_t nslots = (int64_t)S->workers.size();
     for (ServerGraph *g : S->graphs)
-      if (g->state == ServerGraph::PENDING && S->used + g->bytes <= S->budget) { adm = g; break; }
+      if (g->state == ServerGraph::PENDING &&
+          S->used + g->bytes + nslots * std::max(S->max_agg, g->agg_bytes) <= S->budget) {
+        adm = g;
+        break;
+      }
     if (adm) {
       adm->state = ServerGraph::ADMITTING;
       S->used += adm->bytes;
+      S->max_agg = std::max(S->max_agg, adm->agg_bytes);
       S->running++;
       lk.unlock();
       admit(S, adm);
@@ -219,8 +229,9 @@ leiden_status leiden_server_add_graph(leiden_server *S, int64_t n, const int64_t
   if (weights) g->w.assign(weights, weights + offsets[n]);
   else g->w.assign((size_t)offsets[n], 1);
   g->bytes = leiden_footprint_bytes(&S->p, n, offsets);
+  g->agg_bytes = leiden_transient_bytes(n, offsets);
   std::lock_guard<std::mutex> lk(S->mu);
-  if (g->bytes > S->budget) {
+  if (g->bytes + (int64_t)S->workers.size() * g->agg_bytes > S->budget) {
     delete g;
     S->err = "graph footprint exceeds the server's device budget";
     return LEIDEN_ERR_OOM;

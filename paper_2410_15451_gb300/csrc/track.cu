@@ -18,6 +18,20 @@ __device__ __forceinline__ uint64_t hash64(uint64_t k) { return ld_splitmix64(k)
 // argmax: a candidate (the new label of any member) is checked with two
 // coalesced sweeps, and only communities without a majority go through the
 // pair table.
+// Tracking's per-id arrays in one sweep: best weights -1, best ids INT_MAX,
+// candidates -1, use flags and deviant weights 0.
+__global__ void k_tr_init(int64_t N, long long *bw, int32_t *bc, long long *ow, int32_t *ob, int32_t *cand,
+                          int32_t *used, int64_t *dev) {
+  for (int64_t i = ld_gtid(); i < N; i += ld_gstride()) {
+    bw[i] = -1;
+    bc[i] = INT_MAX;
+    ow[i] = -1;
+    ob[i] = INT_MAX;
+    cand[i] = -1;
+    used[i] = 0;
+    dev[i] = 0;
+  }
+}
 __global__ void k_trc_cand(int64_t N, const int32_t *Cold, const int32_t *Cnew, int32_t *cand) {
   for (int64_t i = ld_gtid(); i < N; i += ld_gstride()) cand[Cold[i]] = Cnew[i];  // any member will do
 }
@@ -248,13 +262,7 @@ void track_communities(leiden_handle *h) {
   int32_t *bc = h->ibuf0, *ob = h->ibuf1, *used = h->ibuf2;
   int32_t *cand = h->mtarget, *flag = h->movers;
   int64_t *dev = h->Sp;
-  launch_fill_i64((int64_t *)bw, -1, N, s);
-  launch_fill_i32(bc, INT_MAX, N, s);
-  launch_fill_i64((int64_t *)ow, -1, N, s);
-  launch_fill_i32(ob, INT_MAX, N, s);
-  launch_fill_i32(cand, -1, N, s);
-  cudaMemsetAsync(used, 0, (size_t)N * sizeof(int32_t), s);
-  cudaMemsetAsync(dev, 0, (size_t)N * sizeof(int64_t), s);
+  ld_note_launch(), k_tr_init<<<gN, TB, 0, s>>>(N, bw, bc, ow, ob, cand, used, dev);
   cudaMemsetAsync(&h->dcnt->tr_occ, 0, sizeof(int32_t), s);
   ld_note_launch(), k_trc_cand<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, cand);
   ld_note_launch(), k_trc_deviants<<<gN, TB, 0, s>>>(N, h->C, h->Ctop, h->K, cand, dev);

@@ -39,7 +39,8 @@ class leiden_stats(ctypes.Structure):
         "ms_total", "ms_batch", "ms_move", "ms_refine", "ms_aggregate", "ms_track")] + [
         (k, ctypes.c_int64 * 3) for k in ("lmk_launches", "lmk_vertices", "lmk_arcs", "lmk_bytes")] + [
         ("lmk_ms", ctypes.c_double * 3), ("rebuilds", ctypes.c_int64), ("phase_ms", ctypes.c_double * 6),
-        ("phase_bytes", ctypes.c_int64 * 6)]
+        ("phase_bytes", ctypes.c_int64 * 6), ("xk_launches", ctypes.c_int64 * 3), ("xk_bytes", ctypes.c_int64 * 3),
+        ("xk_ms", ctypes.c_double * 3)]
 
 PHASES = ("batch", "move", "split", "refine", "aggregate", "track")
 
@@ -111,6 +112,8 @@ def load():
     lib.leiden_set_tuning.restype = ctypes.c_int
     lib.leiden_footprint_bytes.argtypes = [P(leiden_params), i64, vp]
     lib.leiden_footprint_bytes.restype = i64
+    lib.leiden_transient_bytes.argtypes = [i64, vp]
+    lib.leiden_transient_bytes.restype = i64
     d = ctypes.c_double
     for name, args in (("leiden_server_create", [P(leiden_params), i64, i32, P(vp)]),
                        ("leiden_server_add_graph", [vp, i64, vp, vp, vp, P(i32)]),
@@ -467,6 +470,11 @@ class LeidenBatch:
 def leiden_footprint_bytes(n, offsets, params=None) -> int:
     off = np.ascontiguousarray(offsets, np.int64)
     return int(load().leiden_footprint_bytes(ctypes.byref(params) if params is not None else None, int(n), _ptr(off)))
+
+
+def leiden_transient_bytes(n, offsets) -> int:
+    off = np.ascontiguousarray(offsets, np.int64)
+    return int(load().leiden_transient_bytes(int(n), _ptr(off)))
 
 
 class LeidenServer:

@@ -286,6 +286,9 @@ def test_stats_timers_and_launch_counter_leave_results_unchanged():
     assert s["phase_bytes"][L.PHASES.index("move")] >= sum(s["lmk_bytes"])
     assert s["affected"] == a.trace()["affected"]
     assert b.stats()["phase_bytes"] == s["phase_bytes"] and b.stats()["phase_ms"] == [0.0] * 6
+    # the other timed kernels: split sampling runs in every DF update that splits
+    assert s["xk_launches"][0] > 0 and s["xk_ms"][0] > 0 and s["xk_bytes"][0] > 0
+    assert b.stats()["xk_bytes"] == s["xk_bytes"] and b.stats()["xk_launches"] == [0, 0, 0]
     v, e = s["lmk_vertices"], s["lmk_arcs"]
     # every visit of a vertex with arcs goes through one of the three kernels
     assert v[0] + v[1] + v[2] <= s["lm_vertices"] and e[0] + e[1] + e[2] == s["lm_arcs"]

@@ -74,7 +74,10 @@ def test_server_results_equal_results_alone():
         for step, c in enumerate(_alone(g, lst)):
             assert np.array_equal(c, expected[k][step]), (k, step)
     fp = [L.leiden_footprint_bytes(g.n, g.off) for g in gs]
-    budget = sum(fp[:4]) + 1  # graphs 4 and 5 wait for memory
+    tr = [L.leiden_transient_bytes(g.n, g.off) for g in gs]
+    # graphs 4 and 5 wait for memory; room for three slots' aggregation buffers
+    budget = sum(fp[:4]) + 3 * max(tr) + 1
+    assert budget < sum(fp[:5]) + 3 * max(tr)
     srv = L.LeidenServer(budget, slots=3)
     ids = [srv.add_graph(g.n, g.off, g.col, g.w) for g in gs]
     tickets = {k: [None] * len(reqs[k]) for k in range(len(gs))}
@@ -116,7 +119,7 @@ def test_server_results_equal_results_alone():
 
 def test_server_bad_batch_leaves_the_graph_unchanged():
     g = synth.planted_partition(1200, 12, 10, 0.2, 91)
-    srv = L.LeidenServer(10 * L.leiden_footprint_bytes(g.n, g.off), slots=2)
+    srv = L.LeidenServer(10 * (L.leiden_footprint_bytes(g.n, g.off) + L.leiden_transient_bytes(g.n, g.off)), slots=2)
     gid = srv.add_graph(g.n, g.off, g.col, g.w)
     before = srv.membership(gid)
     bad = np.array([[0, 1, 1]], np.int32) if not np.any(g.col[g.off[0]:g.off[1]] == 1) else np.array([[0, 0, 1]],
@@ -137,10 +140,12 @@ def test_server_wait_for_times_out_then_the_ticket_completes():
     up with LEIDEN_ERR_TIMEOUT and leaves the ticket valid; once memory is
     freed the graph is admitted and the same ticket completes with the
     oracle's result.  The failure is made on the host (no GPU fault)."""
-    g1 = synth.planted_partition(1200, 12, 10, 0.2, 93)
-    g2 = synth.planted_partition(1500, 15, 10, 0.2, 94)
-    fp1 = L.leiden_footprint_bytes(g1.n, g1.off)
-    srv = L.LeidenServer(fp1 + 1, slots=2)  # g2 does not fit while g1 is resident
+    g1 = synth.planted_partition(1500, 15, 10, 0.2, 93)
+    g2 = synth.planted_partition(1200, 12, 10, 0.2, 94)
+    fp1, fp2 = L.leiden_footprint_bytes(g1.n, g1.off), L.leiden_footprint_bytes(g2.n, g2.off)
+    tr = max(L.leiden_transient_bytes(g1.n, g1.off), L.leiden_transient_bytes(g2.n, g2.off))
+    assert fp2 <= fp1
+    srv = L.LeidenServer(fp1 + fp2 + 2 * tr - 1, slots=2)  # each fits alone, not both
     id1 = srv.add_graph(g1.n, g1.off, g1.col, g1.w)
     while srv.stats()["graphs_resident"] < 1:
         time.sleep(0.01)
