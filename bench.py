@@ -83,8 +83,8 @@ def parse():
     ap.add_argument("--serve-scales", default="17,23", help="R-MAT scales drawn uniformly from lo,hi")
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--mean-gap-us", type=float, default=200.0)
-    ap.add_argument("--slots", type=int, default=8)
-    ap.add_argument("--serve-budget-gb", type=float, default=250.0)
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--serve-budget-gb", type=float, default=230.0)
     ap.add_argument("--ncu-summary", default=None, metavar="CSV",
                     help="write the machine-read DRAM-traffic summary and the launch list from an ncu CSV")
     ap.add_argument("--ncu-command", default="", help="the ncu command line that made the CSV (recorded)")
@@ -1172,11 +1172,17 @@ def serve_record(args):
         lat = np.zeros(n)
         svc = np.zeros(n)
 
+        failed = []
+
         def waiter():
             for r in range(n):
                 while tickets[r] is None:
                     time.sleep(0.0002)
-                _, lat[r], svc[r] = srv.wait(tickets[r])
+                try:
+                    _, lat[r], svc[r] = srv.wait(tickets[r])
+                except L.LeidenError as e:  # reported in the line, not raised from a thread
+                    failed.append(str(e))
+                    lat[r] = svc[r] = np.nan
 
         th = threading.Thread(target=waiter)
         th.start()
@@ -1190,18 +1196,23 @@ def serve_record(args):
             d, i = batches[first + r]
             tickets[r] = srv.submit(ids[which[first + r]], d, i, L.LEIDEN_DF)
         th.join()
-        wall = float(np.max(submit_at + lat / 1e3)) - start
-        edges = int(sizes[first:first + n].sum())
-        return {"requests": n, "edges": edges, "edges_per_s": edges / wall, "wall_s": wall,
+        ok = ~np.isnan(lat)
+        wall = float(np.max((submit_at + lat / 1e3)[ok])) - start if ok.any() else float("nan")
+        edges = int(sizes[first:first + n][ok].sum())
+        return {"requests": n, "failed": len(failed), "first_error": failed[0] if failed else None,
+                "edges": edges, "edges_per_s": edges / wall, "wall_s": wall,
                 "arrival_span_s": float(submit_at[-1] - start),
-                "offered_edges_per_s": edges / max(float(np.sum(gaps)), 1e-9),
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "service_p50_ms": float(np.percentile(svc, 50)), "service_p99_ms": float(np.percentile(svc, 99))}
+                "offered_edges_per_s": int(sizes[first:first + n].sum()) / max(float(np.sum(gaps)), 1e-9),
+                "p50_ms": float(np.percentile(lat[ok], 50)), "p99_ms": float(np.percentile(lat[ok], 99)),
+                "service_p50_ms": float(np.percentile(svc[ok], 50)),
+                "service_p99_ms": float(np.percentile(svc[ok], 99))}
 
     clocks = ClockSampler(0)
     clocks.start()
     launches0 = L.leiden_kernel_launches()
     p1 = arrivals(0, gaps1)
+    print(f"serve: configured load done: {p1['edges_per_s'] / 1e6:.1f}M edges/s, p99 {p1['p99_ms']:.0f} ms, "
+          f"{p1['failed']} failed", file=sys.stderr, flush=True)
     cap = p1["edges_per_s"]
     gap2 = float(np.mean(sizes[R1:])) / (0.5 * cap)
     p2 = arrivals(R1, unit_gaps2 * gap2)

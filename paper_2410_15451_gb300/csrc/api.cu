@@ -239,7 +239,6 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
   const leiden_params &p = h->p;
   int64_t N = h->n;
   memset(h->trace, 0, sizeof(h->trace));
-  release_agg_buffers(h);  // a call that failed part-way may have left them
   const bool B = h->G > 1;
   const int G = h->G;
   GraphCounters hg = B ? gc_layout(h->gc_host, G) : GraphCounters{};
@@ -561,13 +560,23 @@ leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_de
   h->stats = leiden_stats{};
   h->ph_used = 0;
   kt_reset(h);
+  // the aggregation arcs are taken before anything changes, so that running
+  // out of memory leaves the handle as it was
+  if (!acquire_agg_buffers(h)) { h->err = "aggregation buffers (stream-ordered pool)"; return LEIDEN_ERR_OOM; }
   ph_mark(h, LEIDEN_PHASE_BATCH);
   leiden_status st = batch_apply_and_mark(h, d_del, n_del, d_ins, n_ins, (int)mode);
-  if (st != LEIDEN_OK) return st;
+  if (st != LEIDEN_OK) {
+    release_agg_buffers(h);
+    return st;
+  }
   ph_bytes(h, LEIDEN_PHASE_BATCH, 4 * h->n);  // degrees scanned for the bins
   level_maxdeg(h, h->g_deg, h->n);
   sync_all(h);
-  CK(cudaGetLastError());
+  if (cudaError_t e = cudaGetLastError()) {
+    h->err = std::string("after the batch: ") + cudaGetErrorString(e);
+    h->broken = true;
+    return LEIDEN_ERR_CUDA;
+  }
   h->m2 = h->hcnt->m2;
   if (h->G > 1) {
     GraphCounters hg = gc_layout(h->gc_host, h->G);
@@ -575,11 +584,21 @@ leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_de
   }
   h->g_maxdeg = h->hcnt->max_count;
   h->g_huge_slots = h->hcnt->huge_slots;
-  return run_leiden(h, 1, mode == LEIDEN_DS ? h->dV : nullptr);
+  st = run_leiden(h, 1, mode == LEIDEN_DS ? h->dV : nullptr);
+  if (st != LEIDEN_OK) {
+    h->broken = true;
+    release_agg_buffers(h);
+  }
+  return st;
 }
 
 leiden_status check_handle(leiden_handle *h) {
   if (!h) return LEIDEN_ERR_ARG;
+  if (h->broken) {
+    h->err = "an earlier call failed after it began to change the handle (see its status); destroy it and "
+             "create a new one, or import a saved state into a new one";
+    return LEIDEN_ERR_STATE;
+  }
   cudaError_t e = cudaSetDevice(h->device);
   if (e != cudaSuccess) {
     h->err = std::string("cudaSetDevice: ") + cudaGetErrorString(e);
@@ -910,6 +929,7 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   h->stats = leiden_stats{};
   h->ph_used = 0;
   kt_reset(h);
+  if (!acquire_agg_buffers(h)) { h->err = "aggregation buffers (stream-ordered pool)"; return LEIDEN_ERR_OOM; }
   ph_mark(h, LEIDEN_PHASE_BATCH);
   int64_t N = h->n;
   // row sums (offsets, degree, K: 20 B per vertex; a weight per arc), degree
@@ -934,7 +954,11 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   h->g_maxdeg = h->hcnt->max_count;
   h->g_huge_slots = h->hcnt->huge_slots;
   st = run_leiden(h, 0, nullptr);
-  if (st != LEIDEN_OK) return st;
+  if (st != LEIDEN_OK) {
+    h->broken = true;
+    release_agg_buffers(h);
+    return st;
+  }
   h->has_static = true;
   return finish_call(h, membership_out, false);
 }

@@ -596,66 +596,68 @@ void release(leiden_handle *h, void *p) {
     if (q == p) { cudaFree(q); q = nullptr; }
 }
 
+// Buffers that grow with the batch.  A larger set is allocated in full
+// before the old one is freed: a failed allocation leaves the handle with its
+// old, valid buffers and capacity (and frees what it got).
 cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
   BatchBuffers &b = h->b;
   if (b.cap_edges > 0 && edges <= b.cap_edges) return cudaSuccess;  // the first call always allocates
   // geometric growth: a freed buffer synchronises the whole device, which
   // stalls every other stream of a serving process
   int64_t cap = std::max<int64_t>({edges, 2 * b.cap_edges, (int64_t)1024});
-  void *old[] = {b.dkey, b.dkey_alt, b.ikey, b.ikey_alt, b.iw, b.iw_alt, b.dw, b.flag,
-                 b.pos, b.ins_state, b.ins_pos, b.row_dlo, b.row_dhi, b.row_ilo, b.row_ihi, b.row_len,
-                 b.row_tmp_off, b.rows, b.ds_key, b.ds_key_alt, b.ds_w, b.ds_w_alt, b.ds_ukey, b.ds_uw,
-                 b.row_dst, b.row_newcap, b.row_olddeg, b.row_large, b.row_mid};
-  for (void *p : old) release(h, p);
   int64_t arcs = 2 * cap;
-  cudaError_t e = cudaSuccess;
-  auto chk = [&](cudaError_t x) { if (x != cudaSuccess) e = x; };
-  chk(grow(h, &b.dkey, arcs));
-  chk(grow(h, &b.dkey_alt, arcs));
-  chk(grow(h, &b.ikey, arcs));
-  chk(grow(h, &b.ikey_alt, arcs));
-  chk(grow(h, &b.iw, arcs));
-  chk(grow(h, &b.iw_alt, arcs));
-  chk(grow(h, &b.dw, arcs));
-  chk(grow(h, &b.flag, arcs + 1));
-  chk(grow(h, &b.pos, arcs + 1));
-  chk(grow(h, &b.ins_state, arcs));
-  chk(grow(h, &b.ins_pos, arcs));
   int64_t rows = std::min<int64_t>(2 * arcs, h->n) + 1;
-  chk(grow(h, &b.rows, rows));
-  chk(grow(h, &b.row_dlo, rows));
-  chk(grow(h, &b.row_dhi, rows));
-  chk(grow(h, &b.row_ilo, rows));
-  chk(grow(h, &b.row_ihi, rows));
-  chk(grow(h, &b.row_len, rows + 1));
-  chk(grow(h, &b.row_tmp_off, rows + 1));
-  chk(grow(h, &b.row_dst, rows + 1));
-  chk(grow(h, &b.row_newcap, rows + 1));
-  chk(grow(h, &b.row_olddeg, rows + 1));
-  chk(grow(h, &b.row_large, rows + 1));
-  chk(grow(h, &b.row_mid, rows + 1));
-  chk(grow(h, &b.ds_key, arcs));
-  chk(grow(h, &b.ds_key_alt, arcs));
-  chk(grow(h, &b.ds_w, arcs));
-  chk(grow(h, &b.ds_w_alt, arcs));
-  chk(grow(h, &b.ds_ukey, arcs));
-  chk(grow(h, &b.ds_uw, arcs));
-  b.counts = h->dcnt->bcounts;
-  if (!b.row_bits) {
+  BatchBuffers nb = b;
+  void **slot[] = {(void **)&nb.dkey, (void **)&nb.dkey_alt, (void **)&nb.ikey, (void **)&nb.ikey_alt,
+                   (void **)&nb.iw, (void **)&nb.iw_alt, (void **)&nb.dw, (void **)&nb.flag, (void **)&nb.pos,
+                   (void **)&nb.ins_state, (void **)&nb.ins_pos, (void **)&nb.rows, (void **)&nb.row_dlo,
+                   (void **)&nb.row_dhi, (void **)&nb.row_ilo, (void **)&nb.row_ihi, (void **)&nb.row_len,
+                   (void **)&nb.row_tmp_off, (void **)&nb.row_dst, (void **)&nb.row_newcap, (void **)&nb.row_olddeg,
+                   (void **)&nb.row_large, (void **)&nb.row_mid, (void **)&nb.ds_key, (void **)&nb.ds_key_alt,
+                   (void **)&nb.ds_w, (void **)&nb.ds_w_alt, (void **)&nb.ds_ukey, (void **)&nb.ds_uw};
+  size_t bytes[] = {8 * (size_t)arcs, 8 * (size_t)arcs, 8 * (size_t)arcs, 8 * (size_t)arcs, 8 * (size_t)arcs,
+                    8 * (size_t)arcs, 8 * (size_t)arcs, 4 * (size_t)(arcs + 1), 8 * (size_t)(arcs + 1),
+                    4 * (size_t)arcs, 8 * (size_t)arcs, 4 * (size_t)rows, 4 * (size_t)rows, 4 * (size_t)rows,
+                    4 * (size_t)rows, 4 * (size_t)rows, 8 * (size_t)(rows + 1), 8 * (size_t)(rows + 1),
+                    8 * (size_t)(rows + 1), 4 * (size_t)(rows + 1), 4 * (size_t)(rows + 1), 4 * (size_t)(rows + 1),
+                    4 * (size_t)(rows + 1), 8 * (size_t)arcs, 8 * (size_t)arcs, 8 * (size_t)arcs, 8 * (size_t)arcs,
+                    8 * (size_t)arcs, 8 * (size_t)arcs};
+  constexpr int NB = sizeof(slot) / sizeof(slot[0]);
+  static_assert(NB == sizeof(bytes) / sizeof(bytes[0]), "one size per batch buffer");
+  void *fresh[NB] = {};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < NB && e == cudaSuccess; k++) e = cudaMalloc(&fresh[k], bytes[k]);
+  if (e == cudaSuccess && !b.row_bits) {
     int64_t words = (h->n + 31) / 32;
-    chk(grow(h, &b.row_bits, words));
-    if (b.row_bits) chk(cudaMemsetAsync(b.row_bits, 0, (size_t)std::max<int64_t>(words, 1) * sizeof(uint32_t), h->stream));
+    e = grow(h, &nb.row_bits, words);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(nb.row_bits, 0, (size_t)std::max<int64_t>(words, 1) * sizeof(uint32_t), h->stream);
   }
-  if (e == cudaSuccess) b.cap_edges = cap;
-  return e;
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    for (void *q : fresh)
+      if (q) cudaFree(q);
+    return e;
+  }
+  void *old[NB];
+  for (int k = 0; k < NB; k++) {
+    old[k] = *slot[k];
+    *slot[k] = fresh[k];
+    h->owned.push_back(fresh[k]);
+  }
+  for (void *q : old) release(h, q);
+  nb.counts = h->dcnt->bcounts;
+  nb.cap_edges = cap;
+  b = nb;
+  return cudaSuccess;
 }
 
 cudaError_t ensure_scan_tmp(leiden_handle *h, size_t bytes) {
   if (bytes <= h->scan_tmp_bytes) return cudaSuccess;
-  release(h, h->scan_tmp);
   void *p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
-  if (e != cudaSuccess) return e;
+  if (e != cudaSuccess) { cudaGetLastError(); return e; }  // the old scratch stays
+  release(h, h->scan_tmp);
   h->owned.push_back(p);
   h->scan_tmp = p;
   h->scan_tmp_bytes = bytes;
@@ -665,13 +667,23 @@ cudaError_t ensure_scan_tmp(leiden_handle *h, size_t bytes) {
 cudaError_t ensure_tmp_rows(leiden_handle *h, int64_t arcs) {
   BatchBuffers &b = h->b;
   if (arcs <= b.tmp_cap) return cudaSuccess;
+  int64_t cap = std::max<int64_t>({arcs, 2 * b.tmp_cap, (int64_t)4096});
+  int32_t *col = nullptr, *w = nullptr;
+  cudaError_t e = cudaMalloc((void **)&col, (size_t)cap * sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc((void **)&w, (size_t)cap * sizeof(int32_t));
+  if (e != cudaSuccess) {  // the old buffers stay
+    cudaGetLastError();
+    if (col) cudaFree(col);
+    return e;
+  }
   release(h, b.tmp_col);
   release(h, b.tmp_w);
-  int64_t cap = std::max<int64_t>({arcs, 2 * b.tmp_cap, (int64_t)4096});
-  cudaError_t e = grow(h, &b.tmp_col, cap);
-  if (e == cudaSuccess) e = grow(h, &b.tmp_w, cap);
-  if (e == cudaSuccess) b.tmp_cap = cap;
-  return e;
+  h->owned.push_back(col);
+  h->owned.push_back(w);
+  b.tmp_col = col;
+  b.tmp_w = w;
+  b.tmp_cap = cap;
+  return cudaSuccess;
 }
 
 leiden_status fail(leiden_handle *h, leiden_status st, const std::string &msg) {
@@ -818,9 +830,9 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
       // long rows: chunks over the old row, then chunks over the new row
       int32_t *large = b.row_large;
       const int32_t *nlarge = &cnt->large_count;
-      launch_table_plan(large, nlarge, b.row_olddeg, nullptr, h->lbuf0, h->lbuf1, s);
+      launch_table_plan(large, nlarge, b.row_olddeg, nullptr, INT64_MAX, h->lbuf0, h->lbuf1, s);
       ld_note_launch(), k_merge_chunks_write<<<h->sm_count * 16, 256, 0, s>>>(M, large, nlarge, h->lbuf1);
-      launch_table_plan(large, nlarge, nullptr, b.row_tmp_off, h->lbuf2, h->lbuf3, s);
+      launch_table_plan(large, nlarge, nullptr, b.row_tmp_off, INT64_MAX, h->lbuf2, h->lbuf3, s);
       ld_note_launch(), k_merge_chunks_copy<<<h->sm_count * 16, 256, 0, s>>>(M, large, nlarge, h->lbuf3);
     } else {
       ld_note_launch(), k_merge_rows<<<grid_for(nrows * 32, TB), TB, 0, s>>>(b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo,
@@ -828,7 +840,10 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
                                                            h->g_deg, h->g_col, h->g_w, b.tmp_col, b.tmp_w);
       leiden_status st = rebuild_graph(h, nrows, counts + 3);
       h->stats.rebuilds++;
-      if (st != LEIDEN_OK) return st;
+      if (st != LEIDEN_OK) {
+        h->broken = true;  // the batch was applied in part
+        return st;
+      }
     }
   }
   h->g_arcs = h->g_arcs - nd + nn;

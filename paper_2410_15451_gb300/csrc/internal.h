@@ -104,6 +104,10 @@ struct leiden_handle {
   int64_t *K = nullptr, *Sig = nullptr, *dSig = nullptr;
   uint8_t *dV = nullptr;
   bool has_static = false;
+  // A call that failed after it began to change the handle's state (a
+  // failed allocation or CUDA error mid-call) leaves it broken: every later
+  // call that needs the state returns LEIDEN_ERR_STATE.
+  bool broken = false;
 
   // per-vertex work arrays (length n or n+1)
   int32_t *Cp = nullptr, *CB = nullptr, *Ctop = nullptr, *csize = nullptr, *rep = nullptr;
@@ -264,8 +268,10 @@ void launch_fill_i64(int64_t *p, int64_t v, int64_t n, cudaStream_t s);
 void launch_iota_i32(int32_t *p, int64_t n, cudaStream_t s);
 // Per-item global tables and work chunks for the listed items (see prims.cu).
 constexpr int TABLE_CHUNK = 4096;
+// key_cap: the most distinct keys any item can have (tables take
+// pow2 >= 2*min(size, key_cap) slots).
 void launch_table_plan(const int32_t *list, const int32_t *count, const int32_t *deg32, const int64_t *off64,
-                       int64_t *tab_off, int64_t *ch_off, cudaStream_t s);
+                       int64_t key_cap, int64_t *tab_off, int64_t *ch_off, cudaStream_t s);
 int grid_for(int64_t n, int block, int max_blocks = 152 * 16);
 
 // ------------------------------------------------------------ batch.cu

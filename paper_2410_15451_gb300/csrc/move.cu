@@ -1131,7 +1131,7 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
       A.glist = hs_list(h);
       A.gocc = h->hocc;
       int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
-      launch_table_plan(A.list, A.count, g.deg, nullptr, tab_off, ch_off, s);
+      launch_table_plan(A.list, A.count, g.deg, nullptr, g.n, tab_off, ch_off, s);  // keys: communities of the level
       ld_note_launch(), k_huge_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
       if (KIND == KIND_MOVE) kt_begin(h, KT_HUGE_SCAN);
       int hg = sms * h->tune.hub_blocks_per_sm;

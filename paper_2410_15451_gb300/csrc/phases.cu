@@ -83,19 +83,25 @@ __device__ __forceinline__ void uf_unite(int32_t *parent, int32_t a, int32_t b) 
 }
 
 // Sampling round (Afforest, Sutton et al. 2018): link each listed vertex to
-// its first SPLIT_SAMPLES neighbours in the same community.
+// its first SPLIT_SAMPLES neighbours in the same community.  Which
+// neighbours are sampled never changes the result (the link round that
+// follows makes the components exact); sampling only joins most of a
+// community's vertices to one tree cheaply.
 constexpr int SPLIT_SAMPLES = 2;
 constexpr int SPLIT_SAMPLE_SCAN = 64;
-// Eight lanes per vertex read its row prefix eight arcs at a time and the
-// lanes holding the first SPLIT_SAMPLES same-community neighbours link.
+constexpr int SPLIT_LANES = 4;  // lanes per vertex; each reads two arcs of a window of eight
+// Four lanes per vertex (eight vertices per warp) read its row prefix eight
+// arcs at a time, two per lane with independent loads, and the lanes
+// holding the first SPLIT_SAMPLES same-community neighbours link.
 __global__ void k_split_sample(const int32_t *list, DevCounters *cnt, const int64_t *off, const int32_t *deg,
                                const int32_t *col, const int32_t *C, int32_t *parent) {
   int64_t m = cnt->split_count;
-  int lane = threadIdx.x & 31, grp = lane >> 3, sub = lane & 7;
-  uint32_t gmask = 0xffu << (grp * 8);
-  int64_t ngroups = ld_gstride() >> 3;
-  int64_t bytes = 0;  // algorithmic bytes (lane 0 of each group of eight)
-  for (int64_t t0 = (ld_gtid() >> 5) * 4; t0 < m; t0 += ngroups) {  // warp-uniform trip count
+  int lane = threadIdx.x & 31, grp = lane / SPLIT_LANES, sub = lane % SPLIT_LANES;
+  constexpr int GROUPS = 32 / SPLIT_LANES;
+  uint32_t gmask = ((1u << SPLIT_LANES) - 1u) << (grp * SPLIT_LANES);
+  int64_t ngroups = (ld_gstride() >> 5) * GROUPS;
+  int64_t bytes = 0;  // algorithmic bytes (lane 0 of each group)
+  for (int64_t t0 = (ld_gtid() >> 5) * GROUPS; t0 < m; t0 += ngroups) {  // warp-uniform trip count
     int64_t t = t0 + grp;
     bool has = t < m;
     int32_t i = 0, c = 0;
@@ -108,19 +114,26 @@ __global__ void k_split_sample(const int32_t *list, DevCounters *cnt, const int6
       if (d > SPLIT_SAMPLE_SCAN) d = SPLIT_SAMPLE_SCAN;  // sampling looks at a short prefix only
     }
     int got = 0;
-    for (int64_t a0 = 0; a0 < SPLIT_SAMPLE_SCAN; a0 += 8) {
+    for (int64_t a0 = 0; a0 < SPLIT_SAMPLE_SCAN; a0 += 2 * SPLIT_LANES) {
       bool live = has && got < SPLIT_SAMPLES && a0 < d;
       if (!__any_sync(LD_FULL, live)) break;
-      int32_t j = -1;
-      bool hit = false;
-      if (live && a0 + sub < d) {
-        j = col[b + a0 + sub];
-        hit = j != i && C[j] == c;
+      // arcs a0 + sub and a0 + SPLIT_LANES + sub: loads first, then the C gathers
+      int64_t x0 = a0 + sub, x1 = a0 + SPLIT_LANES + sub;
+      int32_t j0 = live && x0 < d ? col[b + x0] : -1;
+      int32_t j1 = live && x1 < d ? col[b + x1] : -1;
+      bool h0 = j0 >= 0 && j0 != i && C[j0] == c;
+      bool h1 = j1 >= 0 && j1 != i && C[j1] == c;
+      // arc order: the first half of the window (lanes' j0), then the second
+      uint32_t hits0 = __ballot_sync(LD_FULL, h0) & gmask, hits1 = __ballot_sync(LD_FULL, h1) & gmask;
+      uint32_t below = (1u << lane) - 1u;
+      int need = SPLIT_SAMPLES - got;
+      int r0 = __popc(hits0 & below), r1 = __popc(hits0) + __popc(hits1 & below);
+      if (h0 && r0 < need) uf_unite(parent, i, j0);
+      if (h1 && r1 < need) uf_unite(parent, i, j1);
+      if (live) {
+        got += __popc(hits0) + __popc(hits1);
+        if (sub == 0) bytes += 8 * (d - a0 < 2 * SPLIT_LANES ? d - a0 : 2 * SPLIT_LANES);  // col and C of the arcs read
       }
-      uint32_t hits = __ballot_sync(LD_FULL, hit) & gmask;
-      if (hit && __popc(hits & ((1u << lane) - 1u)) < SPLIT_SAMPLES - got) uf_unite(parent, i, j);
-      if (live) got += __popc(hits);
-      if (live && sub == 0) bytes += 8 * (d - a0 < 8 ? d - a0 : 8);  // col and C of the arcs read
     }
     if (has && sub == 0) bytes += 20;  // list entry, C, offset, degree
   }
@@ -287,9 +300,10 @@ __global__ void k_yoff(int64_t ncomm, const int64_t *coff, const int64_t *cflat,
     if (c < ncomm) {
       int64_t d = cflat[coff[c + 1]] - cflat[coff[c]];
       atomicMax(&cnt->max_count, (int32_t)(d < INT_MAX ? d : INT_MAX));
-      if (d > BIN_BLOCK_MAX) {  // table slots of the chunked path
+      if (d > BIN_BLOCK_MAX) {  // table slots of the chunked path (at most ncomm distinct keys)
+        int64_t keys = d < ncomm ? d : ncomm;
         int64_t t = 1;
-        while (t < 2 * d) t <<= 1;
+        while (t < 2 * keys) t <<= 1;
         atomicAdd((unsigned long long *)&cnt->huge_slots, (unsigned long long)t);
       }
     }
@@ -760,7 +774,8 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
     A.glist = hs_list(h);
     A.gocc = h->hocc;
     int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
-    launch_table_plan(A.list, A.count, nullptr, h->y_off[out], tab_off, ch_off, s);
+    // a community's super-row has at most one key per community
+    launch_table_plan(A.list, A.count, nullptr, h->y_off[out], ncomm, tab_off, ch_off, s);
     ld_note_launch(), k_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
     A.xk_bytes = &h->dcnt->xk_bytes[1];
     kt_begin(h, KT_AGG_CHUNK);

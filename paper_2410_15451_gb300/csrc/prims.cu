@@ -324,11 +324,12 @@ cudaError_t radix_sort_u64(uint64_t *keys, uint64_t *keys_alt, int64_t *vals, in
 namespace {
 // One block: table and chunk offsets of the listed items (exclusive prefix
 // sums, totals at index count).  An item's size is deg32[v] or
-// off64[v+1] - off64[v]; its table has pow2 >= 2*size slots and it is cut
-// into chunks of TABLE_CHUNK.
+// off64[v+1] - off64[v]; its table has pow2 >= 2*min(size, key_cap) slots
+// (key_cap bounds the distinct keys an item can have, e.g. the number of
+// communities) and it is cut into chunks of TABLE_CHUNK.
 __global__ void __launch_bounds__(1024) k_table_plan(const int32_t *list, const int32_t *count_p,
-                                                      const int32_t *deg32, const int64_t *off64, int64_t *tab_off,
-                                                      int64_t *ch_off) {
+                                                      const int32_t *deg32, const int64_t *off64, int64_t key_cap,
+                                                      int64_t *tab_off, int64_t *ch_off) {
   __shared__ int64_t ws[32][2];
   __shared__ int64_t carry[2];
   int64_t count = *count_p;
@@ -341,8 +342,9 @@ __global__ void __launch_bounds__(1024) k_table_plan(const int32_t *list, const 
     if (k < count) {
       int32_t v = list[k];
       int64_t d = deg32 ? (int64_t)deg32[v] : off64[v + 1] - off64[v];
+      int64_t keys = d < key_cap ? d : key_cap;
       t = 1;
-      while (t < 2 * d) t <<= 1;
+      while (t < 2 * keys) t <<= 1;
       c = d > 0 ? (d + TABLE_CHUNK - 1) / TABLE_CHUNK : 1;  // every item gets at least one chunk
     }
     int64_t it = t, ic = c;  // inclusive warp scans
@@ -394,8 +396,8 @@ void launch_fill_i64(int64_t *p, int64_t v, int64_t n, cudaStream_t s) {
   if (n > 0) ld_note_launch(), k_fill_i64<<<grid_for(n, 256), 256, 0, s>>>(p, v, n);
 }
 void launch_table_plan(const int32_t *list, const int32_t *count, const int32_t *deg32, const int64_t *off64,
-                       int64_t *tab_off, int64_t *ch_off, cudaStream_t s) {
-  ld_note_launch(), k_table_plan<<<1, 1024, 0, s>>>(list, count, deg32, off64, tab_off, ch_off);
+                       int64_t key_cap, int64_t *tab_off, int64_t *ch_off, cudaStream_t s) {
+  ld_note_launch(), k_table_plan<<<1, 1024, 0, s>>>(list, count, deg32, off64, key_cap, tab_off, ch_off);
 }
 
 void launch_iota_i32(int32_t *p, int64_t n, cudaStream_t s) {
