@@ -56,18 +56,30 @@ int64_t level0_huge_slots(const std::vector<int32_t> &deg) {
   return slots;
 }
 
-bool acquire_agg_buffers(leiden_handle *h) {
-  if (h->y_col[0]) return true;
-  size_t slots = (size_t)h->g_arcs + 1;
-  for (int k = 0; k < 2; k++) {
-    if (cudaMallocAsync((void **)&h->y_col[k], slots * sizeof(int32_t), h->stream) != cudaSuccess ||
-        cudaMallocAsync((void **)&h->y_w[k], slots * sizeof(int64_t), h->stream) != cudaSuccess) {
-      cudaGetLastError();
-      release_agg_buffers(h);
-      return false;
+bool acquire_agg_buffers(leiden_handle *h, int64_t arcs) {
+  if (h->y_col[0] && h->y_slots >= arcs + 1) return true;
+  release_agg_buffers(h);
+  size_t slots = (size_t)arcs + 1;
+  for (int attempt = 0; attempt < 2; attempt++) {
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; k++)
+      ok = cudaMallocAsync((void **)&h->y_col[k], slots * sizeof(int32_t), h->stream) == cudaSuccess &&
+           cudaMallocAsync((void **)&h->y_w[k], slots * sizeof(int64_t), h->stream) == cudaSuccess;
+    if (ok) {
+      h->y_slots = arcs + 1;
+      return true;
     }
+    cudaGetLastError();
+    release_agg_buffers(h);
+    // the pool keeps freed blocks cached; blocks of other sizes (other
+    // graphs' calls) may hold the memory this one needs: return the unused
+    // ones to the device and try once more
+    cudaStreamSynchronize(h->stream);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+    cudaGetLastError();
   }
-  return true;
+  return false;
 }
 
 void release_agg_buffers(leiden_handle *h) {
@@ -77,6 +89,7 @@ void release_agg_buffers(leiden_handle *h) {
     h->y_col[k] = nullptr;
     h->y_w[k] = nullptr;
   }
+  h->y_slots = 0;
 }
 
 void ph_mark(leiden_handle *h, int tag) {
@@ -435,7 +448,9 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
       ncomm = tot;
     }
     lookup_dendrogram(h);
-    if (!acquire_agg_buffers(h)) { h->err = "aggregation buffers (stream-ordered pool)"; return LEIDEN_ERR_OOM; }
+    // every aggregated level has at most the arcs of G^t (held since the
+    // call's start; re-taken only if the batch outgrew the bound)
+    if (!acquire_agg_buffers(h, h->g_arcs)) { h->err = "aggregation buffers (stream-ordered pool)"; return LEIDEN_ERR_OOM; }
     aggregate(h, g, ncomm, slot);
     reset_next_pass(h, ncomm, slot);
     level_maxdeg(h, h->y_deg[slot], ncomm);
@@ -561,8 +576,12 @@ leiden_status do_update(leiden_handle *h, const leiden_edge *d_del, int64_t n_de
   h->ph_used = 0;
   kt_reset(h);
   // the aggregation arcs are taken before anything changes, so that running
-  // out of memory leaves the handle as it was
-  if (!acquire_agg_buffers(h)) { h->err = "aggregation buffers (stream-ordered pool)"; return LEIDEN_ERR_OOM; }
+  // out of memory leaves the handle as it was; the batch adds at most two
+  // arcs per inserted edge
+  if (!acquire_agg_buffers(h, h->g_arcs + 2 * n_ins)) {
+    h->err = "aggregation buffers (stream-ordered pool)";
+    return LEIDEN_ERR_OOM;
+  }
   ph_mark(h, LEIDEN_PHASE_BATCH);
   leiden_status st = batch_apply_and_mark(h, d_del, n_del, d_ins, n_ins, (int)mode);
   if (st != LEIDEN_OK) {
@@ -929,7 +948,7 @@ leiden_status leiden_static(leiden_handle *h, int32_t *membership_out) {
   h->stats = leiden_stats{};
   h->ph_used = 0;
   kt_reset(h);
-  if (!acquire_agg_buffers(h)) { h->err = "aggregation buffers (stream-ordered pool)"; return LEIDEN_ERR_OOM; }
+  if (!acquire_agg_buffers(h, h->g_arcs)) { h->err = "aggregation buffers (stream-ordered pool)"; return LEIDEN_ERR_OOM; }
   ph_mark(h, LEIDEN_PHASE_BATCH);
   int64_t N = h->n;
   // row sums (offsets, degree, K: 20 B per vertex; a weight per arc), degree

@@ -134,6 +134,7 @@ struct leiden_handle {
   // hold them between calls (most DF updates never aggregate).
   int32_t *y_col[2] = {nullptr, nullptr};
   int64_t *y_w[2] = {nullptr, nullptr};
+  int64_t y_slots = 0;  // arc slots of the buffers held (0: none)
 
   // global hash scratch for the largest vertices / communities (kept clean)
   void *hscratch = nullptr;
@@ -216,7 +217,10 @@ void ld_note_launch();
 constexpr int PHASE_END = 6;
 // Aggregation arcs from the stream-ordered pool (false: out of memory) and
 // their return at the end of a call (a no-op when none are held).
-bool acquire_agg_buffers(leiden_handle *h);
+// `arcs` bounds the arcs of G^t during the call (taken before a batch is
+// applied, it must count the arcs the batch can add); buffers already held
+// with enough slots are kept.
+bool acquire_agg_buffers(leiden_handle *h, int64_t arcs);
 void release_agg_buffers(leiden_handle *h);
 // Bytes of those buffers for a graph of `arcs` arcs: every aggregated level
 // has at most the arcs of G^t, and its rows are laid out by the members'

@@ -497,3 +497,46 @@ def test_async_mode_quality_rmat16_against_the_snapshot_oracle(seed):
     g = synth.rmat(16, seed=seed)
     for q_gpu, q_sync in _async_run(g, oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)):
         assert q_gpu >= q_sync - 0.005
+
+
+@pytest.mark.parametrize("mode", MODES, ids=["ND", "DS", "DF"])
+def test_insertion_heavy_batch_that_aggregates_bit_exact(mode):
+    """A batch that adds far more arcs than it removes and marks a community
+    for refinement (its Delta Sigma passes tau_re * Sigma), so the update
+    aggregates a graph with more arcs than before the batch: the aggregated
+    levels must fit, and the result must be the oracle's."""
+    gm, om = mode
+    g = synth.planted_partition(2000, 20, 8, 0.2, 64)
+    gpu = L.Leiden(g.n, g.off, g.col, g.w)
+    ref = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    gpu.static()
+    ref.static()
+    C = ref.state()["C"]
+    members = np.nonzero(C == C[0])[0]
+    src = np.repeat(np.arange(g.n), np.diff(g.off))
+    existing = set(zip(src.tolist(), g.col.tolist()))
+    rng = np.random.default_rng(65)
+    ins, seen = [], set()
+    while len(ins) < 6 * len(members):
+        u, v = (int(x) for x in rng.choice(members, 2, replace=False))
+        if (u, v) in existing or (min(u, v), max(u, v)) in seen:
+            continue
+        seen.add((min(u, v), max(u, v)))
+        ins.append([u, v, 1])
+    # plus new edges all over the graph, so that the arcs grow everywhere
+    while len(ins) < 6 * len(members) + 3000:
+        u, v = (int(x) for x in rng.integers(0, g.n, 2))
+        if u == v or (u, v) in existing or (min(u, v), max(u, v)) in seen:
+            continue
+        seen.add((min(u, v), max(u, v)))
+        ins.append([u, v, 1])
+    ins = np.array(ins, np.int32)
+    dels = np.zeros((0, 3), np.int32)
+    cg = gpu.update(dels, ins, gm)
+    cr = ref.update(dels, ins, om)
+    tr = ref.trace()
+    assert tr["passes"][0]["refined_any"] == 1 and len(tr["passes"]) >= 2  # it aggregated
+    assert_same_trace(gpu, ref)
+    assert np.array_equal(cg, cr)
+    assert_same_state(gpu, ref)
+    assert gpu.modularity() == ref.modularity()
