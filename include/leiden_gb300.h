@@ -130,6 +130,11 @@ typedef struct {
   int64_t xk_launches[3];
   int64_t xk_bytes[3];
   double xk_ms[3];
+  /* Communities above 1024 member arcs aggregated through a global table of
+   * their own: [0] an open-addressing hash table (fewer slots than the
+   * level has communities), [1] a table indexed by the community id itself
+   * (a slot per community: one atomic add per key, no probing). */
+  int64_t agg_tables[2];
 } leiden_stats;
 
 /* Phases of a call, as timed and counted in leiden_stats. */

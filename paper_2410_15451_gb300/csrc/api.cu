@@ -146,6 +146,7 @@ void kt_reset(leiden_handle *h) {
   h->kt_used = 0;
   for (int k = 0; k < KT_KERNELS; k++) { h->kt_ms[k] = 0; h->kt_launches[k] = 0; }
   cudaMemsetAsync(h->dcnt->xk_bytes, 0, sizeof(h->dcnt->xk_bytes), h->stream);
+  cudaMemsetAsync(h->dcnt->agg_tables, 0, sizeof(h->dcnt->agg_tables), h->stream);
 }
 
 void kt_resolve(leiden_handle *h) {
@@ -516,6 +517,8 @@ leiden_status run_leiden(leiden_handle *h, int dynamic, const uint8_t *in_range)
     st.xk_ms[k] = h->kt_ms[KT_SPLIT_SAMPLE + k];
     st.xk_bytes[k] = h->hcnt->xk_bytes[k];
   }
+  st.agg_tables[0] = h->hcnt->agg_tables[0];
+  st.agg_tables[1] = h->hcnt->agg_tables[1];
   for (int k = 0; k < 3; k++) {
     st.lmk_vertices[k] = h->hcnt->lmk_visits[k];
     st.lmk_arcs[k] = h->hcnt->lmk_arcs[k];

@@ -54,6 +54,8 @@ struct DevCounters {
   int64_t deg_sum;                // degree sum of the level scanned by level_maxdeg (its arcs)
   int64_t xk_bytes[3];            // algorithmic bytes of the other timed kernels (split sampling,
                                   //   giant-community aggregation scan, block merge of touched rows)
+  int64_t agg_tables[2];          // aggregation's per-community global tables: [0] hashed, [1] indexed
+                                  //   by the key (the table has a slot per community)
 };
 
 // ---------------------------------------------------------------- checked build
@@ -232,6 +234,27 @@ __device__ __forceinline__ void wt_flush(WarpTable &T, int32_t *gkeys, int64_t *
   for (int q = lane; q < n; q += 32) {
     int32_t s = T.list[q];
     ld_gtable_insert(gkeys, gvals, glist, gocc, gmask, T.keys[s], T.vals[s]);
+    T.keys[s] = LD_EMPTY_KEY;
+    T.vals[s] = 0;
+  }
+  __syncwarp();
+  if (lane == 0) T.count = 0;
+  __syncwarp();
+}
+
+// All 32 lanes: move the pairs into a directly indexed table (vals[key], for
+// keys below the table's size) and empty the warp table.  The first add to a
+// key finds 0 there (every weight is positive) and lists the key, so one
+// atomic per key replaces the hash table's claim and add.
+__device__ __forceinline__ void wt_flush_dense(WarpTable &T, int64_t *gvals, int32_t *glist, int32_t *gocc) {
+  int lane = threadIdx.x & 31;
+  __syncwarp();
+  int n = T.count;
+  for (int q = lane; q < n; q += 32) {
+    int32_t s = T.list[q];
+    int32_t key = T.keys[s];
+    unsigned long long old = atomicAdd((unsigned long long *)&gvals[key], (unsigned long long)T.vals[s]);
+    if (old == 0ull) glist[atomicAdd(gocc, 1)] = key;
     T.keys[s] = LD_EMPTY_KEY;
     T.vals[s] = 0;
   }

@@ -344,6 +344,7 @@ struct AggArgs {
   int32_t *glist;  // filled slots of each listed community's table
   int32_t *gocc;   // number of filled slots
   int64_t *xk_bytes;  // algorithmic bytes of the chunked scan
+  int64_t *tables;    // [0] hashed and [1] directly indexed global tables emitted
 };
 
 // Flat arcs [f0, f1) of community c, processed by `stride` threads.
@@ -441,9 +442,17 @@ __global__ void __launch_bounds__(256) k_agg_block(AggArgs A) {
 // col and weight loads of all of them, then the C loads, then the inserts
 // into the warp table (flushed to the community's global table when full).
 constexpr int AGG_UNROLL = 4;
+// A table of at least ncomm slots is indexed by the key directly (dense);
+// a smaller one is an open-addressing hash table.
+__device__ __forceinline__ void agg_flush(WarpTable &T8, bool dense, int32_t *keys, int64_t *vals, int32_t *list,
+                                          int32_t *occ, int tmask) {
+  if (dense) wt_flush_dense(T8, vals, list, occ);
+  else wt_flush(T8, keys, vals, list, occ, tmask);
+}
+
 template <typename W>
-__device__ __forceinline__ void agg_chunk_step(const AggArgs &A, WarpTable &T8, int64_t row, int64_t g0, int64_t gap,
-                                               int64_t s1, int32_t *keys, int64_t *vals, int32_t *list,
+__device__ __forceinline__ void agg_chunk_step(const AggArgs &A, WarpTable &T8, bool dense, int64_t row, int64_t g0,
+                                               int64_t gap, int64_t s1, int32_t *keys, int64_t *vals, int32_t *list,
                                                int32_t *occ, int tmask) {
   const W *w = (const W *)A.w;
   int lane = threadIdx.x & 31;
@@ -463,7 +472,7 @@ __device__ __forceinline__ void agg_chunk_step(const AggArgs &A, WarpTable &T8, 
   }
 #pragma unroll
   for (int u = 0; u < AGG_UNROLL; u++) {
-    if (T8.count > WT_LIMIT) wt_flush(T8, keys, vals, list, occ, tmask);
+    if (T8.count > WT_LIMIT) agg_flush(T8, dense, keys, vals, list, occ, tmask);
     wt_insert_lanes(T8, valid[u], c[u], wa[u]);
   }
 }
@@ -493,6 +502,7 @@ __global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t
     int64_t f1 = A.cflat[m1];
     if (f0 + TABLE_CHUNK < f1) f1 = f0 + TABLE_CHUNK;
     int64_t T = tab_off[lo + 1] - tab_off[lo];
+    bool dense = T >= A.ncomm;  // every key (a community id) has its own slot
     int32_t *keys = A.gkeys + tab_off[lo], *list = A.glist + tab_off[lo];
     int64_t *vals = A.gvals + tab_off[lo];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -518,7 +528,7 @@ __global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t
       }
       int64_t row = A.off[A.cverts[a]] - fa;
       for (int64_t g0 = s0; g0 < s1; g0 += 32 * AGG_UNROLL)
-        agg_chunk_step<W>(A, T8, row, g0, 32, s1, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+        agg_chunk_step<W>(A, T8, dense, row, g0, 32, s1, keys, vals, list, &A.gocc[lo], (int)(T - 1));
     }
     __syncthreads();
     for (int q = 0; q < nlong; q++) {
@@ -526,9 +536,9 @@ __global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t
       int64_t s0 = fa > f0 ? fa : f0, s1 = fb < f1 ? fb : f1;
       int64_t row = A.off[A.cverts[a]] - fa;
       for (int64_t g0 = s0 + 32 * wid; g0 < s1; g0 += 32 * nwarps * AGG_UNROLL)  // warp-uniform
-        agg_chunk_step<W>(A, T8, row, g0, 32 * nwarps, s1, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+        agg_chunk_step<W>(A, T8, dense, row, g0, 32 * nwarps, s1, keys, vals, list, &A.gocc[lo], (int)(T - 1));
     }
-    wt_flush(T8, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+    agg_flush(T8, dense, keys, vals, list, &A.gocc[lo], (int)(T - 1));
     if (threadIdx.x == 0)  // per flat arc: col, C of the neighbour and the weight
       atomicAdd((unsigned long long *)A.xk_bytes, (unsigned long long)((8 + sizeof(W)) * (f1 - f0)));
     __syncthreads();  // nlong and longm are rewritten by the next chunk
@@ -544,12 +554,17 @@ __global__ void __launch_bounds__(1024) k_agg_list_emit(AggArgs A, const int64_t
     int32_t *keys = A.gkeys + tab_off[k], *list = A.glist + tab_off[k];
     int64_t *vals = A.gvals + tab_off[k];
     int32_t occ = A.gocc[k];
-    if (threadIdx.x == 0) { rc = 0; rs = 0; }
+    bool dense = tab_off[k + 1] - tab_off[k] >= A.ncomm;  // the list holds the keys themselves
+    if (threadIdx.x == 0) {
+      rc = 0;
+      rs = 0;
+      atomicAdd((unsigned long long *)&A.tables[dense ? 1 : 0], 1ull);
+    }
     __syncthreads();
     int64_t base = A.yoff[c];
     for (int32_t t = threadIdx.x; t < occ; t += blockDim.x) {
       int32_t s = list[t];
-      int32_t key = keys[s];
+      int32_t key = dense ? s : keys[s];
       int64_t v = vals[s];
       keys[s] = LD_EMPTY_KEY;
       vals[s] = 0;
@@ -778,6 +793,7 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
     launch_table_plan(A.list, A.count, nullptr, h->y_off[out], ncomm, tab_off, ch_off, s);
     ld_note_launch(), k_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
     A.xk_bytes = &h->dcnt->xk_bytes[1];
+    A.tables = h->dcnt->agg_tables;
     kt_begin(h, KT_AGG_CHUNK);
     if (g.w64) ld_note_launch(), k_agg_chunk_scan<int64_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
     else ld_note_launch(), k_agg_chunk_scan<int32_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);

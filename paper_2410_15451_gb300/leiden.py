@@ -40,7 +40,7 @@ class leiden_stats(ctypes.Structure):
         (k, ctypes.c_int64 * 3) for k in ("lmk_launches", "lmk_vertices", "lmk_arcs", "lmk_bytes")] + [
         ("lmk_ms", ctypes.c_double * 3), ("rebuilds", ctypes.c_int64), ("phase_ms", ctypes.c_double * 6),
         ("phase_bytes", ctypes.c_int64 * 6), ("xk_launches", ctypes.c_int64 * 3), ("xk_bytes", ctypes.c_int64 * 3),
-        ("xk_ms", ctypes.c_double * 3)]
+        ("xk_ms", ctypes.c_double * 3), ("agg_tables", ctypes.c_int64 * 2)]
 
 PHASES = ("batch", "move", "split", "refine", "aggregate", "track")
 

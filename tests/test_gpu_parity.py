@@ -422,6 +422,51 @@ def test_long_rows_merge_bit_exact(slack, mode):
     assert np.diff(cur.off)[3] > 4096
 
 
+def cliques_graph(triangles, seed=12):
+    """Four 60-cliques, each with three arcs to other vertices, and
+    `triangles` disjoint triangles.  A clique's refined communities hold more
+    than 1024 member arcs, so aggregation sums them in global tables of their
+    own: with 20000 triangles the level has more communities than twice those
+    arcs and the tables are hashed; with 30 a table has a slot per community
+    and is indexed by the community id."""
+    rng = np.random.default_rng(seed)
+    edges = []
+    for t in range(triangles):
+        a = 3 * t
+        edges += [(a, a + 1), (a, a + 2), (a + 1, a + 2)]
+    base = 3 * triangles
+    for q in range(4):
+        mem = list(range(base + 60 * q, base + 60 * q + 60))
+        edges += [(a, b) for i, a in enumerate(mem) for b in mem[i + 1:]]
+        for v in rng.choice(base + 240, 3, replace=False):
+            if not (mem[0] <= v <= mem[-1]):
+                edges.append((min(mem[0], int(v)), max(mem[0], int(v))))
+    edges = sorted(set(edges))
+    off, col, w = csr_from_edges(base + 240, edges)
+    return synth.Graph(base + 240, off, col, w.astype(np.int32))
+
+
+@pytest.mark.parametrize("triangles,table", [(20000, 0), (30, 1)], ids=["hashed", "indexed"])
+def test_giant_community_aggregation_tables_bit_exact(triangles, table):
+    """Both kinds of global table of the chunked aggregation (hashed, and
+    indexed by the community id) give the oracle's result bit for bit: the
+    static run that builds them, then DF and ND updates."""
+    g = cliques_graph(triangles)
+    gpu = L.Leiden(g.n, g.off, g.col, g.w)
+    ref = oracle.Oracle(g.n, g.off, g.col, g.w, schedule=oracle.SYNC)
+    assert np.array_equal(gpu.static(), ref.static())
+    assert gpu.stats()["agg_tables"][table] > 0
+    assert_same_trace(gpu, ref)
+    assert_same_state(gpu, ref)
+    cur = g
+    for k, (gm, om) in enumerate((MODES[2], MODES[0])):
+        dels, ins = synth.random_batch(cur, 150, seed=1300 + k)
+        assert np.array_equal(gpu.update(dels, ins, gm), ref.update(dels, ins, om)), k
+        cur = synth.apply_batch_numpy(cur, dels, ins)
+        assert_same_trace(gpu, ref)
+        assert_same_state(gpu, ref)
+
+
 @pytest.mark.parametrize("case", ["gain_order", "state_before_batch", "tie"])
 def test_ds_best_community_pin_graphs_bit_exact(case):
     """The hand-derived Delta-screening cases of the oracle pins (the
