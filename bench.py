@@ -190,14 +190,16 @@ def make_batches(g, n_batches, size, seed):
 
 
 ND_DS_STEPS = 3  # ND and DS updates timed (after one untimed each) on the same stream
+ISO_STEPS = 8  # DF updates timed with the side streams off (each kernel alone on the GPU)
 
 
 def stream_batches(args):
     """Batches drawn for the main line's stream: warm-up, the timed DF steps,
-    the e2e steps, then one untimed plus ND_DS_STEPS timed steps each of ND
-    and DS.  All are drawn in one call so that they stay valid in sequence;
-    the reference arm draws the same count and gets the same batches."""
-    return args.warmup + 2 * args.steps + 2 * (ND_DS_STEPS + 1)
+    the e2e steps, one untimed plus ND_DS_STEPS timed steps each of ND and
+    DS, then ISO_STEPS DF steps on one stream.  All are drawn in one call so
+    that they stay valid in sequence; the reference arm draws the same count
+    and gets the same batches."""
+    return args.warmup + 2 * args.steps + 2 * (ND_DS_STEPS + 1) + ISO_STEPS
 
 
 def main_seed(rank=0):
@@ -455,10 +457,19 @@ def run_ours(args, rank, world, local_rank):
                        "speedup_vs_static": t_static / float(np.mean(ms)), "steps": len(ms)}
     modes["DF"] = {"ms_mean": mean_ms, "edges_per_s": size / (mean_ms / 1e3),
                    "speedup_vs_static": t_static / mean_ms, "steps": K}
+    # DF updates with every kernel on the handle's one stream: each timed
+    # kernel then has the GPU to itself, so its event time is its own
+    L.leiden_set_tuning(gpu.h, overlap=0)
+    iso_ms, iso_stats = [], []
+    for j in range(ISO_STEPS):
+        iso_ms.append(timed_update(stream, dev_step(base + j), flush))
+        iso_stats.append(gpu.stats())
+    L.leiden_set_tuning(gpu.h)
     result = dict(value=value, mean_ms=mean_ms, p50=float(np.percentile(times_ms, 50)),
                   p99=float(np.percentile(times_ms, 99)), e2e=e2e_value, q_df=q_df, q_static=q_static,
                   t_static=t_static, clk=clk, lm_stats=lm_stats, E=E, n=g.n, size=size, gen_s=gen_s,
-                  gpu_launches=gpu_launches, checks=chk, modes=modes,
+                  gpu_launches=gpu_launches, checks=chk, modes=modes, iso_stats=iso_stats,
+                  iso_ms=float(np.mean(iso_ms)), iso_p50=float(np.percentile(iso_ms, 50)),
                   steps=[step_record(t, st) for t, st in zip(times_ms, lm_stats)],
                   e2e_p99=float(np.percentile(np.array(e2e_times) * 1e3, 99)))
     # batch-size sweep (each size continues the evolving graph)
@@ -1285,6 +1296,7 @@ def main():
     if rank == 0:
         chk = r["checks"]
         dom, lmk = roofline_kernels(r["lm_stats"])
+        _, lmk_iso = roofline_kernels(r["iso_stats"])
         line = {
             "metric": METRIC, "value": r["value"], "unit": "edges/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["mean_ms"], "higher_is_better": True, "scaling": "weak",
@@ -1302,6 +1314,10 @@ def main():
                     "d2h_bytes_per_step": r["n"] * 4, "p99_ms": r["e2e_p99"]},
             "roofline": dom,
             "roofline_kernels": lmk,
+            # the same kernels on the following DF steps with the side streams
+            # off (one stream, each kernel alone on the GPU)
+            "roofline_kernels_isolated": lmk_iso,
+            "one_stream": {"steps": ISO_STEPS, "ms_mean": r["iso_ms"], "p50_ms": r["iso_p50"]},
             "roofline_step": roofline_step(r["lm_stats"], r["mean_ms"]),
             "gpu_launches": r["gpu_launches"],
             "cpu_baseline": cb,

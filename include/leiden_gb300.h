@@ -151,7 +151,10 @@ typedef struct leiden_handle leiden_handle;
 
 /* Launch shapes of the local-moving and refinement kernels.  They change how
  * the work is spread over the GPU, never a result (the deterministic schedule
- * gives the same bits for every valid setting). */
+ * gives the same bits for every valid setting).  `overlap` lets kernels that
+ * write disjoint data run at once on the handle's two side streams: the
+ * block bin and the hub path beside the warp bin (deterministic schedule
+ * only), and the merges of short, mid and long rows of a batch. */
 typedef struct {
   int32_t tiny_max;           /* degree <= this: eight lanes per vertex; 0 or 1..8, 8       */
   int32_t warp_max;           /* degree <= this: a warp per vertex; tiny_max..128, 128      */
@@ -160,6 +163,7 @@ typedef struct {
   int32_t warp_blocks_per_sm; /* grid of the warp-range kernel, 1..8, 4                     */
   int32_t block_blocks_per_sm;/* grid of the block-bin kernel, 1..8, 7                      */
   int32_t hub_blocks_per_sm;  /* grid of the hub arc scan, 1..32, 16                        */
+  int32_t overlap;            /* side streams: 0 or 1, 1                                    */
 } leiden_tuning;
 
 /* Fill *p with the defaults listed above. */

@@ -123,7 +123,9 @@ void ph_resolve(leiden_handle *h) {
   for (int k = 0; k < 6; k++) st.ms_total += st.phase_ms[k];
 }
 
-void kt_begin(leiden_handle *h, int k) {
+// An event pair around one launch of a timed kernel, on the stream it is
+// launched on (the handle's stream unless given).
+void kt_begin(leiden_handle *h, int k, cudaStream_t s) {
   if (!(h->p.collect_stats & 2)) return;
   size_t need = 2 * (size_t)(h->kt_used + 1);
   while (h->kt_ev.size() < need) {
@@ -133,12 +135,12 @@ void kt_begin(leiden_handle *h, int k) {
   }
   if (h->kt_tag.size() < (size_t)h->kt_used + 1) h->kt_tag.resize(h->kt_used + 1);
   h->kt_tag[h->kt_used] = k;
-  cudaEventRecord(h->kt_ev[2 * h->kt_used], h->stream);
+  cudaEventRecord(h->kt_ev[2 * h->kt_used], s ? s : h->stream);
 }
 
-void kt_end(leiden_handle *h) {
+void kt_end(leiden_handle *h, cudaStream_t s) {
   if (!(h->p.collect_stats & 2) || h->kt_ev.size() < 2 * (size_t)(h->kt_used + 1)) return;
-  cudaEventRecord(h->kt_ev[2 * h->kt_used + 1], h->stream);
+  cudaEventRecord(h->kt_ev[2 * h->kt_used + 1], s ? s : h->stream);
   h->kt_used++;
 }
 
@@ -1127,7 +1129,7 @@ leiden_status leiden_import_state(leiden_handle *h, const int32_t *C, const int6
 }
 
 void leiden_default_tuning(leiden_tuning *t) {
-  if (t) *t = leiden_tuning{8, BIN_WARP_MAX, BIN_BLOCK_MAX, 4, 7, 16};
+  if (t) *t = leiden_tuning{8, BIN_WARP_MAX, BIN_BLOCK_MAX, 4, 7, 16, 1};
 }
 
 leiden_status leiden_set_tuning(leiden_handle *h, const leiden_tuning *t) {
@@ -1135,7 +1137,7 @@ leiden_status leiden_set_tuning(leiden_handle *h, const leiden_tuning *t) {
   if (t->tiny_max < 0 || t->tiny_max > 8 || t->warp_max < t->tiny_max || t->warp_max > BIN_WARP_MAX ||
       t->block_max < t->warp_max || t->block_max > BIN_BLOCK_MAX || t->warp_blocks_per_sm < 1 ||
       t->warp_blocks_per_sm > 8 || t->block_blocks_per_sm < 1 || t->block_blocks_per_sm > 8 ||
-      t->hub_blocks_per_sm < 1 || t->hub_blocks_per_sm > 32) {
+      t->hub_blocks_per_sm < 1 || t->hub_blocks_per_sm > 32 || t->overlap < 0 || t->overlap > 1) {
     h->err = "tuning outside its ranges";
     return LEIDEN_ERR_ARG;
   }
@@ -1239,6 +1241,11 @@ void leiden_destroy(leiden_handle *h) {
     if (ev) cudaEventDestroy(ev);
   for (auto &ev : h->kt_ev)
     if (ev) cudaEventDestroy(ev);
+  for (int k = 0; k < 2; k++) {
+    if (h->side[k]) cudaStreamDestroy(h->side[k]);
+    if (h->join_ev[k]) cudaEventDestroy(h->join_ev[k]);
+  }
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   delete h;
 }
 

@@ -821,19 +821,37 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
       MergeArgs M{b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo, b.row_dhi, b.row_ilo, b.row_ihi, b.row_len,
                   b.row_tmp_off, h->g_off, h->g_deg, h->g_col, h->g_w, b.tmp_col, b.tmp_w,
                   b.row_dst, b.row_newcap, h->g_off, h->g_rcap};
+      // the three row classes write disjoint rows and merge-buffer ranges:
+      // short rows on the handle's stream, mid rows and long rows on its
+      // side streams, joined before the marking below
+      bool fork = h->tune.overlap && side_streams(h);
+      cudaStream_t smid = s, slong = s;
+      if (fork) {
+        cudaEventRecord(h->fork_ev, s);
+        smid = h->side[0];
+        slong = h->side[1];
+        cudaStreamWaitEvent(smid, h->fork_ev, 0);
+        cudaStreamWaitEvent(slong, h->fork_ev, 0);
+      }
       ld_note_launch(), k_merge_small<<<grid_for((nrows + MERGE_WARPS - 1) / MERGE_WARPS, 1, h->sm_count * 16), MERGE_WARPS * 32, 0,
                       s>>>(M);
-      kt_begin(h, KT_MERGE_MID);
-      ld_note_launch(), k_merge_mid<<<h->sm_count * 7, 256, 0, s>>>(M, b.row_mid, &cnt->mid_count,  // 32 KB: 7 per SM
-                                                                   &cnt->xk_bytes[2]);
-      kt_end(h);
+      kt_begin(h, KT_MERGE_MID, smid);
+      ld_note_launch(), k_merge_mid<<<h->sm_count * 7, 256, 0, smid>>>(M, b.row_mid, &cnt->mid_count,  // 32 KB: 7 per SM
+                                                                      &cnt->xk_bytes[2]);
+      kt_end(h, smid);
       // long rows: chunks over the old row, then chunks over the new row
       int32_t *large = b.row_large;
       const int32_t *nlarge = &cnt->large_count;
-      launch_table_plan(large, nlarge, b.row_olddeg, nullptr, INT64_MAX, h->lbuf0, h->lbuf1, s);
-      ld_note_launch(), k_merge_chunks_write<<<h->sm_count * 16, 256, 0, s>>>(M, large, nlarge, h->lbuf1);
-      launch_table_plan(large, nlarge, nullptr, b.row_tmp_off, INT64_MAX, h->lbuf2, h->lbuf3, s);
-      ld_note_launch(), k_merge_chunks_copy<<<h->sm_count * 16, 256, 0, s>>>(M, large, nlarge, h->lbuf3);
+      launch_table_plan(large, nlarge, b.row_olddeg, nullptr, INT64_MAX, h->lbuf0, h->lbuf1, slong);
+      ld_note_launch(), k_merge_chunks_write<<<h->sm_count * 16, 256, 0, slong>>>(M, large, nlarge, h->lbuf1);
+      launch_table_plan(large, nlarge, nullptr, b.row_tmp_off, INT64_MAX, h->lbuf2, h->lbuf3, slong);
+      ld_note_launch(), k_merge_chunks_copy<<<h->sm_count * 16, 256, 0, slong>>>(M, large, nlarge, h->lbuf3);
+      if (fork) {
+        for (int k = 0; k < 2; k++) {
+          cudaEventRecord(h->join_ev[k], h->side[k]);
+          cudaStreamWaitEvent(s, h->join_ev[k], 0);
+        }
+      }
     } else {
       ld_note_launch(), k_merge_rows<<<grid_for(nrows * 32, TB), TB, 0, s>>>(b.rows, counts + 3, vb, DK, NK, NW, b.row_dlo,
                                                            b.row_dhi, b.row_ilo, b.row_ihi, b.row_tmp_off, h->g_off,

@@ -163,16 +163,101 @@ __device__ __forceinline__ bool ld_group_leader(uint32_t peers) {
 // reader visits only filled slots and can empty them again afterwards.
 __device__ __forceinline__ void ld_gtable_insert(int32_t *keys, int64_t *vals, int32_t *list, int32_t *occ, int tmask,
                                                  int32_t c, int64_t w) {
+  // A slot's key only goes from empty to a key while a table is in use, so
+  // a plain read from L2 decides every probe but the claim of an empty slot:
+  // a key already in the table costs a load and an add whose result is not
+  // waited for, instead of a compare-and-swap on a slot every warp touches.
   uint32_t s = ld_hash32((uint32_t)c) & (uint32_t)tmask;
   for (uint32_t probe = 0; ld_ok(probe <= (uint32_t)tmask, LD_CHK_PROBE); probe++) {
-    int32_t k = atomicCAS(&keys[s], LD_EMPTY_KEY, c);
-    if (k == LD_EMPTY_KEY) list[atomicAdd(occ, 1)] = (int32_t)s;
-    if (k == LD_EMPTY_KEY || k == c) {
+    int32_t k = __ldcg(&keys[s]);
+    if (k == LD_EMPTY_KEY) {
+      k = atomicCAS(&keys[s], LD_EMPTY_KEY, c);
+      if (k == LD_EMPTY_KEY) {
+        list[atomicAdd(occ, 1)] = (int32_t)s;
+        k = c;
+      }
+    }
+    if (k == c) {
       atomicAdd((unsigned long long *)&vals[s], (unsigned long long)w);
       return;
     }
     s = (s + 1) & (uint32_t)tmask;
   }
+}
+
+// The same for a table with a slot per key (slot = key): the key array
+// only marks the slots already listed.
+__device__ __forceinline__ void ld_gtable_add_direct(int32_t *keys, int64_t *vals, int32_t *list, int32_t *occ,
+                                                     int32_t c, int64_t w) {
+  if (__ldcg(&keys[c]) == LD_EMPTY_KEY && atomicCAS(&keys[c], LD_EMPTY_KEY, c) == LD_EMPTY_KEY)
+    list[atomicAdd(occ, 1)] = c;
+  atomicAdd((unsigned long long *)&vals[c], (unsigned long long)w);
+}
+
+// All 32 lanes, each with up to GT_KEYS keys (has[u]): add them to a global
+// table (`direct`: slot = key; otherwise open addressing as above).  The
+// first probes of all of a lane's keys are read at once, then the empty
+// slots among them claimed, then the weights added, so a flush waits for
+// about two round trips instead of two per key; a collision probes on
+// alone.  The slots claimed by the warp are listed with one atomic on the
+// fill count, which every warp flushing into the same table would
+// otherwise hit once per new key.
+constexpr int GT_KEYS = 1;
+__device__ __forceinline__ void ld_gtable_add_warp(const bool *has, bool direct, int32_t *keys, int64_t *vals,
+                                                   int32_t *list, int32_t *occ, int tmask, const int32_t *c,
+                                                   const int64_t *w) {
+  int lane = threadIdx.x & 31;
+  uint32_t s[GT_KEYS];
+  int32_t k[GT_KEYS], claimed[GT_KEYS];
+#pragma unroll
+  for (int u = 0; u < GT_KEYS; u++) {
+    s[u] = direct ? (uint32_t)c[u] : ld_hash32((uint32_t)c[u]) & (uint32_t)tmask;
+    k[u] = has[u] ? __ldcg(&keys[s[u]]) : c[u];
+    claimed[u] = -1;
+  }
+#pragma unroll
+  for (int u = 0; u < GT_KEYS; u++) {
+    if (has[u] && k[u] == LD_EMPTY_KEY) {
+      k[u] = atomicCAS(&keys[s[u]], LD_EMPTY_KEY, c[u]);
+      if (k[u] == LD_EMPTY_KEY) {
+        claimed[u] = (int32_t)s[u];
+        k[u] = c[u];
+      }
+    }
+  }
+  int mine = 0;
+#pragma unroll
+  for (int u = 0; u < GT_KEYS; u++) {
+    if (!has[u]) continue;
+    // a collision (hash tables only: a direct slot holds its own key or none)
+    for (uint32_t probe = 1; k[u] != c[u] && ld_ok(probe <= (uint32_t)tmask, LD_CHK_PROBE); probe++) {
+      s[u] = (s[u] + 1) & (uint32_t)tmask;
+      k[u] = __ldcg(&keys[s[u]]);
+      if (k[u] == LD_EMPTY_KEY) {
+        k[u] = atomicCAS(&keys[s[u]], LD_EMPTY_KEY, c[u]);
+        if (k[u] == LD_EMPTY_KEY) {
+          claimed[u] = (int32_t)s[u];
+          k[u] = c[u];
+        }
+      }
+    }
+    if (k[u] == c[u]) atomicAdd((unsigned long long *)&vals[s[u]], (unsigned long long)w[u]);
+    mine += claimed[u] >= 0;
+  }
+  int incl = mine;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(LD_FULL, incl, o);
+    if (lane >= o) incl += y;
+  }
+  int total = __shfl_sync(LD_FULL, incl, 31);
+  if (total == 0) return;  // warp-uniform
+  int32_t base = 0;
+  if (lane == 31) base = atomicAdd(occ, total);
+  base = __shfl_sync(LD_FULL, base, 31) + incl - mine;
+#pragma unroll
+  for (int u = 0; u < GT_KEYS; u++)
+    if (claimed[u] >= 0) list[base++] = claimed[u];
 }
 
 // Shared staging table of one block (local moving and refinement of the
@@ -226,41 +311,47 @@ __device__ __forceinline__ void wt_insert_lanes(WarpTable &T, bool valid, int32_
 }
 
 // All 32 lanes: move the pairs into a global table and empty the warp table.
-__device__ __forceinline__ void wt_flush(WarpTable &T, int32_t *gkeys, int64_t *gvals, int32_t *glist, int32_t *gocc,
-                                         int gmask) {
+__device__ __forceinline__ void wt_flush_to(WarpTable &T, bool direct, int32_t *gkeys, int64_t *gvals,
+                                            int32_t *glist, int32_t *gocc, int gmask) {
   int lane = threadIdx.x & 31;
   __syncwarp();
   int n = T.count;
-  for (int q = lane; q < n; q += 32) {
-    int32_t s = T.list[q];
-    ld_gtable_insert(gkeys, gvals, glist, gocc, gmask, T.keys[s], T.vals[s]);
-    T.keys[s] = LD_EMPTY_KEY;
-    T.vals[s] = 0;
+  for (int q0 = 0; q0 < n; q0 += 32 * GT_KEYS) {  // warp-uniform
+    bool has[GT_KEYS];
+    int32_t sl[GT_KEYS], key[GT_KEYS];
+    int64_t v[GT_KEYS];
+#pragma unroll
+    for (int u = 0; u < GT_KEYS; u++) {
+      int q = q0 + 32 * u + lane;
+      has[u] = q < n;
+      sl[u] = has[u] ? T.list[q] : 0;
+      key[u] = has[u] ? T.keys[sl[u]] : 0;
+      v[u] = has[u] ? T.vals[sl[u]] : 0;
+    }
+    ld_gtable_add_warp(has, direct, gkeys, gvals, glist, gocc, gmask, key, v);
+#pragma unroll
+    for (int u = 0; u < GT_KEYS; u++) {
+      if (has[u]) {
+        T.keys[sl[u]] = LD_EMPTY_KEY;
+        T.vals[sl[u]] = 0;
+      }
+    }
   }
   __syncwarp();
   if (lane == 0) T.count = 0;
   __syncwarp();
 }
 
-// All 32 lanes: move the pairs into a directly indexed table (vals[key], for
-// keys below the table's size) and empty the warp table.  The first add to a
-// key finds 0 there (every weight is positive) and lists the key, so one
-// atomic per key replaces the hash table's claim and add.
-__device__ __forceinline__ void wt_flush_dense(WarpTable &T, int64_t *gvals, int32_t *glist, int32_t *gocc) {
-  int lane = threadIdx.x & 31;
-  __syncwarp();
-  int n = T.count;
-  for (int q = lane; q < n; q += 32) {
-    int32_t s = T.list[q];
-    int32_t key = T.keys[s];
-    unsigned long long old = atomicAdd((unsigned long long *)&gvals[key], (unsigned long long)T.vals[s]);
-    if (old == 0ull) glist[atomicAdd(gocc, 1)] = key;
-    T.keys[s] = LD_EMPTY_KEY;
-    T.vals[s] = 0;
-  }
-  __syncwarp();
-  if (lane == 0) T.count = 0;
-  __syncwarp();
+__device__ __forceinline__ void wt_flush(WarpTable &T, int32_t *gkeys, int64_t *gvals, int32_t *glist, int32_t *gocc,
+                                         int gmask) {
+  wt_flush_to(T, false, gkeys, gvals, glist, gocc, gmask);
+}
+
+// All 32 lanes: move the pairs into a directly indexed table (slot = key,
+// for keys below the table's size) and empty the warp table.
+__device__ __forceinline__ void wt_flush_dense(WarpTable &T, int32_t *gkeys, int64_t *gvals, int32_t *glist,
+                                               int32_t *gocc) {
+  wt_flush_to(T, true, gkeys, gvals, glist, gocc, 0);
 }
 
 // Per-graph sums of a batched handle: every lane of the warp calls these;

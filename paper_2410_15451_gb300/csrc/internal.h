@@ -81,8 +81,13 @@ struct BatchBuffers {
 
 struct leiden_handle {
   leiden_params p{};
-  leiden_tuning tune{8, BIN_WARP_MAX, BIN_BLOCK_MAX, 4, 7, 16};
+  leiden_tuning tune{8, BIN_WARP_MAX, BIN_BLOCK_MAX, 4, 7, 16, 1};
   cudaStream_t stream = nullptr;
+  // side streams of the local-moving and refinement bins (created on first
+  // use): the block bin and the hub path run beside the warp bin
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t fork_ev = nullptr, join_ev[2] = {nullptr, nullptr};
+  bool side_failed = false;
   int device = 0;
   int sm_count = 152;
   int64_t n = 0;
@@ -232,8 +237,9 @@ void ph_resolve(leiden_handle *h);
 // Adds algorithmic bytes to stats.phase_bytes[phase].
 inline void ph_bytes(leiden_handle *h, int phase, int64_t bytes) { h->stats.phase_bytes[phase] += bytes; }
 
-void kt_begin(leiden_handle *h, int k);
-void kt_end(leiden_handle *h);
+bool side_streams(leiden_handle *h);
+void kt_begin(leiden_handle *h, int k, cudaStream_t s = nullptr);
+void kt_end(leiden_handle *h, cudaStream_t s = nullptr);
 void kt_resolve(leiden_handle *h);
 void kt_reset(leiden_handle *h);  // at the start of a call
 

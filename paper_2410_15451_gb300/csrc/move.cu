@@ -746,11 +746,26 @@ __device__ __forceinline__ void wt_flush(WarpTable32 &T, int32_t *gkeys, int64_t
   int lane = threadIdx.x & 31;
   __syncwarp();
   int n = T.count;
-  for (int q = lane; q < n; q += 32) {
-    int32_t s = T.list[q];
-    ld_gtable_insert(gkeys, gvals, glist, gocc, gmask, T.keys[s], (int64_t)T.vals[s]);
-    T.keys[s] = LD_EMPTY_KEY;
-    T.vals[s] = 0;
+  for (int q0 = 0; q0 < n; q0 += 32 * GT_KEYS) {  // warp-uniform
+    bool has[GT_KEYS];
+    int32_t sl[GT_KEYS], key[GT_KEYS];
+    int64_t v[GT_KEYS];
+#pragma unroll
+    for (int u = 0; u < GT_KEYS; u++) {
+      int q = q0 + 32 * u + lane;
+      has[u] = q < n;
+      sl[u] = has[u] ? T.list[q] : 0;
+      key[u] = has[u] ? T.keys[sl[u]] : 0;
+      v[u] = has[u] ? (int64_t)T.vals[sl[u]] : 0;
+    }
+    ld_gtable_add_warp(has, false, gkeys, gvals, glist, gocc, gmask, key, v);
+#pragma unroll
+    for (int u = 0; u < GT_KEYS; u++) {
+      if (has[u]) {
+        T.keys[sl[u]] = LD_EMPTY_KEY;
+        T.vals[sl[u]] = 0;
+      }
+    }
   }
   __syncwarp();
   if (lane == 0) T.count = 0;
@@ -869,43 +884,56 @@ __global__ void __launch_bounds__(HUGE_THREADS) k_huge_decide(Args A, const int6
 __global__ void k_collect(int64_t n, uint32_t *unproc, int cls, int classes_mask, const uint8_t *in_range,
                           const int32_t *deg, int32_t *bins, DevCounters *cnt, const int32_t *gid,
                           const uint8_t *lm_on, const int64_t *loff, leiden_tuning tn) {
-  // Each warp reads 32 bitmap words at once and visits only the non-zero
-  // ones (a frontier is usually sparse), one vertex per lane.
+  // Each lane reads one bitmap word and sorts its set bits into per-bin
+  // masks; a warp scan over the lanes' counts then places every vertex, so
+  // a warp appends the vertices of its 32 words in id order with one atomic
+  // per bin, however sparse the frontier is.  The bits taken are cleared
+  // with one write per word (each word belongs to one lane here).
   int lane = threadIdx.x & 31;
   int64_t nwords = (n + 31) >> 5;
   int64_t warp = ld_gtid() >> 5, nwarps = ld_gstride() >> 5;
-  for (int64_t w0 = warp * 32; w0 < nwords; w0 += nwarps * 32) {
-    uint32_t word = w0 + lane < nwords ? unproc[w0 + lane] : 0u;
-    uint32_t nz = __ballot_sync(LD_FULL, word != 0u);
-    while (nz) {
-      int src = __ffs(nz) - 1;
-      nz &= nz - 1;
-      uint32_t wd = __shfl_sync(LD_FULL, word, src);
-      int64_t v = ((w0 + src) << 5) + lane;
-      // batched handles: the class of a vertex is taken on its id within its
-      // graph, and graphs whose iterations ended are skipped
-      int64_t vl = v < n && gid ? v - loff[gid[v]] : v;
-      bool take = v < n && ((wd >> lane) & 1u) && ld_class_of(vl, classes_mask) == cls &&
-                  (!gid || lm_on[gid[v]]);
-      uint32_t taken = __ballot_sync(LD_FULL, take);
-      if (lane == 0 && taken) atomicAnd(&unproc[w0 + src], ~taken);
-      bool work = take && (!in_range || in_range[v]);
-      int bin = -1;
-      if (work) {
-        // a vertex without arcs has no candidate community: taking it is its visit
-        int dg = deg[v];
-        bin = dg == 0 ? -1 : dg <= tn.tiny_max ? BIN_TINY : dg <= tn.warp_max ? BIN_WARP : dg <= tn.block_max ? BIN_BLOCK : BIN_HUGE;
-      }
+  for (int64_t w0 = warp * 32; w0 < nwords; w0 += nwarps * 32) {  // warp-uniform
+    int64_t wi = w0 + lane;
+    uint32_t word = wi < nwords ? unproc[wi] : 0u, rest = word, taken = 0u;
+    uint32_t bm[NBINS];
 #pragma unroll
-      for (int b = 0; b < NBINS; b++) {
-        uint32_t m = __ballot_sync(LD_FULL, bin == b);
-        if (!m) continue;
-        int32_t pos0 = 0;
-        if (lane == __ffs(m) - 1) pos0 = atomicAdd(&cnt->bin_count[b], __popc(m));
-        pos0 = __shfl_sync(LD_FULL, pos0, __ffs(m) - 1);
-        if (bin == b) bins[(int64_t)b * n + pos0 + __popc(m & ((1u << lane) - 1u))] = (int32_t)v;
-      }
+    for (int b = 0; b < NBINS; b++) bm[b] = 0u;
+    while (rest) {
+      int bit = __ffs(rest) - 1;
+      rest &= rest - 1u;
+      int64_t v = (wi << 5) + bit;
+      if (v >= n) break;
+      // batched handles: the class of a vertex is taken on its id within
+      // its graph, and graphs whose iterations ended are skipped
+      int64_t vl = gid ? v - loff[gid[v]] : v;
+      if (ld_class_of(vl, classes_mask) != cls || (gid && !lm_on[gid[v]])) continue;
+      taken |= 1u << bit;
+      if (in_range && !in_range[v]) continue;
+      // a vertex without arcs has no candidate community: taking it is its visit
+      int dg = deg[v];
+      if (dg == 0) continue;
+      int bin = dg <= tn.tiny_max ? BIN_TINY : dg <= tn.warp_max ? BIN_WARP : dg <= tn.block_max ? BIN_BLOCK : BIN_HUGE;
+#pragma unroll
+      for (int b = 0; b < NBINS; b++)
+        if (bin == b) bm[b] |= 1u << bit;
     }
+#pragma unroll
+    for (int b = 0; b < NBINS; b++) {
+      int k = __popc(bm[b]), incl = k;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(LD_FULL, incl, o);
+        if (lane >= o) incl += y;
+      }
+      int total = __shfl_sync(LD_FULL, incl, 31);
+      if (total == 0) continue;  // warp-uniform
+      int32_t pos0 = 0;
+      if (lane == 31) pos0 = atomicAdd(&cnt->bin_count[b], total);
+      pos0 = __shfl_sync(LD_FULL, pos0, 31) + incl - k;
+      int32_t *dst = bins + (int64_t)b * n + pos0;
+      for (uint32_t m = bm[b]; m; m &= m - 1u) *dst++ = (int32_t)((wi << 5) + __ffs(m) - 1);
+    }
+    if (taken) unproc[wi] = word & ~taken;
   }
 }
 
@@ -1096,10 +1124,33 @@ void block_kernel_carveout() {
   done.fetch_or(1ull << dev, std::memory_order_relaxed);
 }
 
+// The bins of one sub-sweep (or refinement round) read the same state and
+// write disjoint outputs (deferred moves through one atomic counter,
+// frontier bits through atomics), so the block bin and the hub path run on
+// the handle's side streams beside the warp bin, joined before the caller
+// launches anything else: each of these kernels is bound by the latency of
+// its gathers and leaves most of the GPU idle in its tail.
 template <int KIND>
 void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
   cudaStream_t s = h->stream;
   int sms = h->sm_count;
+  bool need_block = g.maxdeg > h->tune.warp_max, need_hub = g.maxdeg > h->tune.block_max;
+  // tables for every listed hub at once: at most huge_slots slots (taken
+  // before the fork: growing them synchronises and frees)
+  if (need_hub && !ensure_hslots(h, g.huge_slots)) {
+    h->fatal = LEIDEN_ERR_OOM;
+    h->err = "global table scratch";
+    return;
+  }
+  // (the in-place mode keeps the bins in order: there a bin's moves are
+  // seen by the bins launched after it)
+  bool fork = h->tune.overlap && h->p.deterministic && (need_block || need_hub) && side_streams(h);
+  cudaStream_t sblock = s, shub = s;
+  if (fork) {
+    cudaEventRecord(h->fork_ev, s);
+    if (need_block) { sblock = h->side[0]; cudaStreamWaitEvent(sblock, h->fork_ev, 0); }
+    if (need_hub) { shub = h->side[1]; cudaStreamWaitEvent(shub, h->fork_ev, 0); }
+  }
   A.list_tiny = h->bins + (int64_t)BIN_TINY * g.n;
   A.count_tiny = &h->dcnt->bin_count[BIN_TINY];
   for (int b = 0; b < NBINS; b++) {
@@ -1119,31 +1170,60 @@ void launch_bins(leiden_handle *h, const LevelGraph &g, Args A) {
       // for 128 threads admit 7, with the carveout set to favour shared memory
       block_kernel_carveout();
       int grid = sms * h->tune.block_blocks_per_sm;
-      if (KIND == KIND_MOVE) kt_begin(h, KT_BLOCK);
-      if (g.w64) ld_note_launch(), k_decide_block<int64_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
-      else ld_note_launch(), k_decide_block<int32_t, KIND><<<grid, BLOCK_THREADS, 0, s>>>(A);
-      if (KIND == KIND_MOVE) kt_end(h);
+      if (KIND == KIND_MOVE) kt_begin(h, KT_BLOCK, sblock);
+      if (g.w64) ld_note_launch(), k_decide_block<int64_t, KIND><<<grid, BLOCK_THREADS, 0, sblock>>>(A);
+      else ld_note_launch(), k_decide_block<int32_t, KIND><<<grid, BLOCK_THREADS, 0, sblock>>>(A);
+      if (KIND == KIND_MOVE) kt_end(h, sblock);
     } else {
-      // tables for every listed vertex at once: at most huge_slots slots
-      if (!ensure_hslots(h, g.huge_slots)) { h->fatal = LEIDEN_ERR_OOM; h->err = "global table scratch"; return; }
       A.gkeys = hs_keys(h);
       A.gvals = hs_vals(h);
       A.glist = hs_list(h);
       A.gocc = h->hocc;
       int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
-      launch_table_plan(A.list, A.count, g.deg, nullptr, g.n, tab_off, ch_off, s);  // keys: communities of the level
-      ld_note_launch(), k_huge_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
-      if (KIND == KIND_MOVE) kt_begin(h, KT_HUGE_SCAN);
+      launch_table_plan(A.list, A.count, g.deg, nullptr, g.n, tab_off, ch_off, shub);  // keys: communities of the level
+      ld_note_launch(), k_huge_zero_occ<<<sms, 256, 0, shub>>>(A.count, A.gocc);
+      if (KIND == KIND_MOVE) kt_begin(h, KT_HUGE_SCAN, shub);
       int hg = sms * h->tune.hub_blocks_per_sm;
-      if (g.w64) ld_note_launch(), k_huge_scan<int64_t, KIND><<<hg, 256, 0, s>>>(A, tab_off, ch_off);
-      else ld_note_launch(), k_huge_scan<int32_t, KIND><<<hg, 256, 0, s>>>(A, tab_off, ch_off);
-      if (KIND == KIND_MOVE) kt_end(h);
-      ld_note_launch(), k_huge_decide<KIND><<<sms * 8, HUGE_THREADS, 0, s>>>(A, tab_off);
+      if (g.w64) ld_note_launch(), k_huge_scan<int64_t, KIND><<<hg, 256, 0, shub>>>(A, tab_off, ch_off);
+      else ld_note_launch(), k_huge_scan<int32_t, KIND><<<hg, 256, 0, shub>>>(A, tab_off, ch_off);
+      if (KIND == KIND_MOVE) kt_end(h, shub);
+      ld_note_launch(), k_huge_decide<KIND><<<sms * 8, HUGE_THREADS, 0, shub>>>(A, tab_off);
+    }
+  }
+  if (fork) {
+    for (int k = 0; k < 2; k++) {
+      if ((k == 0 && !need_block) || (k == 1 && !need_hub)) continue;
+      cudaEventRecord(h->join_ev[k], h->side[k]);
+      cudaStreamWaitEvent(s, h->join_ev[k], 0);
     }
   }
 }
 
 }  // namespace
+
+// The side streams and events of a handle, created on first use; false
+// (and the bins stay on the handle's stream) if they cannot be had.
+bool side_streams(leiden_handle *h) {
+  if (h->side[1]) return true;
+  if (h->side_failed) return false;
+  bool ok = cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; k < 2 && ok; k++)
+    ok = cudaStreamCreateWithFlags(&h->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&h->join_ev[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    for (int k = 0; k < 2; k++) {
+      if (h->side[k]) cudaStreamDestroy(h->side[k]);
+      if (h->join_ev[k]) cudaEventDestroy(h->join_ev[k]);
+      h->side[k] = nullptr;
+      h->join_ev[k] = nullptr;
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    h->fork_ev = nullptr;
+    h->side_failed = true;
+  }
+  return ok;
+}
 
 // Global table scratch of `slots` slots laid out as keys int32[S] | values
 // int64[S] | slot lists int32[S] (16 B per slot).  Every user leaves the

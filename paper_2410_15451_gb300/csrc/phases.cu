@@ -264,28 +264,84 @@ __global__ void k_count_roots(int64_t n, const int32_t *C, DevCounters *cnt, con
 }
 
 // ---------------------------------------------------------------- Alg. leidenag
-__global__ void k_member_count(int64_t n, const int32_t *C, int32_t *cnt_c) {
+// Members per community.  Lanes of a warp in one community are counted
+// with one atomic; a block then sums its warps' counts in a small shared
+// table before the global counters: a giant community has members in every
+// warp, and one atomic per warp on its counter would serialise on one word.
+// A community whose table slot another community holds goes straight to
+// the global counter.
+constexpr int MEMBER_SLOTS = 256;
+
+__device__ __forceinline__ int32_t member_claim(int32_t *hk, int32_t c) {
+  int s = (int)(ld_hash32((uint32_t)c) & (MEMBER_SLOTS - 1));
+  int32_t k = hk[s];
+  if (k == -1) {
+    int32_t old = atomicCAS(&hk[s], -1, c);
+    k = old == -1 ? c : old;
+  }
+  return k == c ? s : -1;
+}
+
+__global__ void __launch_bounds__(256) k_member_count(int64_t n, const int32_t *C, int32_t *cnt_c) {
+  __shared__ int32_t hk[MEMBER_SLOTS], hv[MEMBER_SLOTS];
+  for (int s = threadIdx.x; s < MEMBER_SLOTS; s += blockDim.x) { hk[s] = -1; hv[s] = 0; }
+  __syncthreads();
   int lane = threadIdx.x & 31;
   for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {
     int64_t i = base + lane;
     int32_t c = i < n ? C[i] : -1 - lane;
     uint32_t peers = __match_any_sync(LD_FULL, c);
-    if (i < n && ld_group_leader(peers)) atomicAdd(&cnt_c[c], __popc(peers));
+    if (i < n && ld_group_leader(peers)) {
+      int s = member_claim(hk, c);
+      if (s >= 0) atomicAdd(&hv[s], __popc(peers));
+      else atomicAdd(&cnt_c[c], __popc(peers));
+    }
   }
+  __syncthreads();
+  for (int s = threadIdx.x; s < MEMBER_SLOTS; s += blockDim.x)
+    if (hk[s] != -1) atomicAdd(&cnt_c[hk[s]], hv[s]);
 }
+
 // cursor[c] starts at coff[c]; each member takes the next slot of its
-// community.  Lanes of a warp in the same community claim their slots with
-// one atomic (giant communities would otherwise serialise on one cursor);
-// the order of members within a community does not matter downstream.
-__global__ void k_member_fill(int64_t n, const int32_t *C, unsigned long long *cursor, int32_t *cverts) {
+// community (the order of members within a community does not matter
+// downstream).  As in the count, a block first counts its members of the
+// communities that hold a shared slot, takes their ranges with one atomic
+// each, then places them from shared cursors; the others take their slots
+// from the global cursor, one atomic per group of lanes.  Both sweeps of a
+// block visit the same vertices.
+__global__ void __launch_bounds__(256) k_member_fill(int64_t n, const int32_t *C, unsigned long long *cursor,
+                                                     int32_t *cverts) {
+  __shared__ int32_t hk[MEMBER_SLOTS], hv[MEMBER_SLOTS];
+  __shared__ unsigned long long hb[MEMBER_SLOTS];
+  for (int s = threadIdx.x; s < MEMBER_SLOTS; s += blockDim.x) { hk[s] = -1; hv[s] = 0; }
+  __syncthreads();
   int lane = threadIdx.x & 31;
+  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {  // warp-uniform trip count
+    int64_t i = base + lane;
+    int32_t c = i < n ? C[i] : -1 - lane;
+    uint32_t peers = __match_any_sync(LD_FULL, c);
+    if (i < n && ld_group_leader(peers)) {
+      int s = member_claim(hk, c);
+      if (s >= 0) atomicAdd(&hv[s], __popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int s = threadIdx.x; s < MEMBER_SLOTS; s += blockDim.x) {
+    if (hk[s] != -1) hb[s] = atomicAdd(&cursor[hk[s]], (unsigned long long)hv[s]);
+    hv[s] = 0;
+  }
+  __syncthreads();
   for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {  // warp-uniform trip count
     int64_t i = base + lane;
     int32_t c = i < n ? C[i] : -1 - lane;
     uint32_t peers = __match_any_sync(LD_FULL, c);
     int leader = __ffs(peers) - 1;
     unsigned long long p0 = 0;
-    if (i < n && lane == leader) p0 = atomicAdd(&cursor[c], (unsigned long long)__popc(peers));
+    if (i < n && lane == leader) {
+      int s = (int)(ld_hash32((uint32_t)c) & (MEMBER_SLOTS - 1));
+      if (hk[s] == c) p0 = hb[s] + (unsigned long long)atomicAdd(&hv[s], __popc(peers));
+      else p0 = atomicAdd(&cursor[c], (unsigned long long)__popc(peers));
+    }
     p0 = __shfl_sync(LD_FULL, p0, leader);
     if (i < n) cverts[(int64_t)p0 + __popc(peers & ((1u << lane) - 1u))] = (int32_t)i;
   }
@@ -347,24 +403,23 @@ struct AggArgs {
   int64_t *tables;    // [0] hashed and [1] directly indexed global tables emitted
 };
 
-// Flat arcs [f0, f1) of community c, processed by `stride` threads.
-template <typename W>
-__device__ __forceinline__ void agg_scan(const AggArgs &A, int64_t c, int t0, int stride, int32_t *keys,
-                                         int64_t *vals, int tmask) {
-  const W *w = (const W *)A.w;
-  int64_t m0 = A.coff[c], m1 = A.coff[c + 1];
-  int64_t f0 = A.cflat[m0], f1 = A.cflat[m1];
-  for (int64_t f = f0 + t0; f < f1; f += stride) {
-    // member t with cflat[t] <= f < cflat[t+1]
-    int64_t lo = m0, hi = m1 - 1;
-    while (lo < hi) {
-      int64_t mid = (lo + hi + 1) >> 1;
-      if (A.cflat[mid] <= f) lo = mid; else hi = mid - 1;
-    }
-    int32_t v = A.cverts[lo];
-    int64_t a = A.off[v] + (f - A.cflat[lo]);
-    agg_insert(keys, vals, tmask, A.C[A.col[a]], (int64_t)w[a]);
+// The members of a community are staged in batches (flat start, and row
+// offset minus flat start), so that each thread finds the member of its
+// flat arc by a search among the staged members and the arcs are spread
+// evenly over the threads whatever the members' degrees.
+constexpr int AGG_MB = 256;
+constexpr int AGG_UNROLL = 4;
+
+// The member k of a staged batch whose arcs hold flat arc f, given
+// ms[0] <= f < ms[nb]: the last k with ms[k] <= f (members without arcs
+// share their start with the next one and are passed over).
+__device__ __forceinline__ int agg_member_of(const int64_t *ms, int nb, int64_t f) {
+  int lo = 0, hi = nb - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (ms[mid] <= f) lo = mid; else hi = mid - 1;
   }
+  return lo;
 }
 
 template <int GROUP>
@@ -389,12 +444,16 @@ constexpr int AGG_WARPS = 8;
 constexpr int AGG_WARP_TABLE = 256;
 constexpr int AGG_BLOCK_TABLE = 2048;
 
+// Communities of at most BIN_WARP_MAX flat arcs, a warp each: the warp
+// holds 32 members at a time in registers (lane i the i-th), and a lane
+// finds the member of its flat arc with five shuffles.
 template <typename W>
 __global__ void __launch_bounds__(AGG_WARPS * 32) k_agg_warp(AggArgs A) {
   __shared__ int32_t skeys[AGG_WARPS][AGG_WARP_TABLE];
   __shared__ int64_t svals[AGG_WARPS][AGG_WARP_TABLE];
   __shared__ int32_t scount[AGG_WARPS];
   __shared__ int64_t ssum[AGG_WARPS];
+  const W *w = (const W *)A.w;
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int64_t count = *A.count;
   for (int64_t t = (int64_t)blockIdx.x * AGG_WARPS + wid; t < count; t += (int64_t)gridDim.x * AGG_WARPS) {
@@ -405,7 +464,48 @@ __global__ void __launch_bounds__(AGG_WARPS * 32) k_agg_warp(AggArgs A) {
     for (int s = lane; s < T; s += 32) { skeys[wid][s] = LD_EMPTY_KEY; svals[wid][s] = 0; }
     if (lane == 0) { scount[wid] = 0; ssum[wid] = 0; }
     __syncwarp();
-    agg_scan<W>(A, c, lane, 32, skeys[wid], svals[wid], T - 1);
+    int64_t m0 = A.coff[c], m1 = A.coff[c + 1];
+    int64_t selfw = 0;  // arcs inside the community: summed in registers, added once
+    for (int64_t ab = m0; ab < m1; ab += 32) {  // warp-uniform
+      int nb = m1 - ab < 32 ? (int)(m1 - ab) : 32;
+      int64_t s = 0, r = 0;
+      if (lane < nb) {
+        s = A.cflat[ab + lane];
+        r = A.off[A.cverts[ab + lane]] - s;
+      }
+      int64_t bs = __shfl_sync(LD_FULL, s, 0), be = A.cflat[ab + nb];
+      for (int64_t R = bs; R < be; R += 32 * AGG_UNROLL) {  // warp-uniform
+        int32_t j[AGG_UNROLL];
+        int64_t wa[AGG_UNROLL];
+        bool valid[AGG_UNROLL];
+#pragma unroll
+        for (int u = 0; u < AGG_UNROLL; u++) {
+          int64_t f = R + u * 32 + lane;
+          valid[u] = f < be;
+          int k = 0;  // last staged member with start <= f (all lanes shuffle)
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            int cand = k + step;
+            int64_t sc = __shfl_sync(LD_FULL, s, cand & 31);
+            if (cand < nb && sc <= f) k = cand;
+          }
+          int64_t row = __shfl_sync(LD_FULL, r, k) + f;
+          j[u] = valid[u] ? A.col[row] : 0;
+          wa[u] = valid[u] ? (int64_t)w[row] : 0;
+        }
+        int32_t cj[AGG_UNROLL];  // the C gathers of all of them in flight together
+#pragma unroll
+        for (int u = 0; u < AGG_UNROLL; u++) cj[u] = valid[u] ? A.C[j[u]] : -1;
+#pragma unroll
+        for (int u = 0; u < AGG_UNROLL; u++) {
+          if (cj[u] == (int32_t)c) selfw += wa[u];
+          else if (valid[u]) agg_insert(skeys[wid], svals[wid], T - 1, cj[u], wa[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) selfw += __shfl_xor_sync(LD_FULL, selfw, o);
+    if (lane == 0 && selfw) agg_insert(skeys[wid], svals[wid], T - 1, (int32_t)c, selfw);
     __syncwarp();
     agg_emit<32>(A, c, lane, 32, skeys[wid], svals[wid], T, &scount[wid], &ssum[wid]);
     __syncwarp();
@@ -414,12 +514,81 @@ __global__ void __launch_bounds__(AGG_WARPS * 32) k_agg_warp(AggArgs A) {
   }
 }
 
+// Communities of at most AGG_TINY flat arcs and AGG_TINY members, eight lanes
+// each (four per warp): lane g holds member g and flat arc g, and equal keys
+// are merged with shuffles inside the group -- no table to clear or scan.
+constexpr int AGG_TINY = 8;
+
+template <typename W>
+__global__ void __launch_bounds__(256) k_agg_tiny(AggArgs A) {
+  const W *w = (const W *)A.w;
+  const int lane = threadIdx.x & 31, g = lane & 7, grp = lane >> 3;
+  const uint32_t gmask = 0xffu << (grp * 8);
+  int64_t count = *A.count;
+  int64_t step = (int64_t)gridDim.x * (blockDim.x >> 5) * 4;  // groups in the grid
+  for (int64_t t0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4; t0 < count;
+       t0 += step) {  // warp-uniform
+    int64_t t = t0 + grp;
+    bool on = t < count;
+    int64_t c = on ? A.list[t] : 0;
+    int64_t m0 = on ? A.coff[c] : 0, nm = on ? A.coff[c + 1] - m0 : 0;
+    int64_t f0 = on ? A.yoff[c] : 0, dg = on ? A.yoff[c + 1] - f0 : 0;  // the super-row and the flat arcs
+    bool mem = g < nm;
+    int64_t s = mem ? A.cflat[m0 + g] : INT64_MAX;  // member g: first flat arc, row of flat 0
+    int64_t row = mem ? A.off[A.cverts[m0 + g]] - s : 0;
+    int64_t f = f0 + g;
+    bool arc = g < dg;
+    int k = 0;  // the last member with first flat arc <= f (all lanes shuffle)
+#pragma unroll
+    for (int d = 4; d > 0; d >>= 1) {
+      int64_t sc = __shfl_sync(LD_FULL, s, k + d, 8);
+      if (sc <= f) k += d;
+    }
+    int64_t rw = __shfl_sync(LD_FULL, row, k, 8) + f;
+    int32_t key = -1;
+    int64_t wv = 0;
+    if (arc) {
+      key = A.C[A.col[rw]];
+      wv = (int64_t)w[rw];
+    }
+    int64_t sum = 0;  // the weight of this lane's key in the group; the first lane holding it emits
+    bool first = arc;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+      int32_t kj = __shfl_sync(LD_FULL, key, j, 8);
+      int64_t wj = __shfl_sync(LD_FULL, wv, j, 8);
+      if (arc && kj == key) {
+        sum += wj;
+        if (j < g) first = false;
+      }
+    }
+    uint32_t fm = __ballot_sync(LD_FULL, first) & gmask;
+    if (first) {
+      int pos = __popc(fm & ((1u << lane) - 1u));
+      A.ycol[f0 + pos] = key;
+      A.yw[f0 + pos] = sum;
+    }
+    int64_t ks = wv;
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) ks += __shfl_xor_sync(LD_FULL, ks, o, 8);
+    if (on && g == 0) {
+      A.ydeg[c] = __popc(fm);
+      A.Kout[c] = ks;
+    }
+  }
+}
+
+// Communities of BIN_WARP_MAX+1..BIN_BLOCK_MAX flat arcs, a block each, with
+// the members staged AGG_MB at a time in shared memory.
 template <typename W>
 __global__ void __launch_bounds__(256) k_agg_block(AggArgs A) {
   __shared__ int32_t keys[AGG_BLOCK_TABLE];
   __shared__ int64_t vals[AGG_BLOCK_TABLE];
+  __shared__ int64_t ms[AGG_MB + 1];
+  __shared__ int64_t mr[AGG_MB];
   __shared__ int32_t rc;
   __shared__ int64_t rs;
+  const W *w = (const W *)A.w;
   int64_t count = *A.count;
   for (int64_t t = blockIdx.x; t < count; t += gridDim.x) {
     int64_t c = A.list[t];
@@ -428,8 +597,48 @@ __global__ void __launch_bounds__(256) k_agg_block(AggArgs A) {
     while (T < 2 * dg) T <<= 1;
     for (int s = threadIdx.x; s < T; s += blockDim.x) { keys[s] = LD_EMPTY_KEY; vals[s] = 0; }
     if (threadIdx.x == 0) { rc = 0; rs = 0; }
-    __syncthreads();
-    agg_scan<W>(A, c, threadIdx.x, blockDim.x, keys, vals, T - 1);
+    int64_t m0 = A.coff[c], m1 = A.coff[c + 1];
+    int64_t selfw = 0;  // arcs inside the community: summed in registers, added once per warp
+    for (int64_t ab = m0; ab < m1; ab += AGG_MB) {  // block-uniform
+      int nb = m1 - ab < AGG_MB ? (int)(m1 - ab) : AGG_MB;
+      __syncthreads();  // the table is cleared and the previous batch has been read
+      if ((int)threadIdx.x < nb) {
+        int64_t s = A.cflat[ab + threadIdx.x];
+        ms[threadIdx.x] = s;
+        mr[threadIdx.x] = A.off[A.cverts[ab + threadIdx.x]] - s;
+      }
+      if (threadIdx.x == 0) ms[nb] = A.cflat[ab + nb];
+      __syncthreads();
+      int64_t be = ms[nb];
+      for (int64_t R = ms[0]; R < be; R += 256 * AGG_UNROLL) {
+        int32_t j[AGG_UNROLL];
+        int64_t wa[AGG_UNROLL];
+        bool valid[AGG_UNROLL];
+#pragma unroll
+        for (int u = 0; u < AGG_UNROLL; u++) {
+          int64_t f = R + u * 256 + threadIdx.x;
+          valid[u] = f < be;
+          j[u] = 0;
+          wa[u] = 0;
+          if (valid[u]) {
+            int64_t row = mr[agg_member_of(ms, nb, f)] + f;
+            j[u] = A.col[row];
+            wa[u] = (int64_t)w[row];
+          }
+        }
+        int32_t cj[AGG_UNROLL];  // the C gathers of all of them in flight together
+#pragma unroll
+        for (int u = 0; u < AGG_UNROLL; u++) cj[u] = valid[u] ? A.C[j[u]] : -1;
+#pragma unroll
+        for (int u = 0; u < AGG_UNROLL; u++) {
+          if (cj[u] == (int32_t)c) selfw += wa[u];
+          else if (valid[u]) agg_insert(keys, vals, T - 1, cj[u], wa[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) selfw += __shfl_xor_sync(LD_FULL, selfw, o);
+    if ((threadIdx.x & 31) == 0 && selfw) agg_insert(keys, vals, T - 1, (int32_t)c, selfw);
     __syncthreads();
     agg_emit<256>(A, c, threadIdx.x, blockDim.x, keys, vals, T, &rc, &rs);
     __syncthreads();
@@ -438,58 +647,55 @@ __global__ void __launch_bounds__(256) k_agg_block(AggArgs A) {
   }
 }
 
-// AGG_UNROLL groups of 32 flat arcs, `gap` apart, from f = g0 + lane: the
-// col and weight loads of all of them, then the C loads, then the inserts
-// into the warp table (flushed to the community's global table when full).
-constexpr int AGG_UNROLL = 4;
 // A table of at least ncomm slots is indexed by the key directly (dense);
 // a smaller one is an open-addressing hash table.
 __device__ __forceinline__ void agg_flush(WarpTable &T8, bool dense, int32_t *keys, int64_t *vals, int32_t *list,
                                           int32_t *occ, int tmask) {
-  if (dense) wt_flush_dense(T8, vals, list, occ);
+  if (dense) wt_flush_dense(T8, keys, vals, list, occ);
   else wt_flush(T8, keys, vals, list, occ, tmask);
-}
-
-template <typename W>
-__device__ __forceinline__ void agg_chunk_step(const AggArgs &A, WarpTable &T8, bool dense, int64_t row, int64_t g0,
-                                               int64_t gap, int64_t s1, int32_t *keys, int64_t *vals, int32_t *list,
-                                               int32_t *occ, int tmask) {
-  const W *w = (const W *)A.w;
-  int lane = threadIdx.x & 31;
-  int32_t j[AGG_UNROLL], c[AGG_UNROLL];
-  int64_t wa[AGG_UNROLL];
-  bool valid[AGG_UNROLL];
-#pragma unroll
-  for (int u = 0; u < AGG_UNROLL; u++) {
-    int64_t f = g0 + u * gap + lane;
-    valid[u] = f < s1;
-    j[u] = valid[u] ? A.col[row + f] : 0;
-    wa[u] = valid[u] ? (int64_t)w[row + f] : 0;
-  }
-#pragma unroll
-  for (int u = 0; u < AGG_UNROLL; u++) {
-    c[u] = valid[u] ? A.C[j[u]] : 0;
-  }
-#pragma unroll
-  for (int u = 0; u < AGG_UNROLL; u++) {
-    if (T8.count > WT_LIMIT) agg_flush(T8, dense, keys, vals, list, occ, tmask);
-    wt_insert_lanes(T8, valid[u], c[u], wa[u]);
-  }
 }
 
 // Communities above BIN_BLOCK_MAX flat arcs: each has its own global table
 // (tab_off) and its flat arcs are cut into chunks any block may take
-// (ch_off); the filled slots are listed so the emission visits only them.
+// (ch_off).  Each warp of the block takes an eighth of the chunk on its own
+// (no block barrier, so no warp waits for another): it finds the member
+// holding its first arc with a 32-way search over the members' flat
+// offsets, then takes the members 32 at a time, lane i holding member i's
+// arcs clipped to the warp's range; members with at most AGG_SHORT arcs
+// there are walked by their lanes, the others one at a time by the whole
+// warp.  Arcs go into the warp's table, flushed into the community's
+// global table when full; arcs inside the community are summed in
+// registers and added once per warp, and the weight sum goes to the
+// super-vertex's K.
+constexpr int AGG_SHORT = 16;  // at most this many arcs in range: a lane walks the member's row
+constexpr int AGG_SPAN = TABLE_CHUNK / 8;  // flat arcs of one warp in a chunk
+
 template <typename W>
-__global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t *tab_off, const int64_t *ch_off) {
-  __shared__ WarpTable WT[8];  // per-warp sums by community, flushed into the global table
-  __shared__ int64_t longm[TABLE_CHUNK / 256 + 1];  // members with a long segment in the chunk
-  __shared__ int nlong;
+__device__ __forceinline__ void agg_take(const AggArgs &A, WarpTable &T8, bool dense, int32_t *keys, int64_t *vals,
+                                         int32_t *list, int32_t *occ, int tmask, int32_t self, const bool *valid,
+                                         const int32_t *j, const int64_t *wa, int64_t &ksum, int64_t &selfw) {
+  int32_t cc[AGG_UNROLL];
+#pragma unroll
+  for (int u = 0; u < AGG_UNROLL; u++) cc[u] = valid[u] ? A.C[j[u]] : 0;
+#pragma unroll
+  for (int u = 0; u < AGG_UNROLL; u++) {
+    bool own = valid[u] && cc[u] == self;
+    ksum += wa[u];
+    selfw += own ? wa[u] : 0;
+    if (T8.count > WT_LIMIT) agg_flush(T8, dense, keys, vals, list, occ, tmask);
+    wt_insert_lanes(T8, valid[u] && !own, cc[u], wa[u]);
+  }
+}
+
+template <typename W>
+__global__ void __launch_bounds__(256, 3) k_agg_chunk_scan(AggArgs A, const int64_t *tab_off, const int64_t *ch_off) {
+  __shared__ WarpTable WT[8];  // per-warp sums by community
   WarpTable &T8 = WT[threadIdx.x >> 5];
   wt_init(T8);
   int64_t count = *A.count;
   int64_t nch = ch_off[count];
   const W *w = (const W *)A.w;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int64_t t = blockIdx.x; t < nch; t += gridDim.x) {
     int64_t lo = 0, hi = count - 1;  // community k with ch_off[k] <= t < ch_off[k+1]
     while (lo < hi) {
@@ -498,99 +704,173 @@ __global__ void __launch_bounds__(256) k_agg_chunk_scan(AggArgs A, const int64_t
     }
     int64_t c = A.list[lo];
     int64_t m0 = A.coff[c], m1 = A.coff[c + 1];
-    int64_t f0 = A.cflat[m0] + (t - ch_off[lo]) * TABLE_CHUNK;
-    int64_t f1 = A.cflat[m1];
-    if (f0 + TABLE_CHUNK < f1) f1 = f0 + TABLE_CHUNK;
+    int64_t fc = A.cflat[m0] + (t - ch_off[lo]) * TABLE_CHUNK, fe = A.cflat[m1];
+    int64_t f0 = fc + (int64_t)wid * AGG_SPAN, f1 = f0 + AGG_SPAN;  // this warp's arcs
+    if (f1 > fc + TABLE_CHUNK) f1 = fc + TABLE_CHUNK;
+    if (f1 > fe) f1 = fe;
+    if (f0 >= f1) continue;  // warp-uniform: the chunk is short
     int64_t T = tab_off[lo + 1] - tab_off[lo];
     bool dense = T >= A.ncomm;  // every key (a community id) has its own slot
+    int tmask = (int)(T - 1);
     int32_t *keys = A.gkeys + tab_off[lo], *list = A.glist + tab_off[lo];
     int64_t *vals = A.gvals + tab_off[lo];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    // the chunk's first member (one search per chunk), then each warp walks
-    // the members whose arcs meet [f0, f1), a member's arcs at a time
-    int64_t a0 = m0, b0 = m1 - 1;
-    while (a0 < b0) {
-      int64_t mid = (a0 + b0 + 1) >> 1;
-      if (A.cflat[mid] <= f0) a0 = mid; else b0 = mid - 1;
+    int32_t *occ = &A.gocc[lo];
+    // the member holding f0: the last a in [m0, m1) with cflat[a] <= f0,
+    // narrowed 32-fold per step (cflat[a0] <= f0 holds throughout)
+    int64_t a0 = m0, span = m1 - m0;
+    while (span > 1) {  // warp-uniform
+      int64_t step = (span + 31) >> 5;
+      int64_t p = a0 + lane * step;
+      bool le = p < a0 + span && A.cflat[p] <= f0;
+      int k = 31 - __clz(__ballot_sync(LD_FULL, le));
+      a0 += k * step;
+      span = span - k * step < step ? span - k * step : step;
     }
-    if (threadIdx.x == 0) nlong = 0;
-    __syncthreads();
-    // segments of at most 256 arcs: a warp per member; longer ones: listed
-    // and shared by all the block's warps below
-    for (int64_t a = a0 + wid; a < m1; a += nwarps) {  // warp-uniform
-      int64_t fa = A.cflat[a], fb = A.cflat[a + 1];
-      if (fa >= f1) break;
-      int64_t s0 = fa > f0 ? fa : f0, s1 = fb < f1 ? fb : f1;
-      if (s0 >= s1) continue;
-      if (s1 - s0 > 256) {
-        if (lane == 0) longm[atomicAdd(&nlong, 1)] = a;
-        continue;
+    int64_t ksum = 0, selfw = 0;
+    for (int64_t ab = a0; ab < m1; ab += 32) {  // warp-uniform
+      int64_t a = ab + lane;
+      bool in = a < m1;
+      int64_t s = in ? A.cflat[a] : f1;
+      if (__shfl_sync(LD_FULL, s, 0) >= f1) break;  // past this warp's range
+      int64_t e = in ? A.cflat[a + 1] : f1;
+      int64_t cs = s > f0 ? s : f0, ce = e < f1 ? e : f1;
+      int64_t len = ce > cs ? ce - cs : 0, row = 0;
+      if (len > 0) row = A.off[A.cverts[a]] - s;  // row index of flat arc f: row + f
+      bool shrt = len <= AGG_SHORT;
+      int maxs = __reduce_max_sync(LD_FULL, shrt ? (unsigned)len : 0u);
+      for (int jj = 0; jj < maxs; jj += AGG_UNROLL) {  // warp-uniform
+        int32_t j[AGG_UNROLL];
+        int64_t wa[AGG_UNROLL];
+        bool valid[AGG_UNROLL];
+#pragma unroll
+        for (int u = 0; u < AGG_UNROLL; u++) {
+          valid[u] = shrt && jj + u < len;
+          int64_t rw = row + cs + jj + u;
+          j[u] = valid[u] ? A.col[rw] : 0;
+          wa[u] = valid[u] ? (int64_t)w[rw] : 0;
+        }
+        agg_take<W>(A, T8, dense, keys, vals, list, occ, tmask, (int32_t)c, valid, j, wa, ksum, selfw);
       }
-      int64_t row = A.off[A.cverts[a]] - fa;
-      for (int64_t g0 = s0; g0 < s1; g0 += 32 * AGG_UNROLL)
-        agg_chunk_step<W>(A, T8, dense, row, g0, 32, s1, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+      for (uint32_t med = __ballot_sync(LD_FULL, !shrt); med; med &= med - 1u) {  // warp-uniform
+        int src = __ffs(med) - 1;
+        int64_t mcs = __shfl_sync(LD_FULL, cs, src), mce = __shfl_sync(LD_FULL, ce, src);
+        int64_t mrow = __shfl_sync(LD_FULL, row, src);
+        for (int64_t R = mcs; R < mce; R += 32 * AGG_UNROLL) {  // warp-uniform
+          int32_t j[AGG_UNROLL];
+          int64_t wa[AGG_UNROLL];
+          bool valid[AGG_UNROLL];
+#pragma unroll
+          for (int u = 0; u < AGG_UNROLL; u++) {
+            int64_t f = R + u * 32 + lane;
+            valid[u] = f < mce;
+            j[u] = valid[u] ? A.col[mrow + f] : 0;
+            wa[u] = valid[u] ? (int64_t)w[mrow + f] : 0;
+          }
+          agg_take<W>(A, T8, dense, keys, vals, list, occ, tmask, (int32_t)c, valid, j, wa, ksum, selfw);
+        }
+      }
     }
-    __syncthreads();
-    for (int q = 0; q < nlong; q++) {
-      int64_t a = longm[q], fa = A.cflat[a], fb = A.cflat[a + 1];
-      int64_t s0 = fa > f0 ? fa : f0, s1 = fb < f1 ? fb : f1;
-      int64_t row = A.off[A.cverts[a]] - fa;
-      for (int64_t g0 = s0 + 32 * wid; g0 < s1; g0 += 32 * nwarps * AGG_UNROLL)  // warp-uniform
-        agg_chunk_step<W>(A, T8, dense, row, g0, 32 * nwarps, s1, keys, vals, list, &A.gocc[lo], (int)(T - 1));
+    agg_flush(T8, dense, keys, vals, list, occ, tmask);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ksum += __shfl_xor_sync(LD_FULL, ksum, o);
+      selfw += __shfl_xor_sync(LD_FULL, selfw, o);
     }
-    agg_flush(T8, dense, keys, vals, list, &A.gocc[lo], (int)(T - 1));
-    if (threadIdx.x == 0)  // per flat arc: col, C of the neighbour and the weight
+    if (lane == 0) {
+      if (ksum != 0) atomicAdd((unsigned long long *)&A.Kout[c], (unsigned long long)ksum);
+      if (selfw != 0) {
+        if (dense) ld_gtable_add_direct(keys, vals, list, occ, (int32_t)c, selfw);
+        else ld_gtable_insert(keys, vals, list, occ, tmask, (int32_t)c, selfw);
+      }
+      // per flat arc: col, C of the neighbour and the weight
       atomicAdd((unsigned long long *)A.xk_bytes, (unsigned long long)((8 + sizeof(W)) * (f1 - f0)));
-    __syncthreads();  // nlong and longm are rewritten by the next chunk
+    }
   }
 }
 
-__global__ void __launch_bounds__(1024) k_agg_list_emit(AggArgs A, const int64_t *tab_off) {
-  __shared__ int32_t rc;
-  __shared__ int64_t rs;
+// Emission of the chunked path: a community's listed slots are cut into
+// EMIT_CHUNK pieces any block may take; em_off[k] is the first piece of the
+// k-th listed community (every community has at least one, which also
+// writes its degree).
+constexpr int EMIT_CHUNK = 2048;
+
+__global__ void __launch_bounds__(1024) k_emit_plan(const int32_t *count_p, const int32_t *occ, int64_t *em_off) {
+  __shared__ int64_t ws[32];
+  __shared__ int64_t carry;
+  int64_t count = *count_p;
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < count; base += blockDim.x) {  // block-uniform
+    int64_t k = base + threadIdx.x;
+    int64_t x = k < count ? (occ[k] > 0 ? (occ[k] + EMIT_CHUNK - 1) / EMIT_CHUNK : 1) : 0;
+    int64_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(LD_FULL, incl, o);
+      if (lane >= o) incl += y;
+    }
+    if (lane == 31) ws[wid] = incl;
+    __syncthreads();
+    int64_t before = carry;
+    for (int q = 0; q < wid; q++) before += ws[q];
+    if (k < count) em_off[k] = before + incl - x;
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) carry = before + incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) em_off[count] = carry;
+}
+
+__global__ void __launch_bounds__(256) k_agg_list_emit(AggArgs A, const int64_t *tab_off, const int64_t *em_off) {
   int64_t count = *A.count;
-  for (int64_t k = blockIdx.x; k < count; k += gridDim.x) {
+  int64_t npc = em_off[count];
+  for (int64_t t = blockIdx.x; t < npc; t += gridDim.x) {
+    int64_t k = 0, hi = count - 1;  // community k with em_off[k] <= t < em_off[k+1]
+    while (k < hi) {
+      int64_t mid = (k + hi + 1) >> 1;
+      if (em_off[mid] <= t) k = mid; else hi = mid - 1;
+    }
     int64_t c = A.list[k];
     int32_t *keys = A.gkeys + tab_off[k], *list = A.glist + tab_off[k];
     int64_t *vals = A.gvals + tab_off[k];
-    int32_t occ = A.gocc[k];
+    int64_t occ = A.gocc[k];
     bool dense = tab_off[k + 1] - tab_off[k] >= A.ncomm;  // the list holds the keys themselves
-    if (threadIdx.x == 0) {
-      rc = 0;
-      rs = 0;
+    int64_t q0 = (t - em_off[k]) * EMIT_CHUNK, q1 = q0 + EMIT_CHUNK < occ ? q0 + EMIT_CHUNK : occ;
+    int64_t base = A.yoff[c];
+    for (int64_t q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+      int32_t s = list[q];
+      int32_t key = dense ? s : keys[s];
+      keys[s] = LD_EMPTY_KEY;
+      A.ycol[base + q] = key;
+      A.yw[base + q] = vals[s];
+      vals[s] = 0;
+    }
+    if (q0 == 0 && threadIdx.x == 0) {
+      A.ydeg[c] = (int32_t)occ;
       atomicAdd((unsigned long long *)&A.tables[dense ? 1 : 0], 1ull);
     }
-    __syncthreads();
-    int64_t base = A.yoff[c];
-    for (int32_t t = threadIdx.x; t < occ; t += blockDim.x) {
-      int32_t s = list[t];
-      int32_t key = dense ? s : keys[s];
-      int64_t v = vals[s];
-      keys[s] = LD_EMPTY_KEY;
-      vals[s] = 0;
-      int32_t p = atomicAdd(&rc, 1);
-      A.ycol[base + p] = key;
-      A.yw[base + p] = v;
-      atomicAdd((unsigned long long *)&rs, (unsigned long long)v);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) { A.ydeg[c] = rc; A.Kout[c] = rs; }
-    __syncthreads();
   }
 }
 
-__global__ void k_zero_occ(const int32_t *count_p, int32_t *occ) {
-  for (int64_t k = ld_gtid(); k < *count_p; k += ld_gstride()) occ[k] = 0;
+// Before the chunked scan: empty fill counts, and zero the K of the listed
+// communities (the scan adds its chunks' weight sums into it).
+__global__ void k_zero_occ(const int32_t *count_p, const int32_t *list, int32_t *occ, int64_t *Kout) {
+  for (int64_t k = ld_gtid(); k < *count_p; k += ld_gstride()) {
+    occ[k] = 0;
+    Kout[list[k]] = 0;
+  }
 }
 
-__global__ void k_agg_bin(int64_t ncomm, const int64_t *yoff, int32_t *bins, DevCounters *cnt) {
+__global__ void k_agg_bin(int64_t ncomm, const int64_t *yoff, const int64_t *coff, int32_t *bins, DevCounters *cnt) {
   int lane = threadIdx.x & 31;
   for (int64_t base = (ld_gtid() & ~31ll); base < ncomm; base += ld_gstride()) {
     int64_t c = base + lane;
     int bin = -1;
     if (c < ncomm) {
       int64_t d = yoff[c + 1] - yoff[c];
-      bin = d <= BIN_WARP_MAX ? BIN_WARP : (d <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE);
+      bin = d <= AGG_TINY && coff[c + 1] - coff[c] <= AGG_TINY ? BIN_TINY
+            : d <= BIN_WARP_MAX ? BIN_WARP : (d <= BIN_BLOCK_MAX ? BIN_BLOCK : BIN_HUGE);
     }
 #pragma unroll
     for (int b = 0; b < NBINS; b++) {
@@ -748,7 +1028,7 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
   cudaMemsetAsync(&h->dcnt->huge_slots, 0, sizeof(int64_t), s);
   ld_note_launch(), k_yoff<<<grid_for(ncomm + 1, TB), TB, 0, s>>>(ncomm, h->coff, h->cflat, h->y_off[out], h->dcnt);
   cudaMemsetAsync(&h->dcnt->bin_count[0], 0, sizeof(int32_t) * 4, s);
-  ld_note_launch(), k_agg_bin<<<grid_for(ncomm, TB), TB, 0, s>>>(ncomm, h->y_off[out], h->bins, h->dcnt);
+  ld_note_launch(), k_agg_bin<<<grid_for(ncomm, TB), TB, 0, s>>>(ncomm, h->y_off[out], h->coff, h->bins, h->dcnt);
   cudaMemcpyAsync(&h->hcnt->max_count, &h->dcnt->max_count, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   cudaMemcpyAsync(&h->hcnt->huge_slots, &h->dcnt->huge_slots, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
   cudaStreamSynchronize(s);
@@ -769,6 +1049,10 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
   A.yw = h->y_w[out];
   A.Kout = h->S2;
   int sms = h->sm_count;
+  A.list = h->bins + (int64_t)BIN_TINY * ncomm;
+  A.count = &h->dcnt->bin_count[BIN_TINY];
+  if (g.w64) ld_note_launch(), k_agg_tiny<int64_t><<<sms * 8, 256, 0, s>>>(A);
+  else ld_note_launch(), k_agg_tiny<int32_t><<<sms * 8, 256, 0, s>>>(A);
   A.list = h->bins;
   A.count = &h->dcnt->bin_count[BIN_WARP];
   if (g.w64) ld_note_launch(), k_agg_warp<int64_t><<<sms * 8, AGG_WARPS * 32, 0, s>>>(A);
@@ -791,14 +1075,16 @@ void aggregate(leiden_handle *h, const LevelGraph &g, int64_t ncomm, int out) {
     int64_t *tab_off = h->lbuf2, *ch_off = h->lbuf3;
     // a community's super-row has at most one key per community
     launch_table_plan(A.list, A.count, nullptr, h->y_off[out], ncomm, tab_off, ch_off, s);
-    ld_note_launch(), k_zero_occ<<<sms, 256, 0, s>>>(A.count, A.gocc);
+    ld_note_launch(), k_zero_occ<<<sms, 256, 0, s>>>(A.count, A.list, A.gocc, A.Kout);
     A.xk_bytes = &h->dcnt->xk_bytes[1];
     A.tables = h->dcnt->agg_tables;
     kt_begin(h, KT_AGG_CHUNK);
     if (g.w64) ld_note_launch(), k_agg_chunk_scan<int64_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
     else ld_note_launch(), k_agg_chunk_scan<int32_t><<<sms * 16, 256, 0, s>>>(A, tab_off, ch_off);
     kt_end(h);
-    ld_note_launch(), k_agg_list_emit<<<sms * 2, 1024, 0, s>>>(A, tab_off);
+    int64_t *em_off = h->lbuf0;  // free again after the member fill
+    ld_note_launch(), k_emit_plan<<<1, 1024, 0, s>>>(A.count, A.gocc, em_off);
+    ld_note_launch(), k_agg_list_emit<<<sms * 8, 256, 0, s>>>(A, tab_off, em_off);
   }
 }
 

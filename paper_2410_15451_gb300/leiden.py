@@ -47,7 +47,7 @@ PHASES = ("batch", "move", "split", "refine", "aggregate", "track")
 
 class leiden_tuning(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int32) for k in ("tiny_max", "warp_max", "block_max", "warp_blocks_per_sm",
-                                              "block_blocks_per_sm", "hub_blocks_per_sm")]
+                                              "block_blocks_per_sm", "hub_blocks_per_sm", "overlap")]
 
 
 class leiden_server_stats(ctypes.Structure):

@@ -127,5 +127,5 @@ def test_footprint_estimate_grows_with_the_graph(lib):
 
 def test_default_tuning(lib):
     t = L.leiden_default_tuning()
-    assert (t.tiny_max, t.warp_max, t.block_max) == (8, 128, 1024)
-    assert ctypes.sizeof(L.leiden_tuning) == 6 * 4
+    assert (t.tiny_max, t.warp_max, t.block_max, t.overlap) == (8, 128, 1024, 1)
+    assert ctypes.sizeof(L.leiden_tuning) == 7 * 4

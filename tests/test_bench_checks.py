@@ -91,7 +91,7 @@ def test_oracle_baseline_runs_in_a_spawned_process():
     assert cb["value"] > 0 and cb["unit"] == "edges/s" and cb["cores"] == 1
     assert "R-MAT scale 13" in cb["sample"] and "batches 2..3" in cb["sample"]
     # the same numbers of batches as the GPU arm draws, hence the same batches
-    assert bench.stream_batches(args) == 2 + 2 * 3 + 2 * (bench.ND_DS_STEPS + 1)
+    assert bench.stream_batches(args) == 2 + 2 * 3 + 2 * (bench.ND_DS_STEPS + 1) + bench.ISO_STEPS
 
 
 def test_ncu_summary_reads_the_capture_csv(tmp_path):

@@ -319,9 +319,11 @@ def test_ablation_switches_bit_exact(flags):
 
 @pytest.mark.parametrize("tuning", [dict(tiny_max=0), dict(tiny_max=4, warp_max=32, block_max=256),
                                     dict(warp_max=64, block_max=512, warp_blocks_per_sm=2, block_blocks_per_sm=3,
-                                         hub_blocks_per_sm=4)], ids=["no-tiny", "small-bins", "mixed"])
+                                         hub_blocks_per_sm=4), dict(overlap=0)],
+                         ids=["no-tiny", "small-bins", "mixed", "one-stream"])
 def test_launch_shapes_do_not_change_results(tuning):
-    """Bin thresholds and grid sizes only move work between kernels."""
+    """Bin thresholds, grid sizes and the side streams only move work
+    between kernels and streams."""
     g = GRAPHS["hubs"]()
     a = L.Leiden(g.n, g.off, g.col, g.w)
     b = L.Leiden(g.n, g.off, g.col, g.w)
@@ -334,6 +336,8 @@ def test_launch_shapes_do_not_change_results(tuning):
         assert a.trace()["passes"] == b.trace()["passes"]
     with pytest.raises(L.LeidenError):
         L.leiden_set_tuning(b.h, warp_max=200)
+    with pytest.raises(L.LeidenError):
+        L.leiden_set_tuning(b.h, overlap=2)
 
 
 def test_full_rebuild_when_the_spill_arena_fills():
