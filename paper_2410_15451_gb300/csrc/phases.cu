@@ -688,7 +688,7 @@ __device__ __forceinline__ void agg_take(const AggArgs &A, WarpTable &T8, bool d
 }
 
 template <typename W>
-__global__ void __launch_bounds__(256, 3) k_agg_chunk_scan(AggArgs A, const int64_t *tab_off, const int64_t *ch_off) {
+__global__ void __launch_bounds__(256, 4) k_agg_chunk_scan(AggArgs A, const int64_t *tab_off, const int64_t *ch_off) {
   __shared__ WarpTable WT[8];  // per-warp sums by community
   WarpTable &T8 = WT[threadIdx.x >> 5];
   wt_init(T8);
@@ -736,35 +736,40 @@ __global__ void __launch_bounds__(256, 3) k_agg_chunk_scan(AggArgs A, const int6
       int64_t cs = s > f0 ? s : f0, ce = e < f1 ? e : f1;
       int64_t len = ce > cs ? ce - cs : 0, row = 0;
       if (len > 0) row = A.off[A.cverts[a]] - s;  // row index of flat arc f: row + f
-      bool shrt = len <= AGG_SHORT;
-      int maxs = __reduce_max_sync(LD_FULL, shrt ? (unsigned)len : 0u);
+      // the member's arcs in range start at col + row + cs (32-bit offsets
+      // from there: a range holds at most AGG_SPAN arcs)
+      const int32_t *mcol = A.col + (row + cs);
+      const W *mw = w + (row + cs);
+      int ln = (int)len;
+      bool shrt = ln <= AGG_SHORT;
+      int maxs = __reduce_max_sync(LD_FULL, shrt ? (unsigned)ln : 0u);
       for (int jj = 0; jj < maxs; jj += AGG_UNROLL) {  // warp-uniform
         int32_t j[AGG_UNROLL];
         int64_t wa[AGG_UNROLL];
         bool valid[AGG_UNROLL];
 #pragma unroll
         for (int u = 0; u < AGG_UNROLL; u++) {
-          valid[u] = shrt && jj + u < len;
-          int64_t rw = row + cs + jj + u;
-          j[u] = valid[u] ? A.col[rw] : 0;
-          wa[u] = valid[u] ? (int64_t)w[rw] : 0;
+          valid[u] = shrt && jj + u < ln;
+          j[u] = valid[u] ? mcol[jj + u] : 0;
+          wa[u] = valid[u] ? (int64_t)mw[jj + u] : 0;
         }
         agg_take<W>(A, T8, dense, keys, vals, list, occ, tmask, (int32_t)c, valid, j, wa, ksum, selfw);
       }
       for (uint32_t med = __ballot_sync(LD_FULL, !shrt); med; med &= med - 1u) {  // warp-uniform
         int src = __ffs(med) - 1;
-        int64_t mcs = __shfl_sync(LD_FULL, cs, src), mce = __shfl_sync(LD_FULL, ce, src);
-        int64_t mrow = __shfl_sync(LD_FULL, row, src);
-        for (int64_t R = mcs; R < mce; R += 32 * AGG_UNROLL) {  // warp-uniform
+        const int32_t *pc = (const int32_t *)__shfl_sync(LD_FULL, (unsigned long long)mcol, src);
+        const W *pw = (const W *)__shfl_sync(LD_FULL, (unsigned long long)mw, src);
+        int n = __shfl_sync(LD_FULL, ln, src);
+        for (int r = 0; r < n; r += 32 * AGG_UNROLL) {  // warp-uniform
           int32_t j[AGG_UNROLL];
           int64_t wa[AGG_UNROLL];
           bool valid[AGG_UNROLL];
 #pragma unroll
           for (int u = 0; u < AGG_UNROLL; u++) {
-            int64_t f = R + u * 32 + lane;
-            valid[u] = f < mce;
-            j[u] = valid[u] ? A.col[mrow + f] : 0;
-            wa[u] = valid[u] ? (int64_t)w[mrow + f] : 0;
+            int x = r + u * 32 + lane;
+            valid[u] = x < n;
+            j[u] = valid[u] ? pc[x] : 0;
+            wa[u] = valid[u] ? (int64_t)pw[x] : 0;
           }
           agg_take<W>(A, T8, dense, keys, vals, list, occ, tmask, (int32_t)c, valid, j, wa, ksum, selfw);
         }
