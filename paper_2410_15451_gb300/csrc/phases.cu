@@ -905,23 +905,52 @@ __global__ void k_bits_all(int64_t n, uint32_t *bm) {
 }
 // Start of the pass loop in one sweep: the affected flags become the
 // frontier bitmap (and are counted), Ctop = identity, C' = C, K' = K,
-// Sigma' = Sigma.
+// Sigma' = Sigma.  Four vertices per thread with 16-byte loads and stores
+// (the arrays start 256-byte aligned); eight lanes make one bitmap word.
+// A tail of n % 32 vertices is done one per lane by the first warp.
 __global__ void k_pass_init(int64_t n, const uint8_t *dV, uint32_t *bm, int32_t *Ctop, const int32_t *C, int32_t *Cp,
                             const int64_t *K, int64_t *Kp, const int64_t *Sig, int64_t *Sp, DevCounters *cnt) {
   int lane = threadIdx.x & 31;
   int64_t set = 0;
-  for (int64_t base = (ld_gtid() & ~31ll); base < n; base += ld_gstride()) {  // warp-uniform trip count
-    int64_t v = base + lane;
+  int64_t nq = (n >> 5) << 3;  // quads of whole 32-vertex words
+  for (int64_t q0 = (ld_gtid() & ~31ll); q0 < nq; q0 += ld_gstride()) {  // warp-uniform trip count
+    int64_t q = q0 + lane;
+    uint32_t nib = 0;
+    if (q < nq) {
+      int64_t v = q << 2;
+      uint32_t f = ((const uint32_t *)dV)[q];
+      nib = (f & 0xffu ? 1u : 0u) | (f & 0xff00u ? 2u : 0u) | (f & 0xff0000u ? 4u : 0u) | (f & 0xff000000u ? 8u : 0u);
+      ((int4 *)Ctop)[q] = make_int4((int)v, (int)v + 1, (int)v + 2, (int)v + 3);
+      ((int4 *)Cp)[q] = ((const int4 *)C)[q];
+      ((longlong2 *)Kp)[2 * q] = ((const longlong2 *)K)[2 * q];
+      ((longlong2 *)Kp)[2 * q + 1] = ((const longlong2 *)K)[2 * q + 1];
+      ((longlong2 *)Sp)[2 * q] = ((const longlong2 *)Sig)[2 * q];
+      ((longlong2 *)Sp)[2 * q + 1] = ((const longlong2 *)Sig)[2 * q + 1];
+    }
+    uint32_t word = nib << ((lane & 7) * 4);  // lanes 8k..8k+7 hold word q/8
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) word |= __shfl_xor_sync(LD_FULL, word, o);
+    if (q < nq && (lane & 7) == 0) {
+      bm[q >> 3] = word;
+      set += __popc(word);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x < 32) {  // the last partial word
+    int64_t v = (nq << 2) + lane;
     bool in = v < n;
     uint32_t m = __ballot_sync(LD_FULL, in && dV[v]);
-    if (lane == 0) { bm[base >> 5] = m; set += __popc(m); }
     if (in) {
       Ctop[v] = (int32_t)v;
       Cp[v] = C[v];
       Kp[v] = K[v];
       Sp[v] = Sig[v];
     }
+    if (lane == 0 && (nq << 2) < n) {
+      bm[nq >> 3] = m;
+      set += __popc(m);
+    }
   }
+  set = ld_warp_sum_i64(set);
   if (lane == 0 && set) atomicAdd((unsigned long long *)&cnt->affected, (unsigned long long)set);
 }
 
