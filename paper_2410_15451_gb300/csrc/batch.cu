@@ -31,10 +31,13 @@ __device__ __forceinline__ int64_t lower_bound_u64(const uint64_t *a, int64_t n,
 }
 
 // Mirror each undirected edge into two arcs keyed (src << vb) | dst and
-// validate it.  error := 1 on any violation.
+// validate it.  error := 1 on any violation.  Deletions and insertions go
+// into one array for one sort: the 2*n_del deletion arcs first (weight 0),
+// then the insertion arcs with bit 2*vb set, so that after the sort the
+// deletions come first and each part is sorted by its keys.
 __global__ void k_expand(const leiden_edge *del, int64_t n_del, const leiden_edge *ins, int64_t n_ins,
-                         int64_t n, int vb, uint64_t *dkey, uint64_t *ikey, int64_t *iw, DevCounters *cnt,
-                         const int32_t *gid0) {
+                         int64_t n, int vb, uint64_t *key, int64_t *w, DevCounters *cnt, const int32_t *gid0) {
+  const uint64_t ins_bit = 1ull << (2 * vb);
   for (int64_t e = ld_gtid(); e < n_del + n_ins; e += ld_gstride()) {
     bool is_del = e < n_del;
     leiden_edge x = is_del ? del[e] : ins[e - n_del];
@@ -46,14 +49,17 @@ __global__ void k_expand(const leiden_edge *del, int64_t n_del, const leiden_edg
     }
     uint64_t k1 = ((uint64_t)x.u << vb) | (uint64_t)x.v;
     uint64_t k2 = ((uint64_t)x.v << vb) | (uint64_t)x.u;
-    if (is_del) {
-      dkey[2 * e] = k1; dkey[2 * e + 1] = k2;
-    } else {
-      int64_t f = e - n_del;
-      ikey[2 * f] = k1; ikey[2 * f + 1] = k2;
-      iw[2 * f] = x.w; iw[2 * f + 1] = x.w;
-    }
+    uint64_t tag = is_del ? 0ull : ins_bit;
+    key[2 * e] = k1 | tag;
+    key[2 * e + 1] = k2 | tag;
+    w[2 * e] = is_del ? 0 : x.w;
+    w[2 * e + 1] = is_del ? 0 : x.w;
   }
+}
+
+// Clear the insertion tag of the sorted insertion arcs.
+__global__ void k_untag(uint64_t *key, int64_t n, uint64_t mask) {
+  for (int64_t i = ld_gtid(); i < n; i += ld_gstride()) key[i] &= mask;
 }
 
 __global__ void k_head_flags(const uint64_t *key, int64_t n, int32_t *flag) {
@@ -615,8 +621,11 @@ cudaError_t ensure_batch(leiden_handle *h, int64_t edges) {
                    (void **)&nb.row_tmp_off, (void **)&nb.row_dst, (void **)&nb.row_newcap, (void **)&nb.row_olddeg,
                    (void **)&nb.row_large, (void **)&nb.row_mid, (void **)&nb.ds_key, (void **)&nb.ds_key_alt,
                    (void **)&nb.ds_w, (void **)&nb.ds_w_alt, (void **)&nb.ds_ukey, (void **)&nb.ds_uw};
-  size_t bytes[] = {8 * (size_t)arcs, 8 * (size_t)arcs, 8 * (size_t)arcs, 8 * (size_t)arcs, 8 * (size_t)arcs,
-                    8 * (size_t)arcs, 8 * (size_t)arcs, 4 * (size_t)(arcs + 1), 8 * (size_t)(arcs + 1),
+  // dkey, dkey_alt, iw and iw_alt hold the deletion and insertion arcs of
+  // one sort together (2 * arcs); ikey, ikey_alt and iw_alt's unique part
+  // at most one kind
+  size_t bytes[] = {16 * (size_t)arcs, 16 * (size_t)arcs, 8 * (size_t)arcs, 8 * (size_t)arcs, 16 * (size_t)arcs,
+                    16 * (size_t)arcs, 8 * (size_t)arcs, 4 * (size_t)(arcs + 1), 8 * (size_t)(arcs + 1),
                     4 * (size_t)arcs, 8 * (size_t)arcs, 4 * (size_t)rows, 4 * (size_t)rows, 4 * (size_t)rows,
                     4 * (size_t)rows, 4 * (size_t)rows, 8 * (size_t)(rows + 1), 8 * (size_t)(rows + 1),
                     8 * (size_t)(rows + 1), 4 * (size_t)(rows + 1), 4 * (size_t)(rows + 1), 4 * (size_t)(rows + 1),
@@ -745,17 +754,21 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   DevCounters *cnt = h->dcnt;
   if (ensure_batch(h, std::max(n_del, n_ins)) != cudaSuccess) return fail(h, LEIDEN_ERR_OOM, "batch buffers");
   int64_t nda = 2 * n_del, nia = 2 * n_ins;
-  if (ensure_scan_tmp(h, std::max(sort_tmp_bytes(std::max(nda, nia)), scan_tmp_bytes(n + 1))) != cudaSuccess)
+  if (ensure_scan_tmp(h, std::max(sort_tmp_bytes(nda + nia), scan_tmp_bytes(n + 1))) != cudaSuccess)
     return fail(h, LEIDEN_ERR_OOM, "scan tmp");
   cudaMemsetAsync(&cnt->error, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&cnt->overflow, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&cnt->large_count, 0, sizeof(int32_t), s);
   cudaMemsetAsync(&cnt->mid_count, 0, sizeof(int32_t), s);
+  // one sort of both: the deletion arcs sorted in dkey[0, nda), the
+  // insertion arcs and their weights in dkey, iw [nda, nda + nia)
   if (n_del + n_ins > 0)
-    ld_note_launch(), k_expand<<<grid_for(n_del + n_ins, TB), TB, 0, s>>>(d_del, n_del, d_ins, n_ins, n, vb, b.dkey, b.ikey,
+    ld_note_launch(), k_expand<<<grid_for(n_del + n_ins, TB), TB, 0, s>>>(d_del, n_del, d_ins, n_ins, n, vb, b.dkey,
                                                                           b.iw, cnt, h->gid0);
-  radix_sort_u64(b.dkey, b.dkey_alt, nullptr, nullptr, nda, 2 * vb, h->scan_tmp, s);
-  radix_sort_u64(b.ikey, b.ikey_alt, b.iw, b.iw_alt, nia, 2 * vb, h->scan_tmp, s);
+  radix_sort_u64(b.dkey, b.dkey_alt, b.iw, b.iw_alt, nda + nia, 2 * vb + 1, h->scan_tmp, s);
+  uint64_t *SD = b.dkey, *SI = b.dkey + nda;
+  int64_t *SIW = b.iw + nda;
+  if (nia > 0) ld_note_launch(), k_untag<<<grid_for(nia, TB), TB, 0, s>>>(SI, nia, (1ull << (2 * vb)) - 1);
   // deduplicate: deletions collapse (-> DK), insertions add up (-> IK, IW).
   // The counts stay on the device until the one host read below: launches
   // are sized by the bounds nda, nia and read the counts themselves.
@@ -764,16 +777,16 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
   uint64_t *DK = b.dkey_alt, *IK = b.ikey_alt;
   int64_t *IW = b.iw_alt, *DW = b.dw;
   if (nda > 0) {
-    ld_note_launch(), k_head_flags<<<grid_for(nda, TB), TB, 0, s>>>(b.dkey, nda, b.flag);
+    ld_note_launch(), k_head_flags<<<grid_for(nda, TB), TB, 0, s>>>(SD, nda, b.flag);
     exclusive_scan_i32_to_i64(b.flag, b.pos, nda, h->scan_tmp, s);
-    ld_note_launch(), k_unique<<<grid_for(nda, TB), TB, 0, s>>>(b.dkey, nullptr, nda, b.flag, b.pos, DK, nullptr);
+    ld_note_launch(), k_unique<<<grid_for(nda, TB), TB, 0, s>>>(SD, nullptr, nda, b.flag, b.pos, DK, nullptr);
     cudaMemcpyAsync(counts + 0, b.pos + nda, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   }
   if (nia > 0) {
-    ld_note_launch(), k_head_flags<<<grid_for(nia, TB), TB, 0, s>>>(b.ikey, nia, b.flag);
+    ld_note_launch(), k_head_flags<<<grid_for(nia, TB), TB, 0, s>>>(SI, nia, b.flag);
     exclusive_scan_i32_to_i64(b.flag, b.pos, nia, h->scan_tmp, s);
     cudaMemsetAsync(IW, 0, (size_t)nia * sizeof(int64_t), s);
-    ld_note_launch(), k_unique<<<grid_for(nia, TB), TB, 0, s>>>(b.ikey, b.iw, nia, b.flag, b.pos, IK, IW);
+    ld_note_launch(), k_unique<<<grid_for(nia, TB), TB, 0, s>>>(SI, SIW, nia, b.flag, b.pos, IK, IW);
     cudaMemcpyAsync(counts + 1, b.pos + nia, sizeof(int64_t), cudaMemcpyDeviceToDevice, s);
   }
   // deletions must exist (stored weight -> DW); insertions: existing or new
@@ -781,7 +794,7 @@ leiden_status batch_apply_and_mark(leiden_handle *h, const leiden_edge *d_del, i
     ld_note_launch(), k_check_deletions<<<grid_for(nda, TB), TB, 0, s>>>(DK, counts + 0, vb, h->g_off, h->g_deg,
                                                                          h->g_col, h->g_w, DW, cnt);
   uint64_t *NK = b.ikey;  // new insertions, compacted in sorted order
-  int64_t *NW = b.iw;
+  int64_t *NW = b.iw;      // (the sorted raw arcs there are consumed by then)
   if (nia > 0) {
     ld_note_launch(), k_classify_insertions<<<grid_for(nia, TB), TB, 0, s>>>(IK, counts + 1, DK, counts + 0, vb,
                                                                              h->g_off, h->g_deg, h->g_col,
