@@ -596,8 +596,13 @@ def ncu_summary(csv_path, command, out_json=TRAFFIC_JSON,
             rd, wr = sum(p["read"] for p in sel), sum(p["write"] for p in sel)
             lm[name] = {"launches": n, "dram_read_bytes_per_launch": rd / n, "dram_write_bytes_per_launch": wr / n,
                         "traffic_bytes_per_launch": (rd + wr) / n, "ncu_us_per_launch": sum(p["us"] for p in sel) / n}
+    warm = "--cache-control none" in command
+    cache_note = ("caches are not flushed between launches (--cache-control none), so a kernel's DRAM bytes are "
+                  "those it moves after the kernels before it, as in the step" if warm else
+                  "caches are flushed before every launch (ncu's default), so DRAM bytes are cold-cache bytes")
     out = {"command": command, "workload": "R-MAT scale 22, DF updates of 1e-3|E| (the benchmark's timed steps)",
-           "note": "one pass per launch (three metrics); ncu times are serialised and cold-cache: compare shares",
+           "note": "one pass per launch (three metrics); ncu serialises the launches, so compare time shares; "
+                   + cache_note,
            "source_sha256": {f: source_code_sha256(os.path.join(CSRC, f)) for f in sorted(os.listdir(CSRC))},
            "local_moving": lm,
            "kernels": {k: {"launches": p["launches"], "ncu_us": p["us"], "share": p["us"] / tot_us,
@@ -608,7 +613,7 @@ def ncu_summary(csv_path, command, out_json=TRAFFIC_JSON,
         json.dump(out, f, indent=1)
     md = ["# Launch list: DF updates on R-MAT scale 22, batches of 1e-3|E|", "",
           "Written by `python bench.py --ncu-summary <csv>` from one capture of the benchmark's timed steps",
-          "(one pass per launch; times are serialised and cold-cache under ncu, so compare shares).", "",
+          "(one pass per launch; ncu serialises the launches, so compare time shares; " + cache_note + ").", "",
           "Command (repository root, one GB300):", "", "    " + command, "",
           f"{len(launches)} launches, {tot_us / 1e3:.2f} ms summed, "
           f"{out['total_dram_bytes'] / 1e6:.1f} MB of DRAM traffic.", "",
