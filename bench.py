@@ -788,6 +788,7 @@ TUNING_SPACE = {
     "warp_blocks_per_sm": (2, 4, 8),
     "block_blocks_per_sm": (2, 4, 7),
     "hub_blocks_per_sm": (4, 8, 16, 32),
+    "overlap": (0, 1),
 }
 
 
