@@ -90,16 +90,27 @@ __global__ void k_trc_insert(int64_t N, const int32_t *Cold, const int32_t *Cnew
     if (!__any_sync(LD_FULL, take)) continue;
     uint32_t peers = __match_any_sync(LD_FULL, (unsigned long long)key);
     int64_t sum = ld_group_sum_i64(peers, kw);
-    if (!take || !ld_group_leader(peers)) continue;
-    uint64_t sl = hash64(key) & mask;
-    for (uint64_t probe = 0; ld_ok(probe <= mask, LD_CHK_PROBE); probe++) {
-      unsigned long long k = atomicCAS((unsigned long long *)&keys[sl], EMPTY64, key);
-      if (k == EMPTY64) list[atomicAdd(occ, 1)] = (int32_t)sl;
-      if (k == EMPTY64 || k == key) {
-        atomicAdd((unsigned long long *)&vals[sl], (unsigned long long)sum);
-        break;
+    // the warp lists the slots it claims with one atomic on occ
+    int32_t claimed = -1;
+    if (take && ld_group_leader(peers)) {
+      uint64_t sl = hash64(key) & mask;
+      for (uint64_t probe = 0; ld_ok(probe <= mask, LD_CHK_PROBE); probe++) {
+        unsigned long long k = atomicCAS((unsigned long long *)&keys[sl], EMPTY64, key);
+        if (k == EMPTY64) claimed = (int32_t)sl;
+        if (k == EMPTY64 || k == key) {
+          atomicAdd((unsigned long long *)&vals[sl], (unsigned long long)sum);
+          break;
+        }
+        sl = (sl + 1) & mask;
       }
-      sl = (sl + 1) & mask;
+    }
+    uint32_t m = __ballot_sync(LD_FULL, claimed >= 0);
+    if (m) {
+      int leader = __ffs(m) - 1;
+      int32_t p0 = 0;
+      if (lane == leader) p0 = atomicAdd(occ, __popc(m));
+      p0 = __shfl_sync(LD_FULL, p0, leader);
+      if (claimed >= 0) list[p0 + __popc(m & ((1u << lane) - 1u))] = claimed;
     }
   }
 }
