@@ -195,13 +195,13 @@ __device__ __forceinline__ void ld_gtable_add_direct(int32_t *keys, int64_t *val
 }
 
 // All 32 lanes, each with up to GT_KEYS keys (has[u]): add them to a global
-// table (`direct`: slot = key; otherwise open addressing as above).  The
-// first probes of all of a lane's keys are read at once, then the empty
-// slots among them claimed, then the weights added, so a flush waits for
-// about two round trips instead of two per key; a collision probes on
-// alone.  The slots claimed by the warp are listed with one atomic on the
-// fill count, which every warp flushing into the same table would
-// otherwise hit once per new key.
+// table (`direct`: slot = key; otherwise open addressing as above).  A key's
+// slot is read first and claimed only when empty; the weight add is not
+// waited for; a collision probes on.  The slots claimed by the warp are
+// listed with one atomic on the fill count, which every warp flushing into
+// the same table would otherwise hit once per new key.  GT_KEYS is 1: with
+// more keys per lane in flight the loops' registers cost the hub scan more
+// occupancy than the overlapped reads gained.
 constexpr int GT_KEYS = 1;
 __device__ __forceinline__ void ld_gtable_add_warp(const bool *has, bool direct, int32_t *keys, int64_t *vals,
                                                    int32_t *list, int32_t *occ, int tmask, const int32_t *c,
