@@ -313,9 +313,13 @@ leiden_status leiden_create_batched(const leiden_params *params, int32_t graphs,
 /* Device bytes a handle for this graph (CSR offsets[n+1]) is expected to
  * hold: the allocations of leiden_create plus an allowance for batch buffers
  * and aggregated-level hash tables that grow on demand.  -1 on bad input.
- * Used by the server below to admit graphs by footprint.  Not included: the
- * arcs of the aggregated levels, which a call draws from the device's
- * stream-ordered memory pool only while it aggregates (see the next). */
+ * Used by the server below to admit graphs by footprint.  The batch buffers
+ * take about 160 B per arc of batch capacity (two arcs per edge, capacity
+ * grown geometrically to at most twice the largest batch); the allowance
+ * (8 B per vertex plus 32 MB) covers batches up to about 50k edges on a
+ * small graph, more on a large one.  Not included: the arcs of the
+ * aggregated levels, which a call draws from the device's stream-ordered
+ * memory pool only while it aggregates (see the next). */
 int64_t leiden_footprint_bytes(const leiden_params *params, int64_t n, const int64_t *offsets);
 
 /* Device bytes a call on this graph draws from the stream-ordered pool while
